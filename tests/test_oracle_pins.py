@@ -1,0 +1,556 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the matrices
+and moment vectors printed in Appendix B, the moment conditions of Appendix A,
+closed-form solutions of the continuum equations the models recover (Secs. 2
+and 3), invariants (conservation, symmetry) and limits of the fluid-solid
+forcing (Sec. 3.4).  None of them runs the CUDA path.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2209_01444_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+C5 = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1]], float)
+C9 = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]], float)
+CS2 = 1.0 / 3.0
+
+
+def _sections(name):
+    out, cur = {}, None
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("["):
+            cur = line.strip("[]")
+            out[cur] = []
+        else:
+            out[cur].append(line)
+    return out
+
+
+def _liquid(nx, ny):
+    f = np.zeros((6, ny, nx))
+    f[0] = -1.0
+    return f
+
+
+# ------------------------------------------------------------- Appendix B
+def test_d2q5_M_is_the_printed_matrix():
+    g = _sections("appendix_b_d2q5.txt")
+    printed = np.array([[float(v) for v in r.split()] for r in g["M"]])
+    np.testing.assert_array_equal(O.lattice_M5(), printed)
+
+
+@pytest.mark.parametrize("s0,s1,s2", [(1.0, 1.3, 1.0), (0.7, 1.55, 1.2), (1.9, 0.4, 0.8)])
+def test_d2q5_lambda_is_the_printed_matrix(s0, s1, s2):
+    g = _sections("appendix_b_d2q5.txt")
+    env = {"s0": s0, "s1": s1, "s2": s2}
+    printed = np.array([[eval(v, {}, env) for v in r.split()] for r in g["Lambda"]])
+    np.testing.assert_allclose(O.lambda5(s0, s1, s2), printed, rtol=0, atol=1e-14)
+
+
+def test_d2q9_M_is_the_printed_matrix():
+    g = _sections("appendix_b_d2q9.txt")
+    printed = np.array([[float(v) for v in r.split()] for r in g["M"]])
+    np.testing.assert_array_equal(O.lattice_M9(), printed)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_flow_equilibrium_moments_are_the_printed_ones(seed):
+    """M h^eq of Eq. (25) equals m_h^eq printed in Eq. (B.3)."""
+    rng = np.random.default_rng(seed)
+    u, v, p, rho0 = rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1), rng.uniform(-0.05, 0.05), rng.uniform(0.5, 2)
+    g = _sections("appendix_b_d2q9.txt")
+    env = {"u": u, "v": v, "p": p, "rho0": rho0}
+    printed = np.array([eval(e, {}, env) for e in g["m_heq"]])
+    np.testing.assert_allclose(O.lattice_M9() @ O.heq(p, u, v, rho0), printed, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_flow_forcing_moments_are_the_printed_ones(seed):
+    """M F^u of Eq. (25) equals m_F printed in Eq. (B.3) with varphi = 0 and
+    the fluid-solid force already weighted by [1 - q~] (Eq. 9b)."""
+    rng = np.random.default_rng(100 + seed)
+    Fx, Fy, fx, fy = rng.uniform(-1e-3, 1e-3, 4)
+    g = _sections("appendix_b_d2q9.txt")
+    env = {"Fx": Fx, "Fy": Fy, "fx": fx, "fy": fy, "u": 0.03, "v": -0.02, "varphi": 0.0}
+    printed = np.array([eval(e, {}, env) for e in g["m_F"]])
+    np.testing.assert_allclose(O.lattice_M9() @ O.F_u(Fx + fx, Fy + fy), printed, rtol=0, atol=1e-17)
+
+
+def test_relaxation_matrices_satisfy_appendix_a_eigen_conditions():
+    """Eq. (A.7a): sum_i Lambda_ij = s0, sum_i c_i Lambda_ij = s1 c_j."""
+    L5 = O.lambda5(0.9, 1.4, 1.1)
+    np.testing.assert_allclose(L5.sum(axis=0), 0.9 * np.ones(5), atol=1e-14)
+    np.testing.assert_allclose(C5.T @ L5, 1.4 * C5.T, atol=1e-14)
+    S9 = np.array([1.0, 1.2, 1.2, 0.7, 0.7, 0.7, 1.3, 1.3, 1.6])
+    L9 = O.lambda9(S9)
+    np.testing.assert_allclose(L9.sum(axis=0), np.ones(9), atol=1e-14)
+    np.testing.assert_allclose(C9.T @ L9, 1.2 * C9.T, atol=1e-14)
+
+
+# ------------------------------------------------------------- Appendix A
+def _moments(v, c):
+    return v.sum(), c.T @ v, np.einsum("i,ia,ib->ab", v, c, c)
+
+
+def test_phase_field_distributions_meet_appendix_a():
+    """Eq. (14) against Eq. (A.7) with A = C = phi, B = 0, S = Q/tau0,
+    J = W0^2 N / tau0, kappa = a_s^2 W0^2/tau0: sum c G = -cs^2 J/kappa."""
+    phi, Q, tau, Nx, Ny, as2 = 0.37, -0.21, 20.0, 0.013, -0.007, 1.08
+    m0, m1, m2 = _moments(O.feq_phi(phi), C5)
+    assert m0 == pytest.approx(phi, abs=1e-15)
+    np.testing.assert_allclose(m1, 0, atol=1e-16)
+    np.testing.assert_allclose(m2, CS2 * phi * np.eye(2), atol=1e-15)
+    F0, F1, _ = _moments(O.F_phi(Q, tau), C5)
+    assert F0 == pytest.approx(Q / tau, abs=1e-16)
+    np.testing.assert_allclose(F1, 0, atol=1e-17)
+    G0, G1, _ = _moments(O.G_phi(Nx, Ny, as2), C5)
+    assert G0 == pytest.approx(0, abs=1e-17)
+    W0sq = 1.0
+    J = W0sq * np.array([Nx, Ny]) / tau
+    kappa = as2 * W0sq / tau
+    np.testing.assert_allclose(G1, -CS2 * J / kappa, atol=1e-16)
+
+
+def test_solute_distributions_meet_appendix_a():
+    """Eq. (19) against Eq. (A.7) with A = C, B = Cu, C_var = q~U,
+    kappa = D(1-k), J = -D(1-k)[U grad q~ + J_at/D] (Eq. 17)."""
+    C, qt, U, ux, uy, D, k = 0.83, 0.4, -0.3, 0.011, -0.004, 0.1, 0.15
+    m0, m1, m2 = _moments(O.neq(C, qt * U, C * ux, C * uy), C5)
+    assert m0 == pytest.approx(C, abs=1e-15)
+    np.testing.assert_allclose(m1, [C * ux, C * uy], atol=1e-16)
+    np.testing.assert_allclose(m2, CS2 * qt * U * np.eye(2), atol=1e-15)
+    dCu = np.array([1e-4, -3e-4])
+    gq = np.array([0.02, -0.05])
+    Jat = np.array([0.003, 0.001])
+    G0, G1, _ = _moments(O.G_C(*dCu, U, *gq, *Jat, D), C5)
+    assert G0 == pytest.approx(0, abs=1e-17)
+    kappa = D * (1 - k)
+    J = -kappa * (U * gq + Jat / D)
+    np.testing.assert_allclose(G1, dCu - CS2 * J / kappa, atol=1e-15)
+
+
+def test_heat_distributions_meet_appendix_a():
+    """Eq. (22) against Eq. (A.7) with A = H = theta - h/2, B = Hu,
+    C_var = theta, J = 0: sum g^eq = H, sum c g^eq = Hu, sum cc g^eq = cs^2 theta I."""
+    theta, hphi, ux, uy = -0.41, 0.6, 0.02, 0.013
+    H = theta - hphi / 2
+    m0, m1, m2 = _moments(O.geq(theta, hphi, H * ux, H * uy), C5)
+    assert m0 == pytest.approx(H, abs=1e-15)
+    np.testing.assert_allclose(m1, [H * ux, H * uy], atol=1e-16)
+    np.testing.assert_allclose(m2, CS2 * theta * np.eye(2), atol=1e-15)
+    G0, G1, _ = _moments(O.G_theta(2e-4, -1e-4), C5)
+    assert G0 == pytest.approx(0, abs=1e-18)
+    np.testing.assert_allclose(G1, [2e-4, -1e-4], atol=1e-18)
+
+
+# ------------------------------------------------------------- anisotropy
+@pytest.mark.parametrize("eps", [0.02, 0.05])
+def test_anisotropy_axis_and_diagonal_values(eps):
+    """Eq. (2): a_s = 1 + eps along the crystal axes, 1 - eps on the diagonals."""
+    for g in [(1, 0), (0, -2), (-0.3, 0)]:
+        assert O.anisotropy(*g, eps)[0] == pytest.approx(1 + eps, abs=1e-15)
+    for g in [(1, 1), (-2, 2), (0.1, -0.1)]:
+        assert O.anisotropy(*g, eps)[0] == pytest.approx(1 - eps, abs=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_anisotropic_vector_is_the_derivative_of_a_s(seed):
+    """Eq. (3): N = |grad phi|^2 a_s d a_s / d(grad phi), checked by central
+    differences of a_s itself, and N . grad phi = 0."""
+    rng = np.random.default_rng(seed)
+    gx, gy = rng.normal(size=2)
+    eps, orient = 0.05, rng.uniform(0, math.pi / 2)
+    a, Nx, Ny = O.anisotropy(gx, gy, eps, orient)
+    h = 1e-6
+    dax = (O.anisotropy(gx + h, gy, eps, orient)[0] - O.anisotropy(gx - h, gy, eps, orient)[0]) / (2 * h)
+    day = (O.anisotropy(gx, gy + h, eps, orient)[0] - O.anisotropy(gx, gy - h, eps, orient)[0]) / (2 * h)
+    g2 = gx * gx + gy * gy
+    np.testing.assert_allclose([Nx, Ny], [g2 * a * dax, g2 * a * day], rtol=1e-7, atol=1e-12)
+    assert abs(Nx * gx + Ny * gy) < 1e-14 * max(1.0, g2)
+
+
+def test_anisotropy_rotates_with_the_grain():
+    """A grain rotated by theta sees a gradient rotated by theta exactly as the
+    unrotated grain sees the original gradient; N rotates with it."""
+    gx, gy, eps = 0.7, -0.25, 0.04
+    a0, N0x, N0y = O.anisotropy(gx, gy, eps, 0.0)
+    for th in (0.3, 0.7, 2.0):
+        c, s = math.cos(th), math.sin(th)
+        a, Nx, Ny = O.anisotropy(c * gx - s * gy, s * gx + c * gy, eps, th)
+        assert a == pytest.approx(a0, abs=1e-14)
+        np.testing.assert_allclose([Nx, Ny], [c * N0x - s * N0y, s * N0x + c * N0y], atol=1e-14)
+
+
+def test_degenerate_gradient_reading():
+    a, Nx, Ny = O.anisotropy(1e-7, 0.0, 0.05)
+    assert (a, Nx, Ny) == (1.0, 0.0, 0.0)
+
+
+# ------------------------------------------------------------- closed forms
+def _mode_amplitude(row, n):
+    return 2 * abs(np.fft.rfft(row)[1]) / n
+
+
+def test_scalar_models_reduce_to_diffusion_in_the_liquid():
+    """With phi = -1 (q~ = 1, Q = 0, N = J_at = 0) and u = 0, Eq. (8) becomes
+    dC/dt = D lap C and dtheta/dt = alpha lap theta: a cosine mode decays as
+    exp(-kappa k^2 t) (lattice diffusivities D = 0.1, alpha = 0.1)."""
+    nx = 64
+    p = W.thermosolutal_params(nx, 4, eps_s=0.0, alpha=4.0)
+    o = O.Oracle(p)
+    f = _liquid(nx, 4)
+    x = np.arange(nx)
+    k = 2 * math.pi / nx
+    f[1] = 0.1 * np.cos(k * x)[None, :]
+    f[2] = -0.5 + 0.1 * np.cos(k * x)[None, :]
+    o.init_fields(f)
+    T = 400
+    o.step(T)
+    F = o.fields()
+    aU = _mode_amplitude(F["U"][0], nx)
+    aT = _mode_amplitude(F["theta"][0], nx)
+    assert aU == pytest.approx(0.1 * math.exp(-0.1 * k * k * T), rel=2e-3)
+    assert aT == pytest.approx(0.1 * math.exp(-0.2 * k * k * T), rel=2e-3)
+    # C = 1 + (1 - k) U in the liquid (Eq. 4a with phi = -1)
+    np.testing.assert_allclose(F["C"], 1 + 0.85 * F["U"], atol=1e-14)
+
+
+def test_scalar_models_advect_with_the_flow():
+    """Uniform velocity u in the liquid: theta(x, t) = theta0 + A e^{-alpha k^2 t}
+    cos(k (x - u t)) (Eq. 8b with the convective term)."""
+    nx = 64
+    p = W.thermosolutal_params(nx, 4, eps_s=0.0)
+    o = O.Oracle(p)
+    lp = o.lattice_params()
+    f = _liquid(nx, 4)
+    u = 0.02
+    f[3] = u / lp["vscale"]
+    x = np.arange(nx)
+    k = 2 * math.pi / nx
+    f[2] = -0.5 + 0.1 * np.cos(k * x)[None, :]
+    f[1] = 0.1 * np.cos(k * x)[None, :]
+    o.init_fields(f)
+    T = 400
+    o.step(T)
+    F = o.fields()
+    for name, kap in (("theta", 0.1), ("U", 0.1)):
+        c1 = np.fft.rfft(F[name][0])[1] * 2 / nx
+        assert abs(c1) == pytest.approx(0.1 * math.exp(-kap * k * k * T), rel=2e-3)
+        assert (-np.angle(c1) / k) == pytest.approx(u * T, abs=0.02)
+    np.testing.assert_allclose(F["ux"], u / lp["vscale"], rtol=1e-12)
+
+
+def test_shear_wave_decays_at_the_viscous_rate():
+    """Eq. (9b) linearised: u_x = A sin(k y) decays as exp(-nu k^2 t), nu = 0.1."""
+    ny = 64
+    p = W.thermosolutal_params(4, ny, eps_s=0.0)
+    o = O.Oracle(p)
+    f = _liquid(4, ny)
+    k = 2 * math.pi / ny
+    f[3] = 0.2 * np.sin(k * np.arange(ny))[:, None]
+    o.init_fields(f)
+    T = 300
+    o.step(T)
+    a = _mode_amplitude(o.fields()["ux"][:, 0], ny)
+    assert a / 0.2 == pytest.approx(math.exp(-0.1 * k * k * T), rel=1e-3)
+
+
+def _poiseuille_error(ny):
+    Fx_lat, nu_paper = 1e-5, 10.0
+    p = W.thermosolutal_params(4, ny, eps_s=0.0, nu=nu_paper, bc=("periodic", "periodic", "noslip", "noslip"))
+    lp = O.Oracle(p).lattice_params()
+    p["force"] = (Fx_lat / lp["fscale"], 0.0)
+    o = O.Oracle(p)
+    o.init_fields(_liquid(4, ny))
+    nul = nu_paper * lp["vscale"]  # dx = 1: lattice viscosity = nu dt
+    o.step(int(6 * (ny - 1) ** 2 / nul))
+    H = ny - 1
+    y = np.arange(ny)
+    exact = Fx_lat / (2 * nul) * y * (H - y)
+    ux = o.fields()["ux"][:, 0] * lp["vscale"]
+    assert abs(ux[0]) < 1e-18 and abs(ux[-1]) < 1e-18
+    return np.abs(ux - exact).max() / exact.max()
+
+
+def test_poiseuille_flow_converges_at_second_order():
+    """Body-force Poiseuille flow between the no-slip walls of the
+    non-equilibrium extrapolation (Sec. 4): u = F y (H - y)/(2 nu), with the
+    error falling as H^-2."""
+    e16, e32 = _poiseuille_error(17), _poiseuille_error(33)
+    assert e16 < 0.05
+    assert e32 < 0.0125
+    assert e16 / e32 == pytest.approx(4.0, rel=0.1)
+
+
+def test_inflow_outflow_channel_becomes_plug_flow():
+    """Liquid channel with the inflow/outflow/symmetry walls of Sec. 4.2,
+    started from rest: once the acoustic transient between the velocity inlet
+    and the pressure outlet has decayed, u = u_in and p = 0 everywhere."""
+    nx, ny = 24, 8
+    p = W.thermosolutal_params(nx, ny, eps_s=0.0, bc=("inflow", "outflow", "symmetry", "symmetry"),
+                               u_in=(0.2, 0.0))
+    o = O.Oracle(p)
+    o.init_fields(_liquid(nx, ny))
+    o.step(20000)
+    F = o.fields()
+    np.testing.assert_allclose(F["ux"], 0.2, rtol=1e-8)
+    np.testing.assert_allclose(F["uy"], 0.0, atol=1e-14)
+    np.testing.assert_allclose(F["p"], 0.0, atol=1e-8)
+
+
+def test_dirichlet_walls_give_the_heat_equation_series_solution():
+    """theta held at theta_w on the Dirichlet walls x = 0 and x = L, initially
+    theta_1 inside: theta = theta_w + (theta_1 - theta_w) sum_odd 4/(m pi)
+    sin(m pi x/L) exp(-alpha (m pi/L)^2 t)."""
+    nx, ny = 41, 4
+    p = W.thermosolutal_params(nx, ny, eps_s=0.0, bc=("dirichlet", "dirichlet", "periodic", "periodic"),
+                               dir_theta=-0.2, dir_phi=-1.0, dir_U=0.0)
+    o = O.Oracle(p)
+    f = _liquid(nx, ny)
+    f[2] = -0.6
+    f[2][:, 0] = f[2][:, -1] = -0.2
+    o.init_fields(f)
+    T = 600
+    o.step(T)
+    th = o.fields()["theta"][1]
+    L = nx - 1
+    x = np.arange(nx)
+    series = sum(4 / (m * math.pi) * np.sin(m * math.pi * x / L) * math.exp(-0.1 * (m * math.pi / L) ** 2 * T)
+                 for m in range(1, 400, 2))
+    exact = -0.2 + (-0.6 + 0.2) * series
+    assert th[0] == pytest.approx(-0.2, abs=1e-14) and th[-1] == pytest.approx(-0.2, abs=1e-14)
+    assert np.abs(th - exact).max() < 2e-3
+
+
+def test_planar_interface_profile_is_stationary():
+    """Eq. (1) with lambda = 0 and eps = 0: phi = tanh(x/(sqrt2 W0)) solves
+    W0^2 phi'' + phi - phi^3 = 0 and must stay put (W0 = 4 lattice nodes)."""
+    nx = 128
+    p = W.thermosolutal_params(nx, 4, eps_s=0.0, lambda_=0.0, dx=0.25, dt=1 / 80)
+    o = O.Oracle(p)
+    x = np.arange(nx)
+    W_lu = 4.0
+    prof = np.tanh((x - 32.5) / (math.sqrt(2) * W_lu)) * -np.tanh((x - 96.5) / (math.sqrt(2) * W_lu))
+    f = _liquid(nx, 4)
+    f[0] = prof[None, :]
+    f[2] = 0.0
+    o.init_fields(f)
+    o.step(400)
+    phi = o.fields()["phi"][0]
+    assert np.abs(phi - prof).max() < 2e-3
+
+
+def _relax_1d_reference(prof0, W_lu, as_, tau, T):
+    """Method-of-lines solution of tau a^2 dphi/dt = W^2 a^2 phi'' + phi - phi^3
+    on a periodic grid refined 4x, integrated by scipy."""
+    from scipy.integrate import solve_ivp
+    r = 4
+    n = prof0.size * r
+    xf = np.arange(n) / r
+    xc = np.arange(prof0.size)
+    phi0 = np.interp(xf, xc, prof0, period=prof0.size)
+    h = 1.0 / r
+
+    def rhs(_, ph):
+        lap = (np.roll(ph, 1) - 2 * ph + np.roll(ph, -1)) / h**2
+        return (W_lu**2 * as_**2 * lap + ph - ph**3) / (tau * as_**2)
+
+    sol = solve_ivp(rhs, (0, T), phi0, method="RK45", rtol=1e-9, atol=1e-11)
+    return sol.y[:, -1][::r]
+
+
+def test_anisotropic_planar_front_relaxes_with_a_s_squared():
+    """A front normal to a crystal axis has a_s = 1 + eps and N = 0, so Eq. (1)
+    reads tau0 a^2 phi_t = W0^2 a^2 phi'' + phi - phi^3; the lattice solution
+    from a too-narrow tanh follows the 1-D method-of-lines solution (this
+    fixes both the a_s^2 on the time derivative, i.e. the modified streaming of
+    Eq. 13, and the a_s^2 in the relaxation rate of Sec. 3.1)."""
+    nx, eps = 128, 0.2
+    p = W.thermosolutal_params(nx, 4, eps_s=eps, lambda_=0.0, dx=0.25, dt=1 / 80)
+    o = O.Oracle(p)
+    lp = o.lattice_params()
+    x = np.arange(nx)
+    prof0 = np.tanh((x - 32.5) / (math.sqrt(2) * 2.5)) * -np.tanh((x - 96.5) / (math.sqrt(2) * 2.5))
+    f = _liquid(nx, 4)
+    f[0] = prof0[None, :]
+    f[2] = 0.0
+    o.init_fields(f)
+    T = 240
+    o.step(T)
+    phi = o.fields()["phi"][0]
+    ref = _relax_1d_reference(prof0, lp["W"], 1 + eps, lp["tau"], T)
+    wrong = _relax_1d_reference(prof0, lp["W"], 1.0, lp["tau"], T)
+    err = np.abs(phi - ref).max()
+    assert err < 4e-3
+    assert np.abs(phi - wrong).max() > 5 * err
+
+
+def test_disc_shrinks_by_curvature():
+    """Eq. (1) with lambda = eps = 0 gives Allen-Cahn motion, V = -W0^2/(tau0 R),
+    so d(R^2)/dt = -2 W0^2/tau0 = -0.4 lattice units (W0 = 4 nodes, tau0 = 80
+    steps); measured on the area of phi > 0 between t = 400 and 1600 with
+    R between 38 and 31 nodes, where the finite-width correction is ~1%."""
+    n, R0 = 128, 40.0
+    p = W.thermosolutal_params(n, n, eps_s=0.0, lambda_=0.0, dx=0.25, dt=1 / 80)
+    o = O.Oracle(p)
+    o.init_seeds([[n / 2, n / 2, R0, 0.0]], 0.0, 0.0)
+    R2 = []
+    for T in (400, 1600):
+        o.step(T - o.steps)
+        R2.append(o.metrics(n / 2, n / 2)["solid_fraction"] * n * n / math.pi)
+    assert (R2[1] - R2[0]) / 1200 == pytest.approx(-2 * 16.0 / 80, rel=0.02)
+
+
+# ------------------------------------------------------------- invariants
+def test_periodic_run_conserves_solute_enthalpy_and_flow_mass():
+    """Periodic walls: sum C and sum H are conserved (sum n^eq = C, sum g^eq = H,
+    sum G = 0) and sum h_i = rho0 per node (s0 = 1)."""
+    nx, ny = 48, 40
+    p = W.thermosolutal_params(nx, ny, gbetaT=W.GBETA_T, gbetaC=W.GBETA_C)
+    o = O.Oracle(p)
+    f, orient = W.random_fields(nx, ny, 7)
+    o.init_fields(f, orient)
+    m0 = o.metrics(0, 0)
+    o.step(200)
+    m1 = o.metrics(0, 0)
+    assert abs(m1["sum_C"] - m0["sum_C"]) < 1e-12 * abs(m0["sum_C"])
+    assert abs(m1["sum_H"] - m0["sum_H"]) < 1e-12 * abs(m0["sum_H"])
+    assert m1["sum_h"] == pytest.approx(nx * ny * 1.0, rel=1e-13)
+    assert m1["nonfinite"] == 0
+
+
+def test_centred_seed_keeps_fourfold_symmetry():
+    """No flow and no buoyancy: a centred seed stays D4-symmetric about the
+    centre node (the scheme has no preferred sign or axis)."""
+    n = 33
+    p = W.thermosolutal_params(n, n, eps_s=0.05)
+    o = O.Oracle(p)
+    o.init_seeds([[16.0, 16.0, 5.0, 0.0]], 0.0, -0.55)
+    o.step(300)
+    F = o.fields()
+    for name in ("phi", "C", "theta"):
+        a = F[name]
+        scale = max(1.0, np.abs(a).max())
+        assert np.abs(a - a.T).max() < 1e-12 * scale
+        assert np.abs(a - a[:, ::-1]).max() < 1e-12 * scale
+        assert np.abs(a - a[::-1, :]).max() < 1e-12 * scale
+    assert np.abs(F["ux"]).max() == 0.0
+
+
+def test_rotated_grain_keeps_quarter_turn_symmetry():
+    """A grain rotated by 0.3 rad loses the mirror symmetries but keeps the
+    90-degree rotation symmetry of cubic anisotropy."""
+    n = 33
+    p = W.thermosolutal_params(n, n, eps_s=0.05)
+    o = O.Oracle(p)
+    o.init_seeds([[16.0, 16.0, 5.0, 0.3]], 0.0, -0.55)
+    o.step(300)
+    phi = o.fields()["phi"]
+    assert np.abs(phi - np.rot90(phi)).max() < 1e-12
+    assert np.abs(phi - phi.T).max() > 1e-6
+
+
+def test_buoyancy_keeps_only_the_vertical_mirror():
+    n = 33
+    p = W.thermosolutal_params(n, n, eps_s=0.05, gbetaT=10 * W.GBETA_T, gbetaC=10 * W.GBETA_C)
+    o = O.Oracle(p)
+    o.init_seeds([[16.0, 16.0, 5.0, 0.0]], 0.0, -0.55)
+    o.step(200)
+    F = o.fields()
+    assert np.abs(F["phi"] - F["phi"][:, ::-1]).max() < 1e-12
+    assert np.abs(F["ux"] + F["ux"][:, ::-1]).max() < 1e-15
+    assert np.abs(F["uy"]).max() > 1e-6
+
+
+# ------------------------------------------------------------- fluid-solid force
+def _uniform(phi_value, u):
+    p = W.thermosolutal_params(6, 6, eps_s=0.0, lambda_=0.0)
+    o = O.Oracle(p)
+    f = np.zeros((6, 6, 6))
+    f[0] = phi_value
+    f[2] = 0.0
+    f[3] = u
+    o.init_fields(f)
+    return o
+
+
+def test_solid_stops_the_flow_in_one_step():
+    """Eq. (26) with f = -u*/dt (u_s = 0) and s1 = 1: inside the solid (phi = 1)
+    the momentum after one collision is zero; the liquid keeps its velocity."""
+    o = _uniform(1.0, 0.3)
+    assert o.fields()["ux"][0, 0] == pytest.approx(0.15, abs=1e-15)  # u = u*(1 + q~)/2
+    o.step(1)
+    assert np.abs(o.fields()["ux"]).max() < 1e-15
+    o = _uniform(-1.0, 0.3)
+    o.step(5)
+    np.testing.assert_allclose(o.fields()["ux"], 0.3, rtol=1e-13)
+
+
+def test_interface_forcing_halves_the_momentum_each_step():
+    """At phi = 0 (q~ = 1/2): u = 3u*/4 and each collision halves u*."""
+    o = _uniform(0.0, 0.4)
+    us = [o.fields()["ux"][0, 0]]
+    for _ in range(3):
+        o.step(1)
+        us.append(o.fields()["ux"][0, 0])
+    np.testing.assert_allclose(us, [0.3, 0.15, 0.075, 0.0375], rtol=1e-12)
+
+
+# ------------------------------------------------------------- state and metrics
+def test_initial_supersaturation_round_trips():
+    """C is built from U0 by inverting Eq. (20); recovering U from C returns U0."""
+    p = W.thermosolutal_params(32, 32)
+    o = O.Oracle(p)
+    o.init_seeds([[16, 16, 6, 0.0]], -0.3, -0.5)
+    F = o.fields()
+    np.testing.assert_allclose(F["U"], -0.3, atol=1e-14)
+    np.testing.assert_allclose(F["theta"], -0.5, atol=1e-14)
+
+
+def test_state_round_trip_is_bit_exact():
+    p = W.thermosolutal_params(20, 16)
+    o = O.Oracle(p)
+    f, orient = W.random_fields(20, 16, 3)
+    o.init_fields(f, orient)
+    o.step(3)
+    st = o.state()
+    o2 = O.Oracle(p)
+    o2.init_fields(f, orient)
+    o2.set_state(st)
+    o.step(4)
+    o2.step(4)
+    np.testing.assert_array_equal(o.state(), o2.state())
+
+
+def test_tip_metric_finds_the_disc_radius():
+    n = 64
+    p = W.thermosolutal_params(n, n)
+    o = O.Oracle(p)
+    o.init_seeds([[32.0, 32.0, 12.3, 0.0]], 0.0, -0.5)
+    m = o.metrics(32.0, 32.0)
+    for k in ("tip_px", "tip_mx", "tip_py"):
+        assert m[k] == pytest.approx(12.3, abs=0.02)
+    m = o.metrics(32.0, 32.0, 0.4)
+    assert m["tip_px"] == pytest.approx(12.3, abs=0.05)
+
+
+def test_voronoi_grain_map():
+    p = W.thermosolutal_params(40, 20)
+    o = O.Oracle(p)
+    o.init_seeds([[5, 10, 3, 0.1], [30, 10, 3, 0.6]], 0.0, -0.5)
+    g = o.orient()
+    assert g[10, 10] == 0.1 and g[10, 25] == 0.6
+    # periodic minimum image: node 37 is 8 nodes from seed 0 across the wrap, 7 from seed 1
+    assert g[10, 37] == 0.6
+    assert g[10, 39] == 0.1  # 6 across the wrap versus 9
