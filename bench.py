@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Throughput of the coupled diffuse-interface MRT lattice Boltzmann step.
+
+One bench step is one coupled time step (phase field, solute, heat and flow,
+plus the wall kernels) over the whole grid of the multi-seed thermosolutal
+workload: 4096 x 4096 nodes, 64 seeds (dart throwing, spacing >= 200, radii
+6-10, orientations in [0, 45 deg), RNG seed 3), Delta = 0.45, eps = 0.04,
+periodic in x, no-slip walls in y, buoyancy on, FP32 populations.  The state
+(about 4 GB) is far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded window of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-LB MLUPS and % of HBM roofline; surrogate speedup at matched tip error"
+UNIT = "MLUPS"
+# Algorithmic HBM bytes per node per coupled step (n_sub = 1): every population
+# read once and written once (24 x 2), the six history scalars read and written
+# (6 x 2), and the one-byte grain id read when the domain holds several grains.
+POP_PLANES, HIST_PLANES = 24, 6
+
+
+def algorithmic_bytes_per_node(storage_bytes: int, grains: bool) -> int:
+    return POP_PLANES * 2 * storage_bytes + HIST_PLANES * 2 * 4 + (1 if grains else 0)
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--n", type=int, default=4096, help="grid side (default: the 4096^2 workload)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage lines")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n: int):
+    from paper_2209_01444_gb300 import workloads as W
+
+    if n == 4096:
+        return W.multi_seed()
+    count = max(1, (n // 512) ** 2)
+    return W.multi_seed(n=n, count=count, min_spacing=min(200.0, n / 4))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lbm_step.cu", "lbm_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2209_01444_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "fused_step_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == key and parts[1] == src:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis:
+        try:
+            return int(vis.split(",")[local_rank])
+        except (ValueError, IndexError):
+            pass
+    return local_rank
+
+
+def cpu_oracle_sample(case, target_s: float = 15.0, side: int = 1024, max_steps: int = 400):
+    """The FP64 oracle on a side x side window of the workload (seeded in the
+    coordinates of the full grid), run for about target_s seconds."""
+    from oracle import oracle as O
+
+    p = dict(case.params)
+    p["nx"] = p["ny"] = side
+    p["bc"] = ("periodic",) * 4
+    o = O.Oracle(p)
+    N = case.params["nx"]
+    x0 = y0 = (N - side) // 2
+    o.init_seeds_window(case.seeds, case.U0, case.theta0, x0, y0, N, case.params["ny"], True, False)
+    t = time.perf_counter()
+    o.step(2)
+    per = (time.perf_counter() - t) / 2
+    n = int(max(3, min(max_steps, target_s / max(per, 1e-6))))
+    t = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": side * side * n / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{side}x{side} window at ({x0},{y0}) of the {N}x{N} workload, {n} coupled steps, "
+                      f"FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores: each step is one coupled
+    step of a square window of the workload, the window sized so that the
+    whole --warmup + --steps run takes about 90 s."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    case = workload(args.n)
+    from oracle import oracle as O
+
+    def window(side):
+        p = dict(case.params)
+        p["nx"] = p["ny"] = side
+        p["bc"] = ("periodic",) * 4
+        o = O.Oracle(p)
+        x0 = (args.n - side) // 2
+        o.init_seeds_window(case.seeds, case.U0, case.theta0, x0, x0, args.n, args.n, True, False)
+        return o
+
+    probe = window(256)
+    t = time.perf_counter()
+    probe.step(3)
+    rate = 256 * 256 * 3 / (time.perf_counter() - t)
+    del probe
+    total = max(args.steps + args.warmup, 1)
+    side = int((90.0 * rate / total) ** 0.5) // 64 * 64
+    side = max(64, min(1024, args.n, side))
+    o = window(side)
+    o.step(max(args.warmup, 0))
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    value = side * side * args.steps / dt / 1e6
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"{side}x{side} window of the {args.n}x{args.n} workload per step, FP64 oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(args.steps, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"multi_seed_thermosolutal_{args.n}x{args.n}", "nodes": side * side,
+                   "sample_window": side},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2209_01444_gb300 import build_ext, lbm
+
+    if not os.path.exists(lbm.LIB_PATH):
+        build_ext.build()
+    lbm.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    case = workload(args.n)
+    nodes = case.nodes
+    stream = torch.cuda.current_stream()
+
+    def timed_run(storage: str, steps: int, warmup: int, clocks: bool):
+        sim = lbm.Simulation(case.params, storage, stream=stream)
+        sim.init_seeds(case.seeds, case.U0, case.theta0)
+        sim.step(warmup)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(gpu_index(local)) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        m = sim.metrics(case.seeds[0][0], case.seeds[0][1], case.seeds[0][3], check=False)
+        return sim, ms, (sampler.summary() if sampler else None), m
+
+    sim, ms, clk, m = timed_run(args.storage, args.steps, max(args.warmup, 3), clocks=True)
+    if m["nonfinite"]:
+        raise RuntimeError("non-finite state after the timed run")
+    value = world * nodes * args.steps / (ms / 1e3) / 1e6
+
+    # fused-kernel time from CUDA events on the launching stream
+    sim.set_profiling(True)
+    kp = min(200, max(20, args.steps // 10))
+    sim.step(kp)
+    kms, launches = sim.kernel_time()
+    sim.set_profiling(False)
+    k_avg_ms = kms / max(launches, 1)
+    sb = 4 if args.storage == "fp32" else 2
+    grains = len(case.seeds) > 1
+    bpn = algorithmic_bytes_per_node(sb, grains)
+    achieved = bpn * nodes / (k_avg_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = recorded_traffic(f"multi_seed_{args.n}_{args.storage}")
+
+    # end to end through the C ABI from pinned host memory: load the initial
+    # state, run the steps, read the fields back
+    fresh = lbm.Simulation(case.params, args.storage, stream=stream)
+    fresh.init_seeds(case.seeds, case.U0, case.theta0)
+    blob = fresh.save()
+    del fresh
+    pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[:] = memoryview(blob)
+    e2e_steps = args.steps
+    e2e_sim = lbm.Simulation(case.params, args.storage, stream=stream)
+    names = ("phi", "C", "theta", "ux", "uy")
+    import ctypes as ct
+
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    rc = e2e_sim.lib.lbm_load_state(e2e_sim.h, ct.c_void_p(pinned.data_ptr()), len(blob))
+    if rc:
+        raise RuntimeError(e2e_sim.lib.lbm_last_error(e2e_sim.h).decode())
+    e2e_sim.step(e2e_steps)
+    out = e2e_sim.fields(names)
+    t1 = time.perf_counter()
+    barrier()
+    e2e_s = max_over_ranks(t1 - t0)
+    e2e_value = world * nodes * e2e_steps / e2e_s / 1e6
+    # lbm_get_fields copies the seven FP32 macro planes (pitched rows) to the host
+    d2h = len(lbm.FIELDS) * ((case.params["nx"] + 31) // 32 * 32) * case.params["ny"] * 4
+    del out
+
+    variants = {}
+    if not args.no_variants and args.storage == "fp32":
+        for st in ("fp16", "bf16"):
+            vs, vms, _, vm = timed_run(st, args.steps, max(args.warmup, 3), clocks=False)
+            variants[st] = {"value": world * nodes * args.steps / (vms / 1e3) / 1e6, "unit": UNIT,
+                            "speedup_vs_fp32": ms / vms, "nonfinite": vm["nonfinite"]}
+            del vs
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(case)
+    wall_launches = (0 if case.params["bc"][2] == "periodic" else 1) + (0 if case.params["bc"][0] == "periodic" else 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.storage == "fp32" else f"f32 compute, {args.storage} storage",
+        "data": "synthetic",
+        "config": {"workload": f"multi_seed_thermosolutal_{args.n}x{args.n}", "nodes": nodes,
+                   "seeds": len(case.seeds), "storage": args.storage, "n_sub": case.params["n_sub"],
+                   "walls": "periodic x, no-slip y", "l2": "state larger than L2 (no flush)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "k_coupled_step", "bytes_per_node": bpn,
+                     "kernel_ms": k_avg_ms, "peak_kind": peak_kind},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(blob) / e2e_steps,
+                "d2h_bytes_per_step": d2h / e2e_steps,
+                "what": "lbm_load_state from pinned host memory, lbm_step(steps), lbm_get_fields of 5 fields"},
+        "gpu_launches": args.steps * (1 + wall_launches),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "variants": variants,
+        "metrics_after_run": {"solid_fraction": m["solid_fraction"], "tip_px": m["tip_px"]},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) diffuse-interface MRT lattice
+ * Boltzmann library for dendritic growth with thermosolutal convection.
+ *
+ * The library advances the coupled update of four distribution functions of
+ * Zhan et al., "A diffuse-interface lattice Boltzmann method for the dendritic
+ * growth with thermosolutal convection" (arXiv 2209.01444):
+ *   - the anisotropic phase field phi       (D2Q5, Sec. 3.1, Eqs. 13-15),
+ *   - the concentration C / supersaturation (D2Q5, Sec. 3.2, Eqs. 17-20),
+ *   - the enthalpy H / temperature theta    (D2Q5, Sec. 3.3, Eqs. 21-23),
+ *   - the melt flow                         (D2Q9 MRT, Sec. 3.4, Eqs. 24-26)
+ *     with the order-parameter-weighted fluid-solid force and buoyancy,
+ * with the relaxation rates, seed profile, non-equilibrium-extrapolation
+ * boundaries and two-time-scaling of Sec. 4 and the matrices of Appendix B.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns LBM_OK (0) or a negative LBM_E* code and never
+ *     throws; lbm_last_error() gives a human-readable reason.
+ *   - The library owns all device memory of a handle (allocated in
+ *     lbm_create, released in lbm_destroy).  The caller owns every host buffer
+ *     and seed array passed in; the library copies what it needs and keeps no
+ *     pointer to caller memory after a call returns.
+ *   - Fields and states are row-major planes of ny rows by nx columns, node
+ *     (x, y) at index y*nx + x, x along the first lattice axis.
+ *   - Lengths and seed data are in lattice units (nodes); velocities,
+ *     pressures and forces in the paper's W0/tau0 units.
+ *   - Work is queued on the handle's CUDA stream (default: the legacy default
+ *     stream).  Calls that return host data synchronise that stream.
+ *   - Handles are not thread-safe; use one handle per host thread.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- status codes */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)   /* bad argument or parameter set            */
+#define LBM_ENOMEM (-2)   /* device or host allocation failed         */
+#define LBM_ECUDA (-3)    /* a CUDA runtime call failed               */
+#define LBM_ENUMERIC (-4) /* non-finite value found in the state      */
+#define LBM_ETIMEOUT (-5) /* a bounded device wait ran out            */
+#define LBM_ESTATE (-6)   /* call out of order (e.g. step before init) */
+
+/* --------------------------------------------------------- enumerations */
+/* Wall types (Sec. 4: non-equilibrium extrapolation on the walls).
+ *   PERIODIC  : both opposite sides must be periodic.
+ *   INFLOW    : flow u = u_in, p from the interior; scalars zero-gradient.
+ *   OUTFLOW   : flow u from the interior, p = 0; scalars zero-gradient.
+ *   SYMMETRY  : normal velocity 0, tangential from the interior; scalars
+ *               zero-gradient.
+ *   NOSLIP    : u = 0; scalars zero-gradient.
+ *   DIRICHLET : u = 0; phi = dir_phi, U = dir_U, theta = dir_theta (the
+ *               far-field condition of Sec. 4.4). */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_INFLOW = 1, LBM_BC_OUTFLOW = 2, LBM_BC_SYMMETRY = 3,
+       LBM_BC_NOSLIP = 4, LBM_BC_DIRICHLET = 5 };
+
+/* Population storage precision.  Collisions always run in FP32.  FP16/BF16
+ * store equilibrium-shifted deviations d_i = s (f_i - f_i^ref) from the
+ * equilibrium of a constant reference state (liquid at rest, phi = -1,
+ * C = 1, theta = theta_ref, p = 0); the history fields stay FP32. */
+enum { LBM_FP32 = 0, LBM_FP16 = 1, LBM_BF16 = 2 };
+
+/* Field indices for lbm_get_fields (bit i of the mask selects field i). */
+enum { LBM_FIELD_PHI = 0, LBM_FIELD_C = 1, LBM_FIELD_U = 2, LBM_FIELD_THETA = 3,
+       LBM_FIELD_UX = 4, LBM_FIELD_UY = 5, LBM_FIELD_P = 6, LBM_NUM_FIELDS = 7 };
+
+/* Number of planes in the FP64 state of lbm_get_state/lbm_set_state:
+ * f_0..4 (phi), n_0..4 (C), g_0..4 (H), h_0..8 (flow), then the history
+ * phi^{n-1}, Q^{n-1}, (Cu)^{n-1}_x, (Cu)^{n-1}_y, (Hu)^{n-1}_x, (Hu)^{n-1}_y. */
+#define LBM_STATE_PLANES 30
+
+/* --------------------------------------------------------------- problem */
+/* The problem as the paper states it (Secs. 2-4).  All doubles are in the
+ * paper's units (lengths in W0, times in tau0). */
+typedef struct lbm_params {
+    int nx, ny;            /* lattice nodes along x and y (each >= 4)           */
+    double W0, tau0;       /* interface width and kinetic time, Eq. (1)          */
+    double dx, dt;         /* lattice spacing (W0 units) and coupled time step   */
+    double eps_s;          /* anisotropy strength, Eq. (2), 0 <= eps_s < 1/3     */
+    double lambda;         /* coupling constant, Eq. (5)                         */
+    double k;              /* partition coefficient, Eq. (4a), 0 < k < 1         */
+    double Mc_inf;         /* M c_inf, Eq. (5)                                   */
+    double D, alpha, nu;   /* solute / thermal diffusivity, viscosity (> 0)      */
+    double rho0;           /* reference density of Eq. (25)                      */
+    int n_sub;             /* flow sub-steps per coupled step (Sec. 4; >= 1)     */
+    int h_kind;            /* 0: h = phi, 1: 15/8 (phi - 2phi^3/3 + phi^5/5)     */
+    double gbetaT, gbetaC; /* Boussinesq buoyancy along +y per unit theta and C  */
+    double theta_ref, C_ref; /* buoyancy reference values; theta_ref also sets the
+                                FP16/BF16 reference state                        */
+    double force[2];       /* constant body force                                */
+    int bc[4];             /* wall types: left, right, bottom, top               */
+    double u_in[2];        /* inflow velocity                                    */
+    double dir_phi, dir_U, dir_theta; /* Dirichlet far-field values             */
+    int storage;           /* LBM_FP32, LBM_FP16 or LBM_BF16                     */
+} lbm_params;
+
+/* A seed (Sec. 4): centre and radius in lattice units, crystal-axis
+ * orientation in radians.  phi = max over seeds of tanh[(R - d)/(sqrt2 W0)]
+ * with d the minimum-image distance on periodic axes; each node belongs to
+ * the grain of its nearest seed centre (ties to the lower index). */
+typedef struct lbm_seed {
+    double x, y, R, orient;
+} lbm_seed;
+
+/* Reductions of lbm_get_metrics, accumulated in FP64 on the device. */
+typedef struct lbm_metrics {
+    double tip[3];         /* tip distance (lattice units) from the given centre
+                              along the grain's +x, -x and +y axes: phi sampled
+                              bilinearly every half node, outermost sample with
+                              phi > 0 interpolated to phi = 0; NaN if none     */
+    double solid_fraction; /* sum((1 + phi)/2) / (nx ny)                       */
+    double sum_C;          /* sum over nodes of C = sum_i n_i                  */
+    double sum_H;          /* sum over nodes of H = sum_i g_i                  */
+    double sum_h;          /* sum over nodes and directions of h_i             */
+    double max_u;          /* max |u| in paper units                           */
+    double nonfinite;      /* 1 if any node holds a NaN/Inf macro, else 0      */
+    double sum_phi;        /* sum over nodes of phi                            */
+    long long step;        /* coupled steps taken since initialisation         */
+} lbm_metrics;
+
+typedef struct lbm_handle lbm_handle;
+
+/* ------------------------------------------------------------- life cycle */
+/* Fill *p with the thermosolutal parameter set of Sec. 4.4 on an nx x ny
+ * periodic box (W0 = tau0 = 1, dx = 1, dt = 0.05, eps_s = 0.05, alpha = D = 2,
+ * k = 0.15, Mc_inf = 0.5325, lambda = 3.1913, nu = 2, rho0 = 1, FP32). */
+LBM_API int lbm_params_default(lbm_params* p, int nx, int ny);
+
+/* Validate *p, derive the lattice-unit parameters and relaxation rates of
+ * Sec. 4, and allocate the device state (double-buffered populations, history,
+ * grain map).  On success *out receives a new handle. */
+LBM_API int lbm_create(const lbm_params* p, lbm_handle** out);
+
+/* Release every resource of h (NULL is a no-op). */
+LBM_API void lbm_destroy(lbm_handle* h);
+
+/* Queue all later work of h on `stream` (a cudaStream_t, e.g. the handle of
+ * torch.cuda.current_stream(); NULL selects the legacy default stream). */
+LBM_API int lbm_set_stream(lbm_handle* h, void* stream);
+
+/* --------------------------------------------------------- initial state */
+/* Seeded start (Sec. 4): phi from the seeds, U = U0, theta = theta0, u = 0,
+ * p = 0, populations at equilibrium, history = the time-0 macros.  At most 256
+ * seeds. */
+LBM_API int lbm_init_seeds(lbm_handle* h, const lbm_seed* seeds, int n_seeds, double U0, double theta0);
+
+/* Start from given macroscopic fields: `fields` holds 6 planes (phi, U,
+ * theta, u_x, u_y, p), velocities and pressure in paper units; `orient` is
+ * one plane of grain orientations in radians (NULL: 0 everywhere, at most 256
+ * distinct values).  Populations at equilibrium, history = time-0 macros. */
+LBM_API int lbm_init_fields(lbm_handle* h, const double* fields, const double* orient);
+
+/* ------------------------------------------------------------------ steps */
+/* Queue `nsteps` coupled time steps (the fused stream-collide kernel of all
+ * four models, then the wall kernels, then n_sub - 1 flow-only sub-steps) on
+ * the handle's stream and return without waiting.  Long runs are replayed
+ * from a captured CUDA graph. */
+LBM_API int lbm_step(lbm_handle* h, int nsteps);
+
+/* Wait for all queued work of h; reports an asynchronous CUDA error. */
+LBM_API int lbm_synchronize(lbm_handle* h);
+
+/* Number of coupled steps taken since the last initialisation. */
+LBM_API long long lbm_step_count(const lbm_handle* h);
+
+/* ---------------------------------------------------------------- output */
+/* Write the fields selected by `mask` (bit LBM_FIELD_*) into `out`, in
+ * increasing field order, nx*ny doubles each: phi, C, U (Eq. 20), theta
+ * (Eq. 23), u_x, u_y (corrected velocity of Eq. 26, paper units), p (Eq. 26,
+ * paper units).  Synchronous. */
+LBM_API int lbm_get_fields(lbm_handle* h, unsigned mask, double* out);
+
+/* FP64 copy of the decoded state: LBM_STATE_PLANES planes of nx*ny
+ * (populations in lattice units, history as stored).  Synchronous. */
+LBM_API int lbm_get_state(lbm_handle* h, double* out);
+
+/* FP64 copy of the decoded state restricted to the w x hgt window with
+ * lower-left node (x0, y0): LBM_STATE_PLANES planes of w*hgt, row-major.
+ * The window must lie inside the grid.  Synchronous. */
+LBM_API int lbm_get_state_region(lbm_handle* h, int x0, int y0, int w, int hgt, double* out);
+
+/* Overwrite the state from LBM_STATE_PLANES FP64 planes (rounded to the
+ * storage precision).  The grain map and step counter are kept. */
+LBM_API int lbm_set_state(lbm_handle* h, const double* in);
+
+/* Reductions at the current step (see lbm_metrics) with tips measured from
+ * (cx, cy) along the axes of a grain of orientation `orient`.  Synchronous;
+ * returns LBM_ENUMERIC (with *m filled) when a non-finite value is found. */
+LBM_API int lbm_get_metrics(lbm_handle* h, double cx, double cy, double orient, lbm_metrics* m);
+
+/* ------------------------------------------------------------- checkpoint */
+/* Size in bytes of a checkpoint of h (raw storage-precision populations,
+ * history, grain map and orientation table, step counter, parameters). */
+LBM_API size_t lbm_checkpoint_bytes(const lbm_handle* h);
+
+/* Write a checkpoint into `host` (`bytes` >= lbm_checkpoint_bytes).  Synchronous. */
+LBM_API int lbm_save_state(lbm_handle* h, void* host, size_t bytes);
+
+/* Restore a checkpoint written by a handle with identical parameters;
+ * resuming is bit-exact.  LBM_EINVAL if the size or parameters differ. */
+LBM_API int lbm_load_state(lbm_handle* h, const void* host, size_t bytes);
+
+/* ------------------------------------------------------------ diagnostics */
+/* Kernel timing for roofline measurements: while enabled, lbm_step launches
+ * every coupled step directly (no graph) and brackets the fused
+ * stream-collide kernel with CUDA events on the handle's stream.  Enabling or
+ * disabling resets the accumulated time. */
+LBM_API int lbm_set_profiling(lbm_handle* h, int enable);
+
+/* Total device time (ms) of the fused kernel launches timed since profiling
+ * was enabled, and their number.  Synchronises the pending events. */
+LBM_API int lbm_kernel_time(lbm_handle* h, double* total_ms, long long* launches);
+
+/* Reason for the last failing call on h (or of lbm_create when h is NULL). */
+LBM_API const char* lbm_last_error(const lbm_handle* h);
+
+/* Library version string. */
+LBM_API const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

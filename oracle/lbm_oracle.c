@@ -761,6 +761,7 @@ static void set_equilibrium_state(orc_sim* s, const double* phi, const double* U
         for (int i = 0; i < 9; ++i) s->h[i * N + x] = e[i];
     }
     compute_macros(s);
+#pragma omp parallel for schedule(static)
     for (int x = 0; x < N; ++x) {
         s->phi_prev[x] = s->phi[x];
         s->Q_prev[x] = coupling_Q(s->phi[x], s->theta[x], s->U[x], s->P.lambda, s->P.Mc_inf);
@@ -782,8 +783,12 @@ static double axis_offset(double d, int L, int periodic)
 }
 
 /* Seeds [x, y, R, orientation] in lattice units/radians (reading R1; grain map
- * = nearest seed centre, ties to the lower index). */
-int orc_init_seeds(orc_sim* s, const double* seeds, int ns, double U0, double theta0)
+ * = nearest seed centre, ties to the lower index), placed on a window of a
+ * larger gnx x gny domain: node (i, j) of this grid is node (gx0 + i, gy0 + j)
+ * of the large one, whose periodicity is (gpx, gpy).  The plain seeded start
+ * is the window covering the whole domain. */
+int orc_init_seeds_window(orc_sim* s, const double* seeds, int ns, double U0, double theta0, int gx0, int gy0,
+                          int gnx, int gny, int gpx, int gpy)
 {
     if (!s || ns < 1 || !seeds) return -1;
     const int N = s->N, nx = s->nx;
@@ -791,13 +796,14 @@ int orc_init_seeds(orc_sim* s, const double* seeds, int ns, double U0, double th
     if (!buf) return -1;
     double *phi = buf, *U = buf + N, *th = buf + 2 * N, *ux = buf + 3 * N, *uy = buf + 4 * N,
            *p = buf + 5 * N;
+#pragma omp parallel for schedule(static)
     for (int idx = 0; idx < N; ++idx) {
-        int x = idx % nx, y = idx / nx;
+        int x = (gx0 + idx % nx) % gnx, y = (gy0 + idx / nx) % gny;
         double best_phi = -2.0, best_d2 = 1e300;
         int best = 0;
         for (int j = 0; j < ns; ++j) {
-            double dxs = axis_offset(x - seeds[4 * j + 0], nx, is_periodic_x(s));
-            double dys = axis_offset(y - seeds[4 * j + 1], s->ny, is_periodic_y(s));
+            double dxs = axis_offset(x - seeds[4 * j + 0], gnx, gpx);
+            double dys = axis_offset(y - seeds[4 * j + 1], gny, gpy);
             double d2 = dxs * dxs + dys * dys;
             double ph = tanh((seeds[4 * j + 2] - sqrt(d2)) / (sqrt(2.0) * s->W));
             if (ph > best_phi) best_phi = ph;
@@ -815,6 +821,13 @@ int orc_init_seeds(orc_sim* s, const double* seeds, int ns, double U0, double th
     set_equilibrium_state(s, phi, U, th, ux, uy, p);
     free(buf);
     return 0;
+}
+
+int orc_init_seeds(orc_sim* s, const double* seeds, int ns, double U0, double theta0)
+{
+    if (!s) return -1;
+    return orc_init_seeds_window(s, seeds, ns, U0, theta0, 0, 0, s->nx, s->ny, is_periodic_x(s),
+                                 is_periodic_y(s));
 }
 
 /* fields [6][N]: phi, U, theta, ux, uy, p with velocity and pressure in paper

@@ -32,6 +32,8 @@ typedef struct orc_sim orc_sim;
 orc_sim* orc_create(const orc_params* p);
 void orc_destroy(orc_sim* s);
 int orc_init_seeds(orc_sim* s, const double* seeds, int ns, double U0, double theta0);
+int orc_init_seeds_window(orc_sim* s, const double* seeds, int ns, double U0, double theta0, int gx0, int gy0,
+                          int gnx, int gny, int gpx, int gpy);
 int orc_init_fields(orc_sim* s, const double* fields, const double* orient);
 int orc_step(orc_sim* s, int nsteps);
 long long orc_step_count(const orc_sim* s);

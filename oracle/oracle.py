@@ -73,6 +73,7 @@ def _load():
     lib.orc_create.argtypes = [ct.POINTER(_Params)]
     lib.orc_destroy.argtypes = [ct.c_void_p]
     lib.orc_init_seeds.argtypes = [ct.c_void_p, dp, ct.c_int, ct.c_double, ct.c_double]
+    lib.orc_init_seeds_window.argtypes = [ct.c_void_p, dp, ct.c_int, ct.c_double, ct.c_double] + [ct.c_int] * 6
     lib.orc_init_fields.argtypes = [ct.c_void_p, dp, dp]
     lib.orc_step.argtypes = [ct.c_void_p, ct.c_int]
     lib.orc_step_count.restype = ct.c_longlong
@@ -145,6 +146,15 @@ class Oracle:
         a = np.ascontiguousarray(np.asarray(seeds, dtype=np.float64).reshape(-1, 4))
         if self.lib.orc_init_seeds(self.h, _ptr(a), a.shape[0], U0, theta0):
             raise ValueError("init_seeds failed")
+
+    def init_seeds_window(self, seeds, U0: float, theta0: float, x0: int, y0: int, gnx: int, gny: int,
+                          periodic_x: bool, periodic_y: bool) -> None:
+        """Seeded start of the window with lower-left node (x0, y0) of a larger
+        gnx x gny domain (seed coordinates in that domain)."""
+        a = np.ascontiguousarray(np.asarray(seeds, dtype=np.float64).reshape(-1, 4))
+        if self.lib.orc_init_seeds_window(self.h, _ptr(a), a.shape[0], U0, theta0, x0, y0, gnx, gny,
+                                          int(periodic_x), int(periodic_y)):
+            raise ValueError("init_seeds_window failed")
 
     def init_fields(self, fields: np.ndarray, orient: np.ndarray | None = None) -> None:
         f = np.ascontiguousarray(np.asarray(fields, dtype=np.float64).reshape(6, self.n))

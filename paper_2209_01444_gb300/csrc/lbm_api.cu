@@ -1,0 +1,709 @@
+// C ABI of the library (declared in include/lbm.h): parameter validation and
+// lattice-unit conversion (Sec. 4), device state, CUDA-graph replay of the
+// coupled step, field extraction, reductions and checkpoints.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.h"
+
+using lbm::StepParams;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Steps per captured graph: even, so every buffer returns to its parity.
+constexpr int kGraphSteps = 16;
+
+struct GraphKey {
+    int cs, cf;
+    bool operator<(const GraphKey& o) const { return cs != o.cs ? cs < o.cs : cf < o.cf; }
+};
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_params prm;
+    StepParams P;
+    int storage = 0;
+    size_t esize = 4;
+    cudaStream_t stream = nullptr;
+    lbm::StepBuffers B{};
+    uint8_t* grain = nullptr;          // device grain ids
+    float2* grain_cs = nullptr;        // device (cos, sin) table
+    std::vector<float2> grain_table;   // host copy of the table
+    bool uniform = true;               // one orientation everywhere
+    double* d_partials = nullptr;
+    double* d_red = nullptr;
+    double* d_f64 = nullptr;           // 6 FP64 planes (initialisation)
+    float* d_f32 = nullptr;            // kPlanes FP32 planes (extraction)
+    double* d_seeds = nullptr;
+    long long steps = 0;
+    bool initialised = false;
+    std::string err;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    // kernel timing (lbm_set_profiling)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;   // begin/end pairs of pending fused-kernel launches
+    size_t ev_used = 0;
+    double prof_ms = 0.0;
+    long long prof_launches = 0;
+    // lattice conversion
+    double vf = 1, pscale = 1;  // paper velocity -> flow lattice, lattice pressure -> paper
+};
+
+namespace {
+
+int fail(lbm_handle* h, int code, const std::string& msg)
+{
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(lbm_handle* h, cudaError_t e, const char* where)
+{
+    return fail(h, LBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(h, call)                                  \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+void drop_graphs(lbm_handle* h)
+{
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+bool valid_bc(int b) { return b >= LBM_BC_PERIODIC && b <= LBM_BC_DIRICHLET; }
+
+std::string validate(const lbm_params* p)
+{
+    if (!p) return "params is NULL";
+    if (p->nx < 4 || p->ny < 4) return "nx and ny must be >= 4";
+    if ((long long)p->nx * p->ny > (1LL << 31)) return "grid too large";
+    if (!(p->W0 > 0 && p->tau0 > 0 && p->dx > 0 && p->dt > 0)) return "W0, tau0, dx, dt must be > 0";
+    if (!(p->eps_s >= 0 && p->eps_s < 1.0 / 3.0)) return "eps_s must be in [0, 1/3)";
+    if (!(p->k > 0 && p->k < 1)) return "k must be in (0, 1)";
+    if (!(p->D > 0 && p->alpha > 0 && p->nu > 0)) return "D, alpha, nu must be > 0";
+    if (!(p->rho0 > 0)) return "rho0 must be > 0";
+    if (p->n_sub < 1 || p->n_sub > 1000) return "n_sub must be in [1, 1000]";
+    if (p->h_kind != 0 && p->h_kind != 1) return "h_kind must be 0 or 1";
+    for (int b = 0; b < 4; ++b)
+        if (!valid_bc(p->bc[b])) return "unknown wall type";
+    if ((p->bc[0] == LBM_BC_PERIODIC) != (p->bc[1] == LBM_BC_PERIODIC)) return "left/right periodicity must match";
+    if ((p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) return "bottom/top periodicity must match";
+    if (p->storage < LBM_FP32 || p->storage > LBM_BF16) return "unknown storage";
+    return "";
+}
+
+// Lattice-unit parameters (Sec. 4): dx = dt = 1 for the scalar models,
+// dt/n_sub for the flow.
+void derive(lbm_handle* h)
+{
+    const lbm_params& p = h->prm;
+    StepParams& P = h->P;
+    memset(&P, 0, sizeof(P));
+    P.nx = p.nx;
+    P.ny = p.ny;
+    const size_t align = 32;  // 128-byte rows in FP32, 64-byte rows in 16-bit
+    P.pitch = (int)((p.nx + align - 1) / align * align);
+    P.plane = (long long)P.pitch * p.ny;
+    P.periodic_x = p.bc[0] == LBM_BC_PERIODIC;
+    P.periodic_y = p.bc[2] == LBM_BC_PERIODIC;
+    P.h_kind = p.h_kind;
+    const double W = p.W0 / p.dx, tau = p.tau0 / p.dt;
+    const double dtf = p.dt / p.n_sub;
+    const double Dl = p.D * p.dt / (p.dx * p.dx);
+    const double al = p.alpha * p.dt / (p.dx * p.dx);
+    const double nul = p.nu * dtf / (p.dx * p.dx);
+    P.kappa3 = (float)(3.0 * W * W / tau);
+    P.inv_tau = (float)(1.0 / tau);
+    P.eps = (float)p.eps_s;
+    P.lambda = (float)p.lambda;
+    P.k = (float)p.k;
+    P.Mc = (float)p.Mc_inf;
+    P.W = (float)W;
+    P.inv_D = (float)(1.0 / Dl);
+    P.s1C = (float)(1.0 / (3.0 * Dl * (1.0 - p.k) + 0.5));
+    P.s1T = (float)(1.0 / (3.0 * al + 0.5));
+    P.s2u = (float)(1.0 / (3.0 * nul + 0.5));
+    P.rho0 = (float)p.rho0;
+    h->vf = dtf / p.dx;
+    const double ff = dtf * dtf / p.dx;
+    h->pscale = (p.dx * p.dx) / (dtf * dtf);
+    P.Fx = (float)(p.force[0] * ff);
+    P.Fy = (float)(p.force[1] * ff);
+    P.gbT = (float)(p.gbetaT * ff);
+    P.gbC = (float)(p.gbetaC * ff);
+    P.theta_ref = (float)p.theta_ref;
+    P.C_ref = (float)p.C_ref;
+    P.nsub = (float)p.n_sub;
+    P.cos_o = 1.0f;
+    P.sin_o = 0.0f;
+    for (int b = 0; b < 4; ++b) P.bc[b] = p.bc[b];
+    P.uin_x = (float)(p.u_in[0] * h->vf);
+    P.uin_y = (float)(p.u_in[1] * h->vf);
+    P.dir_phi = (float)p.dir_phi;
+    P.dir_U = (float)p.dir_U;
+    P.dir_theta = (float)p.dir_theta;
+    // Reference state of the shifted 16-bit storage: liquid at rest with
+    // phi = -1, C = 1 (U = 0), theta = theta_ref, p = 0.
+    const double w5[5] = {1.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
+    const double hm1 = p.h_kind == 1 ? -1.0 : -1.0;  // h(-1) = -1 for both kinds
+    for (int i = 0; i < 5; ++i) {
+        P.ref[lbm::kF + i] = (float)(-w5[i]);
+        P.ref[lbm::kN + i] = (float)(i == 0 ? 1.0 : 0.0);
+        P.ref[lbm::kG + i] = (float)(w5[i] * p.theta_ref - (i == 0 ? 0.5 * hm1 : 0.0));
+    }
+    for (int i = 0; i < 9; ++i) P.ref[lbm::kH + i] = (float)(i == 0 ? p.rho0 : 0.0);
+    for (int q = 0; q < lbm::kPlanes; ++q) {
+        float sc = 1.0f;
+        if (p.storage == LBM_FP16) sc = q >= lbm::kH ? 1024.0f : 16.0f;  // keep deviations in the normal range
+        P.scale[q] = sc;
+        P.inv_scale[q] = 1.0f / sc;
+    }
+}
+
+size_t plane_bytes(const lbm_handle* h) { return (size_t)h->P.plane * h->esize; }
+
+int ensure_initialised(lbm_handle* h)
+{
+    if (!h) return LBM_EINVAL;
+    if (!h->initialised) return fail(h, LBM_ESTATE, "state not initialised (call lbm_init_seeds or lbm_init_fields)");
+    return LBM_OK;
+}
+
+int set_grains(lbm_handle* h, const std::vector<double>& orient_of_id, const std::vector<uint8_t>* host_ids)
+{
+    // one orientation everywhere: no grain plane is read by the step kernel
+    h->grain_table.assign(256, make_float2(1.0f, 0.0f));
+    for (size_t j = 0; j < orient_of_id.size(); ++j)
+        h->grain_table[j] = make_float2((float)cos(orient_of_id[j]), (float)sin(orient_of_id[j]));
+    bool uniform = true;
+    for (size_t j = 1; j < orient_of_id.size(); ++j)
+        if (orient_of_id[j] != orient_of_id[0]) uniform = false;
+    h->uniform = uniform;
+    h->P.cos_o = h->grain_table[0].x;
+    h->P.sin_o = h->grain_table[0].y;
+    LBM_CUDA(h, cudaMemcpyAsync(h->grain_cs, h->grain_table.data(), 256 * sizeof(float2), cudaMemcpyHostToDevice,
+                                h->stream));
+    if (host_ids)
+        LBM_CUDA(h, cudaMemcpyAsync(h->grain, host_ids->data(), (size_t)h->P.plane, cudaMemcpyHostToDevice,
+                                    h->stream));
+    h->P.grain_cs = h->grain_cs;
+    h->B.grain = uniform ? nullptr : h->grain;
+    return LBM_OK;
+}
+
+int finish_init(lbm_handle* h)
+{
+    h->B.cs = 0;
+    h->B.cf = 0;
+    h->steps = 0;
+    drop_graphs(h);
+    LBM_CUDA(h, lbm::launch_init_from_fields(h->P, h->storage, h->d_f64, h->B.sc[0], h->B.fl[0], h->B.hist,
+                                             h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->initialised = true;
+    return LBM_OK;
+}
+
+int collect_profile(lbm_handle* h)
+{
+    if (!h->ev_used) return LBM_OK;
+    LBM_CUDA(h, cudaEventSynchronize(h->ev[h->ev_used - 1]));
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+        float ms = 0.0f;
+        LBM_CUDA(h, cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
+        h->prof_ms += ms;
+        h->prof_launches += 1;
+    }
+    h->ev_used = 0;
+    return LBM_OK;
+}
+
+int run_steps_direct(lbm_handle* h, int n)
+{
+    for (int i = 0; i < n; ++i) {
+        if (h->profiling) {
+            if (h->ev_used + 2 > h->ev.size()) {
+                int rc = collect_profile(h);
+                if (rc) return rc;
+                while (h->ev.size() < 512) {
+                    cudaEvent_t e;
+                    LBM_CUDA(h, cudaEventCreate(&e));
+                    h->ev.push_back(e);
+                }
+            }
+            h->B.ev_begin = h->ev[h->ev_used++];
+            h->B.ev_end = h->ev[h->ev_used++];
+        }
+        cudaError_t e = lbm::launch_coupled_step(h->P, h->storage, h->prm.n_sub, h->B, h->stream);
+        h->B.ev_begin = h->B.ev_end = nullptr;
+        if (e != cudaSuccess) return cuda_fail(h, e, "coupled step");
+    }
+    return LBM_OK;
+}
+
+int graph_for(lbm_handle* h, cudaGraphExec_t* out)
+{
+    const GraphKey key{h->B.cs, h->B.cf};
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+        *out = it->second;
+        return LBM_OK;
+    }
+    cudaStream_t cap;
+    LBM_CUDA(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    lbm::StepBuffers saved = h->B;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i)
+            e = lbm::launch_coupled_step(h->P, h->storage, h->prm.n_sub, h->B, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    h->B = saved;  // the capture only recorded the launches
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, e, "graph capture");
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    h->graphs[key] = ex;
+    *out = ex;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_params_default(lbm_params* p, int nx, int ny)
+{
+    if (!p) return LBM_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->nx = nx;
+    p->ny = ny;
+    p->W0 = 1.0;
+    p->tau0 = 1.0;
+    p->dx = 1.0;
+    p->dt = 0.05;
+    p->eps_s = 0.05;
+    p->lambda = 3.1913;
+    p->k = 0.15;
+    p->Mc_inf = 0.5325;
+    p->D = 2.0;
+    p->alpha = 2.0;
+    p->nu = 2.0;
+    p->rho0 = 1.0;
+    p->n_sub = 1;
+    p->h_kind = 0;
+    p->theta_ref = -0.55;
+    p->C_ref = 1.0;
+    for (int b = 0; b < 4; ++b) p->bc[b] = LBM_BC_PERIODIC;
+    p->dir_phi = -1.0;
+    p->dir_U = 0.0;
+    p->dir_theta = -0.55;
+    p->storage = LBM_FP32;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_params* p, lbm_handle** out)
+{
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why = validate(p);
+    if (!why.empty()) return fail(nullptr, LBM_EINVAL, why);
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    h->prm = *p;
+    h->storage = p->storage;
+    h->esize = lbm::storage_bytes(p->storage);
+    derive(h);
+    const size_t pb = plane_bytes(h);
+    const size_t fp = (size_t)h->P.plane * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    };
+    for (int b = 0; b < 2; ++b) {
+        alloc(&h->B.sc[b], pb * (lbm::kH));
+        alloc(&h->B.fl[b], pb * (lbm::kPlanes - lbm::kH));
+    }
+    alloc((void**)&h->B.hist, fp * lbm::kHist);
+    if (p->n_sub > 1) alloc((void**)&h->B.fb, fp);
+    alloc((void**)&h->grain, (size_t)h->P.plane);
+    alloc((void**)&h->grain_cs, 256 * sizeof(float2));
+    alloc((void**)&h->d_partials, lbm::reduce_partials_size(h->P) * sizeof(double));
+    alloc((void**)&h->d_red, 16 * sizeof(double));
+    alloc((void**)&h->d_f64, (size_t)h->P.plane * 6 * sizeof(double));
+    alloc((void**)&h->d_f32, fp * lbm::kPlanes);
+    alloc((void**)&h->d_seeds, 256 * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(h->grain, 0, (size_t)h->P.plane);
+    if (e != cudaSuccess) {
+        std::string msg = std::string("device allocation: ") + cudaGetErrorString(e);
+        lbm_destroy(h);
+        cudaGetLastError();
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, msg);
+    }
+    h->P.grain_cs = h->grain_cs;
+    *out = h;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h)
+{
+    if (!h) return;
+    drop_graphs(h);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    void* ptrs[] = {h->B.sc[0], h->B.sc[1], h->B.fl[0], h->B.fl[1], h->B.hist, h->B.fb, h->grain,
+                    h->grain_cs, h->d_partials, h->d_red, h->d_f64, h->d_f32, h->d_seeds};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete h;
+}
+
+int lbm_set_stream(lbm_handle* h, void* stream)
+{
+    if (!h) return LBM_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+int lbm_init_seeds(lbm_handle* h, const lbm_seed* seeds, int n, double U0, double theta0)
+{
+    if (!h) return LBM_EINVAL;
+    if (!seeds || n < 1 || n > 256) return fail(h, LBM_EINVAL, "need 1..256 seeds");
+    std::vector<double> s(4 * (size_t)n);
+    std::vector<double> orient(n);
+    for (int j = 0; j < n; ++j) {
+        s[4 * j + 0] = seeds[j].x;
+        s[4 * j + 1] = seeds[j].y;
+        s[4 * j + 2] = seeds[j].R;
+        s[4 * j + 3] = seeds[j].orient;
+        orient[j] = seeds[j].orient;
+        if (!isfinite(seeds[j].x) || !isfinite(seeds[j].y) || !isfinite(seeds[j].R) || !isfinite(seeds[j].orient))
+            return fail(h, LBM_EINVAL, "non-finite seed");
+    }
+    LBM_CUDA(h, cudaMemcpyAsync(h->d_seeds, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(h, lbm::launch_seed_fields(h->P, h->d_seeds, n, U0, theta0, h->prm.W0 / h->prm.dx, h->d_f64, h->grain,
+                                        h->stream));
+    int rc = set_grains(h, orient, nullptr);
+    if (rc) return rc;
+    return finish_init(h);
+}
+
+int lbm_init_fields(lbm_handle* h, const double* fields, const double* orient)
+{
+    if (!h) return LBM_EINVAL;
+    if (!fields) return fail(h, LBM_EINVAL, "fields is NULL");
+    const int nx = h->P.nx, ny = h->P.ny, pitch = h->P.pitch;
+    const size_t N = (size_t)nx * ny;
+    std::vector<double> f64((size_t)h->P.plane * 6, 0.0);
+    const double scale[6] = {1, 1, 1, h->vf, h->vf, 1.0 / h->pscale};
+    for (int q = 0; q < 6; ++q)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                double v = fields[q * N + (size_t)y * nx + x];
+                if (!isfinite(v)) return fail(h, LBM_EINVAL, "non-finite initial field");
+                f64[(size_t)q * h->P.plane + (size_t)y * pitch + x] = v * scale[q];
+            }
+    std::vector<double> table;
+    std::vector<uint8_t> ids((size_t)h->P.plane, 0);
+    if (orient) {
+        std::map<double, int> index;
+        for (size_t i = 0; i < N; ++i) {
+            double o = orient[i];
+            if (!isfinite(o)) return fail(h, LBM_EINVAL, "non-finite orientation");
+            auto it = index.find(o);
+            if (it == index.end()) {
+                if (index.size() == 256) return fail(h, LBM_EINVAL, "more than 256 distinct orientations");
+                it = index.emplace(o, (int)table.size()).first;
+                table.push_back(o);
+            }
+            ids[(i / nx) * pitch + (i % nx)] = (uint8_t)it->second;
+        }
+    } else {
+        table.push_back(0.0);
+    }
+    LBM_CUDA(h, cudaMemcpyAsync(h->d_f64, f64.data(), f64.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream));
+    int rc = set_grains(h, table, &ids);
+    if (rc) return rc;
+    return finish_init(h);
+}
+
+int lbm_step(lbm_handle* h, int nsteps)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
+    int left = nsteps;
+    while (!h->profiling && left >= kGraphSteps) {
+        cudaGraphExec_t ex;
+        if ((rc = graph_for(h, &ex))) return rc;
+        LBM_CUDA(h, cudaGraphLaunch(ex, h->stream));
+        left -= kGraphSteps;
+        h->steps += kGraphSteps;
+    }
+    if ((rc = run_steps_direct(h, left))) return rc;
+    h->steps += left;
+    return LBM_OK;
+}
+
+int lbm_synchronize(lbm_handle* h)
+{
+    if (!h) return LBM_EINVAL;
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+long long lbm_step_count(const lbm_handle* h) { return h ? h->steps : -1; }
+
+int lbm_get_fields(lbm_handle* h, unsigned mask, double* out)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (mask >> LBM_NUM_FIELDS) return fail(h, LBM_EINVAL, "unknown field bit");
+    LBM_CUDA(h, lbm::launch_macros(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->d_f32, h->stream));
+    std::vector<float> host((size_t)h->P.plane * LBM_NUM_FIELDS);
+    LBM_CUDA(h, cudaMemcpyAsync(host.data(), h->d_f32, host.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                                h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    const int nx = h->P.nx, ny = h->P.ny, pitch = h->P.pitch;
+    const double scale[LBM_NUM_FIELDS] = {1, 1, 1, 1, 1.0 / h->vf, 1.0 / h->vf, h->pscale};
+    size_t k = 0;
+    for (int q = 0; q < LBM_NUM_FIELDS; ++q) {
+        if (!(mask & (1u << q))) continue;
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                out[k * (size_t)nx * ny + (size_t)y * nx + x] =
+                    (double)host[(size_t)q * h->P.plane + (size_t)y * pitch + x] * scale[q];
+        ++k;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_handle* h, double* out)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    const size_t plane = (size_t)h->P.plane;
+    LBM_CUDA(h, lbm::launch_decode(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->d_f32, h->stream));
+    std::vector<float> host(plane * LBM_STATE_PLANES);
+    LBM_CUDA(h, cudaMemcpyAsync(host.data(), h->d_f32, plane * lbm::kPlanes * sizeof(float), cudaMemcpyDeviceToHost,
+                                h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(host.data() + plane * lbm::kPlanes, h->B.hist, plane * lbm::kHist * sizeof(float),
+                                cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    const int nx = h->P.nx, ny = h->P.ny, pitch = h->P.pitch;
+    for (int q = 0; q < LBM_STATE_PLANES; ++q)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                out[(size_t)q * nx * ny + (size_t)y * nx + x] = host[q * plane + (size_t)y * pitch + x];
+    return LBM_OK;
+}
+
+int lbm_get_state_region(lbm_handle* h, int x0, int y0, int w, int hgt, double* out)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (w < 1 || hgt < 1 || x0 < 0 || y0 < 0 || x0 + w > h->P.nx || y0 + hgt > h->P.ny)
+        return fail(h, LBM_EINVAL, "window outside the grid");
+    const size_t plane = (size_t)h->P.plane, pitch = (size_t)h->P.pitch;
+    LBM_CUDA(h, lbm::launch_decode(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->d_f32, h->stream));
+    std::vector<float> host((size_t)w * hgt * LBM_STATE_PLANES);
+    for (int q = 0; q < LBM_STATE_PLANES; ++q) {
+        const float* src = q < lbm::kPlanes ? h->d_f32 + q * plane : h->B.hist + (q - lbm::kPlanes) * plane;
+        LBM_CUDA(h, cudaMemcpy2DAsync(host.data() + (size_t)q * w * hgt, (size_t)w * sizeof(float),
+                                      src + (size_t)y0 * pitch + x0, pitch * sizeof(float), (size_t)w * sizeof(float),
+                                      hgt, cudaMemcpyDeviceToHost, h->stream));
+    }
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < host.size(); ++i) out[i] = host[i];
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle* h, const double* in)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!in) return fail(h, LBM_EINVAL, "in is NULL");
+    const size_t plane = (size_t)h->P.plane;
+    const int nx = h->P.nx, ny = h->P.ny, pitch = h->P.pitch;
+    std::vector<float> host(plane * LBM_STATE_PLANES, 0.0f);
+    for (int q = 0; q < LBM_STATE_PLANES; ++q)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                double v = in[(size_t)q * nx * ny + (size_t)y * nx + x];
+                if (!isfinite(v)) return fail(h, LBM_EINVAL, "non-finite state value");
+                host[q * plane + (size_t)y * pitch + x] = (float)v;
+            }
+    LBM_CUDA(h, cudaMemcpyAsync(h->d_f32, host.data(), plane * lbm::kPlanes * sizeof(float), cudaMemcpyHostToDevice,
+                                h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(h->B.hist, host.data() + plane * lbm::kPlanes, plane * lbm::kHist * sizeof(float),
+                                cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(h, lbm::launch_encode(h->P, h->storage, h->d_f32, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_get_metrics(lbm_handle* h, double cx, double cy, double orient, lbm_metrics* m)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!m) return fail(h, LBM_EINVAL, "m is NULL");
+    if (!isfinite(cx) || !isfinite(cy) || !isfinite(orient)) return fail(h, LBM_EINVAL, "non-finite tip origin");
+    LBM_CUDA(h, lbm::launch_reduce(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], cx, cy, cos(orient),
+                                   sin(orient), h->d_partials, h->d_red, h->stream));
+    double r[10];
+    LBM_CUDA(h, cudaMemcpyAsync(r, h->d_red, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    const double N = (double)h->P.nx * h->P.ny;
+    m->tip[0] = r[7];
+    m->tip[1] = r[8];
+    m->tip[2] = r[9];
+    m->solid_fraction = r[0] / N;
+    m->sum_C = r[1];
+    m->sum_H = r[2];
+    m->sum_h = r[3];
+    m->max_u = r[4] / h->vf;
+    m->nonfinite = r[5] > 0 ? 1.0 : 0.0;
+    m->sum_phi = r[6];
+    m->step = h->steps;
+    if (r[5] > 0) return fail(h, LBM_ENUMERIC, "non-finite value in the state");
+    return LBM_OK;
+}
+
+// Checkpoint layout: header, then the newest scalar and flow buffers (raw
+// storage precision), history, grain ids, orientation table.
+struct CkptHeader {
+    char magic[8];
+    lbm_params prm;
+    long long steps;
+    int uniform;
+    int pad;
+};
+
+size_t lbm_checkpoint_bytes(const lbm_handle* h)
+{
+    if (!h) return 0;
+    const size_t plane = (size_t)h->P.plane;
+    return sizeof(CkptHeader) + plane * h->esize * lbm::kPlanes + plane * sizeof(float) * lbm::kHist + plane +
+           256 * sizeof(float2);
+}
+
+int lbm_save_state(lbm_handle* h, void* host, size_t bytes)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!host || bytes < lbm_checkpoint_bytes(h)) return fail(h, LBM_EINVAL, "checkpoint buffer too small");
+    char* p = (char*)host;
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "LBMCKPT1", 8);
+    hd.prm = h->prm;
+    hd.steps = h->steps;
+    hd.uniform = h->uniform ? 1 : 0;
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    const size_t plane = (size_t)h->P.plane;
+    const size_t sb = plane * h->esize * lbm::kH, fbz = plane * h->esize * (lbm::kPlanes - lbm::kH);
+    LBM_CUDA(h, cudaMemcpyAsync(p, h->B.sc[h->B.cs], sb, cudaMemcpyDeviceToHost, h->stream));
+    p += sb;
+    LBM_CUDA(h, cudaMemcpyAsync(p, h->B.fl[h->B.cf], fbz, cudaMemcpyDeviceToHost, h->stream));
+    p += fbz;
+    LBM_CUDA(h, cudaMemcpyAsync(p, h->B.hist, plane * sizeof(float) * lbm::kHist, cudaMemcpyDeviceToHost, h->stream));
+    p += plane * sizeof(float) * lbm::kHist;
+    LBM_CUDA(h, cudaMemcpyAsync(p, h->grain, plane, cudaMemcpyDeviceToHost, h->stream));
+    p += plane;
+    memcpy(p, h->grain_table.data(), 256 * sizeof(float2));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_load_state(lbm_handle* h, const void* host, size_t bytes)
+{
+    if (!h) return LBM_EINVAL;
+    if (!host || bytes != lbm_checkpoint_bytes(h)) return fail(h, LBM_EINVAL, "checkpoint size mismatch");
+    const char* p = (const char*)host;
+    CkptHeader hd;
+    memcpy(&hd, p, sizeof(hd));
+    if (memcmp(hd.magic, "LBMCKPT1", 8) != 0) return fail(h, LBM_EINVAL, "not a checkpoint");
+    if (memcmp(&hd.prm, &h->prm, sizeof(lbm_params)) != 0) return fail(h, LBM_EINVAL, "checkpoint parameters differ");
+    p += sizeof(hd);
+    const size_t plane = (size_t)h->P.plane;
+    const size_t sb = plane * h->esize * lbm::kH, fbz = plane * h->esize * (lbm::kPlanes - lbm::kH);
+    h->B.cs = 0;
+    h->B.cf = 0;
+    drop_graphs(h);
+    LBM_CUDA(h, cudaMemcpyAsync(h->B.sc[0], p, sb, cudaMemcpyHostToDevice, h->stream));
+    p += sb;
+    LBM_CUDA(h, cudaMemcpyAsync(h->B.fl[0], p, fbz, cudaMemcpyHostToDevice, h->stream));
+    p += fbz;
+    LBM_CUDA(h, cudaMemcpyAsync(h->B.hist, p, plane * sizeof(float) * lbm::kHist, cudaMemcpyHostToDevice, h->stream));
+    p += plane * sizeof(float) * lbm::kHist;
+    LBM_CUDA(h, cudaMemcpyAsync(h->grain, p, plane, cudaMemcpyHostToDevice, h->stream));
+    p += plane;
+    h->grain_table.resize(256);
+    memcpy(h->grain_table.data(), p, 256 * sizeof(float2));
+    LBM_CUDA(h, cudaMemcpyAsync(h->grain_cs, h->grain_table.data(), 256 * sizeof(float2), cudaMemcpyHostToDevice,
+                                h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->uniform = hd.uniform != 0;
+    h->P.cos_o = h->grain_table[0].x;
+    h->P.sin_o = h->grain_table[0].y;
+    h->B.grain = h->uniform ? nullptr : h->grain;
+    h->steps = hd.steps;
+    h->initialised = true;
+    return LBM_OK;
+}
+
+int lbm_set_profiling(lbm_handle* h, int enable)
+{
+    if (!h) return LBM_EINVAL;
+    int rc = collect_profile(h);
+    if (rc) return rc;
+    h->profiling = enable != 0;
+    h->prof_ms = 0.0;
+    h->prof_launches = 0;
+    return LBM_OK;
+}
+
+int lbm_kernel_time(lbm_handle* h, double* total_ms, long long* launches)
+{
+    if (!h || !total_ms || !launches) return LBM_EINVAL;
+    int rc = collect_profile(h);
+    if (rc) return rc;
+    *total_ms = h->prof_ms;
+    *launches = h->prof_launches;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+const char* lbm_version(void) { return "lbm-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,427 @@
+// Initialisation, field extraction, state codecs and FP64 reductions.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "lbm_kernels.h"
+
+namespace lbm {
+
+namespace {
+
+template <class Store>
+__device__ __forceinline__ void load_node(const StepParams& P, const typename Store::T* sc,
+                                          const typename Store::T* fl, long long o, float* f, float* n, float* g,
+                                          float* h)
+{
+    const long long plane = P.plane;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) f[i] = Store::load(sc, (kF + i) * plane + o, kF + i, P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) n[i] = Store::load(sc, (kN + i) * plane + o, kN + i, P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = Store::load(sc, (kG + i) * plane + o, kG + i, P);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = Store::load(fl, i * plane + o, kH + i, P);
+}
+
+__device__ __forceinline__ double min_image(double d, int L, int periodic)
+{
+    if (!periodic) return d;
+    while (d > 0.5 * L) d -= L;
+    while (d < -0.5 * L) d += L;
+    return d;
+}
+
+// Seeds (Sec. 4): phi = max_j tanh[(R_j - d_j)/(sqrt2 W0)], grain = nearest
+// centre (ties to the lower index); FP64 so that both choices match an FP64
+// evaluation.  fields: 6 FP64 planes (phi, U, theta, ux, uy, p), lattice units.
+__global__ void k_seed_fields(const StepParams P, const double* __restrict__ seeds, int ns, double U0,
+                              double theta0, double W, double* __restrict__ fields, uint8_t* __restrict__ grain)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long o = (long long)y * P.pitch + x;
+    double best_phi = -2.0, best_d2 = 1e300;
+    int best = 0;
+    const double inv = 1.0 / (sqrt(2.0) * W);
+    for (int j = 0; j < ns; ++j) {
+        const double dx = min_image(x - seeds[4 * j + 0], P.nx, P.periodic_x);
+        const double dy = min_image(y - seeds[4 * j + 1], P.ny, P.periodic_y);
+        const double d2 = dx * dx + dy * dy;
+        const double ph = tanh((seeds[4 * j + 2] - sqrt(d2)) * inv);
+        if (ph > best_phi) best_phi = ph;
+        if (d2 < best_d2) {
+            best_d2 = d2;
+            best = j;
+        }
+    }
+    fields[0 * P.plane + o] = best_phi;
+    fields[1 * P.plane + o] = U0;
+    fields[2 * P.plane + o] = theta0;
+    fields[3 * P.plane + o] = 0.0;
+    fields[4 * P.plane + o] = 0.0;
+    fields[5 * P.plane + o] = 0.0;
+    if (grain) grain[o] = (uint8_t)best;
+}
+
+// Equilibrium populations of the given macros, then history = the macros
+// recovered from the stored populations (so the first backward differences
+// vanish).
+template <class Store, bool GRAIN>
+__global__ void k_init(const StepParams P, const double* __restrict__ fields, typename Store::T* __restrict__ sc,
+                       typename Store::T* __restrict__ fl, float* __restrict__ hist)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long plane = P.plane;
+    const long long o = (long long)y * P.pitch + x;
+    const float phi = (float)fields[0 * plane + o], U = (float)fields[1 * plane + o];
+    const float theta = (float)fields[2 * plane + o];
+    const float ux = (float)fields[3 * plane + o], uy = (float)fields[4 * plane + o];
+    const float p = (float)fields[5 * plane + o];
+    const float C = C_of_U(U, phi, P.k);
+    const float hphi = h_of_phi(P.h_kind, phi);
+    const float H = theta - 0.5f * hphi;
+    const float sx = ux * P.nsub, sy = uy * P.nsub;
+    float e[9];
+    feq_phi(phi, e);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store::store(sc, (kF + i) * plane + o, kF + i, e[i], P);
+    feq_C(C, 0.5f * (1.0f - phi) * U, C * sx, C * sy, e);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store::store(sc, (kN + i) * plane + o, kN + i, e[i], P);
+    feq_H(theta, hphi, H * sx, H * sy, e);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store::store(sc, (kG + i) * plane + o, kG + i, e[i], P);
+    feq_flow(p, ux, uy, P.rho0, e);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store::store(fl, i * plane + o, kH + i, e[i], P);
+
+    float f[5], n[5], g[5], h[9];
+    load_node<Store>(P, sc, fl, o, f, n, g, h);
+    const Macro m = node_macros(f, n, g, h, P);
+    const float usx = m.ux * P.nsub, usy = m.uy * P.nsub;
+    hist[0 * plane + o] = m.phi;
+    hist[1 * plane + o] = coupling_Q(m.phi, m.theta, m.U, P);
+    hist[2 * plane + o] = m.C * usx;
+    hist[3 * plane + o] = m.C * usy;
+    hist[4 * plane + o] = m.H * usx;
+    hist[5 * plane + o] = m.H * usy;
+}
+
+template <class Store>
+__global__ void k_macros(const StepParams P, const typename Store::T* __restrict__ sc,
+                         const typename Store::T* __restrict__ fl, float* __restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long o = (long long)y * P.pitch + x;
+    float f[5], n[5], g[5], h[9];
+    load_node<Store>(P, sc, fl, o, f, n, g, h);
+    const Macro m = node_macros(f, n, g, h, P);
+    const long long plane = P.plane;
+    out[0 * plane + o] = m.phi;
+    out[1 * plane + o] = m.C;
+    out[2 * plane + o] = m.U;
+    out[3 * plane + o] = m.theta;
+    out[4 * plane + o] = m.ux;
+    out[5 * plane + o] = m.uy;
+    out[6 * plane + o] = m.p;
+}
+
+template <class Store>
+__global__ void k_decode(const StepParams P, const typename Store::T* __restrict__ sc,
+                         const typename Store::T* __restrict__ fl, float* __restrict__ out)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long total = P.plane * kPlanes;
+    if (i >= total) return;
+    const int q = (int)(i / P.plane);
+    const long long r = i - (long long)q * P.plane;
+    out[i] = q < kH ? Store::load(sc, i, q, P) : Store::load(fl, (q - kH) * P.plane + r, q, P);
+}
+
+template <class Store>
+__global__ void k_encode(const StepParams P, const float* __restrict__ in, typename Store::T* __restrict__ sc,
+                         typename Store::T* __restrict__ fl)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long total = P.plane * kPlanes;
+    if (i >= total) return;
+    const int q = (int)(i / P.plane);
+    const long long r = i - (long long)q * P.plane;
+    if (q < kH)
+        Store::store(sc, i, q, in[i], P);
+    else
+        Store::store(fl, (q - kH) * P.plane + r, q, in[i], P);
+}
+
+// ------------------------------------------------------------- reductions
+constexpr int kRedThreads = 256;
+constexpr int kRedVals = 7;  // sf, C, H, h, max|u|, bad, phi
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, d));
+    return v;
+}
+
+// Pass 1: each block accumulates a fixed, grid-strided subset of nodes in
+// FP64 and writes its kRedVals partials (deterministic order).
+template <class Store>
+__global__ void __launch_bounds__(kRedThreads) k_reduce_nodes(const StepParams P, const typename Store::T* __restrict__ sc,
+                                                              const typename Store::T* __restrict__ fl,
+                                                              double* __restrict__ partials)
+{
+    double acc[kRedVals] = {0, 0, 0, 0, 0, 0, 0};
+    const long long N = (long long)P.nx * P.ny;
+    for (long long t = blockIdx.x * (long long)kRedThreads + threadIdx.x; t < N;
+         t += (long long)gridDim.x * kRedThreads) {
+        const int y = (int)(t / P.nx), x = (int)(t - (long long)y * P.nx);
+        const long long o = (long long)y * P.pitch + x;
+        float f[5], n[5], g[5], h[9];
+        load_node<Store>(P, sc, fl, o, f, n, g, h);
+        const Macro m = node_macros(f, n, g, h, P);
+        double sh = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sh += (double)h[i];
+        const double u = sqrt((double)m.ux * m.ux + (double)m.uy * m.uy);
+        acc[0] += 0.5 * (1.0 + (double)m.phi);
+        acc[1] += (double)m.C;
+        acc[2] += (double)m.H;
+        acc[3] += sh;
+        acc[4] = fmax(acc[4], u);
+        acc[5] += (isfinite(m.phi) && isfinite(m.C) && isfinite(m.theta) && isfinite(u)) ? 0.0 : 1.0;
+        acc[6] += (double)m.phi;
+    }
+    __shared__ double sm[kRedVals][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kRedVals; ++k) {
+        const double v = k == 4 ? warp_max(acc[k]) : warp_sum(acc[k]);
+        if (lane == 0) sm[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kRedVals) {
+        const int k = threadIdx.x;
+        double v = sm[k][0];
+        for (int w = 1; w < kRedThreads / 32; ++w) v = (k == 4) ? fmax(v, sm[k][w]) : v + sm[k][w];
+        partials[(long long)blockIdx.x * kRedVals + k] = v;
+    }
+}
+
+// Pass 2: one block folds the partials in block order.
+__global__ void k_reduce_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out)
+{
+    const int k = threadIdx.x;
+    if (k >= kRedVals) return;
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double p = partials[(long long)b * kRedVals + k];
+        v = (k == 4) ? fmax(v, p) : v + p;
+    }
+    out[k] = v;
+}
+
+template <class Store>
+__device__ __forceinline__ double phi_at(const StepParams& P, const typename Store::T* sc, int x, int y)
+{
+    const long long o = (long long)y * P.pitch + x;
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) s += Store::load(sc, (kF + i) * P.plane + o, kF + i, P);
+    return (double)s;
+}
+
+template <class Store>
+__device__ double phi_bilinear(const StepParams& P, const typename Store::T* sc, double px, double py)
+{
+    int i = (int)floor(px), j = (int)floor(py);
+    if (i > P.nx - 2) i = P.nx - 2;
+    if (j > P.ny - 2) j = P.ny - 2;
+    const double fx = px - i, fy = py - j;
+    return (1 - fx) * (1 - fy) * phi_at<Store>(P, sc, i, j) + fx * (1 - fy) * phi_at<Store>(P, sc, i + 1, j) +
+           (1 - fx) * fy * phi_at<Store>(P, sc, i, j + 1) + fx * fy * phi_at<Store>(P, sc, i + 1, j + 1);
+}
+
+// Tip distance along three rays from (cx, cy): block r handles ray r.
+// phi is sampled every half node while the sample is inside the grid; the
+// outermost sample with phi > 0 and its successor are interpolated to 0.
+template <class Store>
+__global__ void __launch_bounds__(kRedThreads) k_tips(const StepParams P, const typename Store::T* __restrict__ sc,
+                                                      double cx, double cy, double c, double s,
+                                                      double* __restrict__ out)
+{
+    const int r = blockIdx.x;
+    const double ex = r == 0 ? c : (r == 1 ? -c : -s);
+    const double ey = r == 0 ? s : (r == 1 ? -s : c);
+    const int jmax = 2 * (P.nx + P.ny) + 4;
+    int last = -1, first_out = jmax;
+    for (int j = threadIdx.x; j < jmax; j += kRedThreads) {
+        const double px = cx + j * 0.5 * ex, py = cy + j * 0.5 * ey;
+        const bool inside = !(px < 0 || py < 0 || px > P.nx - 1 || py > P.ny - 1);
+        if (!inside) {
+            first_out = min(first_out, j);
+            continue;
+        }
+        if (phi_bilinear<Store>(P, sc, px, py) > 0.0) last = max(last, j);
+    }
+    __shared__ int s_last[kRedThreads / 32], s_out[kRedThreads / 32];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        last = max(last, __shfl_down_sync(0xffffffffu, last, d));
+        first_out = min(first_out, __shfl_down_sync(0xffffffffu, first_out, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_last[threadIdx.x >> 5] = last;
+        s_out[threadIdx.x >> 5] = first_out;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kRedThreads / 32; ++w) {
+            last = max(last, s_last[w]);
+            first_out = min(first_out, s_out[w]);
+        }
+        // samples past the first outside one never count (the ray leaves a
+        // rectangle once), so clip `last` to the inside run
+        double tip;
+        if (last < 0 || last >= first_out) {
+            tip = nan("");
+        } else if (last + 1 >= first_out) {
+            tip = last * 0.5;
+        } else {
+            const double v0 = phi_bilinear<Store>(P, sc, cx + last * 0.5 * ex, cy + last * 0.5 * ey);
+            const double v1 = phi_bilinear<Store>(P, sc, cx + (last + 1) * 0.5 * ex, cy + (last + 1) * 0.5 * ey);
+            tip = (last + v0 / (v0 - v1)) * 0.5;
+        }
+        out[7 + r] = tip;
+    }
+}
+
+template <class Store>
+cudaError_t init_t(const StepParams& P, const double* fields, void* sc, void* fl, float* hist, cudaStream_t s)
+{
+    using T = typename Store::T;
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
+    k_init<Store, false><<<g, b, 0, s>>>(P, fields, (T*)sc, (T*)fl, hist);
+    return cudaGetLastError();
+}
+
+template <class Store>
+cudaError_t macros_t(const StepParams& P, const void* sc, const void* fl, float* out, cudaStream_t s)
+{
+    using T = typename Store::T;
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
+    k_macros<Store><<<g, b, 0, s>>>(P, (const T*)sc, (const T*)fl, out);
+    return cudaGetLastError();
+}
+
+template <class Store>
+cudaError_t decode_t(const StepParams& P, const void* sc, const void* fl, float* out, cudaStream_t s)
+{
+    using T = typename Store::T;
+    const long long total = P.plane * kPlanes;
+    k_decode<Store><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, (const T*)sc, (const T*)fl, out);
+    return cudaGetLastError();
+}
+
+template <class Store>
+cudaError_t encode_t(const StepParams& P, const float* in, void* sc, void* fl, cudaStream_t s)
+{
+    using T = typename Store::T;
+    const long long total = P.plane * kPlanes;
+    k_encode<Store><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, in, (T*)sc, (T*)fl);
+    return cudaGetLastError();
+}
+
+template <class Store>
+cudaError_t reduce_t(const StepParams& P, const void* sc, const void* fl, double cx, double cy, double c, double s,
+                     double* partials, double* out, cudaStream_t st)
+{
+    using T = typename Store::T;
+    const int nb = reduce_blocks(P);
+    k_reduce_nodes<Store><<<nb, kRedThreads, 0, st>>>(P, (const T*)sc, (const T*)fl, partials);
+    k_reduce_final<<<1, 32, 0, st>>>(partials, nb, out);
+    k_tips<Store><<<3, kRedThreads, 0, st>>>(P, (const T*)sc, cx, cy, c, s, out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_seed_fields(const StepParams& P, const double* seeds, int ns, double U0, double theta0, double W,
+                               double* fields, uint8_t* grain, cudaStream_t s)
+{
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
+    k_seed_fields<<<g, b, 0, s>>>(P, seeds, ns, U0, theta0, W, fields, grain);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_from_fields(const StepParams& P, int storage, const double* fields, void* sc, void* fl,
+                                    float* hist, cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return init_t<StoreF16>(P, fields, sc, fl, hist, s);
+    case kStoreBF16: return init_t<StoreBF16>(P, fields, sc, fl, hist, s);
+    default: return init_t<StoreF32>(P, fields, sc, fl, hist, s);
+    }
+}
+
+cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
+                          cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return macros_t<StoreF16>(P, sc, fl, out, s);
+    case kStoreBF16: return macros_t<StoreBF16>(P, sc, fl, out, s);
+    default: return macros_t<StoreF32>(P, sc, fl, out, s);
+    }
+}
+
+cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
+                          cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return decode_t<StoreF16>(P, sc, fl, out, s);
+    case kStoreBF16: return decode_t<StoreBF16>(P, sc, fl, out, s);
+    default: return decode_t<StoreF32>(P, sc, fl, out, s);
+    }
+}
+
+cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return encode_t<StoreF16>(P, in, sc, fl, s);
+    case kStoreBF16: return encode_t<StoreBF16>(P, in, sc, fl, s);
+    default: return encode_t<StoreF32>(P, in, sc, fl, s);
+    }
+}
+
+int reduce_blocks(const StepParams& P)
+{
+    const long long N = (long long)P.nx * P.ny;
+    long long b = (N + kRedThreads - 1) / kRedThreads;
+    return (int)(b < 1024 ? b : 1024);
+}
+
+size_t reduce_partials_size(const StepParams& P) { return (size_t)reduce_blocks(P) * kRedVals; }
+
+cudaError_t launch_reduce(const StepParams& P, int storage, const void* sc, const void* fl, double cx, double cy,
+                          double c, double s, double* partials, double* out, cudaStream_t st)
+{
+    switch (storage) {
+    case kStoreF16: return reduce_t<StoreF16>(P, sc, fl, cx, cy, c, s, partials, out, st);
+    case kStoreBF16: return reduce_t<StoreBF16>(P, sc, fl, cx, cy, c, s, partials, out, st);
+    default: return reduce_t<StoreF32>(P, sc, fl, cx, cy, c, s, partials, out, st);
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,58 @@
+// Host-side declarations of the kernel launchers shared by the C-ABI
+// translation unit and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Storage kinds (same values as LBM_FP32/LBM_FP16/LBM_BF16).
+enum Storage { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
+
+inline size_t storage_bytes(int storage) { return storage == kStoreF32 ? 4 : 2; }
+
+// One coupled step (Sec. 3 + Sec. 4): the fused kernel, the wall kernels and
+// the n_sub - 1 flow-only sub-steps; on return cs/cf name the newest buffers.
+struct StepBuffers {
+    void* sc[2];           // scalar populations (phi, C, H): planes 0..14
+    void* fl[2];           // flow populations: planes 15..23
+    float* hist;           // kHist planes
+    float* fb;             // force plane for flow sub-steps (n_sub > 1) or null
+    const uint8_t* grain;  // grain id plane or null (uniform orientation)
+    int cs, cf;            // indices of the buffers holding the newest populations
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // recorded around the fused kernel when set
+};
+
+cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s);
+
+// Initialisation: equilibrium populations from lattice-unit macros
+// (phi, U, theta, ux, uy, p) in FP64 planes, then history = time-0 macros.
+cudaError_t launch_init_from_fields(const StepParams& P, int storage, const double* fields, void* sc, void* fl,
+                                    float* hist, cudaStream_t s);
+
+// Seeded initial fields: phi, grain id, U = U0, theta = theta0 (FP64 planes).
+cudaError_t launch_seed_fields(const StepParams& P, const double* seeds, int ns, double U0, double theta0,
+                               double W, double* fields, uint8_t* grain, cudaStream_t s);
+
+// Macros of every node (FP32 planes phi, C, U, theta, ux, uy, p; lattice units).
+cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
+                          cudaStream_t s);
+
+// Decode populations to FP32 planes / encode FP32 planes into populations.
+cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
+                          cudaStream_t s);
+cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, cudaStream_t s);
+
+// FP64 reductions: out[0..6] = solid fraction sum, sum C, sum H, sum h,
+// max |u| (flow lattice units), non-finite count, sum phi; then out[7..9] =
+// the three tip distances.  `partials` must hold reduce_partials_size()
+// doubles.
+int reduce_blocks(const StepParams& P);
+size_t reduce_partials_size(const StepParams& P);
+cudaError_t launch_reduce(const StepParams& P, int storage, const void* sc, const void* fl, double cx, double cy,
+                          double c, double s, double* partials, double* out, cudaStream_t st);
+
+}  // namespace lbm

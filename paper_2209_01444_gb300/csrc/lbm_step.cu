@@ -1,0 +1,360 @@
+// Fused coupled step (phase field, solute, heat, flow), wall kernel and flow
+// sub-step kernel for sm_103a.
+//
+// One coupled step n -> n+1 (Sec. 3, time-n macros for every model):
+//   1. macros of Eqs. (15), (20), (23), (26) from the node's populations;
+//   2. grad(phi) by the isotropic nine-point stencil on phi^n, which each CTA
+//      builds in shared memory from the phi populations of its tile and a
+//      one-node halo;
+//   3. a_s and N of Eqs. (2)-(3) in the grain's crystal frame; Q of Eq. (5);
+//      J_at of Eq. (7);
+//   4. MRT collisions of the four models in moment space (Appendix B);
+//   5. push streaming; phi uses the modified streaming of Eq. (13)/Remark 2,
+//      f_i(x+c_i, t+1) = [f*_i(x) - (1 - a_s^2(x)) f_i(x+c_i, t)] / a_s^2(x),
+//      whose f_i(x+c_i, t) is read from the same shared tile;
+//   6. history (phi, Q, Cu, Hu at time n) is written in place for the
+//      backward time differences of the next step.
+// Periodic wrap is applied to every streaming destination; on non-periodic
+// sides the wrapped values land on wall nodes, which the wall kernel then
+// overwrites completely.
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.h"
+
+namespace lbm {
+
+namespace {
+
+__device__ __forceinline__ int mirror_or_wrap_local(int g, int n, int periodic, int local, int d)
+{
+    // Neighbour g = node + d seen from local index `local` of the node: a
+    // periodic neighbour (or one inside the domain) is in the halo at
+    // local + d; a non-periodic ghost is the mirror image at local - d.
+    if (!periodic && (g < 0 || g >= n)) return local - d;
+    return local + d;
+}
+
+template <class Store, bool GRAIN, bool WRITE_FB>
+__global__ void __launch_bounds__(TX* TY)
+    k_coupled_step(const StepParams P, const typename Store::T* __restrict__ src,
+                   const typename Store::T* __restrict__ srcf, typename Store::T* __restrict__ dst,
+                   typename Store::T* __restrict__ dstf, float* __restrict__ hist,
+                   const uint8_t* __restrict__ grain, float* __restrict__ fb)
+{
+    __shared__ float fs[5][TY + 2][TX + 2];
+    __shared__ float ps[TY + 2][TX + 2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const long long plane = P.plane;
+
+    // phi populations of the tile and its halo (periodic wrap), and phi there.
+    for (int e = ty * TX + tx; e < (TX + 2) * (TY + 2); e += TX * TY) {
+        const int hx = e % (TX + 2), hy = e / (TX + 2);
+        const int gx = wrap(x0 - 1 + hx, P.nx), gy = wrap(y0 - 1 + hy, P.ny);
+        const long long o = (long long)gy * P.pitch + gx;
+        float sum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            float v = Store::load(src, kF * plane + i * plane + o, kF + i, P);
+            fs[i][hy][hx] = v;
+            sum += v;
+        }
+        ps[hy][hx] = sum;
+    }
+    __syncthreads();
+
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long o = (long long)y * P.pitch + x;
+    const int lx = tx + 1, ly = ty + 1;
+
+    float f[5], n[5], g[5], h[9];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) f[i] = fs[i][ly][lx];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) n[i] = Store::load(src, (kN + i) * plane + o, kN + i, P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = Store::load(src, (kG + i) * plane + o, kG + i, P);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = Store::load(srcf, i * plane + o, kH + i, P);
+    const float phi_prev = hist[0 * plane + o];
+    const float Q_prev = hist[1 * plane + o];
+    const float Cux_prev = hist[2 * plane + o], Cuy_prev = hist[3 * plane + o];
+    const float Hux_prev = hist[4 * plane + o], Huy_prev = hist[5 * plane + o];
+
+    const Macro m = node_macros(f, n, g, h, P);
+    const float usx = m.ux * P.nsub, usy = m.uy * P.nsub;  // velocity of the scalar lattice
+
+    // grad(phi): (1/cs^2) sum_i w_i c_i phi(x + c_i) over the D2Q9 neighbours
+    const int xl = mirror_or_wrap_local(x - 1, P.nx, P.periodic_x, lx, -1);
+    const int xr = mirror_or_wrap_local(x + 1, P.nx, P.periodic_x, lx, +1);
+    const int yd = mirror_or_wrap_local(y - 1, P.ny, P.periodic_y, ly, -1);
+    const int yu = mirror_or_wrap_local(y + 1, P.ny, P.periodic_y, ly, +1);
+    const float pE = ps[ly][xr], pW = ps[ly][xl], pN = ps[yu][lx], pS = ps[yd][lx];
+    const float pNE = ps[yu][xr], pNW = ps[yu][xl], pSE = ps[yd][xr], pSW = ps[yd][xl];
+    const float gx = (pE - pW) * (1.0f / 3.0f) + (pNE + pSE - pNW - pSW) * (1.0f / 12.0f);
+    const float gy = (pN - pS) * (1.0f / 3.0f) + (pNE + pNW - pSE - pSW) * (1.0f / 12.0f);
+
+    float co = P.cos_o, so = P.sin_o;
+    if (GRAIN) {
+        const float2 cs = P.grain_cs[grain[o]];
+        co = cs.x;
+        so = cs.y;
+    }
+    float as, Nx, Ny;
+    anisotropy(gx, gy, P.eps, co, so, as, Nx, Ny);
+    const float as2 = as * as;
+    const float g2 = gx * gx + gy * gy;
+    const float Q = coupling_Q(m.phi, m.theta, m.U, P);
+
+    // ---- phase field: Eqs. (13)-(14), relaxation rate of Sec. 3.1
+    float fo[5];
+    {
+        const float s1 = 1.0f / (P.kappa3 * as2 + 0.5f);
+        const float S0 = (Q + 0.5f * as2 * (Q - Q_prev)) * P.inv_tau;
+        const float ga = -(1.0f / 3.0f) / as2;
+        collide_d2q5(f, m.phi, 0.0f, 0.0f, m.phi, s1, ga * Nx, ga * Ny, S0, fo);
+    }
+    // ---- solute: Eqs. (17)-(19) with J_at of Eq. (7)
+    float no[5];
+    {
+        float Jx = 0.0f, Jy = 0.0f;
+        if (!(g2 < kGradEps2)) {
+            const float a = -0.35355339059327373f * P.W * (1.0f + (1.0f - P.k) * m.U) * (m.phi - phi_prev) *
+                            rsqrtf(g2);
+            Jx = a * gx;
+            Jy = a * gy;
+        }
+        const float qt = 0.5f * (1.0f - m.phi);
+        const float Cux = m.C * usx, Cuy = m.C * usy;
+        // sum_i c_i G_i = d_t(Cu) + cs^2 (U grad q~ + J_at/D), grad q~ = -grad(phi)/2
+        const float Gx = (Cux - Cux_prev) + (1.0f / 3.0f) * (-0.5f * m.U * gx + Jx * P.inv_D);
+        const float Gy = (Cuy - Cuy_prev) + (1.0f / 3.0f) * (-0.5f * m.U * gy + Jy * P.inv_D);
+        collide_d2q5(n, m.C, Cux, Cuy, qt * m.U, P.s1C, Gx, Gy, 0.0f, no);
+    }
+    // ---- heat: Eqs. (21)-(23)
+    float go[5];
+    {
+        const float Hux = m.H * usx, Huy = m.H * usy;
+        collide_d2q5(g, m.H, Hux, Huy, m.theta, P.s1T, Hux - Hux_prev, Huy - Huy_prev, 0.0f, go);
+    }
+    // ---- flow: Eqs. (24)-(26)
+    float ho[9];
+    collide_flow(h, m, P.s2u, P.rho0, ho);
+
+    // ---- push streaming
+    const int xp = (x + 1 == P.nx) ? 0 : x + 1, xm = (x == 0) ? P.nx - 1 : x - 1;
+    const int yp = (y + 1 == P.ny) ? 0 : y + 1, ym = (y == 0) ? P.ny - 1 : y - 1;
+    const long long rY = (long long)y * P.pitch, rP = (long long)yp * P.pitch, rM = (long long)ym * P.pitch;
+    const long long d5[5] = {rY + x, rY + xp, rP + x, rY + xm, rM + x};
+    const long long d9[9] = {rY + x, rY + xp, rP + x, rY + xm, rM + x, rP + xp, rP + xm, rM + xm, rM + xp};
+
+    {
+        // modified streaming of the phase field: the destination's time-n
+        // population sits in the shared tile (its halo is periodic-wrapped)
+        const float ia = 1.0f / as2, ib = ia - 1.0f;
+        const float fd[5] = {fs[0][ly][lx], fs[1][ly][lx + 1], fs[2][ly + 1][lx], fs[3][ly][lx - 1],
+                             fs[4][ly - 1][lx]};
+#pragma unroll
+        for (int i = 0; i < 5; ++i) Store::store(dst, (kF + i) * plane + d5[i], kF + i, fo[i] * ia - ib * fd[i], P);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store::store(dst, (kN + i) * plane + d5[i], kN + i, no[i], P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store::store(dst, (kG + i) * plane + d5[i], kG + i, go[i], P);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store::store(dstf, i * plane + d9[i], kH + i, ho[i], P);
+
+    // ---- history of the backward differences
+    hist[0 * plane + o] = m.phi;
+    hist[1 * plane + o] = Q;
+    hist[2 * plane + o] = m.C * usx;
+    hist[3 * plane + o] = m.C * usy;
+    hist[4 * plane + o] = m.H * usx;
+    hist[5 * plane + o] = m.H * usy;
+    if (WRITE_FB) fb[o] = m.Fy;
+}
+
+// Flow sub-step (two-time-scaling of Sec. 4): collide and stream h with phi
+// and the force frozen at time n.
+template <class Store>
+__global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const typename Store::T* __restrict__ src,
+                                                      typename Store::T* __restrict__ dst,
+                                                      const float* __restrict__ hist, const float* __restrict__ fb)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long plane = P.plane;
+    const long long o = (long long)y * P.pitch + x;
+    float h[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = Store::load(src, i * plane + o, kH + i, P);
+    Macro m;
+    m.phi = hist[o];
+    m.Fx = P.Fx;
+    m.Fy = fb[o];
+    float jx = h[1] - h[3] + h[5] - h[6] - h[7] + h[8];
+    float jy = h[2] - h[4] + h[5] + h[6] - h[7] - h[8];
+    float rest = h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
+    float usx = jx + 0.5f * m.Fx, usy = jy + 0.5f * m.Fy;
+    float qt = 0.5f * (1.0f - m.phi);
+    m.fsx = -usx;
+    m.fsy = -usy;
+    m.ux = usx + 0.5f * (1.0f - qt) * m.fsx;
+    m.uy = usy + 0.5f * (1.0f - qt) * m.fsy;
+    m.p = 0.6f * (rest - (2.0f / 3.0f) * (m.ux * m.ux + m.uy * m.uy));
+    float ho[9];
+    collide_flow(h, m, P.s2u, P.rho0, ho);
+    const int xp = (x + 1 == P.nx) ? 0 : x + 1, xm = (x == 0) ? P.nx - 1 : x - 1;
+    const int yp = (y + 1 == P.ny) ? 0 : y + 1, ym = (y == 0) ? P.ny - 1 : y - 1;
+    const long long rY = (long long)y * P.pitch, rP = (long long)yp * P.pitch, rM = (long long)ym * P.pitch;
+    const long long d9[9] = {rY + x, rY + xp, rP + x, rY + xm, rM + x, rP + xp, rP + xm, rM + xm, rM + xp};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store::store(dst, i * plane + d9[i], kH + i, ho[i], P);
+}
+
+// Non-equilibrium extrapolation (Guo et al.) on one side pair, applied to the
+// freshly streamed buffer: pop(b) = pop^eq(boundary macros) + pop(f) -
+// pop^eq(macros of f), f the first interior node.  `axis` 1: bottom/top rows
+// over x in [xlo, xhi]; `axis` 0: left/right columns over every y.
+template <class Store>
+__global__ void k_walls(const StepParams P, typename Store::T* __restrict__ pop, typename Store::T* __restrict__ popf,
+                        int axis, int lo, int count, int flow_only)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * count) return;
+    const int which = t / count;           // 0: low side, 1: high side
+    const int j = lo + (t - which * count);
+    const int side = axis == 0 ? which : 2 + which;
+    if (P.bc[side] == 0) return;
+    int xb, yb, xf, yf;
+    if (axis == 0) {
+        yb = yf = j;
+        xb = which ? P.nx - 1 : 0;
+        xf = which ? P.nx - 2 : 1;
+    } else {
+        xb = xf = j;
+        yb = which ? P.ny - 1 : 0;
+        yf = which ? P.ny - 2 : 1;
+    }
+    const long long plane = P.plane;
+    const long long ob = (long long)yb * P.pitch + xb, of = (long long)yf * P.pitch + xf;
+    float f[5], n[5], g[5], h[9];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) f[i] = Store::load(pop, (kF + i) * plane + of, kF + i, P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) n[i] = Store::load(pop, (kN + i) * plane + of, kN + i, P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = Store::load(pop, (kG + i) * plane + of, kG + i, P);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = Store::load(popf, i * plane + of, kH + i, P);
+    const Macro m = node_macros(f, n, g, h, P);
+    const int type = P.bc[side];
+    float ubx = 0.0f, uby = 0.0f, pb = m.p;
+    if (type == 1) {  // inflow
+        ubx = P.uin_x;
+        uby = P.uin_y;
+    } else if (type == 2) {  // outflow
+        ubx = m.ux;
+        uby = m.uy;
+        pb = 0.0f;
+    } else if (type == 3) {  // symmetry
+        ubx = axis == 0 ? 0.0f : m.ux;
+        uby = axis == 0 ? m.uy : 0.0f;
+    }
+    float eb[9], ef[9];
+    feq_flow(pb, ubx, uby, P.rho0, eb);
+    feq_flow(m.p, m.ux, m.uy, P.rho0, ef);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store::store(popf, i * plane + ob, kH + i, eb[i] + h[i] - ef[i], P);
+    if (flow_only) return;
+
+    float phib = m.phi, Cb = m.C, Ub = m.U, thb = m.theta;
+    if (type == 5) {  // Dirichlet far field
+        phib = P.dir_phi;
+        Ub = P.dir_U;
+        Cb = C_of_U(Ub, phib, P.k);
+        thb = P.dir_theta;
+    }
+    const float hb = h_of_phi(P.h_kind, phib), hf = h_of_phi(P.h_kind, m.phi);
+    const float Hb = thb - 0.5f * hb;
+    const float sc = P.nsub;
+    feq_phi(phib, eb);
+    feq_phi(m.phi, ef);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store::store(pop, (kF + i) * plane + ob, kF + i, eb[i] + f[i] - ef[i], P);
+    feq_C(Cb, 0.5f * (1.0f - phib) * Ub, Cb * ubx * sc, Cb * uby * sc, eb);
+    feq_C(m.C, 0.5f * (1.0f - m.phi) * m.U, m.C * m.ux * sc, m.C * m.uy * sc, ef);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store::store(pop, (kN + i) * plane + ob, kN + i, eb[i] + n[i] - ef[i], P);
+    feq_H(thb, hb, Hb * ubx * sc, Hb * uby * sc, eb);
+    feq_H(m.theta, hf, m.H * m.ux * sc, m.H * m.uy * sc, ef);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Store::store(pop, (kG + i) * plane + ob, kG + i, eb[i] + g[i] - ef[i], P);
+}
+
+template <class Store>
+cudaError_t walls(const StepParams& P, void* sc, void* fl, int flow_only, cudaStream_t s)
+{
+    using T = typename Store::T;
+    if (!P.periodic_y) {
+        const int lo = P.periodic_x ? 0 : 1, hi = P.periodic_x ? P.nx - 1 : P.nx - 2;
+        const int count = hi - lo + 1;
+        k_walls<Store><<<(2 * count + 127) / 128, 128, 0, s>>>(P, (T*)sc, (T*)fl, 1, lo, count, flow_only);
+    }
+    if (!P.periodic_x) {
+        k_walls<Store><<<(2 * P.ny + 127) / 128, 128, 0, s>>>(P, (T*)sc, (T*)fl, 0, 0, P.ny, flow_only);
+    }
+    return cudaGetLastError();
+}
+
+template <class Store>
+cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStream_t s)
+{
+    using T = typename Store::T;
+    const dim3 block(TX, TY), grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+    const T* src = (const T*)B.sc[B.cs];
+    const T* srcf = (const T*)B.fl[B.cf];
+    T* dst = (T*)B.sc[1 - B.cs];
+    T* dstf = (T*)B.fl[1 - B.cf];
+    const bool grain = B.grain != nullptr, wfb = n_sub > 1;
+    if (B.ev_begin) cudaEventRecord(B.ev_begin, s);
+    if (grain && wfb)
+        k_coupled_step<Store, true, true><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
+    else if (grain)
+        k_coupled_step<Store, true, false><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
+    else if (wfb)
+        k_coupled_step<Store, false, true><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
+    else
+        k_coupled_step<Store, false, false><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (B.ev_end) cudaEventRecord(B.ev_end, s);
+    if ((e = walls<Store>(P, dst, dstf, 0, s)) != cudaSuccess) return e;
+    B.cs = 1 - B.cs;
+    B.cf = 1 - B.cf;
+    const dim3 fblock(64, 4), fgrid((P.nx + 63) / 64, (P.ny + 3) / 4);
+    for (int sub = 1; sub < n_sub; ++sub) {
+        // phi and the force of time n come from hist/fb; the wall scheme reads
+        // the scalar macros of time n+1 from the newest scalar buffer
+        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, (const T*)B.fl[B.cf], (T*)B.fl[1 - B.cf], B.hist, B.fb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = walls<Store>(P, B.sc[B.cs], B.fl[1 - B.cf], 1, s)) != cudaSuccess) return e;
+        B.cf = 1 - B.cf;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return coupled_step<StoreF16>(P, n_sub, B, s);
+    case kStoreBF16: return coupled_step<StoreBF16>(P, n_sub, B, s);
+    default: return coupled_step<StoreF32>(P, n_sub, B, s);
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,230 @@
+"""ctypes binding of the C ABI in ``include/lbm.h`` (``liblbm.so``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  The raw functions keep their C names (``lbm_create``,
+``lbm_step``, ...); :class:`Simulation` wraps a handle for convenience.  There
+is no CPU fallback: if ``liblbm.so`` cannot be loaded this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENUMERIC, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+BC = {"periodic": 0, "inflow": 1, "outflow": 2, "symmetry": 3, "noslip": 4, "dirichlet": 5}
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+FIELDS = ("phi", "C", "U", "theta", "ux", "uy", "p")
+STATE_PLANES = 30
+ERRORS = {LBM_EINVAL: "EINVAL", LBM_ENOMEM: "ENOMEM", LBM_ECUDA: "ECUDA", LBM_ENUMERIC: "ENUMERIC",
+          LBM_ETIMEOUT: "ETIMEOUT", LBM_ESTATE: "ESTATE"}
+
+
+class lbm_params(ct.Structure):
+    _fields_ = [
+        ("nx", ct.c_int), ("ny", ct.c_int),
+        ("W0", ct.c_double), ("tau0", ct.c_double), ("dx", ct.c_double), ("dt", ct.c_double),
+        ("eps_s", ct.c_double), ("lambda_", ct.c_double), ("k", ct.c_double), ("Mc_inf", ct.c_double),
+        ("D", ct.c_double), ("alpha", ct.c_double), ("nu", ct.c_double), ("rho0", ct.c_double),
+        ("n_sub", ct.c_int), ("h_kind", ct.c_int),
+        ("gbetaT", ct.c_double), ("gbetaC", ct.c_double), ("theta_ref", ct.c_double), ("C_ref", ct.c_double),
+        ("force", ct.c_double * 2),
+        ("bc", ct.c_int * 4),
+        ("u_in", ct.c_double * 2),
+        ("dir_phi", ct.c_double), ("dir_U", ct.c_double), ("dir_theta", ct.c_double),
+        ("storage", ct.c_int),
+    ]
+
+
+class lbm_seed(ct.Structure):
+    _fields_ = [("x", ct.c_double), ("y", ct.c_double), ("R", ct.c_double), ("orient", ct.c_double)]
+
+
+class lbm_metrics(ct.Structure):
+    _fields_ = [("tip", ct.c_double * 3), ("solid_fraction", ct.c_double), ("sum_C", ct.c_double),
+                ("sum_H", ct.c_double), ("sum_h", ct.c_double), ("max_u", ct.c_double),
+                ("nonfinite", ct.c_double), ("sum_phi", ct.c_double), ("step", ct.c_longlong)]
+
+
+# name -> (restype, argtypes) of every function declared in include/lbm.h
+_H = ct.c_void_p
+_DP = ct.POINTER(ct.c_double)
+SIGNATURES = {
+    "lbm_params_default": (ct.c_int, [ct.POINTER(lbm_params), ct.c_int, ct.c_int]),
+    "lbm_create": (ct.c_int, [ct.POINTER(lbm_params), ct.POINTER(ct.c_void_p)]),
+    "lbm_destroy": (None, [_H]),
+    "lbm_set_stream": (ct.c_int, [_H, ct.c_void_p]),
+    "lbm_init_seeds": (ct.c_int, [_H, ct.POINTER(lbm_seed), ct.c_int, ct.c_double, ct.c_double]),
+    "lbm_init_fields": (ct.c_int, [_H, _DP, _DP]),
+    "lbm_step": (ct.c_int, [_H, ct.c_int]),
+    "lbm_synchronize": (ct.c_int, [_H]),
+    "lbm_step_count": (ct.c_longlong, [_H]),
+    "lbm_get_fields": (ct.c_int, [_H, ct.c_uint, _DP]),
+    "lbm_get_state": (ct.c_int, [_H, _DP]),
+    "lbm_get_state_region": (ct.c_int, [_H, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _DP]),
+    "lbm_set_state": (ct.c_int, [_H, _DP]),
+    "lbm_get_metrics": (ct.c_int, [_H, ct.c_double, ct.c_double, ct.c_double, ct.POINTER(lbm_metrics)]),
+    "lbm_checkpoint_bytes": (ct.c_size_t, [_H]),
+    "lbm_save_state": (ct.c_int, [_H, ct.c_void_p, ct.c_size_t]),
+    "lbm_load_state": (ct.c_int, [_H, ct.c_void_p, ct.c_size_t]),
+    "lbm_set_profiling": (ct.c_int, [_H, ct.c_int]),
+    "lbm_kernel_time": (ct.c_int, [_H, _DP, ct.POINTER(ct.c_longlong)]),
+    "lbm_last_error": (ct.c_char_p, [_H]),
+    "lbm_version": (ct.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``liblbm.so`` and declare every C-ABI function; raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(the library has no CPU fallback)")
+    lib = ct.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def make_params(p: dict, storage: str | int = "fp32") -> lbm_params:
+    """Fill an ``lbm_params`` from a problem dict (keys as in the paper's
+    statement, see ``workloads``)."""
+    s = lbm_params()
+    for name, _ in lbm_params._fields_:
+        if name == "storage":
+            s.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+            continue
+        v = p[name]
+        if name == "bc":
+            for i, b in enumerate(v):
+                s.bc[i] = BC[b] if isinstance(b, str) else int(b)
+        elif name in ("force", "u_in"):
+            arr = getattr(s, name)
+            arr[0], arr[1] = float(v[0]), float(v[1])
+        else:
+            setattr(s, name, v)
+    return s
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+class Simulation:
+    """One domain on the current CUDA device."""
+
+    def __init__(self, params: dict, storage: str | int = "fp32", stream=None):
+        self.lib = load()
+        self.params = dict(params)
+        self._p = make_params(params, storage)
+        h = ct.c_void_p()
+        rc = self.lib.lbm_create(ct.byref(self._p), ct.byref(h))
+        if rc != LBM_OK:
+            raise LBMError(rc, self.lib.lbm_last_error(None).decode())
+        self.h = h
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _check(self, rc: int) -> None:
+        if rc != LBM_OK:
+            raise LBMError(rc, self.lib.lbm_last_error(self.h).decode())
+
+    def __del__(self):
+        h, self.h = getattr(self, "h", None), None
+        if h:
+            self.lib.lbm_destroy(h)
+
+    def set_stream(self, stream) -> None:
+        """Accepts a ``torch.cuda.Stream``, a raw ``cudaStream_t`` int, or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.lbm_set_stream(self.h, ct.c_void_p(raw or 0)))
+
+    def init_seeds(self, seeds, U0: float, theta0: float) -> None:
+        a = np.asarray(seeds, np.float64).reshape(-1, 4)
+        arr = (lbm_seed * len(a))(*[lbm_seed(*row) for row in a])
+        self._check(self.lib.lbm_init_seeds(self.h, arr, len(a), U0, theta0))
+
+    def init_fields(self, fields: np.ndarray, orient: np.ndarray | None = None) -> None:
+        f = np.ascontiguousarray(np.asarray(fields, np.float64).reshape(6, self.ny, self.nx))
+        o = None if orient is None else np.ascontiguousarray(np.asarray(orient, np.float64).reshape(self.ny, self.nx))
+        self._check(self.lib.lbm_init_fields(self.h, _dptr(f), None if o is None else _dptr(o)))
+
+    def step(self, n: int = 1) -> None:
+        self._check(self.lib.lbm_step(self.h, int(n)))
+
+    def synchronize(self) -> None:
+        self._check(self.lib.lbm_synchronize(self.h))
+
+    @property
+    def steps(self) -> int:
+        return int(self.lib.lbm_step_count(self.h))
+
+    def fields(self, names=FIELDS) -> dict:
+        mask = 0
+        for n in names:
+            mask |= 1 << FIELDS.index(n)
+        order = [n for n in FIELDS if mask & (1 << FIELDS.index(n))]
+        out = np.empty((len(order), self.ny, self.nx))
+        self._check(self.lib.lbm_get_fields(self.h, mask, _dptr(out)))
+        return {n: out[i] for i, n in enumerate(order)}
+
+    def state(self) -> np.ndarray:
+        out = np.empty((STATE_PLANES, self.ny, self.nx))
+        self._check(self.lib.lbm_get_state(self.h, _dptr(out)))
+        return out
+
+    def state_region(self, x0: int, y0: int, w: int, hgt: int) -> np.ndarray:
+        out = np.empty((STATE_PLANES, hgt, w))
+        self._check(self.lib.lbm_get_state_region(self.h, x0, y0, w, hgt, _dptr(out)))
+        return out
+
+    def set_state(self, st: np.ndarray) -> None:
+        a = np.ascontiguousarray(np.asarray(st, np.float64).reshape(STATE_PLANES, self.ny, self.nx))
+        self._check(self.lib.lbm_set_state(self.h, _dptr(a)))
+
+    def metrics(self, cx: float, cy: float, orient: float = 0.0, check: bool = True) -> dict:
+        m = lbm_metrics()
+        rc = self.lib.lbm_get_metrics(self.h, cx, cy, orient, ct.byref(m))
+        if check:
+            self._check(rc)
+        return {"tip_px": m.tip[0], "tip_mx": m.tip[1], "tip_py": m.tip[2], "solid_fraction": m.solid_fraction,
+                "sum_C": m.sum_C, "sum_H": m.sum_H, "sum_h": m.sum_h, "max_u": m.max_u,
+                "nonfinite": m.nonfinite, "sum_phi": m.sum_phi, "step": m.step, "rc": rc}
+
+    def set_profiling(self, enable: bool) -> None:
+        self._check(self.lib.lbm_set_profiling(self.h, int(enable)))
+
+    def kernel_time(self) -> tuple[float, int]:
+        """(total ms, launches) of the fused kernel since profiling was enabled."""
+        ms, n = ct.c_double(), ct.c_longlong()
+        self._check(self.lib.lbm_kernel_time(self.h, ct.byref(ms), ct.byref(n)))
+        return ms.value, n.value
+
+    def save(self) -> bytes:
+        n = self.lib.lbm_checkpoint_bytes(self.h)
+        buf = ct.create_string_buffer(n)
+        self._check(self.lib.lbm_save_state(self.h, buf, n))
+        return buf.raw
+
+    def load(self, blob: bytes) -> None:
+        buf = ct.create_string_buffer(blob, len(blob))
+        self._check(self.lib.lbm_load_state(self.h, buf, len(blob)))

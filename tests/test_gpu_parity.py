@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Error metric per field X: max|X_gpu - X_ref| / max(max|X_ref|, floor_X) with
+floors phi: 1, C: 1, U: 1, theta: |theta0|, u: 1e-6, p: 1e-6 (paper units).
+Bound: 1e-4 for FP32 storage; 1e-2 (and tips within 1 lattice unit) for the
+FP16/BF16 equilibrium-shifted storage.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2209_01444_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-4
+LOWP_TOL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    from paper_2209_01444_gb300 import build_ext, lbm as L
+
+    build_ext.build()
+    L.load()
+    torch.cuda.init()
+    return L
+
+
+def floors(theta0=0.55):
+    return {"phi": 1.0, "C": 1.0, "U": 1.0, "theta": abs(theta0), "ux": 1e-6, "uy": 1e-6, "p": 1e-6}
+
+
+def field_errors(got, want, theta0=0.55):
+    fl = floors(theta0)
+    out = {}
+    for k, v in want.items():
+        scale = max(np.abs(v).max(), fl[k])
+        out[k] = float(np.abs(got[k] - v).max() / scale)
+    return out
+
+
+def assert_close(got, want, tol, theta0=0.55, where=""):
+    errs = field_errors(got, want, theta0)
+    bad = {k: e for k, e in errs.items() if not e <= tol}
+    assert not bad, f"{where}: {bad} (all: {errs})"
+
+
+def pair(lbm, params, storage="fp32"):
+    return lbm.Simulation(params, storage), O.Oracle(params)
+
+
+# ------------------------------------------------------------------ starts
+def test_seeded_start_matches(lbm):
+    c = W.single_seed_periodic()
+    g, o = pair(lbm, c.params)
+    g.init_seeds(c.seeds, c.U0, c.theta0)
+    o.init_seeds(c.seeds, c.U0, c.theta0)
+    assert_close(g.fields(), o.fields(), 1e-6, where="t=0")
+    np.testing.assert_allclose(g.state(), o.state(), rtol=0, atol=2e-7)
+
+
+def test_multi_seed_grain_map_and_start(lbm):
+    c = W.multi_seed(n=256, count=6, min_spacing=60.0)
+    g, o = pair(lbm, c.params)
+    g.init_seeds(c.seeds, c.U0, c.theta0)
+    o.init_seeds(c.seeds, c.U0, c.theta0)
+    assert_close(g.fields(), o.fields(), 1e-6, c.theta0, where="t=0")
+    g.step(30)
+    o.step(30)
+    assert_close(g.fields(), o.fields(), FP32_TOL, c.theta0, where="t=30")
+
+
+# ------------------------------------------------------------------ runs
+def test_single_seed_periodic_box_1000_steps(lbm):
+    """128 x 128 periodic box, one seed R = 8, Delta = 0.55, eps = 0.05,
+    buoyancy on: fields match the oracle at steps 1, 10, 100 and 1000."""
+    c = W.single_seed_periodic()
+    g, o = pair(lbm, c.params)
+    g.init_seeds(c.seeds, c.U0, c.theta0)
+    o.init_seeds(c.seeds, c.U0, c.theta0)
+    for T in (1, 10, 100, 1000):
+        g.step(T - g.steps)
+        o.step(T - o.steps)
+        assert_close(g.fields(), o.fields(), FP32_TOL, where=f"step {T}")
+
+
+BCS = {
+    "periodic": ("periodic",) * 4,
+    "inflow_outflow_symmetry": ("inflow", "outflow", "symmetry", "symmetry"),
+    "channel_noslip": ("periodic", "periodic", "noslip", "noslip"),
+    "dirichlet": ("dirichlet",) * 4,
+    "mixed": ("inflow", "outflow", "noslip", "symmetry"),
+}
+
+
+@pytest.mark.parametrize("shape", [(37, 23), (70, 45)])
+@pytest.mark.parametrize("bcs", sorted(BCS))
+def test_random_fields_parity(lbm, bcs, shape):
+    """Random smooth fields (liquid, solid and interface, flow, four grains)
+    on grids spanning several tiles with ragged tails, every wall type."""
+    nx, ny = shape
+    p = W.thermosolutal_params(nx, ny, bc=BCS[bcs], u_in=(0.15, 0.02), gbetaT=W.GBETA_T * 5,
+                               gbetaC=W.GBETA_C * 5, theta_ref=-0.5, dir_theta=-0.4)
+    f, orient = W.random_fields(nx, ny, rng_seed=11 + nx)
+    g, o = pair(lbm, p)
+    g.init_fields(f, orient)
+    o.init_fields(f, orient)
+    assert_close(g.fields(), o.fields(), 1e-6, 0.5, where="t=0")
+    for T in (1, 5, 60):
+        g.step(T - g.steps)
+        o.step(T - o.steps)
+        assert_close(g.fields(), o.fields(), FP32_TOL, 0.5, where=f"{bcs} {shape} step {T}")
+
+
+@pytest.mark.parametrize("n_sub,h_kind", [(3, 0), (1, 1), (4, 1)])
+def test_flow_substeps_and_h_kind(lbm, n_sub, h_kind):
+    nx, ny = 48, 40
+    p = W.thermosolutal_params(nx, ny, bc=BCS["inflow_outflow_symmetry"], u_in=(0.3, 0.0), n_sub=n_sub,
+                               h_kind=h_kind, nu=2.0 * n_sub, gbetaT=W.GBETA_T, theta_ref=-0.5)
+    f, orient = W.random_fields(nx, ny, rng_seed=5)
+    g, o = pair(lbm, p)
+    g.init_fields(f, orient)
+    o.init_fields(f, orient)
+    for T in (1, 40):
+        g.step(T - g.steps)
+        o.step(T - o.steps)
+        assert_close(g.fields(), o.fields(), FP32_TOL, 0.5, where=f"n_sub={n_sub} h={h_kind} step {T}")
+
+
+def test_metrics_match(lbm):
+    c = W.single_seed_periodic()
+    g, o = pair(lbm, c.params)
+    g.init_seeds(c.seeds, c.U0, c.theta0)
+    o.init_seeds(c.seeds, c.U0, c.theta0)
+    g.step(300)
+    o.step(300)
+    for orient in (0.0, 0.35):
+        mg, mo = g.metrics(64, 64, orient), o.metrics(64, 64, orient)
+        for k in ("tip_px", "tip_mx", "tip_py"):
+            assert mg[k] == pytest.approx(mo[k], abs=2e-3), k
+        for k in ("solid_fraction", "sum_C", "sum_H", "sum_h", "sum_phi"):
+            assert mg[k] == pytest.approx(mo[k], rel=1e-5, abs=1e-6), k
+        assert mg["max_u"] == pytest.approx(mo["max_u"], rel=1e-3)
+        assert mg["nonfinite"] == 0 and mg["step"] == 300
+
+
+# ------------------------------------------------------------------ state
+def test_graph_replay_equals_direct_launches(lbm):
+    c = W.single_seed_periodic(n=64, R=6.0)
+    a = lbm.Simulation(c.params)
+    b = lbm.Simulation(c.params)
+    for s in (a, b):
+        s.init_seeds(c.seeds, c.U0, c.theta0)
+    a.step(37)          # two captured 16-step graphs + 5 direct steps
+    for _ in range(37):
+        b.step(1)
+    np.testing.assert_array_equal(a.state(), b.state())
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_checkpoint_resume_is_bit_exact(lbm, storage):
+    c = W.single_seed_periodic(n=64, R=6.0)
+    a = lbm.Simulation(c.params, storage)
+    a.init_seeds(c.seeds, c.U0, c.theta0)
+    a.step(20)
+    blob = a.save()
+    a.step(25)
+    b = lbm.Simulation(c.params, storage)
+    b.load(blob)
+    assert b.steps == 20
+    b.step(25)
+    np.testing.assert_array_equal(a.state(), b.state())
+
+
+def test_state_round_trip(lbm):
+    p = W.thermosolutal_params(40, 30)
+    f, orient = W.random_fields(40, 30, rng_seed=2)
+    g = lbm.Simulation(p)
+    g.init_fields(f, orient)
+    g.step(3)
+    st = g.state()
+    g.set_state(st)
+    np.testing.assert_array_equal(g.state(), st)
+    np.testing.assert_array_equal(g.state_region(5, 7, 20, 11), st[:, 7:18, 5:25])
+
+
+def test_non_finite_state_is_reported(lbm):
+    """Non-finite values are refused on the host by lbm_set_state; populations
+    large enough to overflow FP32 sums are caught by the FP64 reduction and
+    reported as LBM_ENUMERIC (no device fault involved)."""
+    p = W.thermosolutal_params(32, 32)
+    g = lbm.Simulation(p)
+    f, orient = W.random_fields(32, 32, rng_seed=4)
+    g.init_fields(f, orient)
+    st = g.state()
+    bad = st.copy()
+    bad[0, 10, 10] = np.inf
+    with pytest.raises(lbm.LBMError) as e:
+        g.set_state(bad)
+    assert e.value.code == lbm.LBM_EINVAL
+    assert g.metrics(16, 16)["nonfinite"] == 0
+    big = st.copy()
+    big[0:5, 10, 10] = 3.0e38      # finite in FP32, their sum is not
+    g.set_state(big)
+    m = g.metrics(16, 16, check=False)
+    assert m["rc"] == lbm.LBM_ENUMERIC and m["nonfinite"] == 1
+
+
+# ------------------------------------------------------------------ precision
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_reduced_precision_storage_accuracy(lbm, storage):
+    """FP16/BF16 equilibrium-shifted population storage with FP32 collisions:
+    every field within 1e-2 of the FP64 oracle after 1000 steps and the tips
+    within one lattice unit."""
+    c = W.single_seed_periodic()
+    g = lbm.Simulation(c.params, storage)
+    o = O.Oracle(c.params)
+    g.init_seeds(c.seeds, c.U0, c.theta0)
+    o.init_seeds(c.seeds, c.U0, c.theta0)
+    g.step(1000)
+    o.step(1000)
+    errs = field_errors(g.fields(), o.fields())
+    assert max(errs["phi"], errs["C"], errs["theta"], errs["U"]) <= LOWP_TOL, errs
+    mg, mo = g.metrics(64, 64), o.metrics(64, 64)
+    for k in ("tip_px", "tip_mx", "tip_py"):
+        assert abs(mg[k] - mo[k]) <= 1.0, (k, mg[k], mo[k])
