@@ -525,12 +525,12 @@ static void collide_stream_flow(orc_sim* s, int x, int y, double phi, double Fx,
  *   pop(b) = pop^eq(boundary macros) + [pop(f) - pop^eq(macros of f)],
  * where the macros of f are those of Eqs. (15), (20), (23), (26) evaluated
  * from the populations held at f. */
-static void nee_node(orc_sim* s, int b, int f, int side, int flow_only)
+static void nee_node(orc_sim* s, double* fp, double* np_, double* gp, int b, int f, int side, int flow_only)
 {
     const int N = s->N;
     const int type = s->P.bc[side];
     const double k = s->P.k;
-    const node_macro mf = macros_at(s, s->f2, s->n2, s->g2, s->h2, f);
+    const node_macro mf = macros_at(s, fp, np_, gp, s->h2, f);
     double ubx, uby, pb = mf.p;
     switch (type) {
     case ORC_BC_INFLOW:
@@ -570,29 +570,32 @@ static void nee_node(orc_sim* s, int b, int f, int side, int flow_only)
     const double sc = s->nsub_scale;
     orc_feq_phi(phib, eb);
     orc_feq_phi(mf.phi, ef);
-    for (int i = 0; i < 5; ++i) s->f2[i * N + b] = eb[i] + s->f2[i * N + f] - ef[i];
+    for (int i = 0; i < 5; ++i) fp[i * N + b] = eb[i] + fp[i * N + f] - ef[i];
     orc_neq(Cb, 0.5 * (1.0 - phib) * Ub, Cb * ubx * sc, Cb * uby * sc, eb);
     orc_neq(mf.C, 0.5 * (1.0 - mf.phi) * mf.U, mf.C * mf.ux * sc, mf.C * mf.uy * sc, ef);
-    for (int i = 0; i < 5; ++i) s->n2[i * N + b] = eb[i] + s->n2[i * N + f] - ef[i];
+    for (int i = 0; i < 5; ++i) np_[i * N + b] = eb[i] + np_[i * N + f] - ef[i];
     orc_geq(thetab, hb, Hb * ubx * sc, Hb * uby * sc, eb);
     orc_geq(mf.theta, hf, mf.H * mf.ux * sc, mf.H * mf.uy * sc, ef);
-    for (int i = 0; i < 5; ++i) s->g2[i * N + b] = eb[i] + s->g2[i * N + f] - ef[i];
+    for (int i = 0; i < 5; ++i) gp[i * N + b] = eb[i] + gp[i * N + f] - ef[i];
 }
 
-static void apply_boundaries(orc_sim* s, int flow_only)
+/* The scalar arrays passed in are the newest scalar populations: the freshly
+ * streamed f2/n2/g2 in the coupled step, f/nC/g (time n+1) during the flow
+ * sub-steps.  The flow populations are always the freshly streamed h2. */
+static void apply_boundaries(orc_sim* s, double* fp, double* np_, double* gp, int flow_only)
 {
     const int nx = s->nx, ny = s->ny;
     if (!is_periodic_y(s)) {
         int xlo = is_periodic_x(s) ? 0 : 1, xhi = is_periodic_x(s) ? nx - 1 : nx - 2;
         for (int x = xlo; x <= xhi; ++x) {
-            nee_node(s, 0 * nx + x, 1 * nx + x, 2, flow_only);
-            nee_node(s, (ny - 1) * nx + x, (ny - 2) * nx + x, 3, flow_only);
+            nee_node(s, fp, np_, gp, 0 * nx + x, 1 * nx + x, 2, flow_only);
+            nee_node(s, fp, np_, gp, (ny - 1) * nx + x, (ny - 2) * nx + x, 3, flow_only);
         }
     }
     if (!is_periodic_x(s)) {
         for (int y = 0; y < ny; ++y) {
-            nee_node(s, y * nx + 0, y * nx + 1, 0, flow_only);
-            nee_node(s, y * nx + nx - 1, y * nx + nx - 2, 1, flow_only);
+            nee_node(s, fp, np_, gp, y * nx + 0, y * nx + 1, 0, flow_only);
+            nee_node(s, fp, np_, gp, y * nx + nx - 1, y * nx + nx - 2, 1, flow_only);
         }
     }
 }
@@ -694,7 +697,7 @@ static void coupled_step(orc_sim* s)
             collide_stream_flow(s, x, y, phi, Fx, Fy);
         }
     }
-    apply_boundaries(s, 0);
+    apply_boundaries(s, s->f2, s->n2, s->g2, 0);
 
     /* history for the backward differences (reading R3) */
 #pragma omp parallel for schedule(static)
@@ -722,7 +725,7 @@ static void coupled_step(orc_sim* s)
                 body_force(s, s->theta[idx], s->C[idx], &Fx, &Fy);
                 collide_stream_flow(s, x, y, s->phi[idx], Fx, Fy);
             }
-        apply_boundaries(s, 1);
+        apply_boundaries(s, s->f, s->nC, s->g, 1);
         swap_ptr(&s->h, &s->h2);
     }
     s->steps++;

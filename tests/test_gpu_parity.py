@@ -63,7 +63,7 @@ def test_seeded_start_matches(lbm):
     g.init_seeds(c.seeds, c.U0, c.theta0)
     o.init_seeds(c.seeds, c.U0, c.theta0)
     assert_close(g.fields(), o.fields(), 1e-6, where="t=0")
-    np.testing.assert_allclose(g.state(), o.state(), rtol=0, atol=2e-7)
+    np.testing.assert_allclose(g.state(), o.state(), rtol=0, atol=1e-6)
 
 
 def test_multi_seed_grain_map_and_start(lbm):
