@@ -58,6 +58,7 @@ struct lbm_handle {
     long long prof_launches = 0;
     // lattice conversion
     double vf = 1, pscale = 1;  // paper velocity -> flow lattice, lattice pressure -> paper
+    double ref[lbm::kPlanes];   // reference equilibrium of the stored deviations
 };
 
 namespace {
@@ -150,7 +151,7 @@ void derive(lbm_handle* h)
     P.gbT = (float)(p.gbetaT * ff);
     P.gbC = (float)(p.gbetaC * ff);
     P.theta_ref = (float)p.theta_ref;
-    P.C_ref = (float)p.C_ref;
+    P.dC_ref = (float)(1.0 - p.C_ref);
     P.nsub = (float)p.n_sub;
     P.cos_o = 1.0f;
     P.sin_o = 0.0f;
@@ -160,19 +161,21 @@ void derive(lbm_handle* h)
     P.dir_phi = (float)p.dir_phi;
     P.dir_U = (float)p.dir_U;
     P.dir_theta = (float)p.dir_theta;
-    // Reference state of the shifted 16-bit storage: liquid at rest with
-    // phi = -1, C = 1 (U = 0), theta = theta_ref, p = 0.
+    // Reference equilibrium whose deviations are stored (liquid at rest:
+    // phi = -1, C = 1, theta = theta_ref, p = 0), kept in FP64 for the state
+    // interface.
     const double w5[5] = {1.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
-    const double hm1 = p.h_kind == 1 ? -1.0 : -1.0;  // h(-1) = -1 for both kinds
+    const double th = (double)P.theta_ref;
     for (int i = 0; i < 5; ++i) {
-        P.ref[lbm::kF + i] = (float)(-w5[i]);
-        P.ref[lbm::kN + i] = (float)(i == 0 ? 1.0 : 0.0);
-        P.ref[lbm::kG + i] = (float)(w5[i] * p.theta_ref - (i == 0 ? 0.5 * hm1 : 0.0));
+        h->ref[lbm::kF + i] = -w5[i];
+        h->ref[lbm::kN + i] = i == 0 ? 1.0 : 0.0;
+        h->ref[lbm::kG + i] = w5[i] * th + (i == 0 ? 0.5 : 0.0);
     }
-    for (int i = 0; i < 9; ++i) P.ref[lbm::kH + i] = (float)(i == 0 ? p.rho0 : 0.0);
+    for (int i = 0; i < 9; ++i) h->ref[lbm::kH + i] = i == 0 ? (double)P.rho0 : 0.0;
+    // 16-bit scales keep the smallest deviations out of the subnormal range
     for (int q = 0; q < lbm::kPlanes; ++q) {
         float sc = 1.0f;
-        if (p.storage == LBM_FP16) sc = q >= lbm::kH ? 1024.0f : 16.0f;  // keep deviations in the normal range
+        if (p.storage == LBM_FP16) sc = q >= lbm::kH ? 1024.0f : 16.0f;
         P.scale[q] = sc;
         P.inv_scale[q] = 1.0f / sc;
     }
@@ -491,14 +494,16 @@ int lbm_get_fields(lbm_handle* h, unsigned mask, double* out)
                                 h->stream));
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     const int nx = h->P.nx, ny = h->P.ny, pitch = h->P.pitch;
+    // device planes hold phi + 1, C - 1, U, theta - theta_ref, ux, uy, p
     const double scale[LBM_NUM_FIELDS] = {1, 1, 1, 1, 1.0 / h->vf, 1.0 / h->vf, h->pscale};
+    const double offset[LBM_NUM_FIELDS] = {-1.0, 1.0, 0, (double)h->P.theta_ref, 0, 0, 0};
     size_t k = 0;
     for (int q = 0; q < LBM_NUM_FIELDS; ++q) {
         if (!(mask & (1u << q))) continue;
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x)
                 out[k * (size_t)nx * ny + (size_t)y * nx + x] =
-                    (double)host[(size_t)q * h->P.plane + (size_t)y * pitch + x] * scale[q];
+                    (double)host[(size_t)q * h->P.plane + (size_t)y * pitch + x] * scale[q] + offset[q];
         ++k;
     }
     return LBM_OK;
@@ -518,10 +523,12 @@ int lbm_get_state(lbm_handle* h, double* out)
                                 cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     const int nx = h->P.nx, ny = h->P.ny, pitch = h->P.pitch;
-    for (int q = 0; q < LBM_STATE_PLANES; ++q)
+    for (int q = 0; q < LBM_STATE_PLANES; ++q) {
+        const double r = q < lbm::kPlanes ? h->ref[q] : 0.0;
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x)
-                out[(size_t)q * nx * ny + (size_t)y * nx + x] = host[q * plane + (size_t)y * pitch + x];
+                out[(size_t)q * nx * ny + (size_t)y * nx + x] = r + (double)host[q * plane + (size_t)y * pitch + x];
+    }
     return LBM_OK;
 }
 
@@ -542,7 +549,11 @@ int lbm_get_state_region(lbm_handle* h, int x0, int y0, int w, int hgt, double* 
                                       hgt, cudaMemcpyDeviceToHost, h->stream));
     }
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-    for (size_t i = 0; i < host.size(); ++i) out[i] = host[i];
+    const size_t wn = (size_t)w * hgt;
+    for (int q = 0; q < LBM_STATE_PLANES; ++q) {
+        const double r = q < lbm::kPlanes ? h->ref[q] : 0.0;
+        for (size_t i = 0; i < wn; ++i) out[q * wn + i] = r + (double)host[q * wn + i];
+    }
     return LBM_OK;
 }
 
@@ -559,7 +570,7 @@ int lbm_set_state(lbm_handle* h, const double* in)
             for (int x = 0; x < nx; ++x) {
                 double v = in[(size_t)q * nx * ny + (size_t)y * nx + x];
                 if (!isfinite(v)) return fail(h, LBM_EINVAL, "non-finite state value");
-                host[q * plane + (size_t)y * pitch + x] = (float)v;
+                host[q * plane + (size_t)y * pitch + x] = (float)(q < lbm::kPlanes ? v - h->ref[q] : v);
             }
     LBM_CUDA(h, cudaMemcpyAsync(h->d_f32, host.data(), plane * lbm::kPlanes * sizeof(float), cudaMemcpyHostToDevice,
                                 h->stream));

@@ -68,7 +68,7 @@ __global__ void k_seed_fields(const StepParams P, const double* __restrict__ see
 // Equilibrium populations of the given macros, then history = the macros
 // recovered from the stored populations (so the first backward differences
 // vanish).
-template <class Store, bool GRAIN>
+template <class Store>
 __global__ void k_init(const StepParams P, const double* __restrict__ fields, typename Store::T* __restrict__ sc,
                        typename Store::T* __restrict__ fl, float* __restrict__ hist)
 {
@@ -77,25 +77,30 @@ __global__ void k_init(const StepParams P, const double* __restrict__ fields, ty
     if (x >= P.nx || y >= P.ny) return;
     const long long plane = P.plane;
     const long long o = (long long)y * P.pitch + x;
-    const float phi = (float)fields[0 * plane + o], U = (float)fields[1 * plane + o];
-    const float theta = (float)fields[2 * plane + o];
+    // macro deviations from the reference state, formed in FP64
+    const double phi = fields[0 * plane + o], U = fields[1 * plane + o];
+    const double k = P.k;
+    const float p1 = (float)(phi + 1.0);
+    const float dC = (float)(0.5 * (1.0 + k - (1.0 - k) * phi) * (1.0 + (1.0 - k) * U) - 1.0);
+    const float dth = (float)(fields[2 * plane + o] - (double)P.theta_ref);
+    const float Uf = (float)U;
     const float ux = (float)fields[3 * plane + o], uy = (float)fields[4 * plane + o];
     const float p = (float)fields[5 * plane + o];
-    const float C = C_of_U(U, phi, P.k);
-    const float hphi = h_of_phi(P.h_kind, phi);
-    const float H = theta - 0.5f * hphi;
+    const float hp1 = h_plus_1(P.h_kind, p1);
+    const float H = (P.theta_ref + 0.5f) + dth - 0.5f * hp1;
+    const float C = 1.0f + dC;
     const float sx = ux * P.nsub, sy = uy * P.nsub;
     float e[9];
-    feq_phi(phi, e);
+    deq_phi(p1, e);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(sc, (kF + i) * plane + o, kF + i, e[i], P);
-    feq_C(C, 0.5f * (1.0f - phi) * U, C * sx, C * sy, e);
+    deq_C(dC, (1.0f - 0.5f * p1) * Uf, C * sx, C * sy, e);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(sc, (kN + i) * plane + o, kN + i, e[i], P);
-    feq_H(theta, hphi, H * sx, H * sy, e);
+    deq_H(dth, hp1, H * sx, H * sy, e);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(sc, (kG + i) * plane + o, kG + i, e[i], P);
-    feq_flow(p, ux, uy, P.rho0, e);
+    deq_flow(p, ux, uy, e);
 #pragma unroll
     for (int i = 0; i < 9; ++i) Store::store(fl, i * plane + o, kH + i, e[i], P);
 
@@ -104,13 +109,15 @@ __global__ void k_init(const StepParams P, const double* __restrict__ fields, ty
     const Macro m = node_macros(f, n, g, h, P);
     const float usx = m.ux * P.nsub, usy = m.uy * P.nsub;
     hist[0 * plane + o] = m.phi;
-    hist[1 * plane + o] = coupling_Q(m.phi, m.theta, m.U, P);
-    hist[2 * plane + o] = m.C * usx;
-    hist[3 * plane + o] = m.C * usy;
+    hist[1 * plane + o] = coupling_Q(m.phi, P.theta_ref + m.dth, m.U, P);
+    hist[2 * plane + o] = (1.0f + m.dC) * usx;
+    hist[3 * plane + o] = (1.0f + m.dC) * usy;
     hist[4 * plane + o] = m.H * usx;
     hist[5 * plane + o] = m.H * usy;
 }
 
+// Macro deviations of every node: phi + 1, C - 1, U, theta - theta_ref, ux,
+// uy, p (flow lattice units); the host adds the reference values in FP64.
 template <class Store>
 __global__ void k_macros(const StepParams P, const typename Store::T* __restrict__ sc,
                          const typename Store::T* __restrict__ fl, float* __restrict__ out)
@@ -123,10 +130,10 @@ __global__ void k_macros(const StepParams P, const typename Store::T* __restrict
     load_node<Store>(P, sc, fl, o, f, n, g, h);
     const Macro m = node_macros(f, n, g, h, P);
     const long long plane = P.plane;
-    out[0 * plane + o] = m.phi;
-    out[1 * plane + o] = m.C;
+    out[0 * plane + o] = m.p1;
+    out[1 * plane + o] = m.dC;
     out[2 * plane + o] = m.U;
-    out[3 * plane + o] = m.theta;
+    out[3 * plane + o] = m.dth;
     out[4 * plane + o] = m.ux;
     out[5 * plane + o] = m.uy;
     out[6 * plane + o] = m.p;
@@ -192,17 +199,17 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_nodes(const StepParams P
         float f[5], n[5], g[5], h[9];
         load_node<Store>(P, sc, fl, o, f, n, g, h);
         const Macro m = node_macros(f, n, g, h, P);
-        double sh = 0.0;
+        double sh = (double)P.rho0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) sh += (double)h[i];
         const double u = sqrt((double)m.ux * m.ux + (double)m.uy * m.uy);
-        acc[0] += 0.5 * (1.0 + (double)m.phi);
-        acc[1] += (double)m.C;
-        acc[2] += (double)m.H;
+        acc[0] += 0.5 * (double)m.p1;
+        acc[1] += 1.0 + (double)m.dC;
+        acc[2] += ((double)P.theta_ref + 0.5) + (double)m.dH;
         acc[3] += sh;
         acc[4] = fmax(acc[4], u);
-        acc[5] += (isfinite(m.phi) && isfinite(m.C) && isfinite(m.theta) && isfinite(u)) ? 0.0 : 1.0;
-        acc[6] += (double)m.phi;
+        acc[5] += (isfinite(m.p1) && isfinite(m.dC) && isfinite(m.dth) && isfinite(u)) ? 0.0 : 1.0;
+        acc[6] += (double)m.p1 - 1.0;
     }
     __shared__ double sm[kRedVals][kRedThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -237,10 +244,10 @@ template <class Store>
 __device__ __forceinline__ double phi_at(const StepParams& P, const typename Store::T* sc, int x, int y)
 {
     const long long o = (long long)y * P.pitch + x;
-    float s = 0.0f;
+    float s = 0.0f;  // phi + 1
 #pragma unroll
     for (int i = 0; i < 5; ++i) s += Store::load(sc, (kF + i) * P.plane + o, kF + i, P);
-    return (double)s;
+    return (double)s - 1.0;
 }
 
 template <class Store>
@@ -313,7 +320,7 @@ cudaError_t init_t(const StepParams& P, const double* fields, void* sc, void* fl
 {
     using T = typename Store::T;
     const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
-    k_init<Store, false><<<g, b, 0, s>>>(P, fields, (T*)sc, (T*)fl, hist);
+    k_init<Store><<<g, b, 0, s>>>(P, fields, (T*)sc, (T*)fl, hist);
     return cudaGetLastError();
 }
 

@@ -10,6 +10,19 @@
 //         raw moments of Eq. (B.2).
 // Relaxation: D2Q5 S = diag(1, s1, s1, 1, 1); D2Q9 S = diag(1, 1, 1, s2, s2,
 // s2, 1, 1, 1) (Sec. 4: every rate not tied to a transport coefficient is 1).
+//
+// Deviation form.  Every population is held as its deviation d_i = f_i -
+// f_i^ref from the equilibrium of a constant reference state, the liquid at
+// rest (phi = -1, C = 1 so U = 0, theta = theta_ref, u = 0, p = 0):
+//   phi:  f^ref = (-1/3, -1/6, -1/6, -1/6, -1/6)       (sum -1)
+//   C:    n^ref = (1, 0, 0, 0, 0)                       (sum 1)
+//   H:    g^ref = (theta_ref/3 + 1/2, theta_ref/6 x 4)  (sum theta_ref + 1/2)
+//   flow: h^ref = (rho0, 0, ..., 0)                     (sum rho0)
+// The references are isotropic, so first moments are unchanged and the macro
+// deviations phi + 1, C - 1, theta - theta_ref follow from sums of small
+// numbers without cancellation; the MRT collision and the modified streaming
+// of Eq. (13) are linear and carry over unchanged to deviations.  16-bit
+// storage rounds the same deviations.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -22,8 +35,7 @@ constexpr int TX = 32;  // tile width of the fused kernel (one warp along x)
 constexpr int TY = 8;   // tile height
 constexpr float kGradEps2 = 1e-12f;  // |grad phi|^2 below which n, N, J_at vanish
 
-// Population slot of model/direction q in a state buffer of 24 planes:
-// phi 0..4, C 5..9, H 10..14, flow 15..23.
+// Population slot of model/direction q: phi 0..4, C 5..9, H 10..14, flow 15..23.
 constexpr int kF = 0, kN = 5, kG = 10, kH = 15, kPlanes = 24;
 // History planes: phi, Q, (Cu)_x, (Cu)_y, (Hu)_x, (Hu)_y.
 constexpr int kHist = 6;
@@ -41,7 +53,9 @@ struct StepParams {
     float inv_D;              // 1/D (lattice)
     float s1C, s1T, s2u;      // relaxation rates of Sec. 4
     float rho0;
-    float Fx, Fy, gbT, gbC, theta_ref, C_ref;  // body force and buoyancy (flow lattice units)
+    float Fx, Fy, gbT, gbC;   // body force and buoyancy (flow lattice units)
+    float theta_ref;          // buoyancy reference = reference state of the deviations
+    float dC_ref;             // 1 - C_ref: buoyancy offset of the solute term
     float nsub;               // flow-lattice velocity -> scalar-lattice velocity
     float cos_o, sin_o;       // orientation when the whole domain is one grain
     const float2* grain_cs;   // (cos, sin) per grain id
@@ -49,13 +63,13 @@ struct StepParams {
     int bc[4];
     float uin_x, uin_y;
     float dir_phi, dir_U, dir_theta;
-    // reduced-precision codec: reference equilibrium and scale per plane
-    float ref[kPlanes];
+    // 16-bit codec scale per plane (FP32 storage ignores it)
     float scale[kPlanes], inv_scale[kPlanes];
 };
 
 // ------------------------------------------------------------------ codecs
-// FP32 stores populations as they are; FP16/BF16 store s (f - f_ref).
+// Deviations are stored as they are (FP32) or scaled and rounded to nearest
+// even (FP16/BF16).
 struct StoreF32 {
     using T = float;
     static __device__ __forceinline__ float load(const T* p, long long i, int, const StepParams&) { return p[i]; }
@@ -65,22 +79,22 @@ struct StoreF16 {
     using T = __half;
     static __device__ __forceinline__ float load(const T* p, long long i, int q, const StepParams& P)
     {
-        return P.ref[q] + __half2float(p[i]) * P.inv_scale[q];
+        return __half2float(p[i]) * P.inv_scale[q];
     }
     static __device__ __forceinline__ void store(T* p, long long i, int q, float v, const StepParams& P)
     {
-        p[i] = __float2half_rn((v - P.ref[q]) * P.scale[q]);
+        p[i] = __float2half_rn(v * P.scale[q]);
     }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float load(const T* p, long long i, int q, const StepParams& P)
     {
-        return P.ref[q] + __bfloat162float(p[i]) * P.inv_scale[q];
+        return __bfloat162float(p[i]) * P.inv_scale[q];
     }
     static __device__ __forceinline__ void store(T* p, long long i, int q, float v, const StepParams& P)
     {
-        p[i] = __float2bfloat16_rn((v - P.ref[q]) * P.scale[q]);
+        p[i] = __float2bfloat16_rn(v * P.scale[q]);
     }
 };
 
@@ -90,24 +104,24 @@ __device__ __forceinline__ int wrap(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-// h(phi) of Sec. 2.
-__device__ __forceinline__ float h_of_phi(int kind, float phi)
+// h(phi) + 1 as a function of p = phi + 1 (Sec. 2): kind 0 is h = phi, kind 1
+// is 15/8 (phi - 2 phi^3/3 + phi^5/5), whose h + 1 = 15/8 p^3 (4/3 - p + p^2/5).
+__device__ __forceinline__ float h_plus_1(int kind, float p)
 {
-    if (kind == 1) {
-        float p2 = phi * phi;
-        return 1.875f * phi * (1.0f - p2 * (2.0f / 3.0f) + p2 * p2 * 0.2f);
-    }
-    return phi;
+    if (kind == 1) return 1.875f * p * p * p * (4.0f / 3.0f - p + 0.2f * p * p);
+    return p;
 }
 
-// Eq. (20) and its inverse.
-__device__ __forceinline__ float U_of_C(float C, float phi, float k)
+// Eq. (20) with C = 1 + dC and phi = p - 1:
+// U = [2C/(1 + k - (1 - k) phi) - 1]/(1 - k) = (2 dC + (1 - k) p) / ((2 - (1 - k) p)(1 - k)).
+__device__ __forceinline__ float U_of(float dC, float p, float k)
 {
-    return (2.0f * C / (1.0f + k - (1.0f - k) * phi) - 1.0f) / (1.0f - k);
+    return (2.0f * dC + (1.0f - k) * p) / ((2.0f - (1.0f - k) * p) * (1.0f - k));
 }
-__device__ __forceinline__ float C_of_U(float U, float phi, float k)
+// Its inverse: C - 1 = (2 - (1 - k) p)(1 + (1 - k) U)/2 - 1.
+__device__ __forceinline__ float dC_of(float U, float p, float k)
 {
-    return 0.5f * (1.0f + k - (1.0f - k) * phi) * (1.0f + (1.0f - k) * U);
+    return 0.5f * (2.0f - (1.0f - k) * p) * (1.0f - k) * U - 0.5f * (1.0f - k) * p;
 }
 
 // Eq. (5).
@@ -117,9 +131,12 @@ __device__ __forceinline__ float coupling_Q(float phi, float theta, float U, con
     return phi * w - P.lambda * (theta + P.Mc * U) * w * w;
 }
 
-// Macroscopic values of one node from its 24 populations (Eqs. 15, 20, 23, 26).
+// Macroscopic values of one node from its 24 population deviations
+// (Eqs. 15, 20, 23, 26).
 struct Macro {
-    float phi, C, U, theta, H;
+    float p1;             // phi + 1
+    float phi, dC, U, dth, hp1;   // phi, C - 1, U, theta - theta_ref, h(phi) + 1
+    float H, dH;          // H = theta - h(phi)/2 and its deviation H - (theta_ref + 1/2)
     float ux, uy, p;      // corrected velocity and pressure (flow lattice units)
     float Fx, Fy;         // external force F (flow lattice units)
     float fsx, fsy;       // fluid-solid force f = -u*
@@ -129,18 +146,22 @@ __device__ __forceinline__ Macro node_macros(const float* f, const float* n, con
                                              const StepParams& P)
 {
     Macro m;
-    m.phi = f[0] + f[1] + f[2] + f[3] + f[4];
-    m.C = n[0] + n[1] + n[2] + n[3] + n[4];
-    m.H = g[0] + g[1] + g[2] + g[3] + g[4];
-    m.theta = m.H + 0.5f * h_of_phi(P.h_kind, m.phi);
-    m.U = U_of_C(m.C, m.phi, P.k);
+    m.p1 = f[0] + f[1] + f[2] + f[3] + f[4];
+    m.phi = m.p1 - 1.0f;
+    m.dC = n[0] + n[1] + n[2] + n[3] + n[4];
+    const float dH = g[0] + g[1] + g[2] + g[3] + g[4];
+    m.hp1 = h_plus_1(P.h_kind, m.p1);
+    m.dth = dH + 0.5f * m.hp1;                 // theta = H + h/2
+    m.dH = dH;
+    m.H = (P.theta_ref + 0.5f) + dH;
+    m.U = U_of(m.dC, m.p1, P.k);
     m.Fx = P.Fx;
-    m.Fy = P.Fy + P.gbT * (m.theta - P.theta_ref) + P.gbC * (m.C - P.C_ref);
+    m.Fy = P.Fy + P.gbT * m.dth + P.gbC * (m.dC + P.dC_ref);
     float jx = h[1] - h[3] + h[5] - h[6] - h[7] + h[8];
     float jy = h[2] - h[4] + h[5] + h[6] - h[7] - h[8];
     float rest = h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
     float usx = jx + 0.5f * m.Fx, usy = jy + 0.5f * m.Fy;   // u*
-    float qt = 0.5f * (1.0f - m.phi);
+    float qt = 1.0f - 0.5f * m.p1;                         // q~ = (1 - phi)/2
     m.fsx = -usx;
     m.fsy = -usy;
     m.ux = usx + 0.5f * (1.0f - qt) * m.fsx;
@@ -175,37 +196,39 @@ __device__ __forceinline__ void anisotropy(float gx, float gy, float eps, float 
 }
 
 // ------------------------------------------------------------- equilibria
-// Population forms (used by initialisation and the wall scheme).
-__device__ __forceinline__ void feq_phi(float phi, float* e)
+// Deviation of the population-form equilibria from the reference state (used
+// by initialisation and the wall scheme).
+// Eq. (14): w_i phi - w_i (-1) = w_i (phi + 1).
+__device__ __forceinline__ void deq_phi(float p1, float* e)
 {
-    e[0] = phi * (1.0f / 3.0f);
-    e[1] = e[2] = e[3] = e[4] = phi * (1.0f / 6.0f);
+    e[0] = p1 * (1.0f / 3.0f);
+    e[1] = e[2] = e[3] = e[4] = p1 * (1.0f / 6.0f);
 }
 // Eq. (19) with qU = q~ U and (jx, jy) = C u.
-__device__ __forceinline__ void feq_C(float C, float qU, float jx, float jy, float* e)
+__device__ __forceinline__ void deq_C(float dC, float qU, float jx, float jy, float* e)
 {
-    e[0] = C - (2.0f / 3.0f) * qU;
+    e[0] = dC - (2.0f / 3.0f) * qU;
     float b = qU * (1.0f / 6.0f);
     e[1] = b + 0.5f * jx;
     e[3] = b - 0.5f * jx;
     e[2] = b + 0.5f * jy;
     e[4] = b - 0.5f * jy;
 }
-// Eq. (22) with (jx, jy) = H u.
-__device__ __forceinline__ void feq_H(float theta, float hphi, float jx, float jy, float* e)
+// Eq. (22) with dth = theta - theta_ref, hp1 = h(phi) + 1 and (jx, jy) = H u.
+__device__ __forceinline__ void deq_H(float dth, float hp1, float jx, float jy, float* e)
 {
-    e[0] = theta * (1.0f / 3.0f) - 0.5f * hphi;
-    float b = theta * (1.0f / 6.0f);
+    e[0] = dth * (1.0f / 3.0f) - 0.5f * hp1;
+    float b = dth * (1.0f / 6.0f);
     e[1] = b + 0.5f * jx;
     e[3] = b - 0.5f * jx;
     e[2] = b + 0.5f * jy;
     e[4] = b - 0.5f * jy;
 }
-// Eq. (25): h_i^eq = sigma_i + w_i [3 c.u + 9/2 (c.u)^2 - 3/2 |u|^2].
-__device__ __forceinline__ void feq_flow(float p, float ux, float uy, float rho0, float* e)
+// Eq. (25): h_i^eq = sigma_i + w_i [3 c.u + 9/2 (c.u)^2 - 3/2 |u|^2], minus rho0 on i = 0.
+__device__ __forceinline__ void deq_flow(float p, float ux, float uy, float* e)
 {
     float uu = 1.5f * (ux * ux + uy * uy);
-    e[0] = rho0 - (5.0f / 3.0f) * p + (4.0f / 9.0f) * (-uu);
+    e[0] = -(5.0f / 3.0f) * p - (4.0f / 9.0f) * uu;
     const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
     float cx[4] = {ux, uy, -ux, -uy};
 #pragma unroll
@@ -216,19 +239,21 @@ __device__ __forceinline__ void feq_flow(float p, float ux, float uy, float rho0
 }
 
 // ------------------------------------------------------------- collisions
-// D2Q5 MRT with S = diag(1, s1, s1, 1, 1), equilibrium moments (A, Bx, By,
-// Cv/3, Cv/3), auxiliary first moments (Gx, Gy) weighted by (1 - s1/2) and an
-// isotropic source S0 added with weights w_i:
-//   f*_0 = (A + S0 - 2 (Cv + S0)/3) ... written through the inverse of Eq. (B.1).
-__device__ __forceinline__ void collide_d2q5(const float* f, float A, float Bx, float By, float Cv, float s1,
+// D2Q5 MRT with S = diag(1, s1, s1, 1, 1) on deviations.  Equilibrium moments
+// (A, Bx, By, Cv/3, Cv/3) enter as the deviations dA = A - A_ref and
+// dCv = Cv - Cv_ref of the reference state; (Gx, Gy) are the first moments of
+// the auxiliary term, weighted by (1 - s1/2); S0 is an isotropic source added
+// with weights w_i.  The post-collision deviations follow through the inverse
+// of Eq. (B.1).
+__device__ __forceinline__ void collide_d2q5(const float* d, float dA, float Bx, float By, float dCv, float s1,
                                              float Gx, float Gy, float S0, float* out)
 {
-    float m1 = f[1] - f[3], m2 = f[2] - f[4];
+    float m1 = d[1] - d[3], m2 = d[2] - d[4];
     float k1 = 1.0f - 0.5f * s1;
     float r1 = m1 - s1 * (m1 - Bx) + k1 * Gx;
     float r2 = m2 - s1 * (m2 - By) + k1 * Gy;
-    float e = (Cv + S0) * (1.0f / 3.0f);   // post-collision second moments (each)
-    out[0] = A + S0 - 2.0f * e;
+    float e = (dCv + S0) * (1.0f / 3.0f);   // deviation of each post-collision second moment
+    out[0] = dA + S0 - 2.0f * e;
     out[1] = 0.5f * (e + r1);
     out[3] = 0.5f * (e - r1);
     out[2] = 0.5f * (e + r2);
@@ -237,10 +262,10 @@ __device__ __forceinline__ void collide_d2q5(const float* f, float A, float Bx, 
 
 // D2Q9 raw-moment MRT of Eq. (24): m* = m - S (m - m^eq) + (I - S/2) m_F with
 // m^eq and m_F of Eq. (B.3) (varphi = 0) and F' = F + [1 - q~] f; returns the
-// post-collision populations through the inverse of Eq. (B.2).
-__device__ __forceinline__ void collide_flow(const float* h, const Macro& m, float s2, float rho0, float* out)
+// post-collision deviations through the inverse of Eq. (B.2) (m0* = rho0).
+__device__ __forceinline__ void collide_flow(const float* h, const Macro& m, float s2, float* out)
 {
-    float qt = 0.5f * (1.0f - m.phi);
+    float qt = 1.0f - 0.5f * m.p1;
     float Fpx = m.Fx + (1.0f - qt) * m.fsx;
     float Fpy = m.Fy + (1.0f - qt) * m.fsy;
     float u = m.ux, v = m.uy, p = m.p;
@@ -249,7 +274,6 @@ __device__ __forceinline__ void collide_flow(const float* h, const Macro& m, flo
     float myy = h[2] + h[4] + h[5] + h[6] + h[7] + h[8];
     float mxy = h[5] - h[6] + h[7] - h[8];
     // post-collision moments
-    float r0 = rho0;
     float r1 = u + 0.5f * Fpx;
     float r2 = v + 0.5f * Fpy;
     float r3 = mxx - s2 * (mxx - (p + u * u));
@@ -258,8 +282,8 @@ __device__ __forceinline__ void collide_flow(const float* h, const Macro& m, flo
     float r6 = (v + 0.5f * Fpy) * (1.0f / 3.0f);
     float r7 = (u + 0.5f * Fpx) * (1.0f / 3.0f);
     float r8 = (p + u * u + v * v) * (1.0f / 3.0f);
-    // inverse of the tensor-product raw-moment matrix
-    out[0] = r0 - r3 - r4 + r8;
+    // inverse of the tensor-product raw-moment matrix (r0 - rho0 = 0)
+    out[0] = -r3 - r4 + r8;
     out[1] = 0.5f * (r1 + r3 - r7 - r8);
     out[3] = 0.5f * (-r1 + r3 + r7 - r8);
     out[2] = 0.5f * (r2 + r4 - r6 - r8);

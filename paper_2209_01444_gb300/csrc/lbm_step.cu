@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(TX* TY)
     anisotropy(gx, gy, P.eps, co, so, as, Nx, Ny);
     const float as2 = as * as;
     const float g2 = gx * gx + gy * gy;
-    const float Q = coupling_Q(m.phi, m.theta, m.U, P);
+    const float Q = coupling_Q(m.phi, P.theta_ref + m.dth, m.U, P);
 
     // ---- phase field: Eqs. (13)-(14), relaxation rate of Sec. 3.1
     float fo[5];
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(TX* TY)
         const float s1 = 1.0f / (P.kappa3 * as2 + 0.5f);
         const float S0 = (Q + 0.5f * as2 * (Q - Q_prev)) * P.inv_tau;
         const float ga = -(1.0f / 3.0f) / as2;
-        collide_d2q5(f, m.phi, 0.0f, 0.0f, m.phi, s1, ga * Nx, ga * Ny, S0, fo);
+        collide_d2q5(f, m.p1, 0.0f, 0.0f, m.p1, s1, ga * Nx, ga * Ny, S0, fo);
     }
     // ---- solute: Eqs. (17)-(19) with J_at of Eq. (7)
     float no[5];
@@ -125,22 +125,23 @@ __global__ void __launch_bounds__(TX* TY)
             Jx = a * gx;
             Jy = a * gy;
         }
-        const float qt = 0.5f * (1.0f - m.phi);
-        const float Cux = m.C * usx, Cuy = m.C * usy;
+        const float qt = 1.0f - 0.5f * m.p1;
+        const float C = 1.0f + m.dC;
+        const float Cux = C * usx, Cuy = C * usy;
         // sum_i c_i G_i = d_t(Cu) + cs^2 (U grad q~ + J_at/D), grad q~ = -grad(phi)/2
         const float Gx = (Cux - Cux_prev) + (1.0f / 3.0f) * (-0.5f * m.U * gx + Jx * P.inv_D);
         const float Gy = (Cuy - Cuy_prev) + (1.0f / 3.0f) * (-0.5f * m.U * gy + Jy * P.inv_D);
-        collide_d2q5(n, m.C, Cux, Cuy, qt * m.U, P.s1C, Gx, Gy, 0.0f, no);
+        collide_d2q5(n, m.dC, Cux, Cuy, qt * m.U, P.s1C, Gx, Gy, 0.0f, no);
     }
     // ---- heat: Eqs. (21)-(23)
     float go[5];
     {
         const float Hux = m.H * usx, Huy = m.H * usy;
-        collide_d2q5(g, m.H, Hux, Huy, m.theta, P.s1T, Hux - Hux_prev, Huy - Huy_prev, 0.0f, go);
+        collide_d2q5(g, m.dH, Hux, Huy, m.dth, P.s1T, Hux - Hux_prev, Huy - Huy_prev, 0.0f, go);
     }
     // ---- flow: Eqs. (24)-(26)
     float ho[9];
-    collide_flow(h, m, P.s2u, P.rho0, ho);
+    collide_flow(h, m, P.s2u, ho);
 
     // ---- push streaming
     const int xp = (x + 1 == P.nx) ? 0 : x + 1, xm = (x == 0) ? P.nx - 1 : x - 1;
@@ -168,8 +169,8 @@ __global__ void __launch_bounds__(TX* TY)
     // ---- history of the backward differences
     hist[0 * plane + o] = m.phi;
     hist[1 * plane + o] = Q;
-    hist[2 * plane + o] = m.C * usx;
-    hist[3 * plane + o] = m.C * usy;
+    hist[2 * plane + o] = (1.0f + m.dC) * usx;
+    hist[3 * plane + o] = (1.0f + m.dC) * usy;
     hist[4 * plane + o] = m.H * usx;
     hist[5 * plane + o] = m.H * usy;
     if (WRITE_FB) fb[o] = m.Fy;
@@ -192,20 +193,21 @@ __global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const 
     for (int i = 0; i < 9; ++i) h[i] = Store::load(src, i * plane + o, kH + i, P);
     Macro m;
     m.phi = hist[o];
+    m.p1 = m.phi + 1.0f;
     m.Fx = P.Fx;
     m.Fy = fb[o];
     float jx = h[1] - h[3] + h[5] - h[6] - h[7] + h[8];
     float jy = h[2] - h[4] + h[5] + h[6] - h[7] - h[8];
     float rest = h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
     float usx = jx + 0.5f * m.Fx, usy = jy + 0.5f * m.Fy;
-    float qt = 0.5f * (1.0f - m.phi);
+    float qt = 1.0f - 0.5f * m.p1;
     m.fsx = -usx;
     m.fsy = -usy;
     m.ux = usx + 0.5f * (1.0f - qt) * m.fsx;
     m.uy = usy + 0.5f * (1.0f - qt) * m.fsy;
     m.p = 0.6f * (rest - (2.0f / 3.0f) * (m.ux * m.ux + m.uy * m.uy));
     float ho[9];
-    collide_flow(h, m, P.s2u, P.rho0, ho);
+    collide_flow(h, m, P.s2u, ho);
     const int xp = (x + 1 == P.nx) ? 0 : x + 1, xm = (x == 0) ? P.nx - 1 : x - 1;
     const int yp = (y + 1 == P.ny) ? 0 : y + 1, ym = (y == 0) ? P.ny - 1 : y - 1;
     const long long rY = (long long)y * P.pitch, rP = (long long)yp * P.pitch, rM = (long long)ym * P.pitch;
@@ -264,32 +266,33 @@ __global__ void k_walls(const StepParams P, typename Store::T* __restrict__ pop,
         uby = axis == 0 ? m.uy : 0.0f;
     }
     float eb[9], ef[9];
-    feq_flow(pb, ubx, uby, P.rho0, eb);
-    feq_flow(m.p, m.ux, m.uy, P.rho0, ef);
+    deq_flow(pb, ubx, uby, eb);
+    deq_flow(m.p, m.ux, m.uy, ef);
 #pragma unroll
     for (int i = 0; i < 9; ++i) Store::store(popf, i * plane + ob, kH + i, eb[i] + h[i] - ef[i], P);
     if (flow_only) return;
 
-    float phib = m.phi, Cb = m.C, Ub = m.U, thb = m.theta;
+    float p1b = m.p1, dCb = m.dC, Ub = m.U, dthb = m.dth;
     if (type == 5) {  // Dirichlet far field
-        phib = P.dir_phi;
+        p1b = P.dir_phi + 1.0f;
         Ub = P.dir_U;
-        Cb = C_of_U(Ub, phib, P.k);
-        thb = P.dir_theta;
+        dCb = dC_of(Ub, p1b, P.k);
+        dthb = P.dir_theta - P.theta_ref;
     }
-    const float hb = h_of_phi(P.h_kind, phib), hf = h_of_phi(P.h_kind, m.phi);
-    const float Hb = thb - 0.5f * hb;
+    const float hp1b = h_plus_1(P.h_kind, p1b);
+    const float Hb = (P.theta_ref + 0.5f) + dthb - 0.5f * hp1b;
+    const float Cb = 1.0f + dCb, Cf = 1.0f + m.dC;
     const float sc = P.nsub;
-    feq_phi(phib, eb);
-    feq_phi(m.phi, ef);
+    deq_phi(p1b, eb);
+    deq_phi(m.p1, ef);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(pop, (kF + i) * plane + ob, kF + i, eb[i] + f[i] - ef[i], P);
-    feq_C(Cb, 0.5f * (1.0f - phib) * Ub, Cb * ubx * sc, Cb * uby * sc, eb);
-    feq_C(m.C, 0.5f * (1.0f - m.phi) * m.U, m.C * m.ux * sc, m.C * m.uy * sc, ef);
+    deq_C(dCb, (1.0f - 0.5f * p1b) * Ub, Cb * ubx * sc, Cb * uby * sc, eb);
+    deq_C(m.dC, (1.0f - 0.5f * m.p1) * m.U, Cf * m.ux * sc, Cf * m.uy * sc, ef);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(pop, (kN + i) * plane + ob, kN + i, eb[i] + n[i] - ef[i], P);
-    feq_H(thb, hb, Hb * ubx * sc, Hb * uby * sc, eb);
-    feq_H(m.theta, hf, m.H * m.ux * sc, m.H * m.uy * sc, ef);
+    deq_H(dthb, hp1b, Hb * ubx * sc, Hb * uby * sc, eb);
+    deq_H(m.dth, m.hp1, m.H * m.ux * sc, m.H * m.uy * sc, ef);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(pop, (kG + i) * plane + ob, kG + i, eb[i] + g[i] - ef[i], P);
 }
