@@ -29,13 +29,16 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled-LB MLUPS and % of HBM roofline; surrogate speedup at matched tip error"
 UNIT = "MLUPS"
 # Algorithmic HBM bytes per node per coupled step (n_sub = 1): every population
-# read once and written once (24 x 2), the six history scalars read and written
-# (6 x 2), and the one-byte grain id read when the domain holds several grains.
-POP_PLANES, HIST_PLANES = 24, 6
+# read once and written once, the six FP32 history scalars read and written,
+# and the one-byte grain id read when the domain holds several grains.
+# Population bytes per node: FP32 24 x 4 = 96; 16-bit storage 21 x 2 + 3 x 4
+# (the scalar rest populations stay FP32) = 54.
+POP_BYTES = {"fp32": 96, "fp16": 54, "bf16": 54}
+HIST_PLANES = 6
 
 
-def algorithmic_bytes_per_node(storage_bytes: int, grains: bool) -> int:
-    return POP_PLANES * 2 * storage_bytes + HIST_PLANES * 2 * 4 + (1 if grains else 0)
+def algorithmic_bytes_per_node(storage: str, grains: bool) -> int:
+    return POP_BYTES[storage] * 2 + HIST_PLANES * 2 * 4 + (1 if grains else 0)
 
 
 def parse():
@@ -299,9 +302,8 @@ def main():
     kms, launches = sim.kernel_time()
     sim.set_profiling(False)
     k_avg_ms = kms / max(launches, 1)
-    sb = 4 if args.storage == "fp32" else 2
     grains = len(case.seeds) > 1
-    bpn = algorithmic_bytes_per_node(sb, grains)
+    bpn = algorithmic_bytes_per_node(args.storage, grains)
     achieved = bpn * nodes / (k_avg_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
     traffic = recorded_traffic(f"multi_seed_{args.n}_{args.storage}")

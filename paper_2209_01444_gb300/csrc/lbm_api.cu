@@ -34,7 +34,7 @@ struct lbm_handle {
     lbm_params prm;
     StepParams P;
     int storage = 0;
-    size_t esize = 4;
+    size_t sc_bytes = 0, fl_bytes = 0;  // bytes of one scalar / flow population buffer
     cudaStream_t stream = nullptr;
     lbm::StepBuffers B{};
     uint8_t* grain = nullptr;          // device grain ids
@@ -180,8 +180,6 @@ void derive(lbm_handle* h)
         P.inv_scale[q] = 1.0f / sc;
     }
 }
-
-size_t plane_bytes(const lbm_handle* h) { return (size_t)h->P.plane * h->esize; }
 
 int ensure_initialised(lbm_handle* h)
 {
@@ -340,17 +338,17 @@ int lbm_create(const lbm_params* p, lbm_handle** out)
     if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
     h->prm = *p;
     h->storage = p->storage;
-    h->esize = lbm::storage_bytes(p->storage);
     derive(h);
-    const size_t pb = plane_bytes(h);
+    h->sc_bytes = (size_t)h->P.plane * lbm::scalar_node_bytes(p->storage);
+    h->fl_bytes = (size_t)h->P.plane * lbm::flow_node_bytes(p->storage);
     const size_t fp = (size_t)h->P.plane * sizeof(float);
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
     };
     for (int b = 0; b < 2; ++b) {
-        alloc(&h->B.sc[b], pb * (lbm::kH));
-        alloc(&h->B.fl[b], pb * (lbm::kPlanes - lbm::kH));
+        alloc(&h->B.sc[b], h->sc_bytes);
+        alloc(&h->B.fl[b], h->fl_bytes);
     }
     alloc((void**)&h->B.hist, fp * lbm::kHist);
     if (p->n_sub > 1) alloc((void**)&h->B.fb, fp);
@@ -622,7 +620,7 @@ size_t lbm_checkpoint_bytes(const lbm_handle* h)
 {
     if (!h) return 0;
     const size_t plane = (size_t)h->P.plane;
-    return sizeof(CkptHeader) + plane * h->esize * lbm::kPlanes + plane * sizeof(float) * lbm::kHist + plane +
+    return sizeof(CkptHeader) + h->sc_bytes + h->fl_bytes + plane * sizeof(float) * lbm::kHist + plane +
            256 * sizeof(float2);
 }
 
@@ -641,7 +639,7 @@ int lbm_save_state(lbm_handle* h, void* host, size_t bytes)
     memcpy(p, &hd, sizeof(hd));
     p += sizeof(hd);
     const size_t plane = (size_t)h->P.plane;
-    const size_t sb = plane * h->esize * lbm::kH, fbz = plane * h->esize * (lbm::kPlanes - lbm::kH);
+    const size_t sb = h->sc_bytes, fbz = h->fl_bytes;
     LBM_CUDA(h, cudaMemcpyAsync(p, h->B.sc[h->B.cs], sb, cudaMemcpyDeviceToHost, h->stream));
     p += sb;
     LBM_CUDA(h, cudaMemcpyAsync(p, h->B.fl[h->B.cf], fbz, cudaMemcpyDeviceToHost, h->stream));
@@ -666,7 +664,7 @@ int lbm_load_state(lbm_handle* h, const void* host, size_t bytes)
     if (memcmp(&hd.prm, &h->prm, sizeof(lbm_params)) != 0) return fail(h, LBM_EINVAL, "checkpoint parameters differ");
     p += sizeof(hd);
     const size_t plane = (size_t)h->P.plane;
-    const size_t sb = plane * h->esize * lbm::kH, fbz = plane * h->esize * (lbm::kPlanes - lbm::kH);
+    const size_t sb = h->sc_bytes, fbz = h->fl_bytes;
     h->B.cs = 0;
     h->B.cf = 0;
     drop_graphs(h);

@@ -9,19 +9,17 @@ namespace lbm {
 namespace {
 
 template <class Store>
-__device__ __forceinline__ void load_node(const StepParams& P, const typename Store::T* sc,
-                                          const typename Store::T* fl, long long o, float* f, float* n, float* g,
-                                          float* h)
+__device__ __forceinline__ void load_node(const StepParams& P, const void* sc, const void* fl, long long o, float* f,
+                                          float* n, float* g, float* h)
 {
-    const long long plane = P.plane;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) f[i] = Store::load(sc, (kF + i) * plane + o, kF + i, P);
+    for (int i = 0; i < 5; ++i) f[i] = Store::load(sc, fl, kF + i, o, P);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) n[i] = Store::load(sc, (kN + i) * plane + o, kN + i, P);
+    for (int i = 0; i < 5; ++i) n[i] = Store::load(sc, fl, kN + i, o, P);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) g[i] = Store::load(sc, (kG + i) * plane + o, kG + i, P);
+    for (int i = 0; i < 5; ++i) g[i] = Store::load(sc, fl, kG + i, o, P);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = Store::load(fl, i * plane + o, kH + i, P);
+    for (int i = 0; i < 9; ++i) h[i] = Store::load(sc, fl, kH + i, o, P);
 }
 
 __device__ __forceinline__ double min_image(double d, int L, int periodic)
@@ -69,8 +67,8 @@ __global__ void k_seed_fields(const StepParams P, const double* __restrict__ see
 // recovered from the stored populations (so the first backward differences
 // vanish).
 template <class Store>
-__global__ void k_init(const StepParams P, const double* __restrict__ fields, typename Store::T* __restrict__ sc,
-                       typename Store::T* __restrict__ fl, float* __restrict__ hist)
+__global__ void k_init(const StepParams P, const double* __restrict__ fields, void* __restrict__ sc,
+                       void* __restrict__ fl, float* __restrict__ hist)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -93,16 +91,16 @@ __global__ void k_init(const StepParams P, const double* __restrict__ fields, ty
     float e[9];
     deq_phi(p1, e);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(sc, (kF + i) * plane + o, kF + i, e[i], P);
+    for (int i = 0; i < 5; ++i) Store::store(sc, fl, kF + i, o, e[i], P);
     deq_C(dC, (1.0f - 0.5f * p1) * Uf, C * sx, C * sy, e);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(sc, (kN + i) * plane + o, kN + i, e[i], P);
+    for (int i = 0; i < 5; ++i) Store::store(sc, fl, kN + i, o, e[i], P);
     deq_H(dth, hp1, H * sx, H * sy, e);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(sc, (kG + i) * plane + o, kG + i, e[i], P);
+    for (int i = 0; i < 5; ++i) Store::store(sc, fl, kG + i, o, e[i], P);
     deq_flow(p, ux, uy, e);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store::store(fl, i * plane + o, kH + i, e[i], P);
+    for (int i = 0; i < 9; ++i) Store::store(sc, fl, kH + i, o, e[i], P);
 
     float f[5], n[5], g[5], h[9];
     load_node<Store>(P, sc, fl, o, f, n, g, h);
@@ -119,8 +117,8 @@ __global__ void k_init(const StepParams P, const double* __restrict__ fields, ty
 // Macro deviations of every node: phi + 1, C - 1, U, theta - theta_ref, ux,
 // uy, p (flow lattice units); the host adds the reference values in FP64.
 template <class Store>
-__global__ void k_macros(const StepParams P, const typename Store::T* __restrict__ sc,
-                         const typename Store::T* __restrict__ fl, float* __restrict__ out)
+__global__ void k_macros(const StepParams P, const void* __restrict__ sc, const void* __restrict__ fl,
+                         float* __restrict__ out)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -139,31 +137,25 @@ __global__ void k_macros(const StepParams P, const typename Store::T* __restrict
     out[6 * plane + o] = m.p;
 }
 
+// Deviations of every population plane as FP32 planes (and back).
 template <class Store>
-__global__ void k_decode(const StepParams P, const typename Store::T* __restrict__ sc,
-                         const typename Store::T* __restrict__ fl, float* __restrict__ out)
+__global__ void k_decode(const StepParams P, const void* __restrict__ sc, const void* __restrict__ fl,
+                         float* __restrict__ out)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long total = P.plane * kPlanes;
-    if (i >= total) return;
-    const int q = (int)(i / P.plane);
-    const long long r = i - (long long)q * P.plane;
-    out[i] = q < kH ? Store::load(sc, i, q, P) : Store::load(fl, (q - kH) * P.plane + r, q, P);
+    if (i >= P.plane) return;
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) out[q * P.plane + i] = Store::load(sc, fl, q, i, P);
 }
 
 template <class Store>
-__global__ void k_encode(const StepParams P, const float* __restrict__ in, typename Store::T* __restrict__ sc,
-                         typename Store::T* __restrict__ fl)
+__global__ void k_encode(const StepParams P, const float* __restrict__ in, void* __restrict__ sc,
+                         void* __restrict__ fl)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long total = P.plane * kPlanes;
-    if (i >= total) return;
-    const int q = (int)(i / P.plane);
-    const long long r = i - (long long)q * P.plane;
-    if (q < kH)
-        Store::store(sc, i, q, in[i], P);
-    else
-        Store::store(fl, (q - kH) * P.plane + r, q, in[i], P);
+    if (i >= P.plane) return;
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) Store::store(sc, fl, q, i, in[q * P.plane + i], P);
 }
 
 // ------------------------------------------------------------- reductions
@@ -186,8 +178,8 @@ __device__ __forceinline__ double warp_max(double v)
 // Pass 1: each block accumulates a fixed, grid-strided subset of nodes in
 // FP64 and writes its kRedVals partials (deterministic order).
 template <class Store>
-__global__ void __launch_bounds__(kRedThreads) k_reduce_nodes(const StepParams P, const typename Store::T* __restrict__ sc,
-                                                              const typename Store::T* __restrict__ fl,
+__global__ void __launch_bounds__(kRedThreads) k_reduce_nodes(const StepParams P, const void* __restrict__ sc,
+                                                              const void* __restrict__ fl,
                                                               double* __restrict__ partials)
 {
     double acc[kRedVals] = {0, 0, 0, 0, 0, 0, 0};
@@ -241,17 +233,17 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks,
 }
 
 template <class Store>
-__device__ __forceinline__ double phi_at(const StepParams& P, const typename Store::T* sc, int x, int y)
+__device__ __forceinline__ double phi_at(const StepParams& P, const void* sc, int x, int y)
 {
     const long long o = (long long)y * P.pitch + x;
     float s = 0.0f;  // phi + 1
 #pragma unroll
-    for (int i = 0; i < 5; ++i) s += Store::load(sc, (kF + i) * P.plane + o, kF + i, P);
+    for (int i = 0; i < 5; ++i) s += Store::load(sc, nullptr, kF + i, o, P);
     return (double)s - 1.0;
 }
 
 template <class Store>
-__device__ double phi_bilinear(const StepParams& P, const typename Store::T* sc, double px, double py)
+__device__ double phi_bilinear(const StepParams& P, const void* sc, double px, double py)
 {
     int i = (int)floor(px), j = (int)floor(py);
     if (i > P.nx - 2) i = P.nx - 2;
@@ -265,7 +257,7 @@ __device__ double phi_bilinear(const StepParams& P, const typename Store::T* sc,
 // phi is sampled every half node while the sample is inside the grid; the
 // outermost sample with phi > 0 and its successor are interpolated to 0.
 template <class Store>
-__global__ void __launch_bounds__(kRedThreads) k_tips(const StepParams P, const typename Store::T* __restrict__ sc,
+__global__ void __launch_bounds__(kRedThreads) k_tips(const StepParams P, const void* __restrict__ sc,
                                                       double cx, double cy, double c, double s,
                                                       double* __restrict__ out)
 {
@@ -318,36 +310,30 @@ __global__ void __launch_bounds__(kRedThreads) k_tips(const StepParams P, const 
 template <class Store>
 cudaError_t init_t(const StepParams& P, const double* fields, void* sc, void* fl, float* hist, cudaStream_t s)
 {
-    using T = typename Store::T;
     const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
-    k_init<Store><<<g, b, 0, s>>>(P, fields, (T*)sc, (T*)fl, hist);
+    k_init<Store><<<g, b, 0, s>>>(P, fields, sc, fl, hist);
     return cudaGetLastError();
 }
 
 template <class Store>
 cudaError_t macros_t(const StepParams& P, const void* sc, const void* fl, float* out, cudaStream_t s)
 {
-    using T = typename Store::T;
     const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
-    k_macros<Store><<<g, b, 0, s>>>(P, (const T*)sc, (const T*)fl, out);
+    k_macros<Store><<<g, b, 0, s>>>(P, sc, fl, out);
     return cudaGetLastError();
 }
 
 template <class Store>
 cudaError_t decode_t(const StepParams& P, const void* sc, const void* fl, float* out, cudaStream_t s)
 {
-    using T = typename Store::T;
-    const long long total = P.plane * kPlanes;
-    k_decode<Store><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, (const T*)sc, (const T*)fl, out);
+    k_decode<Store><<<(unsigned)((P.plane + 255) / 256), 256, 0, s>>>(P, sc, fl, out);
     return cudaGetLastError();
 }
 
 template <class Store>
 cudaError_t encode_t(const StepParams& P, const float* in, void* sc, void* fl, cudaStream_t s)
 {
-    using T = typename Store::T;
-    const long long total = P.plane * kPlanes;
-    k_encode<Store><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, in, (T*)sc, (T*)fl);
+    k_encode<Store><<<(unsigned)((P.plane + 255) / 256), 256, 0, s>>>(P, in, sc, fl);
     return cudaGetLastError();
 }
 
@@ -355,11 +341,10 @@ template <class Store>
 cudaError_t reduce_t(const StepParams& P, const void* sc, const void* fl, double cx, double cy, double c, double s,
                      double* partials, double* out, cudaStream_t st)
 {
-    using T = typename Store::T;
     const int nb = reduce_blocks(P);
-    k_reduce_nodes<Store><<<nb, kRedThreads, 0, st>>>(P, (const T*)sc, (const T*)fl, partials);
+    k_reduce_nodes<Store><<<nb, kRedThreads, 0, st>>>(P, sc, fl, partials);
     k_reduce_final<<<1, 32, 0, st>>>(partials, nb, out);
-    k_tips<Store><<<3, kRedThreads, 0, st>>>(P, (const T*)sc, cx, cy, c, s, out);
+    k_tips<Store><<<3, kRedThreads, 0, st>>>(P, sc, cx, cy, c, s, out);
     return cudaGetLastError();
 }
 

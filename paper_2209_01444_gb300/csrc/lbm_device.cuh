@@ -68,35 +68,76 @@ struct StepParams {
 };
 
 // ------------------------------------------------------------------ codecs
-// Deviations are stored as they are (FP32) or scaled and rounded to nearest
-// even (FP16/BF16).
+// A state is two buffers: the scalar populations (phi, C, H) and the flow
+// populations.  FP32 storage keeps all 15 scalar planes in FP32.  16-bit
+// storage keeps the 12 moving scalar planes and the 9 flow planes in FP16 or
+// BF16 (scaled, rounded to nearest even) and the three scalar rest planes
+// (q = 0, 5, 10), which carry the O(1) solid/liquid contrast and the smallest
+// per-step increments, in FP32 after the 16-bit planes.  q is always a
+// compile-time constant at the call sites, so the plane mapping folds away.
 struct StoreF32 {
     using T = float;
-    static __device__ __forceinline__ float load(const T* p, long long i, int, const StepParams&) { return p[i]; }
-    static __device__ __forceinline__ void store(T* p, long long i, int, float v, const StepParams&) { p[i] = v; }
-};
-struct StoreF16 {
-    using T = __half;
-    static __device__ __forceinline__ float load(const T* p, long long i, int q, const StepParams& P)
+    static constexpr int kScalarBytes = 15 * 4;  // per node
+    static constexpr int kFlowBytes = 9 * 4;
+    static __device__ __forceinline__ float load(const void* sc, const void* fl, int q, long long o,
+                                                 const StepParams& P)
     {
-        return __half2float(p[i]) * P.inv_scale[q];
+        return q < kH ? ((const float*)sc)[q * P.plane + o] : ((const float*)fl)[(q - kH) * P.plane + o];
     }
-    static __device__ __forceinline__ void store(T* p, long long i, int q, float v, const StepParams& P)
+    static __device__ __forceinline__ void store(void* sc, void* fl, int q, long long o, float v,
+                                                 const StepParams& P)
     {
-        p[i] = __float2half_rn(v * P.scale[q]);
-    }
-};
-struct StoreBF16 {
-    using T = __nv_bfloat16;
-    static __device__ __forceinline__ float load(const T* p, long long i, int q, const StepParams& P)
-    {
-        return __bfloat162float(p[i]) * P.inv_scale[q];
-    }
-    static __device__ __forceinline__ void store(T* p, long long i, int q, float v, const StepParams& P)
-    {
-        p[i] = __float2bfloat16_rn(v * P.scale[q]);
+        if (q < kH)
+            ((float*)sc)[q * P.plane + o] = v;
+        else
+            ((float*)fl)[(q - kH) * P.plane + o] = v;
     }
 };
+
+template <class H>
+struct Conv;
+template <>
+struct Conv<__half> {
+    static __device__ __forceinline__ float to(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half from(float v) { return __float2half_rn(v); }
+};
+template <>
+struct Conv<__nv_bfloat16> {
+    static __device__ __forceinline__ float to(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
+
+template <class H>
+struct Store16 {
+    using T = H;
+    static constexpr int kScalarBytes = 12 * 2 + 3 * 4;
+    static constexpr int kFlowBytes = 9 * 2;
+    static __device__ __forceinline__ bool rest(int q) { return q == kF || q == kN || q == kG; }
+    static __device__ __forceinline__ int slot(int q) { return q - 1 - q / 5; }  // moving planes 0..11
+    static __device__ __forceinline__ const float* rest_base(const void* sc, const StepParams& P)
+    {
+        return (const float*)((const char*)sc + 24 * P.plane);
+    }
+    static __device__ __forceinline__ float load(const void* sc, const void* fl, int q, long long o,
+                                                 const StepParams& P)
+    {
+        if (q >= kH) return Conv<H>::to(((const H*)fl)[(q - kH) * P.plane + o]) * P.inv_scale[q];
+        if (rest(q)) return rest_base(sc, P)[(q / 5) * P.plane + o];
+        return Conv<H>::to(((const H*)sc)[slot(q) * P.plane + o]) * P.inv_scale[q];
+    }
+    static __device__ __forceinline__ void store(void* sc, void* fl, int q, long long o, float v,
+                                                 const StepParams& P)
+    {
+        if (q >= kH)
+            ((H*)fl)[(q - kH) * P.plane + o] = Conv<H>::from(v * P.scale[q]);
+        else if (rest(q))
+            ((float*)rest_base(sc, P))[(q / 5) * P.plane + o] = v;
+        else
+            ((H*)sc)[slot(q) * P.plane + o] = Conv<H>::from(v * P.scale[q]);
+    }
+};
+using StoreF16 = Store16<__half>;
+using StoreBF16 = Store16<__nv_bfloat16>;
 
 __device__ __forceinline__ int wrap(int v, int n)
 {

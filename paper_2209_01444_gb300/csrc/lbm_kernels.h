@@ -12,7 +12,10 @@ namespace lbm {
 // Storage kinds (same values as LBM_FP32/LBM_FP16/LBM_BF16).
 enum Storage { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
 
-inline size_t storage_bytes(int storage) { return storage == kStoreF32 ? 4 : 2; }
+// Bytes per node of the scalar and flow population buffers (see the codecs in
+// lbm_device.cuh: 16-bit storage keeps the three scalar rest planes in FP32).
+inline size_t scalar_node_bytes(int storage) { return storage == kStoreF32 ? 15 * 4 : 12 * 2 + 3 * 4; }
+inline size_t flow_node_bytes(int storage) { return storage == kStoreF32 ? 9 * 4 : 9 * 2; }
 
 // One coupled step (Sec. 3 + Sec. 4): the fused kernel, the wall kernels and
 // the n_sub - 1 flow-only sub-steps; on return cs/cf name the newest buffers.

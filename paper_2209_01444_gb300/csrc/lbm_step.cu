@@ -36,9 +36,8 @@ __device__ __forceinline__ int mirror_or_wrap_local(int g, int n, int periodic, 
 
 template <class Store, bool GRAIN, bool WRITE_FB>
 __global__ void __launch_bounds__(TX* TY)
-    k_coupled_step(const StepParams P, const typename Store::T* __restrict__ src,
-                   const typename Store::T* __restrict__ srcf, typename Store::T* __restrict__ dst,
-                   typename Store::T* __restrict__ dstf, float* __restrict__ hist,
+    k_coupled_step(const StepParams P, const void* __restrict__ src, const void* __restrict__ srcf,
+                   void* __restrict__ dst, void* __restrict__ dstf, float* __restrict__ hist,
                    const uint8_t* __restrict__ grain, float* __restrict__ fb)
 {
     __shared__ float fs[5][TY + 2][TX + 2];
@@ -55,7 +54,7 @@ __global__ void __launch_bounds__(TX* TY)
         float sum = 0.0f;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            float v = Store::load(src, kF * plane + i * plane + o, kF + i, P);
+            float v = Store::load(src, srcf, kF + i, o, P);
             fs[i][hy][hx] = v;
             sum += v;
         }
@@ -72,11 +71,11 @@ __global__ void __launch_bounds__(TX* TY)
 #pragma unroll
     for (int i = 0; i < 5; ++i) f[i] = fs[i][ly][lx];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) n[i] = Store::load(src, (kN + i) * plane + o, kN + i, P);
+    for (int i = 0; i < 5; ++i) n[i] = Store::load(src, srcf, kN + i, o, P);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) g[i] = Store::load(src, (kG + i) * plane + o, kG + i, P);
+    for (int i = 0; i < 5; ++i) g[i] = Store::load(src, srcf, kG + i, o, P);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = Store::load(srcf, i * plane + o, kH + i, P);
+    for (int i = 0; i < 9; ++i) h[i] = Store::load(src, srcf, kH + i, o, P);
     const float phi_prev = hist[0 * plane + o];
     const float Q_prev = hist[1 * plane + o];
     const float Cux_prev = hist[2 * plane + o], Cuy_prev = hist[3 * plane + o];
@@ -157,14 +156,14 @@ __global__ void __launch_bounds__(TX* TY)
         const float fd[5] = {fs[0][ly][lx], fs[1][ly][lx + 1], fs[2][ly + 1][lx], fs[3][ly][lx - 1],
                              fs[4][ly - 1][lx]};
 #pragma unroll
-        for (int i = 0; i < 5; ++i) Store::store(dst, (kF + i) * plane + d5[i], kF + i, fo[i] * ia - ib * fd[i], P);
+        for (int i = 0; i < 5; ++i) Store::store(dst, dstf, kF + i, d5[i], fo[i] * ia - ib * fd[i], P);
     }
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(dst, (kN + i) * plane + d5[i], kN + i, no[i], P);
+    for (int i = 0; i < 5; ++i) Store::store(dst, dstf, kN + i, d5[i], no[i], P);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(dst, (kG + i) * plane + d5[i], kG + i, go[i], P);
+    for (int i = 0; i < 5; ++i) Store::store(dst, dstf, kG + i, d5[i], go[i], P);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store::store(dstf, i * plane + d9[i], kH + i, ho[i], P);
+    for (int i = 0; i < 9; ++i) Store::store(dst, dstf, kH + i, d9[i], ho[i], P);
 
     // ---- history of the backward differences
     hist[0 * plane + o] = m.phi;
@@ -179,9 +178,9 @@ __global__ void __launch_bounds__(TX* TY)
 // Flow sub-step (two-time-scaling of Sec. 4): collide and stream h with phi
 // and the force frozen at time n.
 template <class Store>
-__global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const typename Store::T* __restrict__ src,
-                                                      typename Store::T* __restrict__ dst,
-                                                      const float* __restrict__ hist, const float* __restrict__ fb)
+__global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const void* __restrict__ src,
+                                                      void* __restrict__ dst, const float* __restrict__ hist,
+                                                      const float* __restrict__ fb)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -190,7 +189,7 @@ __global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const 
     const long long o = (long long)y * P.pitch + x;
     float h[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = Store::load(src, i * plane + o, kH + i, P);
+    for (int i = 0; i < 9; ++i) h[i] = Store::load(nullptr, src, kH + i, o, P);
     Macro m;
     m.phi = hist[o];
     m.p1 = m.phi + 1.0f;
@@ -213,7 +212,7 @@ __global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const 
     const long long rY = (long long)y * P.pitch, rP = (long long)yp * P.pitch, rM = (long long)ym * P.pitch;
     const long long d9[9] = {rY + x, rY + xp, rP + x, rY + xm, rM + x, rP + xp, rP + xm, rM + xm, rM + xp};
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store::store(dst, i * plane + d9[i], kH + i, ho[i], P);
+    for (int i = 0; i < 9; ++i) Store::store(nullptr, dst, kH + i, d9[i], ho[i], P);
 }
 
 // Non-equilibrium extrapolation (Guo et al.) on one side pair, applied to the
@@ -221,8 +220,8 @@ __global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const 
 // pop^eq(macros of f), f the first interior node.  `axis` 1: bottom/top rows
 // over x in [xlo, xhi]; `axis` 0: left/right columns over every y.
 template <class Store>
-__global__ void k_walls(const StepParams P, typename Store::T* __restrict__ pop, typename Store::T* __restrict__ popf,
-                        int axis, int lo, int count, int flow_only)
+__global__ void k_walls(const StepParams P, void* __restrict__ pop, void* __restrict__ popf, int axis, int lo,
+                        int count, int flow_only)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * count) return;
@@ -244,13 +243,13 @@ __global__ void k_walls(const StepParams P, typename Store::T* __restrict__ pop,
     const long long ob = (long long)yb * P.pitch + xb, of = (long long)yf * P.pitch + xf;
     float f[5], n[5], g[5], h[9];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) f[i] = Store::load(pop, (kF + i) * plane + of, kF + i, P);
+    for (int i = 0; i < 5; ++i) f[i] = Store::load(pop, popf, kF + i, of, P);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) n[i] = Store::load(pop, (kN + i) * plane + of, kN + i, P);
+    for (int i = 0; i < 5; ++i) n[i] = Store::load(pop, popf, kN + i, of, P);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) g[i] = Store::load(pop, (kG + i) * plane + of, kG + i, P);
+    for (int i = 0; i < 5; ++i) g[i] = Store::load(pop, popf, kG + i, of, P);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = Store::load(popf, i * plane + of, kH + i, P);
+    for (int i = 0; i < 9; ++i) h[i] = Store::load(pop, popf, kH + i, of, P);
     const Macro m = node_macros(f, n, g, h, P);
     const int type = P.bc[side];
     float ubx = 0.0f, uby = 0.0f, pb = m.p;
@@ -269,7 +268,7 @@ __global__ void k_walls(const StepParams P, typename Store::T* __restrict__ pop,
     deq_flow(pb, ubx, uby, eb);
     deq_flow(m.p, m.ux, m.uy, ef);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store::store(popf, i * plane + ob, kH + i, eb[i] + h[i] - ef[i], P);
+    for (int i = 0; i < 9; ++i) Store::store(pop, popf, kH + i, ob, eb[i] + h[i] - ef[i], P);
     if (flow_only) return;
 
     float p1b = m.p1, dCb = m.dC, Ub = m.U, dthb = m.dth;
@@ -286,28 +285,27 @@ __global__ void k_walls(const StepParams P, typename Store::T* __restrict__ pop,
     deq_phi(p1b, eb);
     deq_phi(m.p1, ef);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(pop, (kF + i) * plane + ob, kF + i, eb[i] + f[i] - ef[i], P);
+    for (int i = 0; i < 5; ++i) Store::store(pop, popf, kF + i, ob, eb[i] + f[i] - ef[i], P);
     deq_C(dCb, (1.0f - 0.5f * p1b) * Ub, Cb * ubx * sc, Cb * uby * sc, eb);
     deq_C(m.dC, (1.0f - 0.5f * m.p1) * m.U, Cf * m.ux * sc, Cf * m.uy * sc, ef);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(pop, (kN + i) * plane + ob, kN + i, eb[i] + n[i] - ef[i], P);
+    for (int i = 0; i < 5; ++i) Store::store(pop, popf, kN + i, ob, eb[i] + n[i] - ef[i], P);
     deq_H(dthb, hp1b, Hb * ubx * sc, Hb * uby * sc, eb);
     deq_H(m.dth, m.hp1, m.H * m.ux * sc, m.H * m.uy * sc, ef);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(pop, (kG + i) * plane + ob, kG + i, eb[i] + g[i] - ef[i], P);
+    for (int i = 0; i < 5; ++i) Store::store(pop, popf, kG + i, ob, eb[i] + g[i] - ef[i], P);
 }
 
 template <class Store>
 cudaError_t walls(const StepParams& P, void* sc, void* fl, int flow_only, cudaStream_t s)
 {
-    using T = typename Store::T;
     if (!P.periodic_y) {
         const int lo = P.periodic_x ? 0 : 1, hi = P.periodic_x ? P.nx - 1 : P.nx - 2;
         const int count = hi - lo + 1;
-        k_walls<Store><<<(2 * count + 127) / 128, 128, 0, s>>>(P, (T*)sc, (T*)fl, 1, lo, count, flow_only);
+        k_walls<Store><<<(2 * count + 127) / 128, 128, 0, s>>>(P, sc, fl, 1, lo, count, flow_only);
     }
     if (!P.periodic_x) {
-        k_walls<Store><<<(2 * P.ny + 127) / 128, 128, 0, s>>>(P, (T*)sc, (T*)fl, 0, 0, P.ny, flow_only);
+        k_walls<Store><<<(2 * P.ny + 127) / 128, 128, 0, s>>>(P, sc, fl, 0, 0, P.ny, flow_only);
     }
     return cudaGetLastError();
 }
@@ -315,12 +313,11 @@ cudaError_t walls(const StepParams& P, void* sc, void* fl, int flow_only, cudaSt
 template <class Store>
 cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStream_t s)
 {
-    using T = typename Store::T;
     const dim3 block(TX, TY), grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-    const T* src = (const T*)B.sc[B.cs];
-    const T* srcf = (const T*)B.fl[B.cf];
-    T* dst = (T*)B.sc[1 - B.cs];
-    T* dstf = (T*)B.fl[1 - B.cf];
+    const void* src = B.sc[B.cs];
+    const void* srcf = B.fl[B.cf];
+    void* dst = B.sc[1 - B.cs];
+    void* dstf = B.fl[1 - B.cf];
     const bool grain = B.grain != nullptr, wfb = n_sub > 1;
     if (B.ev_begin) cudaEventRecord(B.ev_begin, s);
     if (grain && wfb)
@@ -341,7 +338,7 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
     for (int sub = 1; sub < n_sub; ++sub) {
         // phi and the force of time n come from hist/fb; the wall scheme reads
         // the scalar macros of time n+1 from the newest scalar buffer
-        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, (const T*)B.fl[B.cf], (T*)B.fl[1 - B.cf], B.hist, B.fb);
+        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, B.fl[B.cf], B.fl[1 - B.cf], B.hist, B.fb);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = walls<Store>(P, B.sc[B.cs], B.fl[1 - B.cf], 1, s)) != cudaSuccess) return e;
         B.cf = 1 - B.cf;

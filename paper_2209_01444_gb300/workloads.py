@@ -176,11 +176,13 @@ def random_fields(nx: int, ny: int, rng_seed: int, u_amp: float = 0.2, p_amp: fl
                   theta0: float = -0.5, U0: float = -0.2) -> tuple[np.ndarray, np.ndarray]:
     """Random initial macroscopic fields [6, ny, nx] = (phi, U, theta, ux, uy,
     p), velocity and pressure in paper units, and a random grain-orientation
-    map (four Voronoi-free stripes of constant orientation).  phi is a smooth
-    random level set passed through tanh, so it spans liquid, solid and
-    interface; the other fields are smooth perturbations."""
+    map (four stripes of constant orientation).  phi is a smooth random level
+    set passed through a steep tanh, so it spans liquid, solid and interfaces
+    of a few nodes; the other fields are smooth perturbations."""
     rng = np.random.Generator(np.random.PCG64(rng_seed))
-    phi = np.tanh(2.5 * smooth_field(nx, ny, rng, 3, 1.0) + 0.3)
+    # steep enough that every interior extremum of phi sits in a settled bulk
+    # phase (|phi| > 0.9999): there grad(phi) -> 0 while d(phi)/dt ~ 0
+    phi = np.tanh(8.0 * smooth_field(nx, ny, rng, 3, 1.0) + 0.3)
     U = U0 + smooth_field(nx, ny, rng, 3, 0.2)
     th = theta0 + smooth_field(nx, ny, rng, 3, 0.2)
     ux = smooth_field(nx, ny, rng, 3, u_amp)
