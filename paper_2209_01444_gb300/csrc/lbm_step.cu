@@ -34,8 +34,12 @@ __device__ __forceinline__ int mirror_or_wrap_local(int g, int n, int periodic, 
     return local + d;
 }
 
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for (64 registers)
+#endif
+
 template <class Store, bool GRAIN, bool WRITE_FB>
-__global__ void __launch_bounds__(TX* TY)
+__global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
     k_coupled_step(const StepParams P, const void* __restrict__ src, const void* __restrict__ srcf,
                    void* __restrict__ dst, void* __restrict__ dstf, float* __restrict__ hist,
                    const uint8_t* __restrict__ grain, float* __restrict__ fb)
@@ -45,31 +49,11 @@ __global__ void __launch_bounds__(TX* TY)
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const long long plane = P.plane;
-
-    // phi populations of the tile and its halo (periodic wrap), and phi there.
-    for (int e = ty * TX + tx; e < (TX + 2) * (TY + 2); e += TX * TY) {
-        const int hx = e % (TX + 2), hy = e / (TX + 2);
-        const int gx = wrap(x0 - 1 + hx, P.nx), gy = wrap(y0 - 1 + hy, P.ny);
-        const long long o = (long long)gy * P.pitch + gx;
-        float sum = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            float v = Store::load(src, srcf, kF + i, o, P);
-            fs[i][hy][hx] = v;
-            sum += v;
-        }
-        ps[hy][hx] = sum;
-    }
-    __syncthreads();
-
     const int x = x0 + tx, y = y0 + ty;
-    if (x >= P.nx || y >= P.ny) return;
-    const long long o = (long long)y * P.pitch + x;
-    const int lx = tx + 1, ly = ty + 1;
-
-    float f[5], n[5], g[5], h[9];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) f[i] = fs[i][ly][lx];
+    const bool active = x < P.nx && y < P.ny;
+    // own-node loads first, so that they are in flight while the tile loads
+    const long long o = active ? (long long)y * P.pitch + x : 0;
+    float n[5], g[5], h[9];
 #pragma unroll
     for (int i = 0; i < 5; ++i) n[i] = Store::load(src, srcf, kN + i, o, P);
 #pragma unroll
@@ -80,6 +64,35 @@ __global__ void __launch_bounds__(TX* TY)
     const float Q_prev = hist[1 * plane + o];
     const float Cux_prev = hist[2 * plane + o], Cuy_prev = hist[3 * plane + o];
     const float Hux_prev = hist[4 * plane + o], Huy_prev = hist[5 * plane + o];
+    uint8_t gid = 0;
+    if (GRAIN) gid = grain[o];
+
+    // phi populations of the tile and its halo (periodic wrap), and phi there.
+    for (int e = ty * TX + tx; e < (TX + 2) * (TY + 2); e += TX * TY) {
+        const int hx = e % (TX + 2), hy = e / (TX + 2);
+        int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+        gx = (gx < 0) ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+        gy = (gy < 0) ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+        if (gx >= P.nx) gx = wrap(gx, P.nx);  // domains narrower than a tile
+        if (gy >= P.ny) gy = wrap(gy, P.ny);
+        const long long oh = (long long)gy * P.pitch + gx;
+        float sum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            float v = Store::load(src, srcf, kF + i, oh, P);
+            fs[i][hy][hx] = v;
+            sum += v;
+        }
+        ps[hy][hx] = sum;
+    }
+    __syncthreads();
+
+    if (!active) return;
+    const int lx = tx + 1, ly = ty + 1;
+
+    float f[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) f[i] = fs[i][ly][lx];
 
     const Macro m = node_macros(f, n, g, h, P);
     const float usx = m.ux * P.nsub, usy = m.uy * P.nsub;  // velocity of the scalar lattice
@@ -91,12 +104,14 @@ __global__ void __launch_bounds__(TX* TY)
     const int yu = mirror_or_wrap_local(y + 1, P.ny, P.periodic_y, ly, +1);
     const float pE = ps[ly][xr], pW = ps[ly][xl], pN = ps[yu][lx], pS = ps[yd][lx];
     const float pNE = ps[yu][xr], pNW = ps[yu][xl], pSE = ps[yd][xr], pSW = ps[yd][xl];
-    const float gx = (pE - pW) * (1.0f / 3.0f) + (pNE + pSE - pNW - pSW) * (1.0f / 12.0f);
-    const float gy = (pN - pS) * (1.0f / 3.0f) + (pNE + pNW - pSE - pSW) * (1.0f / 12.0f);
+    // paired differences, so that mirror-symmetric neighbourhoods (a wall
+    // ghost, a symmetric seed) give an exactly zero component
+    const float gx = (pE - pW) * (1.0f / 3.0f) + ((pNE - pNW) + (pSE - pSW)) * (1.0f / 12.0f);
+    const float gy = (pN - pS) * (1.0f / 3.0f) + ((pNE - pSE) + (pNW - pSW)) * (1.0f / 12.0f);
 
     float co = P.cos_o, so = P.sin_o;
     if (GRAIN) {
-        const float2 cs = P.grain_cs[grain[o]];
+        const float2 cs = P.grain_cs[gid];
         co = cs.x;
         so = cs.y;
     }
