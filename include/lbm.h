@@ -211,6 +211,41 @@ LBM_API int lbm_save_state(lbm_handle* h, void* host, size_t bytes);
  * resuming is bit-exact.  LBM_EINVAL if the size or parameters differ. */
 LBM_API int lbm_load_state(lbm_handle* h, const void* host, size_t bytes);
 
+/* ------------------------------------------------ allocation-free reduction */
+/* The reductions of lbm_get_metrics, computed straight from population
+ * buffers the caller owns, without allocating anything.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, such as a process whose device memory is owned by another
+ * allocator (a framework's caching pool that must see every allocation) or a
+ * long-running loop that may only allocate at start-up.  Those callers still
+ * need the per-block scratch of the reduction; here it lives in one static
+ * device array of 448 KiB (8192 blocks x 7 partials) that every GPU loading
+ * the library holds until the process exits.
+ *
+ * Inputs (device memory, read only): the scalar and flow population buffers of
+ * a state for the problem *p, in the layout the library keeps (the two buffers
+ * that lbm_save_state writes right after its header): each plane has
+ * pitch*ny elements with pitch = nx rounded up to a multiple of 32 and holds the
+ * deviations of one population from the reference equilibrium; the scalar
+ * buffer has 15 FP32 planes (LBM_FP32) or 12 16-bit planes followed by the 3
+ * FP32 rest planes (LBM_FP16/LBM_BF16); the flow buffer has 9 planes of the
+ * storage type.  Output: `out`, 10 doubles in device memory: sum (1 + phi)/2,
+ * sum C, sum H, sum of all h_i, max |u| in flow lattice units, number of nodes
+ * with a non-finite macro, sum phi, and the three tip distances of
+ * lbm_metrics.tip.  The work is queued on `stream` (a cudaStream_t, NULL for the
+ * legacy default stream) and the call returns without waiting.
+ *
+ * Limits and sharing: grids larger than 33,554,432 nodes are rejected with
+ * LBM_EINVAL.  The first call on a device looks up the device address of the
+ * static array (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call shares the one array and leaves
+ * its partial sums in it (each call overwrites every row it reads, so nothing
+ * needs clearing), so calls whose kernels overlap on the GPU, for example on two
+ * streams at once, race.  Errors: LBM_EINVAL for bad arguments or parameters,
+ * LBM_ECUDA for a failed CUDA call; lbm_last_error(NULL) gives the reason. */
+LBM_API int lbm_reduce_noalloc(const lbm_params* p, const void* scalar_pops, const void* flow_pops, double cx,
+                               double cy, double orient, double* out, void* stream);
+
 /* ------------------------------------------------------------ diagnostics */
 /* Kernel timing for roofline measurements: while enabled, lbm_step launches
  * every coupled step directly (no graph) and brackets the fused

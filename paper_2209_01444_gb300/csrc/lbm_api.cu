@@ -716,3 +716,27 @@ const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : g_
 const char* lbm_version(void) { return "lbm-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+namespace lbm {
+
+// Lattice-unit parameters of a problem statement without creating a handle
+// (the temporary handle below holds no heap or device memory).
+int params_to_step(const lbm_params* p, StepParams* out, const char** why)
+{
+    static thread_local std::string msg;
+    msg = validate(p);
+    if (!msg.empty()) {
+        *why = msg.c_str();
+        return LBM_EINVAL;
+    }
+    lbm_handle tmp;
+    tmp.prm = *p;
+    derive(&tmp);
+    *out = tmp.P;
+    return LBM_OK;
+}
+
+// Message returned by lbm_last_error(NULL) for calls that take no handle.
+void set_last_error(const char* msg) { g_create_error = msg; }
+
+}  // namespace lbm

@@ -416,4 +416,21 @@ cudaError_t launch_reduce(const StepParams& P, int storage, const void* sc, cons
     }
 }
 
+cudaError_t launch_reduce_final(const double* partials, int nblocks, double* out, cudaStream_t st)
+{
+    k_reduce_final<<<1, 32, 0, st>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tips(const StepParams& P, int storage, const void* sc, double cx, double cy, double c, double s,
+                        double* out, cudaStream_t st)
+{
+    switch (storage) {
+    case kStoreF16: k_tips<StoreF16><<<3, kRedThreads, 0, st>>>(P, sc, cx, cy, c, s, out); break;
+    case kStoreBF16: k_tips<StoreBF16><<<3, kRedThreads, 0, st>>>(P, sc, cx, cy, c, s, out); break;
+    default: k_tips<StoreF32><<<3, kRedThreads, 0, st>>>(P, sc, cx, cy, c, s, out); break;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace lbm

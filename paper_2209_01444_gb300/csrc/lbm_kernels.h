@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lbm.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -57,5 +58,16 @@ int reduce_blocks(const StepParams& P);
 size_t reduce_partials_size(const StepParams& P);
 cudaError_t launch_reduce(const StepParams& P, int storage, const void* sc, const void* fl, double cx, double cy,
                           double c, double s, double* partials, double* out, cudaStream_t st);
+
+// Building blocks of the reduction, for callers that bring their own partials:
+// fold `nblocks` rows of 7 partials into out[0..6]; tips into out[7..9].
+cudaError_t launch_reduce_final(const double* partials, int nblocks, double* out, cudaStream_t st);
+cudaError_t launch_tips(const StepParams& P, int storage, const void* sc, double cx, double cy, double c, double s,
+                        double* out, cudaStream_t st);
+
+// Validation and lattice-unit conversion of lbm_create, for calls without a
+// handle; *why receives the reason on LBM_EINVAL.
+int params_to_step(const lbm_params* p, StepParams* out, const char** why);
+void set_last_error(const char* msg);
 
 }  // namespace lbm

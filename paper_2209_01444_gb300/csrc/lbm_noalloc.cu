@@ -1,0 +1,156 @@
+// lbm_reduce_noalloc: the FP64 reductions of lbm_get_metrics for callers that
+// cannot allocate device memory.  The only scratch, one row of partial sums
+// per block, is a file-scope device array that every GPU loading the library
+// holds until the process exits; nothing here calls cudaMalloc or cudaFree.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <atomic>
+
+#include "lbm.h"
+#include "lbm_kernels.h"
+
+namespace {
+
+using lbm::StepParams;
+
+constexpr int kThreads = 256;
+constexpr int kNodesPerBlock = 4096;       // 16 nodes per thread
+constexpr int kMaxBlocks = 8192;           // 33,554,432 nodes
+constexpr int kVals = 7;                   // same partials as the handle's reduction
+
+// 8192 blocks x 7 partials x 8 bytes = 448 KiB per device.
+static __device__ __align__(256) double g_reduce_scratch[kMaxBlocks * kVals];
+
+constexpr int kMaxDevices = 64;
+std::atomic<double*> g_scratch_ptr[kMaxDevices];
+
+// Device address of the scratch array on the current device.  In host code
+// the name g_reduce_scratch is only a host-side stand-in, so the address is
+// looked up once per device with that device current.
+cudaError_t scratch_for_current_device(double** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    double* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void* q = nullptr;
+        e = cudaGetSymbolAddress(&q, g_reduce_scratch);
+        if (e != cudaSuccess) return e;
+        p = (double*)q;
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, d));
+    return v;
+}
+
+// Variant of the handle's node reduction: block b folds nodes
+// [b * kNodesPerBlock, (b + 1) * kNodesPerBlock) in FP64 and writes its row of
+// partials; every row it writes is overwritten, so nothing needs clearing.
+template <class Store>
+__global__ void __launch_bounds__(kThreads) k_reduce_chunks(const StepParams P, const void* __restrict__ sc,
+                                                            const void* __restrict__ fl, double* __restrict__ partials)
+{
+    double acc[kVals] = {0, 0, 0, 0, 0, 0, 0};
+    const long long N = (long long)P.nx * P.ny;
+    const long long first = (long long)blockIdx.x * kNodesPerBlock;
+    const long long last = min(first + kNodesPerBlock, N);
+    for (long long t = first + threadIdx.x; t < last; t += kThreads) {
+        const int y = (int)(t / P.nx), x = (int)(t - (long long)y * P.nx);
+        const long long o = (long long)y * P.pitch + x;
+        float f[5], n[5], g[5], h[9];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) f[i] = Store::load(sc, fl, lbm::kF + i, o, P);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) n[i] = Store::load(sc, fl, lbm::kN + i, o, P);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i] = Store::load(sc, fl, lbm::kG + i, o, P);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) h[i] = Store::load(sc, fl, lbm::kH + i, o, P);
+        const lbm::Macro m = lbm::node_macros(f, n, g, h, P);
+        double sh = (double)P.rho0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sh += (double)h[i];
+        const double u = sqrt((double)m.ux * m.ux + (double)m.uy * m.uy);
+        acc[0] += 0.5 * (double)m.p1;
+        acc[1] += 1.0 + (double)m.dC;
+        acc[2] += ((double)P.theta_ref + 0.5) + (double)m.dH;
+        acc[3] += sh;
+        acc[4] = fmax(acc[4], u);
+        acc[5] += (isfinite(m.p1) && isfinite(m.dC) && isfinite(m.dth) && isfinite(u)) ? 0.0 : 1.0;
+        acc[6] += (double)m.p1 - 1.0;
+    }
+    __shared__ double sm[kVals][kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kVals; ++k) {
+        const double v = k == 4 ? warp_max(acc[k]) : warp_sum(acc[k]);
+        if (lane == 0) sm[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kVals) {
+        const int k = threadIdx.x;
+        double v = sm[k][0];
+        for (int w = 1; w < kThreads / 32; ++w) v = (k == 4) ? fmax(v, sm[k][w]) : v + sm[k][w];
+        partials[(long long)blockIdx.x * kVals + k] = v;
+    }
+}
+
+int fail(int code, const char* msg)
+{
+    lbm::set_last_error(msg);
+    return code;
+}
+
+}  // namespace
+
+extern "C" int lbm_reduce_noalloc(const lbm_params* p, const void* scalar_pops, const void* flow_pops, double cx,
+                                  double cy, double orient, double* out, void* stream)
+{
+    if (!p || !scalar_pops || !flow_pops || !out) return fail(LBM_EINVAL, "lbm_reduce_noalloc: NULL argument");
+    if (!isfinite(cx) || !isfinite(cy) || !isfinite(orient))
+        return fail(LBM_EINVAL, "lbm_reduce_noalloc: non-finite tip origin");
+    StepParams P;
+    const char* why = nullptr;
+    if (lbm::params_to_step(p, &P, &why) != LBM_OK) return fail(LBM_EINVAL, why);
+    const long long N = (long long)P.nx * P.ny;
+    const long long blocks = (N + kNodesPerBlock - 1) / kNodesPerBlock;
+    if (blocks > kMaxBlocks)
+        return fail(LBM_EINVAL, "lbm_reduce_noalloc: grid larger than its 33554432-node limit");
+    double* scratch = nullptr;
+    cudaError_t e = scratch_for_current_device(&scratch);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (p->storage) {
+    case LBM_FP16:
+        k_reduce_chunks<lbm::StoreF16><<<(unsigned)blocks, kThreads, 0, s>>>(P, scalar_pops, flow_pops, scratch);
+        break;
+    case LBM_BF16:
+        k_reduce_chunks<lbm::StoreBF16><<<(unsigned)blocks, kThreads, 0, s>>>(P, scalar_pops, flow_pops, scratch);
+        break;
+    default:
+        k_reduce_chunks<lbm::StoreF32><<<(unsigned)blocks, kThreads, 0, s>>>(P, scalar_pops, flow_pops, scratch);
+        break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
+    if ((e = lbm::launch_reduce_final(scratch, (int)blocks, out, s)) != cudaSuccess)
+        return fail(LBM_ECUDA, cudaGetErrorString(e));
+    if ((e = lbm::launch_tips(P, p->storage, scalar_pops, cx, cy, cos(orient), sin(orient), out, s)) != cudaSuccess)
+        return fail(LBM_ECUDA, cudaGetErrorString(e));
+    return LBM_OK;
+}

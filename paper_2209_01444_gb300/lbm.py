@@ -71,6 +71,8 @@ SIGNATURES = {
     "lbm_checkpoint_bytes": (ct.c_size_t, [_H]),
     "lbm_save_state": (ct.c_int, [_H, ct.c_void_p, ct.c_size_t]),
     "lbm_load_state": (ct.c_int, [_H, ct.c_void_p, ct.c_size_t]),
+    "lbm_reduce_noalloc": (ct.c_int, [ct.POINTER(lbm_params), ct.c_void_p, ct.c_void_p, ct.c_double, ct.c_double,
+                                      ct.c_double, ct.c_void_p, ct.c_void_p]),
     "lbm_set_profiling": (ct.c_int, [_H, ct.c_int]),
     "lbm_kernel_time": (ct.c_int, [_H, _DP, ct.POINTER(ct.c_longlong)]),
     "lbm_last_error": (ct.c_char_p, [_H]),
