@@ -211,6 +211,42 @@ LBM_API int lbm_save_state(lbm_handle* h, void* host, size_t bytes);
  * resuming is bit-exact.  LBM_EINVAL if the size or parameters differ. */
 LBM_API int lbm_load_state(lbm_handle* h, const void* host, size_t bytes);
 
+/* ------------------------------------------------------------------ batch */
+/* Many independent domains advanced together: each has its own size and
+ * parameters (one storage type for all, n_sub = 1).  One persistent kernel
+ * per coupled step sweeps the tiles of every domain, batched wall kernels
+ * follow, and lbm_batch_step replays 16-step sequences from captured CUDA
+ * graphs.  The tile height (4, 8 or 16 rows of 32 nodes) is chosen by
+ * lbm_batch_tune.  Domains are indexed 0..n-1; per-domain results use the
+ * single-domain conventions above. */
+typedef struct lbm_batch lbm_batch;
+
+/* Create n domains from params[0..n-1] (validated as lbm_create does). */
+LBM_API int lbm_batch_create(const lbm_params* params, int n, lbm_batch** out);
+LBM_API void lbm_batch_destroy(lbm_batch* b);
+LBM_API int lbm_batch_set_stream(lbm_batch* b, void* stream);
+/* Seeded start of one domain (lbm_init_seeds semantics). */
+LBM_API int lbm_batch_init_seeds(lbm_batch* b, int dom, const lbm_seed* seeds, int n_seeds, double U0,
+                                 double theta0);
+/* Queue nsteps coupled steps of every domain; all must be initialised. */
+LBM_API int lbm_batch_step(lbm_batch* b, int nsteps);
+LBM_API int lbm_batch_synchronize(lbm_batch* b);
+LBM_API int lbm_batch_get_fields(lbm_batch* b, int dom, unsigned mask, double* out);
+LBM_API int lbm_batch_get_metrics(lbm_batch* b, int dom, double cx, double cy, double orient, lbm_metrics* m);
+/* Total nodes of all domains; current tile height. */
+LBM_API long long lbm_batch_nodes(const lbm_batch* b);
+LBM_API int lbm_batch_tile_height(const lbm_batch* b);
+/* Force the tile height (4, 8 or 16) instead of tuning it. */
+LBM_API int lbm_batch_set_tile_height(lbm_batch* b, int tile_height);
+/* Autotuner: pick the fastest tile height for this batch on this GPU.  A
+ * cache file (one "key height" line per GPU name, storage, size class and
+ * domain count; NULL for none) is read first and appended to after a
+ * measurement.  Measuring times 12 steps per height on a device copy of the
+ * current state, which is restored afterwards (needs that much free memory);
+ * the step counter does not move. */
+LBM_API int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height);
+LBM_API const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* ------------------------------------------------ allocation-free reduction */
 /* The reductions of lbm_get_metrics, computed straight from population
  * buffers the caller owns, without allocating anything.  The paper has no

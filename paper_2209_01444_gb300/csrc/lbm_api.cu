@@ -740,3 +740,416 @@ int params_to_step(const lbm_params* p, StepParams* out, const char** why)
 void set_last_error(const char* msg) { g_create_error = msg; }
 
 }  // namespace lbm
+
+// ===================================================================== batch
+// Many independent domains (their own sizes and parameters, one storage type,
+// n_sub = 1) advanced together: each domain keeps the buffers of a
+// single-domain handle; one persistent kernel per step sweeps the tiles of all
+// of them, batched wall kernels follow, and 16-step sequences replay from
+// captured CUDA graphs.
+
+struct lbm_batch {
+    std::vector<lbm_handle*> dom;
+    int storage = 0;
+    int parity = 0;          // buffer index holding the newest populations of every domain
+    int ty = 8;              // tile height of the batched kernel
+    int ctas[3] = {0, 0, 0}; // resident CTAs for tile heights 4, 8, 16
+    cudaStream_t stream = nullptr;
+    lbm::DomainDesc* d_descs = nullptr;
+    int4* d_tiles[3] = {nullptr, nullptr, nullptr};
+    int ntiles[3] = {0, 0, 0};
+    int4* d_walls[2] = {nullptr, nullptr};
+    int nwall[2] = {0, 0};
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (parity, ty)
+    long long steps = 0, nodes = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+int bfail(lbm_batch* b, int code, const std::string& msg)
+{
+    if (b)
+        b->err = msg;
+    else
+        g_batch_error = msg;
+    return code;
+}
+
+#define LBM_BCUDA(b, call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return bfail(b, LBM_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+int tyk(int ty) { return ty == 4 ? 0 : ty == 8 ? 1 : 2; }
+
+void drop_batch_graphs(lbm_batch* b)
+{
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+lbm::BatchTables tables(const lbm_batch* b)
+{
+    lbm::BatchTables T;
+    T.descs = b->d_descs;
+    for (int k = 0; k < 3; ++k) {
+        T.tiles[k] = b->d_tiles[k];
+        T.ntiles[k] = b->ntiles[k];
+    }
+    for (int k = 0; k < 2; ++k) {
+        T.walls[k] = b->d_walls[k];
+        T.nwall[k] = b->nwall[k];
+    }
+    return T;
+}
+
+// Descriptor table from the domains' current parameters and buffers.
+int upload_descs(lbm_batch* b)
+{
+    std::vector<lbm::DomainDesc> d(b->dom.size());
+    for (size_t i = 0; i < b->dom.size(); ++i) {
+        lbm_handle* h = b->dom[i];
+        d[i].P = h->P;
+        for (int k = 0; k < 2; ++k) {
+            d[i].sc[k] = h->B.sc[k];
+            d[i].fl[k] = h->B.fl[k];
+        }
+        d[i].hist = h->B.hist;
+        d[i].grain = h->B.grain;
+    }
+    LBM_BCUDA(b, cudaMemcpyAsync(b->d_descs, d.data(), d.size() * sizeof(lbm::DomainDesc), cudaMemcpyHostToDevice,
+                                 b->stream));
+    LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    drop_batch_graphs(b);
+    return LBM_OK;
+}
+
+int batch_graph(lbm_batch* b, cudaGraphExec_t* out)
+{
+    const auto key = std::make_pair(b->parity, b->ty);
+    auto it = b->graphs.find(key);
+    if (it != b->graphs.end()) {
+        *out = it->second;
+        return LBM_OK;
+    }
+    cudaStream_t cap;
+    LBM_BCUDA(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    const lbm::BatchTables T = tables(b);
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int par = b->parity;
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) {
+        e = lbm::launch_batch_step(T, b->storage, b->ty, par, b->ctas[tyk(b->ty)], cap);
+        par = 1 - par;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = e2;
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(b, LBM_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    b->graphs[key] = ex;
+    *out = ex;
+    return LBM_OK;
+}
+
+int batch_ready(lbm_batch* b)
+{
+    if (!b) return LBM_EINVAL;
+    for (lbm_handle* h : b->dom)
+        if (!h->initialised) return bfail(b, LBM_ESTATE, "every domain must be initialised before stepping");
+    return LBM_OK;
+}
+
+int batch_run_direct(lbm_batch* b, int n)
+{
+    const lbm::BatchTables T = tables(b);
+    for (int i = 0; i < n; ++i) {
+        LBM_BCUDA(b, lbm::launch_batch_step(T, b->storage, b->ty, b->parity, b->ctas[tyk(b->ty)], b->stream));
+        b->parity = 1 - b->parity;
+    }
+    return LBM_OK;
+}
+
+void sync_domain_parity(lbm_batch* b)
+{
+    for (lbm_handle* h : b->dom) {
+        h->B.cs = b->parity;
+        h->B.cf = b->parity;
+        h->steps = b->steps;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(const lbm_params* params, int n, lbm_batch** out)
+{
+    if (!out) return bfail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!params || n < 1) return bfail(nullptr, LBM_EINVAL, "need at least one domain");
+    for (int i = 0; i < n; ++i) {
+        if (params[i].storage != params[0].storage) return bfail(nullptr, LBM_EINVAL, "domains must share one storage");
+        if (params[i].n_sub != 1) return bfail(nullptr, LBM_EINVAL, "batched domains need n_sub = 1");
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return bfail(nullptr, LBM_ENOMEM, "host allocation failed");
+    b->storage = params[0].storage;
+    for (int i = 0; i < n; ++i) {
+        lbm_handle* h = nullptr;
+        int rc = lbm_create(&params[i], &h);
+        if (rc != LBM_OK) {
+            std::string why = "domain " + std::to_string(i) + ": " + lbm_last_error(nullptr);
+            lbm_batch_destroy(b);
+            return bfail(nullptr, rc, why);
+        }
+        b->dom.push_back(h);
+        b->nodes += (long long)params[i].nx * params[i].ny;
+    }
+    // tile tables for each tile height, domain-major
+    const int tys[3] = {4, 8, 16};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        std::vector<int4> t;
+        for (int i = 0; i < n; ++i)
+            for (int y0 = 0; y0 < params[i].ny; y0 += tys[k])
+                for (int x0 = 0; x0 < params[i].nx; x0 += lbm::TX) t.push_back(make_int4(i, x0, y0, 0));
+        b->ntiles[k] = (int)t.size();
+        e = cudaMalloc(&b->d_tiles[k], t.size() * sizeof(int4));
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_tiles[k], t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    }
+    // wall lists: y walls (axis 1) and x walls (axis 0), same node sets as the single-domain walls
+    std::vector<int4> w[2];
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const lbm_params& p = params[i];
+        const bool px = p.bc[0] == LBM_BC_PERIODIC, py = p.bc[2] == LBM_BC_PERIODIC;
+        if (!py) {
+            const int lo = px ? 0 : 1, hi = px ? p.nx - 1 : p.nx - 2;
+            for (int which = 0; which < 2; ++which)
+                for (int j = lo; j <= hi; ++j) w[0].push_back(make_int4(i, 1, which, j));
+        }
+        if (!px)
+            for (int which = 0; which < 2; ++which)
+                for (int j = 0; j < p.ny; ++j) w[1].push_back(make_int4(i, 0, which, j));
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        b->nwall[k] = (int)w[k].size();
+        if (w[k].empty()) continue;
+        e = cudaMalloc(&b->d_walls[k], w[k].size() * sizeof(int4));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_walls[k], w[k].data(), w[k].size() * sizeof(int4), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_descs, n * sizeof(lbm::DomainDesc));
+    if (e != cudaSuccess) {
+        std::string why = std::string("batch tables: ") + cudaGetErrorString(e);
+        lbm_batch_destroy(b);
+        return bfail(nullptr, LBM_ECUDA, why);
+    }
+    for (int k = 0; k < 3; ++k) b->ctas[k] = lbm::batch_resident_ctas(b->storage, tys[k]);
+    *out = b;
+    return upload_descs(b);
+}
+
+void lbm_batch_destroy(lbm_batch* b)
+{
+    if (!b) return;
+    drop_batch_graphs(b);
+    for (lbm_handle* h : b->dom) lbm_destroy(h);
+    for (int k = 0; k < 3; ++k)
+        if (b->d_tiles[k]) cudaFree(b->d_tiles[k]);
+    for (int k = 0; k < 2; ++k)
+        if (b->d_walls[k]) cudaFree(b->d_walls[k]);
+    if (b->d_descs) cudaFree(b->d_descs);
+    delete b;
+}
+
+int lbm_batch_set_stream(lbm_batch* b, void* stream)
+{
+    if (!b) return LBM_EINVAL;
+    b->stream = (cudaStream_t)stream;
+    for (lbm_handle* h : b->dom) h->stream = b->stream;
+    return LBM_OK;
+}
+
+int lbm_batch_init_seeds(lbm_batch* b, int dom, const lbm_seed* seeds, int n, double U0, double theta0)
+{
+    if (!b) return LBM_EINVAL;
+    if (dom < 0 || dom >= (int)b->dom.size()) return bfail(b, LBM_EINVAL, "domain index out of range");
+    lbm_handle* h = b->dom[dom];
+    int rc = lbm_init_seeds(h, seeds, n, U0, theta0);
+    if (rc) return bfail(b, rc, h->err);
+    // the handle initialised buffer 0; the batch may be at the other parity
+    if (b->parity == 1) {
+        LBM_BCUDA(b, cudaMemcpyAsync(h->B.sc[1], h->B.sc[0], h->sc_bytes, cudaMemcpyDeviceToDevice, b->stream));
+        LBM_BCUDA(b, cudaMemcpyAsync(h->B.fl[1], h->B.fl[0], h->fl_bytes, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    h->B.cs = h->B.cf = b->parity;
+    return upload_descs(b);
+}
+
+int lbm_batch_step(lbm_batch* b, int nsteps)
+{
+    int rc = batch_ready(b);
+    if (rc) return rc;
+    if (nsteps < 0) return bfail(b, LBM_EINVAL, "nsteps < 0");
+    int left = nsteps;
+    while (left >= kGraphSteps) {
+        cudaGraphExec_t ex;
+        if ((rc = batch_graph(b, &ex))) return rc;
+        LBM_BCUDA(b, cudaGraphLaunch(ex, b->stream));
+        left -= kGraphSteps;  // even: the parity is unchanged
+    }
+    if ((rc = batch_run_direct(b, left))) return rc;
+    b->steps += nsteps;
+    sync_domain_parity(b);
+    return LBM_OK;
+}
+
+int lbm_batch_synchronize(lbm_batch* b)
+{
+    if (!b) return LBM_EINVAL;
+    LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+int lbm_batch_get_fields(lbm_batch* b, int dom, unsigned mask, double* out)
+{
+    if (!b) return LBM_EINVAL;
+    if (dom < 0 || dom >= (int)b->dom.size()) return bfail(b, LBM_EINVAL, "domain index out of range");
+    int rc = lbm_get_fields(b->dom[dom], mask, out);
+    return rc ? bfail(b, rc, b->dom[dom]->err) : LBM_OK;
+}
+
+int lbm_batch_get_metrics(lbm_batch* b, int dom, double cx, double cy, double orient, lbm_metrics* m)
+{
+    if (!b) return LBM_EINVAL;
+    if (dom < 0 || dom >= (int)b->dom.size()) return bfail(b, LBM_EINVAL, "domain index out of range");
+    int rc = lbm_get_metrics(b->dom[dom], cx, cy, orient, m);
+    return rc ? bfail(b, rc, b->dom[dom]->err) : LBM_OK;
+}
+
+long long lbm_batch_nodes(const lbm_batch* b) { return b ? b->nodes : -1; }
+
+int lbm_batch_tile_height(const lbm_batch* b) { return b ? b->ty : -1; }
+
+int lbm_batch_set_tile_height(lbm_batch* b, int tile_height)
+{
+    if (!b) return LBM_EINVAL;
+    if (tile_height != 4 && tile_height != 8 && tile_height != 16) return bfail(b, LBM_EINVAL, "tile height must be 4, 8 or 16");
+    b->ty = tile_height;
+    return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height)
+{
+    int rc = batch_ready(b);
+    if (rc) return rc;
+    cudaDeviceProp prop;
+    int dev = 0;
+    LBM_BCUDA(b, cudaGetDevice(&dev));
+    LBM_BCUDA(b, cudaGetDeviceProperties(&prop, dev));
+    // size class: total nodes to two significant digits
+    long long cls = b->nodes;
+    long long scale = 1;
+    while (cls >= 100) {
+        cls /= 10;
+        scale *= 10;
+    }
+    char key[256];
+    snprintf(key, sizeof(key), "%s|storage%d|nodes%lld|domains%zu", prop.name, b->storage, cls * scale, b->dom.size());
+    for (char* c = key; *c; ++c)
+        if (*c == ' ') *c = '_';
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char k[256];
+            int v;
+            while (fscanf(f, "%255s %d", k, &v) == 2)
+                if (strcmp(k, key) == 0 && (v == 4 || v == 8 || v == 16)) {
+                    b->ty = v;
+                    fclose(f);
+                    if (tile_height) *tile_height = v;
+                    return LBM_OK;
+                }
+            fclose(f);
+        }
+    }
+    // time each tile height on a snapshot of the state, then restore it
+    std::vector<void*> backup;
+    for (lbm_handle* h : b->dom) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, h->sc_bytes + h->fl_bytes + (size_t)h->P.plane * sizeof(float) * lbm::kHist);
+        if (e != cudaSuccess) {
+            for (void* q : backup) cudaFree(q);
+            return bfail(b, LBM_ENOMEM, "no device memory for the tuning snapshot");
+        }
+        char* c = (char*)p;
+        cudaMemcpyAsync(c, h->B.sc[b->parity], h->sc_bytes, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(c + h->sc_bytes, h->B.fl[b->parity], h->fl_bytes, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(c + h->sc_bytes + h->fl_bytes, h->B.hist, (size_t)h->P.plane * sizeof(float) * lbm::kHist,
+                        cudaMemcpyDeviceToDevice, b->stream);
+        backup.push_back(p);
+    }
+    const int start_parity = b->parity;
+    const int tys[3] = {4, 8, 16};
+    float best_ms = 1e30f;
+    int best = b->ty;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const lbm::BatchTables T = tables(b);
+    for (int k = 0; k < 3; ++k) {
+        int par = start_parity;
+        for (int i = 0; i < 2; ++i, par = 1 - par)
+            lbm::launch_batch_step(T, b->storage, tys[k], par, b->ctas[k], b->stream);
+        cudaEventRecord(e0, b->stream);
+        for (int i = 0; i < 10; ++i, par = 1 - par)
+            lbm::launch_batch_step(T, b->storage, tys[k], par, b->ctas[k], b->stream);
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = tys[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (size_t i = 0; i < b->dom.size(); ++i) {
+        lbm_handle* h = b->dom[i];
+        char* c = (char*)backup[i];
+        cudaMemcpyAsync(h->B.sc[start_parity], c, h->sc_bytes, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(h->B.fl[start_parity], c + h->sc_bytes, h->fl_bytes, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(h->B.hist, c + h->sc_bytes + h->fl_bytes, (size_t)h->P.plane * sizeof(float) * lbm::kHist,
+                        cudaMemcpyDeviceToDevice, b->stream);
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    for (void* q : backup) cudaFree(q);
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, std::string("tuning: ") + cudaGetErrorString(e));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, std::string("tuning: ") + cudaGetErrorString(e));
+    b->parity = start_parity;
+    b->ty = best;
+    drop_batch_graphs(b);
+    if (cache_path)
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s %d\n", key, best);
+            fclose(f);
+        }
+    if (tile_height) *tile_height = best;
+    return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+}  // extern "C"

@@ -32,6 +32,32 @@ struct StepBuffers {
 
 cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s);
 
+// One domain of a batch as the batched kernels see it: its parameters and the
+// two parities of its population buffers (n_sub = 1).
+struct DomainDesc {
+    StepParams P;
+    void* sc[2];
+    void* fl[2];
+    float* hist;
+    const uint8_t* grain;  // null when the domain is one grain
+};
+
+// Device tables of a batch: tiles {domain, x0, y0, 0} for tile heights 4, 8,
+// 16 (index 0, 1, 2), wall nodes {domain, axis, side, index} for the y walls
+// (0) and the x walls (1).
+struct BatchTables {
+    const DomainDesc* descs;
+    const int4* tiles[3];
+    int ntiles[3];
+    const int4* walls[2];
+    int nwall[2];
+};
+
+// One coupled step of every domain: buffers `parity` -> 1 - parity, then walls.
+cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int parity, int ctas, cudaStream_t s);
+// CTAs of the persistent batched kernel that fit on the current device at once.
+int batch_resident_ctas(int storage, int ty);
+
 // Initialisation: equilibrium populations from lattice-unit macros
 // (phi, U, theta, ux, uy, p) in FP64 planes, then history = time-0 macros.
 cudaError_t launch_init_from_fields(const StepParams& P, int storage, const double* fields, void* sc, void* fl,

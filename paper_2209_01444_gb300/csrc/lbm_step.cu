@@ -38,16 +38,18 @@ __device__ __forceinline__ int mirror_or_wrap_local(int g, int n, int periodic, 
 #define LBM_STEP_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for (64 registers)
 #endif
 
-template <class Store, bool GRAIN, bool WRITE_FB>
-__global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
-    k_coupled_step(const StepParams P, const void* __restrict__ src, const void* __restrict__ srcf,
-                   void* __restrict__ dst, void* __restrict__ dstf, float* __restrict__ hist,
-                   const uint8_t* __restrict__ grain, float* __restrict__ fb)
+// One tile of the coupled step: the CTA (TX x TYV threads) updates the nodes
+// [x0, x0 + TX) x [y0, y0 + TYV) of one domain.  GRAIN: the domain may carry a
+// grain map (read when `grain` is not null).  All threads reach the one
+// barrier, so callers may loop over tiles.
+template <class Store, bool GRAIN, bool WRITE_FB, int TYV>
+__device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __restrict__ src,
+                                             const void* __restrict__ srcf, void* __restrict__ dst,
+                                             void* __restrict__ dstf, float* __restrict__ hist,
+                                             const uint8_t* __restrict__ grain, float* __restrict__ fb, int x0,
+                                             int y0, float (&fs)[5][TYV + 2][TX + 2], float (&ps)[TYV + 2][TX + 2])
 {
-    __shared__ float fs[5][TY + 2][TX + 2];
-    __shared__ float ps[TY + 2][TX + 2];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const long long plane = P.plane;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < P.nx && y < P.ny;
@@ -65,10 +67,10 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
     const float Cux_prev = hist[2 * plane + o], Cuy_prev = hist[3 * plane + o];
     const float Hux_prev = hist[4 * plane + o], Huy_prev = hist[5 * plane + o];
     uint8_t gid = 0;
-    if (GRAIN) gid = grain[o];
+    if (GRAIN && grain) gid = grain[o];
 
     // phi populations of the tile and its halo (periodic wrap), and phi there.
-    for (int e = ty * TX + tx; e < (TX + 2) * (TY + 2); e += TX * TY) {
+    for (int e = ty * TX + tx; e < (TX + 2) * (TYV + 2); e += TX * TYV) {
         const int hx = e % (TX + 2), hy = e / (TX + 2);
         int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
         gx = (gx < 0) ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
     const float gy = (pN - pS) * (1.0f / 3.0f) + ((pNE - pSE) + (pNW - pSW)) * (1.0f / 12.0f);
 
     float co = P.cos_o, so = P.sin_o;
-    if (GRAIN) {
+    if (GRAIN && grain) {
         const float2 cs = P.grain_cs[gid];
         co = cs.x;
         so = cs.y;
@@ -190,6 +192,52 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
     if (WRITE_FB) fb[o] = m.Fy;
 }
 
+template <class Store, bool GRAIN, bool WRITE_FB>
+__global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
+    k_coupled_step(const StepParams P, const void* __restrict__ src, const void* __restrict__ srcf,
+                   void* __restrict__ dst, void* __restrict__ dstf, float* __restrict__ hist,
+                   const uint8_t* __restrict__ grain, float* __restrict__ fb)
+{
+    __shared__ float fs[5][TY + 2][TX + 2];
+    __shared__ float ps[TY + 2][TX + 2];
+    coupled_tile<Store, GRAIN, WRITE_FB, TY>(P, src, srcf, dst, dstf, hist, grain, fb, blockIdx.x * TX,
+                                             blockIdx.y * TY, fs, ps);
+}
+
+// Batched coupled step: one persistent grid sweeps the tile table of every
+// domain, reloading the domain's parameters into shared memory when the
+// domain changes.  A kernel boundary separates steps.
+template <class Store, int TYV>
+__global__ void __launch_bounds__(TX* TYV, 32 / TYV)
+    k_batch_step(const DomainDesc* __restrict__ descs, const int4* __restrict__ tiles, int ntiles, int chunk,
+                 int parity)
+{
+    __shared__ float fs[5][TYV + 2][TX + 2];
+    __shared__ float ps[TYV + 2][TX + 2];
+    __shared__ DomainDesc sd;
+    __shared__ int s_dom;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    if (tid == 0) s_dom = -1;
+    __syncthreads();
+    // each CTA takes a contiguous run of tiles: consecutive tiles share the
+    // domain and their halos stay in L2
+    const int t_end = min(ntiles, (blockIdx.x + 1) * chunk);
+    for (int t = blockIdx.x * chunk; t < t_end; ++t) {
+        const int4 tl = tiles[t];
+        if (tl.x != s_dom) {
+            __syncthreads();  // every thread has read s_dom
+            const int* srcw = (const int*)(descs + tl.x);
+            int* dstw = (int*)&sd;
+            for (int w = tid; w < (int)(sizeof(DomainDesc) / sizeof(int)); w += TX * TYV) dstw[w] = srcw[w];
+            if (tid == 0) s_dom = tl.x;
+            __syncthreads();
+        }
+        coupled_tile<Store, true, false, TYV>(sd.P, sd.sc[parity], sd.fl[parity], sd.sc[1 - parity],
+                                              sd.fl[1 - parity], sd.hist, sd.grain, nullptr, tl.y, tl.z, fs, ps);
+        __syncthreads();  // the tile arrays are reused by the next tile
+    }
+}
+
 // Flow sub-step (two-time-scaling of Sec. 4): collide and stream h with phi
 // and the force frozen at time n.
 template <class Store>
@@ -235,13 +283,9 @@ __global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const 
 // pop^eq(macros of f), f the first interior node.  `axis` 1: bottom/top rows
 // over x in [xlo, xhi]; `axis` 0: left/right columns over every y.
 template <class Store>
-__global__ void k_walls(const StepParams P, void* __restrict__ pop, void* __restrict__ popf, int axis, int lo,
-                        int count, int flow_only)
+__device__ __forceinline__ void wall_node(const StepParams& P, void* __restrict__ pop, void* __restrict__ popf,
+                                          int axis, int which, int j, int flow_only)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 2 * count) return;
-    const int which = t / count;           // 0: low side, 1: high side
-    const int j = lo + (t - which * count);
     const int side = axis == 0 ? which : 2 + which;
     if (P.bc[side] == 0) return;
     int xb, yb, xf, yf;
@@ -312,6 +356,29 @@ __global__ void k_walls(const StepParams P, void* __restrict__ pop, void* __rest
 }
 
 template <class Store>
+__global__ void k_walls(const StepParams P, void* __restrict__ pop, void* __restrict__ popf, int axis, int lo,
+                        int count, int flow_only)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * count) return;
+    const int which = t / count;           // 0: low side, 1: high side
+    wall_node<Store>(P, pop, popf, axis, which, lo + (t - which * count), flow_only);
+}
+
+// Batched walls: one thread per entry {domain, axis, side, index} of a list
+// holding one axis of every domain.
+template <class Store>
+__global__ void k_batch_walls(const DomainDesc* __restrict__ descs, const int4* __restrict__ nodes, int count,
+                              int parity)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int4 e = nodes[t];
+    const DomainDesc& d = descs[e.x];
+    wall_node<Store>(d.P, d.sc[parity], d.fl[parity], e.y, e.z, e.w, 0);
+}
+
+template <class Store>
 cudaError_t walls(const StepParams& P, void* sc, void* fl, int flow_only, cudaStream_t s)
 {
     if (!P.periodic_y) {
@@ -361,7 +428,60 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
     return cudaSuccess;
 }
 
+template <class Store, int TYV>
+cudaError_t batch_step_t(const BatchTables& T, int parity, int ctas, cudaStream_t s)
+{
+    const int k = TYV == 4 ? 0 : TYV == 8 ? 1 : 2;
+    const int chunk = (T.ntiles[k] + ctas - 1) / ctas;
+    const int grid = (T.ntiles[k] + chunk - 1) / chunk;
+    k_batch_step<Store, TYV><<<grid, dim3(TX, TYV), 0, s>>>(T.descs, T.tiles[k], T.ntiles[k], chunk, parity);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the fused kernel wrote buffers 1 - parity; walls act on those
+    if (T.nwall[0])
+        k_batch_walls<Store><<<(T.nwall[0] + 127) / 128, 128, 0, s>>>(T.descs, T.walls[0], T.nwall[0], 1 - parity);
+    if (T.nwall[1])
+        k_batch_walls<Store><<<(T.nwall[1] + 127) / 128, 128, 0, s>>>(T.descs, T.walls[1], T.nwall[1], 1 - parity);
+    return cudaGetLastError();
+}
+
+template <class Store>
+cudaError_t batch_step_store(const BatchTables& T, int ty, int parity, int ctas, cudaStream_t s)
+{
+    switch (ty) {
+    case 4: return batch_step_t<Store, 4>(T, parity, ctas, s);
+    case 16: return batch_step_t<Store, 16>(T, parity, ctas, s);
+    default: return batch_step_t<Store, 8>(T, parity, ctas, s);
+    }
+}
+
+template <class Store, int TYV>
+int batch_ctas_t()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_step<Store, TYV>, TX * TYV, 0);
+    return sms * (per > 0 ? per : 1);
+}
+
 }  // namespace
+
+cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int parity, int ctas, cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return batch_step_store<StoreF16>(T, ty, parity, ctas, s);
+    case kStoreBF16: return batch_step_store<StoreBF16>(T, ty, parity, ctas, s);
+    default: return batch_step_store<StoreF32>(T, ty, parity, ctas, s);
+    }
+}
+
+int batch_resident_ctas(int storage, int ty)
+{
+    if (storage == kStoreF16) return ty == 4 ? batch_ctas_t<StoreF16, 4>() : ty == 16 ? batch_ctas_t<StoreF16, 16>() : batch_ctas_t<StoreF16, 8>();
+    if (storage == kStoreBF16) return ty == 4 ? batch_ctas_t<StoreBF16, 4>() : ty == 16 ? batch_ctas_t<StoreBF16, 16>() : batch_ctas_t<StoreBF16, 8>();
+    return ty == 4 ? batch_ctas_t<StoreF32, 4>() : ty == 16 ? batch_ctas_t<StoreF32, 16>() : batch_ctas_t<StoreF32, 8>();
+}
 
 cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s)
 {

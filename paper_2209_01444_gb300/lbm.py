@@ -73,6 +73,20 @@ SIGNATURES = {
     "lbm_load_state": (ct.c_int, [_H, ct.c_void_p, ct.c_size_t]),
     "lbm_reduce_noalloc": (ct.c_int, [ct.POINTER(lbm_params), ct.c_void_p, ct.c_void_p, ct.c_double, ct.c_double,
                                       ct.c_double, ct.c_void_p, ct.c_void_p]),
+    "lbm_batch_create": (ct.c_int, [ct.POINTER(lbm_params), ct.c_int, ct.POINTER(ct.c_void_p)]),
+    "lbm_batch_destroy": (None, [_H]),
+    "lbm_batch_set_stream": (ct.c_int, [_H, ct.c_void_p]),
+    "lbm_batch_init_seeds": (ct.c_int, [_H, ct.c_int, ct.POINTER(lbm_seed), ct.c_int, ct.c_double, ct.c_double]),
+    "lbm_batch_step": (ct.c_int, [_H, ct.c_int]),
+    "lbm_batch_synchronize": (ct.c_int, [_H]),
+    "lbm_batch_get_fields": (ct.c_int, [_H, ct.c_int, ct.c_uint, _DP]),
+    "lbm_batch_get_metrics": (ct.c_int, [_H, ct.c_int, ct.c_double, ct.c_double, ct.c_double,
+                                         ct.POINTER(lbm_metrics)]),
+    "lbm_batch_nodes": (ct.c_longlong, [_H]),
+    "lbm_batch_tile_height": (ct.c_int, [_H]),
+    "lbm_batch_set_tile_height": (ct.c_int, [_H, ct.c_int]),
+    "lbm_batch_tune": (ct.c_int, [_H, ct.c_char_p, ct.POINTER(ct.c_int)]),
+    "lbm_batch_last_error": (ct.c_char_p, [_H]),
     "lbm_set_profiling": (ct.c_int, [_H, ct.c_int]),
     "lbm_kernel_time": (ct.c_int, [_H, _DP, ct.POINTER(ct.c_longlong)]),
     "lbm_last_error": (ct.c_char_p, [_H]),
@@ -230,3 +244,77 @@ class Simulation:
     def load(self, blob: bytes) -> None:
         buf = ct.create_string_buffer(blob, len(blob))
         self._check(self.lib.lbm_load_state(self.h, buf, len(blob)))
+
+
+class Batch:
+    """Independent domains advanced together by the batched persistent kernel."""
+
+    def __init__(self, params_list, storage: str | int = "fp32", stream=None):
+        self.lib = load()
+        self.params = [dict(p) for p in params_list]
+        arr = (lbm_params * len(params_list))(*[make_params(p, storage) for p in params_list])
+        h = ct.c_void_p()
+        rc = self.lib.lbm_batch_create(arr, len(params_list), ct.byref(h))
+        if rc != LBM_OK:
+            raise LBMError(rc, self.lib.lbm_batch_last_error(None).decode())
+        self.h = h
+        if stream is not None:
+            raw = getattr(stream, "cuda_stream", stream)
+            self._check(self.lib.lbm_batch_set_stream(self.h, ct.c_void_p(raw or 0)))
+
+    def _check(self, rc: int) -> None:
+        if rc != LBM_OK:
+            raise LBMError(rc, self.lib.lbm_batch_last_error(self.h).decode())
+
+    def __del__(self):
+        h, self.h = getattr(self, "h", None), None
+        if h:
+            self.lib.lbm_batch_destroy(h)
+
+    def __len__(self):
+        return len(self.params)
+
+    @property
+    def nodes(self) -> int:
+        return int(self.lib.lbm_batch_nodes(self.h))
+
+    @property
+    def tile_height(self) -> int:
+        return int(self.lib.lbm_batch_tile_height(self.h))
+
+    @tile_height.setter
+    def tile_height(self, ty: int) -> None:
+        self._check(self.lib.lbm_batch_set_tile_height(self.h, int(ty)))
+
+    def init_seeds(self, dom: int, seeds, U0: float, theta0: float) -> None:
+        a = np.asarray(seeds, np.float64).reshape(-1, 4)
+        arr = (lbm_seed * len(a))(*[lbm_seed(*row) for row in a])
+        self._check(self.lib.lbm_batch_init_seeds(self.h, dom, arr, len(a), U0, theta0))
+
+    def tune(self, cache_path: str | None = None) -> int:
+        ty = ct.c_int()
+        self._check(self.lib.lbm_batch_tune(self.h, cache_path.encode() if cache_path else None, ct.byref(ty)))
+        return ty.value
+
+    def step(self, n: int = 1) -> None:
+        self._check(self.lib.lbm_batch_step(self.h, int(n)))
+
+    def synchronize(self) -> None:
+        self._check(self.lib.lbm_batch_synchronize(self.h))
+
+    def fields(self, dom: int, names=FIELDS) -> dict:
+        nx, ny = int(self.params[dom]["nx"]), int(self.params[dom]["ny"])
+        mask = 0
+        for n in names:
+            mask |= 1 << FIELDS.index(n)
+        order = [n for n in FIELDS if mask & (1 << FIELDS.index(n))]
+        out = np.empty((len(order), ny, nx))
+        self._check(self.lib.lbm_batch_get_fields(self.h, dom, mask, _dptr(out)))
+        return {n: out[i] for i, n in enumerate(order)}
+
+    def metrics(self, dom: int, cx: float, cy: float, orient: float = 0.0) -> dict:
+        m = lbm_metrics()
+        self._check(self.lib.lbm_batch_get_metrics(self.h, dom, cx, cy, orient, ct.byref(m)))
+        return {"tip_px": m.tip[0], "tip_mx": m.tip[1], "tip_py": m.tip[2], "solid_fraction": m.solid_fraction,
+                "sum_C": m.sum_C, "sum_H": m.sum_H, "sum_h": m.sum_h, "max_u": m.max_u,
+                "nonfinite": m.nonfinite, "sum_phi": m.sum_phi, "step": m.step}
