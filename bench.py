@@ -245,9 +245,10 @@ def batch_leg(lbm, torch, stream, steps, world, max_over_ranks, barrier):
     b = lbm.Batch([c.params for c in cases], "fp16", stream=stream)
     for j, c in enumerate(cases):
         b.init_seeds(j, c.seeds, c.U0, c.theta0)
-    cache = os.path.join(os.path.expanduser("~"), ".cache", "lbm_gb300", "batch_tiles.txt")
+    cache = os.path.join(os.path.expanduser("~"), ".cache", "lbm_gb300", "batch_tiling.txt")
     os.makedirs(os.path.dirname(cache), exist_ok=True)
     ty = b.tune(cache)
+    tiles_per_cta = b.tiles_per_cta
     b.step(16)
     torch.cuda.synchronize()
     barrier()
@@ -281,7 +282,8 @@ def batch_leg(lbm, torch, stream, steps, world, max_over_ranks, barrier):
     seq_value = world * nodes * k2 / (seq_ms / 1e3) / 1e6
     del sims
     return {"workload": "256 domains, sides log-uniform 128..1024 (seed 4), inflow/outflow/symmetry walls",
-            "nodes": nodes, "storage": "fp16", "tile_height": ty, "steps": k, "value": value, "unit": UNIT,
+            "nodes": nodes, "storage": "fp16", "tile_height": ty, "tiles_per_cta": tiles_per_cta, "steps": k,
+            "value": value, "unit": UNIT,
             "ms_per_step": ms / k, "sequential_fp32_value": seq_value, "speedup_vs_sequential_fp32": value / seq_value,
             "nonfinite_domains_of_first_8": bad}
 

@@ -221,7 +221,10 @@ LBM_API int lbm_load_state(lbm_handle* h, const void* host, size_t bytes);
  * single-domain conventions above. */
 typedef struct lbm_batch lbm_batch;
 
-/* Create n domains from params[0..n-1] (validated as lbm_create does). */
+/* Create n domains (1 <= n <= 256) from params[0..n-1] (validated as
+ * lbm_create does).  Batches stepped concurrently on different streams of one
+ * device share the constant-memory copy of the domain table and must not
+ * overlap. */
 LBM_API int lbm_batch_create(const lbm_params* params, int n, lbm_batch** out);
 LBM_API void lbm_batch_destroy(lbm_batch* b);
 LBM_API int lbm_batch_set_stream(lbm_batch* b, void* stream);
@@ -233,17 +236,21 @@ LBM_API int lbm_batch_step(lbm_batch* b, int nsteps);
 LBM_API int lbm_batch_synchronize(lbm_batch* b);
 LBM_API int lbm_batch_get_fields(lbm_batch* b, int dom, unsigned mask, double* out);
 LBM_API int lbm_batch_get_metrics(lbm_batch* b, int dom, double cx, double cy, double orient, lbm_metrics* m);
-/* Total nodes of all domains; current tile height. */
+/* Total nodes of all domains; current tiling (tile height, tiles per CTA). */
 LBM_API long long lbm_batch_nodes(const lbm_batch* b);
 LBM_API int lbm_batch_tile_height(const lbm_batch* b);
-/* Force the tile height (4, 8 or 16) instead of tuning it. */
-LBM_API int lbm_batch_set_tile_height(lbm_batch* b, int tile_height);
-/* Autotuner: pick the fastest tile height for this batch on this GPU.  A
- * cache file (one "key height" line per GPU name, storage, size class and
- * domain count; NULL for none) is read first and appended to after a
- * measurement.  Measuring times 12 steps per height on a device copy of the
- * current state, which is restored afterwards (needs that much free memory);
- * the step counter does not move. */
+LBM_API int lbm_batch_tiles_per_cta(const lbm_batch* b);
+/* Force the tiling instead of tuning it: tile height 4, 8 or 16 rows of 32
+ * nodes; tiles per CTA >= 1, or 0 for a persistent grid of as many CTAs as fit
+ * on the GPU at once, each taking one contiguous run of tiles.  Default (8, 1). */
+LBM_API int lbm_batch_set_tiling(lbm_batch* b, int tile_height, int tiles_per_cta);
+/* Autotuner: pick the fastest tiling for this batch on this GPU among tile
+ * heights {4, 8, 16} x tiles per CTA {1, 4, persistent}.  A cache file (one
+ * "key height tiles_per_cta" line per GPU name, storage, size class and domain
+ * count; NULL for none) is read first and appended to after a measurement.
+ * Measuring times 12 steps per tiling on a device copy of the current state,
+ * which is restored afterwards (needs that much free memory); the step counter
+ * does not move. */
 LBM_API int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height);
 LBM_API const char* lbm_batch_last_error(const lbm_batch* b);
 

@@ -172,13 +172,6 @@ void derive(lbm_handle* h)
         h->ref[lbm::kG + i] = w5[i] * th + (i == 0 ? 0.5 : 0.0);
     }
     for (int i = 0; i < 9; ++i) h->ref[lbm::kH + i] = i == 0 ? (double)P.rho0 : 0.0;
-    // 16-bit scales keep the smallest deviations out of the subnormal range
-    for (int q = 0; q < lbm::kPlanes; ++q) {
-        float sc = 1.0f;
-        if (p.storage == LBM_FP16) sc = q >= lbm::kH ? 1024.0f : 16.0f;
-        P.scale[q] = sc;
-        P.inv_scale[q] = 1.0f / sc;
-    }
 }
 
 int ensure_initialised(lbm_handle* h)
@@ -753,6 +746,7 @@ struct lbm_batch {
     int storage = 0;
     int parity = 0;          // buffer index holding the newest populations of every domain
     int ty = 8;              // tile height of the batched kernel
+    int run = 1;             // tiles per CTA (0: persistent grid)
     int ctas[3] = {0, 0, 0}; // resident CTAs for tile heights 4, 8, 16
     cudaStream_t stream = nullptr;
     lbm::DomainDesc* d_descs = nullptr;
@@ -760,7 +754,7 @@ struct lbm_batch {
     int ntiles[3] = {0, 0, 0};
     int4* d_walls[2] = {nullptr, nullptr};
     int nwall[2] = {0, 0};
-    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (parity, ty)
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (parity, ty * 1000 + run)
     long long steps = 0, nodes = 0;
     std::string err;
 };
@@ -796,6 +790,7 @@ lbm::BatchTables tables(const lbm_batch* b)
 {
     lbm::BatchTables T;
     T.descs = b->d_descs;
+    T.ndomains = (int)b->dom.size();
     for (int k = 0; k < 3; ++k) {
         T.tiles[k] = b->d_tiles[k];
         T.ntiles[k] = b->ntiles[k];
@@ -830,7 +825,7 @@ int upload_descs(lbm_batch* b)
 
 int batch_graph(lbm_batch* b, cudaGraphExec_t* out)
 {
-    const auto key = std::make_pair(b->parity, b->ty);
+    const auto key = std::make_pair(b->parity, b->ty * 1000 + b->run);
     auto it = b->graphs.find(key);
     if (it != b->graphs.end()) {
         *out = it->second;
@@ -843,7 +838,7 @@ int batch_graph(lbm_batch* b, cudaGraphExec_t* out)
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     int par = b->parity;
     for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) {
-        e = lbm::launch_batch_step(T, b->storage, b->ty, par, b->ctas[tyk(b->ty)], cap);
+        e = lbm::launch_batch_step(T, b->storage, b->ty, b->run, par, b->ctas[tyk(b->ty)], cap);
         par = 1 - par;
     }
     cudaError_t e2 = cudaStreamEndCapture(cap, &g);
@@ -874,7 +869,7 @@ int batch_run_direct(lbm_batch* b, int n)
 {
     const lbm::BatchTables T = tables(b);
     for (int i = 0; i < n; ++i) {
-        LBM_BCUDA(b, lbm::launch_batch_step(T, b->storage, b->ty, b->parity, b->ctas[tyk(b->ty)], b->stream));
+        LBM_BCUDA(b, lbm::launch_batch_step(T, b->storage, b->ty, b->run, b->parity, b->ctas[tyk(b->ty)], b->stream));
         b->parity = 1 - b->parity;
     }
     return LBM_OK;
@@ -898,6 +893,7 @@ int lbm_batch_create(const lbm_params* params, int n, lbm_batch** out)
     if (!out) return bfail(nullptr, LBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (!params || n < 1) return bfail(nullptr, LBM_EINVAL, "need at least one domain");
+    if (n > lbm::kMaxBatchDomains) return bfail(nullptr, LBM_EINVAL, "at most 256 domains per batch");
     for (int i = 0; i < n; ++i) {
         if (params[i].storage != params[0].storage) return bfail(nullptr, LBM_EINVAL, "domains must share one storage");
         if (params[i].n_sub != 1) return bfail(nullptr, LBM_EINVAL, "batched domains need n_sub = 1");
@@ -1042,11 +1038,16 @@ long long lbm_batch_nodes(const lbm_batch* b) { return b ? b->nodes : -1; }
 
 int lbm_batch_tile_height(const lbm_batch* b) { return b ? b->ty : -1; }
 
-int lbm_batch_set_tile_height(lbm_batch* b, int tile_height)
+int lbm_batch_tiles_per_cta(const lbm_batch* b) { return b ? b->run : -1; }
+
+int lbm_batch_set_tiling(lbm_batch* b, int tile_height, int tiles_per_cta)
 {
     if (!b) return LBM_EINVAL;
-    if (tile_height != 4 && tile_height != 8 && tile_height != 16) return bfail(b, LBM_EINVAL, "tile height must be 4, 8 or 16");
+    if (tile_height != 4 && tile_height != 8 && tile_height != 16)
+        return bfail(b, LBM_EINVAL, "tile height must be 4, 8 or 16");
+    if (tiles_per_cta < 0) return bfail(b, LBM_EINVAL, "tiles per CTA must be >= 0");
     b->ty = tile_height;
+    b->run = tiles_per_cta;
     return LBM_OK;
 }
 
@@ -1072,10 +1073,11 @@ int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height)
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
             char k[256];
-            int v;
-            while (fscanf(f, "%255s %d", k, &v) == 2)
-                if (strcmp(k, key) == 0 && (v == 4 || v == 8 || v == 16)) {
+            int v, r;
+            while (fscanf(f, "%255s %d %d", k, &v, &r) == 3)
+                if (strcmp(k, key) == 0 && (v == 4 || v == 8 || v == 16) && r >= 0) {
                     b->ty = v;
+                    b->run = r;
                     fclose(f);
                     if (tile_height) *tile_height = v;
                     return LBM_OK;
@@ -1101,28 +1103,31 @@ int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height)
     }
     const int start_parity = b->parity;
     const int tys[3] = {4, 8, 16};
+    const int runs[3] = {1, 4, 0};
     float best_ms = 1e30f;
-    int best = b->ty;
+    int best = b->ty, best_run = b->run;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const lbm::BatchTables T = tables(b);
-    for (int k = 0; k < 3; ++k) {
-        int par = start_parity;
-        for (int i = 0; i < 2; ++i, par = 1 - par)
-            lbm::launch_batch_step(T, b->storage, tys[k], par, b->ctas[k], b->stream);
-        cudaEventRecord(e0, b->stream);
-        for (int i = 0; i < 10; ++i, par = 1 - par)
-            lbm::launch_batch_step(T, b->storage, tys[k], par, b->ctas[k], b->stream);
-        cudaEventRecord(e1, b->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = tys[k];
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r) {
+            int par = start_parity;
+            for (int i = 0; i < 2; ++i, par = 1 - par)
+                lbm::launch_batch_step(T, b->storage, tys[k], runs[r], par, b->ctas[k], b->stream);
+            cudaEventRecord(e0, b->stream);
+            for (int i = 0; i < 10; ++i, par = 1 - par)
+                lbm::launch_batch_step(T, b->storage, tys[k], runs[r], par, b->ctas[k], b->stream);
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = tys[k];
+                best_run = runs[r];
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (size_t i = 0; i < b->dom.size(); ++i) {
@@ -1140,10 +1145,11 @@ int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height)
     if (e != cudaSuccess) return bfail(b, LBM_ECUDA, std::string("tuning: ") + cudaGetErrorString(e));
     b->parity = start_parity;
     b->ty = best;
+    b->run = best_run;
     drop_batch_graphs(b);
     if (cache_path)
         if (FILE* f = fopen(cache_path, "a")) {
-            fprintf(f, "%s %d\n", key, best);
+            fprintf(f, "%s %d %d\n", key, best, best_run);
             fclose(f);
         }
     if (tile_height) *tile_height = best;

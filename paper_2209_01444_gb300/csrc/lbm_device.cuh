@@ -63,8 +63,6 @@ struct StepParams {
     int bc[4];
     float uin_x, uin_y;
     float dir_phi, dir_U, dir_theta;
-    // 16-bit codec scale per plane (FP32 storage ignores it)
-    float scale[kPlanes], inv_scale[kPlanes];
 };
 
 // ------------------------------------------------------------------ codecs
@@ -107,9 +105,13 @@ struct Conv<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
 };
 
-template <class H>
+// S_SC, S_FL: power-of-two scales of the scalar and flow deviations before
+// rounding (FP16 keeps the smallest deviations out of its subnormal range).
+template <class H, int S_SC, int S_FL>
 struct Store16 {
     using T = H;
+    static __device__ __forceinline__ float scale(int q) { return q >= kH ? (float)S_FL : (float)S_SC; }
+    static __device__ __forceinline__ float inv_scale(int q) { return q >= kH ? 1.0f / S_FL : 1.0f / S_SC; }
     static constexpr int kScalarBytes = 12 * 2 + 3 * 4;
     static constexpr int kFlowBytes = 9 * 2;
     static __device__ __forceinline__ bool rest(int q) { return q == kF || q == kN || q == kG; }
@@ -121,23 +123,23 @@ struct Store16 {
     static __device__ __forceinline__ float load(const void* sc, const void* fl, int q, long long o,
                                                  const StepParams& P)
     {
-        if (q >= kH) return Conv<H>::to(((const H*)fl)[(q - kH) * P.plane + o]) * P.inv_scale[q];
+        if (q >= kH) return Conv<H>::to(((const H*)fl)[(q - kH) * P.plane + o]) * inv_scale(q);
         if (rest(q)) return rest_base(sc, P)[(q / 5) * P.plane + o];
-        return Conv<H>::to(((const H*)sc)[slot(q) * P.plane + o]) * P.inv_scale[q];
+        return Conv<H>::to(((const H*)sc)[slot(q) * P.plane + o]) * inv_scale(q);
     }
     static __device__ __forceinline__ void store(void* sc, void* fl, int q, long long o, float v,
                                                  const StepParams& P)
     {
         if (q >= kH)
-            ((H*)fl)[(q - kH) * P.plane + o] = Conv<H>::from(v * P.scale[q]);
+            ((H*)fl)[(q - kH) * P.plane + o] = Conv<H>::from(v * scale(q));
         else if (rest(q))
             ((float*)rest_base(sc, P))[(q / 5) * P.plane + o] = v;
         else
-            ((H*)sc)[slot(q) * P.plane + o] = Conv<H>::from(v * P.scale[q]);
+            ((H*)sc)[slot(q) * P.plane + o] = Conv<H>::from(v * scale(q));
     }
 };
-using StoreF16 = Store16<__half>;
-using StoreBF16 = Store16<__nv_bfloat16>;
+using StoreF16 = Store16<__half, 16, 1024>;
+using StoreBF16 = Store16<__nv_bfloat16, 1, 1>;
 
 __device__ __forceinline__ int wrap(int v, int n)
 {

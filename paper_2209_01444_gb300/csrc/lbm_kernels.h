@@ -45,8 +45,13 @@ struct DomainDesc {
 // Device tables of a batch: tiles {domain, x0, y0, 0} for tile heights 4, 8,
 // 16 (index 0, 1, 2), wall nodes {domain, axis, side, index} for the y walls
 // (0) and the x walls (1).
+// Domains per batch: the batched kernel reads its descriptors from constant
+// memory (64 KiB).
+constexpr int kMaxBatchDomains = 256;
+
 struct BatchTables {
-    const DomainDesc* descs;
+    const DomainDesc* descs;  // device copy, loaded into constant memory before each step
+    int ndomains;
     const int4* tiles[3];
     int ntiles[3];
     const int4* walls[2];
@@ -54,7 +59,10 @@ struct BatchTables {
 };
 
 // One coupled step of every domain: buffers `parity` -> 1 - parity, then walls.
-cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int parity, int ctas, cudaStream_t s);
+// ty: tile height 4, 8 or 16; run: tiles per CTA (0: persistent grid of
+// `ctas` CTAs, each taking one contiguous run).
+cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int run, int parity, int ctas,
+                              cudaStream_t s);
 // CTAs of the persistent batched kernel that fit on the current device at once.
 int batch_resident_ctas(int storage, int ty);
 

@@ -34,6 +34,10 @@ __device__ __forceinline__ int mirror_or_wrap_local(int g, int n, int periodic, 
     return local + d;
 }
 
+#ifndef LBM_BATCH_WARPS
+#define LBM_BATCH_WARPS 32  // resident warps per SM the batched kernel's register budget is sized for
+#endif
+
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for (64 registers)
 #endif
@@ -204,36 +208,27 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
                                              blockIdx.y * TY, fs, ps);
 }
 
+// Descriptors of the batch being stepped, in constant memory: the domain
+// index is uniform across a CTA, so parameter reads are broadcast from the
+// constant cache as in the single-domain kernel.  launch_batch_step copies the
+// batch's table in before each step.
+__constant__ DomainDesc c_batch_desc[kMaxBatchDomains];
+
 // Batched coupled step: one persistent grid sweeps the tile table of every
-// domain, reloading the domain's parameters into shared memory when the
-// domain changes.  A kernel boundary separates steps.
+// domain; each CTA takes a contiguous run of tiles, so consecutive tiles share
+// the domain and their halos stay in L2.  A kernel boundary separates steps.
 template <class Store, int TYV>
-__global__ void __launch_bounds__(TX* TYV, 32 / TYV)
-    k_batch_step(const DomainDesc* __restrict__ descs, const int4* __restrict__ tiles, int ntiles, int chunk,
-                 int parity)
+__global__ void __launch_bounds__(TX* TYV, (LBM_BATCH_WARPS / TYV > 0 ? LBM_BATCH_WARPS / TYV : 1))
+    k_batch_step(const int4* __restrict__ tiles, int ntiles, int chunk, int parity)
 {
     __shared__ float fs[5][TYV + 2][TX + 2];
     __shared__ float ps[TYV + 2][TX + 2];
-    __shared__ DomainDesc sd;
-    __shared__ int s_dom;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid == 0) s_dom = -1;
-    __syncthreads();
-    // each CTA takes a contiguous run of tiles: consecutive tiles share the
-    // domain and their halos stay in L2
     const int t_end = min(ntiles, (blockIdx.x + 1) * chunk);
     for (int t = blockIdx.x * chunk; t < t_end; ++t) {
         const int4 tl = tiles[t];
-        if (tl.x != s_dom) {
-            __syncthreads();  // every thread has read s_dom
-            const int* srcw = (const int*)(descs + tl.x);
-            int* dstw = (int*)&sd;
-            for (int w = tid; w < (int)(sizeof(DomainDesc) / sizeof(int)); w += TX * TYV) dstw[w] = srcw[w];
-            if (tid == 0) s_dom = tl.x;
-            __syncthreads();
-        }
-        coupled_tile<Store, true, false, TYV>(sd.P, sd.sc[parity], sd.fl[parity], sd.sc[1 - parity],
-                                              sd.fl[1 - parity], sd.hist, sd.grain, nullptr, tl.y, tl.z, fs, ps);
+        const DomainDesc& d = c_batch_desc[tl.x];
+        coupled_tile<Store, true, false, TYV>(d.P, d.sc[parity], d.fl[parity], d.sc[1 - parity],
+                                              d.fl[1 - parity], d.hist, d.grain, nullptr, tl.y, tl.z, fs, ps);
         __syncthreads();  // the tile arrays are reused by the next tile
     }
 }
@@ -428,13 +423,15 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
     return cudaSuccess;
 }
 
+// run: tiles per CTA; 0 makes the grid persistent (one contiguous run of
+// tiles per resident CTA).
 template <class Store, int TYV>
-cudaError_t batch_step_t(const BatchTables& T, int parity, int ctas, cudaStream_t s)
+cudaError_t batch_step_t(const BatchTables& T, int parity, int ctas, int run, cudaStream_t s)
 {
     const int k = TYV == 4 ? 0 : TYV == 8 ? 1 : 2;
-    const int chunk = (T.ntiles[k] + ctas - 1) / ctas;
+    const int chunk = run > 0 ? run : (T.ntiles[k] + ctas - 1) / ctas;
     const int grid = (T.ntiles[k] + chunk - 1) / chunk;
-    k_batch_step<Store, TYV><<<grid, dim3(TX, TYV), 0, s>>>(T.descs, T.tiles[k], T.ntiles[k], chunk, parity);
+    k_batch_step<Store, TYV><<<grid, dim3(TX, TYV), 0, s>>>(T.tiles[k], T.ntiles[k], chunk, parity);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the fused kernel wrote buffers 1 - parity; walls act on those
@@ -446,12 +443,15 @@ cudaError_t batch_step_t(const BatchTables& T, int parity, int ctas, cudaStream_
 }
 
 template <class Store>
-cudaError_t batch_step_store(const BatchTables& T, int ty, int parity, int ctas, cudaStream_t s)
+cudaError_t batch_step_store(const BatchTables& T, int ty, int parity, int ctas, int run, cudaStream_t s)
 {
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_batch_desc, T.descs, sizeof(DomainDesc) * T.ndomains, 0,
+                                            cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
     switch (ty) {
-    case 4: return batch_step_t<Store, 4>(T, parity, ctas, s);
-    case 16: return batch_step_t<Store, 16>(T, parity, ctas, s);
-    default: return batch_step_t<Store, 8>(T, parity, ctas, s);
+    case 4: return batch_step_t<Store, 4>(T, parity, ctas, run, s);
+    case 16: return batch_step_t<Store, 16>(T, parity, ctas, run, s);
+    default: return batch_step_t<Store, 8>(T, parity, ctas, run, s);
     }
 }
 
@@ -467,12 +467,13 @@ int batch_ctas_t()
 
 }  // namespace
 
-cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int parity, int ctas, cudaStream_t s)
+cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int run, int parity, int ctas,
+                              cudaStream_t s)
 {
     switch (storage) {
-    case kStoreF16: return batch_step_store<StoreF16>(T, ty, parity, ctas, s);
-    case kStoreBF16: return batch_step_store<StoreBF16>(T, ty, parity, ctas, s);
-    default: return batch_step_store<StoreF32>(T, ty, parity, ctas, s);
+    case kStoreF16: return batch_step_store<StoreF16>(T, ty, parity, ctas, run, s);
+    case kStoreBF16: return batch_step_store<StoreBF16>(T, ty, parity, ctas, run, s);
+    default: return batch_step_store<StoreF32>(T, ty, parity, ctas, run, s);
     }
 }
 

@@ -84,7 +84,8 @@ SIGNATURES = {
                                          ct.POINTER(lbm_metrics)]),
     "lbm_batch_nodes": (ct.c_longlong, [_H]),
     "lbm_batch_tile_height": (ct.c_int, [_H]),
-    "lbm_batch_set_tile_height": (ct.c_int, [_H, ct.c_int]),
+    "lbm_batch_tiles_per_cta": (ct.c_int, [_H]),
+    "lbm_batch_set_tiling": (ct.c_int, [_H, ct.c_int, ct.c_int]),
     "lbm_batch_tune": (ct.c_int, [_H, ct.c_char_p, ct.POINTER(ct.c_int)]),
     "lbm_batch_last_error": (ct.c_char_p, [_H]),
     "lbm_set_profiling": (ct.c_int, [_H, ct.c_int]),
@@ -282,9 +283,12 @@ class Batch:
     def tile_height(self) -> int:
         return int(self.lib.lbm_batch_tile_height(self.h))
 
-    @tile_height.setter
-    def tile_height(self, ty: int) -> None:
-        self._check(self.lib.lbm_batch_set_tile_height(self.h, int(ty)))
+    @property
+    def tiles_per_cta(self) -> int:
+        return int(self.lib.lbm_batch_tiles_per_cta(self.h))
+
+    def set_tiling(self, tile_height: int, tiles_per_cta: int = 1) -> None:
+        self._check(self.lib.lbm_batch_set_tiling(self.h, int(tile_height), int(tiles_per_cta)))
 
     def init_seeds(self, dom: int, seeds, U0: float, theta0: float) -> None:
         a = np.asarray(seeds, np.float64).reshape(-1, 4)

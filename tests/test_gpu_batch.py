@@ -43,11 +43,11 @@ def small_cases():
     return cases
 
 
-@pytest.mark.parametrize("ty", [4, 8, 16])
-def test_batch_matches_single_domain_runs(lbm, ty):
+@pytest.mark.parametrize("ty,run", [(4, 1), (8, 1), (16, 1), (8, 4), (4, 0), (16, 0)])
+def test_batch_matches_single_domain_runs(lbm, ty, run):
     cases = small_cases()
     b = lbm.Batch([c.params for c in cases])
-    b.tile_height = ty
+    b.set_tiling(ty, run)
     singles = []
     for j, c in enumerate(cases):
         b.init_seeds(j, c.seeds, c.U0, c.theta0)
@@ -95,7 +95,7 @@ def test_tuning_picks_a_height_and_leaves_the_state(lbm, tmp_path):
     for x, y in zip(before, after):
         for k in x:
             np.testing.assert_array_equal(x[k], y[k])
-    assert open(cache).read().split()[-1] == str(ty)
+    assert open(cache).read().split()[-2:] == [str(ty), str(b.tiles_per_cta)]
     b2 = lbm.Batch([c.params for c in cases])
     for j, c in enumerate(cases):
         b2.init_seeds(j, c.seeds, c.U0, c.theta0)
