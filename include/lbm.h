@@ -254,6 +254,24 @@ LBM_API int lbm_batch_set_tiling(lbm_batch* b, int tile_height, int tiles_per_ct
 LBM_API int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height);
 LBM_API const char* lbm_batch_last_error(const lbm_batch* b);
 
+/* ------------------------------------------------------- surrogate network */
+/* Building blocks of the learned surrogate (a convolutional network that
+ * advances the fields K steps at a time; the paper has no counterpart).  All
+ * tensors are device memory owned by the caller; work is queued on `stream`.
+ *
+ * Tensor-core GEMM: D[M][N] = act(A[M][K] B[N][K]^T + bias[N]) with A and B
+ * BF16, row-major with K contiguous and row pitches lda, ldb (multiples of 8
+ * elements, >= K, 16-byte aligned bases); FP32 accumulation; D BF16
+ * (out_fp32 = 0) or FP32 with pitch ldd; bias FP32[N] or NULL; relu != 0
+ * clamps at zero.  N must be 32, 64, 128 or a multiple of 256.  Runs on
+ * tcgen05 (sm_103a).  LBM_EINVAL for unsupported shapes or alignment. */
+LBM_API int lbm_nn_gemm(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,
+                        int N, int K, int out_fp32, int relu, void* stream);
+
+/* LBM_ETIMEOUT if a network kernel gave up a bounded wait since the flag was
+ * last cleared (clear != 0 clears it), else LBM_OK.  Synchronous. */
+LBM_API int lbm_nn_error(int clear);
+
 /* ------------------------------------------------ allocation-free reduction */
 /* The reductions of lbm_get_metrics, computed straight from population
  * buffers the caller owns, without allocating anything.  The paper has no

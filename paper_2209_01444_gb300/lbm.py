@@ -88,6 +88,9 @@ SIGNATURES = {
     "lbm_batch_set_tiling": (ct.c_int, [_H, ct.c_int, ct.c_int]),
     "lbm_batch_tune": (ct.c_int, [_H, ct.c_char_p, ct.POINTER(ct.c_int)]),
     "lbm_batch_last_error": (ct.c_char_p, [_H]),
+    "lbm_nn_gemm": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
+                               ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]),
+    "lbm_nn_error": (ct.c_int, [ct.c_int]),
     "lbm_set_profiling": (ct.c_int, [_H, ct.c_int]),
     "lbm_kernel_time": (ct.c_int, [_H, _DP, ct.POINTER(ct.c_longlong)]),
     "lbm_last_error": (ct.c_char_p, [_H]),
