@@ -199,3 +199,28 @@ def noise(shape, rng_seed: int, amp: float) -> np.ndarray:
     """Uniform noise in [-amp, amp] of the given shape."""
     rng = np.random.Generator(np.random.PCG64(rng_seed))
     return rng.uniform(-amp, amp, shape)
+
+
+# -------------------------------------------------------------- network weights
+def bf16_exact(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even), returned as FP64, so
+    that FP64 and BF16 consumers of the same weights see the same numbers."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def unet_params(shapes, rng_seed: int, out_scale: float = 0.01) -> dict:
+    """He-normal weights (standard deviation sqrt(2 / fan_in)), small random
+    biases, a small output projection; every value BF16-exact.  `shapes` is
+    the ordered (name, shape) list of the network definition."""
+    rng = np.random.Generator(np.random.PCG64(rng_seed))
+    out = {}
+    for name, shape in shapes:
+        if name.endswith(".W"):
+            fan_in = shape[1]
+            std = math.sqrt(2.0 / fan_in) * (out_scale if name.startswith("out") else 1.0)
+            out[name] = bf16_exact(rng.normal(0.0, std, shape))
+        else:
+            out[name] = bf16_exact(rng.normal(0.0, 0.01, shape))
+    return out
