@@ -263,10 +263,125 @@ LBM_API const char* lbm_batch_last_error(const lbm_batch* b);
  * BF16, row-major with K contiguous and row pitches lda, ldb (multiples of 8
  * elements, >= K, 16-byte aligned bases); FP32 accumulation; D BF16
  * (out_fp32 = 0) or FP32 with pitch ldd; bias FP32[N] or NULL; relu != 0
- * clamps at zero.  N must be 32, 64, 128 or a multiple of 256.  Runs on
+ * clamps at zero.  N must be a multiple of 8.  Runs on
  * tcgen05 (sm_103a).  LBM_EINVAL for unsupported shapes or alignment. */
 LBM_API int lbm_nn_gemm(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,
                         int N, int K, int out_fp32, int relu, void* stream);
+
+/* lbm_nn_gemm with K split into `splits` slices computed by separate CTAs
+ * (for long reductions such as weight gradients over every pixel); their FP32
+ * partial tiles go to `workspace` (splits * M * N floats) and a reduction adds
+ * them, the bias and the activation. */
+LBM_API int lbm_nn_gemm_split(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias,
+                              int M, int N, int K, int out_fp32, int relu, int splits, float* workspace,
+                              void* stream);
+
+/* Layers around the GEMM.  Activations are NHWC: [B][H][W][channels] with a
+ * channel pitch (the row length of one pixel), BF16 unless named FP32.
+ * im2col3x3: A[(b,y,x)][(ky,kx,c)] = X[b, y+ky-1, x+kx-1, c], zero outside
+ *   the image (C and cpitch multiples of 8; A has 9C columns).
+ * col2im3x3: FP32 dX[b,y,x,c] = sum over taps of dA[(b,y-ky+1,x-kx+1)][(ky,kx,c)].
+ * relu_bwd: g[r][c] = 0 where y[r][c] <= 0 (g FP32 or BF16).
+ * transpose: out[c][r] = in[r][c] (BF16).
+ * maxpool_fwd / _bwd: 2 x 2 max pooling; the backward adds the FP32 gradient
+ *   to the first maximum of each window.
+ * shuffle_fwd / _bwd: the 2 x 2 stride-2 up-convolution's GEMM output
+ *   U[(b,y,x)][(dy,dx,c)] <-> Y[b, 2y+dy, 2x+dx, c0+c].
+ * proj_fwd: FP32 Y[p][o] = R[p][o] + b[o] + sum_c X[p][c] Wt[o][c] (O <= 8
+ *   outputs, R the residual or NULL); proj_bwd: FP32 dX (skipped when NULL),
+ *   dW (O x C) and db (O) from per-block partials `part` (part_blocks * O *
+ *   (C + 1) floats).
+ * flip3x3: weights of the gradient-to-input convolution, Wf[ci][t*cout+co] =
+ *   W[co][(8-t)*cin+ci] (BF16; W is [cout][9*cin]).
+ * colsum: out[c] = sum_r g[r][c] through `part` (part_blocks * C floats).
+ * mse: loss[0] = sum (pred - target)^2, grad = 2 (pred - target)/n; `part`
+ *   holds n/256 + 1 floats.
+ * adam: one Adam step (bias-corrected, step t >= 1) on FP32 weights; writes
+ *   their BF16 copy when w_bf16 is not NULL.
+ * pack: FP32 fields [P][F] -> BF16 [P][cpitch], (x - mean)/std, zero padded;
+ *   R (FP32 [P][F], or NULL) receives the normalised fields unrounded.
+ * unpack: FP32 fields [P][F] = mean + std * Y.
+ * cast_bf16: FP32 [rows][C] (pitch apitch) -> BF16 (pitch bpitch). */
+LBM_API int lbm_nn_im2col3x3(const void* X, int B, int H, int W, int C, int cpitch, void* A, void* stream);
+LBM_API int lbm_nn_col2im3x3(const float* dA, int B, int H, int W, int C, float* dX, int cpitch, void* stream);
+LBM_API int lbm_nn_relu_bwd(void* g, int g_fp32, int gpitch, const void* y, int ypitch, long long rows, int C,
+                            void* stream);
+LBM_API int lbm_nn_transpose(const void* in, int rows, int cols, int ipitch, void* out, int opitch, void* stream);
+LBM_API int lbm_nn_maxpool_fwd(const void* X, int B, int H, int W, int C, int xpitch, void* Y, void* stream);
+LBM_API int lbm_nn_maxpool_bwd(const void* X, int B, int H, int W, int C, int xpitch, const float* dY, float* dX,
+                               int dpitch, void* stream);
+LBM_API int lbm_nn_shuffle_fwd(const void* U, int B, int H, int W, int C, void* Y, int ypitch, int c0, void* stream);
+LBM_API int lbm_nn_shuffle_bwd(const void* dY, int dy_fp32, int ypitch, int c0, int B, int H, int W, int C, void* dU,
+                               void* stream);
+LBM_API int lbm_nn_proj_fwd(const void* X, int P, int C, int xpitch, const float* Wt, const float* bias, int O,
+                            const float* R, float* Y, void* stream);
+LBM_API int lbm_nn_proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, const float* Wt, int O,
+                            float* dX, int dpitch, float* dW, float* db, float* part, int part_blocks,
+                            void* stream);
+LBM_API int lbm_nn_flip3x3(const void* W, int cout, int cin, void* Wf, void* stream);
+LBM_API int lbm_nn_colsum(const void* g, int g_fp32, long long rows, int C, int pitch, float* out, float* part,
+                          int part_blocks, void* stream);
+LBM_API int lbm_nn_mse(const float* pred, const float* target, long long n, float* grad, float* loss, float* part,
+                       void* stream);
+LBM_API int lbm_nn_adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                        float eps, int t, void* w_bf16, void* stream);
+LBM_API int lbm_nn_pack(const float* fields, long long P, int F, const float* mean, const float* inv_std, void* X,
+                        int cpitch, float* R, void* stream);
+LBM_API int lbm_nn_unpack(const float* Y, long long P, int F, const float* mean, const float* inv_std, float* fields,
+                          void* stream);
+LBM_API int lbm_nn_cast_bf16(const float* a, long long rows, int C, int apitch, void* b, int bpitch, void* stream);
+
+/* The surrogate network as one object (the paper has no counterpart): a
+ * convolutional U-Net with `levels` levels of widths base * 2^l (3 x 3
+ * convolutions, two per level and side, ReLU, 2 x 2 max pooling, 2 x 2
+ * stride-2 up-convolutions, skip concatenation) and a 1 x 1 output projection
+ * added to the input fields (residual), run on tensor cores in BF16 with FP32
+ * accumulation.  It is sized at creation for `batch` images of
+ * height x width pixels with `fields` <= 8 fields per pixel; height and width
+ * must be multiples of 2^(levels-1) and batch*height*width/4^(levels-1) a
+ * multiple of 8.  The object owns every device buffer it uses.
+ *
+ * Parameters are one FP32 vector (lbm_unet_param_count values): the tensors
+ * in the order enc{l}a.W, enc{l}a.b, enc{l}b.W, enc{l}b.b for l = 0 ..
+ * levels-1, then up{l}.W, up{l}.b, dec{l}a.W, dec{l}a.b, dec{l}b.W, dec{l}b.b
+ * for l = levels-2 .. 0, then out.W, out.b, each row-major: conv weight
+ * [cout][9*cin] with column (ky*3+kx)*cin+ci (enc0a has cin = 8, the padded
+ * field count), bias [cout]; up-convolution weight [4c][2c] with row
+ * (dy*2+dx)*c+co and bias [4c]; out.W [fields][base], out.b [fields].
+ *
+ * Fields x, targets and predictions are FP32 device arrays [batch][height]
+ * [width][fields].  The network works in normalised units (x - mean)/std
+ * (lbm_unet_set_norm; default mean 0, std 1); the loss is the mean squared
+ * error in normalised units.  All calls queue work on the object's stream and
+ * return without waiting, except set_params, get_params, get_grads, set_norm
+ * and loss, which synchronise.  Errors: LBM_EINVAL for bad arguments,
+ * LBM_ENOMEM / LBM_ECUDA from CUDA; lbm_unet_last_error gives the reason. */
+typedef struct lbm_unet lbm_unet;
+LBM_API int lbm_unet_create(int levels, int base, int fields, int batch, int height, int width, lbm_unet** out);
+LBM_API void lbm_unet_destroy(lbm_unet* u);
+LBM_API int lbm_unet_set_stream(lbm_unet* u, void* stream);
+LBM_API long long lbm_unet_param_count(const lbm_unet* u);
+LBM_API long long lbm_unet_device_bytes(const lbm_unet* u);
+/* Loads parameters (host, FP32) and resets the Adam moments and step. */
+LBM_API int lbm_unet_set_params(lbm_unet* u, const float* host);
+LBM_API int lbm_unet_get_params(lbm_unet* u, float* host);
+/* Gradients of the loss from the last lbm_unet_backward / train_step. */
+LBM_API int lbm_unet_get_grads(lbm_unet* u, float* host);
+LBM_API int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_);
+/* Prediction y (physical units, may be NULL) for the fields x. */
+LBM_API int lbm_unet_forward(lbm_unet* u, const float* x, float* y);
+/* Forward, loss against `target` and the gradients of every parameter. */
+LBM_API int lbm_unet_backward(lbm_unet* u, const float* x, const float* target);
+/* One Adam step (bias-corrected) on the current gradients; refreshes the BF16
+ * weights the kernels read. */
+LBM_API int lbm_unet_adam(lbm_unet* u, float lr, float beta1, float beta2, float eps);
+/* backward + adam(lr, 0.9, 0.999, 1e-8). */
+LBM_API int lbm_unet_train_step(lbm_unet* u, const float* x, const float* target, float lr);
+/* Mean squared error of the last backward (normalised units). */
+LBM_API int lbm_unet_loss(lbm_unet* u, double* out);
+/* Copies the last prediction in normalised units (FP32 device array). */
+LBM_API int lbm_unet_output(lbm_unet* u, float* y_norm);
+LBM_API const char* lbm_unet_last_error(const lbm_unet* u);
 
 /* LBM_ETIMEOUT if a network kernel gave up a bounded wait since the flag was
  * last cleared (clear != 0 clears it), else LBM_OK.  Synchronous. */

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm.so")
-SOURCES = ["lbm_step.cu", "lbm_aux.cu", "lbm_api.cu", "lbm_noalloc.cu", "nn_gemm.cu", "nn_api.cu"]
+SOURCES = ["lbm_step.cu", "lbm_aux.cu", "lbm_api.cu", "lbm_noalloc.cu", "nn_gemm.cu", "nn_layers.cu", "nn_api.cu", "nn_unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

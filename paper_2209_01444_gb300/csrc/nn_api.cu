@@ -4,6 +4,7 @@
 #include "lbm.h"
 #include "lbm_kernels.h"
 #include "nn_kernels.h"
+#include "nn_layers.h"
 
 namespace {
 
@@ -21,11 +22,114 @@ extern "C" {
 int lbm_nn_gemm(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M, int N,
                 int K, int out_fp32, int relu, void* stream)
 {
+    return lbm_nn_gemm_split(A, lda, B, ldb, D, ldd, bias, M, N, K, out_fp32, relu, 1, nullptr, stream);
+}
+
+int lbm_nn_gemm_split(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,
+                      int N, int K, int out_fp32, int relu, int splits, float* workspace, void* stream)
+{
     if (!A || !B || !D) {
         lbm::set_last_error("lbm_nn_gemm: NULL operand");
         return LBM_EINVAL;
     }
-    return nn_status(nn::gemm_bf16(A, lda, B, ldb, D, ldd, bias, M, N, K, !out_fp32, relu != 0, (cudaStream_t)stream));
+    return nn_status(nn::gemm_bf16(A, lda, B, ldb, D, ldd, bias, M, N, K, !out_fp32, relu != 0, (cudaStream_t)stream,
+                                   splits, workspace));
+}
+
+#define NN_S(stream) ((cudaStream_t)(stream))
+
+int lbm_nn_im2col3x3(const void* X, int B, int H, int W, int C, int cpitch, void* A, void* stream)
+{
+    return nn_status(nn::im2col3x3(X, B, H, W, C, cpitch, A, NN_S(stream)));
+}
+
+int lbm_nn_col2im3x3(const float* dA, int B, int H, int W, int C, float* dX, int cpitch, void* stream)
+{
+    return nn_status(nn::col2im3x3(dA, B, H, W, C, dX, cpitch, NN_S(stream)));
+}
+
+int lbm_nn_relu_bwd(void* g, int g_fp32, int gpitch, const void* y, int ypitch, long long rows, int C, void* stream)
+{
+    return nn_status(nn::relu_bwd(g, g_fp32 != 0, gpitch, y, ypitch, rows, C, NN_S(stream)));
+}
+
+int lbm_nn_transpose(const void* in, int rows, int cols, int ipitch, void* out, int opitch, void* stream)
+{
+    return nn_status(nn::transpose(in, rows, cols, ipitch, out, opitch, NN_S(stream)));
+}
+
+int lbm_nn_maxpool_fwd(const void* X, int B, int H, int W, int C, int xpitch, void* Y, void* stream)
+{
+    return nn_status(nn::maxpool_fwd(X, B, H, W, C, xpitch, Y, NN_S(stream)));
+}
+
+int lbm_nn_maxpool_bwd(const void* X, int B, int H, int W, int C, int xpitch, const float* dY, float* dX, int dpitch,
+                       void* stream)
+{
+    return nn_status(nn::maxpool_bwd(X, B, H, W, C, xpitch, dY, dX, dpitch, NN_S(stream)));
+}
+
+int lbm_nn_shuffle_fwd(const void* U, int B, int H, int W, int C, void* Y, int ypitch, int c0, void* stream)
+{
+    return nn_status(nn::shuffle_fwd(U, B, H, W, C, Y, ypitch, c0, NN_S(stream)));
+}
+
+int lbm_nn_shuffle_bwd(const void* dY, int dy_fp32, int ypitch, int c0, int B, int H, int W, int C, void* dU,
+                       void* stream)
+{
+    return nn_status(nn::shuffle_bwd(dY, dy_fp32 != 0, ypitch, c0, B, H, W, C, dU, NN_S(stream)));
+}
+
+int lbm_nn_proj_fwd(const void* X, int P, int C, int xpitch, const float* Wt, const float* bias, int O, const float* R,
+                    float* Y, void* stream)
+{
+    return nn_status(nn::proj_fwd(X, P, C, xpitch, Wt, bias, O, R, Y, NN_S(stream)));
+}
+
+int lbm_nn_proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, const float* Wt, int O, float* dX,
+                    int dpitch, float* dW, float* db, float* part, int part_blocks, void* stream)
+{
+    return nn_status(nn::proj_bwd(dY, X, P, C, xpitch, Wt, O, dX, dpitch, dW, db, part, part_blocks, NN_S(stream)));
+}
+
+int lbm_nn_flip3x3(const void* W, int cout, int cin, void* Wf, void* stream)
+{
+    return nn_status(nn::flip3x3(W, cout, cin, Wf, NN_S(stream)));
+}
+
+int lbm_nn_colsum(const void* g, int g_fp32, long long rows, int C, int pitch, float* out, float* part,
+                  int part_blocks, void* stream)
+{
+    return nn_status(nn::colsum(g, g_fp32 != 0, rows, C, pitch, out, part, part_blocks, NN_S(stream)));
+}
+
+int lbm_nn_mse(const float* pred, const float* target, long long n, float* grad, float* loss, float* part,
+               void* stream)
+{
+    return nn_status(nn::mse(pred, target, n, grad, loss, part, NN_S(stream)));
+}
+
+int lbm_nn_adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
+                int t, void* w_bf16, void* stream)
+{
+    return nn_status(nn::adam(w, g, m, v, n, lr, b1, b2, eps, t, w_bf16, NN_S(stream)));
+}
+
+int lbm_nn_pack(const float* fields, long long P, int F, const float* mean, const float* inv_std, void* X, int cpitch,
+                float* R, void* stream)
+{
+    return nn_status(nn::pack(fields, P, F, mean, inv_std, X, cpitch, R, NN_S(stream)));
+}
+
+int lbm_nn_unpack(const float* Y, long long P, int F, const float* mean, const float* inv_std, float* fields,
+                  void* stream)
+{
+    return nn_status(nn::unpack(Y, P, F, mean, inv_std, fields, NN_S(stream)));
+}
+
+int lbm_nn_cast_bf16(const float* a, long long rows, int C, int apitch, void* b, int bpitch, void* stream)
+{
+    return nn_status(nn::cast_bf16(a, rows, C, apitch, b, bpitch, NN_S(stream)));
 }
 
 int lbm_nn_error(int clear)

@@ -118,10 +118,13 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar)
                  : "memory");
 }
 
+// blockIdx.z selects a slice of kb_per_split K blocks; with more than one
+// slice each writes its FP32 partial tile to D + z * M * ldd (no bias or
+// activation) and a reduction kernel finishes.
 template <int BN, bool OUT_BF16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, void* __restrict__ D,
-           const float* __restrict__ bias, int M, int N, int K, int ldd, int relu)
+           const float* __restrict__ bias, int M, int N, int K, int ldd, int relu, int kb_per_split)
 {
     constexpr int A_BYTES = kBM * kBK * 2;
     constexpr int B_BYTES = BN * kBK * 2;
@@ -138,7 +141,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-    const int nk = (K + kBK - 1) / kBK;
+    const int kb0 = blockIdx.z * kb_per_split;
+    const int nk = min((K + kBK - 1) / kBK - kb0, kb_per_split);  // K blocks of this slice
+    if (gridDim.z > 1) {
+        D = (float*)D + (size_t)blockIdx.z * M * ldd;
+        bias = nullptr;
+        relu = 0;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -166,8 +175,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int kb = 0; kb < nk && kb < kStages - 1; ++kb) {
             mbar_expect_tx(&full[kb], STAGE);
-            tma_load_2d(smem + kb * STAGE, &tmA, kb * kBK, m0, &full[kb]);
-            tma_load_2d(smem + kb * STAGE + A_BYTES, &tmB, kb * kBK, n0, &full[kb]);
+            tma_load_2d(smem + kb * STAGE, &tmA, (kb0 + kb) * kBK, m0, &full[kb]);
+            tma_load_2d(smem + kb * STAGE + A_BYTES, &tmB, (kb0 + kb) * kBK, n0, &full[kb]);
             ++issued;
         }
         for (int kb = 0; kb < nk && ok; ++kb) {
@@ -177,8 +186,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (pf >= kStages) ok = mbar_wait(&empty[ps], (uint32_t)((pf / kStages - 1) & 1));
                 if (!ok) break;
                 mbar_expect_tx(&full[ps], STAGE);
-                tma_load_2d(smem + ps * STAGE, &tmA, pf * kBK, m0, &full[ps]);
-                tma_load_2d(smem + ps * STAGE + A_BYTES, &tmB, pf * kBK, n0, &full[ps]);
+                tma_load_2d(smem + ps * STAGE, &tmA, (kb0 + pf) * kBK, m0, &full[ps]);
+                tma_load_2d(smem + ps * STAGE + A_BYTES, &tmB, (kb0 + pf) * kBK, n0, &full[ps]);
                 ++issued;
             }
             const int s = kb % kStages;
@@ -223,10 +232,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    float x = __uint_as_float(r[j]) + (bias ? bias[col + j] : 0.0f);
+                    float x = __uint_as_float(r[j]) + ((bias && col + j < N) ? bias[col + j] : 0.0f);
                     v[j] = relu ? fmaxf(x, 0.0f) : x;
                 }
-                if (OUT_BF16) {
+                if (col + 16 > N) {  // ragged last tile: element stores
+                    for (int j = 0; col + j < N; ++j) {
+                        if (OUT_BF16)
+                            ((__nv_bfloat16*)D)[(size_t)row * ldd + col + j] = __float2bfloat16_rn(v[j]);
+                        else
+                            ((float*)D)[(size_t)row * ldd + col + j] = v[j];
+                    }
+                } else if (OUT_BF16) {
                     __nv_bfloat162 h[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
@@ -279,7 +295,7 @@ cudaError_t make_map(CUtensorMap* tm, const void* ptr, int rows, int cols, int l
 
 template <int BN, bool OUT_BF16>
 cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
-                      int ldd, int relu, cudaStream_t s)
+                      int ldd, int relu, int splits, int kb_per_split, cudaStream_t s)
 {
     constexpr int smem = kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024 + 256;
     static bool configured = false;
@@ -288,29 +304,56 @@ cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((M + kBM - 1) / kBM, N / BN);
-    k_gemm<BN, OUT_BF16><<<grid, kThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu);
+    dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, splits);
+    k_gemm<BN, OUT_BF16><<<grid, kThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu, kb_per_split);
     return cudaGetLastError();
+}
+
+// Sum of the FP32 partial tiles of a split-K GEMM, plus bias and activation.
+template <bool OUT_BF16>
+__global__ void k_split_reduce(const float* __restrict__ part, int splits, int M, int N, int ldp, void* __restrict__ D,
+                               int ldd, const float* __restrict__ bias, int relu)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)M * N) return;
+    const int row = (int)(i / N), col = (int)(i - (long long)row * N);
+    float acc = bias ? bias[col] : 0.0f;
+    for (int z = 0; z < splits; ++z) acc += part[(size_t)z * M * ldp + (size_t)row * ldp + col];
+    if (relu) acc = fmaxf(acc, 0.0f);
+    if (OUT_BF16)
+        ((__nv_bfloat16*)D)[(size_t)row * ldd + col] = __float2bfloat16_rn(acc);
+    else
+        ((float*)D)[(size_t)row * ldd + col] = acc;
 }
 
 }  // namespace
 
 cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,
-                      int N, int K, bool out_bf16, bool relu, cudaStream_t s)
+                      int N, int K, bool out_bf16, bool relu, cudaStream_t s, int splits, float* workspace)
 {
-    int bn = N >= 256 ? 256 : N;
-    if (N % bn != 0 || (bn != 32 && bn != 64 && bn != 128 && bn != 256)) return cudaErrorInvalidValue;
+    const int bn = N >= 256 ? 256 : N > 64 ? 128 : N > 32 ? 64 : 32;
+    if (N < 8 || N % 8) return cudaErrorInvalidValue;
     if (lda % 8 || ldb % 8 || ldd % 8 || K > lda || K > ldb || N > ldd || M < 1 || K < 1) return cudaErrorInvalidValue;
     if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)D) & 15) return cudaErrorInvalidValue;
+    const int nkb = (K + kBK - 1) / kBK;
+    if (splits < 1) splits = 1;
+    if (splits > nkb) splits = nkb;
+    const int kb_per_split = (nkb + splits - 1) / splits;
+    splits = (nkb + kb_per_split - 1) / kb_per_split;
+    if (splits > 1 && !workspace) return cudaErrorInvalidValue;
     CUtensorMap ta, tb;
     cudaError_t e = make_map(&ta, A, M, K, lda, kBM);
     if (e == cudaSuccess) e = make_map(&tb, B, N, K, ldb, bn);
     if (e != cudaSuccess) return e;
     const int r = relu ? 1 : 0;
-#define NN_GEMM_CASE(BNV)                                                                              \
-    case BNV:                                                                                          \
-        return out_bf16 ? launch_bn<BNV, true>(ta, tb, D, bias, M, N, K, ldd, r, s)                    \
-                        : launch_bn<BNV, false>(ta, tb, D, bias, M, N, K, ldd, r, s);
+    void* out = splits > 1 ? (void*)workspace : D;
+    const int ldo = splits > 1 ? N : ldd;
+    const bool ob = splits > 1 ? false : out_bf16;
+#define NN_GEMM_CASE(BNV)                                                                                      \
+    case BNV:                                                                                                  \
+        e = ob ? launch_bn<BNV, true>(ta, tb, out, bias, M, N, K, ldo, r, splits, kb_per_split, s)            \
+               : launch_bn<BNV, false>(ta, tb, out, bias, M, N, K, ldo, r, splits, kb_per_split, s);          \
+        break;
     switch (bn) {
         NN_GEMM_CASE(32)
         NN_GEMM_CASE(64)
@@ -318,7 +361,14 @@ cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, i
         NN_GEMM_CASE(256)
     }
 #undef NN_GEMM_CASE
-    return cudaErrorInvalidValue;
+    if (e != cudaSuccess || splits == 1) return e;
+    const long long n = (long long)M * N;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (out_bf16)
+        k_split_reduce<true><<<grid, 256, 0, s>>>(workspace, splits, M, N, N, D, ldd, bias, r);
+    else
+        k_split_reduce<false><<<grid, 256, 0, s>>>(workspace, splits, M, N, N, D, ldd, bias, r);
+    return cudaGetLastError();
 }
 
 cudaError_t gemm_error(int* flag, bool clear)

@@ -1,0 +1,473 @@
+// Memory-bound layers of the surrogate network (NHWC, BF16 activations,
+// FP32 where values are summed).  Every kernel here is a plain grid over its
+// output elements; the contractions go to the tensor-core GEMM.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nn_layers.h"
+
+namespace nn {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ float bf(bf16 v) { return __bfloat162float(v); }
+
+inline unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// A[(b, y, x)][(ky, kx, c)] = X[b, y + ky - 1, x + kx - 1, c] (zero outside):
+// one thread per (pixel, tap, 8-channel group), 16-byte moves.
+__global__ void k_im2col3x3(const bf16* __restrict__ X, int B, int H, int W, int C, int cpitch, bf16* __restrict__ A)
+{
+    const int groups = C / 8;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n = (long long)B * H * W * 9 * groups;
+    if (i >= n) return;
+    const int g = (int)(i % groups);
+    long long r = i / groups;
+    const int tap = (int)(r % 9);
+    const long long p = r / 9;
+    const int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((long long)W * H));
+    const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+        v = *(const uint4*)(X + (((long long)b * H + yy) * W + xx) * cpitch + g * 8);
+    *(uint4*)(A + p * (9LL * C) + tap * C + g * 8) = v;
+}
+
+// dX[b, y, x, c] = sum over taps of dA[(b, y - ky + 1, x - kx + 1)][(ky, kx, c)].
+__global__ void k_col2im3x3(const float* __restrict__ dA, int B, int H, int W, int C, float* __restrict__ dX,
+                            int cpitch)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n = (long long)B * H * W * C;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    const long long p = i / C;
+    const int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((long long)W * H));
+    float acc = 0.0f;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            const int yo = y - ky + 1, xo = x - kx + 1;
+            if (yo < 0 || yo >= H || xo < 0 || xo >= W) continue;
+            acc += dA[(((long long)b * H + yo) * W + xo) * (9LL * C) + (ky * 3 + kx) * C + c];
+        }
+    dX[p * cpitch + c] = acc;
+}
+
+// g <- g * (y > 0) on a [rows][C] slice of pitch `pitch` (BF16 or FP32 g).
+template <class G>
+__global__ void k_relu_bwd(G* __restrict__ g, int gpitch, const bf16* __restrict__ y, int ypitch, long long rows, int C)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= rows * C) return;
+    const long long r = i / C;
+    const int c = (int)(i - r * C);
+    if (!(bf(y[r * ypitch + c]) > 0.0f)) g[r * gpitch + c] = (G)0.0f;
+}
+
+// Out[c][r] = In[r][c] (BF16), 32 x 32 tiles through shared memory.
+__global__ void k_transpose(const bf16* __restrict__ in, int rows, int cols, int ipitch, bf16* __restrict__ out,
+                            int opitch)
+{
+    __shared__ bf16 t[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;  // rows on x: up to 2^31 blocks
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        t[k][threadIdx.x] = (r < rows && c < cols) ? in[(long long)r * ipitch + c] : __float2bfloat16(0.0f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[(long long)c * opitch + r] = t[threadIdx.x][k];
+    }
+}
+
+__global__ void k_maxpool_fwd(const bf16* __restrict__ X, int B, int H, int W, int C, int xpitch, bf16* __restrict__ Y)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * Ho * Wo * C) return;
+    const int c = (int)(i % C);
+    const long long p = i / C;
+    const int x = (int)(p % Wo), y = (int)((p / Wo) % Ho), b = (int)(p / ((long long)Wo * Ho));
+    const long long base = (((long long)b * H + 2 * y) * W + 2 * x) * xpitch + c;
+    float m = bf(X[base]);
+    m = fmaxf(m, bf(X[base + xpitch]));
+    m = fmaxf(m, bf(X[base + (long long)W * xpitch]));
+    m = fmaxf(m, bf(X[base + (long long)W * xpitch + xpitch]));
+    Y[p * C + c] = __float2bfloat16(m);
+}
+
+// The gradient goes to the first maximum of each 2 x 2 window (row-major order).
+__global__ void k_maxpool_bwd(const bf16* __restrict__ X, int B, int H, int W, int C, int xpitch,
+                              const float* __restrict__ dY, float* __restrict__ dX, int dpitch)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * Ho * Wo * C) return;
+    const int c = (int)(i % C);
+    const long long p = i / C;
+    const int x = (int)(p % Wo), y = (int)((p / Wo) % Ho), b = (int)(p / ((long long)Wo * Ho));
+    long long off[4];
+    float v[4];
+    for (int k = 0; k < 4; ++k) {
+        const long long q = ((long long)b * H + 2 * y + k / 2) * W + 2 * x + k % 2;
+        off[k] = q;
+        v[k] = bf(X[q * xpitch + c]);
+    }
+    int arg = 0;
+    for (int k = 1; k < 4; ++k)
+        if (v[k] > v[arg]) arg = k;
+    const float g = dY[p * C + c];
+    for (int k = 0; k < 4; ++k) dX[off[k] * dpitch + c] += (k == arg) ? g : 0.0f;
+}
+
+// U[(b, y, x)][(dy, dx, c)] (2 x 2 up-convolution output) -> Y[b, 2y + dy, 2x + dx, c0 + c].
+__global__ void k_shuffle_fwd(const bf16* __restrict__ U, int B, int H, int W, int C, bf16* __restrict__ Y,
+                              int ypitch, int c0)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * H * W * 4 * C) return;
+    const int c = (int)(i % C);
+    long long r = i / C;
+    const int sub = (int)(r % 4);
+    const long long p = r / 4;
+    const int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((long long)W * H));
+    const long long q = ((long long)b * 2 * H + 2 * y + sub / 2) * (2 * W) + 2 * x + sub % 2;
+    Y[q * ypitch + c0 + c] = U[i];
+}
+
+// Inverse gather for the gradient: dU[(b, y, x)][(dy, dx, c)] = dY[b, 2y + dy, 2x + dx, c0 + c].
+template <class G>
+__global__ void k_shuffle_bwd(const G* __restrict__ dY, int ypitch, int c0, int B, int H, int W, int C,
+                              bf16* __restrict__ dU)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * H * W * 4 * C) return;
+    const int c = (int)(i % C);
+    long long r = i / C;
+    const int sub = (int)(r % 4);
+    const long long p = r / 4;
+    const int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((long long)W * H));
+    const long long q = ((long long)b * 2 * H + 2 * y + sub / 2) * (2 * W) + 2 * x + sub % 2;
+    dU[i] = __float2bfloat16((float)dY[q * ypitch + c0 + c]);
+}
+
+// Output projection (1 x 1 convolution to O <= 8 channels) with residual:
+// Y[p][o] = R[p][o] + b[o] + sum_c X[p][c] Wt[o][c].
+__global__ void k_proj_fwd(const bf16* __restrict__ X, int P, int C, int xpitch, const float* __restrict__ Wt,
+                           const float* __restrict__ bias, int O, const float* __restrict__ R, float* __restrict__ Y)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    for (int o = 0; o < O; ++o) {
+        float acc = bias[o] + (R ? R[p * O + o] : 0.0f);
+        for (int c = 0; c < C; ++c) acc += bf(X[p * xpitch + c]) * Wt[o * C + c];
+        Y[p * O + o] = acc;
+    }
+}
+
+// dX[p][c] = sum_o dY[p][o] Wt[o][c] (FP32, pitch dpitch).
+__global__ void k_proj_bwd_x(const float* __restrict__ dY, int P, int O, const float* __restrict__ Wt, int C,
+                             float* __restrict__ dX, int dpitch)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)P * C) return;
+    const long long p = i / C;
+    const int c = (int)(i - p * C);
+    float acc = 0.0f;
+    for (int o = 0; o < O; ++o) acc += dY[p * O + o] * Wt[o * C + c];
+    dX[p * dpitch + c] = acc;
+}
+
+// Per-block partial sums of dW[o][c] = sum_p dY[p][o] X[p][c] and db[o] =
+// sum_p dY[p][o]: block b covers pixels [b * chunk, (b + 1) * chunk).
+__global__ void k_proj_bwd_w(const float* __restrict__ dY, const bf16* __restrict__ X, int P, int C, int xpitch, int O,
+                             int chunk, float* __restrict__ part)
+{
+    const int slots = O * (C + 1);
+    const int p0 = blockIdx.x * chunk, p1 = min(P, p0 + chunk);
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+        const int o = s / (C + 1), c = s % (C + 1);
+        float acc = 0.0f;
+        for (int p = p0; p < p1; ++p) acc += dY[(long long)p * O + o] * (c < C ? bf(X[(long long)p * xpitch + c]) : 1.0f);
+        part[(long long)blockIdx.x * slots + s] = acc;
+    }
+}
+
+// Weights of the transposed 3 x 3 convolution that carries the gradient back
+// to the input: Wf[ci][t * cout + co] = W[co][(8 - t) * cin + ci] (the
+// kernel rotated by 180 degrees, input and output channels swapped).
+__global__ void k_flip3x3(const bf16* __restrict__ W, int cout, int cin, bf16* __restrict__ Wf)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)cout * 9 * cin) return;
+    const int ci = (int)(i % cin);
+    const long long r = i / cin;
+    const int t = (int)(r % 9), co = (int)(r / 9);
+    Wf[((long long)ci * 9 + (8 - t)) * cout + co] = W[i];
+}
+
+// Column sums of a [rows][C] matrix (pitch), as per-block partials over row chunks.
+template <class G>
+__global__ void k_colsum_part(const G* __restrict__ g, long long rows, int C, int pitch, int chunk,
+                              float* __restrict__ part)
+{
+    const long long r0 = (long long)blockIdx.x * chunk;
+    const long long r1 = r0 + chunk < rows ? r0 + chunk : rows;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float acc = 0.0f;
+        for (long long r = r0; r < r1; ++r) acc += (float)g[r * pitch + c];
+        part[(long long)blockIdx.x * C + c] = acc;
+    }
+}
+
+// dW[o][c] and db[o] from the nb partial rows of O x (C + 1) slots (fixed order).
+__global__ void k_proj_sum(const float* __restrict__ part, int nb, int O, int C, float* __restrict__ dW,
+                           float* __restrict__ db)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slots = O * (C + 1);
+    if (s >= slots) return;
+    float acc = 0.0f;
+    for (int b = 0; b < nb; ++b) acc += part[(long long)b * slots + s];
+    const int o = s / (C + 1), c = s % (C + 1);
+    if (c < C)
+        dW[o * C + c] = acc;
+    else
+        db[o] = acc;
+}
+
+// out[s] = sum over the nb partial rows (fixed order).
+__global__ void k_sum_parts(const float* __restrict__ part, int nb, int slots, float* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= slots) return;
+    float acc = 0.0f;
+    for (int b = 0; b < nb; ++b) acc += part[(long long)b * slots + s];
+    out[s] = acc;
+}
+
+// Squared error: d[i] = pred - target; per-block partial sums of d^2 and
+// the gradient 2 d / n.
+__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target, long long n,
+                      float* __restrict__ grad, float* __restrict__ part)
+{
+    __shared__ float sm[256];
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float d = 0.0f;
+    if (i < n) {
+        d = pred[i] - target[i];
+        grad[i] = 2.0f * d / (float)n;
+    }
+    sm[threadIdx.x] = d * d;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// Adam with bias correction on FP32 master weights; writes the BF16 copy.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2,
+                       bf16* __restrict__ wb)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16(wi);
+}
+
+// FP32 [P][F] fields -> BF16 NHWC [P][cpitch] with (x - mean) / std per field
+// and zero extra channels.
+// R (optional) receives the same normalised fields in FP32 [P][F].
+__global__ void k_pack(const float* __restrict__ f, long long P, int F, const float* __restrict__ mean,
+                       const float* __restrict__ inv_std, bf16* __restrict__ X, int cpitch, float* __restrict__ R)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= P * cpitch) return;
+    const long long p = i / cpitch;
+    const int c = (int)(i - p * cpitch);
+    const float v = c < F ? (f[p * F + c] - mean[c]) * inv_std[c] : 0.0f;
+    if (X) X[i] = __float2bfloat16(v);
+    if (R && c < F) R[p * F + c] = v;
+}
+
+// FP32 [rows][C] (pitch apitch) -> BF16 [rows][C] (pitch bpitch).
+__global__ void k_cast_bf16(const float* __restrict__ a, long long rows, int C, int apitch, bf16* __restrict__ b,
+                            int bpitch)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= rows * C) return;
+    const long long r = i / C;
+    const int c = (int)(i - r * C);
+    b[r * bpitch + c] = __float2bfloat16(a[r * apitch + c]);
+}
+
+// FP32 fields [P][F] = mean + std * Y[P][F] (undo the normalisation).
+__global__ void k_unpack(const float* __restrict__ Y, long long P, int F, const float* __restrict__ mean,
+                         const float* __restrict__ inv_std, float* __restrict__ f)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= P * F) return;
+    const int c = (int)(i % F);
+    f[i] = mean[c] + Y[i] / inv_std[c];
+}
+
+}  // namespace
+
+cudaError_t im2col3x3(const void* X, int B, int H, int W, int C, int cpitch, void* A, cudaStream_t s)
+{
+    if (C % 8 || cpitch % 8) return cudaErrorInvalidValue;
+    const long long n = (long long)B * H * W * 9 * (C / 8);
+    k_im2col3x3<<<blocks(n), 256, 0, s>>>((const bf16*)X, B, H, W, C, cpitch, (bf16*)A);
+    return cudaGetLastError();
+}
+
+cudaError_t col2im3x3(const float* dA, int B, int H, int W, int C, float* dX, int cpitch, cudaStream_t s)
+{
+    const long long n = (long long)B * H * W * C;
+    k_col2im3x3<<<blocks(n), 256, 0, s>>>(dA, B, H, W, C, dX, cpitch);
+    return cudaGetLastError();
+}
+
+cudaError_t relu_bwd(void* g, bool g_fp32, int gpitch, const void* y, int ypitch, long long rows, int C, cudaStream_t s)
+{
+    if (g_fp32)
+        k_relu_bwd<float><<<blocks(rows * C), 256, 0, s>>>((float*)g, gpitch, (const bf16*)y, ypitch, rows, C);
+    else
+        k_relu_bwd<bf16><<<blocks(rows * C), 256, 0, s>>>((bf16*)g, gpitch, (const bf16*)y, ypitch, rows, C);
+    return cudaGetLastError();
+}
+
+cudaError_t transpose(const void* in, int rows, int cols, int ipitch, void* out, int opitch, cudaStream_t s)
+{
+    if ((cols + 31) / 32 > 65535) return cudaErrorInvalidValue;
+    dim3 grid((rows + 31) / 32, (cols + 31) / 32), block(32, 8);
+    k_transpose<<<grid, block, 0, s>>>((const bf16*)in, rows, cols, ipitch, (bf16*)out, opitch);
+    return cudaGetLastError();
+}
+
+cudaError_t maxpool_fwd(const void* X, int B, int H, int W, int C, int xpitch, void* Y, cudaStream_t s)
+{
+    if (H % 2 || W % 2) return cudaErrorInvalidValue;
+    k_maxpool_fwd<<<blocks((long long)B * (H / 2) * (W / 2) * C), 256, 0, s>>>((const bf16*)X, B, H, W, C, xpitch,
+                                                                             (bf16*)Y);
+    return cudaGetLastError();
+}
+
+cudaError_t maxpool_bwd(const void* X, int B, int H, int W, int C, int xpitch, const float* dY, float* dX, int dpitch,
+                        cudaStream_t s)
+{
+    k_maxpool_bwd<<<blocks((long long)B * (H / 2) * (W / 2) * C), 256, 0, s>>>((const bf16*)X, B, H, W, C, xpitch, dY,
+                                                                             dX, dpitch);
+    return cudaGetLastError();
+}
+
+cudaError_t shuffle_fwd(const void* U, int B, int H, int W, int C, void* Y, int ypitch, int c0, cudaStream_t s)
+{
+    k_shuffle_fwd<<<blocks((long long)B * H * W * 4 * C), 256, 0, s>>>((const bf16*)U, B, H, W, C, (bf16*)Y, ypitch,
+                                                                      c0);
+    return cudaGetLastError();
+}
+
+cudaError_t shuffle_bwd(const void* dY, bool dy_fp32, int ypitch, int c0, int B, int H, int W, int C, void* dU,
+                        cudaStream_t s)
+{
+    const long long n = (long long)B * H * W * 4 * C;
+    if (dy_fp32)
+        k_shuffle_bwd<float><<<blocks(n), 256, 0, s>>>((const float*)dY, ypitch, c0, B, H, W, C, (bf16*)dU);
+    else
+        k_shuffle_bwd<bf16><<<blocks(n), 256, 0, s>>>((const bf16*)dY, ypitch, c0, B, H, W, C, (bf16*)dU);
+    return cudaGetLastError();
+}
+
+cudaError_t proj_fwd(const void* X, int P, int C, int xpitch, const float* Wt, const float* bias, int O,
+                     const float* R, float* Y, cudaStream_t s)
+{
+    k_proj_fwd<<<blocks(P), 256, 0, s>>>((const bf16*)X, P, C, xpitch, Wt, bias, O, R, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, const float* Wt, int O, float* dX,
+                     int dpitch, float* dW, float* db, float* part, int part_blocks, cudaStream_t s)
+{
+    if (dX) k_proj_bwd_x<<<blocks((long long)P * C), 256, 0, s>>>(dY, P, O, Wt, C, dX, dpitch);
+    const int chunk = (P + part_blocks - 1) / part_blocks;
+    const int nb = (P + chunk - 1) / chunk;
+    k_proj_bwd_w<<<nb, 128, 0, s>>>(dY, (const bf16*)X, P, C, xpitch, O, chunk, part);
+    k_proj_sum<<<blocks(O * (C + 1)), 256, 0, s>>>(part, nb, O, C, dW, db);
+    return cudaGetLastError();
+}
+
+cudaError_t flip3x3(const void* W, int cout, int cin, void* Wf, cudaStream_t s)
+{
+    k_flip3x3<<<blocks((long long)cout * 9 * cin), 256, 0, s>>>((const bf16*)W, cout, cin, (bf16*)Wf);
+    return cudaGetLastError();
+}
+
+cudaError_t colsum(const void* g, bool g_fp32, long long rows, int C, int pitch, float* out, float* part,
+                   int part_blocks, cudaStream_t s)
+{
+    const int chunk = (int)((rows + part_blocks - 1) / part_blocks);
+    const int nb = (int)((rows + chunk - 1) / chunk);
+    if (g_fp32)
+        k_colsum_part<float><<<nb, 128, 0, s>>>((const float*)g, rows, C, pitch, chunk, part);
+    else
+        k_colsum_part<bf16><<<nb, 128, 0, s>>>((const bf16*)g, rows, C, pitch, chunk, part);
+    k_sum_parts<<<blocks(C), 256, 0, s>>>(part, nb, C, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mse(const float* pred, const float* target, long long n, float* grad, float* loss, float* part,
+                cudaStream_t s)
+{
+    const int nb = (int)((n + 255) / 256);
+    k_mse<<<nb, 256, 0, s>>>(pred, target, n, grad, part);
+    k_sum_parts<<<1, 32, 0, s>>>(part, nb, 1, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
+                 int t, void* wb, cudaStream_t s)
+{
+    const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+    k_adam<<<blocks(n), 256, 0, s>>>(w, g, m, v, n, lr, b1, b2, eps, c1, c2, (bf16*)wb);
+    return cudaGetLastError();
+}
+
+cudaError_t pack(const float* f, long long P, int F, const float* mean, const float* inv_std, void* X, int cpitch,
+                 float* R, cudaStream_t s)
+{
+    if (F > cpitch) return cudaErrorInvalidValue;
+    k_pack<<<blocks(P * cpitch), 256, 0, s>>>(f, P, F, mean, inv_std, (bf16*)X, cpitch, R);
+    return cudaGetLastError();
+}
+
+cudaError_t unpack(const float* Y, long long P, int F, const float* mean, const float* inv_std, float* f,
+                   cudaStream_t s)
+{
+    k_unpack<<<blocks(P * F), 256, 0, s>>>(Y, P, F, mean, inv_std, f);
+    return cudaGetLastError();
+}
+
+cudaError_t cast_bf16(const float* a, long long rows, int C, int apitch, void* b, int bpitch, cudaStream_t s)
+{
+    k_cast_bf16<<<blocks(rows * C), 256, 0, s>>>(a, rows, C, apitch, (bf16*)b, bpitch);
+    return cudaGetLastError();
+}
+
+}  // namespace nn

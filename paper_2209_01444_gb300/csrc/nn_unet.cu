@@ -1,0 +1,572 @@
+// The surrogate network as one object: a convolutional U-Net over NHWC BF16
+// activations whose forward, backward and Adam update are sequences of the
+// tensor-core GEMM (nn_gemm.cu) and the layer kernels (nn_layers.cu) on one
+// stream.  The host code here only plans buffers and issues launches.
+//
+// Network (levels L, base width w, level l has c_l = w * 2^l channels):
+//   encoder l = 0 .. L-1: a_l = relu(conv3x3(in_l)), s_l = relu(conv3x3(a_l)),
+//     in_{l+1} = maxpool2x2(s_l);
+//   decoder l = L-2 .. 0: u_l = upconv2x2(h_{l+1}) (h_{L-1} = s_{L-1},
+//     otherwise the decoder output d_{l+1}), cat_l = [s_l, u_l],
+//     d_l = relu(conv3x3(relu(conv3x3(cat_l))));
+//   output y = x[:, :F] + proj1x1(d_0) in normalised units.
+// A 3 x 3 convolution is an im2col gather followed by a GEMM with the bias and
+// ReLU in its epilogue; its input gradient is the same gather of the output
+// gradient times the 180-degree-rotated kernel; its weight gradient is a
+// split-K GEMM over all pixels.  s_l is written straight into the first half
+// of the concatenation buffer cat_l and u_l into the second half, so the
+// concatenation costs nothing.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "nn_kernels.h"
+#include "nn_layers.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kInPitch = 8;  // input channels (fields, zero padded)
+constexpr int kPartBlocks = 1024;
+
+struct Conv {
+    int cin = 0, cout = 0;
+    long long w = 0, b = 0;  // offsets in the padded parameter vector
+    bf16* wf = nullptr;      // [cin][9 cout] rotated kernel for the input gradient
+};
+
+struct Up {
+    int cin = 0, cout = 0;  // cin = 2 cout
+    long long w = 0, b = 0;
+    bf16* wt = nullptr;  // [cin][4 cout] transpose for the input gradient
+};
+
+struct Level {
+    int c = 0, H = 0, W = 0;
+    long long P = 0;
+    Conv ea, eb, da, db;
+    Up up;
+    bf16* a = nullptr;     // [P][c]
+    bf16* s = nullptr;     // cat_l [P][2c] (s in the first half) or, at the bottom, [P][c]
+    int spitch = 0;
+    bf16* pool = nullptr;  // [P/4][c]
+    bf16* u = nullptr;     // up-convolution GEMM output [P_{l+1}][4c]
+    bf16* dA = nullptr;    // decoder activations [P][c]
+    bf16* dD = nullptr;
+    float* dcat = nullptr;  // gradient of cat_l, FP32 [P][2c]
+};
+
+struct Tensor {
+    long long packed, padded, n;
+};
+
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct lbm_unet {
+    int L = 0, base = 0, F = 0, B = 0, H = 0, W = 0;
+    long long P0 = 0;
+    std::vector<Tensor> tensors;  // in the order of the network definition
+    long long n_packed = 0, n_padded = 0;
+    long long out_w = 0, out_b = 0;
+    std::vector<Level> lv;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    bf16* wb = nullptr;
+    int t = 0;
+    float *mean = nullptr, *inv_std = nullptr;
+    bf16* x0 = nullptr;
+    float *R = nullptr, *Y = nullptr, *T = nullptr, *G = nullptr;
+    float *loss = nullptr, *part = nullptr;
+    bf16 *col = nullptr, *colT = nullptr, *tA = nullptr, *tB = nullptr;
+    bf16 *gA = nullptr, *gB = nullptr, *dU = nullptr;
+    float* g32 = nullptr;
+    float* ws = nullptr;
+    long long ws_n = 0;
+    cudaStream_t s = nullptr;
+    std::vector<void*> allocs;
+    long long bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_unet* u, int code, const std::string& what)
+{
+    if (u) u->err = what;
+    return code;
+}
+
+int cuda_fail(lbm_unet* u, cudaError_t e, const char* where)
+{
+    return fail(u, LBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define UN_CHECK(u, call)                                           \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((u), e_, #call);    \
+    } while (0)
+
+template <class T>
+cudaError_t alloc(lbm_unet* u, T** p, long long n)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (size_t)std::max<long long>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    u->allocs.push_back(q);
+    u->bytes += std::max<long long>(n, 1) * (long long)sizeof(T);
+    *p = (T*)q;
+    return cudaMemset(q, 0, (size_t)std::max<long long>(n, 1) * sizeof(T));
+}
+
+// K slices so that the weight-gradient GEMM fills about two waves of CTAs.
+int splits_for(int M, int N, long long K)
+{
+    const int bn = N >= 256 ? 256 : N > 64 ? 128 : N > 32 ? 64 : 32;
+    const long long tiles = (long long)((M + 127) / 128) * ((N + bn - 1) / bn);
+    const long long nkb = (K + 63) / 64;
+    long long sp = (304 + tiles - 1) / tiles;
+    sp = std::min<long long>(sp, nkb);
+    sp = std::min<long long>(sp, 256);
+    return (int)std::max<long long>(sp, 1);
+}
+
+long long split_ws(int M, int N, long long K) { return (long long)splits_for(M, N, K) * M * N; }
+
+// The planned shapes and offsets, before any allocation.
+void plan(lbm_unet* u)
+{
+    long long packed = 0, padded = 0;
+    auto add = [&](long long n) {
+        Tensor t{packed, padded, n};
+        u->tensors.push_back(t);
+        packed += n;
+        padded = round_up(padded + n, 64);
+        return t.padded;
+    };
+    u->lv.resize(u->L);
+    int cprev = kInPitch;
+    long long P = u->P0;
+    int H = u->H, W = u->W;
+    for (int l = 0; l < u->L; ++l) {
+        Level& L = u->lv[l];
+        L.c = u->base << l;
+        L.H = H;
+        L.W = W;
+        L.P = P;
+        L.ea.cin = cprev;
+        L.ea.cout = L.c;
+        L.ea.w = add(9LL * cprev * L.c);
+        L.ea.b = add(L.c);
+        L.eb.cin = L.c;
+        L.eb.cout = L.c;
+        L.eb.w = add(9LL * L.c * L.c);
+        L.eb.b = add(L.c);
+        cprev = L.c;
+        H /= 2;
+        W /= 2;
+        P /= 4;
+    }
+    for (int l = u->L - 2; l >= 0; --l) {
+        Level& L = u->lv[l];
+        const int c = L.c;
+        L.up.cin = 2 * c;
+        L.up.cout = c;
+        L.up.w = add(4LL * c * 2 * c);
+        L.up.b = add(4LL * c);
+        L.da.cin = 2 * c;
+        L.da.cout = c;
+        L.da.w = add(9LL * 2 * c * c);
+        L.da.b = add(c);
+        L.db.cin = c;
+        L.db.cout = c;
+        L.db.w = add(9LL * c * c);
+        L.db.b = add(c);
+    }
+    u->out_w = add((long long)u->F * u->base);
+    u->out_b = add(u->F);
+    u->n_packed = packed;
+    u->n_padded = padded;
+}
+
+cudaError_t allocate(lbm_unet* u)
+{
+    cudaError_t e = cudaSuccess;
+#define UN_ALLOC(p, n)                        \
+    do {                                      \
+        if ((e = alloc(u, &(p), (n)))) return e; \
+    } while (0)
+    const long long np = u->n_padded;
+    UN_ALLOC(u->w, np);
+    UN_ALLOC(u->g, np);
+    UN_ALLOC(u->m, np);
+    UN_ALLOC(u->v, np);
+    UN_ALLOC(u->wb, np);
+    UN_ALLOC(u->mean, kInPitch);
+    UN_ALLOC(u->inv_std, kInPitch);
+    const long long P0 = u->P0;
+    UN_ALLOC(u->x0, P0 * kInPitch);
+    UN_ALLOC(u->R, P0 * u->F);
+    UN_ALLOC(u->Y, P0 * u->F);
+    UN_ALLOC(u->T, P0 * u->F);
+    UN_ALLOC(u->G, P0 * u->F);
+    UN_ALLOC(u->loss, 4);
+    const long long part_n = std::max<long long>((long long)kPartBlocks * (u->base + 1) * 8, P0 * u->F / 256 + 2);
+    UN_ALLOC(u->part, std::max<long long>(part_n, (long long)kPartBlocks * 4 * (u->base << (u->L - 1))));
+    long long col_n = 0, ws_n = 0, t_n = 0, g_n = 0;
+    const int L = u->L;
+    for (int l = 0; l < L; ++l) {
+        Level& v = u->lv[l];
+        const long long P = v.P;
+        const int c = v.c;
+        UN_ALLOC(v.a, P * c);
+        if (l < L - 1) {
+            v.spitch = 2 * c;
+            UN_ALLOC(v.s, P * 2 * c);
+            UN_ALLOC(v.pool, P / 4 * c);
+            UN_ALLOC(v.u, P / 4 * 4 * c);
+            UN_ALLOC(v.dA, P * c);
+            UN_ALLOC(v.dD, P * c);
+            UN_ALLOC(v.dcat, P * 2 * c);
+        } else {
+            v.spitch = c;
+            UN_ALLOC(v.s, P * c);
+        }
+        for (Conv* cv : {&v.ea, &v.eb, &v.da, &v.db}) {
+            if (!cv->cout) continue;
+            col_n = std::max(col_n, 9 * P * std::max(cv->cin, cv->cout));
+            ws_n = std::max(ws_n, split_ws(cv->cout, 9 * cv->cin, P));
+            t_n = std::max(t_n, P * std::max(cv->cout, cv->cin));
+            g_n = std::max(g_n, P * std::max(cv->cout, cv->cin));
+            UN_ALLOC(cv->wf, 9LL * cv->cin * cv->cout);
+        }
+        if (v.up.cout) {
+            const long long Pl = P / 4;
+            ws_n = std::max(ws_n, split_ws(4 * c, 2 * c, Pl));
+            t_n = std::max(t_n, Pl * 4 * c);
+            g_n = std::max(g_n, Pl * 4 * c);
+            UN_ALLOC(v.up.wt, 8LL * c * c);
+        }
+    }
+    g_n = std::max(g_n, P0 * u->base);
+    UN_ALLOC(u->col, col_n);
+    UN_ALLOC(u->colT, col_n);
+    UN_ALLOC(u->tA, t_n);
+    UN_ALLOC(u->tB, t_n);
+    UN_ALLOC(u->gA, g_n);
+    UN_ALLOC(u->gB, g_n);
+    UN_ALLOC(u->dU, g_n);
+    UN_ALLOC(u->g32, g_n);
+    UN_ALLOC(u->ws, ws_n);
+    u->ws_n = ws_n;
+#undef UN_ALLOC
+    return e;
+}
+
+// BF16 copy-derived weights: the rotated conv kernels and transposed
+// up-convolution matrices used by the backward pass.
+cudaError_t derive(lbm_unet* u)
+{
+    cudaError_t e = cudaSuccess;
+    for (Level& v : u->lv) {
+        for (Conv* cv : {&v.ea, &v.eb, &v.da, &v.db}) {
+            if (!cv->cout) continue;
+            if ((e = nn::flip3x3(u->wb + cv->w, cv->cout, cv->cin, cv->wf, u->s))) return e;
+        }
+        if (v.up.cout) {
+            const int c = v.c;
+            if ((e = nn::transpose(u->wb + v.up.w, 4 * c, 2 * c, 2 * c, v.up.wt, 4 * c, u->s))) return e;
+        }
+    }
+    return e;
+}
+
+cudaError_t conv_fwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in, int inpitch, bf16* out,
+                     int outpitch)
+{
+    cudaError_t e = nn::im2col3x3(in, u->B, v.H, v.W, cv.cin, inpitch, u->col, u->s);
+    if (e) return e;
+    return nn::gemm_bf16(u->col, 9 * cv.cin, u->wb + cv.w, 9 * cv.cin, out, outpitch, u->w + cv.b, (int)v.P, cv.cout,
+                         9 * cv.cin, true, true, u->s);
+}
+
+// Weight and bias gradients of one convolution from its input `in` and the
+// (masked) BF16 output gradient dY [P][cout]; the FP32 input gradient goes to
+// dx (pitch dxpitch) when dx is not NULL.
+cudaError_t conv_bwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in, int inpitch, const bf16* dY,
+                     float* dx, int dxpitch)
+{
+    const long long P = v.P;
+    const int K9 = 9 * cv.cin;
+    cudaError_t e;
+    if ((e = nn::im2col3x3(in, u->B, v.H, v.W, cv.cin, inpitch, u->col, u->s))) return e;
+    if ((e = nn::transpose(u->col, (int)P, K9, K9, u->colT, (int)P, u->s))) return e;
+    if ((e = nn::transpose(dY, (int)P, cv.cout, cv.cout, u->tA, (int)P, u->s))) return e;
+    const int sp = splits_for(cv.cout, K9, P);
+    if ((e = nn::gemm_bf16(u->tA, (int)P, u->colT, (int)P, u->g + cv.w, K9, nullptr, cv.cout, K9, (int)P, false, false,
+                           u->s, sp, u->ws)))
+        return e;
+    if ((e = nn::colsum(dY, false, P, cv.cout, cv.cout, u->g + cv.b, u->part, kPartBlocks, u->s))) return e;
+    if (!dx) return cudaSuccess;
+    if ((e = nn::im2col3x3(dY, u->B, v.H, v.W, cv.cout, cv.cout, u->col, u->s))) return e;
+    return nn::gemm_bf16(u->col, 9 * cv.cout, cv.wf, 9 * cv.cout, dx, dxpitch, nullptr, (int)P, cv.cin, 9 * cv.cout,
+                         false, false, u->s);
+}
+
+// g32 [rows][C] (pitch) masked by y > 0, then rounded into BF16 [rows][C].
+cudaError_t mask_cast(lbm_unet* u, float* g32, int gpitch, const bf16* y, int ypitch, long long rows, int C, bf16* out)
+{
+    cudaError_t e = nn::relu_bwd(g32, true, gpitch, y, ypitch, rows, C, u->s);
+    if (e) return e;
+    return nn::cast_bf16(g32, rows, C, gpitch, out, C, u->s);
+}
+
+cudaError_t forward(lbm_unet* u, const float* x)
+{
+    cudaError_t e;
+    if ((e = nn::pack(x, u->P0, u->F, u->mean, u->inv_std, u->x0, kInPitch, u->R, u->s))) return e;
+    const bf16* in = u->x0;
+    int inpitch = kInPitch;
+    const int L = u->L;
+    for (int l = 0; l < L; ++l) {
+        Level& v = u->lv[l];
+        if ((e = conv_fwd(u, v, v.ea, in, inpitch, v.a, v.c))) return e;
+        if ((e = conv_fwd(u, v, v.eb, v.a, v.c, v.s, v.spitch))) return e;
+        if (l < L - 1) {
+            if ((e = nn::maxpool_fwd(v.s, u->B, v.H, v.W, v.c, v.spitch, v.pool, u->s))) return e;
+            in = v.pool;
+            inpitch = v.c;
+        }
+    }
+    const bf16* h = u->lv[L - 1].s;
+    for (int l = L - 2; l >= 0; --l) {
+        Level& v = u->lv[l];
+        const Level& lo = u->lv[l + 1];
+        const int c = v.c;
+        if ((e = nn::gemm_bf16(h, 2 * c, u->wb + v.up.w, 2 * c, v.u, 4 * c, u->w + v.up.b, (int)lo.P, 4 * c, 2 * c,
+                               true, false, u->s)))
+            return e;
+        if ((e = nn::shuffle_fwd(v.u, u->B, lo.H, lo.W, c, v.s, 2 * c, c, u->s))) return e;
+        if ((e = conv_fwd(u, v, v.da, v.s, 2 * c, v.dA, c))) return e;
+        if ((e = conv_fwd(u, v, v.db, v.dA, c, v.dD, c))) return e;
+        h = v.dD;
+    }
+    const bf16* top = L > 1 ? u->lv[0].dD : u->lv[0].s;
+    return nn::proj_fwd(top, (int)u->P0, u->base, u->base, u->w + u->out_w, u->w + u->out_b, u->F, u->R, u->Y, u->s);
+}
+
+// Loss and parameter gradients for the target t (physical units); forward() ran.
+cudaError_t backward(lbm_unet* u, const float* t)
+{
+    cudaError_t e;
+    const long long P0 = u->P0;
+    const int L = u->L, F = u->F, w0 = u->base;
+    if ((e = nn::pack(t, P0, F, u->mean, u->inv_std, nullptr, F, u->T, u->s))) return e;
+    if ((e = nn::mse(u->Y, u->T, P0 * F, u->G, u->loss, u->part, u->s))) return e;
+    const bf16* top = L > 1 ? u->lv[0].dD : u->lv[0].s;
+    if ((e = nn::proj_bwd(u->G, top, (int)P0, w0, w0, u->w + u->out_w, F, u->g32, w0, u->g + u->out_w, u->g + u->out_b,
+                          u->part, kPartBlocks, u->s)))
+        return e;
+    if ((e = mask_cast(u, u->g32, w0, top, L > 1 ? w0 : u->lv[0].spitch, P0, w0, u->gA))) return e;
+    // decoder, top level first; gA holds the masked gradient of the level's output
+    for (int l = 0; l < L - 1; ++l) {
+        Level& v = u->lv[l];
+        const Level& lo = u->lv[l + 1];
+        const int c = v.c;
+        if ((e = conv_bwd(u, v, v.db, v.dA, c, u->gA, u->g32, c))) return e;
+        if ((e = mask_cast(u, u->g32, c, v.dA, c, v.P, c, u->gB))) return e;
+        if ((e = conv_bwd(u, v, v.da, v.s, 2 * c, u->gB, v.dcat, 2 * c))) return e;
+        // up-convolution: gradient of u_l is the second half of dcat
+        if ((e = nn::shuffle_bwd(v.dcat, true, 2 * c, c, u->B, lo.H, lo.W, c, u->dU, u->s))) return e;
+        if ((e = nn::colsum(u->dU, false, lo.P, 4 * c, 4 * c, u->g + v.up.b, u->part, kPartBlocks, u->s))) return e;
+        const bf16* hlow = (l + 1 < L - 1) ? lo.dD : lo.s;
+        if ((e = nn::transpose(u->dU, (int)lo.P, 4 * c, 4 * c, u->tA, (int)lo.P, u->s))) return e;
+        if ((e = nn::transpose(hlow, (int)lo.P, 2 * c, 2 * c, u->tB, (int)lo.P, u->s))) return e;
+        const int sp = splits_for(4 * c, 2 * c, lo.P);
+        if ((e = nn::gemm_bf16(u->tA, (int)lo.P, u->tB, (int)lo.P, u->g + v.up.w, 2 * c, nullptr, 4 * c, 2 * c,
+                               (int)lo.P, false, false, u->s, sp, u->ws)))
+            return e;
+        if ((e = nn::gemm_bf16(u->dU, 4 * c, v.up.wt, 4 * c, u->g32, 2 * c, nullptr, (int)lo.P, 2 * c, 4 * c, false,
+                               false, u->s)))
+            return e;
+        if ((e = mask_cast(u, u->g32, 2 * c, hlow, 2 * c, lo.P, 2 * c, u->gA))) return e;
+    }
+    // encoder, bottom level first
+    for (int l = L - 1; l >= 0; --l) {
+        Level& v = u->lv[l];
+        const int c = v.c;
+        if (l < L - 1) {
+            // skip gradient (first half of dcat) plus the pooled path's gradient in g32
+            if ((e = nn::maxpool_bwd(v.s, u->B, v.H, v.W, c, 2 * c, u->g32, v.dcat, 2 * c, u->s))) return e;
+            if ((e = mask_cast(u, v.dcat, 2 * c, v.s, 2 * c, v.P, c, u->gA))) return e;
+        }
+        if ((e = conv_bwd(u, v, v.eb, v.a, c, u->gA, u->g32, c))) return e;
+        if ((e = mask_cast(u, u->g32, c, v.a, c, v.P, c, u->gB))) return e;
+        const bf16* in = l == 0 ? u->x0 : u->lv[l - 1].pool;
+        const int inpitch = l == 0 ? kInPitch : u->lv[l - 1].c;
+        if ((e = conv_bwd(u, v, v.ea, in, inpitch, u->gB, l == 0 ? nullptr : u->g32, v.ea.cin))) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_unet_create(int levels, int base, int fields, int batch, int height, int width, lbm_unet** out)
+{
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (levels < 1 || levels > 8 || base < 8 || base % 8 || fields < 1 || fields > kInPitch || batch < 1)
+        return LBM_EINVAL;
+    const int div = 1 << (levels - 1);
+    if (height < div || width < div || height % div || width % div) return LBM_EINVAL;
+    const long long P0 = (long long)batch * height * width;
+    const long long Pb = P0 >> (2 * (levels - 1));
+    if (Pb % 8 || P0 > (1LL << 30)) return LBM_EINVAL;
+    lbm_unet* u = new lbm_unet;
+    u->L = levels;
+    u->base = base;
+    u->F = fields;
+    u->B = batch;
+    u->H = height;
+    u->W = width;
+    u->P0 = P0;
+    plan(u);
+    cudaError_t e = allocate(u);
+    if (e == cudaSuccess) {
+        float ones[kInPitch], zeros[kInPitch] = {0};
+        for (float& o : ones) o = 1.0f;
+        e = cudaMemcpy(u->mean, zeros, sizeof zeros, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(u->inv_std, ones, sizeof ones, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        lbm_unet_destroy(u);
+        return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    }
+    *out = u;
+    return LBM_OK;
+}
+
+void lbm_unet_destroy(lbm_unet* u)
+{
+    if (!u) return;
+    for (void* p : u->allocs) cudaFree(p);
+    delete u;
+}
+
+int lbm_unet_set_stream(lbm_unet* u, void* stream)
+{
+    if (!u) return LBM_EINVAL;
+    u->s = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+long long lbm_unet_param_count(const lbm_unet* u) { return u ? u->n_packed : -1; }
+
+long long lbm_unet_device_bytes(const lbm_unet* u) { return u ? u->bytes : -1; }
+
+int lbm_unet_set_params(lbm_unet* u, const float* host)
+{
+    if (!u || !host) return LBM_EINVAL;
+    std::vector<float> pad((size_t)u->n_padded, 0.0f);
+    for (const Tensor& t : u->tensors) std::memcpy(&pad[t.padded], host + t.packed, (size_t)t.n * sizeof(float));
+    UN_CHECK(u, cudaMemcpyAsync(u->w, pad.data(), pad.size() * sizeof(float), cudaMemcpyHostToDevice, u->s));
+    UN_CHECK(u, cudaMemsetAsync(u->m, 0, pad.size() * sizeof(float), u->s));
+    UN_CHECK(u, cudaMemsetAsync(u->v, 0, pad.size() * sizeof(float), u->s));
+    UN_CHECK(u, nn::cast_bf16(u->w, 1, (int)u->n_padded, (int)u->n_padded, u->wb, (int)u->n_padded, u->s));
+    UN_CHECK(u, derive(u));
+    UN_CHECK(u, cudaStreamSynchronize(u->s));
+    u->t = 0;
+    return LBM_OK;
+}
+
+static int get_vec(lbm_unet* u, const float* dev, float* host)
+{
+    if (!u || !host) return LBM_EINVAL;
+    std::vector<float> pad((size_t)u->n_padded);
+    UN_CHECK(u, cudaStreamSynchronize(u->s));
+    UN_CHECK(u, cudaMemcpy(pad.data(), dev, pad.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    for (const Tensor& t : u->tensors) std::memcpy(host + t.packed, &pad[t.padded], (size_t)t.n * sizeof(float));
+    return LBM_OK;
+}
+
+int lbm_unet_get_params(lbm_unet* u, float* host) { return get_vec(u, u ? u->w : nullptr, host); }
+
+int lbm_unet_get_grads(lbm_unet* u, float* host) { return get_vec(u, u ? u->g : nullptr, host); }
+
+int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_)
+{
+    if (!u || !mean || !std_) return LBM_EINVAL;
+    float mu[kInPitch] = {0}, is[kInPitch];
+    for (int c = 0; c < kInPitch; ++c) is[c] = 1.0f;
+    for (int c = 0; c < u->F; ++c) {
+        if (!(std_[c] > 0.0f)) return fail(u, LBM_EINVAL, "normalisation scale must be positive");
+        mu[c] = mean[c];
+        is[c] = 1.0f / std_[c];
+    }
+    UN_CHECK(u, cudaMemcpyAsync(u->mean, mu, sizeof mu, cudaMemcpyHostToDevice, u->s));
+    UN_CHECK(u, cudaMemcpyAsync(u->inv_std, is, sizeof is, cudaMemcpyHostToDevice, u->s));
+    UN_CHECK(u, cudaStreamSynchronize(u->s));
+    return LBM_OK;
+}
+
+int lbm_unet_forward(lbm_unet* u, const float* x, float* y)
+{
+    if (!u || !x) return LBM_EINVAL;
+    UN_CHECK(u, forward(u, x));
+    if (y) UN_CHECK(u, nn::unpack(u->Y, u->P0, u->F, u->mean, u->inv_std, y, u->s));
+    return LBM_OK;
+}
+
+int lbm_unet_backward(lbm_unet* u, const float* x, const float* target)
+{
+    if (!u || !x || !target) return LBM_EINVAL;
+    UN_CHECK(u, forward(u, x));
+    UN_CHECK(u, backward(u, target));
+    return LBM_OK;
+}
+
+int lbm_unet_adam(lbm_unet* u, float lr, float beta1, float beta2, float eps)
+{
+    if (!u || !(lr >= 0.0f)) return LBM_EINVAL;
+    ++u->t;
+    UN_CHECK(u, nn::adam(u->w, u->g, u->m, u->v, u->n_padded, lr, beta1, beta2, eps, u->t, u->wb, u->s));
+    UN_CHECK(u, derive(u));
+    return LBM_OK;
+}
+
+int lbm_unet_train_step(lbm_unet* u, const float* x, const float* target, float lr)
+{
+    int r = lbm_unet_backward(u, x, target);
+    if (r != LBM_OK) return r;
+    return lbm_unet_adam(u, lr, 0.9f, 0.999f, 1e-8f);
+}
+
+int lbm_unet_loss(lbm_unet* u, double* out)
+{
+    if (!u || !out) return LBM_EINVAL;
+    float l = 0.0f;
+    UN_CHECK(u, cudaStreamSynchronize(u->s));
+    UN_CHECK(u, cudaMemcpy(&l, u->loss, sizeof l, cudaMemcpyDeviceToHost));
+    *out = (double)l / (double)(u->P0 * u->F);
+    return LBM_OK;
+}
+
+int lbm_unet_output(lbm_unet* u, float* y_norm)
+{
+    if (!u || !y_norm) return LBM_EINVAL;
+    UN_CHECK(u, cudaMemcpyAsync(y_norm, u->Y, (size_t)u->P0 * u->F * sizeof(float), cudaMemcpyDeviceToDevice, u->s));
+    return LBM_OK;
+}
+
+const char* lbm_unet_last_error(const lbm_unet* u) { return u ? u->err.c_str() : "null network"; }
+
+}  // extern "C"

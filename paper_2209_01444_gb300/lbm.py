@@ -91,6 +91,55 @@ SIGNATURES = {
     "lbm_nn_gemm": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
                                ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]),
     "lbm_nn_error": (ct.c_int, [ct.c_int]),
+    "lbm_nn_gemm_split": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int,
+                                     ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int,
+                                     ct.c_void_p, ct.c_void_p]),
+    "lbm_nn_im2col3x3": (ct.c_int, [ct.c_void_p] + [ct.c_int] * 5 + [ct.c_void_p, ct.c_void_p]),
+    "lbm_nn_col2im3x3": (ct.c_int, [ct.c_void_p] + [ct.c_int] * 4 + [ct.c_void_p, ct.c_int, ct.c_void_p]),
+    "lbm_nn_relu_bwd": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_int, ct.c_longlong, ct.c_int,
+                                   ct.c_void_p]),
+    "lbm_nn_transpose": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p]),
+    "lbm_nn_maxpool_fwd": (ct.c_int, [ct.c_void_p] + [ct.c_int] * 5 + [ct.c_void_p, ct.c_void_p]),
+    "lbm_nn_maxpool_bwd": (ct.c_int, [ct.c_void_p] + [ct.c_int] * 5 + [ct.c_void_p, ct.c_void_p, ct.c_int,
+                                                                       ct.c_void_p]),
+    "lbm_nn_shuffle_fwd": (ct.c_int, [ct.c_void_p] + [ct.c_int] * 4 + [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p]),
+    "lbm_nn_shuffle_bwd": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int] + [ct.c_int] * 4 +
+                           [ct.c_void_p, ct.c_void_p]),
+    "lbm_nn_proj_fwd": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int,
+                                   ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "lbm_nn_proj_bwd": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_int,
+                                   ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
+                                   ct.c_void_p]),
+    "lbm_nn_flip3x3": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_create": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]),
+    "lbm_unet_destroy": (None, [ct.c_void_p]),
+    "lbm_unet_set_stream": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_param_count": (ct.c_longlong, [ct.c_void_p]),
+    "lbm_unet_device_bytes": (ct.c_longlong, [ct.c_void_p]),
+    "lbm_unet_set_params": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_get_params": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_get_grads": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_set_norm": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_forward": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_backward": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_adam": (ct.c_int, [ct.c_void_p, ct.c_float, ct.c_float, ct.c_float, ct.c_float]),
+    "lbm_unet_train_step": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_float]),
+    "lbm_unet_loss": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_output": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_last_error": (ct.c_char_p, [ct.c_void_p]),
+    "lbm_nn_colsum": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_longlong, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                 ct.c_int, ct.c_void_p]),
+    "lbm_nn_mse": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_longlong, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                              ct.c_void_p]),
+    "lbm_nn_adam": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_longlong, ct.c_float,
+                               ct.c_float, ct.c_float, ct.c_float, ct.c_int, ct.c_void_p, ct.c_void_p]),
+    "lbm_nn_pack": (ct.c_int, [ct.c_void_p, ct.c_longlong, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
+                               ct.c_void_p, ct.c_void_p]),
+    "lbm_nn_unpack": (ct.c_int, [ct.c_void_p, ct.c_longlong, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                 ct.c_void_p]),
+    "lbm_nn_cast_bf16": (ct.c_int, [ct.c_void_p, ct.c_longlong, ct.c_int, ct.c_int, ct.c_void_p, ct.c_int,
+                                    ct.c_void_p]),
+
     "lbm_set_profiling": (ct.c_int, [_H, ct.c_int]),
     "lbm_kernel_time": (ct.c_int, [_H, _DP, ct.POINTER(ct.c_longlong)]),
     "lbm_last_error": (ct.c_char_p, [_H]),

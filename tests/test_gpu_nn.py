@@ -58,5 +58,195 @@ def test_gemm_rejects_bad_shapes(env):
     torch, lib = env
     A = torch.zeros(128, 64, dtype=torch.bfloat16, device="cuda")
     D = torch.zeros(128, 48, dtype=torch.float32, device="cuda")
-    assert lib.lbm_nn_gemm(_p(A), 64, _p(A), 64, _p(D), 48, None, 128, 48, 64, 1, 0, None) != 0  # N = 48
+    assert lib.lbm_nn_gemm(_p(A), 64, _p(A), 64, _p(D), 48, None, 128, 44, 64, 1, 0, None) != 0  # N % 8
     assert lib.lbm_nn_gemm(_p(A), 60, _p(A), 64, _p(D), 64, None, 128, 64, 64, 1, 0, None) != 0  # lda % 8
+    assert lib.lbm_nn_gemm(_p(A), 64, _p(A), 64, _p(D), 48, None, 128, 48, 72, 1, 0, None) != 0  # K > lda
+    assert lib.lbm_nn_gemm_split(_p(A), 64, _p(A), 64, _p(D), 48, None, 128, 48, 1024, 1, 0, 4, None,
+                                 None) != 0  # split without workspace
+
+
+def _stream(torch):
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("M,N,K,splits", [(32, 72, 4096, 16), (64, 288, 2048, 7), (512, 200, 1000, 3),
+                                          (128, 264, 640, 1), (96, 8, 512, 2), (1024, 576, 16384, 64)])
+def test_gemm_ragged_n_and_split_k(env, M, N, K, splits):
+    """Ragged N (multiples of 8 between tile widths) and split-K slices with
+    their FP32 reduction, against an FP32 matmul of the same BF16 inputs."""
+    torch, lib = env
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N + K)
+    ld = (K + 7) // 8 * 8
+    A = torch.zeros(M, ld, dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros(N, ld, dtype=torch.bfloat16, device="cuda")
+    A[:, :K] = torch.randn(M, K, generator=g, device="cuda").to(torch.bfloat16)
+    B[:, :K] = torch.randn(N, K, generator=g, device="cuda").to(torch.bfloat16)
+    bias = torch.randn(N, generator=g, device="cuda")
+    ws = torch.empty(splits * M * N, dtype=torch.float32, device="cuda")
+    ref = A[:, :K].float() @ B[:, :K].float().T + bias
+    for out_fp32 in (1, 0):
+        ldd = N + 8  # pitched output
+        D = torch.full((M, ldd), 7.0, dtype=torch.float32 if out_fp32 else torch.bfloat16, device="cuda")
+        rc = lib.lbm_nn_gemm_split(_p(A), ld, _p(B), ld, _p(D), ldd, _p(bias), M, N, K, out_fp32, 0, splits,
+                                   _p(ws), _stream(torch))
+        assert rc == 0
+        torch.cuda.synchronize()
+        assert lib.lbm_nn_error(1) == 0
+        err = float((D[:, :N].float() - ref).abs().max())
+        tol = (2e-5 if out_fp32 else 8e-3) * float(ref.abs().max())
+        assert err <= tol, (M, N, K, splits, out_fp32, err)
+        assert bool((D[:, N:].float() == 7.0).all()), "wrote past N"
+
+
+def _bf(torch, shape, g, scale=1.0):
+    return (torch.randn(*shape, generator=g, device="cuda") * scale).to(torch.bfloat16)
+
+
+def test_im2col_flip_transpose_exact(env):
+    torch, lib = env
+    g = torch.Generator(device="cuda").manual_seed(5)
+    B, H, W, C, cp = 2, 5, 7, 16, 24
+    X = _bf(torch, (B, H, W, cp), g)
+    A = torch.empty(B * H * W, 9 * C, dtype=torch.bfloat16, device="cuda")
+    assert lib.lbm_nn_im2col3x3(_p(X), B, H, W, C, cp, _p(A), _stream(torch)) == 0
+    Xp = torch.nn.functional.pad(X[..., :C].float(), (0, 0, 1, 1, 1, 1))
+    ref = torch.stack([Xp[:, ky:ky + H, kx:kx + W, :] for ky in range(3) for kx in range(3)], dim=3)
+    assert torch.equal(A.float(), ref.reshape(B * H * W, 9 * C))
+    # rotated kernel
+    cout, cin = 24, 16
+    Wt = _bf(torch, (cout, 9 * cin), g)
+    Wf = torch.empty(cin, 9 * cout, dtype=torch.bfloat16, device="cuda")
+    assert lib.lbm_nn_flip3x3(_p(Wt), cout, cin, _p(Wf), _stream(torch)) == 0
+    ref = Wt.reshape(cout, 9, cin).flip(1).permute(2, 1, 0).reshape(cin, 9 * cout)
+    assert torch.equal(Wf, ref)
+    # transpose with pitches
+    T = torch.empty(40, 80, dtype=torch.bfloat16, device="cuda")
+    S = _bf(torch, (70, 48), g)
+    assert lib.lbm_nn_transpose(_p(S), 70, 40, 48, _p(T), 80, _stream(torch)) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(T[:, :70], S[:, :40].T)
+
+
+def test_pool_and_shuffle_exact(env):
+    torch, lib = env
+    g = torch.Generator(device="cuda").manual_seed(6)
+    B, H, W, C, xp = 2, 6, 8, 16, 32
+    X = _bf(torch, (B, H, W, xp), g)
+    X[0, 0, 0, 0] = X[0, 1, 1, 0] = 9.0  # tie: the first maximum takes the gradient
+    Y = torch.empty(B, H // 2, W // 2, C, dtype=torch.bfloat16, device="cuda")
+    assert lib.lbm_nn_maxpool_fwd(_p(X), B, H, W, C, xp, _p(Y), _stream(torch)) == 0
+    win = X[..., :C].float().reshape(B, H // 2, 2, W // 2, 2, C).permute(0, 1, 3, 2, 4, 5).reshape(B, H // 2, W // 2, 4, C)
+    assert torch.equal(Y.float(), win.max(dim=3).values)
+    dY = torch.randn(B, H // 2, W // 2, C, generator=g, device="cuda")
+    dX = torch.randn(B, H, W, xp, generator=g, device="cuda")
+    base = dX.clone()
+    assert lib.lbm_nn_maxpool_bwd(_p(X), B, H, W, C, xp, _p(dY), _p(dX), xp, _stream(torch)) == 0
+    torch.cuda.synchronize()
+    w = win.cpu().numpy()
+    arg = w.argmax(axis=3)  # first maximum
+    add = np.zeros(w.shape, np.float32)
+    np.put_along_axis(add, arg[:, :, :, None, :], dY.cpu().numpy()[:, :, :, None, :], axis=3)
+    add = add.reshape(B, H // 2, W // 2, 2, 2, C).transpose(0, 1, 3, 2, 4, 5).reshape(B, H, W, C)
+    ref = base.cpu().numpy()
+    ref[..., :C] = ref[..., :C] + add
+    assert np.array_equal(dX.cpu().numpy(), ref)
+    # up-convolution shuffle into the second half of a concatenation buffer and back
+    Hl, Wl, c = 3, 4, 8
+    U = _bf(torch, (B * Hl * Wl, 4 * c), g)
+    Ycat = torch.zeros(B, 2 * Hl, 2 * Wl, 2 * c, dtype=torch.bfloat16, device="cuda")
+    assert lib.lbm_nn_shuffle_fwd(_p(U), B, Hl, Wl, c, _p(Ycat), 2 * c, c, _stream(torch)) == 0
+    ref = U.reshape(B, Hl, Wl, 2, 2, c).permute(0, 1, 3, 2, 4, 5).reshape(B, 2 * Hl, 2 * Wl, c)
+    assert torch.equal(Ycat[..., c:], ref) and bool((Ycat[..., :c] == 0).all())
+    dU = torch.empty_like(U)
+    dcat = torch.randn(B, 2 * Hl, 2 * Wl, 2 * c, generator=g, device="cuda")
+    assert lib.lbm_nn_shuffle_bwd(_p(dcat), 1, 2 * c, c, B, Hl, Wl, c, _p(dU), _stream(torch)) == 0
+    torch.cuda.synchronize()
+    ref = dcat[..., c:].reshape(B, Hl, 2, Wl, 2, c).permute(0, 1, 3, 2, 4, 5).reshape(B * Hl * Wl, 4 * c)
+    assert torch.equal(dU, ref.to(torch.bfloat16))
+
+
+def test_reductions_projection_and_adam(env):
+    torch, lib = env
+    g = torch.Generator(device="cuda").manual_seed(7)
+    s = _stream(torch)
+    rows, C, pitch = 5000, 40, 48
+    G = torch.randn(rows, pitch, generator=g, device="cuda")
+    out = torch.empty(C, device="cuda")
+    part = torch.empty(1 << 20, device="cuda")
+    assert lib.lbm_nn_colsum(_p(G), 1, rows, C, pitch, _p(out), _p(part), 300, s) == 0
+    torch.cuda.synchronize()
+    ref = G[:, :C].double().sum(0)
+    assert float((out.double() - ref).abs().max()) <= 1e-4 * float(G[:, :C].abs().sum(0).max())
+    # projection with residual, and its backward
+    P, Cx, O = 3000, 32, 5
+    X = _bf(torch, (P, Cx), g)
+    Wt = torch.randn(O, Cx, generator=g, device="cuda")
+    b = torch.randn(O, generator=g, device="cuda")
+    R = torch.randn(P, O, generator=g, device="cuda")
+    Y = torch.empty(P, O, device="cuda")
+    assert lib.lbm_nn_proj_fwd(_p(X), P, Cx, Cx, _p(Wt), _p(b), O, _p(R), _p(Y), s) == 0
+    torch.cuda.synchronize()
+    ref = R.double() + b.double() + X.double() @ Wt.double().T
+    assert float((Y.double() - ref).abs().max()) <= 1e-5 * float(ref.abs().max())
+    dY = torch.randn(P, O, generator=g, device="cuda")
+    dX = torch.empty(P, Cx, device="cuda")
+    dW = torch.empty(O, Cx, device="cuda")
+    db = torch.empty(O, device="cuda")
+    assert lib.lbm_nn_proj_bwd(_p(dY), _p(X), P, Cx, Cx, _p(Wt), O, _p(dX), Cx, _p(dW), _p(db), _p(part), 64, s) == 0
+    torch.cuda.synchronize()
+    assert float((dX.double() - dY.double() @ Wt.double()).abs().max()) <= 1e-5 * 10
+    refW = dY.double().T @ X.double()
+    assert float((dW.double() - refW).abs().max()) <= 1e-5 * float(refW.abs().max()) * 10
+    assert float((db.double() - dY.double().sum(0)).abs().max()) <= 1e-3
+    # mean squared error
+    n = 100_003
+    pr, tg = torch.randn(n, generator=g, device="cuda"), torch.randn(n, generator=g, device="cuda")
+    grad, loss = torch.empty(n, device="cuda"), torch.empty(1, device="cuda")
+    assert lib.lbm_nn_mse(_p(pr), _p(tg), n, _p(grad), _p(loss), _p(part), s) == 0
+    torch.cuda.synchronize()
+    d = pr.double() - tg.double()
+    assert abs(float(loss) - float((d * d).sum())) <= 1e-4 * float((d * d).sum())
+    assert float((grad.double() - 2 * d / n).abs().max()) <= 1e-6 * float((2 * d / n).abs().max()) + 1e-12
+    # Adam, three steps, against the textbook update in FP64
+    m_ = 10_000
+    w = torch.randn(m_, generator=g, device="cuda")
+    mom, vel = torch.zeros(m_, device="cuda"), torch.zeros(m_, device="cuda")
+    wb = torch.empty(m_, dtype=torch.bfloat16, device="cuda")
+    wr, mr, vr = w.double().clone(), torch.zeros(m_, dtype=torch.float64, device="cuda"), \
+        torch.zeros(m_, dtype=torch.float64, device="cuda")
+    for t in (1, 2, 3):
+        gr = torch.randn(m_, generator=g, device="cuda")
+        assert lib.lbm_nn_adam(_p(w), _p(gr), _p(mom), _p(vel), m_, ct.c_float(1e-2), ct.c_float(0.9),
+                               ct.c_float(0.999), ct.c_float(1e-8), t, _p(wb), s) == 0
+        gd = gr.double()
+        mr = 0.9 * mr + 0.1 * gd
+        vr = 0.999 * vr + 0.001 * gd * gd
+        wr = wr - 1e-2 * (mr / (1 - 0.9 ** t)) / ((vr / (1 - 0.999 ** t)).sqrt() + 1e-8)
+    torch.cuda.synchronize()
+    assert float((w.double() - wr).abs().max()) <= 1e-5
+    assert torch.equal(wb, w.to(torch.bfloat16))
+
+
+def test_pack_unpack_cast(env):
+    torch, lib = env
+    g = torch.Generator(device="cuda").manual_seed(8)
+    s = _stream(torch)
+    P, F = 1000, 5
+    f = torch.randn(P, F, generator=g, device="cuda") * 3 + 1
+    mean = torch.tensor([0.5, -1.0, 2.0, 0.0, 0.25], device="cuda")
+    std = torch.tensor([2.0, 0.5, 4.0, 1.0, 0.125], device="cuda")
+    inv = 1.0 / std
+    X = torch.full((P, 8), 3.0, dtype=torch.bfloat16, device="cuda")
+    R = torch.empty(P, F, device="cuda")
+    assert lib.lbm_nn_pack(_p(f), P, F, _p(mean), _p(inv), _p(X), 8, _p(R), s) == 0
+    back = torch.empty(P, F, device="cuda")
+    assert lib.lbm_nn_unpack(_p(R), P, F, _p(mean), _p(inv), _p(back), s) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(R, (f - mean) * inv)
+    assert torch.equal(X[:, :F], R.to(torch.bfloat16)) and bool((X[:, F:] == 0).all())
+    assert float((back - f).abs().max()) <= 1e-5 * float(f.abs().max())
+    A = torch.randn(300, 40, generator=g, device="cuda")
+    Bt = torch.zeros(300, 48, dtype=torch.bfloat16, device="cuda")
+    assert lib.lbm_nn_cast_bf16(_p(A), 300, 33, 40, _p(Bt), 48, s) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(Bt[:, :33], A[:, :33].to(torch.bfloat16)) and bool((Bt[:, 33:] == 0).all())
