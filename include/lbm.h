@@ -276,6 +276,22 @@ LBM_API int lbm_nn_gemm_split(const void* A, int lda, const void* B, int ldb, vo
                               int M, int N, int K, int out_fp32, int relu, int splits, float* workspace,
                               void* stream);
 
+/* Implicit 3 x 3 convolution with zero padding (no gathered copy: the tensor
+ * cores read shifted tiles of X through 4-D TMA loads): D[p][n] =
+ * act(sum_{tap, c < C} X[p shifted by tap][c] * Wm[n][tap*C + c] + bias[n]),
+ * X NHWC BF16 [B][H][W][cpitch], Wm BF16 [N][ldw] (ldw >= 9C, tap = ky*3+kx),
+ * D [B*H*W][ldd] BF16 or FP32.  C a multiple of 32; a 128-pixel tile must be
+ * whole rows of whole images (W a multiple of 128, or W and H dividing 128
+ * appropriately): LBM_EINVAL otherwise. */
+LBM_API int lbm_nn_conv3x3(const void* X, int B, int H, int W, int C, int cpitch, const void* Wm, int ldw, void* D,
+                           int ldd, const float* bias, int N, int out_fp32, int relu, void* stream);
+/* 2 x 2 stride-2 up-convolution stored straight into a concatenation buffer:
+ * Y[b][2y+dy][2x+dx][c0+co] = bias[k] + sum_i X[(b,y,x)][i] Wm[k][i] with
+ * k = (dy*2+dx)*c + co; X [B*Hl*Wl][lda], Wm [4c][ldw] BF16, Y BF16 pitch
+ * ypitch; c a multiple of 16. */
+LBM_API int lbm_nn_upconv2x2(const void* X, int lda, const void* Wm, int ldw, void* Y, int ypitch, int c0,
+                             const float* bias, int B, int Hl, int Wl, int cin, int c, void* stream);
+
 /* Layers around the GEMM.  Activations are NHWC: [B][H][W][channels] with a
  * channel pitch (the row length of one pixel), BF16 unless named FP32.
  * im2col3x3: A[(b,y,x)][(ky,kx,c)] = X[b, y+ky-1, x+kx-1, c], zero outside
@@ -382,6 +398,45 @@ LBM_API int lbm_unet_loss(lbm_unet* u, double* out);
 /* Copies the last prediction in normalised units (FP32 device array). */
 LBM_API int lbm_unet_output(lbm_unet* u, float* y_norm);
 LBM_API const char* lbm_unet_last_error(const lbm_unet* u);
+LBM_API int lbm_unet_shape(const lbm_unet* u, int* batch, int* height, int* width, int* fields);
+
+/* ------------------------------------------- device-side field exchange */
+/* Device snapshots of a handle's state (populations, history, step count) in
+ * library-owned memory, slot 0 or 1 (allocated on first use; queued on the
+ * handle's stream).  lbm_surrogate_advance with audit != 0 overwrites slot 1.
+ * Restoring an empty slot gives LBM_ESTATE. */
+LBM_API int lbm_snapshot_save(lbm_handle* h, int slot);
+LBM_API int lbm_snapshot_restore(lbm_handle* h, int slot);
+
+/* The fields of every node as one FP32 device array [ny][nx][5], per node
+ * phi, C, theta, u_x, u_y (the paper's units), for the surrogate network;
+ * and the reverse: every node's populations replaced by the equilibrium of
+ * the given fields (phi clamped to [-1, 1], U recovered from C and phi, the
+ * node's pressure kept; history reset to the new macros).  Both queue on the
+ * handle's stream. */
+LBM_API int lbm_fields_nhwc(lbm_handle* h, float* dst);
+LBM_API int lbm_set_fields_nhwc(lbm_handle* h, const float* src);
+LBM_API int lbm_batch_fields_nhwc(lbm_batch* b, int dom, float* dst);
+
+/* One surrogate window of K steps (the paper has no counterpart).  The network
+ * (sized for one ny x nx image of 5 fields, run on the handle's stream)
+ * predicts the fields K steps ahead.  audit == 0: the state becomes the
+ * equilibrium of the prediction and the step count advances by K.  audit != 0:
+ * the plain LB also runs the window from the same state and its result is
+ * kept; the report compares the two: the largest tip difference over the
+ * three rays of lbm_metrics (origin cx, cy, orientation `orient`), the nodes
+ * whose phi sign differs and the largest |phi| difference; accepted = tip
+ * error <= tip_tol (a non-finite prediction is never accepted).
+ * Synchronises when audit != 0. */
+typedef struct lbm_surrogate_report {
+    int audited, accepted;
+    double tip_err;     /* lattice units */
+    double tip[3];      /* tips of the LB result (audited windows) */
+    long long mismatch; /* nodes where the sign of phi differs */
+    double max_dphi;
+} lbm_surrogate_report;
+LBM_API int lbm_surrogate_advance(lbm_handle* h, lbm_unet* net, int K, double tip_tol, int audit, double cx,
+                                  double cy, double orient, lbm_surrogate_report* rep);
 
 /* LBM_ETIMEOUT if a network kernel gave up a bounded wait since the flag was
  * last cleared (clear != 0 clears it), else LBM_OK.  Synchronous. */

@@ -59,6 +59,13 @@ struct lbm_handle {
     // lattice conversion
     double vf = 1, pscale = 1;  // paper velocity -> flow lattice, lattice pressure -> paper
     double ref[lbm::kPlanes];   // reference equilibrium of the stored deviations
+    // device snapshots (lbm_snapshot_save) and surrogate scratch, allocated on first use
+    void* snap_sc[2] = {nullptr, nullptr};
+    void* snap_fl[2] = {nullptr, nullptr};
+    float* snap_hist[2] = {nullptr, nullptr};
+    long long snap_steps[2] = {-1, -1};
+    float *sur_x = nullptr, *sur_y = nullptr, *sur_l = nullptr;
+    unsigned long long* d_mis = nullptr;
 };
 
 namespace {
@@ -370,7 +377,9 @@ void lbm_destroy(lbm_handle* h)
     drop_graphs(h);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     void* ptrs[] = {h->B.sc[0], h->B.sc[1], h->B.fl[0], h->B.fl[1], h->B.hist, h->B.fb, h->grain,
-                    h->grain_cs, h->d_partials, h->d_red, h->d_f64, h->d_f32, h->d_seeds};
+                    h->grain_cs, h->d_partials, h->d_red, h->d_f64, h->d_f32, h->d_seeds,
+                    h->snap_sc[0], h->snap_sc[1], h->snap_fl[0], h->snap_fl[1], h->snap_hist[0], h->snap_hist[1],
+                    h->sur_x, h->sur_y, h->sur_l, h->d_mis};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;
@@ -680,6 +689,135 @@ int lbm_load_state(lbm_handle* h, const void* host, size_t bytes)
     h->B.grain = h->uniform ? nullptr : h->grain;
     h->steps = hd.steps;
     h->initialised = true;
+    return LBM_OK;
+}
+
+// ------------------------------------------------ device snapshots, surrogate
+int lbm_snapshot_save(lbm_handle* h, int slot)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (slot < 0 || slot > 1) return fail(h, LBM_EINVAL, "snapshot slot must be 0 or 1");
+    const size_t hb = (size_t)h->P.plane * sizeof(float) * lbm::kHist;
+    if (!h->snap_sc[slot]) {
+        LBM_CUDA(h, cudaMalloc(&h->snap_sc[slot], h->sc_bytes));
+        LBM_CUDA(h, cudaMalloc(&h->snap_fl[slot], h->fl_bytes));
+        LBM_CUDA(h, cudaMalloc((void**)&h->snap_hist[slot], hb));
+    }
+    LBM_CUDA(h, cudaMemcpyAsync(h->snap_sc[slot], h->B.sc[h->B.cs], h->sc_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(h->snap_fl[slot], h->B.fl[h->B.cf], h->fl_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(h->snap_hist[slot], h->B.hist, hb, cudaMemcpyDeviceToDevice, h->stream));
+    h->snap_steps[slot] = h->steps;
+    return LBM_OK;
+}
+
+int lbm_snapshot_restore(lbm_handle* h, int slot)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (slot < 0 || slot > 1) return fail(h, LBM_EINVAL, "snapshot slot must be 0 or 1");
+    if (h->snap_steps[slot] < 0) return fail(h, LBM_ESTATE, "no snapshot in this slot");
+    const size_t hb = (size_t)h->P.plane * sizeof(float) * lbm::kHist;
+    LBM_CUDA(h, cudaMemcpyAsync(h->B.sc[h->B.cs], h->snap_sc[slot], h->sc_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(h->B.fl[h->B.cf], h->snap_fl[slot], h->fl_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(h->B.hist, h->snap_hist[slot], hb, cudaMemcpyDeviceToDevice, h->stream));
+    h->steps = h->snap_steps[slot];
+    return LBM_OK;
+}
+
+int lbm_fields_nhwc(lbm_handle* h, float* dst)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!dst) return fail(h, LBM_EINVAL, "dst is NULL");
+    LBM_CUDA(h, lbm::launch_fields_nhwc(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], (float)(1.0 / h->vf),
+                                        dst, h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_fields_nhwc(lbm_handle* h, const float* src)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!src) return fail(h, LBM_EINVAL, "src is NULL");
+    LBM_CUDA(h, lbm::launch_set_fields_nhwc(h->P, h->storage, src, (float)h->vf, h->B.sc[h->B.cs], h->B.fl[h->B.cf],
+                                            h->B.hist, h->stream));
+    return LBM_OK;
+}
+
+namespace {
+
+int tips_now(lbm_handle* h, double cx, double cy, double orient, double tip[3])
+{
+    lbm_metrics m;
+    int rc = lbm_get_metrics(h, cx, cy, orient, &m);
+    if (rc) return rc;
+    for (int r = 0; r < 3; ++r) tip[r] = m.tip[r];
+    return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_surrogate_advance(lbm_handle* h, lbm_unet* net, int K, double tip_tol, int audit, double cx, double cy,
+                          double orient, lbm_surrogate_report* rep)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!net || !rep || K < 1) return fail(h, LBM_EINVAL, "need a network, a report and K >= 1");
+    int nb = 0, nh = 0, nw = 0, nf = 0;
+    lbm_unet_shape(net, &nb, &nh, &nw, &nf);
+    if (nb != 1 || nh != h->P.ny || nw != h->P.nx || nf != 5)
+        return fail(h, LBM_EINVAL, "network must be sized for one ny x nx image of 5 fields");
+    const size_t n5 = (size_t)h->P.nx * h->P.ny * 5;
+    if (!h->sur_x) {
+        LBM_CUDA(h, cudaMalloc((void**)&h->sur_x, n5 * sizeof(float)));
+        LBM_CUDA(h, cudaMalloc((void**)&h->sur_y, n5 * sizeof(float)));
+        LBM_CUDA(h, cudaMalloc((void**)&h->sur_l, n5 * sizeof(float)));
+        LBM_CUDA(h, cudaMalloc((void**)&h->d_mis, 2 * sizeof(unsigned long long)));
+    }
+    memset(rep, 0, sizeof(*rep));
+    if ((rc = lbm_unet_set_stream(net, h->stream))) return fail(h, rc, "lbm_unet_set_stream failed");
+    if ((rc = lbm_fields_nhwc(h, h->sur_x))) return rc;
+    if ((rc = lbm_unet_forward(net, h->sur_x, h->sur_y)))
+        return fail(h, rc, std::string("network: ") + lbm_unet_last_error(net));
+    if (!audit) {
+        if ((rc = lbm_set_fields_nhwc(h, h->sur_y))) return rc;
+        h->steps += K;
+        return LBM_OK;
+    }
+    // audit: the plain LB over the same window decides; its result is kept
+    rep->audited = 1;
+    if ((rc = lbm_step(h, K))) return rc;
+    if ((rc = lbm_fields_nhwc(h, h->sur_l))) return rc;
+    LBM_CUDA(h, lbm::launch_phi_mismatch(h->sur_y, h->sur_l, (long long)h->P.nx * h->P.ny, h->d_mis, h->stream));
+    double tl[3], ts[3];
+    if ((rc = tips_now(h, cx, cy, orient, tl))) return rc;
+    if ((rc = lbm_snapshot_save(h, 1))) return rc;
+    if ((rc = lbm_set_fields_nhwc(h, h->sur_y))) return rc;
+    rc = tips_now(h, cx, cy, orient, ts);
+    const int rr = lbm_snapshot_restore(h, 1);
+    if (rc == LBM_ENUMERIC) {
+        ts[0] = ts[1] = ts[2] = INFINITY;  // the prediction is not finite: reject it
+        rc = LBM_OK;
+    }
+    if (rc) return rc;
+    if (rr) return rr;
+    unsigned long long mis[2];
+    LBM_CUDA(h, cudaMemcpyAsync(mis, h->d_mis, sizeof mis, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    double err = 0.0;
+    for (int r = 0; r < 3; ++r) {
+        rep->tip[r] = tl[r];
+        const double d = fabs(ts[r] - tl[r]);
+        err = (d > err || d != d) ? d : err;
+    }
+    rep->tip_err = err;
+    rep->mismatch = (long long)mis[0];
+    uint32_t bits = (uint32_t)mis[1];
+    float mx;
+    memcpy(&mx, &bits, sizeof mx);
+    rep->max_dphi = mx;
+    rep->accepted = err <= tip_tol ? 1 : 0;
     return LBM_OK;
 }
 
@@ -1023,6 +1161,14 @@ int lbm_batch_get_fields(lbm_batch* b, int dom, unsigned mask, double* out)
     if (!b) return LBM_EINVAL;
     if (dom < 0 || dom >= (int)b->dom.size()) return bfail(b, LBM_EINVAL, "domain index out of range");
     int rc = lbm_get_fields(b->dom[dom], mask, out);
+    return rc ? bfail(b, rc, b->dom[dom]->err) : LBM_OK;
+}
+
+int lbm_batch_fields_nhwc(lbm_batch* b, int dom, float* dst)
+{
+    if (!b) return LBM_EINVAL;
+    if (dom < 0 || dom >= (int)b->dom.size()) return bfail(b, LBM_EINVAL, "domain index out of range");
+    int rc = lbm_fields_nhwc(b->dom[dom], dst);
     return rc ? bfail(b, rc, b->dom[dom]->err) : LBM_OK;
 }
 

@@ -63,27 +63,15 @@ __global__ void k_seed_fields(const StepParams P, const double* __restrict__ see
     if (grain) grain[o] = (uint8_t)best;
 }
 
-// Equilibrium populations of the given macros, then history = the macros
-// recovered from the stored populations (so the first backward differences
-// vanish).
+// Equilibrium populations of node o for the macro deviations (phi + 1,
+// C - 1, U, theta - theta_ref, u in flow lattice units, p), then history = the
+// macros recovered from the stored populations (so the first backward
+// differences vanish).
 template <class Store>
-__global__ void k_init(const StepParams P, const double* __restrict__ fields, void* __restrict__ sc,
-                       void* __restrict__ fl, float* __restrict__ hist)
+__device__ void init_node(const StepParams& P, long long o, float p1, float dC, float Uf, float dth, float ux,
+                          float uy, float p, void* __restrict__ sc, void* __restrict__ fl, float* __restrict__ hist)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
     const long long plane = P.plane;
-    const long long o = (long long)y * P.pitch + x;
-    // macro deviations from the reference state, formed in FP64
-    const double phi = fields[0 * plane + o], U = fields[1 * plane + o];
-    const double k = P.k;
-    const float p1 = (float)(phi + 1.0);
-    const float dC = (float)(0.5 * (1.0 + k - (1.0 - k) * phi) * (1.0 + (1.0 - k) * U) - 1.0);
-    const float dth = (float)(fields[2 * plane + o] - (double)P.theta_ref);
-    const float Uf = (float)U;
-    const float ux = (float)fields[3 * plane + o], uy = (float)fields[4 * plane + o];
-    const float p = (float)fields[5 * plane + o];
     const float hp1 = h_plus_1(P.h_kind, p1);
     const float H = (P.theta_ref + 0.5f) + dth - 0.5f * hp1;
     const float C = 1.0f + dC;
@@ -112,6 +100,95 @@ __global__ void k_init(const StepParams P, const double* __restrict__ fields, vo
     hist[3 * plane + o] = (1.0f + m.dC) * usy;
     hist[4 * plane + o] = m.H * usx;
     hist[5 * plane + o] = m.H * usy;
+}
+
+template <class Store>
+__global__ void k_init(const StepParams P, const double* __restrict__ fields, void* __restrict__ sc,
+                       void* __restrict__ fl, float* __restrict__ hist)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long plane = P.plane;
+    const long long o = (long long)y * P.pitch + x;
+    // macro deviations from the reference state, formed in FP64
+    const double phi = fields[0 * plane + o], U = fields[1 * plane + o];
+    const double k = P.k;
+    const float p1 = (float)(phi + 1.0);
+    const float dC = (float)(0.5 * (1.0 + k - (1.0 - k) * phi) * (1.0 + (1.0 - k) * U) - 1.0);
+    const float dth = (float)(fields[2 * plane + o] - (double)P.theta_ref);
+    init_node<Store>(P, o, p1, dC, (float)U, dth, (float)fields[3 * plane + o], (float)fields[4 * plane + o],
+                     (float)fields[5 * plane + o], sc, fl, hist);
+}
+
+// Fields of every node, pixel-interleaved for the surrogate network:
+// dst[(y * nx + x) * 5 + c] for c = phi, C, theta, u_x, u_y (velocities in
+// the paper's units: flow lattice units times inv_vf).
+template <class Store>
+__global__ void k_fields_nhwc(const StepParams P, const void* __restrict__ sc, const void* __restrict__ fl,
+                              float inv_vf, float* __restrict__ dst)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long o = (long long)y * P.pitch + x;
+    float f[5], n[5], g[5], h[9];
+    load_node<Store>(P, sc, fl, o, f, n, g, h);
+    const Macro m = node_macros(f, n, g, h, P);
+    float* d = dst + ((long long)y * P.nx + x) * 5;
+    d[0] = m.phi;
+    d[1] = 1.0f + m.dC;
+    d[2] = P.theta_ref + m.dth;
+    d[3] = m.ux * inv_vf;
+    d[4] = m.uy * inv_vf;
+}
+
+// Replaces every node's populations by the equilibrium of the given fields
+// (layout of k_fields_nhwc; phi clamped to [-1, 1], U recovered from C and
+// phi by the definition of U), keeping the node's current pressure.  Each
+// thread reads and writes only its own node, so this works in place.
+template <class Store>
+__global__ void k_set_fields_nhwc(const StepParams P, const float* __restrict__ src, float vf, void* __restrict__ sc,
+                                  void* __restrict__ fl, float* __restrict__ hist)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long o = (long long)y * P.pitch + x;
+    float f[5], n[5], g[5], h[9];
+    load_node<Store>(P, sc, fl, o, f, n, g, h);
+    const float p = node_macros(f, n, g, h, P).p;
+    const float* d = src + ((long long)y * P.nx + x) * 5;
+    const float phi = fminf(1.0f, fmaxf(-1.0f, d[0]));
+    const float C = d[1];
+    const float k = P.k;
+    const float U = (2.0f * C / (1.0f + k - (1.0f - k) * phi) - 1.0f) / (1.0f - k);
+    init_node<Store>(P, o, phi + 1.0f, C - 1.0f, U, d[2] - P.theta_ref, d[3] * vf, d[4] * vf, p, sc, fl, hist);
+}
+
+// Interface mismatch between two pixel-interleaved field sets (stride 5,
+// phi first): out[0] += nodes where the signs of phi differ, out[1] = max
+// |phi_a - phi_b| (as the bits of a non-negative float, so integer maximum
+// orders them).
+__global__ void k_phi_mismatch(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                               unsigned long long* __restrict__ out)
+{
+    unsigned long long cnt = 0;
+    float mx = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float pa = a[i * 5], pb = b[i * 5];
+        cnt += ((pa > 0.0f) != (pb > 0.0f)) ? 1ull : 0ull;
+        const float d = fabsf(pa - pb);
+        mx = (d > mx || d != d) ? d : mx;
+    }
+    for (int s = 16; s > 0; s >>= 1) {
+        cnt += __shfl_down_sync(0xffffffffu, cnt, s);
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, s));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], cnt);
+        atomicMax(&out[1], (unsigned long long)__float_as_uint(mx));
+    }
 }
 
 // Macro deviations of every node: phi + 1, C - 1, U, theta - theta_ref, ux,
@@ -316,6 +393,24 @@ cudaError_t init_t(const StepParams& P, const double* fields, void* sc, void* fl
 }
 
 template <class Store>
+cudaError_t fields_nhwc_t(const StepParams& P, const void* sc, const void* fl, float inv_vf, float* dst,
+                          cudaStream_t s)
+{
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
+    k_fields_nhwc<Store><<<g, b, 0, s>>>(P, sc, fl, inv_vf, dst);
+    return cudaGetLastError();
+}
+
+template <class Store>
+cudaError_t set_fields_nhwc_t(const StepParams& P, const float* src, float vf, void* sc, void* fl, float* hist,
+                              cudaStream_t s)
+{
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
+    k_set_fields_nhwc<Store><<<g, b, 0, s>>>(P, src, vf, sc, fl, hist);
+    return cudaGetLastError();
+}
+
+template <class Store>
 cudaError_t macros_t(const StepParams& P, const void* sc, const void* fl, float* out, cudaStream_t s)
 {
     const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
@@ -366,6 +461,37 @@ cudaError_t launch_init_from_fields(const StepParams& P, int storage, const doub
     case kStoreBF16: return init_t<StoreBF16>(P, fields, sc, fl, hist, s);
     default: return init_t<StoreF32>(P, fields, sc, fl, hist, s);
     }
+}
+
+cudaError_t launch_fields_nhwc(const StepParams& P, int storage, const void* sc, const void* fl, float inv_vf,
+                               float* dst, cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return fields_nhwc_t<StoreF16>(P, sc, fl, inv_vf, dst, s);
+    case kStoreBF16: return fields_nhwc_t<StoreBF16>(P, sc, fl, inv_vf, dst, s);
+    default: return fields_nhwc_t<StoreF32>(P, sc, fl, inv_vf, dst, s);
+    }
+}
+
+cudaError_t launch_set_fields_nhwc(const StepParams& P, int storage, const float* src, float vf, void* sc, void* fl,
+                                   float* hist, cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return set_fields_nhwc_t<StoreF16>(P, src, vf, sc, fl, hist, s);
+    case kStoreBF16: return set_fields_nhwc_t<StoreBF16>(P, src, vf, sc, fl, hist, s);
+    default: return set_fields_nhwc_t<StoreF32>(P, src, vf, sc, fl, hist, s);
+    }
+}
+
+cudaError_t launch_phi_mismatch(const float* a, const float* b, long long n, unsigned long long* out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 1216) blocks = 1216;
+    if (blocks < 1) blocks = 1;
+    k_phi_mismatch<<<(unsigned)blocks, 256, 0, s>>>(a, b, n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out,

@@ -12,7 +12,7 @@ int nn_status(cudaError_t e)
 {
     if (e == cudaSuccess) return LBM_OK;
     lbm::set_last_error(cudaGetErrorString(e));
-    return e == cudaErrorInvalidValue ? LBM_EINVAL : LBM_ECUDA;
+    return (e == cudaErrorInvalidValue || e == cudaErrorNotSupported) ? LBM_EINVAL : LBM_ECUDA;
 }
 
 }  // namespace
@@ -90,6 +90,19 @@ int lbm_nn_proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, co
                     int dpitch, float* dW, float* db, float* part, int part_blocks, void* stream)
 {
     return nn_status(nn::proj_bwd(dY, X, P, C, xpitch, Wt, O, dX, dpitch, dW, db, part, part_blocks, NN_S(stream)));
+}
+
+int lbm_nn_conv3x3(const void* X, int B, int H, int W, int C, int cpitch, const void* Wm, int ldw, void* D, int ldd,
+                   const float* bias, int N, int out_fp32, int relu, void* stream)
+{
+    return nn_status(nn::conv3x3_bf16(X, B, H, W, C, cpitch, Wm, ldw, D, ldd, bias, N, out_fp32 == 0, relu != 0,
+                                      NN_S(stream)));
+}
+
+int lbm_nn_upconv2x2(const void* X, int lda, const void* Wm, int ldw, void* Y, int ypitch, int c0, const float* bias,
+                     int B, int Hl, int Wl, int cin, int c, void* stream)
+{
+    return nn_status(nn::upconv2x2_bf16(X, lda, Wm, ldw, Y, ypitch, c0, bias, B, Hl, Wl, cin, c, NN_S(stream)));
 }
 
 int lbm_nn_flip3x3(const void* W, int cout, int cin, void* Wf, void* stream)

@@ -118,39 +118,104 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar)
                  : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Descriptor of a K-major tile with 64-byte rows (32 BF16) in the 64-byte
+// swizzle TMA produces: 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;  // 64-byte swizzle
+    return d;
+}
+
+template <int BK>
+__device__ __forceinline__ uint64_t tile_desc(uint32_t saddr)
+{
+    if constexpr (BK == 64)
+        return sw128_desc(saddr);
+    else
+        return sw64_desc(saddr);
+}
+
+template <int BK>
+constexpr int stages_for() { return BK == 64 ? 4 : 8; }
+
+}  // namespace
+
+// Geometry of an implicit 3 x 3 convolution (the A operand gathered by
+// 4-D TMA loads shifted by each tap) and of the up-convolution epilogue.
+struct ConvGeo {
+    int W = 0, H = 0;      // image size; W == 0: plain 2-D A operand
+    int C = 0;             // input channels (a multiple of BK)
+    int cblocks = 0;       // C / BK
+};
+struct ShuffleGeo {
+    int Wl = 0, Hl = 0;    // low-resolution image; Wl == 0: plain row-major store
+    int c = 0, c0 = 0;     // channels per sub-pixel, first destination channel
+};
+
+namespace {
+
+// One CTA of 128 threads computes a 128 x BN tile of D.  Plain mode: K block
+// kb of A is the TMA box at (kb * BK, m0).  Convolution mode (CONV): the M
+// tile is 128 consecutive output pixels (whole rows, or 128 pixels of one
+// row), K runs over (tap, channel block) and the A box is the input tile
+// shifted by the tap, (cb * BK, x0 + kx - 1, y0 + ky - 1, b0); TMA fills what
+// lies outside the image with zeros, which is the convolution's zero padding.
 // blockIdx.z selects a slice of kb_per_split K blocks; with more than one
 // slice each writes its FP32 partial tile to D + z * M * ldd (no bias or
 // activation) and a reduction kernel finishes.
-template <int BN, bool OUT_BF16>
+template <int BN, bool OUT_BF16, int BK, bool CONV>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, void* __restrict__ D,
-           const float* __restrict__ bias, int M, int N, int K, int ldd, int relu, int kb_per_split)
+           const float* __restrict__ bias, int M, int N, int K, int ldd, int relu, int kb_per_split, ConvGeo geo,
+           ShuffleGeo sh)
 {
-    constexpr int A_BYTES = kBM * kBK * 2;
-    constexpr int B_BYTES = BN * kBK * 2;
+    constexpr int S = stages_for<BK>();
+    constexpr int A_BYTES = kBM * BK * 2;
+    constexpr int B_BYTES = BN * BK * 2;
     constexpr int STAGE = A_BYTES + B_BYTES;
     constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
     constexpr uint32_t IDESC = idesc_bf16(kBM, BN);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + kStages * STAGE);
-    uint64_t* empty = full + kStages;
-    uint64_t* done = empty + kStages;
+    uint64_t* full = (uint64_t*)(smem + S * STAGE);
+    uint64_t* empty = full + S;
+    uint64_t* done = empty + S;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     int* status = (int*)(tmem_slot + 1);  // 0 ok, 1 timed out
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
     const int kb0 = blockIdx.z * kb_per_split;
-    const int nk = min((K + kBK - 1) / kBK - kb0, kb_per_split);  // K blocks of this slice
+    const int nk = min((K + BK - 1) / BK - kb0, kb_per_split);  // K blocks of this slice
     if (gridDim.z > 1) {
         D = (float*)D + (size_t)blockIdx.z * M * ldd;
         bias = nullptr;
         relu = 0;
     }
+    int x0 = 0, y0 = 0, b0 = 0;
+    if (CONV) {
+        x0 = m0 % geo.W;
+        y0 = (m0 / geo.W) % geo.H;
+        b0 = m0 / (geo.W * geo.H);
+    }
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -169,35 +234,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    int issued = 0;  // blocks whose loads were issued (thread 0)
+    auto load = [&](int kb, int st) {
+        uint8_t* a = smem + st * STAGE;
+        mbar_expect_tx(&full[st], STAGE);
+        if constexpr (CONV) {
+            const int tap = kb / geo.cblocks, cb = kb - tap * geo.cblocks;
+            const int ky = tap / 3, kx = tap - 3 * ky;
+            tma_load_4d(a, &tmA, cb * BK, x0 + kx - 1, y0 + ky - 1, b0, &full[st]);
+            tma_load_2d(a + A_BYTES, &tmB, tap * geo.C + cb * BK, n0, &full[st]);
+        } else {
+            tma_load_2d(a, &tmA, (kb0 + kb) * BK, m0, &full[st]);
+            tma_load_2d(a + A_BYTES, &tmB, (kb0 + kb) * BK, n0, &full[st]);
+        }
+    };
+
+    int issued = 0;    // blocks whose loads were issued (thread 0)
     int consumed = 0;  // blocks whose MMAs were issued (thread 0)
     if (threadIdx.x == 0) {
         bool ok = true;
-        for (int kb = 0; kb < nk && kb < kStages - 1; ++kb) {
-            mbar_expect_tx(&full[kb], STAGE);
-            tma_load_2d(smem + kb * STAGE, &tmA, (kb0 + kb) * kBK, m0, &full[kb]);
-            tma_load_2d(smem + kb * STAGE + A_BYTES, &tmB, (kb0 + kb) * kBK, n0, &full[kb]);
+        for (int kb = 0; kb < nk && kb < S - 1; ++kb) {
+            load(kb, kb);
             ++issued;
         }
         for (int kb = 0; kb < nk && ok; ++kb) {
-            const int pf = kb + kStages - 1;  // block to prefetch now
+            const int pf = kb + S - 1;  // block to prefetch now
             if (pf < nk) {
-                const int ps = pf % kStages;
-                if (pf >= kStages) ok = mbar_wait(&empty[ps], (uint32_t)((pf / kStages - 1) & 1));
+                const int ps = pf % S;
+                if (pf >= S) ok = mbar_wait(&empty[ps], (uint32_t)((pf / S - 1) & 1));
                 if (!ok) break;
-                mbar_expect_tx(&full[ps], STAGE);
-                tma_load_2d(smem + ps * STAGE, &tmA, (kb0 + pf) * kBK, m0, &full[ps]);
-                tma_load_2d(smem + ps * STAGE + A_BYTES, &tmB, (kb0 + pf) * kBK, n0, &full[ps]);
+                load(pf, ps);
                 ++issued;
             }
-            const int s = kb % kStages;
-            ok = mbar_wait(&full[s], (uint32_t)((kb / kStages) & 1));
+            const int s = kb % S;
+            ok = mbar_wait(&full[s], (uint32_t)((kb / S) & 1));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(smem + s * STAGE), b0 = a0 + A_BYTES;
+            const uint32_t a0 = smem_u32(smem + s * STAGE), b0s = a0 + A_BYTES;
 #pragma unroll
-            for (int k = 0; k < kBK / 16; ++k)
-                umma(tmem, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < BK / 16; ++k)
+                umma(tmem, tile_desc<BK>(a0 + k * 32), tile_desc<BK>(b0s + k * 32), IDESC,
+                     (kb > 0 || k > 0) ? 1u : 0u);
             umma_commit(&empty[s]);
             ++consumed;
         }
@@ -206,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             *status = 1;
             atomicExch(&g_gemm_error, 1);
             // drain: loads issued but never consumed, bounded
-            for (int kb = consumed; kb < issued; ++kb) mbar_wait(&full[kb % kStages], (uint32_t)((kb / kStages) & 1));
+            for (int kb = consumed; kb < issued; ++kb) mbar_wait(&full[kb % S], (uint32_t)((kb / S) & 1));
         }
     }
     __syncthreads();
@@ -216,6 +292,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (finished && *status == 0) {
         const int row = m0 + warp * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        // destination of this row: plain, or the 2 x 2 pixel shuffle of an up-convolution
+        long long rbase = (long long)row * ldd;
+        int sy = 0, sx = 0, sb = 0;
+        if (sh.Wl) {
+            sx = row % sh.Wl;
+            sy = (row / sh.Wl) % sh.Hl;
+            sb = row / (sh.Wl * sh.Hl);
+        }
 #pragma unroll 1
         for (int c = 0; c < BN; c += 16) {
             uint32_t r[16];
@@ -235,22 +319,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float x = __uint_as_float(r[j]) + ((bias && col + j < N) ? bias[col + j] : 0.0f);
                     v[j] = relu ? fmaxf(x, 0.0f) : x;
                 }
+                long long off = rbase + col;
+                if (sh.Wl) {  // 16 columns of one sub-pixel (c is a multiple of 16)
+                    const int sub = col / sh.c, co = col - sub * sh.c;
+                    const long long q = ((long long)sb * 2 * sh.Hl + 2 * sy + (sub >> 1)) * (2LL * sh.Wl) +
+                                        2 * sx + (sub & 1);
+                    off = q * ldd + sh.c0 + co;
+                }
                 if (col + 16 > N) {  // ragged last tile: element stores
                     for (int j = 0; col + j < N; ++j) {
                         if (OUT_BF16)
-                            ((__nv_bfloat16*)D)[(size_t)row * ldd + col + j] = __float2bfloat16_rn(v[j]);
+                            ((__nv_bfloat16*)D)[off + j] = __float2bfloat16_rn(v[j]);
                         else
-                            ((float*)D)[(size_t)row * ldd + col + j] = v[j];
+                            ((float*)D)[off + j] = v[j];
                     }
                 } else if (OUT_BF16) {
                     __nv_bfloat162 h[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                    uint4* dst = (uint4*)((__nv_bfloat16*)D + (size_t)row * ldd + col);
+                    uint4* dst = (uint4*)((__nv_bfloat16*)D + off);
                     dst[0] = *(uint4*)&h[0];
                     dst[1] = *(uint4*)&h[4];
                 } else {
-                    float4* dst = (float4*)((float*)D + (size_t)row * ldd + col);
+                    float4* dst = (float4*)((float*)D + off);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 }
@@ -278,35 +369,77 @@ cudaError_t encoder()
 }
 
 // 2-D tensor map of a row-major BF16 matrix [rows][ld] with K = cols valid
-// columns, box of 64 columns x box_rows rows, 128-byte swizzle, zero fill.
-cudaError_t make_map(CUtensorMap* tm, const void* ptr, int rows, int cols, int ld, int box_rows)
+// columns, box of BK columns x box_rows rows, swizzle of BK * 2 bytes, zero fill.
+cudaError_t make_map(CUtensorMap* tm, const void* ptr, int rows, int cols, int ld, int box_rows, int bk)
 {
     cudaError_t e = encoder();
     if (e != cudaSuccess) return e;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN, bool OUT_BF16>
-cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
-                      int ldd, int relu, int splits, int kb_per_split, cudaStream_t s)
+// 4-D tensor map of an NHWC BF16 image batch [B][H][W][cpitch] whose first C
+// channels are read, with the box (bk channels, bw, bh, bb) of one 128-pixel
+// tile.
+cudaError_t make_map_4d(CUtensorMap* tm, const void* ptr, int B, int H, int W, int C, int cpitch, int bw, int bh,
+                        int bb, int bk)
 {
-    constexpr int smem = kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024 + 256;
+    cudaError_t e = encoder();
+    if (e != cudaSuccess) return e;
+    cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    cuuint64_t strides[3] = {(cuuint64_t)cpitch * 2, (cuuint64_t)W * cpitch * 2, (cuuint64_t)H * W * cpitch * 2};
+    cuuint32_t box[4] = {(cuuint32_t)bk, (cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bb};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, bool OUT_BF16, int BK, bool CONV>
+cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
+                      int ldd, int relu, int splits, int kb_per_split, const ConvGeo& geo, const ShuffleGeo& sh,
+                      cudaStream_t s)
+{
+    constexpr int smem = stages_for<BK>() * (kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, OUT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, OUT_BF16, BK, CONV>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, splits);
-    k_gemm<BN, OUT_BF16><<<grid, kThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu, kb_per_split);
+    k_gemm<BN, OUT_BF16, BK, CONV><<<grid, kThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu, kb_per_split,
+                                                                geo, sh);
     return cudaGetLastError();
+}
+
+int bn_for(int N) { return N >= 256 ? 256 : N > 64 ? 128 : N > 32 ? 64 : 32; }
+
+template <int BK, bool CONV>
+cudaError_t dispatch(int bn, bool ob, const CUtensorMap& ta, const CUtensorMap& tb, void* out, const float* bias, int M,
+                     int N, int K, int ldo, int r, int splits, int kbps, const ConvGeo& geo, const ShuffleGeo& sh,
+                     cudaStream_t s)
+{
+#define NN_GEMM_CASE(BNV)                                                                                            \
+    case BNV:                                                                                                        \
+        return ob ? launch_bn<BNV, true, BK, CONV>(ta, tb, out, bias, M, N, K, ldo, r, splits, kbps, geo, sh, s)    \
+                  : launch_bn<BNV, false, BK, CONV>(ta, tb, out, bias, M, N, K, ldo, r, splits, kbps, geo, sh, s);
+    switch (bn) {
+        NN_GEMM_CASE(32)
+        NN_GEMM_CASE(64)
+        NN_GEMM_CASE(128)
+        NN_GEMM_CASE(256)
+    }
+#undef NN_GEMM_CASE
+    return cudaErrorInvalidValue;
 }
 
 // Sum of the FP32 partial tiles of a split-K GEMM, plus bias and activation.
@@ -331,7 +464,7 @@ __global__ void k_split_reduce(const float* __restrict__ part, int splits, int M
 cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,
                       int N, int K, bool out_bf16, bool relu, cudaStream_t s, int splits, float* workspace)
 {
-    const int bn = N >= 256 ? 256 : N > 64 ? 128 : N > 32 ? 64 : 32;
+    const int bn = bn_for(N);
     if (N < 8 || N % 8) return cudaErrorInvalidValue;
     if (lda % 8 || ldb % 8 || ldd % 8 || K > lda || K > ldb || N > ldd || M < 1 || K < 1) return cudaErrorInvalidValue;
     if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)D) & 15) return cudaErrorInvalidValue;
@@ -342,25 +475,15 @@ cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, i
     splits = (nkb + kb_per_split - 1) / kb_per_split;
     if (splits > 1 && !workspace) return cudaErrorInvalidValue;
     CUtensorMap ta, tb;
-    cudaError_t e = make_map(&ta, A, M, K, lda, kBM);
-    if (e == cudaSuccess) e = make_map(&tb, B, N, K, ldb, bn);
+    cudaError_t e = make_map(&ta, A, M, K, lda, kBM, kBK);
+    if (e == cudaSuccess) e = make_map(&tb, B, N, K, ldb, bn, kBK);
     if (e != cudaSuccess) return e;
     const int r = relu ? 1 : 0;
     void* out = splits > 1 ? (void*)workspace : D;
     const int ldo = splits > 1 ? N : ldd;
     const bool ob = splits > 1 ? false : out_bf16;
-#define NN_GEMM_CASE(BNV)                                                                                      \
-    case BNV:                                                                                                  \
-        e = ob ? launch_bn<BNV, true>(ta, tb, out, bias, M, N, K, ldo, r, splits, kb_per_split, s)            \
-               : launch_bn<BNV, false>(ta, tb, out, bias, M, N, K, ldo, r, splits, kb_per_split, s);          \
-        break;
-    switch (bn) {
-        NN_GEMM_CASE(32)
-        NN_GEMM_CASE(64)
-        NN_GEMM_CASE(128)
-        NN_GEMM_CASE(256)
-    }
-#undef NN_GEMM_CASE
+    e = dispatch<kBK, false>(bn, ob, ta, tb, out, bias, M, N, K, ldo, r, splits, kb_per_split, ConvGeo{}, ShuffleGeo{},
+                             s);
     if (e != cudaSuccess || splits == 1) return e;
     const long long n = (long long)M * N;
     const unsigned grid = (unsigned)((n + 255) / 256);
@@ -369,6 +492,82 @@ cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, i
     else
         k_split_reduce<false><<<grid, 256, 0, s>>>(workspace, splits, M, N, N, D, ldd, bias, r);
     return cudaGetLastError();
+}
+
+bool conv_tile(int B, int H, int W, int* bw, int* bh, int* bb)
+{
+    // a 128-pixel tile must be whole rows of whole images, in pixel order
+    if (W >= kBM) {
+        if (W % kBM) return false;
+        *bw = kBM;
+        *bh = *bb = 1;
+        return true;
+    }
+    if (kBM % W) return false;
+    *bw = W;
+    const int rows = kBM / W;
+    if (H >= rows) {
+        if (H % rows) return false;
+        *bh = rows;
+        *bb = 1;
+        return true;
+    }
+    if (rows % H) return false;
+    *bh = H;
+    *bb = rows / H;
+    (void)B;
+    return true;
+}
+
+bool conv3x3_supported(int B, int H, int W, int C)
+{
+    int bw, bh, bb;
+    return C % 32 == 0 && conv_tile(B, H, W, &bw, &bh, &bb);
+}
+
+cudaError_t conv3x3_bf16(const void* X, int B, int H, int W, int C, int cpitch, const void* Wm, int ldw, void* D,
+                         int ldd, const float* bias, int N, bool out_bf16, bool relu, cudaStream_t s)
+{
+    const int bk = C % 64 == 0 ? 64 : C % 32 == 0 ? 32 : 0;
+    int bw, bh, bb;
+    if (!bk || !conv_tile(B, H, W, &bw, &bh, &bb)) return cudaErrorNotSupported;
+    if (N < 8 || N % 8 || cpitch % 8 || C > cpitch || ldw % 8 || ldw < 9 * C || ldd % 8 || N > ldd)
+        return cudaErrorInvalidValue;
+    if (((uintptr_t)X | (uintptr_t)Wm | (uintptr_t)D) & 15) return cudaErrorInvalidValue;
+    const int bn = bn_for(N);
+    CUtensorMap ta, tb;
+    cudaError_t e = make_map_4d(&ta, X, B, H, W, C, cpitch, bw, bh, bb, bk);
+    if (e == cudaSuccess) e = make_map(&tb, Wm, N, 9 * C, ldw, bn, bk);
+    if (e != cudaSuccess) return e;
+    ConvGeo geo;
+    geo.W = W;
+    geo.H = H;
+    geo.C = C;
+    geo.cblocks = C / bk;
+    const int M = B * H * W, K = 9 * C;
+    return bk == 64 ? dispatch<64, true>(bn, out_bf16, ta, tb, D, bias, M, N, K, ldd, relu ? 1 : 0, 1, 1 << 30, geo,
+                                         ShuffleGeo{}, s)
+                    : dispatch<32, true>(bn, out_bf16, ta, tb, D, bias, M, N, K, ldd, relu ? 1 : 0, 1, 1 << 30, geo,
+                                         ShuffleGeo{}, s);
+}
+
+cudaError_t upconv2x2_bf16(const void* X, int lda, const void* Wm, int ldw, void* Y, int ypitch, int c0,
+                           const float* bias, int B, int Hl, int Wl, int cin, int c, cudaStream_t s)
+{
+    const int N = 4 * c, M = B * Hl * Wl, K = cin;
+    if (c % 16 || lda % 8 || ldw % 8 || ypitch % 8 || K > lda || K > ldw || c0 + c > ypitch) return cudaErrorInvalidValue;
+    if (((uintptr_t)X | (uintptr_t)Wm | (uintptr_t)Y) & 15) return cudaErrorInvalidValue;
+    const int bn = bn_for(N);
+    CUtensorMap ta, tb;
+    cudaError_t e = make_map(&ta, X, M, K, lda, kBM, kBK);
+    if (e == cudaSuccess) e = make_map(&tb, Wm, N, K, ldw, bn, kBK);
+    if (e != cudaSuccess) return e;
+    ShuffleGeo sh;
+    sh.Wl = Wl;
+    sh.Hl = Hl;
+    sh.c = c;
+    sh.c0 = c0;
+    return dispatch<kBK, false>(bn, true, ta, tb, Y, bias, M, N, K, ypitch, 0, 1, 1 << 30, ConvGeo{}, sh, s);
 }
 
 cudaError_t gemm_error(int* flag, bool clear)

@@ -14,6 +14,23 @@ cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, i
                       int N, int K, bool out_bf16, bool relu, cudaStream_t s, int splits = 1,
                       float* workspace = nullptr);
 
+// Implicit 3 x 3 convolution (zero padding) on tensor cores:
+// D[p][n] = act(sum over taps t and channels c < C of X[pixel p shifted by t][c]
+// * Wm[n][t * C + c] + bias[n]) with X NHWC BF16 [B][H][W][cpitch] and the
+// weight matrix Wm [N][ldw] (ldw >= 9C).  C must be a multiple of 32 and a
+// 128-pixel tile whole rows of whole images (W a multiple of 128, or a divisor
+// of 128 with matching H); cudaErrorNotSupported otherwise.
+cudaError_t conv3x3_bf16(const void* X, int B, int H, int W, int C, int cpitch, const void* Wm, int ldw, void* D,
+                         int ldd, const float* bias, int N, bool out_bf16, bool relu, cudaStream_t s);
+
+bool conv3x3_supported(int B, int H, int W, int C);
+
+// 2 x 2 stride-2 up-convolution: the GEMM of X [B*Hl*Wl][cin] with Wm [4c][cin]
+// plus bias[4c], stored BF16 straight into Y[b][2y+dy][2x+dx][c0 + co] (pitch
+// ypitch) from column (dy * 2 + dx) * c + co; c a multiple of 16.
+cudaError_t upconv2x2_bf16(const void* X, int lda, const void* Wm, int ldw, void* Y, int ypitch, int c0,
+                           const float* bias, int B, int Hl, int Wl, int cin, int c, cudaStream_t s);
+
 // Read (and optionally clear) the flag a GEMM raises when a bounded wait ran out.
 cudaError_t gemm_error(int* flag, bool clear);
 

@@ -56,7 +56,6 @@ struct Level {
     bf16* s = nullptr;     // cat_l [P][2c] (s in the first half) or, at the bottom, [P][c]
     int spitch = 0;
     bf16* pool = nullptr;  // [P/4][c]
-    bf16* u = nullptr;     // up-convolution GEMM output [P_{l+1}][4c]
     bf16* dA = nullptr;    // decoder activations [P][c]
     bf16* dD = nullptr;
     float* dcat = nullptr;  // gradient of cat_l, FP32 [P][2c]
@@ -220,7 +219,6 @@ cudaError_t allocate(lbm_unet* u)
     UN_ALLOC(u->loss, 4);
     const long long part_n = std::max<long long>((long long)kPartBlocks * (u->base + 1) * 8, P0 * u->F / 256 + 2);
     UN_ALLOC(u->part, std::max<long long>(part_n, (long long)kPartBlocks * 4 * (u->base << (u->L - 1))));
-    long long col_n = 0, ws_n = 0, t_n = 0, g_n = 0;
     const int L = u->L;
     for (int l = 0; l < L; ++l) {
         Level& v = u->lv[l];
@@ -231,32 +229,60 @@ cudaError_t allocate(lbm_unet* u)
             v.spitch = 2 * c;
             UN_ALLOC(v.s, P * 2 * c);
             UN_ALLOC(v.pool, P / 4 * c);
-            UN_ALLOC(v.u, P / 4 * 4 * c);
             UN_ALLOC(v.dA, P * c);
             UN_ALLOC(v.dD, P * c);
-            UN_ALLOC(v.dcat, P * 2 * c);
         } else {
             v.spitch = c;
             UN_ALLOC(v.s, P * c);
         }
+        for (Conv* cv : {&v.ea, &v.eb, &v.da, &v.db})
+            if (cv->cout) UN_ALLOC(cv->wf, 9LL * cv->cin * cv->cout);
+        if (v.up.cout) UN_ALLOC(v.up.wt, 8LL * c * c);
+    }
+    // gathered-copy buffer for the convolutions the implicit kernel does not
+    // take (the first one, 8 input channels; any level of an odd image size)
+    long long col_n = 9LL * P0 * kInPitch;
+    for (const Level& v : u->lv)
+        for (const Conv* cv : {&v.ea, &v.eb, &v.da, &v.db})
+            if (cv->cout && !nn::conv3x3_supported(u->B, v.H, v.W, cv->cin)) col_n = std::max(col_n, 9 * v.P * cv->cin);
+    UN_ALLOC(u->col, col_n);
+#undef UN_ALLOC
+    return e;
+}
+
+// Buffers only training needs, allocated at the first backward pass.
+cudaError_t allocate_backward(lbm_unet* u)
+{
+    if (u->ws) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define UN_ALLOC(p, n)                           \
+    do {                                         \
+        if ((e = alloc(u, &(p), (n)))) return e; \
+    } while (0)
+    long long col_n = 9LL * u->P0 * kInPitch, ws_n = 0, t_n = 0, g_n = u->P0 * u->base;
+    const int L = u->L;
+    for (int l = 0; l < L; ++l) {
+        Level& v = u->lv[l];
+        const long long P = v.P;
+        const int c = v.c;
+        if (l < L - 1) UN_ALLOC(v.dcat, P * 2 * c);
         for (Conv* cv : {&v.ea, &v.eb, &v.da, &v.db}) {
             if (!cv->cout) continue;
             col_n = std::max(col_n, 9 * P * std::max(cv->cin, cv->cout));
             ws_n = std::max(ws_n, split_ws(cv->cout, 9 * cv->cin, P));
             t_n = std::max(t_n, P * std::max(cv->cout, cv->cin));
             g_n = std::max(g_n, P * std::max(cv->cout, cv->cin));
-            UN_ALLOC(cv->wf, 9LL * cv->cin * cv->cout);
         }
         if (v.up.cout) {
             const long long Pl = P / 4;
             ws_n = std::max(ws_n, split_ws(4 * c, 2 * c, Pl));
             t_n = std::max(t_n, Pl * 4 * c);
             g_n = std::max(g_n, Pl * 4 * c);
-            UN_ALLOC(v.up.wt, 8LL * c * c);
         }
     }
-    g_n = std::max(g_n, P0 * u->base);
-    UN_ALLOC(u->col, col_n);
+    bf16* col = nullptr;
+    UN_ALLOC(col, col_n);
+    u->col = col;  // the forward's smaller buffer stays allocated until destroy
     UN_ALLOC(u->colT, col_n);
     UN_ALLOC(u->tA, t_n);
     UN_ALLOC(u->tB, t_n);
@@ -291,8 +317,11 @@ cudaError_t derive(lbm_unet* u)
 cudaError_t conv_fwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in, int inpitch, bf16* out,
                      int outpitch)
 {
-    cudaError_t e = nn::im2col3x3(in, u->B, v.H, v.W, cv.cin, inpitch, u->col, u->s);
-    if (e) return e;
+    cudaError_t e = nn::conv3x3_bf16(in, u->B, v.H, v.W, cv.cin, inpitch, u->wb + cv.w, 9 * cv.cin, out, outpitch,
+                                     u->w + cv.b, cv.cout, true, true, u->s);
+    if (e != cudaErrorNotSupported) return e;
+    // layouts the implicit convolution does not take (cin = 8): gathered copy + GEMM
+    if ((e = nn::im2col3x3(in, u->B, v.H, v.W, cv.cin, inpitch, u->col, u->s))) return e;
     return nn::gemm_bf16(u->col, 9 * cv.cin, u->wb + cv.w, 9 * cv.cin, out, outpitch, u->w + cv.b, (int)v.P, cv.cout,
                          9 * cv.cin, true, true, u->s);
 }
@@ -315,6 +344,9 @@ cudaError_t conv_bwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in
         return e;
     if ((e = nn::colsum(dY, false, P, cv.cout, cv.cout, u->g + cv.b, u->part, kPartBlocks, u->s))) return e;
     if (!dx) return cudaSuccess;
+    e = nn::conv3x3_bf16(dY, u->B, v.H, v.W, cv.cout, cv.cout, cv.wf, 9 * cv.cout, dx, dxpitch, nullptr, cv.cin, false,
+                         false, u->s);
+    if (e != cudaErrorNotSupported) return e;
     if ((e = nn::im2col3x3(dY, u->B, v.H, v.W, cv.cout, cv.cout, u->col, u->s))) return e;
     return nn::gemm_bf16(u->col, 9 * cv.cout, cv.wf, 9 * cv.cout, dx, dxpitch, nullptr, (int)P, cv.cin, 9 * cv.cout,
                          false, false, u->s);
@@ -350,10 +382,9 @@ cudaError_t forward(lbm_unet* u, const float* x)
         Level& v = u->lv[l];
         const Level& lo = u->lv[l + 1];
         const int c = v.c;
-        if ((e = nn::gemm_bf16(h, 2 * c, u->wb + v.up.w, 2 * c, v.u, 4 * c, u->w + v.up.b, (int)lo.P, 4 * c, 2 * c,
-                               true, false, u->s)))
+        if ((e = nn::upconv2x2_bf16(h, 2 * c, u->wb + v.up.w, 2 * c, v.s, 2 * c, c, u->w + v.up.b, u->B, lo.H, lo.W,
+                                    2 * c, c, u->s)))
             return e;
-        if ((e = nn::shuffle_fwd(v.u, u->B, lo.H, lo.W, c, v.s, 2 * c, c, u->s))) return e;
         if ((e = conv_fwd(u, v, v.da, v.s, 2 * c, v.dA, c))) return e;
         if ((e = conv_fwd(u, v, v.db, v.dA, c, v.dD, c))) return e;
         h = v.dD;
@@ -471,6 +502,16 @@ int lbm_unet_set_stream(lbm_unet* u, void* stream)
 
 long long lbm_unet_param_count(const lbm_unet* u) { return u ? u->n_packed : -1; }
 
+int lbm_unet_shape(const lbm_unet* u, int* batch, int* height, int* width, int* fields)
+{
+    if (!u || !batch || !height || !width || !fields) return LBM_EINVAL;
+    *batch = u->B;
+    *height = u->H;
+    *width = u->W;
+    *fields = u->F;
+    return LBM_OK;
+}
+
 long long lbm_unet_device_bytes(const lbm_unet* u) { return u ? u->bytes : -1; }
 
 int lbm_unet_set_params(lbm_unet* u, const float* host)
@@ -529,6 +570,7 @@ int lbm_unet_forward(lbm_unet* u, const float* x, float* y)
 int lbm_unet_backward(lbm_unet* u, const float* x, const float* target)
 {
     if (!u || !x || !target) return LBM_EINVAL;
+    UN_CHECK(u, allocate_backward(u));
     UN_CHECK(u, forward(u, x));
     UN_CHECK(u, backward(u, target));
     return LBM_OK;

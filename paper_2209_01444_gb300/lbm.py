@@ -44,6 +44,11 @@ class lbm_seed(ct.Structure):
     _fields_ = [("x", ct.c_double), ("y", ct.c_double), ("R", ct.c_double), ("orient", ct.c_double)]
 
 
+class lbm_surrogate_report(ct.Structure):
+    _fields_ = [("audited", ct.c_int), ("accepted", ct.c_int), ("tip_err", ct.c_double),
+                ("tip", ct.c_double * 3), ("mismatch", ct.c_longlong), ("max_dphi", ct.c_double)]
+
+
 class lbm_metrics(ct.Structure):
     _fields_ = [("tip", ct.c_double * 3), ("solid_fraction", ct.c_double), ("sum_C", ct.c_double),
                 ("sum_H", ct.c_double), ("sum_h", ct.c_double), ("max_u", ct.c_double),
@@ -111,6 +116,11 @@ SIGNATURES = {
                                    ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
                                    ct.c_void_p]),
     "lbm_nn_flip3x3": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
+    "lbm_nn_conv3x3": (ct.c_int, [ct.c_void_p] + [ct.c_int] * 5 + [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int,
+                                                                    ct.c_void_p, ct.c_int, ct.c_int, ct.c_int,
+                                                                    ct.c_void_p]),
+    "lbm_nn_upconv2x2": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int,
+                                    ct.c_void_p] + [ct.c_int] * 5 + [ct.c_void_p]),
     "lbm_unet_create": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]),
     "lbm_unet_destroy": (None, [ct.c_void_p]),
     "lbm_unet_set_stream": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
@@ -127,6 +137,14 @@ SIGNATURES = {
     "lbm_unet_loss": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_output": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_last_error": (ct.c_char_p, [ct.c_void_p]),
+    "lbm_unet_shape": (ct.c_int, [ct.c_void_p] + [ct.POINTER(ct.c_int)] * 4),
+    "lbm_snapshot_save": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "lbm_snapshot_restore": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "lbm_fields_nhwc": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbm_set_fields_nhwc": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbm_batch_fields_nhwc": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p]),
+    "lbm_surrogate_advance": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_double,
+                                         ct.c_double, ct.c_double, ct.c_void_p]),
     "lbm_nn_colsum": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_longlong, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p,
                                  ct.c_int, ct.c_void_p]),
     "lbm_nn_mse": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_longlong, ct.c_void_p, ct.c_void_p, ct.c_void_p,
@@ -279,6 +297,37 @@ class Simulation:
                 "sum_C": m.sum_C, "sum_H": m.sum_H, "sum_h": m.sum_h, "max_u": m.max_u,
                 "nonfinite": m.nonfinite, "sum_phi": m.sum_phi, "step": m.step, "rc": rc}
 
+    # ---- device-side exchange with the surrogate network
+    def snapshot_save(self, slot: int = 0) -> None:
+        self._check(self.lib.lbm_snapshot_save(self.h, slot))
+
+    def snapshot_restore(self, slot: int = 0) -> None:
+        self._check(self.lib.lbm_snapshot_restore(self.h, slot))
+
+    def fields_nhwc(self, out=None):
+        """Device FP32 tensor [ny, nx, 5] of phi, C, theta, u_x, u_y."""
+        import torch
+
+        if out is None:
+            out = torch.empty(self.ny, self.nx, 5, dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == self.ny * self.nx * 5
+        self._check(self.lib.lbm_fields_nhwc(self.h, ct.c_void_p(out.data_ptr())))
+        return out
+
+    def set_fields_nhwc(self, src) -> None:
+        import torch
+
+        assert src.is_cuda and src.dtype == torch.float32 and src.is_contiguous() and src.numel() == self.ny * self.nx * 5
+        self._check(self.lib.lbm_set_fields_nhwc(self.h, ct.c_void_p(src.data_ptr())))
+
+    def surrogate_advance(self, net, K: int, tip_tol: float, audit: bool, cx: float, cy: float,
+                          orient: float = 0.0) -> dict:
+        rep = lbm_surrogate_report()
+        self._check(self.lib.lbm_surrogate_advance(self.h, net.h, K, tip_tol, 1 if audit else 0, cx, cy, orient,
+                                                   ct.byref(rep)))
+        return {"audited": bool(rep.audited), "accepted": bool(rep.accepted), "tip_err": rep.tip_err,
+                "tip": tuple(rep.tip), "mismatch": rep.mismatch, "max_dphi": rep.max_dphi}
+
     def set_profiling(self, enable: bool) -> None:
         self._check(self.lib.lbm_set_profiling(self.h, int(enable)))
 
@@ -367,6 +416,17 @@ class Batch:
         out = np.empty((len(order), ny, nx))
         self._check(self.lib.lbm_batch_get_fields(self.h, dom, mask, _dptr(out)))
         return {n: out[i] for i, n in enumerate(order)}
+
+    def fields_nhwc(self, dom: int, out):
+        """Writes domain `dom`'s phi, C, theta, u_x, u_y into the device FP32
+        tensor `out` [ny, nx, 5]."""
+        import torch
+
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        p = self.params[dom]
+        assert out.numel() == int(p["nx"]) * int(p["ny"]) * 5
+        self._check(self.lib.lbm_batch_fields_nhwc(self.h, dom, ct.c_void_p(out.data_ptr())))
+        return out
 
     def metrics(self, dom: int, cx: float, cy: float, orient: float = 0.0) -> dict:
         m = lbm_metrics()

@@ -8,6 +8,7 @@ used for device memory and streams only.
 from __future__ import annotations
 
 import ctypes as ct
+import math
 
 import numpy as np
 
@@ -150,3 +151,113 @@ class UNet:
         out = ct.c_double()
         self._check(self.lib.lbm_unet_loss(self.h, ct.byref(out)))
         return out.value
+
+
+# ---------------------------------------------------------------- training
+def make_dataset(cases, K: int, windows: int, warm: int = 0, storage: str = "fp32"):
+    """Runs the cases (equal grid sizes) as one batched LB launch and records
+    the fields every K steps after `warm` steps.  Returns device tensors x, t
+    [windows * len(cases), ny, nx, 5] of consecutive snapshots (t is x advanced
+    by K steps)."""
+    import torch
+
+    ny, nx = int(cases[0].params["ny"]), int(cases[0].params["nx"])
+    assert all(int(c.params["ny"]) == ny and int(c.params["nx"]) == nx for c in cases)
+    b = L.Batch([c.params for c in cases], storage=storage)
+    for d, c in enumerate(cases):
+        b.init_seeds(d, c.seeds, c.U0, c.theta0)
+    if warm:
+        b.step(warm)
+    D = len(cases)
+    snaps = torch.empty(windows + 1, D, ny, nx, 5, dtype=torch.float32, device="cuda")
+    for w in range(windows + 1):
+        for d in range(D):
+            b.fields_nhwc(d, snaps[w, d])
+        if w < windows:
+            b.step(K)
+    b.synchronize()
+    x = snaps[:-1].reshape(windows * D, ny, nx, 5)
+    t = snaps[1:].reshape(windows * D, ny, nx, 5)
+    return x, t
+
+
+def normalisation(x, t, floor: float = 1e-4):
+    """Per-field mean of the inputs and standard deviation of the K-step
+    increments (so that every field's increment weighs alike in the loss)."""
+    step = max(1, x.shape[0] // 64)
+    xs = x[::step].cpu().numpy().astype(np.float64).reshape(-1, 5)
+    ds = t[::step].cpu().numpy().astype(np.float64).reshape(-1, 5) - xs
+    mean = xs.mean(axis=0)
+    std = np.maximum(ds.std(axis=0), floor)
+    return mean.astype(np.float32), std.astype(np.float32)
+
+
+def train(net: UNet, x, t, steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 0):
+    """Adam on random mini-batches of (x, t) pairs (batch = the network's
+    batch); cosine decay of the learning rate to a tenth.  Returns the loss
+    history [(step, loss)] read every log_every steps."""
+    import torch
+
+    B = net.shape[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xb = torch.empty(net.shape, dtype=torch.float32, device="cuda")
+    tb = torch.empty_like(xb)
+    hist = []
+    n = x.shape[0]
+    for it in range(steps):
+        idx = rng.integers(0, n, B)
+        for j, i in enumerate(idx):  # device-to-device copies
+            xb[j].copy_(x[int(i)])
+            tb[j].copy_(t[int(i)])
+        a = lr * (0.1 + 0.9 * 0.5 * (1.0 + math.cos(math.pi * it / max(1, steps))))
+        net.train_step(xb, tb, a)
+        if log_every and (it % log_every == 0 or it == steps - 1):
+            hist.append((it, net.loss()))
+    return hist
+
+
+def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: int, backoff: int,
+            cx: float, cy: float, orient: float = 0.0):
+    """Surrogate-accelerated run of `windows` windows of K steps.
+
+    Policy: the network advances windows; every audit_every-th window is also
+    run by the plain LB from the same state (the LB result is kept).  If the
+    audit's tip error exceeds tip_tol, the state returns to the snapshot taken
+    at the previous passed audit, every window since is re-run by the LB, and
+    the network sits out the next `backoff` windows.  Returns counts."""
+    st = {"surrogate": 0, "audited": 0, "rejected": 0, "lb_rerun": 0, "lb_backoff": 0, "tip_err": []}
+    sim.snapshot_save(0)
+    since, off = 0, 0
+    w = 0
+    while w < windows:
+        if off > 0:
+            sim.step(K)
+            st["lb_backoff"] += 1
+            off -= 1
+            w += 1
+            if off == 0:
+                sim.snapshot_save(0)
+                since = 0
+            continue
+        audit = since + 1 >= audit_every or w == windows - 1
+        rep = sim.surrogate_advance(net, K, tip_tol, audit, cx, cy, orient)
+        w += 1
+        if not audit:
+            st["surrogate"] += 1
+            since += 1
+            continue
+        st["audited"] += 1
+        st["tip_err"].append(rep["tip_err"])
+        if rep["accepted"]:
+            sim.snapshot_save(0)
+            since = 0
+        else:
+            st["rejected"] += 1
+            st["surrogate"] -= since
+            sim.snapshot_restore(0)
+            sim.step(K * (since + 1))
+            st["lb_rerun"] += since
+            off = backoff
+            sim.snapshot_save(0)
+            since = 0
+    return st

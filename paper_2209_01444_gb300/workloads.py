@@ -224,3 +224,26 @@ def unet_params(shapes, rng_seed: int, out_scale: float = 0.01) -> dict:
         else:
             out[name] = bf16_exact(rng.normal(0.0, 0.01, shape))
     return out
+
+
+def surrogate_domains(count: int = 32, n: int = 256, rng_seed: int = 5, steps: int = 4000) -> list[Case]:
+    """Training trajectories for the surrogate: n x n domains in the forced-flow
+    geometry (inflow left, outflow right, symmetry top and bottom) with the
+    parameters drawn as in the batched-domain workload: Delta in [0.45, 0.65],
+    eps in [0.03, 0.06], inflow u_x in [0, 0.02] lattice units, one seed of
+    radius 6-12 near (0.375 n, 0.5 n); half the seeds at orientation 0 (the
+    forced-flow case), half in [0, 45 deg)."""
+    rng = np.random.Generator(np.random.PCG64(rng_seed))
+    cases = []
+    for j in range(count):
+        delta = float(rng.uniform(0.45, 0.65))
+        eps = float(rng.uniform(0.03, 0.06))
+        uin = float(rng.uniform(0.0, 0.02))
+        orient = 0.0 if j % 2 == 0 else float(rng.uniform(0.0, math.pi / 4))
+        cx = 0.375 * n + float(rng.uniform(-0.05, 0.05)) * n
+        cy = 0.5 * n + float(rng.uniform(-0.05, 0.05)) * n
+        R = float(rng.uniform(6.0, 12.0))
+        p = thermosolutal_params(n, n, eps_s=eps, theta_ref=-delta, bc=("inflow", "outflow", "symmetry", "symmetry"),
+                                 u_in=(uin * DX / DT, 0.0))
+        cases.append(Case(f"surrogate_{j}_{n}", p, np.array([[cx, cy, R, orient]]), 0.0, -delta, steps))
+    return cases

@@ -250,3 +250,63 @@ def test_pack_unpack_cast(env):
     assert lib.lbm_nn_cast_bf16(_p(A), 300, 33, 40, _p(Bt), 48, s) == 0
     torch.cuda.synchronize()
     assert torch.equal(Bt[:, :33], A[:, :33].to(torch.bfloat16)) and bool((Bt[:, 33:] == 0).all())
+
+
+@pytest.mark.parametrize("B,H,W,C,cp,N", [(2, 16, 16, 32, 32, 32), (1, 8, 256, 64, 128, 128), (3, 8, 8, 64, 64, 72),
+                                          (1, 4, 4, 96, 96, 64), (2, 32, 32, 128, 128, 256), (1, 2, 2, 512, 512, 512),
+                                          (4, 64, 64, 32, 64, 40)])
+@pytest.mark.parametrize("out_fp32", [1, 0])
+def test_implicit_conv3x3_matches_fp64_conv2d(env, B, H, W, C, cp, N, out_fp32):
+    """The implicit convolution (4-D TMA tap shifts, zero padding from the
+    out-of-bounds fill) against a CPU FP64 conv2d of the same BF16 values,
+    over tiles of whole rows, several rows and several images, 64- and 32-
+    channel K blocks, channel pitches wider than C and ragged N."""
+    torch, lib = env
+    g = torch.Generator(device="cuda").manual_seed(B * 1000 + H * 10 + C + N)
+    X = _bf(torch, (B, H, W, cp), g)
+    Wm = _bf(torch, (N, 9 * C), g, scale=1.0 / (3.0 * C ** 0.5))
+    bias = torch.randn(N, generator=g, device="cuda")
+    D = torch.full((B * H * W, N + 8), 3.0, dtype=torch.float32 if out_fp32 else torch.bfloat16, device="cuda")
+    for relu in (0, 1):
+        rc = lib.lbm_nn_conv3x3(_p(X), B, H, W, C, cp, _p(Wm), 9 * C, _p(D), N + 8, _p(bias), N, out_fp32, relu,
+                                _stream(torch))
+        assert rc == 0
+        torch.cuda.synchronize()
+        assert lib.lbm_nn_error(1) == 0
+        x = X[..., :C].double().cpu().permute(0, 3, 1, 2)
+        w = Wm.double().cpu().reshape(N, 3, 3, C).permute(0, 3, 1, 2)
+        ref = torch.nn.functional.conv2d(x, w, bias.double().cpu(), padding=1).permute(0, 2, 3, 1).reshape(-1, N)
+        if relu:
+            ref = ref.clamp(min=0.0)
+        got = D[:, :N].double().cpu()
+        err = float((got - ref).abs().max())
+        tol = (2e-5 if out_fp32 else 8e-3) * float(ref.abs().max())
+        assert err <= tol, (B, H, W, C, N, relu, err)
+        assert bool((D[:, N:].float() == 3.0).all())
+
+
+def test_implicit_conv3x3_rejects_unsupported_tiles(env):
+    torch, lib = env
+    X = torch.zeros(1, 48, 48, 32, dtype=torch.bfloat16, device="cuda")
+    Wm = torch.zeros(32, 288, dtype=torch.bfloat16, device="cuda")
+    D = torch.zeros(48 * 48, 32, device="cuda")
+    assert lib.lbm_nn_conv3x3(_p(X), 1, 48, 48, 32, 32, _p(Wm), 288, _p(D), 32, None, 32, 1, 0, None) != 0  # W = 48
+    assert lib.lbm_nn_conv3x3(_p(X), 1, 16, 16, 24, 32, _p(Wm), 288, _p(D), 32, None, 32, 1, 0, None) != 0  # C = 24
+
+
+@pytest.mark.parametrize("B,Hl,Wl,cin,c", [(2, 4, 4, 64, 32), (1, 16, 32, 128, 64), (3, 2, 2, 512, 256)])
+def test_upconv2x2_shuffle_epilogue(env, B, Hl, Wl, cin, c):
+    torch, lib = env
+    g = torch.Generator(device="cuda").manual_seed(B + Hl + cin)
+    X = _bf(torch, (B * Hl * Wl, cin), g)
+    Wm = _bf(torch, (4 * c, cin), g, scale=cin ** -0.5)
+    bias = torch.randn(4 * c, generator=g, device="cuda")
+    Y = torch.full((B, 2 * Hl, 2 * Wl, 2 * c), 5.0, dtype=torch.bfloat16, device="cuda")
+    assert lib.lbm_nn_upconv2x2(_p(X), cin, _p(Wm), cin, _p(Y), 2 * c, c, _p(bias), B, Hl, Wl, cin, c,
+                                _stream(torch)) == 0
+    torch.cuda.synchronize()
+    U = X.double().cpu() @ Wm.double().cpu().T + bias.double().cpu()
+    ref = U.reshape(B, Hl, Wl, 2, 2, c).permute(0, 1, 3, 2, 4, 5).reshape(B, 2 * Hl, 2 * Wl, c)
+    err = float((Y[..., c:].double().cpu() - ref).abs().max())
+    assert err <= 8e-3 * float(ref.abs().max())
+    assert bool((Y[..., :c] == 5.0).all())
