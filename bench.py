@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-domain leg")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
+    ap.add_argument("--surrogate-train-steps", type=int, default=1500)
+    ap.add_argument("--surrogate-windows", type=int, default=40)
     return ap.parse_args()
 
 
@@ -288,6 +291,92 @@ def batch_leg(lbm, torch, stream, steps, world, max_over_ranks, barrier):
             "nonfinite_domains_of_first_8": bad}
 
 
+def surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, train_steps: int = 1500, windows: int = 40,
+                  warm: int = 2000, domains: int = 12, side: int = 512, data_windows: int = 60, data_warm: int = 1000,
+                  batch: int = 4, lr: float = 1e-3, audit_every: int = 4):
+    """The learned surrogate against the plain LB on the forced-flow case
+    (1024^2, one seed, inflow u_x = 0.01): trained here on (t, t + 50) pairs of
+    LB trajectories (`domains` domains of side^2, half with the forced-flow
+    parameters, half drawn), then run for `windows` windows of K = 50 steps
+    after `warm` LB steps, auditing every audit_every-th window against the LB
+    (tip tolerance 1 lattice unit, back-off 4 windows).  Reports the wall time
+    of both runs on the device clock, the final tip difference and the window
+    counts."""
+    from paper_2209_01444_gb300 import surrogate as S, workloads as W
+
+    K = 50
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    cases = W.surrogate_domains(count=domains, n=side, rng_seed=5)
+    x, t = S.make_dataset(cases, K=K, windows=data_windows, warm=data_warm)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    mean, std_in, std_out = S.normalisation(x, t)
+    net = S.UNet(batch, side, side, stream=stream)
+    net.set_params(W.unet_params(S.param_shapes(), 3))
+    net.set_norm(mean, std_in, std_out)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    hist = S.train(net, x, t, steps=train_steps, lr=lr, seed=1, log_every=max(1, train_steps // 10))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = ev0.elapsed_time(ev1)
+    params = net.params()
+    del net, x, t
+    case = W.forced_flow(1024)
+    cx, cy = float(case.seeds[0][0]), float(case.seeds[0][1])
+    ev = S.UNet(1, 1024, 1024, stream=stream)
+    ev.set_params(params)
+    ev.set_norm(mean, std_in, std_out)
+
+    def fresh():
+        s_ = lbm.Simulation(case.params, "fp32", stream=stream)
+        s_.init_seeds(case.seeds, case.U0, case.theta0)
+        s_.step(warm)
+        return s_
+
+    ref, sur = fresh(), fresh()
+    torch.cuda.synchronize()
+    barrier()
+    ev0.record(stream)
+    ref.step(K * windows)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    lb_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    ev0.record(stream)
+    st = S.rollout(sur, ev, windows, K, 1.0, audit_every=audit_every, backoff=4, cx=cx, cy=cy)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sur_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    mr, ms_ = ref.metrics(cx, cy), sur.metrics(cx, cy, check=False)
+    tip_err = max(abs(mr[k] - ms_[k]) for k in ("tip_px", "tip_mx", "tip_py"))
+    xin = sur.fields_nhwc().reshape(1, 1024, 1024, 5)
+    yout = torch.empty_like(xin)
+    for _ in range(3):
+        ev.forward(xin, yout)
+    ev0.record(stream)
+    for _ in range(10):
+        ev.forward(xin, yout)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / 10
+    return {
+        "workload": "forced_flow 1024x1024, one seed, inflow u_x = 0.01; K = 50 steps per window",
+        "windows": windows, "warm_lb_steps": warm,
+        "lb_ms": lb_ms, "surrogate_ms": sur_ms, "speedup_vs_plain_lb": lb_ms / sur_ms,
+        "final_tip_error_lu": tip_err, "tip_tolerance_lu": 1.0,
+        "windows_by_network": st["surrogate"], "audited": st["audited"], "rejected_audits": st["rejected"],
+        "lb_reruns": st["lb_rerun"], "lb_backoff": st["lb_backoff"],
+        "audit_tip_errors_lu": [round(v, 3) for v in st["tip_err"]],
+        "network_forward_ms_1024": fwd_ms, "lb_ms_per_window": lb_ms / windows,
+        "audit_every": audit_every,
+        "training": {"data": f"{domains} domains {side}^2 (forced-flow geometry; half the forced-flow parameters, "
+                             f"half drawn; seed 5), {data_windows} windows after {data_warm} steps",
+                     "pairs": int(data_windows * domains), "data_s": t_data, "steps": train_steps, "batch": batch,
+                     "lr": lr, "ms": train_ms, "loss_first_last": [hist[0][1], hist[-1][1]]},
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -406,6 +495,11 @@ def main():
     if not args.no_batch:
         batch = batch_leg(lbm, torch, stream, args.steps, world, max_over_ranks, barrier)
 
+    surrogate = None
+    if not args.no_surrogate:
+        surrogate = surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, args.surrogate_train_steps,
+                                  args.surrogate_windows)
+
     if rank != 0:
         return
     cpu = None
@@ -432,6 +526,7 @@ def main():
         "cpu_baseline": cpu,
         "variants": variants,
         "batch": batch,
+        "surrogate": surrogate,
         "metrics_after_run": {"solid_fraction": m["solid_fraction"], "tip_px": m["tip_px"]},
     }
     print(json.dumps(line))

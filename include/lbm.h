@@ -366,9 +366,10 @@ LBM_API int lbm_nn_cast_bf16(const float* a, long long rows, int C, int apitch, 
  * (dy*2+dx)*c+co and bias [4c]; out.W [fields][base], out.b [fields].
  *
  * Fields x, targets and predictions are FP32 device arrays [batch][height]
- * [width][fields].  The network works in normalised units (x - mean)/std
- * (lbm_unet_set_norm; default mean 0, std 1); the loss is the mean squared
- * error in normalised units.  All calls queue work on the object's stream and
+ * [width][fields].  The network reads the inputs as (x - mean)/std_in and its
+ * output is the increment in units of std_out: the prediction is
+ * y = x + std_out * out (lbm_unet_set_norm; default mean 0, both scales 1);
+ * the loss is the mean squared error of out against (target - x)/std_out.  All calls queue work on the object's stream and
  * return without waiting, except set_params, get_params, get_grads, set_norm
  * and loss, which synchronise.  Errors: LBM_EINVAL for bad arguments,
  * LBM_ENOMEM / LBM_ECUDA from CUDA; lbm_unet_last_error gives the reason. */
@@ -383,7 +384,7 @@ LBM_API int lbm_unet_set_params(lbm_unet* u, const float* host);
 LBM_API int lbm_unet_get_params(lbm_unet* u, float* host);
 /* Gradients of the loss from the last lbm_unet_backward / train_step. */
 LBM_API int lbm_unet_get_grads(lbm_unet* u, float* host);
-LBM_API int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_);
+LBM_API int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_in, const float* std_out);
 /* Prediction y (physical units, may be NULL) for the fields x. */
 LBM_API int lbm_unet_forward(lbm_unet* u, const float* x, float* y);
 /* Forward, loss against `target` and the gradients of every parameter. */
@@ -393,9 +394,9 @@ LBM_API int lbm_unet_backward(lbm_unet* u, const float* x, const float* target);
 LBM_API int lbm_unet_adam(lbm_unet* u, float lr, float beta1, float beta2, float eps);
 /* backward + adam(lr, 0.9, 0.999, 1e-8). */
 LBM_API int lbm_unet_train_step(lbm_unet* u, const float* x, const float* target, float lr);
-/* Mean squared error of the last backward (normalised units). */
+/* Mean squared error of the last backward (output units). */
 LBM_API int lbm_unet_loss(lbm_unet* u, double* out);
-/* Copies the last prediction in normalised units (FP32 device array). */
+/* Copies the last network output (the increment in units of std_out). */
 LBM_API int lbm_unet_output(lbm_unet* u, float* y_norm);
 LBM_API const char* lbm_unet_last_error(const lbm_unet* u);
 LBM_API int lbm_unet_shape(const lbm_unet* u, int* batch, int* height, int* width, int* fields);
@@ -412,10 +413,13 @@ LBM_API int lbm_snapshot_restore(lbm_handle* h, int slot);
  * phi, C, theta, u_x, u_y (the paper's units), for the surrogate network;
  * and the reverse: every node's populations replaced by the equilibrium of
  * the given fields (phi clamped to [-1, 1], U recovered from C and phi, the
- * node's pressure kept; history reset to the new macros).  Both queue on the
- * handle's stream. */
+ * node's pressure kept; the stored flow momentum chosen so that the recovered
+ * velocity, with the forcing and the fluid-solid force, is the given one).
+ * With prev (the fields K steps earlier, same layout) the history is set one
+ * step back on the line between prev and src; with prev NULL it equals the
+ * new macros.  Both queue on the handle's stream. */
 LBM_API int lbm_fields_nhwc(lbm_handle* h, float* dst);
-LBM_API int lbm_set_fields_nhwc(lbm_handle* h, const float* src);
+LBM_API int lbm_set_fields_nhwc(lbm_handle* h, const float* src, const float* prev, int K);
 LBM_API int lbm_batch_fields_nhwc(lbm_batch* b, int dom, float* dst);
 
 /* One surrogate window of K steps (the paper has no counterpart).  The network

@@ -735,13 +735,14 @@ int lbm_fields_nhwc(lbm_handle* h, float* dst)
     return LBM_OK;
 }
 
-int lbm_set_fields_nhwc(lbm_handle* h, const float* src)
+int lbm_set_fields_nhwc(lbm_handle* h, const float* src, const float* prev, int K)
 {
     int rc = ensure_initialised(h);
     if (rc) return rc;
     if (!src) return fail(h, LBM_EINVAL, "src is NULL");
+    if (prev && K < 1) return fail(h, LBM_EINVAL, "K must be >= 1 with prev");
     LBM_CUDA(h, lbm::launch_set_fields_nhwc(h->P, h->storage, src, (float)h->vf, h->B.sc[h->B.cs], h->B.fl[h->B.cf],
-                                            h->B.hist, h->stream));
+                                            h->B.hist, prev, K, h->stream));
     return LBM_OK;
 }
 
@@ -781,7 +782,7 @@ int lbm_surrogate_advance(lbm_handle* h, lbm_unet* net, int K, double tip_tol, i
     if ((rc = lbm_unet_forward(net, h->sur_x, h->sur_y)))
         return fail(h, rc, std::string("network: ") + lbm_unet_last_error(net));
     if (!audit) {
-        if ((rc = lbm_set_fields_nhwc(h, h->sur_y))) return rc;
+        if ((rc = lbm_set_fields_nhwc(h, h->sur_y, nullptr, 0))) return rc;
         h->steps += K;
         return LBM_OK;
     }
@@ -793,7 +794,7 @@ int lbm_surrogate_advance(lbm_handle* h, lbm_unet* net, int K, double tip_tol, i
     double tl[3], ts[3];
     if ((rc = tips_now(h, cx, cy, orient, tl))) return rc;
     if ((rc = lbm_snapshot_save(h, 1))) return rc;
-    if ((rc = lbm_set_fields_nhwc(h, h->sur_y))) return rc;
+    if ((rc = lbm_set_fields_nhwc(h, h->sur_y, nullptr, 0))) return rc;
     rc = tips_now(h, cx, cy, orient, ts);
     const int rr = lbm_snapshot_restore(h, 1);
     if (rc == LBM_ENUMERIC) {

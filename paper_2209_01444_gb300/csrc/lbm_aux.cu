@@ -69,7 +69,8 @@ __global__ void k_seed_fields(const StepParams P, const double* __restrict__ see
 // differences vanish).
 template <class Store>
 __device__ void init_node(const StepParams& P, long long o, float p1, float dC, float Uf, float dth, float ux,
-                          float uy, float p, void* __restrict__ sc, void* __restrict__ fl, float* __restrict__ hist)
+                          float uy, float p, void* __restrict__ sc, void* __restrict__ fl, float* __restrict__ hist,
+                          float heqx, float heqy)
 {
     const long long plane = P.plane;
     const float hp1 = h_plus_1(P.h_kind, p1);
@@ -86,7 +87,7 @@ __device__ void init_node(const StepParams& P, long long o, float p1, float dC, 
     deq_H(dth, hp1, H * sx, H * sy, e);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(sc, fl, kG + i, o, e[i], P);
-    deq_flow(p, ux, uy, e);
+    deq_flow(p, heqx, heqy, e);
 #pragma unroll
     for (int i = 0; i < 9; ++i) Store::store(sc, fl, kH + i, o, e[i], P);
 
@@ -117,8 +118,8 @@ __global__ void k_init(const StepParams P, const double* __restrict__ fields, vo
     const float p1 = (float)(phi + 1.0);
     const float dC = (float)(0.5 * (1.0 + k - (1.0 - k) * phi) * (1.0 + (1.0 - k) * U) - 1.0);
     const float dth = (float)(fields[2 * plane + o] - (double)P.theta_ref);
-    init_node<Store>(P, o, p1, dC, (float)U, dth, (float)fields[3 * plane + o], (float)fields[4 * plane + o],
-                     (float)fields[5 * plane + o], sc, fl, hist);
+    const float ux = (float)fields[3 * plane + o], uy = (float)fields[4 * plane + o];
+    init_node<Store>(P, o, p1, dC, (float)U, dth, ux, uy, (float)fields[5 * plane + o], sc, fl, hist, ux, uy);
 }
 
 // Fields of every node, pixel-interleaved for the surrogate network:
@@ -149,7 +150,8 @@ __global__ void k_fields_nhwc(const StepParams P, const void* __restrict__ sc, c
 // thread reads and writes only its own node, so this works in place.
 template <class Store>
 __global__ void k_set_fields_nhwc(const StepParams P, const float* __restrict__ src, float vf, void* __restrict__ sc,
-                                  void* __restrict__ fl, float* __restrict__ hist)
+                                  void* __restrict__ fl, float* __restrict__ hist, const float* __restrict__ prev,
+                                  float inv_k)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -163,7 +165,35 @@ __global__ void k_set_fields_nhwc(const StepParams P, const float* __restrict__ 
     const float C = d[1];
     const float k = P.k;
     const float U = (2.0f * C / (1.0f + k - (1.0f - k) * phi) - 1.0f) / (1.0f - k);
-    init_node<Store>(P, o, phi + 1.0f, C - 1.0f, U, d[2] - P.theta_ref, d[3] * vf, d[4] * vf, p, sc, fl, hist);
+    const float p1 = phi + 1.0f, dC = C - 1.0f, dth = d[2] - P.theta_ref;
+    const float ux = d[3] * vf, uy = d[4] * vf;
+    // The stored momentum j is what the macro recovery turns into
+    // u = (j + F/2)(1 + q~)/2 (Guo forcing and the fluid-solid force, q~ =
+    // (1 - phi)/2), so the flow equilibrium takes j = 2u/(1 + q~) - F/2; its
+    // pressure argument compensates the |j|^2 - |u|^2 the recovery removes.
+    const float a = 0.5f * (1.0f + (1.0f - 0.5f * p1));
+    const float Fx = P.Fx, Fy = P.Fy + P.gbT * dth + P.gbC * (dC + P.dC_ref);
+    const float jx = ux / a - 0.5f * Fx, jy = uy / a - 0.5f * Fy;
+    const float peq = p - 0.4f * (jx * jx + jy * jy - ux * ux - uy * uy);
+    init_node<Store>(P, o, p1, dC, U, dth, ux, uy, peq, sc, fl, hist, jx, jy);
+    if (!prev) return;
+    // History one step back on the straight line from the fields K steps
+    // earlier (prev), so that the first backward differences after the
+    // rebuild carry the window's mean rate of change.
+    const float* q = prev + ((long long)y * P.nx + x) * 5;
+    const float phi_b = phi - (phi - fminf(1.0f, fmaxf(-1.0f, q[0]))) * inv_k;
+    const float C_b = C - (C - q[1]) * inv_k;
+    const float th_b = d[2] - (d[2] - q[2]) * inv_k;
+    const float ux_b = ux - (ux - q[3] * vf) * inv_k, uy_b = uy - (uy - q[4] * vf) * inv_k;
+    const float U_b = (2.0f * C_b / (1.0f + k - (1.0f - k) * phi_b) - 1.0f) / (1.0f - k);
+    const float H_b = th_b - 0.5f * (h_plus_1(P.h_kind, phi_b + 1.0f) - 1.0f);  // H = theta - h/2
+    const long long plane = P.plane;
+    hist[0 * plane + o] = phi_b;
+    hist[1 * plane + o] = coupling_Q(phi_b, th_b, U_b, P);
+    hist[2 * plane + o] = C_b * ux_b * P.nsub;
+    hist[3 * plane + o] = C_b * uy_b * P.nsub;
+    hist[4 * plane + o] = H_b * ux_b * P.nsub;
+    hist[5 * plane + o] = H_b * uy_b * P.nsub;
 }
 
 // Interface mismatch between two pixel-interleaved field sets (stride 5,
@@ -403,10 +433,10 @@ cudaError_t fields_nhwc_t(const StepParams& P, const void* sc, const void* fl, f
 
 template <class Store>
 cudaError_t set_fields_nhwc_t(const StepParams& P, const float* src, float vf, void* sc, void* fl, float* hist,
-                              cudaStream_t s)
+                              const float* prev, int K, cudaStream_t s)
 {
     const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
-    k_set_fields_nhwc<Store><<<g, b, 0, s>>>(P, src, vf, sc, fl, hist);
+    k_set_fields_nhwc<Store><<<g, b, 0, s>>>(P, src, vf, sc, fl, hist, prev, 1.0f / (float)(K > 0 ? K : 1));
     return cudaGetLastError();
 }
 
@@ -474,12 +504,12 @@ cudaError_t launch_fields_nhwc(const StepParams& P, int storage, const void* sc,
 }
 
 cudaError_t launch_set_fields_nhwc(const StepParams& P, int storage, const float* src, float vf, void* sc, void* fl,
-                                   float* hist, cudaStream_t s)
+                                   float* hist, const float* prev, int K, cudaStream_t s)
 {
     switch (storage) {
-    case kStoreF16: return set_fields_nhwc_t<StoreF16>(P, src, vf, sc, fl, hist, s);
-    case kStoreBF16: return set_fields_nhwc_t<StoreBF16>(P, src, vf, sc, fl, hist, s);
-    default: return set_fields_nhwc_t<StoreF32>(P, src, vf, sc, fl, hist, s);
+    case kStoreF16: return set_fields_nhwc_t<StoreF16>(P, src, vf, sc, fl, hist, prev, K, s);
+    case kStoreBF16: return set_fields_nhwc_t<StoreBF16>(P, src, vf, sc, fl, hist, prev, K, s);
+    default: return set_fields_nhwc_t<StoreF32>(P, src, vf, sc, fl, hist, prev, K, s);
     }
 }
 

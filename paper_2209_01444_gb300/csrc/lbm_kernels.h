@@ -79,7 +79,7 @@ cudaError_t launch_seed_fields(const StepParams& P, const double* seeds, int ns,
 cudaError_t launch_fields_nhwc(const StepParams& P, int storage, const void* sc, const void* fl, float inv_vf,
                                float* dst, cudaStream_t s);
 cudaError_t launch_set_fields_nhwc(const StepParams& P, int storage, const float* src, float vf, void* sc, void* fl,
-                                   float* hist, cudaStream_t s);
+                                   float* hist, const float* prev, int K, cudaStream_t s);
 cudaError_t launch_phi_mismatch(const float* a, const float* b, long long n, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
                           cudaStream_t s);

@@ -74,6 +74,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
     }
 }
 
+__device__ __forceinline__ uint32_t mbar_try(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done;
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int c0, int c1, uint64_t* bar)
 {
     asm volatile(
@@ -354,6 +367,247 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// ----------------------------------------------------------------------------
+// Persistent, warp-specialised form of the same tile computation.  Each CTA
+// loops over tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (M fastest, so
+// neighbouring CTAs share weight tiles and, for convolutions, input halos in
+// L2).  Warp 0 (one lane) issues the TMA loads into an S-deep ring, warp 1
+// (one lane) issues the MMAs into one of two TMEM accumulators, and warps
+// 2-5 drain the other accumulator (tcgen05.ld, bias, activation, stores), so
+// the epilogue of one tile overlaps the main loop of the next.  Every wait is
+// bounded; a wait that runs out raises the error flag and a shared abort flag
+// that makes the other roles stop, then the CTA drains its copies and MMAs
+// (bounded) and frees its TMEM.
+constexpr int kWsThreads = 192;
+
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
+{
+    const uint32_t addr = smem_u32(bar);
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > kWaitNs) {
+                *abort_flag = 1;
+                atomicExch(&g_gemm_error, 1);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int BN, bool OUT_BF16, int BK, bool CONV>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, void* __restrict__ D,
+              const float* __restrict__ bias, int M, int N, int K, int ldd, int relu, ConvGeo geo, ShuffleGeo sh,
+              int tiles_m, int tiles)
+{
+    constexpr int S = stages_for<BK>();
+    constexpr int A_BYTES = kBM * BK * 2;
+    constexpr int B_BYTES = BN * BK * 2;
+    constexpr int STAGE = A_BYTES + B_BYTES;
+    constexpr uint32_t ACC_COLS = BN < 32 ? 32 : BN;
+    constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+    constexpr uint32_t IDESC = idesc_bf16(kBM, BN);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + S * STAGE);
+    uint64_t* empty = full + S;
+    uint64_t* acc_full = empty + S;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* done = acc_empty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    int* counts = (int*)(tmem_slot + 2);  // [0] loads issued, [1] k blocks consumed
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 128);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        counts[0] = counts[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {  // ---------------------------------------- producer
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const int m0 = (t % tiles_m) * kBM, n0 = (t / tiles_m) * BN;
+                int x0 = 0, y0 = 0, b0 = 0;
+                if (CONV) {
+                    x0 = m0 % geo.W;
+                    y0 = (m0 / geo.W) % geo.H;
+                    b0 = m0 / (geo.W * geo.H);
+                }
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int st = it % S;
+                    if (it >= S && !(ok = mbar_wait_abort(&empty[st], (uint32_t)((it / S - 1) & 1), abort_flag)))
+                        break;
+                    uint8_t* a = smem + st * STAGE;
+                    mbar_expect_tx(&full[st], STAGE);
+                    if constexpr (CONV) {
+                        const int tap = kb / geo.cblocks, cb = kb - tap * geo.cblocks;
+                        const int ky = tap / 3, kx = tap - 3 * ky;
+                        tma_load_4d(a, &tmA, cb * BK, x0 + kx - 1, y0 + ky - 1, b0, &full[st]);
+                        tma_load_2d(a + A_BYTES, &tmB, tap * geo.C + cb * BK, n0, &full[st]);
+                    } else {
+                        tma_load_2d(a, &tmA, kb * BK, m0, &full[st]);
+                        tma_load_2d(a + A_BYTES, &tmB, kb * BK, n0, &full[st]);
+                    }
+                    counts[0] = it + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // --------------------------------------------- MMA
+            int it = 0, lt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++lt) {
+                const int acc = lt & 1;
+                if (lt >= 2 && !(ok = mbar_wait_abort(&acc_empty[acc], (uint32_t)((lt / 2 - 1) & 1), abort_flag)))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(acc * ACC_COLS);
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int st = it % S;
+                    if (!(ok = mbar_wait_abort(&full[st], (uint32_t)((it / S) & 1), abort_flag))) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(smem + st * STAGE), b0s = a0 + A_BYTES;
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        umma(d, tile_desc<BK>(a0 + k * 32), tile_desc<BK>(b0s + k * 32), IDESC,
+                             (kb > 0 || k > 0) ? 1u : 0u);
+                    umma_commit(&empty[st]);
+                    counts[1] = it + 1;
+                }
+                if (ok) umma_commit(&acc_full[acc]);
+            }
+            umma_commit(done);  // completes once every MMA issued has finished
+        }
+    } else {  // --------------------------------------------------- epilogue
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        const int et = threadIdx.x - 64;
+        (void)et;
+        int lt = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            if (!mbar_wait_abort(&acc_full[acc], (uint32_t)((lt / 2) & 1), abort_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (t % tiles_m) * kBM, n0 = (t / tiles_m) * BN;
+            const int row = m0 + q * 32 + lane;
+            const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * ACC_COLS);
+            long long rbase = (long long)row * ldd;
+            int sy = 0, sx = 0, sb = 0;
+            if (sh.Wl) {
+                sx = row % sh.Wl;
+                sy = (row / sh.Wl) % sh.Hl;
+                sb = row / (sh.Wl * sh.Hl);
+            }
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 16) {
+                uint32_t r[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                    "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15])
+                    : "r"(lane_base + (uint32_t)c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int col = n0 + c;
+                if (row < M && col < N) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float x = __uint_as_float(r[j]) + ((bias && col + j < N) ? bias[col + j] : 0.0f);
+                        v[j] = relu ? fmaxf(x, 0.0f) : x;
+                    }
+                    long long off = rbase + col;
+                    if (sh.Wl) {
+                        const int sub = col / sh.c, co = col - sub * sh.c;
+                        const long long qq = ((long long)sb * 2 * sh.Hl + 2 * sy + (sub >> 1)) * (2LL * sh.Wl) +
+                                             2 * sx + (sub & 1);
+                        off = qq * ldd + sh.c0 + co;
+                    }
+                    if (col + 16 > N) {
+                        for (int j = 0; col + j < N; ++j) {
+                            if (OUT_BF16)
+                                ((__nv_bfloat16*)D)[off + j] = __float2bfloat16_rn(v[j]);
+                            else
+                                ((float*)D)[off + j] = v[j];
+                        }
+                    } else if (OUT_BF16) {
+                        __nv_bfloat162 h[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        uint4* dst = (uint4*)((__nv_bfloat16*)D + off);
+                        dst[0] = *(uint4*)&h[0];
+                        dst[1] = *(uint4*)&h[4];
+                    } else {
+                        float4* dst = (float4*)((float*)D + off);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&acc_empty[acc]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // every issued MMA completes before TMEM is freed; on an abort also
+        // every issued copy lands before the CTA's shared memory goes away
+        unsigned long long t0 = global_ns();
+        bool fin = false;
+        while (!(fin = (bool)mbar_try(done, 0)) && global_ns() - t0 < kWaitNs) {
+        }
+        if (!fin) atomicExch(&g_gemm_error, 1);
+        if (*abort_flag)
+            for (int it = counts[1]; it < counts[0]; ++it) mbar_wait(&full[it % S], (uint32_t)((it / S) & 1));
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 cudaError_t encoder()
@@ -421,6 +675,33 @@ cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const
     return cudaGetLastError();
 }
 
+template <int BN, bool OUT_BF16, int BK, bool CONV>
+cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
+                      int ldd, int relu, const ConvGeo& geo, const ShuffleGeo& sh, cudaStream_t s)
+{
+    constexpr int smem = stages_for<BK>() * (kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_ws<BN, OUT_BF16, BK, CONV>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev))) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+        int occ = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gemm_ws<BN, OUT_BF16, BK, CONV>, kWsThreads,
+                                                               smem)))
+            return e;
+        per_sm = occ < 1 ? 1 : occ;
+    }
+    const int tiles_m = (M + kBM - 1) / kBM;
+    const int tiles = tiles_m * ((N + BN - 1) / BN);
+    const int grid = tiles < sms * per_sm ? tiles : sms * per_sm;
+    k_gemm_ws<BN, OUT_BF16, BK, CONV><<<grid, kWsThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu, geo, sh,
+                                                                     tiles_m, tiles);
+    return cudaGetLastError();
+}
+
 int bn_for(int N) { return N >= 256 ? 256 : N > 64 ? 128 : N > 32 ? 64 : 32; }
 
 template <int BK, bool CONV>
@@ -430,6 +711,9 @@ cudaError_t dispatch(int bn, bool ob, const CUtensorMap& ta, const CUtensorMap& 
 {
 #define NN_GEMM_CASE(BNV)                                                                                            \
     case BNV:                                                                                                        \
+        if (splits == 1)                                                                                             \
+            return ob ? launch_ws<BNV, true, BK, CONV>(ta, tb, out, bias, M, N, K, ldo, r, geo, sh, s)               \
+                      : launch_ws<BNV, false, BK, CONV>(ta, tb, out, bias, M, N, K, ldo, r, geo, sh, s);             \
         return ob ? launch_bn<BNV, true, BK, CONV>(ta, tb, out, bias, M, N, K, ldo, r, splits, kbps, geo, sh, s)    \
                   : launch_bn<BNV, false, BK, CONV>(ta, tb, out, bias, M, N, K, ldo, r, splits, kbps, geo, sh, s);
     switch (bn) {

@@ -172,6 +172,43 @@ __global__ void k_proj_fwd(const bf16* __restrict__ X, int P, int C, int xpitch,
     }
 }
 
+// The same with 16-byte loads of X (C and xpitch multiples of 8) and the
+// weights staged in shared memory: one thread per pixel.
+__global__ void k_proj_fwd_vec(const bf16* __restrict__ X, int P, int C, int xpitch, const float* __restrict__ Wt,
+                               const float* __restrict__ bias, int O, const float* __restrict__ R,
+                               float* __restrict__ Y)
+{
+    extern __shared__ float wsh[];  // O * C weights, then O biases
+    for (int i = threadIdx.x; i < O * C; i += blockDim.x) wsh[i] = Wt[i];
+    for (int i = threadIdx.x; i < O; i += blockDim.x) wsh[O * C + i] = bias[i];
+    __syncthreads();
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float acc[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) acc[o] = o < O ? wsh[O * C + o] + (R ? R[p * O + o] : 0.0f) : 0.0f;
+    const uint4* xp = (const uint4*)(X + p * xpitch);
+    for (int c8 = 0; c8 < C / 8; ++c8) {
+        const uint4 q = xp[c8];
+        const __nv_bfloat162* h = (const __nv_bfloat162*)&q;
+        float xv[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 f = __bfloat1622float2(h[j]);
+            xv[2 * j] = f.x;
+            xv[2 * j + 1] = f.y;
+        }
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            if (o >= O) break;
+            const float* w = wsh + o * C + c8 * 8;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[o] += xv[j] * w[j];
+        }
+    }
+    for (int o = 0; o < O; ++o) Y[p * O + o] = acc[o];
+}
+
 // dX[p][c] = sum_o dY[p][o] Wt[o][c] (FP32, pitch dpitch).
 __global__ void k_proj_bwd_x(const float* __restrict__ dY, int P, int O, const float* __restrict__ Wt, int C,
                              float* __restrict__ dX, int dpitch)
@@ -317,6 +354,25 @@ __global__ void k_cast_bf16(const float* __restrict__ a, long long rows, int C, 
     b[r * bpitch + c] = __float2bfloat16(a[r * apitch + c]);
 }
 
+// T[p][c] = (t[p][c] - x[p][c]) * inv_out[c]: the K-step increment in the
+// network's output units.
+__global__ void k_increment(const float* __restrict__ t, const float* __restrict__ x, long long P, int F,
+                            const float* __restrict__ inv_out, float* __restrict__ T)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= P * F) return;
+    T[i] = (t[i] - x[i]) * inv_out[(int)(i % F)];
+}
+
+// y[p][c] = x[p][c] + Y[p][c] / inv_out[c].
+__global__ void k_add_increment(const float* __restrict__ Y, const float* __restrict__ x, long long P, int F,
+                                const float* __restrict__ inv_out, float* __restrict__ y)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= P * F) return;
+    y[i] = x[i] + Y[i] / inv_out[(int)(i % F)];
+}
+
 // FP32 fields [P][F] = mean + std * Y[P][F] (undo the normalisation).
 __global__ void k_unpack(const float* __restrict__ Y, long long P, int F, const float* __restrict__ mean,
                          const float* __restrict__ inv_std, float* __restrict__ f)
@@ -398,7 +454,12 @@ cudaError_t shuffle_bwd(const void* dY, bool dy_fp32, int ypitch, int c0, int B,
 cudaError_t proj_fwd(const void* X, int P, int C, int xpitch, const float* Wt, const float* bias, int O,
                      const float* R, float* Y, cudaStream_t s)
 {
-    k_proj_fwd<<<blocks(P), 256, 0, s>>>((const bf16*)X, P, C, xpitch, Wt, bias, O, R, Y);
+    if (O > 8) return cudaErrorInvalidValue;
+    const size_t sh = (size_t)(O * C + O) * sizeof(float);
+    if (C % 8 == 0 && xpitch % 8 == 0 && ((uintptr_t)X & 15) == 0 && sh <= 48 * 1024)
+        k_proj_fwd_vec<<<blocks(P, 128), 128, sh, s>>>((const bf16*)X, P, C, xpitch, Wt, bias, O, R, Y);
+    else
+        k_proj_fwd<<<blocks(P), 256, 0, s>>>((const bf16*)X, P, C, xpitch, Wt, bias, O, R, Y);
     return cudaGetLastError();
 }
 
@@ -461,6 +522,20 @@ cudaError_t unpack(const float* Y, long long P, int F, const float* mean, const 
                    cudaStream_t s)
 {
     k_unpack<<<blocks(P * F), 256, 0, s>>>(Y, P, F, mean, inv_std, f);
+    return cudaGetLastError();
+}
+
+cudaError_t increment(const float* t, const float* x, long long P, int F, const float* inv_out, float* T,
+                      cudaStream_t s)
+{
+    k_increment<<<blocks(P * F), 256, 0, s>>>(t, x, P, F, inv_out, T);
+    return cudaGetLastError();
+}
+
+cudaError_t add_increment(const float* Y, const float* x, long long P, int F, const float* inv_out, float* y,
+                          cudaStream_t s)
+{
+    k_add_increment<<<blocks(P * F), 256, 0, s>>>(Y, x, P, F, inv_out, y);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,10 @@ cudaError_t pack(const float* f, long long P, int F, const float* mean, const fl
                  float* R, cudaStream_t s);
 cudaError_t unpack(const float* Y, long long P, int F, const float* mean, const float* inv_std, float* f,
                    cudaStream_t s);
+cudaError_t increment(const float* t, const float* x, long long P, int F, const float* inv_out, float* T,
+                      cudaStream_t s);
+cudaError_t add_increment(const float* Y, const float* x, long long P, int F, const float* inv_out, float* y,
+                          cudaStream_t s);
 cudaError_t cast_bf16(const float* a, long long rows, int C, int apitch, void* b, int bpitch, cudaStream_t s);
 
 }  // namespace nn

@@ -9,7 +9,9 @@
 //   decoder l = L-2 .. 0: u_l = upconv2x2(h_{l+1}) (h_{L-1} = s_{L-1},
 //     otherwise the decoder output d_{l+1}), cat_l = [s_l, u_l],
 //     d_l = relu(conv3x3(relu(conv3x3(cat_l))));
-//   output y = x[:, :F] + proj1x1(d_0) in normalised units.
+//   output: the K-step increment proj1x1(d_0) in output units, so that the
+//   prediction is y = x + std_out * proj1x1(d_0), with the inputs normalised
+//   as (x - mean) / std_in.
 // A 3 x 3 convolution is an im2col gather followed by a GEMM with the bias and
 // ReLU in its epilogue; its input gradient is the same gather of the output
 // gradient times the 180-degree-rotated kernel; its weight gradient is a
@@ -79,9 +81,9 @@ struct lbm_unet {
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
     bf16* wb = nullptr;
     int t = 0;
-    float *mean = nullptr, *inv_std = nullptr;
+    float *mean = nullptr, *inv_std = nullptr, *inv_out = nullptr;
     bf16* x0 = nullptr;
-    float *R = nullptr, *Y = nullptr, *T = nullptr, *G = nullptr;
+    float *Y = nullptr, *T = nullptr, *G = nullptr;
     float *loss = nullptr, *part = nullptr;
     bf16 *col = nullptr, *colT = nullptr, *tA = nullptr, *tB = nullptr;
     bf16 *gA = nullptr, *gB = nullptr, *dU = nullptr;
@@ -210,9 +212,9 @@ cudaError_t allocate(lbm_unet* u)
     UN_ALLOC(u->wb, np);
     UN_ALLOC(u->mean, kInPitch);
     UN_ALLOC(u->inv_std, kInPitch);
+    UN_ALLOC(u->inv_out, kInPitch);
     const long long P0 = u->P0;
     UN_ALLOC(u->x0, P0 * kInPitch);
-    UN_ALLOC(u->R, P0 * u->F);
     UN_ALLOC(u->Y, P0 * u->F);
     UN_ALLOC(u->T, P0 * u->F);
     UN_ALLOC(u->G, P0 * u->F);
@@ -363,7 +365,7 @@ cudaError_t mask_cast(lbm_unet* u, float* g32, int gpitch, const bf16* y, int yp
 cudaError_t forward(lbm_unet* u, const float* x)
 {
     cudaError_t e;
-    if ((e = nn::pack(x, u->P0, u->F, u->mean, u->inv_std, u->x0, kInPitch, u->R, u->s))) return e;
+    if ((e = nn::pack(x, u->P0, u->F, u->mean, u->inv_std, u->x0, kInPitch, nullptr, u->s))) return e;
     const bf16* in = u->x0;
     int inpitch = kInPitch;
     const int L = u->L;
@@ -390,16 +392,17 @@ cudaError_t forward(lbm_unet* u, const float* x)
         h = v.dD;
     }
     const bf16* top = L > 1 ? u->lv[0].dD : u->lv[0].s;
-    return nn::proj_fwd(top, (int)u->P0, u->base, u->base, u->w + u->out_w, u->w + u->out_b, u->F, u->R, u->Y, u->s);
+    return nn::proj_fwd(top, (int)u->P0, u->base, u->base, u->w + u->out_w, u->w + u->out_b, u->F, nullptr, u->Y,
+                        u->s);
 }
 
-// Loss and parameter gradients for the target t (physical units); forward() ran.
-cudaError_t backward(lbm_unet* u, const float* t)
+// Loss and parameter gradients for the target t (physical units); forward(x) ran.
+cudaError_t backward(lbm_unet* u, const float* x, const float* t)
 {
     cudaError_t e;
     const long long P0 = u->P0;
     const int L = u->L, F = u->F, w0 = u->base;
-    if ((e = nn::pack(t, P0, F, u->mean, u->inv_std, nullptr, F, u->T, u->s))) return e;
+    if ((e = nn::increment(t, x, P0, F, u->inv_out, u->T, u->s))) return e;
     if ((e = nn::mse(u->Y, u->T, P0 * F, u->G, u->loss, u->part, u->s))) return e;
     const bf16* top = L > 1 ? u->lv[0].dD : u->lv[0].s;
     if ((e = nn::proj_bwd(u->G, top, (int)P0, w0, w0, u->w + u->out_w, F, u->g32, w0, u->g + u->out_w, u->g + u->out_b,
@@ -477,6 +480,7 @@ int lbm_unet_create(int levels, int base, int fields, int batch, int height, int
         for (float& o : ones) o = 1.0f;
         e = cudaMemcpy(u->mean, zeros, sizeof zeros, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(u->inv_std, ones, sizeof ones, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(u->inv_out, ones, sizeof ones, cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
         lbm_unet_destroy(u);
@@ -543,18 +547,21 @@ int lbm_unet_get_params(lbm_unet* u, float* host) { return get_vec(u, u ? u->w :
 
 int lbm_unet_get_grads(lbm_unet* u, float* host) { return get_vec(u, u ? u->g : nullptr, host); }
 
-int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_)
+int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_in, const float* std_out)
 {
-    if (!u || !mean || !std_) return LBM_EINVAL;
-    float mu[kInPitch] = {0}, is[kInPitch];
-    for (int c = 0; c < kInPitch; ++c) is[c] = 1.0f;
+    if (!u || !mean || !std_in) return LBM_EINVAL;
+    if (!std_out) std_out = std_in;
+    float mu[kInPitch] = {0}, is[kInPitch], io[kInPitch];
+    for (int c = 0; c < kInPitch; ++c) is[c] = io[c] = 1.0f;
     for (int c = 0; c < u->F; ++c) {
-        if (!(std_[c] > 0.0f)) return fail(u, LBM_EINVAL, "normalisation scale must be positive");
+        if (!(std_in[c] > 0.0f) || !(std_out[c] > 0.0f)) return fail(u, LBM_EINVAL, "scales must be positive");
         mu[c] = mean[c];
-        is[c] = 1.0f / std_[c];
+        is[c] = 1.0f / std_in[c];
+        io[c] = 1.0f / std_out[c];
     }
     UN_CHECK(u, cudaMemcpyAsync(u->mean, mu, sizeof mu, cudaMemcpyHostToDevice, u->s));
     UN_CHECK(u, cudaMemcpyAsync(u->inv_std, is, sizeof is, cudaMemcpyHostToDevice, u->s));
+    UN_CHECK(u, cudaMemcpyAsync(u->inv_out, io, sizeof io, cudaMemcpyHostToDevice, u->s));
     UN_CHECK(u, cudaStreamSynchronize(u->s));
     return LBM_OK;
 }
@@ -563,7 +570,7 @@ int lbm_unet_forward(lbm_unet* u, const float* x, float* y)
 {
     if (!u || !x) return LBM_EINVAL;
     UN_CHECK(u, forward(u, x));
-    if (y) UN_CHECK(u, nn::unpack(u->Y, u->P0, u->F, u->mean, u->inv_std, y, u->s));
+    if (y) UN_CHECK(u, nn::add_increment(u->Y, x, u->P0, u->F, u->inv_out, y, u->s));
     return LBM_OK;
 }
 
@@ -572,7 +579,7 @@ int lbm_unet_backward(lbm_unet* u, const float* x, const float* target)
     if (!u || !x || !target) return LBM_EINVAL;
     UN_CHECK(u, allocate_backward(u));
     UN_CHECK(u, forward(u, x));
-    UN_CHECK(u, backward(u, target));
+    UN_CHECK(u, backward(u, x, target));
     return LBM_OK;
 }
 

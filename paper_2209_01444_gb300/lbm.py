@@ -129,7 +129,7 @@ SIGNATURES = {
     "lbm_unet_set_params": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_get_params": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_get_grads": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
-    "lbm_unet_set_norm": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_set_norm": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "lbm_unet_forward": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "lbm_unet_backward": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "lbm_unet_adam": (ct.c_int, [ct.c_void_p, ct.c_float, ct.c_float, ct.c_float, ct.c_float]),
@@ -141,7 +141,7 @@ SIGNATURES = {
     "lbm_snapshot_save": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "lbm_snapshot_restore": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "lbm_fields_nhwc": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
-    "lbm_set_fields_nhwc": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "lbm_set_fields_nhwc": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
     "lbm_batch_fields_nhwc": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p]),
     "lbm_surrogate_advance": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_double,
                                          ct.c_double, ct.c_double, ct.c_void_p]),
@@ -314,11 +314,13 @@ class Simulation:
         self._check(self.lib.lbm_fields_nhwc(self.h, ct.c_void_p(out.data_ptr())))
         return out
 
-    def set_fields_nhwc(self, src) -> None:
+    def set_fields_nhwc(self, src, prev=None, K: int = 0) -> None:
         import torch
 
-        assert src.is_cuda and src.dtype == torch.float32 and src.is_contiguous() and src.numel() == self.ny * self.nx * 5
-        self._check(self.lib.lbm_set_fields_nhwc(self.h, ct.c_void_p(src.data_ptr())))
+        for t in (src,) if prev is None else (src, prev):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == self.ny * self.nx * 5
+        self._check(self.lib.lbm_set_fields_nhwc(self.h, ct.c_void_p(src.data_ptr()),
+                                                 None if prev is None else ct.c_void_p(prev.data_ptr()), int(K)))
 
     def surrogate_advance(self, net, K: int, tip_tol: float, audit: bool, cx: float, cy: float,
                           orient: float = 0.0) -> dict:

@@ -115,11 +115,16 @@ class UNet:
     def grads(self) -> dict:
         return self._get(self.lib.lbm_unet_get_grads)
 
-    def set_norm(self, mean, std) -> None:
+    def set_norm(self, mean, std_in, std_out=None) -> None:
+        """Inputs read as (x - mean) / std_in; the output is the increment in
+        units of std_out (default std_in)."""
         m = np.ascontiguousarray(mean, np.float32)
-        s = np.ascontiguousarray(std, np.float32)
-        assert m.size == self.fields and s.size == self.fields
-        self._check(self.lib.lbm_unet_set_norm(self.h, m.ctypes.data_as(ct.c_void_p), s.ctypes.data_as(ct.c_void_p)))
+        si = np.ascontiguousarray(std_in, np.float32)
+        so = si if std_out is None else np.ascontiguousarray(std_out, np.float32)
+        assert m.size == self.fields and si.size == self.fields and so.size == self.fields
+        self._check(self.lib.lbm_unet_set_norm(self.h, m.ctypes.data_as(ct.c_void_p), si.ctypes.data_as(ct.c_void_p),
+                                               so.ctypes.data_as(ct.c_void_p)))
+        self.norm = (m, si, so)
 
     def forward(self, x, y=None):
         """Prediction in physical units (into `y` when given)."""
@@ -131,7 +136,8 @@ class UNet:
         return y
 
     def output_normalised(self):
-        """The last prediction in normalised units (a new CUDA tensor)."""
+        """The last network output, the increment in units of std_out (a new
+        CUDA tensor)."""
         import torch
 
         out = torch.empty(self.shape, dtype=torch.float32, device="cuda")
@@ -181,15 +187,17 @@ def make_dataset(cases, K: int, windows: int, warm: int = 0, storage: str = "fp3
     return x, t
 
 
-def normalisation(x, t, floor: float = 1e-4):
-    """Per-field mean of the inputs and standard deviation of the K-step
-    increments (so that every field's increment weighs alike in the loss)."""
+def normalisation(x, t, floor: float = 1e-6):
+    """Per-field mean and standard deviation of the inputs, and the standard
+    deviation of the K-step increments (so that every field's increment
+    weighs alike in the loss)."""
     step = max(1, x.shape[0] // 64)
     xs = x[::step].cpu().numpy().astype(np.float64).reshape(-1, 5)
     ds = t[::step].cpu().numpy().astype(np.float64).reshape(-1, 5) - xs
     mean = xs.mean(axis=0)
-    std = np.maximum(ds.std(axis=0), floor)
-    return mean.astype(np.float32), std.astype(np.float32)
+    std_in = np.maximum(xs.std(axis=0), floor)
+    std_out = np.maximum(ds.std(axis=0), floor)
+    return mean.astype(np.float32), std_in.astype(np.float32), std_out.astype(np.float32)
 
 
 def train(net: UNet, x, t, steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 0):

@@ -226,20 +226,25 @@ def unet_params(shapes, rng_seed: int, out_scale: float = 0.01) -> dict:
     return out
 
 
-def surrogate_domains(count: int = 32, n: int = 256, rng_seed: int = 5, steps: int = 4000) -> list[Case]:
+def surrogate_domains(count: int = 32, n: int = 256, rng_seed: int = 5, steps: int = 4000,
+                      forced_flow_share: float = 0.5) -> list[Case]:
     """Training trajectories for the surrogate: n x n domains in the forced-flow
-    geometry (inflow left, outflow right, symmetry top and bottom) with the
-    parameters drawn as in the batched-domain workload: Delta in [0.45, 0.65],
-    eps in [0.03, 0.06], inflow u_x in [0, 0.02] lattice units, one seed of
-    radius 6-12 near (0.375 n, 0.5 n); half the seeds at orientation 0 (the
-    forced-flow case), half in [0, 45 deg)."""
+    geometry (inflow left, outflow right, symmetry top and bottom), one seed of
+    radius 6-12 near (0.375 n, 0.5 n).  The first forced_flow_share of them
+    take the forced-flow case's parameters (Delta = 0.55, eps = 0.05, inflow
+    u_x = 0.01 lattice units, orientation 0); the rest draw them as the
+    batched-domain workload does: Delta in [0.45, 0.65], eps in [0.03, 0.06],
+    inflow u_x in [0, 0.02], orientation in [0, 45 deg)."""
     rng = np.random.Generator(np.random.PCG64(rng_seed))
     cases = []
+    n_ff = int(round(forced_flow_share * count))
     for j in range(count):
         delta = float(rng.uniform(0.45, 0.65))
         eps = float(rng.uniform(0.03, 0.06))
         uin = float(rng.uniform(0.0, 0.02))
-        orient = 0.0 if j % 2 == 0 else float(rng.uniform(0.0, math.pi / 4))
+        orient = float(rng.uniform(0.0, math.pi / 4))
+        if j < n_ff:
+            delta, eps, uin, orient = 0.55, 0.05, 0.01, 0.0
         cx = 0.375 * n + float(rng.uniform(-0.05, 0.05)) * n
         cy = 0.5 * n + float(rng.uniform(-0.05, 0.05)) * n
         R = float(rng.uniform(6.0, 12.0))

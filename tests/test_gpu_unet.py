@@ -167,21 +167,28 @@ def test_gradients_five_levels(env):
                                                           min(v[1] for v in err.values())))
 
 
-def test_normalisation_round_trip(env):
-    """With mean/std set, the network sees (x - mean)/std and returns physical
-    units; a zero output projection makes it the identity."""
+def test_normalisation_and_output_units(env):
+    """The output is the increment in units of std_out: with a zero output
+    weight and biases b the prediction is x + std_out * b; the input scaling
+    reaches the network (its loss gradient changes with std_in)."""
     torch, lib, S = env
     B, H, W = 1, 16, 16
     net = S.UNet(B, H, W, levels=3)
     shapes = U.init_shapes(3, BASE, 8, F)
     p3 = workloads.unet_params(shapes, 13)
     p3["out.W"][:] = 0.0
-    p3["out.b"][:] = 0.0
+    p3["out.b"][:] = [1.0, 2.0, -3.0, 0.5, 0.25]
     net.set_params(p3)
-    net.set_norm([0.5, -1.0, 2.0, 0.0, 0.1], [2.0, 0.5, 4.0, 1.0, 0.01])
+    std_out = np.array([0.5, 1.0, 2.0, 0.25, 4.0], np.float32)
+    net.set_norm([0.5, -1.0, 2.0, 0.0, 0.1], [2.0, 0.5, 4.0, 1.0, 0.01], std_out)
     x = np.random.default_rng(3).normal(size=(B, H, W, F))
     y = net.forward(_dev(torch, x)).cpu().numpy()
-    assert np.abs(y - x).max() <= 1e-5 * np.abs(x).max()
+    ref = x + std_out * p3["out.b"]
+    assert np.abs(y - ref).max() <= 1e-5 * np.abs(ref).max()
+    # the loss is taken on (t - x) / std_out
+    t = x + std_out * p3["out.b"] + std_out * 0.1
+    net.backward(_dev(torch, x), _dev(torch, t))
+    assert abs(net.loss() - 0.01) <= 1e-5
 
 
 def test_training_reduces_loss(env):
