@@ -163,8 +163,15 @@ __device__ __forceinline__ uint64_t tile_desc(uint32_t saddr)
         return sw64_desc(saddr);
 }
 
-template <int BK>
-constexpr int stages_for() { return BK == 64 ? 4 : 8; }
+// Ring depth: as many stages as fit in about 200 KB of shared memory, 2 to 8
+// (a stage holds MT 128-row A tiles and one BN-row B tile of BK columns).
+template <int BK, int BN, int MT = 1>
+constexpr int stages_for()
+{
+    constexpr int stage = (MT * kBM + BN) * BK * 2;
+    constexpr int n = (200 * 1024) / stage;
+    return n < 2 ? 2 : n > 8 ? 8 : n;
+}
 
 }  // namespace
 
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1)
            const float* __restrict__ bias, int M, int N, int K, int ldd, int relu, int kb_per_split, ConvGeo geo,
            ShuffleGeo sh)
 {
-    constexpr int S = stages_for<BK>();
+    constexpr int S = stages_for<BK, BN>();
     constexpr int A_BYTES = kBM * BK * 2;
     constexpr int B_BYTES = BN * BK * 2;
     constexpr int STAGE = A_BYTES + B_BYTES;
@@ -410,17 +417,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int BN, bool OUT_BF16, int BK, bool CONV>
+template <int BN, bool OUT_BF16, int BK, bool CONV, int MT>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, void* __restrict__ D,
               const float* __restrict__ bias, int M, int N, int K, int ldd, int relu, ConvGeo geo, ShuffleGeo sh,
               int tiles_m, int tiles)
 {
-    constexpr int S = stages_for<BK>();
-    constexpr int A_BYTES = kBM * BK * 2;
+    constexpr int S = stages_for<BK, BN, MT>();
+    constexpr int A_BYTES = kBM * BK * 2;          // one 128-row sub-tile
     constexpr int B_BYTES = BN * BK * 2;
-    constexpr int STAGE = A_BYTES + B_BYTES;
-    constexpr uint32_t ACC_COLS = BN < 32 ? 32 : BN;
+    constexpr int STAGE = MT * A_BYTES + B_BYTES;
+    constexpr uint32_t SUB_COLS = BN < 32 ? 32 : BN;
+    constexpr uint32_t ACC_COLS = MT * SUB_COLS;
     constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
     constexpr uint32_t IDESC = idesc_bf16(kBM, BN);
     extern __shared__ uint8_t smem_raw[];
@@ -464,15 +472,22 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {  // ---------------------------------------- producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
             int it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-                const int m0 = (t % tiles_m) * kBM, n0 = (t / tiles_m) * BN;
-                int x0 = 0, y0 = 0, b0 = 0;
-                if (CONV) {
-                    x0 = m0 % geo.W;
-                    y0 = (m0 / geo.W) % geo.H;
-                    b0 = m0 / (geo.W * geo.H);
+                const int m0 = (t % tiles_m) * (kBM * MT), n0 = (t / tiles_m) * BN;
+                int x0[MT], y0[MT], b0[MT];
+#pragma unroll
+                for (int i = 0; i < MT; ++i) {
+                    const int mi = m0 + i * kBM;
+                    x0[i] = y0[i] = b0[i] = 0;
+                    if (CONV) {
+                        x0[i] = mi % geo.W;
+                        y0[i] = (mi / geo.W) % geo.H;
+                        b0[i] = mi / (geo.W * geo.H);
+                    }
                 }
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int st = it % S;
@@ -483,11 +498,15 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     if constexpr (CONV) {
                         const int tap = kb / geo.cblocks, cb = kb - tap * geo.cblocks;
                         const int ky = tap / 3, kx = tap - 3 * ky;
-                        tma_load_4d(a, &tmA, cb * BK, x0 + kx - 1, y0 + ky - 1, b0, &full[st]);
-                        tma_load_2d(a + A_BYTES, &tmB, tap * geo.C + cb * BK, n0, &full[st]);
+#pragma unroll
+                        for (int i = 0; i < MT; ++i)
+                            tma_load_4d(a + i * A_BYTES, &tmA, cb * BK, x0[i] + kx - 1, y0[i] + ky - 1, b0[i],
+                                        &full[st]);
+                        tma_load_2d(a + MT * A_BYTES, &tmB, tap * geo.C + cb * BK, n0, &full[st]);
                     } else {
-                        tma_load_2d(a, &tmA, kb * BK, m0, &full[st]);
-                        tma_load_2d(a + A_BYTES, &tmB, kb * BK, n0, &full[st]);
+#pragma unroll
+                        for (int i = 0; i < MT; ++i) tma_load_2d(a + i * A_BYTES, &tmA, kb * BK, m0 + i * kBM, &full[st]);
+                        tma_load_2d(a + MT * A_BYTES, &tmB, kb * BK, n0, &full[st]);
                     }
                     counts[0] = it + 1;
                 }
@@ -507,11 +526,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     const int st = it % S;
                     if (!(ok = mbar_wait_abort(&full[st], (uint32_t)((it / S) & 1), abort_flag))) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t a0 = smem_u32(smem + st * STAGE), b0s = a0 + A_BYTES;
+                    const uint32_t a0 = smem_u32(smem + st * STAGE), b0s = a0 + MT * A_BYTES;
 #pragma unroll
                     for (int k = 0; k < BK / 16; ++k)
-                        umma(d, tile_desc<BK>(a0 + k * 32), tile_desc<BK>(b0s + k * 32), IDESC,
-                             (kb > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+                        for (int i = 0; i < MT; ++i)
+                            umma(d + (uint32_t)(i * SUB_COLS), tile_desc<BK>(a0 + i * A_BYTES + k * 32),
+                                 tile_desc<BK>(b0s + k * 32), IDESC, (kb > 0 || k > 0) ? 1u : 0u);
                     umma_commit(&empty[st]);
                     counts[1] = it + 1;
                 }
@@ -528,9 +549,12 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             const int acc = lt & 1;
             if (!mbar_wait_abort(&acc_full[acc], (uint32_t)((lt / 2) & 1), abort_flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int m0 = (t % tiles_m) * kBM, n0 = (t / tiles_m) * BN;
-            const int row = m0 + q * 32 + lane;
-            const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * ACC_COLS);
+            const int n0 = (t / tiles_m) * BN;
+#pragma unroll 1
+            for (int sub = 0; sub < MT; ++sub) {
+            const int row = (t % tiles_m) * (kBM * MT) + sub * kBM + q * 32 + lane;
+            const uint32_t lane_base =
+                tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * ACC_COLS + sub * SUB_COLS);
             long long rbase = (long long)row * ldd;
             int sy = 0, sx = 0, sb = 0;
             if (sh.Wl) {
@@ -585,6 +609,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                             dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                     }
                 }
+            }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(&acc_empty[acc]);
@@ -661,7 +686,7 @@ cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const
                       int ldd, int relu, int splits, int kb_per_split, const ConvGeo& geo, const ShuffleGeo& sh,
                       cudaStream_t s)
 {
-    constexpr int smem = stages_for<BK>() * (kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
+    constexpr int smem = stages_for<BK, BN>() * (kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, OUT_BF16, BK, CONV>,
@@ -679,26 +704,27 @@ template <int BN, bool OUT_BF16, int BK, bool CONV>
 cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
                       int ldd, int relu, const ConvGeo& geo, const ShuffleGeo& sh, cudaStream_t s)
 {
-    constexpr int smem = stages_for<BK>() * (kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
+    constexpr int MT = BN <= 64 ? 2 : 1;  // narrow tiles: two 128-row sub-tiles share each weight tile
+    constexpr int smem = stages_for<BK, BN, MT>() * (MT * kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
     static int per_sm = 0, sms = 0;
     if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_ws<BN, OUT_BF16, BK, CONV>,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_ws<BN, OUT_BF16, BK, CONV, MT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         int dev = 0;
         if ((e = cudaGetDevice(&dev))) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
         int occ = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gemm_ws<BN, OUT_BF16, BK, CONV>, kWsThreads,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gemm_ws<BN, OUT_BF16, BK, CONV, MT>, kWsThreads,
                                                                smem)))
             return e;
         per_sm = occ < 1 ? 1 : occ;
     }
-    const int tiles_m = (M + kBM - 1) / kBM;
+    const int tiles_m = (M + kBM * MT - 1) / (kBM * MT);
     const int tiles = tiles_m * ((N + BN - 1) / BN);
     const int grid = tiles < sms * per_sm ? tiles : sms * per_sm;
-    k_gemm_ws<BN, OUT_BF16, BK, CONV><<<grid, kWsThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu, geo, sh,
-                                                                     tiles_m, tiles);
+    k_gemm_ws<BN, OUT_BF16, BK, CONV, MT><<<grid, kWsThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu, geo, sh,
+                                                                         tiles_m, tiles);
     return cudaGetLastError();
 }
 
