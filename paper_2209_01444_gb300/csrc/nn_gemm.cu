@@ -700,11 +700,10 @@ cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const
     return cudaGetLastError();
 }
 
-template <int BN, bool OUT_BF16, int BK, bool CONV>
-cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
-                      int ldd, int relu, const ConvGeo& geo, const ShuffleGeo& sh, cudaStream_t s)
+template <int BN, bool OUT_BF16, int BK, bool CONV, int MT>
+cudaError_t launch_ws_mt(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
+                         int ldd, int relu, const ConvGeo& geo, const ShuffleGeo& sh, cudaStream_t s)
 {
-    constexpr int MT = BN <= 64 ? 2 : 1;  // narrow tiles: two 128-row sub-tiles share each weight tile
     constexpr int smem = stages_for<BK, BN, MT>() * (MT * kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
     static int per_sm = 0, sms = 0;
     if (!per_sm) {
@@ -728,6 +727,39 @@ cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& b, void* D, const
     return cudaGetLastError();
 }
 
+int g_sms = 0;
+
+int sm_count()
+{
+    if (!g_sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            g_sms = 1;
+    }
+    return g_sms;
+}
+
+// Sub-tiles per tile: narrow tiles stack 128-row sub-tiles that share each
+// weight tile (four for N = 32 with 32-channel K blocks, two up to N = 128),
+// unless that leaves fewer tiles than SMs.
+template <int BN, bool OUT_BF16, int BK, bool CONV>
+cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
+                      int ldd, int relu, const ConvGeo& geo, const ShuffleGeo& sh, cudaStream_t s)
+{
+    sm_count();
+    constexpr int MTMAX = (BN <= 32 && BK == 32) ? 4 : BN <= 128 ? 2 : 1;
+    const long long ntiles_n = (N + BN - 1) / BN;
+    auto fills = [&](int mt) { return (M + 128LL * mt - 1) / (128LL * mt) * ntiles_n >= g_sms; };
+    if constexpr (MTMAX == 4)
+        if (fills(4)) return launch_ws_mt<BN, OUT_BF16, BK, CONV, 4>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
+    if constexpr (MTMAX >= 2)
+        if (fills(2)) return launch_ws_mt<BN, OUT_BF16, BK, CONV, 2>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
+    return launch_ws_mt<BN, OUT_BF16, BK, CONV, 1>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
+}
+
+// Widest tile that N allows: narrower tiles with more CTAs re-read A and
+// measured slower even where the wide tiles leave SMs idle.
 int bn_for(int N) { return N >= 256 ? 256 : N > 64 ? 128 : N > 32 ? 64 : 32; }
 
 template <int BK, bool CONV>
