@@ -269,3 +269,79 @@ def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: i
             sim.snapshot_save(0)
             since = 0
     return st
+
+
+def _main(argv=None) -> int:
+    """Command line: run the network forward (or one training step) on a
+    seeded random field with seeded weights and print the device time;
+    a target for profilers."""
+    import argparse
+
+    import torch
+
+    from . import workloads
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2209_01444_gb300.surrogate")
+    ap.add_argument("mode", choices=["forward", "train", "conv"])
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--cin", type=int, default=32, help="conv mode: input channels")
+    ap.add_argument("--cout", type=int, default=32, help="conv mode: output channels")
+    a = ap.parse_args(argv)
+    if a.mode == "conv":
+        return _conv_main(a)
+    net = UNet(a.batch, a.size, a.size)
+    net.set_params(workloads.unet_params(param_shapes(), 1))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(a.batch, a.size, a.size, 5, generator=g, device="cuda")
+    t = x + 0.01
+    y = torch.empty_like(x)
+    run = (lambda: net.forward(x, y)) if a.mode == "forward" else (lambda: net.train_step(x, t, 1e-4))
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"{a.mode} batch {a.batch} {a.size}x{a.size}: {e0.elapsed_time(e1) / a.reps:.3f} ms per call")
+    return 0
+
+
+def _conv_main(a) -> int:
+    """One implicit 3 x 3 convolution (lbm_nn_conv3x3) of a seeded field."""
+    import torch
+
+    lib = L.load()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn(a.batch, a.size, a.size, a.cin, generator=g, device="cuda").to(torch.bfloat16)
+    Wm = (torch.randn(a.cout, 9 * a.cin, generator=g, device="cuda") * 0.05).to(torch.bfloat16)
+    bias = torch.zeros(a.cout, device="cuda")
+    D = torch.empty(a.batch * a.size * a.size, a.cout, dtype=torch.bfloat16, device="cuda")
+    st = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def run():
+        rc = lib.lbm_nn_conv3x3(ct.c_void_p(X.data_ptr()), a.batch, a.size, a.size, a.cin, a.cin,
+                                ct.c_void_p(Wm.data_ptr()), 9 * a.cin, ct.c_void_p(D.data_ptr()), a.cout,
+                                ct.c_void_p(bias.data_ptr()), a.cout, 0, 1, st)
+        if rc != L.LBM_OK:
+            raise L.LBMError(rc, "lbm_nn_conv3x3")
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    flop = 2.0 * a.batch * a.size * a.size * 9 * a.cin * a.cout
+    print(f"conv {a.batch}x{a.size}x{a.size}, {a.cin} -> {a.cout}: {ms * 1e3:.1f} us, {flop / ms / 1e9:.0f} TFLOP/s")
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(_main())
