@@ -194,6 +194,20 @@ LBM_API int lbm_get_state_region(lbm_handle* h, int x0, int y0, int w, int hgt, 
  * storage precision).  The grain map and step counter are kept. */
 LBM_API int lbm_set_state(lbm_handle* h, const double* in);
 
+/* Periodic reductions (the paper measures tip velocities from tip positions
+ * over time): with every > 0, lbm_step stops at every multiple of `every`
+ * steps and queues the lbm_metrics reduction (tips from cx, cy along the
+ * orientation `orient`) into a device ring of `capacity` records, without
+ * host synchronisation; every = 0 turns it off.  Enabling frees the previous
+ * ring, synchronises, and records the current state if its step count is a
+ * multiple of `every`.
+ * lbm_get_monitor copies the newest min(max, recorded, capacity) records,
+ * oldest first, into out[] and, if v_tip is not NULL, the tip velocities
+ * v_tip[3 i + a] = (tip_a(record i) - tip_a(record before)) dx / elapsed time,
+ * in W0/tau0 (NaN where the earlier record is gone); synchronous. */
+LBM_API int lbm_set_monitor(lbm_handle* h, int every, int capacity, double cx, double cy, double orient);
+LBM_API int lbm_get_monitor(lbm_handle* h, lbm_metrics* out, double* v_tip, int max, int* count);
+
 /* Reductions at the current step (see lbm_metrics) with tips measured from
  * (cx, cy) along the axes of a grain of orientation `orient`.  Synchronous;
  * returns LBM_ENUMERIC (with *m filled) when a non-finite value is found. */

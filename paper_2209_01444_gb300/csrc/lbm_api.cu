@@ -66,6 +66,11 @@ struct lbm_handle {
     long long snap_steps[2] = {-1, -1};
     float *sur_x = nullptr, *sur_y = nullptr, *sur_l = nullptr;
     unsigned long long* d_mis = nullptr;
+    // periodic reductions (lbm_set_monitor): device ring of 10-double records
+    int mon_every = 0, mon_cap = 0;
+    double mon_cx = 0, mon_cy = 0, mon_c = 1, mon_s = 0;
+    double* d_ring = nullptr;
+    std::vector<long long> mon_steps;  // step of each record, in order of recording
 };
 
 namespace {
@@ -379,7 +384,7 @@ void lbm_destroy(lbm_handle* h)
     void* ptrs[] = {h->B.sc[0], h->B.sc[1], h->B.fl[0], h->B.fl[1], h->B.hist, h->B.fb, h->grain,
                     h->grain_cs, h->d_partials, h->d_red, h->d_f64, h->d_f32, h->d_seeds,
                     h->snap_sc[0], h->snap_sc[1], h->snap_fl[0], h->snap_fl[1], h->snap_hist[0], h->snap_hist[1],
-                    h->sur_x, h->sur_y, h->sur_l, h->d_mis};
+                    h->sur_x, h->sur_y, h->sur_l, h->d_mis, h->d_ring};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;
@@ -455,11 +460,11 @@ int lbm_init_fields(lbm_handle* h, const double* fields, const double* orient)
     return finish_init(h);
 }
 
-int lbm_step(lbm_handle* h, int nsteps)
+namespace {
+
+int step_chunk(lbm_handle* h, int nsteps)
 {
-    int rc = ensure_initialised(h);
-    if (rc) return rc;
-    if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
+    int rc;
     int left = nsteps;
     while (!h->profiling && left >= kGraphSteps) {
         cudaGraphExec_t ex;
@@ -470,6 +475,107 @@ int lbm_step(lbm_handle* h, int nsteps)
     }
     if ((rc = run_steps_direct(h, left))) return rc;
     h->steps += left;
+    return LBM_OK;
+}
+
+// Queues the metrics reduction of the current state into the next ring slot.
+int monitor_record(lbm_handle* h)
+{
+    const int slot = (int)(h->mon_steps.size() % (size_t)h->mon_cap);
+    LBM_CUDA(h, lbm::launch_reduce(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->mon_cx, h->mon_cy,
+                                   h->mon_c, h->mon_s, h->d_partials, h->d_ring + (size_t)slot * 10, h->stream));
+    h->mon_steps.push_back(h->steps);
+    return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_step(lbm_handle* h, int nsteps)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
+    if (!h->mon_every) return step_chunk(h, nsteps);
+    // with a monitor: stop at every multiple of the period and record
+    int left = nsteps;
+    while (left > 0) {
+        const int to_next = h->mon_every - (int)(h->steps % h->mon_every);
+        const int n = left < to_next ? left : to_next;
+        if ((rc = step_chunk(h, n))) return rc;
+        left -= n;
+        if (h->steps % h->mon_every == 0 && (rc = monitor_record(h))) return rc;
+    }
+    return LBM_OK;
+}
+
+int lbm_set_monitor(lbm_handle* h, int every, int capacity, double cx, double cy, double orient)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (every < 0 || (every > 0 && (capacity < 2 || capacity > (1 << 20))))
+        return fail(h, LBM_EINVAL, "monitor: every >= 0 and 2 <= capacity <= 2^20");
+    if (!isfinite(cx) || !isfinite(cy) || !isfinite(orient)) return fail(h, LBM_EINVAL, "non-finite tip origin");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->d_ring) {
+        cudaFree(h->d_ring);
+        h->d_ring = nullptr;
+    }
+    h->mon_steps.clear();
+    h->mon_every = every;
+    h->mon_cap = capacity;
+    if (!every) return LBM_OK;
+    h->mon_cx = cx;
+    h->mon_cy = cy;
+    h->mon_c = cos(orient);
+    h->mon_s = sin(orient);
+    LBM_CUDA(h, cudaMalloc((void**)&h->d_ring, (size_t)capacity * 10 * sizeof(double)));
+    if (h->steps % every == 0) return monitor_record(h);
+    return LBM_OK;
+}
+
+int lbm_get_monitor(lbm_handle* h, lbm_metrics* out, double* v_tip, int max, int* count)
+{
+    if (!h || !count || (max > 0 && !out)) return LBM_EINVAL;
+    *count = 0;
+    if (!h->mon_every) return LBM_OK;
+    const size_t total = h->mon_steps.size();
+    const size_t avail = total < (size_t)h->mon_cap ? total : (size_t)h->mon_cap;
+    std::vector<double> ring((size_t)h->mon_cap * 10);
+    LBM_CUDA(h, cudaMemcpyAsync(ring.data(), h->d_ring, ring.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    const size_t first = total - avail;  // oldest record still in the ring
+    const size_t n = avail < (size_t)max ? avail : (size_t)(max > 0 ? max : 0);
+    const size_t start = total - n;      // the newest n records, oldest first
+    const double N = (double)h->P.nx * h->P.ny;
+    for (size_t i = 0; i < n; ++i) {
+        const size_t k = start + i;
+        const double* r = &ring[(k % (size_t)h->mon_cap) * 10];
+        lbm_metrics& m = out[i];
+        m.tip[0] = r[7];
+        m.tip[1] = r[8];
+        m.tip[2] = r[9];
+        m.solid_fraction = r[0] / N;
+        m.sum_C = r[1];
+        m.sum_H = r[2];
+        m.sum_h = r[3];
+        m.max_u = r[4] / h->vf;
+        m.nonfinite = r[5] > 0 ? 1.0 : 0.0;
+        m.sum_phi = r[6];
+        m.step = h->mon_steps[k];
+        if (v_tip) {
+            for (int a = 0; a < 3; ++a) {
+                double v = NAN;
+                if (i > 0 || k > first) {
+                    const double* p = &ring[((k - 1) % (size_t)h->mon_cap) * 10];
+                    const double dt = (double)(h->mon_steps[k] - h->mon_steps[k - 1]) * h->prm.dt;
+                    v = (r[7 + a] - p[7 + a]) * h->prm.dx / dt;
+                }
+                v_tip[i * 3 + a] = v;
+            }
+        }
+    }
+    *count = (int)n;
     return LBM_OK;
 }
 

@@ -138,6 +138,8 @@ SIGNATURES = {
     "lbm_unet_output": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_last_error": (ct.c_char_p, [ct.c_void_p]),
     "lbm_unet_shape": (ct.c_int, [ct.c_void_p] + [ct.POINTER(ct.c_int)] * 4),
+    "lbm_set_monitor": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_double, ct.c_double, ct.c_double]),
+    "lbm_get_monitor": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int)]),
     "lbm_snapshot_save": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "lbm_snapshot_restore": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "lbm_fields_nhwc": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
@@ -296,6 +298,27 @@ class Simulation:
         return {"tip_px": m.tip[0], "tip_mx": m.tip[1], "tip_py": m.tip[2], "solid_fraction": m.solid_fraction,
                 "sum_C": m.sum_C, "sum_H": m.sum_H, "sum_h": m.sum_h, "max_u": m.max_u,
                 "nonfinite": m.nonfinite, "sum_phi": m.sum_phi, "step": m.step, "rc": rc}
+
+    # ---- periodic reductions
+    def set_monitor(self, every: int, capacity: int, cx: float, cy: float, orient: float = 0.0) -> None:
+        self._check(self.lib.lbm_set_monitor(self.h, int(every), int(capacity), cx, cy, orient))
+
+    def monitor(self, max_records: int = 1 << 20) -> list[dict]:
+        """Recorded metrics, oldest first, each with the tip velocities v_tip
+        (paper units; NaN for the first record)."""
+        cap = max(1, int(max_records))
+        arr = (lbm_metrics * cap)()
+        v = np.empty(3 * cap)
+        n = ct.c_int()
+        self._check(self.lib.lbm_get_monitor(self.h, arr, v.ctypes.data_as(ct.c_void_p), cap, ct.byref(n)))
+        out = []
+        for i in range(n.value):
+            m = arr[i]
+            out.append({"step": m.step, "tip_px": m.tip[0], "tip_mx": m.tip[1], "tip_py": m.tip[2],
+                        "v_px": v[3 * i], "v_mx": v[3 * i + 1], "v_py": v[3 * i + 2],
+                        "solid_fraction": m.solid_fraction, "sum_C": m.sum_C, "sum_H": m.sum_H, "sum_h": m.sum_h,
+                        "max_u": m.max_u, "nonfinite": m.nonfinite, "sum_phi": m.sum_phi})
+        return out
 
     # ---- device-side exchange with the surrogate network
     def snapshot_save(self, slot: int = 0) -> None:
