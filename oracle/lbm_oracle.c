@@ -731,6 +731,63 @@ static void coupled_step(orc_sim* s)
     s->steps++;
 }
 
+/* Flow-only steps with phi, C and theta frozen: the flow model of Sec. 3.4
+ * alone, as in the stationary-cylinder problem of Sec. 4.1 (the phase field
+ * does not evolve there).  Each step is one collision + streaming of h with
+ * the fluid-solid force and the body force of the frozen fields, then the
+ * flow boundaries (the same operations as a two-time-scaling sub-step).  The
+ * coupled-step count does not change. */
+int orc_step_flow(orc_sim* s, int nsteps)
+{
+    if (!s || nsteps < 0) return -1;
+    const int nx = s->nx, ny = s->ny;
+    compute_macros(s);
+    for (int n = 0; n < nsteps; ++n) {
+#pragma omp parallel for schedule(static)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int idx = y * nx + x;
+                double Fx, Fy;
+                body_force(s, s->theta[idx], s->C[idx], &Fx, &Fy);
+                collide_stream_flow(s, x, y, s->phi[idx], Fx, Fy);
+            }
+        apply_boundaries(s, s->f, s->nC, s->g, 1);
+        swap_ptr(&s->h, &s->h2);
+    }
+    return 0;
+}
+
+/* Hydrodynamic force and torque on the solid, Eq. (27) (HDforce): the paper
+ * sums f over the nodes covered by the solid; in the diffuse interface the
+ * force the flow feels at a node is [1 - q~] f (Eq. 24), so the sum here is
+ * weighted by 1 - q~ = (1 + phi)/2 (reading).  With dx = 1 in flow lattice
+ * units: out[0..1] = F_f = -sum (1 - q~) f, out[2] = T_f = -sum (x - xs) x
+ * (1 - q~) f about (cx, cy), in flow lattice units. */
+int orc_force(orc_sim* s, double cx, double cy, double* out)
+{
+    if (!s || !out) return -1;
+    compute_macros(s);
+    const int nx = s->nx, ny = s->ny, N = s->N;
+    double Fx = 0, Fy = 0, T = 0;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const int idx = y * nx + x;
+            double hn[9];
+            for (int i = 0; i < 9; ++i) hn[i] = s->h[i * N + idx];
+            double bx, by, ux, uy, fsx, fsy, p;
+            body_force(s, s->theta[idx], s->C[idx], &bx, &by);
+            flow_macros(hn, s->phi[idx], bx, by, &ux, &uy, &fsx, &fsy, &p);
+            const double w = 0.5 * (1.0 + s->phi[idx]);
+            Fx -= w * fsx;
+            Fy -= w * fsy;
+            T -= (x - cx) * w * fsy - (y - cy) * w * fsx;
+        }
+    out[0] = Fx;
+    out[1] = Fy;
+    out[2] = T;
+    return 0;
+}
+
 int orc_step(orc_sim* s, int nsteps)
 {
     if (!s || nsteps < 0) return -1;

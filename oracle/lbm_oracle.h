@@ -36,6 +36,8 @@ int orc_init_seeds_window(orc_sim* s, const double* seeds, int ns, double U0, do
                           int gnx, int gny, int gpx, int gpy);
 int orc_init_fields(orc_sim* s, const double* fields, const double* orient);
 int orc_step(orc_sim* s, int nsteps);
+int orc_step_flow(orc_sim* s, int nsteps);
+int orc_force(orc_sim* s, double cx, double cy, double* out);
 long long orc_step_count(const orc_sim* s);
 int orc_get_fields(orc_sim* s, double* out);
 int orc_get_state(const orc_sim* s, double* out);

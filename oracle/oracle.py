@@ -76,6 +76,8 @@ def _load():
     lib.orc_init_seeds_window.argtypes = [ct.c_void_p, dp, ct.c_int, ct.c_double, ct.c_double] + [ct.c_int] * 6
     lib.orc_init_fields.argtypes = [ct.c_void_p, dp, dp]
     lib.orc_step.argtypes = [ct.c_void_p, ct.c_int]
+    lib.orc_step_flow.argtypes = [ct.c_void_p, ct.c_int]
+    lib.orc_force.argtypes = [ct.c_void_p, ct.c_double, ct.c_double, dp]
     lib.orc_step_count.restype = ct.c_longlong
     lib.orc_step_count.argtypes = [ct.c_void_p]
     for name in ("orc_get_fields", "orc_get_state", "orc_set_state", "orc_get_orient", "orc_lattice_params"):
@@ -165,6 +167,17 @@ class Oracle:
     def step(self, n: int = 1) -> None:
         if self.lib.orc_step(self.h, int(n)):
             raise ValueError("step failed")
+
+    def step_flow(self, n: int = 1) -> None:
+        """n flow-only steps with phi, C, theta frozen."""
+        if self.lib.orc_step_flow(self.h, int(n)):
+            raise ValueError("step_flow failed")
+
+    def force(self, cx: float, cy: float) -> tuple[float, float, float]:
+        """Hydrodynamic force (x, y) and torque about (cx, cy), flow lattice units."""
+        out = np.empty(3)
+        self.lib.orc_force(self.h, cx, cy, _ptr(out))
+        return float(out[0]), float(out[1]), float(out[2])
 
     @property
     def steps(self) -> int:

@@ -252,3 +252,20 @@ def surrogate_domains(count: int = 32, n: int = 256, rng_seed: int = 5, steps: i
                                  u_in=(uin * DX / DT, 0.0))
         cases.append(Case(f"surrogate_{j}_{n}", p, np.array([[cx, cy, R, orient]]), 0.0, -delta, steps))
     return cases
+
+
+def cylinder_flow(Re: float = 40.0, nx: int = 1400, ny: int = 800, R: float = 20.0, u0: float = 0.1) -> Case:
+    """Flow past a stationary cylinder (Sec. 4.1): a (70 x 40) R_s domain of
+    nx x ny nodes, the disc of radius R nodes at (20 R, 20 R) as a diffuse
+    circle with W0 = 0.5 dx, inflow u0 = 0.1 (lattice) on the left, outflow on
+    the right, symmetry walls at the top and bottom (reading), Re = 2 u0 R / nu.
+    Paper units: W0 = tau0 = 1, dx = 2 W0, dt = tau0, so nu (lattice) = 4 / Re
+    for R = 20, u0 = 0.1, and s2 = 1.25 at Re = 40 as in the paper.  No
+    buoyancy; the scalar fields are frozen by the flow-only stepping."""
+    dx, dt = 2.0, 1.0
+    nu_lu = 2.0 * u0 * R / Re
+    p = thermosolutal_params(nx, ny, dx=dx, dt=dt, nu=nu_lu * dx * dx / dt, gbetaT=0.0, gbetaC=0.0,
+                             bc=("inflow", "outflow", "symmetry", "symmetry"), u_in=(u0 * dx / dt, 0.0),
+                             theta_ref=-0.55)
+    seeds = np.array([[R * 20.0, R * 20.0, R, 0.0]])
+    return Case(f"cylinder_Re{Re:g}_{nx}x{ny}", p, seeds, 0.0, -0.55, 0)
