@@ -194,6 +194,19 @@ LBM_API int lbm_get_state_region(lbm_handle* h, int x0, int y0, int w, int hgt, 
  * storage precision).  The grain map and step counter are kept. */
 LBM_API int lbm_set_state(lbm_handle* h, const double* in);
 
+/* Flow-only steps: the flow model alone (collision, streaming, flow walls)
+ * with phi, C and theta frozen at their current values, as in the stationary-
+ * cylinder problem of Sec. 4.1.  The coupled-step count does not change.
+ * Queued on the handle's stream; the flow populations alternate buffers as in
+ * lbm_step. */
+LBM_API int lbm_step_flow(lbm_handle* h, int nsteps);
+/* Hydrodynamic force and torque on the solid, Eq. (27): out[0..1] = F_f =
+ * -sum (1 - q~) f, out[2] = T_f = -sum (x - (cx, cy)) x (1 - q~) f, summed in
+ * FP64 over all nodes in flow lattice units, with f = (u_s - u*)/dt, u_s = 0
+ * and the diffuse-interface weight 1 - q~ = (1 + phi)/2 of Eq. (24).
+ * Synchronous. */
+LBM_API int lbm_get_force(lbm_handle* h, double cx, double cy, double* out);
+
 /* Periodic reductions (the paper measures tip velocities from tip positions
  * over time): with every > 0, lbm_step stops at every multiple of `every`
  * steps and queues the lbm_metrics reduction (tips from cx, cy along the

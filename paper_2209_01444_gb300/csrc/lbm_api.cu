@@ -71,6 +71,8 @@ struct lbm_handle {
     double mon_cx = 0, mon_cy = 0, mon_c = 1, mon_s = 0;
     double* d_ring = nullptr;
     std::vector<long long> mon_steps;  // step of each record, in order of recording
+    // flow-only steps: frozen phi and F_y
+    float *flow_phi = nullptr, *flow_fy = nullptr;
 };
 
 namespace {
@@ -384,7 +386,7 @@ void lbm_destroy(lbm_handle* h)
     void* ptrs[] = {h->B.sc[0], h->B.sc[1], h->B.fl[0], h->B.fl[1], h->B.hist, h->B.fb, h->grain,
                     h->grain_cs, h->d_partials, h->d_red, h->d_f64, h->d_f32, h->d_seeds,
                     h->snap_sc[0], h->snap_sc[1], h->snap_fl[0], h->snap_fl[1], h->snap_hist[0], h->snap_hist[1],
-                    h->sur_x, h->sur_y, h->sur_l, h->d_mis, h->d_ring};
+                    h->sur_x, h->sur_y, h->sur_l, h->d_mis, h->d_ring, h->flow_phi, h->flow_fy};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;
@@ -505,6 +507,36 @@ int lbm_step(lbm_handle* h, int nsteps)
         left -= n;
         if (h->steps % h->mon_every == 0 && (rc = monitor_record(h))) return rc;
     }
+    return LBM_OK;
+}
+
+int lbm_step_flow(lbm_handle* h, int nsteps)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
+    if (!h->flow_phi) {
+        LBM_CUDA(h, cudaMalloc((void**)&h->flow_phi, (size_t)h->P.plane * sizeof(float)));
+        LBM_CUDA(h, cudaMalloc((void**)&h->flow_fy, (size_t)h->P.plane * sizeof(float)));
+    }
+    LBM_CUDA(h, lbm::launch_flow_inputs(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->flow_phi, h->flow_fy,
+                                        h->stream));
+    void* const fl[2] = {h->B.fl[0], h->B.fl[1]};
+    LBM_CUDA(h, lbm::flow_steps(h->P, h->storage, nsteps, h->B.sc[h->B.cs], fl, &h->B.cf, h->flow_phi, h->flow_fy,
+                                h->stream));
+    return LBM_OK;
+}
+
+int lbm_get_force(lbm_handle* h, double cx, double cy, double* out)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (!isfinite(cx) || !isfinite(cy)) return fail(h, LBM_EINVAL, "non-finite centre");
+    LBM_CUDA(h, lbm::launch_force(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], cx, cy, h->d_partials,
+                                  h->d_red, h->stream));
+    LBM_CUDA(h, cudaMemcpyAsync(out, h->d_red, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
 

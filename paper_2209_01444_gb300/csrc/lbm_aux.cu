@@ -339,6 +339,69 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks,
     out[k] = v;
 }
 
+// Hydrodynamic force and torque on the solid (Eq. 27, weighted by 1 - q~ =
+// (1 + phi)/2, the share of the fluid-solid force the flow feels): per-block
+// FP64 partials of -sum w f_x, -sum w f_y and -sum ((x - cx) w f_y - (y - cy) w f_x).
+template <class Store>
+__global__ void __launch_bounds__(kRedThreads) k_force(const StepParams P, const void* __restrict__ sc,
+                                                       const void* __restrict__ fl, double cx, double cy,
+                                                       double* __restrict__ partials)
+{
+    double acc[3] = {0, 0, 0};
+    const long long N = (long long)P.nx * P.ny;
+    for (long long t = blockIdx.x * (long long)kRedThreads + threadIdx.x; t < N;
+         t += (long long)gridDim.x * kRedThreads) {
+        const int y = (int)(t / P.nx), x = (int)(t - (long long)y * P.nx);
+        const long long o = (long long)y * P.pitch + x;
+        float f[5], n[5], g[5], h[9];
+        load_node<Store>(P, sc, fl, o, f, n, g, h);
+        const Macro m = node_macros(f, n, g, h, P);
+        const double w = 0.5 * (double)m.p1;
+        const double fx = w * (double)m.fsx, fy = w * (double)m.fsy;
+        acc[0] -= fx;
+        acc[1] -= fy;
+        acc[2] -= (x - cx) * fy - (y - cy) * fx;
+    }
+    __shared__ double sm[3][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sm[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) v += sm[threadIdx.x][w];
+        partials[(long long)blockIdx.x * 3 + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_force_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out)
+{
+    const int k = threadIdx.x;
+    if (k >= 3) return;
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) v += partials[(long long)b * 3 + k];
+    out[k] = v;
+}
+
+// Frozen inputs of flow-only steps: phi and the body force F_y of every node.
+template <class Store>
+__global__ void k_flow_inputs(const StepParams P, const void* __restrict__ sc, const void* __restrict__ fl,
+                              float* __restrict__ phi, float* __restrict__ fy)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long o = (long long)y * P.pitch + x;
+    float f[5], n[5], g[5], h[9];
+    load_node<Store>(P, sc, fl, o, f, n, g, h);
+    const Macro m = node_macros(f, n, g, h, P);
+    phi[o] = m.phi;
+    fy[o] = m.Fy;
+}
+
 template <class Store>
 __device__ __forceinline__ double phi_at(const StepParams& P, const void* sc, int x, int y)
 {
@@ -511,6 +574,31 @@ cudaError_t launch_set_fields_nhwc(const StepParams& P, int storage, const float
     case kStoreBF16: return set_fields_nhwc_t<StoreBF16>(P, src, vf, sc, fl, hist, prev, K, s);
     default: return set_fields_nhwc_t<StoreF32>(P, src, vf, sc, fl, hist, prev, K, s);
     }
+}
+
+cudaError_t launch_force(const StepParams& P, int storage, const void* sc, const void* fl, double cx, double cy,
+                         double* partials, double* out, cudaStream_t st)
+{
+    const int nb = reduce_blocks(P);
+    switch (storage) {
+    case kStoreF16: k_force<StoreF16><<<nb, kRedThreads, 0, st>>>(P, sc, fl, cx, cy, partials); break;
+    case kStoreBF16: k_force<StoreBF16><<<nb, kRedThreads, 0, st>>>(P, sc, fl, cx, cy, partials); break;
+    default: k_force<StoreF32><<<nb, kRedThreads, 0, st>>>(P, sc, fl, cx, cy, partials); break;
+    }
+    k_force_final<<<1, 32, 0, st>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow_inputs(const StepParams& P, int storage, const void* sc, const void* fl, float* phi, float* fy,
+                               cudaStream_t st)
+{
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
+    switch (storage) {
+    case kStoreF16: k_flow_inputs<StoreF16><<<g, b, 0, st>>>(P, sc, fl, phi, fy); break;
+    case kStoreBF16: k_flow_inputs<StoreBF16><<<g, b, 0, st>>>(P, sc, fl, phi, fy); break;
+    default: k_flow_inputs<StoreF32><<<g, b, 0, st>>>(P, sc, fl, phi, fy); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_phi_mismatch(const float* a, const float* b, long long n, unsigned long long* out, cudaStream_t s)

@@ -80,6 +80,14 @@ cudaError_t launch_fields_nhwc(const StepParams& P, int storage, const void* sc,
                                float* dst, cudaStream_t s);
 cudaError_t launch_set_fields_nhwc(const StepParams& P, int storage, const float* src, float vf, void* sc, void* fl,
                                    float* hist, const float* prev, int K, cudaStream_t s);
+cudaError_t launch_force(const StepParams& P, int storage, const void* sc, const void* fl, double cx, double cy,
+                         double* partials, double* out, cudaStream_t st);
+cudaError_t launch_flow_inputs(const StepParams& P, int storage, const void* sc, const void* fl, float* phi, float* fy,
+                               cudaStream_t st);
+// n flow-only steps (collide + stream h, flow walls) with frozen phi and F_y;
+// *cf is the flow buffer parity, updated.
+cudaError_t flow_steps(const StepParams& P, int storage, int n, void* sc, void* const fl[2], int* cf, const float* phi,
+                       const float* fy, cudaStream_t s);
 cudaError_t launch_phi_mismatch(const float* a, const float* b, long long n, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
                           cudaStream_t s);

@@ -388,6 +388,21 @@ cudaError_t walls(const StepParams& P, void* sc, void* fl, int flow_only, cudaSt
 }
 
 template <class Store>
+cudaError_t flow_steps_t(const StepParams& P, int n, void* sc, void* const fl[2], int* cf, const float* phi,
+                         const float* fy, cudaStream_t s)
+{
+    const dim3 fblock(64, 4), fgrid((P.nx + 63) / 64, (P.ny + 3) / 4);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < n; ++k) {
+        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, fl[*cf], fl[1 - *cf], phi, fy);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = walls<Store>(P, sc, fl[1 - *cf], 1, s)) != cudaSuccess) return e;
+        *cf = 1 - *cf;
+    }
+    return e;
+}
+
+template <class Store>
 cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStream_t s)
 {
     const dim3 block(TX, TY), grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
@@ -482,6 +497,16 @@ int batch_resident_ctas(int storage, int ty)
     if (storage == kStoreF16) return ty == 4 ? batch_ctas_t<StoreF16, 4>() : ty == 16 ? batch_ctas_t<StoreF16, 16>() : batch_ctas_t<StoreF16, 8>();
     if (storage == kStoreBF16) return ty == 4 ? batch_ctas_t<StoreBF16, 4>() : ty == 16 ? batch_ctas_t<StoreBF16, 16>() : batch_ctas_t<StoreBF16, 8>();
     return ty == 4 ? batch_ctas_t<StoreF32, 4>() : ty == 16 ? batch_ctas_t<StoreF32, 16>() : batch_ctas_t<StoreF32, 8>();
+}
+
+cudaError_t flow_steps(const StepParams& P, int storage, int n, void* sc, void* const fl[2], int* cf, const float* phi,
+                       const float* fy, cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return flow_steps_t<StoreF16>(P, n, sc, fl, cf, phi, fy, s);
+    case kStoreBF16: return flow_steps_t<StoreBF16>(P, n, sc, fl, cf, phi, fy, s);
+    default: return flow_steps_t<StoreF32>(P, n, sc, fl, cf, phi, fy, s);
+    }
 }
 
 cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s)

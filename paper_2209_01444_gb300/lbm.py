@@ -138,6 +138,8 @@ SIGNATURES = {
     "lbm_unet_output": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_last_error": (ct.c_char_p, [ct.c_void_p]),
     "lbm_unet_shape": (ct.c_int, [ct.c_void_p] + [ct.POINTER(ct.c_int)] * 4),
+    "lbm_step_flow": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "lbm_get_force": (ct.c_int, [ct.c_void_p, ct.c_double, ct.c_double, ct.c_void_p]),
     "lbm_set_monitor": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_double, ct.c_double, ct.c_double]),
     "lbm_get_monitor": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int)]),
     "lbm_snapshot_save": (ct.c_int, [ct.c_void_p, ct.c_int]),
@@ -298,6 +300,17 @@ class Simulation:
         return {"tip_px": m.tip[0], "tip_mx": m.tip[1], "tip_py": m.tip[2], "solid_fraction": m.solid_fraction,
                 "sum_C": m.sum_C, "sum_H": m.sum_H, "sum_h": m.sum_h, "max_u": m.max_u,
                 "nonfinite": m.nonfinite, "sum_phi": m.sum_phi, "step": m.step, "rc": rc}
+
+    # ---- flow-only steps and the hydrodynamic force
+    def step_flow(self, n: int = 1) -> None:
+        """n steps of the flow model alone, phi, C and theta frozen."""
+        self._check(self.lib.lbm_step_flow(self.h, int(n)))
+
+    def force(self, cx: float, cy: float) -> tuple[float, float, float]:
+        """Hydrodynamic force (x, y) on the solid and torque about (cx, cy), flow lattice units."""
+        out = np.empty(3)
+        self._check(self.lib.lbm_get_force(self.h, cx, cy, out.ctypes.data_as(ct.c_void_p)))
+        return float(out[0]), float(out[1]), float(out[2])
 
     # ---- periodic reductions
     def set_monitor(self, every: int, capacity: int, cx: float, cy: float, orient: float = 0.0) -> None:
