@@ -103,6 +103,35 @@ __global__ void k_maxpool_fwd(const bf16* __restrict__ X, int B, int H, int W, i
     Y[p * C + c] = __float2bfloat16(m);
 }
 
+// The same, eight channels per thread with 16-byte loads and stores (C and
+// xpitch multiples of 8, 16-byte aligned bases).
+__global__ void k_maxpool_fwd8(const bf16* __restrict__ X, int B, int H, int W, int C, int xpitch,
+                               bf16* __restrict__ Y)
+{
+    const int Ho = H / 2, Wo = W / 2, G = C / 8;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)B * Ho * Wo * G) return;
+    const int g = (int)(i % G);
+    const long long p = i / G;
+    const int x = (int)(p % Wo), y = (int)((p / Wo) % Ho), b = (int)(p / ((long long)Wo * Ho));
+    const bf16* base = X + (((long long)b * H + 2 * y) * W + 2 * x) * xpitch + g * 8;
+    const uint4 q[4] = {*(const uint4*)base, *(const uint4*)(base + xpitch), *(const uint4*)(base + (long long)W * xpitch),
+                        *(const uint4*)(base + (long long)W * xpitch + xpitch)};
+    __nv_bfloat162 r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float2 m = __bfloat1622float2(((const __nv_bfloat162*)&q[0])[j]);
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            const float2 v = __bfloat1622float2(((const __nv_bfloat162*)&q[k])[j]);
+            m.x = fmaxf(m.x, v.x);
+            m.y = fmaxf(m.y, v.y);
+        }
+        r[j] = __floats2bfloat162_rn(m.x, m.y);
+    }
+    *(uint4*)(Y + p * C + g * 8) = *(const uint4*)r;
+}
+
 // The gradient goes to the first maximum of each 2 x 2 window (row-major order).
 __global__ void k_maxpool_bwd(const bf16* __restrict__ X, int B, int H, int W, int C, int xpitch,
                               const float* __restrict__ dY, float* __restrict__ dX, int dpitch)
@@ -250,6 +279,18 @@ __global__ void k_flip3x3(const bf16* __restrict__ W, int cout, int cin, bf16* _
     Wf[((long long)ci * 9 + (8 - t)) * cout + co] = W[i];
 }
 
+// Wp[co][t * cin_pad + ci] = W[co][t * cin + ci] for ci < cin, else 0: the
+// kernel of a convolution whose input carries cin_pad channels, the extra ones zero.
+__global__ void k_pad_conv3x3(const bf16* __restrict__ W, int cout, int cin, int cin_pad, bf16* __restrict__ Wp)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)cout * 9 * cin_pad) return;
+    const int ci = (int)(i % cin_pad);
+    const long long r = i / cin_pad;
+    const int t = (int)(r % 9), co = (int)(r / 9);
+    Wp[i] = ci < cin ? W[((long long)co * 9 + t) * cin + ci] : __float2bfloat16(0.0f);
+}
+
 // Column sums of a [rows][C] matrix (pitch), as per-block partials over row chunks.
 template <class G>
 __global__ void k_colsum_part(const G* __restrict__ g, long long rows, int C, int pitch, int chunk,
@@ -330,6 +371,25 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
 
 // FP32 [P][F] fields -> BF16 NHWC [P][cpitch] with (x - mean) / std per field
 // and zero extra channels.
+// One thread per pixel: F <= 8 fields in, cpitch BF16 channels out as
+// 16-byte stores (cpitch a multiple of 8, X 16-byte aligned).
+__global__ void k_pack_px(const float* __restrict__ f, long long P, int F, const float* __restrict__ mean,
+                          const float* __restrict__ inv_std, bf16* __restrict__ X, int cpitch)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    __nv_bfloat162 h[4];
+    float v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = c < F ? (f[p * F + c] - mean[c]) * inv_std[c] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    uint4* dst = (uint4*)(X + p * cpitch);
+    dst[0] = *(const uint4*)h;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (int g = 1; g < cpitch / 8; ++g) dst[g] = z;
+}
+
 // R (optional) receives the same normalised fields in FP32 [P][F].
 __global__ void k_pack(const float* __restrict__ f, long long P, int F, const float* __restrict__ mean,
                        const float* __restrict__ inv_std, bf16* __restrict__ X, int cpitch, float* __restrict__ R)
@@ -364,13 +424,17 @@ __global__ void k_increment(const float* __restrict__ t, const float* __restrict
     T[i] = (t[i] - x[i]) * inv_out[(int)(i % F)];
 }
 
-// y[p][c] = x[p][c] + Y[p][c] / inv_out[c].
+// y[p][c] = x[p][c] + Y[p][c] / inv_out[c]; a block covers a contiguous run
+// of elements, and the per-field scale comes from a shared table.
 __global__ void k_add_increment(const float* __restrict__ Y, const float* __restrict__ x, long long P, int F,
                                 const float* __restrict__ inv_out, float* __restrict__ y)
 {
+    __shared__ float so[8];
+    if (threadIdx.x < F) so[threadIdx.x] = 1.0f / inv_out[threadIdx.x];
+    __syncthreads();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= P * F) return;
-    y[i] = x[i] + Y[i] / inv_out[(int)(i % F)];
+    y[i] = x[i] + Y[i] * so[(int)(i % F)];
 }
 
 // FP32 fields [P][F] = mean + std * Y[P][F] (undo the normalisation).
@@ -420,8 +484,12 @@ cudaError_t transpose(const void* in, int rows, int cols, int ipitch, void* out,
 cudaError_t maxpool_fwd(const void* X, int B, int H, int W, int C, int xpitch, void* Y, cudaStream_t s)
 {
     if (H % 2 || W % 2) return cudaErrorInvalidValue;
-    k_maxpool_fwd<<<blocks((long long)B * (H / 2) * (W / 2) * C), 256, 0, s>>>((const bf16*)X, B, H, W, C, xpitch,
-                                                                             (bf16*)Y);
+    if (C % 8 == 0 && xpitch % 8 == 0 && (((uintptr_t)X | (uintptr_t)Y) & 15) == 0)
+        k_maxpool_fwd8<<<blocks((long long)B * (H / 2) * (W / 2) * (C / 8)), 256, 0, s>>>((const bf16*)X, B, H, W, C,
+                                                                                        xpitch, (bf16*)Y);
+    else
+        k_maxpool_fwd<<<blocks((long long)B * (H / 2) * (W / 2) * C), 256, 0, s>>>((const bf16*)X, B, H, W, C, xpitch,
+                                                                                 (bf16*)Y);
     return cudaGetLastError();
 }
 
@@ -474,6 +542,13 @@ cudaError_t proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, c
     return cudaGetLastError();
 }
 
+cudaError_t pad_conv3x3(const void* W, int cout, int cin, int cin_pad, void* Wp, cudaStream_t s)
+{
+    if (cin_pad < cin) return cudaErrorInvalidValue;
+    k_pad_conv3x3<<<blocks((long long)cout * 9 * cin_pad), 256, 0, s>>>((const bf16*)W, cout, cin, cin_pad, (bf16*)Wp);
+    return cudaGetLastError();
+}
+
 cudaError_t flip3x3(const void* W, int cout, int cin, void* Wf, cudaStream_t s)
 {
     k_flip3x3<<<blocks((long long)cout * 9 * cin), 256, 0, s>>>((const bf16*)W, cout, cin, (bf16*)Wf);
@@ -514,7 +589,10 @@ cudaError_t pack(const float* f, long long P, int F, const float* mean, const fl
                  float* R, cudaStream_t s)
 {
     if (F > cpitch) return cudaErrorInvalidValue;
-    k_pack<<<blocks(P * cpitch), 256, 0, s>>>(f, P, F, mean, inv_std, (bf16*)X, cpitch, R);
+    if (X && !R && F <= 8 && cpitch % 8 == 0 && ((uintptr_t)X & 15) == 0)
+        k_pack_px<<<blocks(P), 256, 0, s>>>(f, P, F, mean, inv_std, (bf16*)X, cpitch);
+    else
+        k_pack<<<blocks(P * cpitch), 256, 0, s>>>(f, P, F, mean, inv_std, (bf16*)X, cpitch, R);
     return cudaGetLastError();
 }
 

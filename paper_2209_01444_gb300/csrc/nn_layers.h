@@ -21,6 +21,7 @@ cudaError_t proj_fwd(const void* X, int P, int C, int xpitch, const float* Wt, c
 cudaError_t proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, const float* Wt, int O, float* dX,
                      int dpitch, float* dW, float* db, float* part, int part_blocks, cudaStream_t s);
 cudaError_t flip3x3(const void* W, int cout, int cin, void* Wf, cudaStream_t s);
+cudaError_t pad_conv3x3(const void* W, int cout, int cin, int cin_pad, void* Wp, cudaStream_t s);
 cudaError_t colsum(const void* g, bool g_fp32, long long rows, int C, int pitch, float* out, float* part,
                    int part_blocks, cudaStream_t s);
 cudaError_t mse(const float* pred, const float* target, long long n, float* grad, float* loss, float* part,

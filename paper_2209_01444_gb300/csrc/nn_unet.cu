@@ -34,13 +34,16 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kInPitch = 8;  // input channels (fields, zero padded)
+constexpr int kInPitch = 8;   // input channels the first convolution's weights see (fields, zero padded)
+constexpr int kX0Pitch = 32;  // stored input pitch: the first convolution runs as a 32-channel implicit one
 constexpr int kPartBlocks = 1024;
 
 struct Conv {
     int cin = 0, cout = 0;
     long long w = 0, b = 0;  // offsets in the padded parameter vector
     bf16* wf = nullptr;      // [cin][9 cout] rotated kernel for the input gradient
+    bf16* wpad = nullptr;    // [cout][9 cin_pad] kernel with zero channels (first convolution only)
+    int cin_pad = 0;
 };
 
 struct Up {
@@ -214,7 +217,7 @@ cudaError_t allocate(lbm_unet* u)
     UN_ALLOC(u->inv_std, kInPitch);
     UN_ALLOC(u->inv_out, kInPitch);
     const long long P0 = u->P0;
-    UN_ALLOC(u->x0, P0 * kInPitch);
+    UN_ALLOC(u->x0, P0 * kX0Pitch);
     UN_ALLOC(u->Y, P0 * u->F);
     UN_ALLOC(u->T, P0 * u->F);
     UN_ALLOC(u->G, P0 * u->F);
@@ -239,6 +242,10 @@ cudaError_t allocate(lbm_unet* u)
         }
         for (Conv* cv : {&v.ea, &v.eb, &v.da, &v.db})
             if (cv->cout) UN_ALLOC(cv->wf, 9LL * cv->cin * cv->cout);
+        if (l == 0 && nn::conv3x3_supported(u->B, v.H, v.W, kX0Pitch)) {
+            v.ea.cin_pad = kX0Pitch;
+            UN_ALLOC(v.ea.wpad, 9LL * kX0Pitch * v.ea.cout);
+        }
         if (v.up.cout) UN_ALLOC(v.up.wt, 8LL * c * c);
     }
     // gathered-copy buffer for the convolutions the implicit kernel does not
@@ -307,6 +314,8 @@ cudaError_t derive(lbm_unet* u)
         for (Conv* cv : {&v.ea, &v.eb, &v.da, &v.db}) {
             if (!cv->cout) continue;
             if ((e = nn::flip3x3(u->wb + cv->w, cv->cout, cv->cin, cv->wf, u->s))) return e;
+            if (cv->wpad && (e = nn::pad_conv3x3(u->wb + cv->w, cv->cout, cv->cin, cv->cin_pad, cv->wpad, u->s)))
+                return e;
         }
         if (v.up.cout) {
             const int c = v.c;
@@ -319,8 +328,13 @@ cudaError_t derive(lbm_unet* u)
 cudaError_t conv_fwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in, int inpitch, bf16* out,
                      int outpitch)
 {
-    cudaError_t e = nn::conv3x3_bf16(in, u->B, v.H, v.W, cv.cin, inpitch, u->wb + cv.w, 9 * cv.cin, out, outpitch,
-                                     u->w + cv.b, cv.cout, true, true, u->s);
+    cudaError_t e;
+    if (cv.wpad)  // zero channels cin .. cin_pad-1 of the input meet zero weights
+        e = nn::conv3x3_bf16(in, u->B, v.H, v.W, cv.cin_pad, inpitch, cv.wpad, 9 * cv.cin_pad, out, outpitch,
+                             u->w + cv.b, cv.cout, true, true, u->s);
+    else
+        e = nn::conv3x3_bf16(in, u->B, v.H, v.W, cv.cin, inpitch, u->wb + cv.w, 9 * cv.cin, out, outpitch,
+                             u->w + cv.b, cv.cout, true, true, u->s);
     if (e != cudaErrorNotSupported) return e;
     // layouts the implicit convolution does not take (cin = 8): gathered copy + GEMM
     if ((e = nn::im2col3x3(in, u->B, v.H, v.W, cv.cin, inpitch, u->col, u->s))) return e;
@@ -365,9 +379,9 @@ cudaError_t mask_cast(lbm_unet* u, float* g32, int gpitch, const bf16* y, int yp
 cudaError_t forward(lbm_unet* u, const float* x)
 {
     cudaError_t e;
-    if ((e = nn::pack(x, u->P0, u->F, u->mean, u->inv_std, u->x0, kInPitch, nullptr, u->s))) return e;
+    if ((e = nn::pack(x, u->P0, u->F, u->mean, u->inv_std, u->x0, kX0Pitch, nullptr, u->s))) return e;
     const bf16* in = u->x0;
-    int inpitch = kInPitch;
+    int inpitch = kX0Pitch;
     const int L = u->L;
     for (int l = 0; l < L; ++l) {
         Level& v = u->lv[l];
@@ -444,7 +458,7 @@ cudaError_t backward(lbm_unet* u, const float* x, const float* t)
         if ((e = conv_bwd(u, v, v.eb, v.a, c, u->gA, u->g32, c))) return e;
         if ((e = mask_cast(u, u->g32, c, v.a, c, v.P, c, u->gB))) return e;
         const bf16* in = l == 0 ? u->x0 : u->lv[l - 1].pool;
-        const int inpitch = l == 0 ? kInPitch : u->lv[l - 1].c;
+        const int inpitch = l == 0 ? kX0Pitch : u->lv[l - 1].c;
         if ((e = conv_bwd(u, v, v.ea, in, inpitch, u->gB, l == 0 ? nullptr : u->g32, v.ea.cin))) return e;
     }
     return cudaSuccess;
