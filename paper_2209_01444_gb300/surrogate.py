@@ -160,6 +160,30 @@ class UNet:
 
 
 # ---------------------------------------------------------------- training
+def make_snapshots(cases, K: int, windows: int, warm: int = 0, storage: str = "fp32"):
+    """Runs the cases (equal grid sizes) as one batched LB launch and records
+    the fields every K steps after `warm` steps: a device tensor
+    [windows + 1, len(cases), ny, nx, 5]."""
+    import torch
+
+    ny, nx = int(cases[0].params["ny"]), int(cases[0].params["nx"])
+    assert all(int(c.params["ny"]) == ny and int(c.params["nx"]) == nx for c in cases)
+    b = L.Batch([c.params for c in cases], storage=storage)
+    for d, c in enumerate(cases):
+        b.init_seeds(d, c.seeds, c.U0, c.theta0)
+    if warm:
+        b.step(warm)
+    D = len(cases)
+    snaps = torch.empty(windows + 1, D, ny, nx, 5, dtype=torch.float32, device="cuda")
+    for w in range(windows + 1):
+        for d in range(D):
+            b.fields_nhwc(d, snaps[w, d])
+        if w < windows:
+            b.step(K)
+    b.synchronize()
+    return snaps
+
+
 def make_dataset(cases, K: int, windows: int, warm: int = 0, storage: str = "fp32"):
     """Runs the cases (equal grid sizes) as one batched LB launch and records
     the fields every K steps after `warm` steps.  Returns device tensors x, t
@@ -200,6 +224,43 @@ def normalisation(x, t, floor: float = 1e-6):
     return mean.astype(np.float32), std_in.astype(np.float32), std_out.astype(np.float32)
 
 
+def train_rollout(net: UNet, snaps, steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 0,
+                  pushforward: float = 0.5):
+    """Adam on snapshot sequences [windows + 1, domains, ny, nx, 5]: a sample
+    is a random (window w, domain d); with probability `pushforward` its input
+    is the network's own prediction from window w and its target window
+    w + 2, otherwise the input is window w and the target w + 1 (training on
+    the network's own outputs keeps long rollouts close to the solver's
+    states).  Cosine decay of the learning rate to a tenth.  Returns the loss
+    history [(step, loss)] read every log_every steps."""
+    import torch
+
+    B = net.shape[0]
+    n_w, n_d = int(snaps.shape[0]), int(snaps.shape[1])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xb = torch.empty(net.shape, dtype=torch.float32, device="cuda")
+    tb = torch.empty_like(xb)
+    yb = torch.empty_like(xb)
+    hist = []
+    for it in range(steps):
+        pf = [bool(rng.random() < pushforward) and n_w >= 3 for _ in range(B)]
+        for j in range(B):
+            w = int(rng.integers(0, n_w - (2 if pf[j] else 1)))
+            d = int(rng.integers(0, n_d))
+            xb[j].copy_(snaps[w, d])
+            tb[j].copy_(snaps[w + (2 if pf[j] else 1), d])
+        if any(pf):
+            net.forward(xb, yb)
+            for j in range(B):
+                if pf[j]:
+                    xb[j].copy_(yb[j])
+        a = lr * (0.1 + 0.9 * 0.5 * (1.0 + math.cos(math.pi * it / max(1, steps))))
+        net.train_step(xb, tb, a)
+        if log_every and (it % log_every == 0 or it == steps - 1):
+            hist.append((it, net.loss()))
+    return hist
+
+
 def train(net: UNet, x, t, steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 0):
     """Adam on random mini-batches of (x, t) pairs (batch = the network's
     batch); cosine decay of the learning rate to a tenth.  Returns the loss
@@ -225,18 +286,33 @@ def train(net: UNet, x, t, steps: int, lr: float = 1e-3, seed: int = 0, log_ever
 
 
 def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: int, backoff: int,
-            cx: float, cy: float, orient: float = 0.0):
+            cx: float, cy: float, orient: float = 0.0, lb_first: int = 0, drift_budget: float | None = None):
     """Surrogate-accelerated run of `windows` windows of K steps.
 
-    Policy: the network advances windows; every audit_every-th window is also
-    run by the plain LB from the same state (the LB result is kept).  If the
+    Policy: the first lb_first windows are run by the plain LB; then the
+    network advances windows, and every audit_every-th window is also run by
+    the plain LB from the same state (the LB result is kept).  If the
     audit's tip error exceeds tip_tol, the state returns to the snapshot taken
     at the previous passed audit, every window since is re-run by the LB, and
-    the network sits out the next `backoff` windows.  Returns counts."""
-    st = {"surrogate": 0, "audited": 0, "rejected": 0, "lb_rerun": 0, "lb_backoff": 0, "tip_err": []}
+    the network sits out the next `backoff` windows.
+
+    Drift budget: window errors add up over a rollout, which a one-window
+    audit does not see.  Each passed audit charges its tip error once for
+    every network window it stands for (those since the previous audit); when
+    the charges would exceed `drift_budget` (default tip_tol) with the next
+    stretch, the network stops and the LB runs the remaining windows.
+    Returns counts."""
+    budget = tip_tol if drift_budget is None else drift_budget
+    st = {"surrogate": 0, "audited": 0, "rejected": 0, "lb_rerun": 0, "lb_backoff": 0, "lb_first": 0,
+          "lb_after_budget": 0, "drift_charged": 0.0, "tip_err": []}
+    w = 0
+    if lb_first:  # the first windows (fast early growth of the seed) by the LB
+        n = min(lb_first, windows)
+        sim.step(K * n)
+        st["lb_first"] = n
+        w = n
     sim.snapshot_save(0)
     since, off = 0, 0
-    w = 0
     while w < windows:
         if off > 0:
             sim.step(K)
@@ -257,8 +333,13 @@ def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: i
         st["audited"] += 1
         st["tip_err"].append(rep["tip_err"])
         if rep["accepted"]:
+            st["drift_charged"] += rep["tip_err"] * since
             sim.snapshot_save(0)
             since = 0
+            if st["drift_charged"] + rep["tip_err"] * (audit_every - 1) > budget and w < windows:
+                st["lb_after_budget"] = windows - w
+                sim.step(K * (windows - w))
+                w = windows
         else:
             st["rejected"] += 1
             st["surrogate"] -= since

@@ -37,7 +37,9 @@ class FakeSim:
             return {"audited": False, "accepted": False, "tip_err": 0.0}
         self.source.append("lb")  # an audited window keeps the LB result
         ok = self.verdicts.pop(0)
-        return {"audited": True, "accepted": ok, "tip_err": 0.5 if ok else 3.0}
+        return {"audited": True, "accepted": ok, "tip_err": self.err if ok else 3.0}
+
+    err = 0.01
 
 
 def test_all_audits_pass():
@@ -65,3 +67,22 @@ def test_last_window_is_audited():
     st = S.rollout(sim, None, windows=5, K=50, tip_tol=1.0, audit_every=4, backoff=1, cx=0, cy=0)
     assert sim.source == ["nn", "nn", "nn", "lb", "lb"]
     assert st["audited"] == 2
+
+
+def test_lb_first_windows():
+    sim = FakeSim([True, True])
+    st = S.rollout(sim, None, windows=8, K=50, tip_tol=1.0, audit_every=3, backoff=1, cx=0, cy=0, lb_first=2)
+    assert sim.source == ["lb", "lb", "nn", "nn", "lb", "nn", "nn", "lb"]
+    assert st["lb_first"] == 2 and st["surrogate"] == 4
+
+
+def test_drift_budget_stops_the_network():
+    """Audits pass with 0.15 lattice units each; every one charges 0.15 per
+    network window it covers (3): after two audits 0.9 is charged and the
+    next stretch would reach 1.35 > 1, so the rest goes to the LB."""
+    sim = FakeSim([True] * 10)
+    sim.err = 0.15
+    st = S.rollout(sim, None, windows=20, K=50, tip_tol=1.0, audit_every=4, backoff=1, cx=0, cy=0)
+    assert sim.source[:8] == ["nn", "nn", "nn", "lb"] * 2
+    assert sim.source[8:] == ["lb"] * 12 and sim.steps == 1000
+    assert abs(st["drift_charged"] - 0.9) < 1e-12 and st["lb_after_budget"] == 12
