@@ -362,6 +362,12 @@ LBM_API int lbm_nn_proj_bwd(const float* dY, const void* X, int P, int C, int xp
                             float* dX, int dpitch, float* dW, float* db, float* part, int part_blocks,
                             void* stream);
 LBM_API int lbm_nn_flip3x3(const void* W, int cout, int cin, void* Wf, void* stream);
+/* Transposed gather for weight gradients: AT[t*C + c][p] = X[pixel p shifted
+ * by tap t][c] (zero outside the image) for taps = 9 (t = ky*3 + kx), or
+ * AT[c][p] = X[p][c] for taps = 1; BF16, row pitch atpitch; C, cpitch, atpitch
+ * and B*H*W multiples of 8. */
+LBM_API int lbm_nn_gather_t(const void* X, int B, int H, int W, int C, int cpitch, int taps, void* AT,
+                            long long atpitch, void* stream);
 LBM_API int lbm_nn_colsum(const void* g, int g_fp32, long long rows, int C, int pitch, float* out, float* part,
                           int part_blocks, void* stream);
 LBM_API int lbm_nn_mse(const float* pred, const float* target, long long n, float* grad, float* loss, float* part,

@@ -105,6 +105,12 @@ int lbm_nn_upconv2x2(const void* X, int lda, const void* Wm, int ldw, void* Y, i
     return nn_status(nn::upconv2x2_bf16(X, lda, Wm, ldw, Y, ypitch, c0, bias, B, Hl, Wl, cin, c, NN_S(stream)));
 }
 
+int lbm_nn_gather_t(const void* X, int B, int H, int W, int C, int cpitch, int taps, void* AT, long long atpitch,
+                    void* stream)
+{
+    return nn_status(nn::gatherT(X, B, H, W, C, cpitch, taps, AT, atpitch, NN_S(stream)));
+}
+
 int lbm_nn_flip3x3(const void* W, int cout, int cin, void* Wf, void* stream)
 {
     return nn_status(nn::flip3x3(W, cout, cin, Wf, NN_S(stream)));

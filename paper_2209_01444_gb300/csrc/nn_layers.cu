@@ -70,6 +70,69 @@ __global__ void k_relu_bwd(G* __restrict__ g, int gpitch, const bf16* __restrict
     if (!(bf(y[r * ypitch + c]) > 0.0f)) g[r * gpitch + c] = (G)0.0f;
 }
 
+// Transposed gather for weight gradients:
+//   AT[t * C + c][p] = X[pixel p shifted by tap t][c]   (zero outside)
+// with taps 9 (the 3 x 3 neighbourhood, t = ky * 3 + kx) or 1 (no shift: a
+// plain transpose of [P][C] with pitch).  One CTA moves a 64-pixel x
+// 64-channel block through shared memory: 16-byte reads along channels,
+// 16-byte writes along pixels.  C and the pitches are multiples of 8; P and
+// the AT pitch multiples of 8.
+__global__ void __launch_bounds__(256) k_gatherT(const bf16* __restrict__ X, int B, int H, int W, int C, int cpitch,
+                                                 int taps, bf16* __restrict__ AT, long long atpitch)
+{
+    __shared__ __align__(16) bf16 tile[64][64 + 8];  // [pixel][channel], padded rows
+    const long long P = (long long)B * H * W;
+    const long long p0 = (long long)blockIdx.x * 64;
+    const int cblk = blockIdx.y;                 // 64-channel block within (tap, channel)
+    const int cpb = (C + 63) / 64;                // channel blocks per tap
+    const int t = taps == 9 ? cblk / cpb : 4;     // tap 4 is the centre
+    const int c0 = (cblk % cpb) * 64;
+    const int dy = t / 3 - 1, dx = t % 3 - 1;
+    // load: 64 pixels x 64 channels, 8 channels (16 bytes) per thread-step
+    for (int k = threadIdx.x; k < 64 * 8; k += 256) {
+        const int pi = k >> 3, g = k & 7;
+        const long long p = p0 + pi;
+        const int c = c0 + g * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (p < P && c < C) {
+            const int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((long long)W * H));
+            const int xx = x + dx, yy = y + dy;
+            if (xx >= 0 && xx < W && yy >= 0 && yy < H)
+                v = *(const uint4*)(X + (((long long)b * H + yy) * W + xx) * cpitch + c);
+        }
+        *(uint4*)&tile[pi][g * 8] = v;
+    }
+    __syncthreads();
+    // store: for each of the 64 channels, 64 consecutive pixels (8 per thread-step)
+    for (int k = threadIdx.x; k < 64 * 8; k += 256) {
+        const int ci = k >> 3, g = k & 7;
+        const int c = c0 + ci;
+        const long long p = p0 + g * 8;
+        if (c >= C || p >= P) continue;
+        __align__(16) bf16 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = tile[g * 8 + j][ci];
+        const long long row = (long long)(taps == 9 ? t * C + c : c);
+        if (p + 8 <= P)
+            *(uint4*)(AT + row * atpitch + p) = *(const uint4*)v;
+        else
+            for (int j = 0; p + j < P; ++j) AT[row * atpitch + p + j] = v[j];
+    }
+}
+
+// out[r][c] = BF16(y[r][c] > 0 ? g[r][c] : 0): the ReLU mask of an FP32
+// gradient and its rounding for the next GEMM, in one pass.
+__global__ void k_mask_cast(const float* __restrict__ g, int gpitch, const bf16* __restrict__ y, int ypitch,
+                            long long rows, int C, bf16* __restrict__ out, int opitch)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= rows * C) return;
+    const long long r = i / C;
+    const int c = (int)(i - r * C);
+    const float v = bf(y[r * ypitch + c]) > 0.0f ? g[r * gpitch + c] : 0.0f;
+    out[r * opitch + c] = __float2bfloat16(v);
+}
+
 // Out[c][r] = In[r][c] (BF16), 32 x 32 tiles through shared memory.
 __global__ void k_transpose(const bf16* __restrict__ in, int rows, int cols, int ipitch, bf16* __restrict__ out,
                             int opitch)
@@ -296,12 +359,27 @@ template <class G>
 __global__ void k_colsum_part(const G* __restrict__ g, long long rows, int C, int pitch, int chunk,
                               float* __restrict__ part)
 {
+    // the block's 128 threads split into 128 / L row lanes of L = min(C, 128)
+    // column threads; each column's row lanes are then added in shared memory
+    __shared__ float sm[128];
+    const int L = C < 128 ? C : 128;
+    const int lanes = 128 / L;
+    const int cl = threadIdx.x % L, rl = threadIdx.x / L;
     const long long r0 = (long long)blockIdx.x * chunk;
     const long long r1 = r0 + chunk < rows ? r0 + chunk : rows;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    for (int cb = 0; cb < C; cb += L) {
+        const int c = cb + cl;
         float acc = 0.0f;
-        for (long long r = r0; r < r1; ++r) acc += (float)g[r * pitch + c];
-        part[(long long)blockIdx.x * C + c] = acc;
+        if (rl < lanes && c < C)
+            for (long long r = r0 + rl; r < r1; r += lanes) acc += (float)g[r * pitch + c];
+        sm[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < L && cb + threadIdx.x < C) {
+            float v = 0.0f;
+            for (int k = 0; k < lanes; ++k) v += sm[k * L + threadIdx.x];
+            part[(long long)blockIdx.x * C + cb + threadIdx.x] = v;
+        }
+        __syncthreads();
     }
 }
 
@@ -321,14 +399,19 @@ __global__ void k_proj_sum(const float* __restrict__ part, int nb, int O, int C,
         db[o] = acc;
 }
 
-// out[s] = sum over the nb partial rows (fixed order).
+// out[s] = sum over the nb partial rows: one warp per slot, lanes take
+// partial rows b = lane, lane + 32, ... and a shuffle tree adds the lanes
+// (a fixed order, so the result is reproducible).
 __global__ void k_sum_parts(const float* __restrict__ part, int nb, int slots, float* __restrict__ out)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (s >= slots) return;
     float acc = 0.0f;
-    for (int b = 0; b < nb; ++b) acc += part[(long long)b * slots + s];
-    out[s] = acc;
+    for (int b = lane; b < nb; b += 32) acc += part[(long long)b * slots + s];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+    if (lane == 0) out[s] = acc;
 }
 
 // Squared error: d[i] = pred - target; per-block partial sums of d^2 and
@@ -542,6 +625,26 @@ cudaError_t proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, c
     return cudaGetLastError();
 }
 
+cudaError_t gatherT(const void* X, int B, int H, int W, int C, int cpitch, int taps, void* AT, long long atpitch,
+                    cudaStream_t s)
+{
+    const long long P = (long long)B * H * W;
+    if ((taps != 9 && taps != 1) || C % 8 || cpitch % 8 || atpitch % 8 || P % 8) return cudaErrorInvalidValue;
+    if (((uintptr_t)X | (uintptr_t)AT) & 15) return cudaErrorInvalidValue;
+    const long long cblocks = (long long)((C + 63) / 64) * taps;
+    if (cblocks > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((P + 63) / 64), (unsigned)cblocks);
+    k_gatherT<<<grid, 256, 0, s>>>((const bf16*)X, B, H, W, C, cpitch, taps, (bf16*)AT, atpitch);
+    return cudaGetLastError();
+}
+
+cudaError_t mask_cast(const float* g, int gpitch, const void* y, int ypitch, long long rows, int C, void* out,
+                      int opitch, cudaStream_t s)
+{
+    k_mask_cast<<<blocks(rows * C), 256, 0, s>>>(g, gpitch, (const bf16*)y, ypitch, rows, C, (bf16*)out, opitch);
+    return cudaGetLastError();
+}
+
 cudaError_t pad_conv3x3(const void* W, int cout, int cin, int cin_pad, void* Wp, cudaStream_t s)
 {
     if (cin_pad < cin) return cudaErrorInvalidValue;
@@ -564,7 +667,7 @@ cudaError_t colsum(const void* g, bool g_fp32, long long rows, int C, int pitch,
         k_colsum_part<float><<<nb, 128, 0, s>>>((const float*)g, rows, C, pitch, chunk, part);
     else
         k_colsum_part<bf16><<<nb, 128, 0, s>>>((const bf16*)g, rows, C, pitch, chunk, part);
-    k_sum_parts<<<blocks(C), 256, 0, s>>>(part, nb, C, out);
+    k_sum_parts<<<(unsigned)((C + 7) / 8), 256, 0, s>>>(part, nb, C, out);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,10 @@ cudaError_t proj_fwd(const void* X, int P, int C, int xpitch, const float* Wt, c
 cudaError_t proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, const float* Wt, int O, float* dX,
                      int dpitch, float* dW, float* db, float* part, int part_blocks, cudaStream_t s);
 cudaError_t flip3x3(const void* W, int cout, int cin, void* Wf, cudaStream_t s);
+cudaError_t gatherT(const void* X, int B, int H, int W, int C, int cpitch, int taps, void* AT, long long atpitch,
+                    cudaStream_t s);
+cudaError_t mask_cast(const float* g, int gpitch, const void* y, int ypitch, long long rows, int C, void* out,
+                      int opitch, cudaStream_t s);
 cudaError_t pad_conv3x3(const void* W, int cout, int cin, int cin_pad, void* Wp, cudaStream_t s);
 cudaError_t colsum(const void* g, bool g_fp32, long long rows, int C, int pitch, float* out, float* part,
                    int part_blocks, cudaStream_t s);

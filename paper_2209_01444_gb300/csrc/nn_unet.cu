@@ -351,9 +351,8 @@ cudaError_t conv_bwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in
     const long long P = v.P;
     const int K9 = 9 * cv.cin;
     cudaError_t e;
-    if ((e = nn::im2col3x3(in, u->B, v.H, v.W, cv.cin, inpitch, u->col, u->s))) return e;
-    if ((e = nn::transpose(u->col, (int)P, K9, K9, u->colT, (int)P, u->s))) return e;
-    if ((e = nn::transpose(dY, (int)P, cv.cout, cv.cout, u->tA, (int)P, u->s))) return e;
+    if ((e = nn::gatherT(in, u->B, v.H, v.W, cv.cin, inpitch, 9, u->colT, P, u->s))) return e;
+    if ((e = nn::gatherT(dY, u->B, v.H, v.W, cv.cout, cv.cout, 1, u->tA, P, u->s))) return e;
     const int sp = splits_for(cv.cout, K9, P);
     if ((e = nn::gemm_bf16(u->tA, (int)P, u->colT, (int)P, u->g + cv.w, K9, nullptr, cv.cout, K9, (int)P, false, false,
                            u->s, sp, u->ws)))
@@ -371,9 +370,7 @@ cudaError_t conv_bwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in
 // g32 [rows][C] (pitch) masked by y > 0, then rounded into BF16 [rows][C].
 cudaError_t mask_cast(lbm_unet* u, float* g32, int gpitch, const bf16* y, int ypitch, long long rows, int C, bf16* out)
 {
-    cudaError_t e = nn::relu_bwd(g32, true, gpitch, y, ypitch, rows, C, u->s);
-    if (e) return e;
-    return nn::cast_bf16(g32, rows, C, gpitch, out, C, u->s);
+    return nn::mask_cast(g32, gpitch, y, ypitch, rows, C, out, C, u->s);
 }
 
 cudaError_t forward(lbm_unet* u, const float* x)
@@ -435,8 +432,8 @@ cudaError_t backward(lbm_unet* u, const float* x, const float* t)
         if ((e = nn::shuffle_bwd(v.dcat, true, 2 * c, c, u->B, lo.H, lo.W, c, u->dU, u->s))) return e;
         if ((e = nn::colsum(u->dU, false, lo.P, 4 * c, 4 * c, u->g + v.up.b, u->part, kPartBlocks, u->s))) return e;
         const bf16* hlow = (l + 1 < L - 1) ? lo.dD : lo.s;
-        if ((e = nn::transpose(u->dU, (int)lo.P, 4 * c, 4 * c, u->tA, (int)lo.P, u->s))) return e;
-        if ((e = nn::transpose(hlow, (int)lo.P, 2 * c, 2 * c, u->tB, (int)lo.P, u->s))) return e;
+        if ((e = nn::gatherT(u->dU, u->B, lo.H, lo.W, 4 * c, 4 * c, 1, u->tA, lo.P, u->s))) return e;
+        if ((e = nn::gatherT(hlow, u->B, lo.H, lo.W, 2 * c, 2 * c, 1, u->tB, lo.P, u->s))) return e;
         const int sp = splits_for(4 * c, 2 * c, lo.P);
         if ((e = nn::gemm_bf16(u->tA, (int)lo.P, u->tB, (int)lo.P, u->g + v.up.w, 2 * c, nullptr, 4 * c, 2 * c,
                                (int)lo.P, false, false, u->s, sp, u->ws)))

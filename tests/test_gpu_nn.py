@@ -310,3 +310,24 @@ def test_upconv2x2_shuffle_epilogue(env, B, Hl, Wl, cin, c):
     err = float((Y[..., c:].double().cpu() - ref).abs().max())
     assert err <= 8e-3 * float(ref.abs().max())
     assert bool((Y[..., :c] == 5.0).all())
+
+
+@pytest.mark.parametrize("B,H,W,C,cp,taps", [(2, 4, 7, 16, 24, 9), (1, 16, 16, 8, 32, 9), (3, 8, 8, 72, 80, 9),
+                                            (2, 6, 10, 40, 48, 1), (1, 1, 1000, 200, 200, 1)])
+def test_gather_transposed_exact(env, B, H, W, C, cp, taps):
+    torch, lib = env
+    g = torch.Generator(device="cuda").manual_seed(B * H * W + C)
+    X = _bf(torch, (B, H, W, cp), g)
+    P = B * H * W
+    pitch = P + 8
+    AT = torch.full((taps * C, pitch), 9.0, dtype=torch.bfloat16, device="cuda")
+    assert lib.lbm_nn_gather_t(_p(X), B, H, W, C, cp, taps, _p(AT), pitch, _stream(torch)) == 0
+    torch.cuda.synchronize()
+    if taps == 9:
+        Xp = torch.nn.functional.pad(X[..., :C].float(), (0, 0, 1, 1, 1, 1))
+        ref = torch.stack([Xp[:, ky:ky + H, kx:kx + W, :] for ky in range(3) for kx in range(3)], dim=3)
+        ref = ref.reshape(P, 9 * C).T
+    else:
+        ref = X[..., :C].float().reshape(P, C).T
+    assert torch.equal(AT[:, :P].float(), ref)
+    assert bool((AT[:, P:] == 9.0).all())
