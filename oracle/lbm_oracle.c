@@ -26,6 +26,11 @@
  *   R4  grad(phi) by the isotropic nine-point stencil
  *       grad(phi) = (1/cs^2) sum_i w_i c_i phi(x + c_i) (D2Q9 weights),
  *       mirror ghosts at non-periodic walls;
+ *   R21 the local scheme of Sec. 3.1 (grad_mode 1): grad(phi) =
+ *       -(s1/(cs^2 dt)) (sum_i c_i f_i + W0^2 N / tau0) with the node's own
+ *       pre-collision f; s1 and N depend on grad(phi), so the formula is
+ *       solved by fixed-point iteration from the isotropic guess (a_s = 1,
+ *       N = 0), LOCAL_GRAD_ITERS passes;
  *   R5  |grad(phi)|^2 < 1e-12 (lattice units): n = N = J_at = 0, a_s = 1;
  *   R6  D2Q5 weights 1/3, 1/6 (forced by cs^2 = 1/3), D2Q9 weights 4/9, 1/9,
  *       1/36;
@@ -304,6 +309,9 @@ struct orc_sim {
 static int is_periodic_x(const orc_sim* s) { return s->P.bc[0] == ORC_BC_PERIODIC; }
 static int is_periodic_y(const orc_sim* s) { return s->P.bc[2] == ORC_BC_PERIODIC; }
 
+/* Fixed-point passes of the local gradient scheme (reading R21). */
+#define LOCAL_GRAD_ITERS 2
+
 /* Index of (x + dx, y + dy) for the gradient stencil: periodic wrap, or a
  * mirror ghost about the wall node (reading R4). */
 static int stencil_index(const orc_sim* s, int x, int y)
@@ -339,6 +347,7 @@ orc_sim* orc_create(const orc_params* P)
     if (P->W0 <= 0 || P->tau0 <= 0 || P->dx <= 0 || P->dt <= 0) return NULL;
     if (P->eps_s < 0 || P->eps_s >= 1.0 / 3.0 || P->k <= 0 || P->k >= 1) return NULL;
     if (P->D <= 0 || P->alpha <= 0 || P->nu <= 0 || P->n_sub < 1) return NULL;
+    if (P->grad_mode != 0 && P->grad_mode != 1) return NULL;
     for (int b = 0; b < 4; ++b)
         if (!valid_bc(P->bc[b])) return NULL;
     if ((P->bc[0] == ORC_BC_PERIODIC) != (P->bc[1] == ORC_BC_PERIODIC)) return NULL;
@@ -607,6 +616,57 @@ static void swap_ptr(double** a, double** b)
     *b = t;
 }
 
+/* grad(phi) at node (x, y) of the current state (phi from compute_macros):
+ * the nine-point stencil of reading R4, or the local scheme of Sec. 3.1
+ * (reading R21) from the node's own pre-collision f. */
+static void grad_phi(const orc_sim* s, int x, int y, double* gxo, double* gyo)
+{
+    const orc_params* P = &s->P;
+    const int N = s->N, idx = y * s->nx + x;
+    double gx = 0.0, gy = 0.0;
+    if (P->grad_mode == 1) {
+        double jx = 0.0, jy = 0.0;
+        for (int i = 1; i < 5; ++i) {
+            jx += C5[i][0] * s->f[i * N + idx];
+            jy += C5[i][1] * s->f[i * N + idx];
+        }
+        double a1 = 1.0, nx_ = 0.0, ny_ = 0.0;
+        for (int it = 0; it <= LOCAL_GRAD_ITERS; ++it) {
+            if (it > 0) orc_anisotropy(gx, gy, P->eps_s, s->orient[idx], &a1, &nx_, &ny_);
+            const double s1 = 1.0 / (a1 * a1 * s->kappa0 / CS2 + 0.5);
+            gx = -s1 / CS2 * (jx + s->kappa0 * nx_);
+            gy = -s1 / CS2 * (jy + s->kappa0 * ny_);
+        }
+    } else {
+        for (int i = 1; i < 9; ++i) {
+            double ph = s->phi[stencil_index(s, x + C9[i][0], y + C9[i][1])];
+            gx += W9[i] * C9[i][0] * ph;
+            gy += W9[i] * C9[i][1] * ph;
+        }
+        gx /= CS2;
+        gy /= CS2;
+    }
+    *gxo = gx;
+    *gyo = gy;
+}
+
+/* grad(phi) of every node by the given scheme (0 stencil, 1 local), out =
+ * [2][ny][nx] in lattice units (per lattice spacing). */
+int orc_grad_phi(orc_sim* s, int mode, double* out)
+{
+    if (!s || !out || (mode != 0 && mode != 1)) return -1;
+    compute_macros(s);
+    const int keep = s->P.grad_mode;
+    s->P.grad_mode = mode;
+    for (int y = 0; y < s->ny; ++y)
+        for (int x = 0; x < s->nx; ++x) {
+            const int idx = y * s->nx + x;
+            grad_phi(s, x, y, &out[idx], &out[s->N + idx]);
+        }
+    s->P.grad_mode = keep;
+    return 0;
+}
+
 /* One coupled step n -> n+1 (the order of reading R12). */
 static void coupled_step(orc_sim* s)
 {
@@ -623,15 +683,8 @@ static void coupled_step(orc_sim* s)
             /* velocity seen by the scalar models (reading R10) */
             const double usx = s->ux[idx] * s->nsub_scale, usy = s->uy[idx] * s->nsub_scale;
 
-            /* grad(phi), reading R4: (1/cs^2) sum_i w_i c_i phi(x + c_i), D2Q9 weights */
-            double gx = 0.0, gy = 0.0;
-            for (int i = 1; i < 9; ++i) {
-                double ph = s->phi[stencil_index(s, x + C9[i][0], y + C9[i][1])];
-                gx += W9[i] * C9[i][0] * ph;
-                gy += W9[i] * C9[i][1] * ph;
-            }
-            gx /= CS2;
-            gy /= CS2;
+            double gx, gy;
+            grad_phi(s, x, y, &gx, &gy);
             double as, Nx, Ny;
             orc_anisotropy(gx, gy, P->eps_s, s->orient[idx], &as, &Nx, &Ny);
             const double as2 = as * as;

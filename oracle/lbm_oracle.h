@@ -25,6 +25,7 @@ typedef struct {
     int bc[4];                     /* left, right, bottom, top */
     double u_in[2];
     double dir_phi, dir_U, dir_theta;
+    int grad_mode;                 /* 0: nine-point stencil (reading R4), 1: local scheme of Sec. 3.1 */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -38,6 +39,7 @@ int orc_init_fields(orc_sim* s, const double* fields, const double* orient);
 int orc_step(orc_sim* s, int nsteps);
 int orc_step_flow(orc_sim* s, int nsteps);
 int orc_force(orc_sim* s, double cx, double cy, double* out);
+int orc_grad_phi(orc_sim* s, int mode, double* out);
 long long orc_step_count(const orc_sim* s);
 int orc_get_fields(orc_sim* s, double* out);
 int orc_get_state(const orc_sim* s, double* out);

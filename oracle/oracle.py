@@ -43,6 +43,7 @@ class _Params(ct.Structure):
         ("bc", ct.c_int * 4),
         ("u_in", ct.c_double * 2),
         ("dir_phi", ct.c_double), ("dir_U", ct.c_double), ("dir_theta", ct.c_double),
+        ("grad_mode", ct.c_int),
     ]
 
 
@@ -78,6 +79,7 @@ def _load():
     lib.orc_step.argtypes = [ct.c_void_p, ct.c_int]
     lib.orc_step_flow.argtypes = [ct.c_void_p, ct.c_int]
     lib.orc_force.argtypes = [ct.c_void_p, ct.c_double, ct.c_double, dp]
+    lib.orc_grad_phi.argtypes = [ct.c_void_p, ct.c_int, dp]
     lib.orc_step_count.restype = ct.c_longlong
     lib.orc_step_count.argtypes = [ct.c_void_p]
     for name in ("orc_get_fields", "orc_get_state", "orc_set_state", "orc_get_orient", "orc_lattice_params"):
@@ -178,6 +180,14 @@ class Oracle:
         out = np.empty(3)
         self.lib.orc_force(self.h, cx, cy, _ptr(out))
         return float(out[0]), float(out[1]), float(out[2])
+
+    def grad_phi(self, mode: int) -> np.ndarray:
+        """grad(phi) [2, ny, nx] (lattice units) by the stencil (0) or the
+        local scheme (1) from the current state."""
+        out = np.empty((2, self.ny, self.nx))
+        if self.lib.orc_grad_phi(self.h, int(mode), _ptr(out)):
+            raise ValueError("grad_phi failed")
+        return out
 
     @property
     def steps(self) -> int:

@@ -37,7 +37,7 @@ def thermosolutal_params(nx: int, ny: int, **over) -> dict:
              D=2.0, alpha=2.0, nu=2.0, rho0=1.0, n_sub=1, h_kind=0,
              gbetaT=0.0, gbetaC=0.0, theta_ref=-0.55, C_ref=1.0,
              force=(0.0, 0.0), bc=("periodic",) * 4, u_in=(0.0, 0.0),
-             dir_phi=-1.0, dir_U=0.0, dir_theta=-0.55)
+             dir_phi=-1.0, dir_U=0.0, dir_theta=-0.55, grad_mode=0)
     p.update(over)
     return p
 
