@@ -70,6 +70,7 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_INFLOW = 1, LBM_BC_OUTFLOW = 2, LBM_BC_SYMMET
  * equilibrium of a constant reference state (liquid at rest, phi = -1,
  * C = 1, theta = theta_ref, p = 0); the history fields stay FP32. */
 enum { LBM_FP32 = 0, LBM_FP16 = 1, LBM_BF16 = 2 };
+enum { LBM_GRAD_FD9 = 0, LBM_GRAD_LOCAL = 1 };
 
 /* Field indices for lbm_get_fields (bit i of the mask selects field i). */
 enum { LBM_FIELD_PHI = 0, LBM_FIELD_C = 1, LBM_FIELD_U = 2, LBM_FIELD_THETA = 3,
@@ -103,6 +104,10 @@ typedef struct lbm_params {
     double u_in[2];        /* inflow velocity                                    */
     double dir_phi, dir_U, dir_theta; /* Dirichlet far-field values             */
     int storage;           /* LBM_FP32, LBM_FP16 or LBM_BF16                     */
+    int grad_mode;         /* LBM_GRAD_FD9 (nine-point stencil) or LBM_GRAD_LOCAL
+                              (the local scheme of Sec. 3.1: grad(phi) from the
+                              node's own first moment, solved by two
+                              fixed-point passes from a_s = 1, N = 0)      */
 } lbm_params;
 
 /* A seed (Sec. 4): centre and radius in lattice units, crystal-axis

@@ -122,6 +122,7 @@ std::string validate(const lbm_params* p)
     if ((p->bc[0] == LBM_BC_PERIODIC) != (p->bc[1] == LBM_BC_PERIODIC)) return "left/right periodicity must match";
     if ((p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) return "bottom/top periodicity must match";
     if (p->storage < LBM_FP32 || p->storage > LBM_BF16) return "unknown storage";
+    if (p->grad_mode != LBM_GRAD_FD9 && p->grad_mode != LBM_GRAD_LOCAL) return "unknown grad_mode";
     return "";
 }
 
@@ -146,6 +147,7 @@ void derive(lbm_handle* h)
     const double al = p.alpha * p.dt / (p.dx * p.dx);
     const double nul = p.nu * dtf / (p.dx * p.dx);
     P.kappa3 = (float)(3.0 * W * W / tau);
+    P.grad_local = p.grad_mode == LBM_GRAD_LOCAL ? 1 : 0;
     P.inv_tau = (float)(1.0 / tau);
     P.eps = (float)p.eps_s;
     P.lambda = (float)p.lambda;
@@ -332,6 +334,7 @@ int lbm_params_default(lbm_params* p, int nx, int ny)
     p->dir_U = 0.0;
     p->dir_theta = -0.55;
     p->storage = LBM_FP32;
+    p->grad_mode = LBM_GRAD_FD9;
     return LBM_OK;
 }
 

@@ -45,6 +45,7 @@ struct StepParams {
     long long plane;          // elements per plane (pitch * ny)
     int periodic_x, periodic_y;
     int h_kind;
+    int grad_local;           // 0: nine-point stencil, 1: local scheme of Sec. 3.1
     float kappa3;             // 3 W0^2/tau0: s1^phi = 1/(kappa3 a_s^2 + 1/2)
     float inv_tau;            // 1/tau0 (lattice)
     float eps;                // anisotropy strength

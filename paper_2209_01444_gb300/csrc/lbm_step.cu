@@ -25,6 +25,8 @@ namespace lbm {
 
 namespace {
 
+constexpr int kLocalGradIters = 2;  // fixed-point passes of the local grad(phi) scheme
+
 __device__ __forceinline__ int mirror_or_wrap_local(int g, int n, int periodic, int local, int d)
 {
     // Neighbour g = node + d seen from local index `local` of the node: a
@@ -103,23 +105,41 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
     const Macro m = node_macros(f, n, g, h, P);
     const float usx = m.ux * P.nsub, usy = m.uy * P.nsub;  // velocity of the scalar lattice
 
-    // grad(phi): (1/cs^2) sum_i w_i c_i phi(x + c_i) over the D2Q9 neighbours
-    const int xl = mirror_or_wrap_local(x - 1, P.nx, P.periodic_x, lx, -1);
-    const int xr = mirror_or_wrap_local(x + 1, P.nx, P.periodic_x, lx, +1);
-    const int yd = mirror_or_wrap_local(y - 1, P.ny, P.periodic_y, ly, -1);
-    const int yu = mirror_or_wrap_local(y + 1, P.ny, P.periodic_y, ly, +1);
-    const float pE = ps[ly][xr], pW = ps[ly][xl], pN = ps[yu][lx], pS = ps[yd][lx];
-    const float pNE = ps[yu][xr], pNW = ps[yu][xl], pSE = ps[yd][xr], pSW = ps[yd][xl];
-    // paired differences, so that mirror-symmetric neighbourhoods (a wall
-    // ghost, a symmetric seed) give an exactly zero component
-    const float gx = (pE - pW) * (1.0f / 3.0f) + ((pNE - pNW) + (pSE - pSW)) * (1.0f / 12.0f);
-    const float gy = (pN - pS) * (1.0f / 3.0f) + ((pNE - pSE) + (pNW - pSW)) * (1.0f / 12.0f);
-
     float co = P.cos_o, so = P.sin_o;
     if (GRAIN && grain) {
         const float2 cs = P.grain_cs[gid];
         co = cs.x;
         so = cs.y;
+    }
+    float gx, gy;
+    if (!P.grad_local) {
+        // grad(phi): (1/cs^2) sum_i w_i c_i phi(x + c_i) over the D2Q9 neighbours
+        const int xl = mirror_or_wrap_local(x - 1, P.nx, P.periodic_x, lx, -1);
+        const int xr = mirror_or_wrap_local(x + 1, P.nx, P.periodic_x, lx, +1);
+        const int yd = mirror_or_wrap_local(y - 1, P.ny, P.periodic_y, ly, -1);
+        const int yu = mirror_or_wrap_local(y + 1, P.ny, P.periodic_y, ly, +1);
+        const float pE = ps[ly][xr], pW = ps[ly][xl], pN = ps[yu][lx], pS = ps[yd][lx];
+        const float pNE = ps[yu][xr], pNW = ps[yu][xl], pSE = ps[yd][xr], pSW = ps[yd][xl];
+        // paired differences, so that mirror-symmetric neighbourhoods (a wall
+        // ghost, a symmetric seed) give an exactly zero component
+        gx = (pE - pW) * (1.0f / 3.0f) + ((pNE - pNW) + (pSE - pSW)) * (1.0f / 12.0f);
+        gy = (pN - pS) * (1.0f / 3.0f) + ((pNE - pSE) + (pNW - pSW)) * (1.0f / 12.0f);
+    } else {
+        // local scheme of Sec. 3.1: grad(phi) = -(s1/cs^2)(sum_i c_i f_i + W0^2 N/tau0)
+        // with s1 and N taken at grad(phi): two fixed-point passes from a_s = 1, N = 0
+        const float jx = f[1] - f[3], jy = f[2] - f[4];
+        const float k0 = P.kappa3 * (1.0f / 3.0f);
+        float s1 = 1.0f / (P.kappa3 + 0.5f);
+        gx = -3.0f * s1 * jx;
+        gy = -3.0f * s1 * jy;
+#pragma unroll
+        for (int it = 0; it < kLocalGradIters; ++it) {
+            float a1, nx_, ny_;
+            anisotropy(gx, gy, P.eps, co, so, a1, nx_, ny_);
+            s1 = 1.0f / (P.kappa3 * a1 * a1 + 0.5f);
+            gx = -3.0f * s1 * (jx + k0 * nx_);
+            gy = -3.0f * s1 * (jy + k0 * ny_);
+        }
     }
     float as, Nx, Ny;
     anisotropy(gx, gy, P.eps, co, so, as, Nx, Ny);

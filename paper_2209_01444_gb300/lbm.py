@@ -37,6 +37,7 @@ class lbm_params(ct.Structure):
         ("u_in", ct.c_double * 2),
         ("dir_phi", ct.c_double), ("dir_U", ct.c_double), ("dir_theta", ct.c_double),
         ("storage", ct.c_int),
+        ("grad_mode", ct.c_int),
     ]
 
 
