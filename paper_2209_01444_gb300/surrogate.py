@@ -286,7 +286,8 @@ def train(net: UNet, x, t, steps: int, lr: float = 1e-3, seed: int = 0, log_ever
 
 
 def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: int, backoff: int,
-            cx: float, cy: float, orient: float = 0.0, lb_first: int = 0, drift_budget: float | None = None):
+            cx: float, cy: float, orient: float = 0.0, lb_first: int = 0, drift_budget: float | None = None,
+            drift_factor: float = 1.0):
     """Surrogate-accelerated run of `windows` windows of K steps.
 
     Policy: the first lb_first windows are run by the plain LB; then the
@@ -297,10 +298,11 @@ def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: i
     the network sits out the next `backoff` windows.
 
     Drift budget: window errors add up over a rollout, which a one-window
-    audit does not see.  Each passed audit charges its tip error once for
-    every network window it stands for (those since the previous audit); when
-    the charges would exceed `drift_budget` (default tip_tol) with the next
-    stretch, the network stops and the LB runs the remaining windows.
+    audit does not see.  Each passed audit charges drift_factor times its tip
+    error for every network window it stands for (those since the previous
+    audit); when the charges would exceed `drift_budget` (default tip_tol)
+    with the next stretch, the network stops and the LB runs the remaining
+    windows.
     Returns counts."""
     budget = tip_tol if drift_budget is None else drift_budget
     st = {"surrogate": 0, "audited": 0, "rejected": 0, "lb_rerun": 0, "lb_backoff": 0, "lb_first": 0,
@@ -333,10 +335,10 @@ def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: i
         st["audited"] += 1
         st["tip_err"].append(rep["tip_err"])
         if rep["accepted"]:
-            st["drift_charged"] += rep["tip_err"] * since
+            st["drift_charged"] += drift_factor * rep["tip_err"] * since
             sim.snapshot_save(0)
             since = 0
-            if st["drift_charged"] + rep["tip_err"] * (audit_every - 1) > budget and w < windows:
+            if st["drift_charged"] + drift_factor * rep["tip_err"] * (audit_every - 1) > budget and w < windows:
                 st["lb_after_budget"] = windows - w
                 sim.step(K * (windows - w))
                 w = windows
