@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include "lbm_kernels.h"
+#include "lbm_reduce.cuh"
 
 namespace lbm {
 
@@ -267,7 +268,7 @@ __global__ void k_encode(const StepParams P, const float* __restrict__ in, void*
 
 // ------------------------------------------------------------- reductions
 constexpr int kRedThreads = 256;
-constexpr int kRedVals = 7;  // sf, C, H, h, max|u|, bad, phi
+constexpr int kRedVals = kRedValues;
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -282,8 +283,9 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// Pass 1: each block accumulates a fixed, grid-strided subset of nodes in
-// FP64 and writes its kRedVals partials (deterministic order).
+// Pass 1: each block accumulates a fixed, grid-strided subset of nodes
+// (FP64 sums of FP32 per-node terms, reduce_accumulate) and writes its
+// kRedVals partials (deterministic order).
 template <class Store>
 __global__ void __launch_bounds__(kRedThreads) k_reduce_nodes(const StepParams P, const void* __restrict__ sc,
                                                               const void* __restrict__ fl,
@@ -298,17 +300,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_nodes(const StepParams P
         float f[5], n[5], g[5], h[9];
         load_node<Store>(P, sc, fl, o, f, n, g, h);
         const Macro m = node_macros(f, n, g, h, P);
-        double sh = (double)P.rho0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) sh += (double)h[i];
-        const double u = sqrt((double)m.ux * m.ux + (double)m.uy * m.uy);
-        acc[0] += 0.5 * (double)m.p1;
-        acc[1] += 1.0 + (double)m.dC;
-        acc[2] += ((double)P.theta_ref + 0.5) + (double)m.dH;
-        acc[3] += sh;
-        acc[4] = fmax(acc[4], u);
-        acc[5] += (isfinite(m.p1) && isfinite(m.dC) && isfinite(m.dth) && isfinite(u)) ? 0.0 : 1.0;
-        acc[6] += (double)m.p1 - 1.0;
+        reduce_accumulate(P, m, h, acc);
     }
     __shared__ double sm[kRedVals][kRedThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -326,17 +318,19 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_nodes(const StepParams P
     }
 }
 
-// Pass 2: one block folds the partials in block order.
+// Pass 2: one warp per value folds the partials: lane l takes blocks
+// l, l + 32, ..., then a shuffle tree adds the lanes (a fixed order).
 __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out)
 {
-    const int k = threadIdx.x;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k >= kRedVals) return;
     double v = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
+    for (int b = lane; b < nblocks; b += 32) {
         const double p = partials[(long long)b * kRedVals + k];
         v = (k == 4) ? fmax(v, p) : v + p;
     }
-    out[k] = v;
+    v = (k == 4) ? warp_max(v) : warp_sum(v);
+    if (lane == 0) out[k] = v;
 }
 
 // Hydrodynamic force and torque on the solid (Eq. 27, weighted by 1 - q~ =
@@ -531,7 +525,7 @@ cudaError_t reduce_t(const StepParams& P, const void* sc, const void* fl, double
 {
     const int nb = reduce_blocks(P);
     k_reduce_nodes<Store><<<nb, kRedThreads, 0, st>>>(P, sc, fl, partials);
-    k_reduce_final<<<1, 32, 0, st>>>(partials, nb, out);
+    k_reduce_final<<<1, 32 * kRedVals, 0, st>>>(partials, nb, out);
     k_tips<Store><<<3, kRedThreads, 0, st>>>(P, sc, cx, cy, c, s, out);
     return cudaGetLastError();
 }
@@ -662,7 +656,7 @@ cudaError_t launch_reduce(const StepParams& P, int storage, const void* sc, cons
 
 cudaError_t launch_reduce_final(const double* partials, int nblocks, double* out, cudaStream_t st)
 {
-    k_reduce_final<<<1, 32, 0, st>>>(partials, nblocks, out);
+    k_reduce_final<<<1, 32 * kRedVals, 0, st>>>(partials, nblocks, out);
     return cudaGetLastError();
 }
 

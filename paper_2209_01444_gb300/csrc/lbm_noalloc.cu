@@ -9,6 +9,7 @@
 
 #include "lbm.h"
 #include "lbm_kernels.h"
+#include "lbm_reduce.cuh"
 
 namespace {
 
@@ -17,7 +18,7 @@ using lbm::StepParams;
 constexpr int kThreads = 256;
 constexpr int kNodesPerBlock = 4096;       // 16 nodes per thread
 constexpr int kMaxBlocks = 8192;           // 33,554,432 nodes
-constexpr int kVals = 7;                   // same partials as the handle's reduction
+constexpr int kVals = lbm::kRedValues;     // same partials as the handle's reduction
 
 // 8192 blocks x 7 partials x 8 bytes = 448 KiB per device.
 static __device__ __align__(256) double g_reduce_scratch[kMaxBlocks * kVals];
@@ -60,7 +61,8 @@ __device__ __forceinline__ double warp_max(double v)
 }
 
 // Variant of the handle's node reduction: block b folds nodes
-// [b * kNodesPerBlock, (b + 1) * kNodesPerBlock) in FP64 and writes its row of
+// [b * kNodesPerBlock, (b + 1) * kNodesPerBlock) with the same per-node
+// arithmetic (reduce_accumulate) and writes its row of
 // partials; every row it writes is overwritten, so nothing needs clearing.
 template <class Store>
 __global__ void __launch_bounds__(kThreads) k_reduce_chunks(const StepParams P, const void* __restrict__ sc,
@@ -83,17 +85,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce_chunks(const StepParams P, 
 #pragma unroll
         for (int i = 0; i < 9; ++i) h[i] = Store::load(sc, fl, lbm::kH + i, o, P);
         const lbm::Macro m = lbm::node_macros(f, n, g, h, P);
-        double sh = (double)P.rho0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) sh += (double)h[i];
-        const double u = sqrt((double)m.ux * m.ux + (double)m.uy * m.uy);
-        acc[0] += 0.5 * (double)m.p1;
-        acc[1] += 1.0 + (double)m.dC;
-        acc[2] += ((double)P.theta_ref + 0.5) + (double)m.dH;
-        acc[3] += sh;
-        acc[4] = fmax(acc[4], u);
-        acc[5] += (isfinite(m.p1) && isfinite(m.dC) && isfinite(m.dth) && isfinite(u)) ? 0.0 : 1.0;
-        acc[6] += (double)m.p1 - 1.0;
+        lbm::reduce_accumulate(P, m, h, acc);
     }
     __shared__ double sm[kVals][kThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
