@@ -31,6 +31,9 @@
  *       pre-collision f; s1 and N depend on grad(phi), so the formula is
  *       solved by fixed-point iteration from the isotropic guess (a_s = 1,
  *       N = 0), LOCAL_GRAD_ITERS passes;
+ *   R22 the isothermal alloy of Sec. 4.3 (isothermal 1) drops the latent
+ *       heat from the enthalpy, H = theta, so a uniform theta0 = 0 stays
+ *       0 exactly and the phase field sees only the solute;
  *   R5  |grad(phi)|^2 < 1e-12 (lattice units): n = N = J_at = 0, a_s = 1;
  *   R6  D2Q5 weights 1/3, 1/6 (forced by cs^2 = 1/3), D2Q9 weights 4/9, 1/9,
  *       1/36;
@@ -198,10 +201,12 @@ void orc_G_C(double dCux, double dCuy, double U, double gqx, double gqy, double 
     for (int i = 0; i < 5; ++i) out[i] = W5[i] * (C5[i][0] * vx + C5[i][1] * vy);
 }
 
-/* Eq. (22): g_0^eq = w_0 theta - h(phi)/2,  g_i^eq = w_i theta + w_i c_i . (H u)/cs^2. */
-void orc_geq(double theta, double hphi, double Hux, double Huy, double* out)
+/* Eq. (22): g_0^eq = w_0 theta - L h(phi),  g_i^eq = w_i theta + w_i c_i . (H u)/cs^2,
+ * with the latent term Lh = L h(phi): L = 1/2 as printed, L = 0 in the
+ * isothermal mode (reading R22). */
+void orc_geq(double theta, double Lh, double Hux, double Huy, double* out)
 {
-    out[0] = W5[0] * theta - 0.5 * hphi;
+    out[0] = W5[0] * theta - Lh;
     for (int i = 1; i < 5; ++i) out[i] = W5[i] * theta + W5[i] * (C5[i][0] * Hux + C5[i][1] * Huy) / CS2;
 }
 
@@ -306,6 +311,10 @@ struct orc_sim {
     long long steps;
 };
 
+/* Latent-heat factor L of H = theta - L h(phi): 1/2 (Eq. 21), 0 in the
+ * isothermal mode (reading R22). */
+static double latent(const orc_sim* s) { return s->P.isothermal ? 0.0 : 0.5; }
+
 static int is_periodic_x(const orc_sim* s) { return s->P.bc[0] == ORC_BC_PERIODIC; }
 static int is_periodic_y(const orc_sim* s) { return s->P.bc[2] == ORC_BC_PERIODIC; }
 
@@ -348,6 +357,7 @@ orc_sim* orc_create(const orc_params* P)
     if (P->eps_s < 0 || P->eps_s >= 1.0 / 3.0 || P->k <= 0 || P->k >= 1) return NULL;
     if (P->D <= 0 || P->alpha <= 0 || P->nu <= 0 || P->n_sub < 1) return NULL;
     if (P->grad_mode != 0 && P->grad_mode != 1) return NULL;
+    if (P->isothermal != 0 && P->isothermal != 1) return NULL;
     for (int b = 0; b < 4; ++b)
         if (!valid_bc(P->bc[b])) return NULL;
     if ((P->bc[0] == ORC_BC_PERIODIC) != (P->bc[1] == ORC_BC_PERIODIC)) return NULL;
@@ -464,7 +474,7 @@ static node_macro macros_at(const orc_sim* s, const double* f, const double* n, 
         H += g[i * N + x];
     }
     for (int i = 0; i < 9; ++i) hn[i] = h[i * N + x];
-    double theta = H + 0.5 * h_of_phi(s->P.h_kind, phi);
+    double theta = H + latent(s) * h_of_phi(s->P.h_kind, phi);
     double Fx, Fy, fsx, fsy;
     body_force(s, theta, C, &Fx, &Fy);
     flow_macros(hn, phi, Fx, Fy, &m.ux, &m.uy, &fsx, &fsy, &m.p);
@@ -575,7 +585,8 @@ static void nee_node(orc_sim* s, double* fp, double* np_, double* gp, int b, int
         thetab = s->P.dir_theta;
     }
     const double hb = h_of_phi(s->P.h_kind, phib), hf = h_of_phi(s->P.h_kind, mf.phi);
-    const double Hb = thetab - 0.5 * hb;
+    const double L = latent(s);
+    const double Hb = thetab - L * hb;
     const double sc = s->nsub_scale;
     orc_feq_phi(phib, eb);
     orc_feq_phi(mf.phi, ef);
@@ -583,8 +594,8 @@ static void nee_node(orc_sim* s, double* fp, double* np_, double* gp, int b, int
     orc_neq(Cb, 0.5 * (1.0 - phib) * Ub, Cb * ubx * sc, Cb * uby * sc, eb);
     orc_neq(mf.C, 0.5 * (1.0 - mf.phi) * mf.U, mf.C * mf.ux * sc, mf.C * mf.uy * sc, ef);
     for (int i = 0; i < 5; ++i) np_[i * N + b] = eb[i] + np_[i * N + f] - ef[i];
-    orc_geq(thetab, hb, Hb * ubx * sc, Hb * uby * sc, eb);
-    orc_geq(mf.theta, hf, mf.H * mf.ux * sc, mf.H * mf.uy * sc, ef);
+    orc_geq(thetab, L * hb, Hb * ubx * sc, Hb * uby * sc, eb);
+    orc_geq(mf.theta, L * hf, mf.H * mf.ux * sc, mf.H * mf.uy * sc, ef);
     for (int i = 0; i < 5; ++i) gp[i * N + b] = eb[i] + gp[i * N + f] - ef[i];
 }
 
@@ -736,7 +747,7 @@ static void coupled_step(orc_sim* s)
             const double Hux = H * usx, Huy = H * usy;
             double gg[5], geq[5], GT[5], gs[5];
             for (int i = 0; i < 5; ++i) gg[i] = s->g[i * N + idx];
-            orc_geq(theta, h_of_phi(P->h_kind, phi), Hux, Huy, geq);
+            orc_geq(theta, latent(s) * h_of_phi(P->h_kind, phi), Hux, Huy, geq);
             orc_G_theta(Hux - s->Hu_prev[idx], Huy - s->Hu_prev[N + idx], GT);
             collide(5, s->LamT, gg, geq, GT, gs);
             for (int i = 0; i < 5; ++i) {
@@ -862,13 +873,13 @@ static void set_equilibrium_state(orc_sim* s, const double* phi, const double* U
     for (int x = 0; x < N; ++x) {
         double C = C_of_U(U[x], phi[x], k);
         double hphi = h_of_phi(s->P.h_kind, phi[x]);
-        double H = theta[x] - 0.5 * hphi;
+        double H = theta[x] - latent(s) * hphi;
         double e[9];
         orc_feq_phi(phi[x], e);
         for (int i = 0; i < 5; ++i) s->f[i * N + x] = e[i];
         orc_neq(C, 0.5 * (1.0 - phi[x]) * U[x], C * ux[x] * sc, C * uy[x] * sc, e);
         for (int i = 0; i < 5; ++i) s->nC[i * N + x] = e[i];
-        orc_geq(theta[x], hphi, H * ux[x] * sc, H * uy[x] * sc, e);
+        orc_geq(theta[x], latent(s) * hphi, H * ux[x] * sc, H * uy[x] * sc, e);
         for (int i = 0; i < 5; ++i) s->g[i * N + x] = e[i];
         orc_heq(p[x], ux[x], uy[x], s->P.rho0, e);
         for (int i = 0; i < 9; ++i) s->h[i * N + x] = e[i];

@@ -26,6 +26,7 @@ typedef struct {
     double u_in[2];
     double dir_phi, dir_U, dir_theta;
     int grad_mode;                 /* 0: nine-point stencil (reading R4), 1: local scheme of Sec. 3.1 */
+    int isothermal;                /* 0: H = theta - h(phi)/2 (Eq. 21); 1: H = theta (Sec. 4.3, reading R22) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -59,7 +60,7 @@ void orc_G_phi(double Nx, double Ny, double as2, double* out);
 void orc_neq(double C, double qU, double Cux, double Cuy, double* out);
 void orc_G_C(double dCux, double dCuy, double U, double gqx, double gqy, double Jx, double Jy, double D,
              double* out);
-void orc_geq(double theta, double hphi, double Hux, double Huy, double* out);
+void orc_geq(double theta, double Lh, double Hux, double Huy, double* out);
 void orc_G_theta(double dHux, double dHuy, double* out);
 void orc_heq(double p, double ux, double uy, double rho0, double* out);
 void orc_F_u(double Fx, double Fy, double* out);

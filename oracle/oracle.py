@@ -44,6 +44,7 @@ class _Params(ct.Structure):
         ("u_in", ct.c_double * 2),
         ("dir_phi", ct.c_double), ("dir_U", ct.c_double), ("dir_theta", ct.c_double),
         ("grad_mode", ct.c_int),
+        ("isothermal", ct.c_int),
     ]
 
 
@@ -270,8 +271,8 @@ def G_C(dCux, dCuy, U, gqx, gqy, Jx, Jy, D):
     return _vec(5, _load().orc_G_C, dCux, dCuy, U, gqx, gqy, Jx, Jy, D)
 
 
-def geq(theta, hphi, Hux, Huy):
-    return _vec(5, _load().orc_geq, theta, hphi, Hux, Huy)
+def geq(theta, Lh, Hux, Huy):
+    return _vec(5, _load().orc_geq, theta, Lh, Hux, Huy)
 
 
 def G_theta(dHux, dHuy):

@@ -37,7 +37,7 @@ def thermosolutal_params(nx: int, ny: int, **over) -> dict:
              D=2.0, alpha=2.0, nu=2.0, rho0=1.0, n_sub=1, h_kind=0,
              gbetaT=0.0, gbetaC=0.0, theta_ref=-0.55, C_ref=1.0,
              force=(0.0, 0.0), bc=("periodic",) * 4, u_in=(0.0, 0.0),
-             dir_phi=-1.0, dir_U=0.0, dir_theta=-0.55, grad_mode=0)
+             dir_phi=-1.0, dir_U=0.0, dir_theta=-0.55, grad_mode=0, isothermal=0)
     p.update(over)
     return p
 
@@ -49,6 +49,22 @@ def thermal_params(nx: int, ny: int, **over) -> dict:
     lam = 0.8839 / 0.1385
     p = thermosolutal_params(nx, ny, dx=0.4, dt=0.008, eps_s=0.05, Mc_inf=0.0, alpha=4.0, D=4.0,
                              lambda_=lam, nu=4.0 * 23.1, bc=("symmetry",) * 4, theta_ref=-0.55)
+    p.update(over)
+    return p
+
+
+def solutal_params(n: int, flow: bool = False, **over) -> dict:
+    """The isothermal alloy of Sec. 4.3: L = n dx with dx = 0.4 W0 (as in
+    Sec. 4.2), dt = 0.02 tau0, eps = 0.02, theta0 = 0 with no latent heat,
+    D = 2, Mc_inf = 1, k = 0.15, lambda = 3.191 (d0 = a1 W0/lambda = 0.277 W0),
+    symmetry walls.  With flow: inflow of 1 W0/tau0 on the left, outflow on
+    the right, and the viscosity and n_sub = 15 of the Sec. 4.2 flow run (the
+    paper gives neither for this case)."""
+    p = thermosolutal_params(n, n, dx=0.4, dt=0.02, eps_s=0.02, Mc_inf=1.0, alpha=2.0, D=2.0, k=0.15,
+                             lambda_=3.191, nu=4.0 * 23.1, bc=("symmetry",) * 4, theta_ref=0.0,
+                             dir_theta=0.0, isothermal=1)
+    if flow:
+        p.update(n_sub=15, bc=("inflow", "outflow", "symmetry", "symmetry"), u_in=(1.0, 0.0))
     p.update(over)
     return p
 

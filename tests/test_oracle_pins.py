@@ -141,14 +141,16 @@ def test_solute_distributions_meet_appendix_a():
 
 
 def test_heat_distributions_meet_appendix_a():
-    """Eq. (22) against Eq. (A.7) with A = H = theta - h/2, B = Hu,
-    C_var = theta, J = 0: sum g^eq = H, sum c g^eq = Hu, sum cc g^eq = cs^2 theta I."""
+    """Eq. (22) against Eq. (A.7) with A = H = theta - L h, B = Hu,
+    C_var = theta, J = 0: sum g^eq = H, sum c g^eq = Hu, sum cc g^eq = cs^2 theta I,
+    for the printed L = 1/2 and the isothermal L = 0."""
     theta, hphi, ux, uy = -0.41, 0.6, 0.02, 0.013
-    H = theta - hphi / 2
-    m0, m1, m2 = _moments(O.geq(theta, hphi, H * ux, H * uy), C5)
-    assert m0 == pytest.approx(H, abs=1e-15)
-    np.testing.assert_allclose(m1, [H * ux, H * uy], atol=1e-16)
-    np.testing.assert_allclose(m2, CS2 * theta * np.eye(2), atol=1e-15)
+    for L in (0.5, 0.0):
+        H = theta - L * hphi
+        m0, m1, m2 = _moments(O.geq(theta, L * hphi, H * ux, H * uy), C5)
+        assert m0 == pytest.approx(H, abs=1e-15)
+        np.testing.assert_allclose(m1, [H * ux, H * uy], atol=1e-16)
+        np.testing.assert_allclose(m2, CS2 * theta * np.eye(2), atol=1e-15)
     G0, G1, _ = _moments(O.G_theta(2e-4, -1e-4), C5)
     assert G0 == pytest.approx(0, abs=1e-18)
     np.testing.assert_allclose(G1, [2e-4, -1e-4], atol=1e-18)
@@ -497,6 +499,30 @@ def test_periodic_run_conserves_solute_enthalpy_and_flow_mass():
     assert abs(m1["sum_H"] - m0["sum_H"]) < 1e-12 * abs(m0["sum_H"])
     assert m1["sum_h"] == pytest.approx(nx * ny * 1.0, rel=1e-13)
     assert m1["nonfinite"] == 0
+
+
+def test_isothermal_mode_keeps_theta_and_latent_mode_releases_heat():
+    """Reading R22 against Eq. (21).  One growing seed (U0 = -0.55, theta0 = 0,
+    Mc_inf = 1, solutal buoyancy drives a flow) in both modes.  Isothermal:
+    g^eq = 0 and G = 0 at theta = 0, so theta stays 0 bit for bit.  With the
+    latent heat the enthalpy H = theta - phi/2 is conserved on the periodic
+    box, so the melt warms by exactly half the growth of sum phi."""
+    n = 40
+    for iso in (1, 0):
+        p = W.thermosolutal_params(n, n, Mc_inf=1.0, gbetaC=10 * W.GBETA_C, theta_ref=0.0, isothermal=iso)
+        o = O.Oracle(p)
+        o.init_seeds([[20.0, 20.0, 6.0, 0.0]], -0.55, 0.0)
+        f0, m0 = o.fields(), o.metrics(20, 20)
+        o.step(150)
+        f1, m1 = o.fields(), o.metrics(20, 20)
+        grow = f1["phi"].sum() - f0["phi"].sum()
+        assert grow > 1.0 and np.abs(f1["uy"]).max() > 1e-6
+        if iso:
+            assert np.abs(f1["theta"]).max() == 0.0 and m1["sum_H"] == 0.0
+        else:
+            assert f1["theta"].max() > 1e-3
+            assert m1["sum_H"] == pytest.approx(m0["sum_H"], rel=1e-12, abs=1e-9)
+            assert f1["theta"].sum() - f0["theta"].sum() == pytest.approx(0.5 * grow, rel=1e-9)
 
 
 def test_centred_seed_keeps_fourfold_symmetry():
