@@ -108,6 +108,12 @@ typedef struct lbm_params {
                               (the local scheme of Sec. 3.1: grad(phi) from the
                               node's own first moment, solved by two
                               fixed-point passes from a_s = 1, N = 0)      */
+    int isothermal;        /* 0: enthalpy H = theta - h(phi)/2 (Eq. 21, latent
+                              heat released at the interface); 1: H = theta,
+                              no latent heat, the isothermal alloy of Sec. 4.3:
+                              a start at uniform theta0 = 0 keeps theta = 0
+                              exactly; a uniform theta0 != 0 stays uniform up
+                              to the flow's O(Ma^2) divergence                */
 } lbm_params;
 
 /* A seed (Sec. 4): centre and radius in lattice units, crystal-axis

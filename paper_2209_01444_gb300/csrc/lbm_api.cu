@@ -123,6 +123,7 @@ std::string validate(const lbm_params* p)
     if ((p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) return "bottom/top periodicity must match";
     if (p->storage < LBM_FP32 || p->storage > LBM_BF16) return "unknown storage";
     if (p->grad_mode != LBM_GRAD_FD9 && p->grad_mode != LBM_GRAD_LOCAL) return "unknown grad_mode";
+    if (p->isothermal != 0 && p->isothermal != 1) return "isothermal must be 0 or 1";
     return "";
 }
 
@@ -148,6 +149,7 @@ void derive(lbm_handle* h)
     const double nul = p.nu * dtf / (p.dx * p.dx);
     P.kappa3 = (float)(3.0 * W * W / tau);
     P.grad_local = p.grad_mode == LBM_GRAD_LOCAL ? 1 : 0;
+    P.latent = p.isothermal ? 0.0f : 0.5f;
     P.inv_tau = (float)(1.0 / tau);
     P.eps = (float)p.eps_s;
     P.lambda = (float)p.lambda;
@@ -178,14 +180,14 @@ void derive(lbm_handle* h)
     P.dir_U = (float)p.dir_U;
     P.dir_theta = (float)p.dir_theta;
     // Reference equilibrium whose deviations are stored (liquid at rest:
-    // phi = -1, C = 1, theta = theta_ref, p = 0), kept in FP64 for the state
+    // phi = -1, C = 1, theta = theta_ref, p = 0, H = theta_ref + L), kept in FP64 for the state
     // interface.
     const double w5[5] = {1.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
     const double th = (double)P.theta_ref;
     for (int i = 0; i < 5; ++i) {
         h->ref[lbm::kF + i] = -w5[i];
         h->ref[lbm::kN + i] = i == 0 ? 1.0 : 0.0;
-        h->ref[lbm::kG + i] = w5[i] * th + (i == 0 ? 0.5 : 0.0);
+        h->ref[lbm::kG + i] = w5[i] * th + (i == 0 ? (double)P.latent : 0.0);
     }
     for (int i = 0; i < 9; ++i) h->ref[lbm::kH + i] = i == 0 ? (double)P.rho0 : 0.0;
 }
@@ -335,6 +337,7 @@ int lbm_params_default(lbm_params* p, int nx, int ny)
     p->dir_theta = -0.55;
     p->storage = LBM_FP32;
     p->grad_mode = LBM_GRAD_FD9;
+    p->isothermal = 0;
     return LBM_OK;
 }
 

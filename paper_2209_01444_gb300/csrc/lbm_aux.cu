@@ -75,7 +75,7 @@ __device__ void init_node(const StepParams& P, long long o, float p1, float dC, 
 {
     const long long plane = P.plane;
     const float hp1 = h_plus_1(P.h_kind, p1);
-    const float H = (P.theta_ref + 0.5f) + dth - 0.5f * hp1;
+    const float H = (P.theta_ref + P.latent) + dth - P.latent * hp1;
     const float C = 1.0f + dC;
     const float sx = ux * P.nsub, sy = uy * P.nsub;
     float e[9];
@@ -85,7 +85,7 @@ __device__ void init_node(const StepParams& P, long long o, float p1, float dC, 
     deq_C(dC, (1.0f - 0.5f * p1) * Uf, C * sx, C * sy, e);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(sc, fl, kN + i, o, e[i], P);
-    deq_H(dth, hp1, H * sx, H * sy, e);
+    deq_H(dth, P.latent * hp1, H * sx, H * sy, e);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(sc, fl, kG + i, o, e[i], P);
     deq_flow(p, heqx, heqy, e);

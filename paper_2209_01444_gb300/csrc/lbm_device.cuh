@@ -16,9 +16,11 @@
 // rest (phi = -1, C = 1 so U = 0, theta = theta_ref, u = 0, p = 0):
 //   phi:  f^ref = (-1/3, -1/6, -1/6, -1/6, -1/6)       (sum -1)
 //   C:    n^ref = (1, 0, 0, 0, 0)                       (sum 1)
-//   H:    g^ref = (theta_ref/3 + 1/2, theta_ref/6 x 4)  (sum theta_ref + 1/2)
+//   H:    g^ref = (theta_ref/3 + L, theta_ref/6 x 4)    (sum theta_ref + L)
 //   flow: h^ref = (rho0, 0, ..., 0)                     (sum rho0)
 // The references are isotropic, so first moments are unchanged and the macro
+// (L = 1/2 is the latent-heat factor of H = theta - h(phi)/2, Eq. 21; L = 0
+// in the isothermal mode, where H = theta).  The macro
 // deviations phi + 1, C - 1, theta - theta_ref follow from sums of small
 // numbers without cancellation; the MRT collision and the modified streaming
 // of Eq. (13) are linear and carry over unchanged to deviations.  16-bit
@@ -56,6 +58,7 @@ struct StepParams {
     float rho0;
     float Fx, Fy, gbT, gbC;   // body force and buoyancy (flow lattice units)
     float theta_ref;          // buoyancy reference = reference state of the deviations
+    float latent;             // L in H = theta - L h(phi): 1/2 (Eq. 21), 0 when isothermal
     float dC_ref;             // 1 - C_ref: buoyancy offset of the solute term
     float nsub;               // flow-lattice velocity -> scalar-lattice velocity
     float cos_o, sin_o;       // orientation when the whole domain is one grain
@@ -180,7 +183,7 @@ __device__ __forceinline__ float coupling_Q(float phi, float theta, float U, con
 struct Macro {
     float p1;             // phi + 1
     float phi, dC, U, dth, hp1;   // phi, C - 1, U, theta - theta_ref, h(phi) + 1
-    float H, dH;          // H = theta - h(phi)/2 and its deviation H - (theta_ref + 1/2)
+    float H, dH;          // H = theta - L h(phi) and its deviation H - (theta_ref + L)
     float ux, uy, p;      // corrected velocity and pressure (flow lattice units)
     float Fx, Fy;         // external force F (flow lattice units)
     float fsx, fsy;       // fluid-solid force f = -u*
@@ -195,9 +198,9 @@ __device__ __forceinline__ Macro node_macros(const float* f, const float* n, con
     m.dC = n[0] + n[1] + n[2] + n[3] + n[4];
     const float dH = g[0] + g[1] + g[2] + g[3] + g[4];
     m.hp1 = h_plus_1(P.h_kind, m.p1);
-    m.dth = dH + 0.5f * m.hp1;                 // theta = H + h/2
+    m.dth = dH + P.latent * m.hp1;             // theta = H + L h
     m.dH = dH;
-    m.H = (P.theta_ref + 0.5f) + dH;
+    m.H = (P.theta_ref + P.latent) + dH;
     m.U = U_of(m.dC, m.p1, P.k);
     m.Fx = P.Fx;
     m.Fy = P.Fy + P.gbT * m.dth + P.gbC * (m.dC + P.dC_ref);
@@ -258,10 +261,10 @@ __device__ __forceinline__ void deq_C(float dC, float qU, float jx, float jy, fl
     e[2] = b + 0.5f * jy;
     e[4] = b - 0.5f * jy;
 }
-// Eq. (22) with dth = theta - theta_ref, hp1 = h(phi) + 1 and (jx, jy) = H u.
-__device__ __forceinline__ void deq_H(float dth, float hp1, float jx, float jy, float* e)
+// Eq. (22) with dth = theta - theta_ref, lhp1 = L (h(phi) + 1) and (jx, jy) = H u.
+__device__ __forceinline__ void deq_H(float dth, float lhp1, float jx, float jy, float* e)
 {
-    e[0] = dth * (1.0f / 3.0f) - 0.5f * hp1;
+    e[0] = dth * (1.0f / 3.0f) - lhp1;
     float b = dth * (1.0f / 6.0f);
     e[1] = b + 0.5f * jx;
     e[3] = b - 0.5f * jx;

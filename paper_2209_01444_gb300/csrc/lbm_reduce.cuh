@@ -3,8 +3,8 @@
 // that both give the same numbers.  The node's own arithmetic is FP32 (the
 // macros, the sum of its nine flow deviations, |u|); the running sums over
 // nodes are FP64, with the constant reference terms (C = 1 + dC, H =
-// theta_ref + 1/2 + dH, sum h = rho0 + sum of deviations) added per node in
-// FP64 so that long sums keep their digits.  FP64 work per node is a few
+// theta_ref + L + dH with L the latent-heat factor, sum h = rho0 + sum of
+// deviations) added per node in FP64 so that long sums keep their digits.  FP64 work per node is a few
 // additions: GB300's FP64 rate is a small fraction of its FP32 rate.
 #pragma once
 
@@ -22,7 +22,7 @@ __device__ __forceinline__ void reduce_accumulate(const StepParams& P, const Mac
     const float u = sqrtf(m.ux * m.ux + m.uy * m.uy);
     acc[0] += 0.5 * (double)m.p1;
     acc[1] += 1.0 + (double)m.dC;
-    acc[2] += ((double)P.theta_ref + 0.5) + (double)m.dH;
+    acc[2] += ((double)P.theta_ref + (double)P.latent) + (double)m.dH;
     acc[3] += (double)P.rho0 + (double)s9;
     acc[4] = fmax(acc[4], (double)u);
     acc[5] += (isfinite(m.p1) && isfinite(m.dC) && isfinite(m.dth) && isfinite(u)) ? 0.0 : 1.0;

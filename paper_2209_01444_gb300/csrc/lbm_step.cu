@@ -353,7 +353,7 @@ __device__ __forceinline__ void wall_node(const StepParams& P, void* __restrict_
         dthb = P.dir_theta - P.theta_ref;
     }
     const float hp1b = h_plus_1(P.h_kind, p1b);
-    const float Hb = (P.theta_ref + 0.5f) + dthb - 0.5f * hp1b;
+    const float Hb = (P.theta_ref + P.latent) + dthb - P.latent * hp1b;
     const float Cb = 1.0f + dCb, Cf = 1.0f + m.dC;
     const float sc = P.nsub;
     deq_phi(p1b, eb);
@@ -364,8 +364,8 @@ __device__ __forceinline__ void wall_node(const StepParams& P, void* __restrict_
     deq_C(m.dC, (1.0f - 0.5f * m.p1) * m.U, Cf * m.ux * sc, Cf * m.uy * sc, ef);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(pop, popf, kN + i, ob, eb[i] + n[i] - ef[i], P);
-    deq_H(dthb, hp1b, Hb * ubx * sc, Hb * uby * sc, eb);
-    deq_H(m.dth, m.hp1, m.H * m.ux * sc, m.H * m.uy * sc, ef);
+    deq_H(dthb, P.latent * hp1b, Hb * ubx * sc, Hb * uby * sc, eb);
+    deq_H(m.dth, P.latent * m.hp1, m.H * m.ux * sc, m.H * m.uy * sc, ef);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Store::store(pop, popf, kG + i, ob, eb[i] + g[i] - ef[i], P);
 }

@@ -38,6 +38,7 @@ class lbm_params(ct.Structure):
         ("dir_phi", ct.c_double), ("dir_U", ct.c_double), ("dir_theta", ct.c_double),
         ("storage", ct.c_int),
         ("grad_mode", ct.c_int),
+        ("isothermal", ct.c_int),
     ]
 
 
