@@ -71,6 +71,8 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_INFLOW = 1, LBM_BC_OUTFLOW = 2, LBM_BC_SYMMET
  * C = 1, theta = theta_ref, p = 0); the history fields stay FP32. */
 enum { LBM_FP32 = 0, LBM_FP16 = 1, LBM_BF16 = 2 };
 enum { LBM_GRAD_FD9 = 0, LBM_GRAD_LOCAL = 1 };
+/* Fused-step kernels (lbm_set_step_kernel). */
+enum { LBM_STEP_KERNEL_AUTO = 0, LBM_STEP_KERNEL_TILED = 1, LBM_STEP_KERNEL_TMA = 2 };
 
 /* Field indices for lbm_get_fields (bit i of the mask selects field i). */
 enum { LBM_FIELD_PHI = 0, LBM_FIELD_C = 1, LBM_FIELD_U = 2, LBM_FIELD_THETA = 3,
@@ -179,8 +181,25 @@ LBM_API int lbm_init_fields(lbm_handle* h, const double* fields, const double* o
  * from a captured CUDA graph. */
 LBM_API int lbm_step(lbm_handle* h, int nsteps);
 
-/* Wait for all queued work of h; reports an asynchronous CUDA error. */
+/* Wait for all queued work of h; reports an asynchronous CUDA error, and
+ * LBM_ETIMEOUT (once; the flag is then cleared) if a fused step of the TMA
+ * kernel gave up a bounded wait (1 s) for its copies since the last report
+ * (the flag is per process: any handle's kernel may have raised it). */
 LBM_API int lbm_synchronize(lbm_handle* h);
+
+/* Choose the kernel of the fused coupled step; both compute the same update
+ * bit for bit.  LBM_STEP_KERNEL_TILED: one CTA per 32 x 8 tile, loads staged
+ * in registers.  LBM_STEP_KERNEL_TMA: persistent CTAs; each tile's
+ * populations, history and grain ids are copied into shared memory by TMA
+ * while the previous tile is computed (FP32 storage and grids of at least
+ * 40 x 10 nodes only, else LBM_EINVAL).  LBM_STEP_KERNEL_AUTO (the default)
+ * takes the tiled kernel, the faster of the two on GB300 so far.  Drops the
+ * captured step graphs. */
+LBM_API int lbm_set_step_kernel(lbm_handle* h, int kernel);
+
+/* The kernel lbm_step uses now: LBM_STEP_KERNEL_TILED or LBM_STEP_KERNEL_TMA
+ * (negative for a NULL handle). */
+LBM_API int lbm_step_kernel(const lbm_handle* h);
 
 /* Number of coupled steps taken since the last initialisation. */
 LBM_API long long lbm_step_count(const lbm_handle* h);

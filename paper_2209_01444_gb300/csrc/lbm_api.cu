@@ -50,6 +50,8 @@ struct lbm_handle {
     bool initialised = false;
     std::string err;
     std::map<GraphKey, cudaGraphExec_t> graphs;
+    lbm::StepMaps* maps = nullptr;     // TMA descriptors of the fused step, when supported
+    int step_kernel = LBM_STEP_KERNEL_AUTO;
     // kernel timing (lbm_set_profiling)
     bool profiling = false;
     std::vector<cudaEvent_t> ev;   // begin/end pairs of pending fused-kernel launches
@@ -380,14 +382,43 @@ int lbm_create(const lbm_params* p, lbm_handle** out)
         return fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, msg);
     }
     h->P.grain_cs = h->grain_cs;
+    if (lbm::step_maps_supported(h->P, h->storage)) {
+        lbm::StepBuffers b = h->B;
+        b.grain = h->grain;  // the map covers the grain plane, used once the grid has grains
+        if (lbm::create_step_maps(h->P, h->storage, b, &h->maps) != cudaSuccess) {
+            h->maps = nullptr;  // the tiled kernel serves
+            cudaGetLastError();
+        }
+    }
+    h->B.maps = nullptr;  // LBM_STEP_KERNEL_AUTO: the tiled kernel
     *out = h;
     return LBM_OK;
+}
+
+int lbm_set_step_kernel(lbm_handle* h, int kernel)
+{
+    if (!h) return LBM_EINVAL;
+    if (kernel != LBM_STEP_KERNEL_AUTO && kernel != LBM_STEP_KERNEL_TILED && kernel != LBM_STEP_KERNEL_TMA)
+        return fail(h, LBM_EINVAL, "unknown step kernel");
+    if (kernel == LBM_STEP_KERNEL_TMA && !h->maps)
+        return fail(h, LBM_EINVAL, "the TMA step kernel needs FP32 storage and a grid of at least 40 x 10 nodes");
+    h->step_kernel = kernel;
+    h->B.maps = kernel == LBM_STEP_KERNEL_TMA ? h->maps : nullptr;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+int lbm_step_kernel(const lbm_handle* h)
+{
+    if (!h) return LBM_EINVAL;
+    return h->B.maps ? LBM_STEP_KERNEL_TMA : LBM_STEP_KERNEL_TILED;
 }
 
 void lbm_destroy(lbm_handle* h)
 {
     if (!h) return;
     drop_graphs(h);
+    lbm::destroy_step_maps(h->maps);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     void* ptrs[] = {h->B.sc[0], h->B.sc[1], h->B.fl[0], h->B.fl[1], h->B.hist, h->B.fb, h->grain,
                     h->grain_cs, h->d_partials, h->d_red, h->d_f64, h->d_f32, h->d_seeds,
@@ -621,6 +652,9 @@ int lbm_synchronize(lbm_handle* h)
 {
     if (!h) return LBM_EINVAL;
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    int flag = 0;
+    LBM_CUDA(h, lbm::step_error(&flag, true));
+    if (flag) return fail(h, LBM_ETIMEOUT, "a fused step gave up a bounded wait for its TMA copies");
     return LBM_OK;
 }
 

@@ -2,6 +2,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "lbm_kernels.h"
 #include "lbm_reduce.cuh"
 
@@ -268,6 +270,8 @@ __global__ void k_encode(const StepParams P, const float* __restrict__ in, void*
 
 // ------------------------------------------------------------- reductions
 constexpr int kRedThreads = 256;
+constexpr int kTipThreads = 256;
+constexpr int kTipCluster = 8;  // CTAs per ray
 constexpr int kRedVals = kRedValues;
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -283,39 +287,14 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// Pass 1: each block accumulates a fixed, grid-strided subset of nodes
-// (FP64 sums of FP32 per-node terms, reduce_accumulate) and writes its
-// kRedVals partials (deterministic order).
+// Pass 1: block b folds its chunk of nodes into kRedVals partials
+// (reduce_chunk: FP32 per thread, FP64 across threads, fixed order).
 template <class Store>
-__global__ void __launch_bounds__(kRedThreads) k_reduce_nodes(const StepParams P, const void* __restrict__ sc,
-                                                              const void* __restrict__ fl,
-                                                              double* __restrict__ partials)
+__global__ void __launch_bounds__(kRedThreadsPerBlock) k_reduce_nodes(const StepParams P, const void* __restrict__ sc,
+                                                                      const void* __restrict__ fl,
+                                                                      double* __restrict__ partials)
 {
-    double acc[kRedVals] = {0, 0, 0, 0, 0, 0, 0};
-    const long long N = (long long)P.nx * P.ny;
-    for (long long t = blockIdx.x * (long long)kRedThreads + threadIdx.x; t < N;
-         t += (long long)gridDim.x * kRedThreads) {
-        const int y = (int)(t / P.nx), x = (int)(t - (long long)y * P.nx);
-        const long long o = (long long)y * P.pitch + x;
-        float f[5], n[5], g[5], h[9];
-        load_node<Store>(P, sc, fl, o, f, n, g, h);
-        const Macro m = node_macros(f, n, g, h, P);
-        reduce_accumulate(P, m, h, acc);
-    }
-    __shared__ double sm[kRedVals][kRedThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kRedVals; ++k) {
-        const double v = k == 4 ? warp_max(acc[k]) : warp_sum(acc[k]);
-        if (lane == 0) sm[k][wid] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < kRedVals) {
-        const int k = threadIdx.x;
-        double v = sm[k][0];
-        for (int w = 1; w < kRedThreads / 32; ++w) v = (k == 4) ? fmax(v, sm[k][w]) : v + sm[k][w];
-        partials[(long long)blockIdx.x * kRedVals + k] = v;
-    }
+    reduce_chunk<Store>(P, sc, fl, partials);
 }
 
 // Pass 2: one warp per value folds the partials: lane l takes blocks
@@ -417,29 +396,56 @@ __device__ double phi_bilinear(const StepParams& P, const void* sc, double px, d
            (1 - fx) * fy * phi_at<Store>(P, sc, i, j + 1) + fx * fy * phi_at<Store>(P, sc, i + 1, j + 1);
 }
 
-// Tip distance along three rays from (cx, cy): block r handles ray r.
-// phi is sampled every half node while the sample is inside the grid; the
-// outermost sample with phi > 0 and its successor are interpolated to 0.
 template <class Store>
-__global__ void __launch_bounds__(kRedThreads) k_tips(const StepParams P, const void* __restrict__ sc,
-                                                      double cx, double cy, double c, double s,
-                                                      double* __restrict__ out)
+__device__ __forceinline__ float phi_at_f(const StepParams& P, const void* sc, int x, int y)
 {
-    const int r = blockIdx.x;
+    const long long o = (long long)y * P.pitch + x;
+    float s = 0.0f;  // phi + 1
+#pragma unroll
+    for (int i = 0; i < 5; ++i) s += Store::load(sc, nullptr, kF + i, o, P);
+    return s - 1.0f;
+}
+
+// Tip distance along three rays from (cx, cy).  A cluster of kTipCluster
+// CTAs handles one ray; its threads take the half-node samples j in turn.  A
+// sample counts while its position (FP64) is inside the grid; phi there is
+// interpolated bilinearly in FP32 to decide phi > 0 (the FP64 pipe of
+// GB300 would otherwise bound this kernel).  The CTAs combine the outermost
+// positive sample and the first outside one through distributed shared
+// memory, and rank 0 interpolates between that sample and its successor
+// to phi = 0 in FP64.
+template <class Store>
+__global__ void __cluster_dims__(kTipCluster, 1, 1) __launch_bounds__(kTipThreads)
+    k_tips(const StepParams P, const void* __restrict__ sc, double cx, double cy, double c, double s,
+           double* __restrict__ out)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int r = blockIdx.x / kTipCluster;
     const double ex = r == 0 ? c : (r == 1 ? -c : -s);
     const double ey = r == 0 ? s : (r == 1 ? -s : c);
     const int jmax = 2 * (P.nx + P.ny) + 4;
     int last = -1, first_out = jmax;
-    for (int j = threadIdx.x; j < jmax; j += kRedThreads) {
+    for (int j = rank * kTipThreads + threadIdx.x; j < jmax; j += kTipCluster * kTipThreads) {
         const double px = cx + j * 0.5 * ex, py = cy + j * 0.5 * ey;
         const bool inside = !(px < 0 || py < 0 || px > P.nx - 1 || py > P.ny - 1);
         if (!inside) {
             first_out = min(first_out, j);
             continue;
         }
-        if (phi_bilinear<Store>(P, sc, px, py) > 0.0) last = max(last, j);
+        int i0 = (int)floor(px), j0 = (int)floor(py);
+        if (i0 > P.nx - 2) i0 = P.nx - 2;
+        if (j0 > P.ny - 2) j0 = P.ny - 2;
+        const float fx = (float)(px - i0), fy = (float)(py - j0);
+        const float v = (1.0f - fx) * (1.0f - fy) * phi_at_f<Store>(P, sc, i0, j0) +
+                        fx * (1.0f - fy) * phi_at_f<Store>(P, sc, i0 + 1, j0) +
+                        (1.0f - fx) * fy * phi_at_f<Store>(P, sc, i0, j0 + 1) +
+                        fx * fy * phi_at_f<Store>(P, sc, i0 + 1, j0 + 1);
+        if (v > 0.0f) last = max(last, j);
     }
-    __shared__ int s_last[kRedThreads / 32], s_out[kRedThreads / 32];
+    __shared__ int s_last[kTipThreads / 32], s_out[kTipThreads / 32];
+    __shared__ int c_last, c_out;  // this CTA's result, read by rank 0
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         last = max(last, __shfl_down_sync(0xffffffffu, last, d));
@@ -451,9 +457,18 @@ __global__ void __launch_bounds__(kRedThreads) k_tips(const StepParams P, const 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < kRedThreads / 32; ++w) {
+        for (int w = 1; w < kTipThreads / 32; ++w) {
             last = max(last, s_last[w]);
             first_out = min(first_out, s_out[w]);
+        }
+        c_last = last;
+        c_out = first_out;
+    }
+    cluster.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        for (int q = 1; q < kTipCluster; ++q) {
+            last = max(last, *cluster.map_shared_rank(&c_last, q));
+            first_out = min(first_out, *cluster.map_shared_rank(&c_out, q));
         }
         // samples past the first outside one never count (the ray leaves a
         // rectangle once), so clip `last` to the inside run
@@ -469,6 +484,7 @@ __global__ void __launch_bounds__(kRedThreads) k_tips(const StepParams P, const 
         }
         out[7 + r] = tip;
     }
+    cluster.sync();  // rank 0 has read the other CTAs' shared memory
 }
 
 template <class Store>
@@ -524,9 +540,9 @@ cudaError_t reduce_t(const StepParams& P, const void* sc, const void* fl, double
                      double* partials, double* out, cudaStream_t st)
 {
     const int nb = reduce_blocks(P);
-    k_reduce_nodes<Store><<<nb, kRedThreads, 0, st>>>(P, sc, fl, partials);
+    k_reduce_nodes<Store><<<nb, kRedThreadsPerBlock, 0, st>>>(P, sc, fl, partials);
     k_reduce_final<<<1, 32 * kRedVals, 0, st>>>(partials, nb, out);
-    k_tips<Store><<<3, kRedThreads, 0, st>>>(P, sc, cx, cy, c, s, out);
+    k_tips<Store><<<3 * kTipCluster, kTipThreads, 0, st>>>(P, sc, cx, cy, c, s, out);
     return cudaGetLastError();
 }
 
@@ -635,12 +651,7 @@ cudaError_t launch_encode(const StepParams& P, int storage, const float* in, voi
     }
 }
 
-int reduce_blocks(const StepParams& P)
-{
-    const long long N = (long long)P.nx * P.ny;
-    long long b = (N + kRedThreads - 1) / kRedThreads;
-    return (int)(b < 1024 ? b : 1024);
-}
+int reduce_blocks(const StepParams& P) { return (int)reduce_chunk_blocks((long long)P.nx * P.ny); }
 
 size_t reduce_partials_size(const StepParams& P) { return (size_t)reduce_blocks(P) * kRedVals; }
 
@@ -664,9 +675,9 @@ cudaError_t launch_tips(const StepParams& P, int storage, const void* sc, double
                         double* out, cudaStream_t st)
 {
     switch (storage) {
-    case kStoreF16: k_tips<StoreF16><<<3, kRedThreads, 0, st>>>(P, sc, cx, cy, c, s, out); break;
-    case kStoreBF16: k_tips<StoreBF16><<<3, kRedThreads, 0, st>>>(P, sc, cx, cy, c, s, out); break;
-    default: k_tips<StoreF32><<<3, kRedThreads, 0, st>>>(P, sc, cx, cy, c, s, out); break;
+    case kStoreF16: k_tips<StoreF16><<<3 * kTipCluster, kTipThreads, 0, st>>>(P, sc, cx, cy, c, s, out); break;
+    case kStoreBF16: k_tips<StoreBF16><<<3 * kTipCluster, kTipThreads, 0, st>>>(P, sc, cx, cy, c, s, out); break;
+    default: k_tips<StoreF32><<<3 * kTipCluster, kTipThreads, 0, st>>>(P, sc, cx, cy, c, s, out); break;
     }
     return cudaGetLastError();
 }

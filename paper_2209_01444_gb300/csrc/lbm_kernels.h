@@ -28,7 +28,18 @@ struct StepBuffers {
     const uint8_t* grain;  // grain id plane or null (uniform orientation)
     int cs, cf;            // indices of the buffers holding the newest populations
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // recorded around the fused kernel when set
+    const struct StepMaps* maps = nullptr;  // TMA descriptors: use the TMA-staged fused kernel when set
 };
+
+// TMA descriptors of a handle's buffers for the TMA-staged fused kernel
+// (FP32 storage, grids of at least 40 x 10 nodes): cudaErrorNotSupported
+// otherwise.  The buffers of B must stay where they are while the maps live.
+struct StepMaps;
+bool step_maps_supported(const StepParams& P, int storage);
+cudaError_t create_step_maps(const StepParams& P, int storage, const StepBuffers& B, StepMaps** out);
+void destroy_step_maps(StepMaps* m);
+// Flag raised when a bounded wait of the TMA-staged kernel expired.
+cudaError_t step_error(int* flag, bool clear);
 
 cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s);
 

@@ -15,8 +15,8 @@ namespace {
 
 using lbm::StepParams;
 
-constexpr int kThreads = 256;
-constexpr int kNodesPerBlock = 4096;       // 16 nodes per thread
+constexpr int kThreads = lbm::kRedThreadsPerBlock;
+constexpr int kNodesPerBlock = lbm::kRedNodesPerBlock;  // 16 nodes per thread
 constexpr int kMaxBlocks = 8192;           // 33,554,432 nodes
 constexpr int kVals = lbm::kRedValues;     // same partials as the handle's reduction
 
@@ -47,60 +47,15 @@ cudaError_t scratch_for_current_device(double** out)
     return cudaSuccess;
 }
 
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v)
-{
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, d));
-    return v;
-}
-
-// Variant of the handle's node reduction: block b folds nodes
-// [b * kNodesPerBlock, (b + 1) * kNodesPerBlock) with the same per-node
-// arithmetic (reduce_accumulate) and writes its row of
-// partials; every row it writes is overwritten, so nothing needs clearing.
+// Variant of the handle's node pass: block b folds its chunk of
+// kNodesPerBlock nodes with the same arithmetic and order (reduce_chunk) and
+// writes its row of partials; every row it writes is overwritten, so nothing
+// needs clearing.
 template <class Store>
 __global__ void __launch_bounds__(kThreads) k_reduce_chunks(const StepParams P, const void* __restrict__ sc,
                                                             const void* __restrict__ fl, double* __restrict__ partials)
 {
-    double acc[kVals] = {0, 0, 0, 0, 0, 0, 0};
-    const long long N = (long long)P.nx * P.ny;
-    const long long first = (long long)blockIdx.x * kNodesPerBlock;
-    const long long last = min(first + kNodesPerBlock, N);
-    for (long long t = first + threadIdx.x; t < last; t += kThreads) {
-        const int y = (int)(t / P.nx), x = (int)(t - (long long)y * P.nx);
-        const long long o = (long long)y * P.pitch + x;
-        float f[5], n[5], g[5], h[9];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) f[i] = Store::load(sc, fl, lbm::kF + i, o, P);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) n[i] = Store::load(sc, fl, lbm::kN + i, o, P);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) g[i] = Store::load(sc, fl, lbm::kG + i, o, P);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = Store::load(sc, fl, lbm::kH + i, o, P);
-        const lbm::Macro m = lbm::node_macros(f, n, g, h, P);
-        lbm::reduce_accumulate(P, m, h, acc);
-    }
-    __shared__ double sm[kVals][kThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kVals; ++k) {
-        const double v = k == 4 ? warp_max(acc[k]) : warp_sum(acc[k]);
-        if (lane == 0) sm[k][wid] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < kVals) {
-        const int k = threadIdx.x;
-        double v = sm[k][0];
-        for (int w = 1; w < kThreads / 32; ++w) v = (k == 4) ? fmax(v, sm[k][w]) : v + sm[k][w];
-        partials[(long long)blockIdx.x * kVals + k] = v;
-    }
+    lbm::reduce_chunk<Store>(P, sc, fl, partials);
 }
 
 int fail(int code, const char* msg)

@@ -17,11 +17,28 @@
 // Periodic wrap is applied to every streaming destination; on non-periodic
 // sides the wrapped values land on wall nodes, which the wall kernel then
 // overwrites completely.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stddef.h>
 
+#include <mutex>
+#include <type_traits>
+
+#include "lbm_tma.cuh"
 #include "lbm_kernels.h"
 
 namespace lbm {
+
+// Tensor maps of the TMA-staged fused kernel for one pair of source buffers.
+struct StepTensorMaps {
+    CUtensorMap f, ng, h, hist, grain;
+};
+
+struct StepMaps {
+    StepTensorMaps m[2][2];  // [scalar buffer index][flow buffer index]
+    int ctas;                // persistent CTAs: resident CTAs per SM x SMs
+};
 
 namespace {
 
@@ -44,69 +61,31 @@ __device__ __forceinline__ int mirror_or_wrap_local(int g, int n, int periodic, 
 #define LBM_STEP_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for (64 registers)
 #endif
 
-// One tile of the coupled step: the CTA (TX x TYV threads) updates the nodes
-// [x0, x0 + TX) x [y0, y0 + TYV) of one domain.  GRAIN: the domain may carry a
-// grain map (read when `grain` is not null).  All threads reach the one
-// barrier, so callers may loop over tiles.
-template <class Store, bool GRAIN, bool WRITE_FB, int TYV>
-__device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __restrict__ src,
-                                             const void* __restrict__ srcf, void* __restrict__ dst,
-                                             void* __restrict__ dstf, float* __restrict__ hist,
-                                             const uint8_t* __restrict__ grain, float* __restrict__ fb, int x0,
-                                             int y0, float (&fs)[5][TYV + 2][TX + 2], float (&ps)[TYV + 2][TX + 2])
+// Per-node part of the coupled step for node (x, y) = tile-local (lx - 1, ly - 1):
+// f, n, g, h are its populations at time n, the *_prev values its history;
+// fs holds the tile's phi populations with a one-node halo, node (x, y) at
+// column fx = lx - 1 + XO of rows of FW floats; ps holds phi on the tile and
+// halo with node (x, y) at [ly][lx].  Collides, push-streams (the phase field
+// by the modified streaming of Eq. 13) and writes the history.
+template <class Store, bool GRAIN, bool WRITE_FB, int TYV, int FW, int XO>
+__device__ __forceinline__ void coupled_node(const StepParams& P, void* __restrict__ dst, void* __restrict__ dstf,
+                                             float* __restrict__ hist, float* __restrict__ fb, int x, int y,
+                                             int lx, int ly, const float (&f)[5], const float (&n)[5],
+                                             const float (&g)[5], const float (&h)[9], float phi_prev,
+                                             float Q_prev, float Cux_prev, float Cuy_prev, float Hux_prev,
+                                             float Huy_prev, bool grain_on, uint8_t gid,
+                                             const float (&fs)[5][TYV + 2][FW],
+                                             const float (&ps)[TYV + 2][TX + 2])
 {
-    const int tx = threadIdx.x, ty = threadIdx.y;
     const long long plane = P.plane;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool active = x < P.nx && y < P.ny;
-    // own-node loads first, so that they are in flight while the tile loads
-    const long long o = active ? (long long)y * P.pitch + x : 0;
-    float n[5], g[5], h[9];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) n[i] = Store::load(src, srcf, kN + i, o, P);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) g[i] = Store::load(src, srcf, kG + i, o, P);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = Store::load(src, srcf, kH + i, o, P);
-    const float phi_prev = hist[0 * plane + o];
-    const float Q_prev = hist[1 * plane + o];
-    const float Cux_prev = hist[2 * plane + o], Cuy_prev = hist[3 * plane + o];
-    const float Hux_prev = hist[4 * plane + o], Huy_prev = hist[5 * plane + o];
-    uint8_t gid = 0;
-    if (GRAIN && grain) gid = grain[o];
-
-    // phi populations of the tile and its halo (periodic wrap), and phi there.
-    for (int e = ty * TX + tx; e < (TX + 2) * (TYV + 2); e += TX * TYV) {
-        const int hx = e % (TX + 2), hy = e / (TX + 2);
-        int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-        gx = (gx < 0) ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-        gy = (gy < 0) ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
-        if (gx >= P.nx) gx = wrap(gx, P.nx);  // domains narrower than a tile
-        if (gy >= P.ny) gy = wrap(gy, P.ny);
-        const long long oh = (long long)gy * P.pitch + gx;
-        float sum = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            float v = Store::load(src, srcf, kF + i, oh, P);
-            fs[i][hy][hx] = v;
-            sum += v;
-        }
-        ps[hy][hx] = sum;
-    }
-    __syncthreads();
-
-    if (!active) return;
-    const int lx = tx + 1, ly = ty + 1;
-
-    float f[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) f[i] = fs[i][ly][lx];
+    const long long o = (long long)y * P.pitch + x;
+    const int fx = lx - 1 + XO;
 
     const Macro m = node_macros(f, n, g, h, P);
     const float usx = m.ux * P.nsub, usy = m.uy * P.nsub;  // velocity of the scalar lattice
 
     float co = P.cos_o, so = P.sin_o;
-    if (GRAIN && grain) {
+    if (GRAIN && grain_on) {
         const float2 cs = P.grain_cs[gid];
         co = cs.x;
         so = cs.y;
@@ -194,8 +173,8 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
         // modified streaming of the phase field: the destination's time-n
         // population sits in the shared tile (its halo is periodic-wrapped)
         const float ia = 1.0f / as2, ib = ia - 1.0f;
-        const float fd[5] = {fs[0][ly][lx], fs[1][ly][lx + 1], fs[2][ly + 1][lx], fs[3][ly][lx - 1],
-                             fs[4][ly - 1][lx]};
+        const float fd[5] = {fs[0][ly][fx], fs[1][ly][fx + 1], fs[2][ly + 1][fx], fs[3][ly][fx - 1],
+                             fs[4][ly - 1][fx]};
 #pragma unroll
         for (int i = 0; i < 5; ++i) Store::store(dst, dstf, kF + i, d5[i], fo[i] * ia - ib * fd[i], P);
     }
@@ -216,6 +195,67 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
     if (WRITE_FB) fb[o] = m.Fy;
 }
 
+
+// One tile of the coupled step: the CTA (TX x TYV threads) updates the nodes
+// [x0, x0 + TX) x [y0, y0 + TYV) of one domain.  GRAIN: the domain may carry a
+// grain map (read when `grain` is not null).  All threads reach the one
+// barrier, so callers may loop over tiles.
+template <class Store, bool GRAIN, bool WRITE_FB, int TYV>
+__device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __restrict__ src,
+                                             const void* __restrict__ srcf, void* __restrict__ dst,
+                                             void* __restrict__ dstf, float* __restrict__ hist,
+                                             const uint8_t* __restrict__ grain, float* __restrict__ fb, int x0,
+                                             int y0, float (&fs)[5][TYV + 2][TX + 2], float (&ps)[TYV + 2][TX + 2])
+{
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long plane = P.plane;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < P.nx && y < P.ny;
+    // own-node loads first, so that they are in flight while the tile loads
+    const long long o = active ? (long long)y * P.pitch + x : 0;
+    float n[5], g[5], h[9];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) n[i] = Store::load(src, srcf, kN + i, o, P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = Store::load(src, srcf, kG + i, o, P);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = Store::load(src, srcf, kH + i, o, P);
+    const float phi_prev = hist[0 * plane + o];
+    const float Q_prev = hist[1 * plane + o];
+    const float Cux_prev = hist[2 * plane + o], Cuy_prev = hist[3 * plane + o];
+    const float Hux_prev = hist[4 * plane + o], Huy_prev = hist[5 * plane + o];
+    uint8_t gid = 0;
+    if (GRAIN && grain) gid = grain[o];
+
+    // phi populations of the tile and its halo (periodic wrap), and phi there.
+    for (int e = ty * TX + tx; e < (TX + 2) * (TYV + 2); e += TX * TYV) {
+        const int hx = e % (TX + 2), hy = e / (TX + 2);
+        int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+        gx = (gx < 0) ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+        gy = (gy < 0) ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+        if (gx >= P.nx) gx = wrap(gx, P.nx);  // domains narrower than a tile
+        if (gy >= P.ny) gy = wrap(gy, P.ny);
+        const long long oh = (long long)gy * P.pitch + gx;
+        float sum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            float v = Store::load(src, srcf, kF + i, oh, P);
+            fs[i][hy][hx] = v;
+            sum += v;
+        }
+        ps[hy][hx] = sum;
+    }
+    __syncthreads();
+
+    if (!active) return;
+    float f[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) f[i] = fs[i][ty + 1][tx + 1];
+    coupled_node<Store, GRAIN, WRITE_FB, TYV, TX + 2, 1>(P, dst, dstf, hist, fb, x, y, tx + 1, ty + 1, f, n, g, h,
+                                                          phi_prev, Q_prev, Cux_prev, Cuy_prev, Hux_prev, Huy_prev,
+                                                          grain != nullptr, gid, fs, ps);
+}
+
 template <class Store, bool GRAIN, bool WRITE_FB>
 __global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
     k_coupled_step(const StepParams P, const void* __restrict__ src, const void* __restrict__ srcf,
@@ -227,6 +267,151 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
     coupled_tile<Store, GRAIN, WRITE_FB, TY>(P, src, srcf, dst, dstf, hist, grain, fb, blockIdx.x * TX,
                                              blockIdx.y * TY, fs, ps);
 }
+
+// ------------------------------------------------------- TMA-staged variant
+// The same per-node update (coupled_node) with the tile's inputs staged in
+// shared memory by TMA.  Persistent CTAs walk the tiles; while a CTA computes
+// one tile, the copies of its next tile are in flight into the other of two
+// stages, so the loads no longer wait in registers (the register-staged
+// kernel holds 25 loads per thread across its tile barrier).  FP32 storage.
+//
+// Per stage, five boxes of the populations at time n (x fastest):
+//   f:     phi populations, x0 - 4 .. x0 + 35 (a 16-byte aligned start that
+//          covers the one-node halo), y0 - 1 .. y0 + TY, planes 0..4;
+//   ng:    C and H populations of the tile, planes 5..14;
+//   h:     flow populations of the tile;
+//   hist:  the kHist history planes of the tile;
+//   grain: grain ids of the tile (grain map only).
+// Boxes reaching past the grid are zero-filled by TMA; the halo cells there
+// are then loaded with the periodic wrap the register-staged kernel uses.
+namespace tmastep {
+
+constexpr int FW = 40;          // f-box row: x0 - 4 .. x0 + 35
+constexpr int XO = 4;           // column of node x0 in the f-box
+constexpr int kStages = 2;
+constexpr int kMinBlocks = 3;   // resident CTAs per SM (shared memory and registers)
+
+struct __align__(128) Stage {
+    float f[5][TY + 2][FW];
+    float pad[16];  // next box 128-byte aligned
+    float ng[10][TY][TX];
+    float h[9][TY][TX];
+    float hist[kHist][TY][TX];
+    uint8_t grain[TY][TX];
+};
+static_assert(offsetof(Stage, ng) % 128 == 0 && offsetof(Stage, h) % 128 == 0, "TMA box alignment");
+static_assert(offsetof(Stage, hist) % 128 == 0 && offsetof(Stage, grain) % 128 == 0, "TMA box alignment");
+static_assert(sizeof(Stage) % 128 == 0, "stage alignment");
+
+constexpr uint32_t kBytesF = sizeof(float) * 5 * (TY + 2) * FW;
+constexpr uint32_t kBytesNG = sizeof(float) * 10 * TY * TX;
+constexpr uint32_t kBytesH = sizeof(float) * 9 * TY * TX;
+constexpr uint32_t kBytesHist = sizeof(float) * kHist * TY * TX;
+constexpr uint32_t kBytesGrain = TY * TX;
+constexpr size_t kSmemBytes = kStages * sizeof(Stage) + 128;  // + alignment slack
+
+__device__ int g_step_error;  // set when a bounded wait of the staged kernel expired
+
+using Maps = StepTensorMaps;
+
+__device__ __forceinline__ void issue(Stage& st, uint64_t* bar, const Maps& M, bool grain, int x0, int y0)
+{
+    tma_mbar_expect(bar, kBytesF + kBytesNG + kBytesH + kBytesHist + (grain ? kBytesGrain : 0));
+    tma_load_3d(&st.f[0][0][0], &M.f, x0 - XO, y0 - 1, kF, bar);
+    tma_load_3d(&st.ng[0][0][0], &M.ng, x0, y0, kN, bar);
+    tma_load_3d(&st.h[0][0][0], &M.h, x0, y0, 0, bar);
+    tma_load_3d(&st.hist[0][0][0], &M.hist, x0, y0, 0, bar);
+    if (grain) tma_load_2d(&st.grain[0][0], &M.grain, x0, y0, bar);
+}
+
+template <bool GRAIN, bool WRITE_FB>
+__global__ void __launch_bounds__(TX* TY, kMinBlocks)
+    k_coupled_step_tma(const StepParams P, const __grid_constant__ Maps M, const void* __restrict__ src,
+                       void* __restrict__ dst, void* __restrict__ dstf, float* __restrict__ hist,
+                       const uint8_t* __restrict__ grain, float* __restrict__ fb, int tiles_x, int ntiles)
+{
+    extern __shared__ unsigned char smem_raw[];
+    Stage* stages = (Stage*)(smem_raw + ((128u - (tma_smem_u32(smem_raw) & 127u)) & 127u));
+    __shared__ uint64_t full[kStages];
+    __shared__ float ps[TY + 2][TX + 2];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const bool has_grain = GRAIN && grain != nullptr;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) tma_mbar_init(&full[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&M.f) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&M.ng) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&M.h) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&M.hist) : "memory");
+    }
+    __syncthreads();
+    int tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles)
+        issue(stages[0], &full[0], M, has_grain, (tile % tiles_x) * TX, (tile / tiles_x) * TY);
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const int s = it & 1;
+        const int next = tile + gridDim.x;
+        if (tid == 0 && next < ntiles) {
+            // stage s ^ 1 was released by the barrier that ended the last tile
+            issue(stages[s ^ 1], &full[s ^ 1], M, has_grain, (next % tiles_x) * TX, (next / tiles_x) * TY);
+        }
+        const bool ok = tma_mbar_wait(&full[s], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(&g_step_error, 1);
+                // let the copies in flight land (bounded) before the CTA exits
+                tma_mbar_wait(&full[s], (uint32_t)((it >> 1) & 1));
+                if (next < ntiles) tma_mbar_wait(&full[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            return;
+        }
+        Stage& st = stages[s];
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+
+        // halo cells outside the grid: periodic wrap, as the register-staged
+        // kernel loads them; then phi = sum f on the tile and its halo
+        const bool edge = x0 == 0 || y0 == 0 || x0 + TX + 1 > P.nx || y0 + TY + 1 > P.ny;
+        for (int e = tid; e < (TX + 2) * (TY + 2); e += TX * TY) {
+            const int hx = e % (TX + 2), hy = e / (TX + 2);
+            const int c = hx + XO - 1;
+            if (edge) {
+                const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+                if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny) {
+                    const long long oh = (long long)wrap(gy, P.ny) * P.pitch + wrap(gx, P.nx);
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) st.f[i][hy][c] = ((const float*)src)[(kF + i) * P.plane + oh];
+                }
+            }
+            float sum = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) sum += st.f[i][hy][c];
+            ps[hy][hx] = sum;
+        }
+        __syncthreads();
+
+        const int x = x0 + tx, y = y0 + ty;
+        if (x < P.nx && y < P.ny) {
+            float f[5], n[5], g[5], h[9];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) f[i] = st.f[i][ty + 1][tx + XO];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) n[i] = st.ng[i][ty][tx];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) g[i] = st.ng[5 + i][ty][tx];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) h[i] = st.h[i][ty][tx];
+            const uint8_t gid = has_grain ? st.grain[ty][tx] : (uint8_t)0;
+            coupled_node<StoreF32, GRAIN, WRITE_FB, TY, FW, XO>(
+                P, dst, dstf, hist, fb, x, y, tx + 1, ty + 1, f, n, g, h, st.hist[0][ty][tx], st.hist[1][ty][tx],
+                st.hist[2][ty][tx], st.hist[3][ty][tx], st.hist[4][ty][tx], st.hist[5][ty][tx], has_grain, gid,
+                st.f, ps);
+        }
+        tma_fence_proxy();  // this thread's accesses of stage s precede the TMA copies that refill it
+        __syncthreads();    // stage s and ps are free again
+    }
+}
+
+}  // namespace tmastep
 
 // Descriptors of the batch being stepped, in constant memory: the domain
 // index is uniform across a CTA, so parameter reads are broadcast from the
@@ -422,6 +607,52 @@ cudaError_t flow_steps_t(const StepParams& P, int n, void* sc, void* const fl[2]
     return e;
 }
 
+// ------------------------------------------------ TMA descriptors (host)
+PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
+std::mutex g_encode_mutex;
+
+cudaError_t tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* out)
+{
+    std::lock_guard<std::mutex> lock(g_encode_mutex);
+    if (!g_encode_tiled) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        cudaError_t e =
+            cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        g_encode_tiled = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    *out = g_encode_tiled;
+    return cudaSuccess;
+}
+
+// Tensor map of `planes` planes of an nx x ny grid (row pitch `pitch`,
+// plane stride `plane` elements) with the given box; zero fill outside.
+cudaError_t plane_map(CUtensorMap* tm, CUtensorMapDataType dt, size_t esize, const void* base, const StepParams& P,
+                      int planes, int bx, int by, int bq, CUtensorMapL2promotion promo)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    cudaError_t e = tensor_map_encoder(&enc);
+    if (e != cudaSuccess) return e;
+    const cuuint32_t rank = planes > 1 ? 3 : 2;
+    cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)P.pitch * esize, (cuuint64_t)P.plane * esize};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bq};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, promo,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <bool G, bool W>
+cudaError_t tma_attributes()
+{
+    return cudaFuncSetAttribute(tmastep::k_coupled_step_tma<G, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tmastep::kSmemBytes);
+}
+
 template <class Store>
 cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStream_t s)
 {
@@ -432,7 +663,25 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
     void* dstf = B.fl[1 - B.cf];
     const bool grain = B.grain != nullptr, wfb = n_sub > 1;
     if (B.ev_begin) cudaEventRecord(B.ev_begin, s);
-    if (grain && wfb)
+    const StepMaps* SM = B.maps;
+    if (std::is_same<Store, StoreF32>::value && SM) {
+        const tmastep::Maps& M = SM->m[B.cs][B.cf];
+        const int tiles_x = (P.nx + TX - 1) / TX, ntiles = tiles_x * ((P.ny + TY - 1) / TY);
+        const int ctas = ntiles < SM->ctas ? ntiles : SM->ctas;
+        const size_t sm = tmastep::kSmemBytes;
+        if (grain && wfb)
+            tmastep::k_coupled_step_tma<true, true>
+                <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+        else if (grain)
+            tmastep::k_coupled_step_tma<true, false>
+                <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+        else if (wfb)
+            tmastep::k_coupled_step_tma<false, true>
+                <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+        else
+            tmastep::k_coupled_step_tma<false, false>
+                <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+    } else if (grain && wfb)
         k_coupled_step<Store, true, true><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
     else if (grain)
         k_coupled_step<Store, true, false><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
@@ -501,6 +750,63 @@ int batch_ctas_t()
 }
 
 }  // namespace
+
+bool step_maps_supported(const StepParams& P, int storage)
+{
+    // boxes no larger than the grid: 40 columns and TY + 2 rows of phi
+    return storage == kStoreF32 && P.nx >= tmastep::FW && P.ny >= TY + 2;
+}
+
+cudaError_t create_step_maps(const StepParams& P, int storage, const StepBuffers& B, StepMaps** out)
+{
+    *out = nullptr;
+    if (!step_maps_supported(P, storage)) return cudaErrorNotSupported;
+    StepMaps* M = new StepMaps();
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+        for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
+            tmastep::Maps& m = M->m[c][d];
+            // no promotion on the phi box: its 16-byte halo edges would pull
+            // whole 256-byte lines of the neighbouring tiles
+            const CUtensorMapL2promotion none = CU_TENSOR_MAP_L2_PROMOTION_NONE;
+            const CUtensorMapL2promotion line = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+            e = plane_map(&m.f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.sc[c], P, 15, tmastep::FW, TY + 2, 5, none);
+            if (e == cudaSuccess)
+                e = plane_map(&m.ng, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.sc[c], P, 15, TX, TY, 10, line);
+            if (e == cudaSuccess)
+                e = plane_map(&m.h, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.fl[d], P, 9, TX, TY, 9, line);
+            if (e == cudaSuccess)
+                e = plane_map(&m.hist, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.hist, P, kHist, TX, TY, kHist, line);
+            if (e == cudaSuccess && B.grain)
+                e = plane_map(&m.grain, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, B.grain, P, 1, TX, TY, 1, line);
+        }
+    if (e == cudaSuccess) e = tma_attributes<true, true>();
+    if (e == cudaSuccess) e = tma_attributes<true, false>();
+    if (e == cudaSuccess) e = tma_attributes<false, true>();
+    if (e == cudaSuccess) e = tma_attributes<false, false>();
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete M;
+        return e;
+    }
+    M->ctas = sms * tmastep::kMinBlocks;
+    *out = M;
+    return cudaSuccess;
+}
+
+void destroy_step_maps(StepMaps* m) { delete m; }
+
+cudaError_t step_error(int* flag, bool clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(flag, tmastep::g_step_error, sizeof(int));
+    if (e == cudaSuccess && clear && *flag) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(tmastep::g_step_error, &zero, sizeof(int));
+    }
+    return e;
+}
 
 cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int run, int parity, int ctas,
                               cudaStream_t s)

@@ -1,0 +1,88 @@
+"""The two kernels of the fused coupled step: the TMA-staged persistent kernel
+and the register-staged tiled kernel run the same per-node arithmetic on the
+same inputs, so their states must agree bit for bit, on every wall type,
+ragged grids, grain maps and flow sub-steps.  Also the kernel choice itself."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_2209_01444_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2209_01444_gb300 import build_ext, lbm as L
+
+    build_ext.build()
+    L.load()
+    return L
+
+
+BCS = {
+    "periodic": ("periodic",) * 4,
+    "inflow_outflow_symmetry": ("inflow", "outflow", "symmetry", "symmetry"),
+    "channel_noslip": ("periodic", "periodic", "noslip", "noslip"),
+    "dirichlet": ("dirichlet",) * 4,
+    "mixed": ("inflow", "outflow", "noslip", "symmetry"),
+}
+
+
+def _both(L, p, start, steps):
+    out = []
+    for kernel in ("tma", "tiled"):
+        s = L.Simulation(p)
+        s.set_step_kernel(kernel)
+        assert s.step_kernel == kernel
+        start(s)
+        s.step(steps)
+        s.synchronize()
+        out.append(s.state())
+    return out
+
+
+@pytest.mark.parametrize("shape", [(40, 10), (70, 45), (129, 67)])
+@pytest.mark.parametrize("bcs", sorted(BCS))
+def test_tma_kernel_equals_tiled_kernel(lbm, bcs, shape):
+    """Random fields with four grains; ragged tiles in x and y, and the
+    smallest grid the TMA kernel takes (one box row wide)."""
+    nx, ny = shape
+    p = W.thermosolutal_params(nx, ny, bc=BCS[bcs], u_in=(0.15, 0.02), gbetaT=W.GBETA_T * 5,
+                               gbetaC=W.GBETA_C * 5, theta_ref=-0.5, dir_theta=-0.4)
+    f, orient = W.random_fields(nx, ny, rng_seed=3 + nx)
+    a, b = _both(lbm, p, lambda s: s.init_fields(f, orient), 37)
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("n_sub", [1, 3])
+def test_tma_kernel_equals_tiled_kernel_seeded(lbm, n_sub):
+    """Multi-seed start with a grain map on 256 x 192, and the flow sub-steps
+    (the kernel then also writes the frozen force plane)."""
+    c = W.multi_seed(n=256, count=6, min_spacing=60.0)
+    p = dict(c.params, ny=192, n_sub=n_sub, nu=2.0 * n_sub)
+    seeds = c.seeds[c.seeds[:, 1] < 180]
+    a, b = _both(lbm, p, lambda s: s.init_seeds(seeds, c.U0, c.theta0), 50)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_kernel_choice(lbm):
+    big = W.thermosolutal_params(64, 64)
+    s = lbm.Simulation(big)
+    assert s.step_kernel == "tiled"         # the default
+    s.set_step_kernel("tma")
+    assert s.step_kernel == "tma"
+    s.set_step_kernel("auto")
+    assert s.step_kernel == "tiled"
+    s.set_step_kernel("tma")
+    small = lbm.Simulation(W.thermosolutal_params(39, 64))
+    assert small.step_kernel == "tiled"     # narrower than one f box
+    with pytest.raises(lbm.LBMError):
+        small.set_step_kernel("tma")
+    h = lbm.Simulation(big, "fp16")
+    assert h.step_kernel == "tiled"         # 16-bit storage: tiled kernel
+    with pytest.raises(lbm.LBMError):
+        h.set_step_kernel("tma")
+    assert s.lib.lbm_set_step_kernel(s.h, 7) < 0
+    assert s.step_kernel == "tma"
