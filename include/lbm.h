@@ -191,8 +191,8 @@ LBM_API int lbm_synchronize(lbm_handle* h);
  * bit for bit.  LBM_STEP_KERNEL_TILED: one CTA per 32 x 8 tile, loads staged
  * in registers.  LBM_STEP_KERNEL_TMA: persistent CTAs; each tile's
  * populations, history and grain ids are copied into shared memory by TMA
- * while the previous tile is computed (FP32 storage and grids of at least
- * 40 x 10 nodes only, else LBM_EINVAL).  LBM_STEP_KERNEL_AUTO (the default)
+ * while the previous tile is computed (grids of at least 40 x 10 nodes, 48 x 10
+ * with 16-bit storage, else LBM_EINVAL).  LBM_STEP_KERNEL_AUTO (the default)
  * takes the tiled kernel, the faster of the two on GB300 so far.  Drops the
  * captured step graphs. */
 LBM_API int lbm_set_step_kernel(lbm_handle* h, int kernel);

@@ -401,7 +401,7 @@ int lbm_set_step_kernel(lbm_handle* h, int kernel)
     if (kernel != LBM_STEP_KERNEL_AUTO && kernel != LBM_STEP_KERNEL_TILED && kernel != LBM_STEP_KERNEL_TMA)
         return fail(h, LBM_EINVAL, "unknown step kernel");
     if (kernel == LBM_STEP_KERNEL_TMA && !h->maps)
-        return fail(h, LBM_EINVAL, "the TMA step kernel needs FP32 storage and a grid of at least 40 x 10 nodes");
+        return fail(h, LBM_EINVAL, "the TMA step kernel needs a grid of at least 40 x 10 nodes (48 x 10 with 16-bit storage)");
     h->step_kernel = kernel;
     h->B.maps = kernel == LBM_STEP_KERNEL_TMA ? h->maps : nullptr;
     drop_graphs(h);

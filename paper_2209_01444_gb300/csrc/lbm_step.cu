@@ -33,6 +33,7 @@ namespace lbm {
 // Tensor maps of the TMA-staged fused kernel for one pair of source buffers.
 struct StepTensorMaps {
     CUtensorMap f, ng, h, hist, grain;
+    CUtensorMap f_rest, ng_rest;  // 16-bit storage: the FP32 rest planes of phi and of C, H
 };
 
 struct StepMaps {
@@ -411,6 +412,156 @@ __global__ void __launch_bounds__(TX* TY, kMinBlocks)
     }
 }
 
+
+// 16-bit storage (FP16 or BF16 deviations, FP32 rest planes).  The boxes of a
+// stage hold the raw 16-bit values; each tile decodes its phi populations
+// and halo into an FP32 tile (the layout of the tiled kernel), and each node
+// decodes its own populations from shared memory, with the same conversion
+// and scale as Store16::load.  A stage is 22.7 KB, so four CTAs (32 warps)
+// fit on an SM, as many as the tiled kernel keeps.
+constexpr int FW16 = 48;          // 16-bit phi box row: x0 - 8 .. x0 + 39 (16-byte aligned start)
+constexpr int XO16 = 8;
+constexpr int kMinBlocks16 = 4;
+
+struct __align__(128) Stage16 {
+    uint16_t fm[4][TY + 2][FW16];   // phi moving planes (slots 0..3)
+    float fr[TY + 2][FW];           // phi rest plane, x0 - 4 .. x0 + 35
+    float pad[16];
+    uint16_t ngm[8][TY][TX];        // C and H moving planes (slots 4..11)
+    float ngr[2][TY][TX];           // C and H rest planes
+    uint16_t h[9][TY][TX];
+    float hist[kHist][TY][TX];
+    uint8_t grain[TY][TX];
+};
+static_assert(offsetof(Stage16, fr) % 128 == 0 && offsetof(Stage16, ngm) % 128 == 0, "TMA box alignment");
+static_assert(offsetof(Stage16, ngr) % 128 == 0 && offsetof(Stage16, h) % 128 == 0, "TMA box alignment");
+static_assert(offsetof(Stage16, hist) % 128 == 0 && offsetof(Stage16, grain) % 128 == 0, "TMA box alignment");
+static_assert(sizeof(Stage16) % 128 == 0, "stage alignment");
+
+constexpr uint32_t kBytes16 = 2 * 4 * (TY + 2) * FW16 + 4 * (TY + 2) * FW + 2 * 8 * TY * TX + 4 * 2 * TY * TX +
+                              2 * 9 * TY * TX + 4 * kHist * TY * TX;
+constexpr size_t kSmemBytes16 = kStages * sizeof(Stage16) + 128;
+
+__device__ __forceinline__ void issue16(Stage16& st, uint64_t* bar, const Maps& M, bool grain, int x0, int y0)
+{
+    tma_mbar_expect(bar, kBytes16 + (grain ? kBytesGrain : 0));
+    tma_load_3d(&st.fm[0][0][0], &M.f, x0 - XO16, y0 - 1, 0, bar);
+    tma_load_3d(&st.fr[0][0], &M.f_rest, x0 - XO, y0 - 1, 0, bar);
+    tma_load_3d(&st.ngm[0][0][0], &M.ng, x0, y0, 4, bar);
+    tma_load_3d(&st.ngr[0][0][0], &M.ng_rest, x0, y0, 1, bar);
+    tma_load_3d(&st.h[0][0][0], &M.h, x0, y0, 0, bar);
+    tma_load_3d(&st.hist[0][0][0], &M.hist, x0, y0, 0, bar);
+    if (grain) tma_load_2d(&st.grain[0][0], &M.grain, x0, y0, bar);
+}
+
+template <class H>
+__device__ __forceinline__ H __ushort_as_half_or_bf16(uint16_t raw);
+template <>
+__device__ __forceinline__ __half __ushort_as_half_or_bf16<__half>(uint16_t raw)
+{
+    return __ushort_as_half(raw);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 __ushort_as_half_or_bf16<__nv_bfloat16>(uint16_t raw)
+{
+    return __ushort_as_bfloat16(raw);
+}
+
+template <class Store>
+__device__ __forceinline__ float dec16(uint16_t raw, int q)
+{
+    return Conv<typename Store::T>::to(__ushort_as_half_or_bf16<typename Store::T>(raw)) * Store::inv_scale(q);
+}
+
+template <class Store, bool GRAIN, bool WRITE_FB>
+__global__ void __launch_bounds__(TX* TY, kMinBlocks16)
+    k_coupled_step_tma16(const StepParams P, const __grid_constant__ Maps M, const void* __restrict__ src,
+                         void* __restrict__ dst, void* __restrict__ dstf, float* __restrict__ hist,
+                         const uint8_t* __restrict__ grain, float* __restrict__ fb, int tiles_x, int ntiles)
+{
+    extern __shared__ unsigned char smem_raw[];
+    Stage16* stages = (Stage16*)(smem_raw + ((128u - (tma_smem_u32(smem_raw) & 127u)) & 127u));
+    __shared__ uint64_t full[kStages];
+    __shared__ float fs[5][TY + 2][TX + 2];
+    __shared__ float ps[TY + 2][TX + 2];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const bool has_grain = GRAIN && grain != nullptr;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) tma_mbar_init(&full[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles)
+        issue16(stages[0], &full[0], M, has_grain, (tile % tiles_x) * TX, (tile / tiles_x) * TY);
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const int s = it & 1;
+        const int next = tile + gridDim.x;
+        if (tid == 0 && next < ntiles)
+            issue16(stages[s ^ 1], &full[s ^ 1], M, has_grain, (next % tiles_x) * TX, (next / tiles_x) * TY);
+        const bool ok = tma_mbar_wait(&full[s], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(&g_step_error, 1);
+                tma_mbar_wait(&full[s], (uint32_t)((it >> 1) & 1));
+                if (next < ntiles) tma_mbar_wait(&full[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            return;
+        }
+        Stage16& st = stages[s];
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+
+        // decoded phi populations of the tile and halo (cells outside the
+        // grid: periodic wrap, as the tiled kernel loads them), and phi there
+        const bool edge = x0 == 0 || y0 == 0 || x0 + TX + 1 > P.nx || y0 + TY + 1 > P.ny;
+        for (int e = tid; e < (TX + 2) * (TY + 2); e += TX * TY) {
+            const int hx = e % (TX + 2), hy = e / (TX + 2);
+            float v[5];
+            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+            if (edge && (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny)) {
+                const long long oh = (long long)wrap(gy, P.ny) * P.pitch + wrap(gx, P.nx);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) v[i] = Store::load(src, nullptr, kF + i, oh, P);
+            } else {
+                v[0] = st.fr[hy][hx + XO - 1];
+#pragma unroll
+                for (int i = 1; i < 5; ++i) v[i] = dec16<Store>(st.fm[i - 1][hy][hx + XO16 - 1], kF + i);
+            }
+            float sum = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                fs[i][hy][hx] = v[i];
+                sum += v[i];
+            }
+            ps[hy][hx] = sum;
+        }
+        __syncthreads();
+
+        const int x = x0 + tx, y = y0 + ty;
+        if (x < P.nx && y < P.ny) {
+            float f[5], n[5], g[5], h[9];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) f[i] = fs[i][ty + 1][tx + 1];
+            n[0] = st.ngr[0][ty][tx];
+            g[0] = st.ngr[1][ty][tx];
+#pragma unroll
+            for (int i = 1; i < 5; ++i) {
+                n[i] = dec16<Store>(st.ngm[i - 1][ty][tx], kN + i);
+                g[i] = dec16<Store>(st.ngm[3 + i][ty][tx], kG + i);
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) h[i] = dec16<Store>(st.h[i][ty][tx], kH + i);
+            const uint8_t gid = has_grain ? st.grain[ty][tx] : (uint8_t)0;
+            coupled_node<Store, GRAIN, WRITE_FB, TY, TX + 2, 1>(
+                P, dst, dstf, hist, fb, x, y, tx + 1, ty + 1, f, n, g, h, st.hist[0][ty][tx], st.hist[1][ty][tx],
+                st.hist[2][ty][tx], st.hist[3][ty][tx], st.hist[4][ty][tx], st.hist[5][ty][tx], has_grain, gid,
+                fs, ps);
+        }
+        tma_fence_proxy();
+        __syncthreads();
+    }
+}
+
 }  // namespace tmastep
 
 // Descriptors of the batch being stepped, in constant memory: the domain
@@ -654,6 +805,24 @@ cudaError_t tma_attributes()
 }
 
 template <class Store>
+cudaError_t tma16_attributes()
+{
+    const int b = (int)tmastep::kSmemBytes16;
+    cudaError_t e = cudaFuncSetAttribute(tmastep::k_coupled_step_tma16<Store, true, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tmastep::k_coupled_step_tma16<Store, true, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tmastep::k_coupled_step_tma16<Store, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tmastep::k_coupled_step_tma16<Store, false, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return e;
+}
+
+template <class Store>
 cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStream_t s)
 {
     const dim3 block(TX, TY), grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
@@ -664,24 +833,51 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
     const bool grain = B.grain != nullptr, wfb = n_sub > 1;
     if (B.ev_begin) cudaEventRecord(B.ev_begin, s);
     const StepMaps* SM = B.maps;
-    if (std::is_same<Store, StoreF32>::value && SM) {
-        const tmastep::Maps& M = SM->m[B.cs][B.cf];
-        const int tiles_x = (P.nx + TX - 1) / TX, ntiles = tiles_x * ((P.ny + TY - 1) / TY);
-        const int ctas = ntiles < SM->ctas ? ntiles : SM->ctas;
-        const size_t sm = tmastep::kSmemBytes;
-        if (grain && wfb)
-            tmastep::k_coupled_step_tma<true, true>
-                <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-        else if (grain)
-            tmastep::k_coupled_step_tma<true, false>
-                <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-        else if (wfb)
-            tmastep::k_coupled_step_tma<false, true>
-                <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-        else
-            tmastep::k_coupled_step_tma<false, false>
-                <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-    } else if (grain && wfb)
+    bool staged = false;
+    if constexpr (!std::is_same<Store, StoreF32>::value) {
+        if (SM) {
+            staged = true;
+            const tmastep::Maps& M = SM->m[B.cs][B.cf];
+            const int tiles_x = (P.nx + TX - 1) / TX, ntiles = tiles_x * ((P.ny + TY - 1) / TY);
+            const int ctas = ntiles < SM->ctas ? ntiles : SM->ctas;
+            const size_t sm = tmastep::kSmemBytes16;
+            if (grain && wfb)
+                tmastep::k_coupled_step_tma16<Store, true, true>
+                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+            else if (grain)
+                tmastep::k_coupled_step_tma16<Store, true, false>
+                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+            else if (wfb)
+                tmastep::k_coupled_step_tma16<Store, false, true>
+                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+            else
+                tmastep::k_coupled_step_tma16<Store, false, false>
+                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+        }
+    } else {
+        if (SM) {
+            staged = true;
+            const tmastep::Maps& M = SM->m[B.cs][B.cf];
+            const int tiles_x = (P.nx + TX - 1) / TX, ntiles = tiles_x * ((P.ny + TY - 1) / TY);
+            const int ctas = ntiles < SM->ctas ? ntiles : SM->ctas;
+            const size_t sm = tmastep::kSmemBytes;
+            if (grain && wfb)
+                tmastep::k_coupled_step_tma<true, true>
+                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+            else if (grain)
+                tmastep::k_coupled_step_tma<true, false>
+                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+            else if (wfb)
+                tmastep::k_coupled_step_tma<false, true>
+                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+            else
+                tmastep::k_coupled_step_tma<false, false>
+                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
+        }
+    }
+    if (staged)
+        ;  // the TMA-staged kernel above
+    else if (grain && wfb)
         k_coupled_step<Store, true, true><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
     else if (grain)
         k_coupled_step<Store, true, false><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
@@ -753,8 +949,9 @@ int batch_ctas_t()
 
 bool step_maps_supported(const StepParams& P, int storage)
 {
-    // boxes no larger than the grid: 40 columns and TY + 2 rows of phi
-    return storage == kStoreF32 && P.nx >= tmastep::FW && P.ny >= TY + 2;
+    // boxes no larger than the grid: the phi box (40 FP32 or 48 16-bit
+    // columns, TY + 2 rows)
+    return P.nx >= (storage == kStoreF32 ? tmastep::FW : tmastep::FW16) && P.ny >= TY + 2;
 }
 
 cudaError_t create_step_maps(const StepParams& P, int storage, const StepBuffers& B, StepMaps** out)
@@ -763,9 +960,25 @@ cudaError_t create_step_maps(const StepParams& P, int storage, const StepBuffers
     if (!step_maps_supported(P, storage)) return cudaErrorNotSupported;
     StepMaps* M = new StepMaps();
     cudaError_t e = cudaSuccess;
+    const bool b16 = storage != kStoreF32;
     for (int c = 0; c < 2 && e == cudaSuccess; ++c)
         for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
             tmastep::Maps& m = M->m[c][d];
+            if (b16) {
+                const CUtensorMapL2promotion none = CU_TENSOR_MAP_L2_PROMOTION_NONE;
+                const CUtensorMapL2promotion line = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+                const CUtensorMapDataType u16 = CU_TENSOR_MAP_DATA_TYPE_UINT16, f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+                const void* rest = (const char*)B.sc[c] + 24 * (size_t)P.plane;  // FP32 rest planes
+                e = plane_map(&m.f, u16, 2, B.sc[c], P, 12, tmastep::FW16, TY + 2, 4, none);
+                if (e == cudaSuccess) e = plane_map(&m.f_rest, f32, 4, rest, P, 3, tmastep::FW, TY + 2, 1, none);
+                if (e == cudaSuccess) e = plane_map(&m.ng, u16, 2, B.sc[c], P, 12, TX, TY, 8, line);
+                if (e == cudaSuccess) e = plane_map(&m.ng_rest, f32, 4, rest, P, 3, TX, TY, 2, line);
+                if (e == cudaSuccess) e = plane_map(&m.h, u16, 2, B.fl[d], P, 9, TX, TY, 9, line);
+                if (e == cudaSuccess) e = plane_map(&m.hist, f32, 4, B.hist, P, kHist, TX, TY, kHist, line);
+                if (e == cudaSuccess && B.grain)
+                    e = plane_map(&m.grain, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, B.grain, P, 1, TX, TY, 1, line);
+                continue;
+            }
             // no promotion on the phi box: its 16-byte halo edges would pull
             // whole 256-byte lines of the neighbouring tiles
             const CUtensorMapL2promotion none = CU_TENSOR_MAP_L2_PROMOTION_NONE;
@@ -780,10 +993,16 @@ cudaError_t create_step_maps(const StepParams& P, int storage, const StepBuffers
             if (e == cudaSuccess && B.grain)
                 e = plane_map(&m.grain, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, B.grain, P, 1, TX, TY, 1, line);
         }
-    if (e == cudaSuccess) e = tma_attributes<true, true>();
-    if (e == cudaSuccess) e = tma_attributes<true, false>();
-    if (e == cudaSuccess) e = tma_attributes<false, true>();
-    if (e == cudaSuccess) e = tma_attributes<false, false>();
+    if (!b16) {
+        if (e == cudaSuccess) e = tma_attributes<true, true>();
+        if (e == cudaSuccess) e = tma_attributes<true, false>();
+        if (e == cudaSuccess) e = tma_attributes<false, true>();
+        if (e == cudaSuccess) e = tma_attributes<false, false>();
+    } else if (storage == kStoreF16) {
+        if (e == cudaSuccess) e = tma16_attributes<StoreF16>();
+    } else {
+        if (e == cudaSuccess) e = tma16_attributes<StoreBF16>();
+    }
     int dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -791,7 +1010,7 @@ cudaError_t create_step_maps(const StepParams& P, int storage, const StepBuffers
         delete M;
         return e;
     }
-    M->ctas = sms * tmastep::kMinBlocks;
+    M->ctas = sms * (b16 ? tmastep::kMinBlocks16 : tmastep::kMinBlocks);
     *out = M;
     return cudaSuccess;
 }

@@ -30,10 +30,10 @@ BCS = {
 }
 
 
-def _both(L, p, start, steps):
+def _both(L, p, start, steps, storage="fp32"):
     out = []
     for kernel in ("tma", "tiled"):
-        s = L.Simulation(p)
+        s = L.Simulation(p, storage)
         s.set_step_kernel(kernel)
         assert s.step_kernel == kernel
         start(s)
@@ -43,27 +43,36 @@ def _both(L, p, start, steps):
     return out
 
 
-@pytest.mark.parametrize("shape", [(40, 10), (70, 45), (129, 67)])
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("shape", [(48, 10), (70, 45), (129, 67)])
 @pytest.mark.parametrize("bcs", sorted(BCS))
-def test_tma_kernel_equals_tiled_kernel(lbm, bcs, shape):
+def test_tma_kernel_equals_tiled_kernel(lbm, bcs, shape, storage):
     """Random fields with four grains; ragged tiles in x and y, and the
-    smallest grid the TMA kernel takes (one box row wide)."""
+    smallest grid the 16-bit TMA kernel takes (one phi box wide)."""
     nx, ny = shape
     p = W.thermosolutal_params(nx, ny, bc=BCS[bcs], u_in=(0.15, 0.02), gbetaT=W.GBETA_T * 5,
                                gbetaC=W.GBETA_C * 5, theta_ref=-0.5, dir_theta=-0.4)
     f, orient = W.random_fields(nx, ny, rng_seed=3 + nx)
+    a, b = _both(lbm, p, lambda s: s.init_fields(f, orient), 37, storage)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_tma_kernel_smallest_fp32_grid(lbm):
+    p = W.thermosolutal_params(40, 10, bc=BCS["mixed"], u_in=(0.15, 0.02), gbetaT=W.GBETA_T * 5)
+    f, orient = W.random_fields(40, 10, rng_seed=43)
     a, b = _both(lbm, p, lambda s: s.init_fields(f, orient), 37)
     np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
 @pytest.mark.parametrize("n_sub", [1, 3])
-def test_tma_kernel_equals_tiled_kernel_seeded(lbm, n_sub):
+def test_tma_kernel_equals_tiled_kernel_seeded(lbm, n_sub, storage):
     """Multi-seed start with a grain map on 256 x 192, and the flow sub-steps
     (the kernel then also writes the frozen force plane)."""
     c = W.multi_seed(n=256, count=6, min_spacing=60.0)
     p = dict(c.params, ny=192, n_sub=n_sub, nu=2.0 * n_sub)
     seeds = c.seeds[c.seeds[:, 1] < 180]
-    a, b = _both(lbm, p, lambda s: s.init_seeds(seeds, c.U0, c.theta0), 50)
+    a, b = _both(lbm, p, lambda s: s.init_seeds(seeds, c.U0, c.theta0), 50, storage)
     np.testing.assert_array_equal(a, b)
 
 
@@ -81,8 +90,10 @@ def test_kernel_choice(lbm):
     with pytest.raises(lbm.LBMError):
         small.set_step_kernel("tma")
     h = lbm.Simulation(big, "fp16")
-    assert h.step_kernel == "tiled"         # 16-bit storage: tiled kernel
-    with pytest.raises(lbm.LBMError):
-        h.set_step_kernel("tma")
+    assert h.step_kernel == "tiled"
+    h.set_step_kernel("tma")
+    assert h.step_kernel == "tma"
+    with pytest.raises(lbm.LBMError):       # 16-bit: the phi box is 48 wide
+        lbm.Simulation(W.thermosolutal_params(47, 64), "fp16").set_step_kernel("tma")
     assert s.lib.lbm_set_step_kernel(s.h, 7) < 0
     assert s.step_kernel == "tma"
