@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--step-kernel", choices=["auto", "tiled", "tma"], default="auto",
+                    help="fused-step kernel of the main line (lbm_set_step_kernel)")
     ap.add_argument("--n", type=int, default=4096, help="grid side (default: the 4096^2 workload)")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -457,6 +459,8 @@ def main():
     def timed_run(storage: str, steps: int, warmup: int, clocks: bool):
         sim = lbm.Simulation(case.params, storage, stream=stream)
         sim.init_seeds(case.seeds, case.U0, case.theta0)
+        if storage == args.storage:
+            sim.set_step_kernel(args.step_kernel)
         sim.step(warmup)
         torch.cuda.synchronize()
         sampler = ClockSampler(gpu_index(local)) if clocks else None
@@ -492,7 +496,10 @@ def main():
     bpn = algorithmic_bytes_per_node(args.storage, grains)
     achieved = bpn * nodes / (k_avg_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
-    traffic = recorded_traffic(f"multi_seed_{args.n}_{args.storage}")
+    kernel_kind = sim.step_kernel
+    kernel_name = ("k_coupled_step" if kernel_kind == "tiled"
+                   else ("k_coupled_step_tma" if args.storage == "fp32" else "k_coupled_step_tma16"))
+    traffic = recorded_traffic(f"multi_seed_{args.n}_{args.storage}" + ("" if kernel_kind == "tiled" else "_tma"))
 
     # end to end through the C ABI from pinned host memory: load the initial
     # state, run the steps, read the fields back
@@ -554,9 +561,10 @@ def main():
         "config": {"workload": f"multi_seed_thermosolutal_{args.n}x{args.n}", "nodes": nodes,
                    "seeds": len(case.seeds), "storage": args.storage, "n_sub": case.params["n_sub"],
                    "walls": "periodic x, no-slip y", "l2": "state larger than L2 (no flush)",
+                   "step_kernel": kernel_kind,
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "k_coupled_step", "bytes_per_node": bpn,
+                     "traffic": traffic, "kernel": kernel_name, "bytes_per_node": bpn,
                      "kernel_ms": k_avg_ms, "peak_kind": peak_kind},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(blob) / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps,
