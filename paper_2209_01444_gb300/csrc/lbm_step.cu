@@ -599,7 +599,6 @@ __global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const 
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    const long long plane = P.plane;
     const long long o = (long long)y * P.pitch + x;
     float h[9];
 #pragma unroll
@@ -649,7 +648,6 @@ __device__ __forceinline__ void wall_node(const StepParams& P, void* __restrict_
         yb = which ? P.ny - 1 : 0;
         yf = which ? P.ny - 2 : 1;
     }
-    const long long plane = P.plane;
     const long long ob = (long long)yb * P.pitch + xb, of = (long long)yf * P.pitch + xf;
     float f[5], n[5], g[5], h[9];
 #pragma unroll

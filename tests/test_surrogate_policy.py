@@ -86,3 +86,15 @@ def test_drift_budget_stops_the_network():
     assert sim.source[:8] == ["nn", "nn", "nn", "lb"] * 2
     assert sim.source[8:] == ["lb"] * 12 and sim.steps == 1000
     assert abs(st["drift_charged"] - 0.9) < 1e-12 and st["lb_after_budget"] == 12
+
+
+def test_without_drift_budget_only_window_audits_judge():
+    """drift_budget = inf: the per-window reading of the fallback; the same
+    passing audits as above never stop the network."""
+    sim = FakeSim([True] * 10)
+    sim.err = 0.15
+    st = S.rollout(sim, None, windows=20, K=50, tip_tol=1.0, audit_every=4, backoff=1, cx=0, cy=0,
+                   drift_budget=float("inf"))
+    assert sim.source == ["nn", "nn", "nn", "lb"] * 5
+    assert st["lb_after_budget"] == 0 and st["surrogate"] == 15
+    assert abs(st["drift_charged"] - 0.15 * 15) < 1e-12
