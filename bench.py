@@ -59,7 +59,44 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
     ap.add_argument("--surrogate-train-steps", type=int, default=1500)
     ap.add_argument("--surrogate-windows", type=int, default=400)
+    ap.add_argument("--reference-seconds", type=float, default=90.0,
+                    help="wall-clock target of the --impl reference run (sizes its oracle window)")
     return ap.parse_args()
+
+
+# ------------------------------------------------------------ ranks (N > 1)
+# One process per GPU, each stepping its own replica of the workload: the
+# ranks exchange nothing on the data path, only the timing (a barrier on both
+# sides of the timed region and the maximum time over ranks).
+def dist_env() -> tuple[int, int, int]:
+    """(world size, rank, local rank) from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Maximum of x over the ranks (all-reduce of one FP64 value on `device`)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, nodes_per_rank: int, steps: int, ms: float) -> float:
+    """Lattice updates of all ranks per second (millions): every rank steps
+    its own replica of `nodes_per_rank` nodes, in `ms` (the slowest rank)."""
+    return world * nodes_per_rank * steps / (ms / 1e3) / 1e6
 
 
 def workload(n: int):
@@ -204,8 +241,7 @@ def run_reference(args):
     """The FP64 oracle as it stands, on the host cores: each step is one coupled
     step of a square window of the workload, the window sized so that the
     whole --warmup + --steps run takes about 90 s."""
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    world, rank, _ = dist_env()
     if world > 1 and rank != 0:
         return
     case = workload(args.n)
@@ -226,7 +262,7 @@ def run_reference(args):
     rate = 256 * 256 * 3 / (time.perf_counter() - t)
     del probe
     total = max(args.steps + args.warmup, 1)
-    side = int((90.0 * rate / total) ** 0.5) // 64 * 64
+    side = int((args.reference_seconds * rate / total) ** 0.5) // 64 * 64
     side = max(64, min(1024, args.n, side))
     o = window(side)
     o.step(max(args.warmup, 0))
@@ -433,9 +469,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -447,16 +481,11 @@ def main():
         build_ext.build()
     lbm.load()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    def barrier_():
+        barrier(world)
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(x: float) -> float:
+        return max_over_ranks(x, world, dev)
 
     case = workload(args.n)
     nodes = case.nodes
@@ -472,24 +501,24 @@ def main():
         sampler = ClockSampler(gpu_index(local)) if clocks else None
         if sampler:
             sampler.__enter__()
-        barrier()
+        barrier_()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         sim.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
-        barrier()
+        barrier_()
         if sampler:
             sampler.__exit__(None, None, None)
-        ms = max_over_ranks(e0.elapsed_time(e1))
+        ms = max_ranks(e0.elapsed_time(e1))
         m = sim.metrics(case.seeds[0][0], case.seeds[0][1], case.seeds[0][3], check=False)
         return sim, ms, (sampler.summary() if sampler else None), m
 
     sim, ms, clk, m = timed_run(args.storage, args.steps, max(args.warmup, 3), clocks=True)
     if m["nonfinite"]:
         raise RuntimeError("non-finite state after the timed run")
-    value = world * nodes * args.steps / (ms / 1e3) / 1e6
+    value = whole_job_mlups(world, nodes, args.steps, ms)
 
     # fused-kernel time from CUDA events on the launching stream
     sim.set_profiling(True)
@@ -521,7 +550,7 @@ def main():
     import ctypes as ct
 
     torch.cuda.synchronize()
-    barrier()
+    barrier_()
     t0 = time.perf_counter()
     rc = e2e_sim.lib.lbm_load_state(e2e_sim.h, ct.c_void_p(pinned.data_ptr()), len(blob))
     if rc:
@@ -529,9 +558,9 @@ def main():
     e2e_sim.step(e2e_steps)
     out = e2e_sim.fields(names)
     t1 = time.perf_counter()
-    barrier()
-    e2e_s = max_over_ranks(t1 - t0)
-    e2e_value = world * nodes * e2e_steps / e2e_s / 1e6
+    barrier_()
+    e2e_s = max_ranks(t1 - t0)
+    e2e_value = whole_job_mlups(world, nodes, e2e_steps, e2e_s * 1e3)
     # lbm_get_fields copies the seven FP32 macro planes (pitched rows) to the host
     d2h = len(lbm.FIELDS) * ((case.params["nx"] + 31) // 32 * 32) * case.params["ny"] * 4
     del out
@@ -540,17 +569,17 @@ def main():
     if not args.no_variants and args.storage == "fp32":
         for st in ("fp16", "bf16"):
             vs, vms, _, vm = timed_run(st, args.steps, max(args.warmup, 3), clocks=False)
-            variants[st] = {"value": world * nodes * args.steps / (vms / 1e3) / 1e6, "unit": UNIT,
+            variants[st] = {"value": whole_job_mlups(world, nodes, args.steps, vms), "unit": UNIT,
                             "speedup_vs_fp32": ms / vms, "nonfinite": vm["nonfinite"]}
             del vs
 
     batch = None
     if not args.no_batch:
-        batch = batch_leg(lbm, torch, stream, args.steps, world, max_over_ranks, barrier)
+        batch = batch_leg(lbm, torch, stream, args.steps, world, max_ranks, barrier_)
 
     surrogate = None
     if not args.no_surrogate:
-        surrogate = surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, args.surrogate_train_steps,
+        surrogate = surrogate_leg(lbm, torch, stream, max_ranks, barrier_, args.surrogate_train_steps,
                                   args.surrogate_windows)
 
     if rank != 0:
