@@ -135,3 +135,16 @@ def test_flow_arms_and_tip_radii(lbm, pure):
     for r in (vert, down):
         assert r[-1] >= 1.15 * r.min() and r.argmin() < len(r) - 1
     assert up[-1] < vert[-1] < down[-1]
+
+
+def test_planar_front_on_the_gpu_follows_the_stefan_solution(lbm):
+    """The closed-form pin of the oracle's anti-trapping current, run through
+    the CUDA path: the 1-D isothermal front against the one-sided Stefan
+    solution and the solid it leaves at the equilibrium composition."""
+    from test_oracle_pins import planar_solutal_front
+
+    ((a, pa), (b, pb)), U = planar_solutal_front(lambda p: lbm.Simulation(p), (5000, 20000))
+    print(f"front {a:.2f} / {b:.2f} lattice units, Stefan {pa:.2f} / {pb:.2f}")
+    assert abs(a - pa) <= 0.03 * (pa - 20.0) and abs(b - pb) <= 0.02 * (pb - 20.0)
+    xs = np.arange(int(a) + 5, int(b) - 15)
+    assert np.abs(U[xs]).max() <= 0.01
