@@ -448,6 +448,16 @@ LBM_API int lbm_unet_get_params(lbm_unet* u, float* host);
 /* Gradients of the loss from the last lbm_unet_backward / train_step. */
 LBM_API int lbm_unet_get_grads(lbm_unet* u, float* host);
 LBM_API int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_in, const float* std_out);
+/* Writes the FP32 parameters and the normalisation to a file (magic
+ * "LBMUNET1", int32 levels, base, fields, 0, int64 parameter count, FP32 mean,
+ * std_in, std_out and parameters, little-endian); synchronous.  The Adam
+ * moments are not saved. */
+LBM_API int lbm_unet_save(lbm_unet* u, const char* path);
+/* Reads such a file into u, whose levels, base and fields must match (batch,
+ * height and width may differ: train on patches, infer on whole fields);
+ * LBM_EINVAL with the reason in lbm_unet_last_error for a missing, truncated,
+ * mismatched or non-finite file.  Resets the Adam moments. */
+LBM_API int lbm_unet_load(lbm_unet* u, const char* path);
 /* Prediction y (physical units, may be NULL) for the fields x. */
 LBM_API int lbm_unet_forward(lbm_unet* u, const float* x, float* y);
 /* Forward, loss against `target` and the gradients of every parameter. */

@@ -22,6 +22,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -85,6 +88,7 @@ struct lbm_unet {
     bf16* wb = nullptr;
     int t = 0;
     float *mean = nullptr, *inv_std = nullptr, *inv_out = nullptr;
+    std::vector<float> norm_h;  // host copy: mean, std_in, std_out (F each)
     bf16* x0 = nullptr;
     float *Y = nullptr, *T = nullptr, *G = nullptr;
     float *loss = nullptr, *part = nullptr;
@@ -570,11 +574,74 @@ int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_in, const
         is[c] = 1.0f / std_in[c];
         io[c] = 1.0f / std_out[c];
     }
+    u->norm_h.assign(3 * (size_t)u->F, 0.0f);
+    for (int c = 0; c < u->F; ++c) {
+        u->norm_h[c] = mean[c];
+        u->norm_h[u->F + c] = std_in[c];
+        u->norm_h[2 * u->F + c] = std_out[c];
+    }
     UN_CHECK(u, cudaMemcpyAsync(u->mean, mu, sizeof mu, cudaMemcpyHostToDevice, u->s));
     UN_CHECK(u, cudaMemcpyAsync(u->inv_std, is, sizeof is, cudaMemcpyHostToDevice, u->s));
     UN_CHECK(u, cudaMemcpyAsync(u->inv_out, io, sizeof io, cudaMemcpyHostToDevice, u->s));
     UN_CHECK(u, cudaStreamSynchronize(u->s));
     return LBM_OK;
+}
+
+// Weight file: "LBMUNET1", int32 levels, base, fields, 0, int64 parameter
+// count, FP32 mean, std_in, std_out (fields each), FP32 parameters; all
+// little-endian, as the hosts this builds for store them.
+static const char kUnetMagic[8] = {'L', 'B', 'M', 'U', 'N', 'E', 'T', '1'};
+
+int lbm_unet_save(lbm_unet* u, const char* path)
+{
+    if (!u || !path) return LBM_EINVAL;
+    std::vector<float> p((size_t)lbm_unet_param_count(u));
+    int rc = lbm_unet_get_params(u, p.data());
+    if (rc) return rc;
+    std::vector<float> norm = u->norm_h;
+    if (norm.empty()) {  // never set: mean 0, scales 1
+        norm.assign(3 * (size_t)u->F, 1.0f);
+        std::fill(norm.begin(), norm.begin() + u->F, 0.0f);
+    }
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(u, LBM_EINVAL, std::string("cannot open ") + path + " for writing");
+    const int32_t shape[4] = {u->L, u->base, u->F, 0};
+    const int64_t n = (int64_t)p.size();
+    bool ok = std::fwrite(kUnetMagic, 1, 8, f) == 8 && std::fwrite(shape, sizeof shape, 1, f) == 1 &&
+              std::fwrite(&n, sizeof n, 1, f) == 1 && std::fwrite(norm.data(), sizeof(float), norm.size(), f) == norm.size() &&
+              std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? LBM_OK : fail(u, LBM_EINVAL, std::string("write to ") + path + " failed");
+}
+
+int lbm_unet_load(lbm_unet* u, const char* path)
+{
+    if (!u || !path) return LBM_EINVAL;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(u, LBM_EINVAL, std::string("cannot open ") + path);
+    char magic[8];
+    int32_t shape[4];
+    int64_t n = 0;
+    std::vector<float> norm(3 * (size_t)u->F), p((size_t)lbm_unet_param_count(u));
+    std::string why;
+    if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kUnetMagic, 8) != 0)
+        why = "not a network weight file";
+    else if (std::fread(shape, sizeof shape, 1, f) != 1 || std::fread(&n, sizeof n, 1, f) != 1)
+        why = "truncated header";
+    else if (shape[0] != u->L || shape[1] != u->base || shape[2] != u->F || n != (int64_t)p.size())
+        why = "the file holds a network of another shape";
+    else if (std::fread(norm.data(), sizeof(float), norm.size(), f) != norm.size() ||
+             std::fread(p.data(), sizeof(float), p.size(), f) != p.size())
+        why = "truncated weights";
+    else if (std::fgetc(f) != EOF)
+        why = "trailing bytes after the weights";
+    std::fclose(f);
+    if (!why.empty()) return fail(u, LBM_EINVAL, std::string(path) + ": " + why);
+    for (float x : p)
+        if (!std::isfinite(x)) return fail(u, LBM_EINVAL, std::string(path) + ": non-finite weight");
+    int rc = lbm_unet_set_params(u, p.data());
+    if (rc) return rc;
+    return lbm_unet_set_norm(u, norm.data(), norm.data() + u->F, norm.data() + 2 * u->F);
 }
 
 int lbm_unet_forward(lbm_unet* u, const float* x, float* y)

@@ -135,6 +135,8 @@ SIGNATURES = {
     "lbm_unet_get_params": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_get_grads": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_set_norm": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_save": (ct.c_int, [ct.c_void_p, ct.c_char_p]),
+    "lbm_unet_load": (ct.c_int, [ct.c_void_p, ct.c_char_p]),
     "lbm_unet_forward": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "lbm_unet_backward": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "lbm_unet_adam": (ct.c_int, [ct.c_void_p, ct.c_float, ct.c_float, ct.c_float, ct.c_float]),

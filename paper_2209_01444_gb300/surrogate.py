@@ -8,6 +8,7 @@ used for device memory and streams only.
 from __future__ import annotations
 
 import ctypes as ct
+import os
 import math
 
 import numpy as np
@@ -125,6 +126,15 @@ class UNet:
         self._check(self.lib.lbm_unet_set_norm(self.h, m.ctypes.data_as(ct.c_void_p), si.ctypes.data_as(ct.c_void_p),
                                                so.ctypes.data_as(ct.c_void_p)))
         self.norm = (m, si, so)
+
+    def save(self, path: str) -> None:
+        """Parameters and normalisation to a weight file (lbm_unet_save)."""
+        self._check(self.lib.lbm_unet_save(self.h, os.fsencode(path)))
+
+    def load(self, path: str) -> None:
+        """Parameters and normalisation from a weight file of a network of the
+        same levels, base and fields (lbm_unet_load)."""
+        self._check(self.lib.lbm_unet_load(self.h, os.fsencode(path)))
 
     def forward(self, x, y=None):
         """Prediction in physical units (into `y` when given)."""

@@ -271,3 +271,42 @@ def test_batch_slots_are_independent(env):
     y = net.forward(_dev(torch, x)).cpu().numpy()
     assert np.array_equal(y[0], y[2])
     assert not np.array_equal(y[0], y[1])
+
+
+def test_weight_file_round_trip_across_sizes(env, tmp_path):
+    """A network trained a few steps on 2 x 32^2 is saved and loaded into one
+    sized 1 x 64^2: parameters and normalisation come back exactly, and the
+    loaded network predicts the same fields as one given them directly.
+    Files of another shape, truncated or not weight files are refused."""
+    torch, lib, S = env
+    net = S.UNet(2, 32, 32)
+    net.set_params(_params(21, out_scale=0.01))
+    mean, sin, sout = np.array([0.1, 0.2, -0.3, 0.0, 0.01]), np.array([1, 2, 3, 4, 5.0]), np.array([.5, .25, 2, 1, 3.0])
+    net.set_norm(mean, sin, sout)
+    x, _ = _inputs(5, 2, 32, 32)
+    xd = _dev(torch, x)
+    for _ in range(3):
+        net.train_step(xd, xd * 1.01, 1e-3)
+    path = str(tmp_path / "net.lbmunet")
+    net.save(path)
+    trained = net.params()
+    big = S.UNet(1, 64, 64)
+    big.load(path)
+    got = big.params()
+    for k in trained:
+        np.testing.assert_array_equal(got[k], trained[k])
+    ref = S.UNet(1, 64, 64)
+    ref.set_params(trained)
+    ref.set_norm(mean, sin, sout)
+    xb = _dev(torch, _inputs(6, 1, 64, 64)[0])
+    assert torch.equal(big.forward(xb), ref.forward(xb))
+    other = S.UNet(1, 32, 32, levels=4)
+    with pytest.raises(Exception, match="another shape"):
+        other.load(path)
+    raw = open(path, "rb").read()
+    open(path, "wb").write(raw[:-10])
+    with pytest.raises(Exception, match="truncated"):
+        big.load(path)
+    open(path, "wb").write(b"not weights" * 10)
+    with pytest.raises(Exception, match="not a network weight file"):
+        big.load(path)
