@@ -212,6 +212,50 @@ def gpu_index(local_rank: int) -> int:
     return local_rank
 
 
+ACCURACY_FIELDS = ("phi", "C", "theta", "ux", "uy")
+
+
+def field_errors(got: dict, ref: dict, theta_scale: float) -> dict:
+    """max|X - X_ref| / max(max|X_ref|, floor) per field, the floors of the
+    parity tests (phi, C: 1; theta: |theta0|; velocities: 1e-6)."""
+    floor = {"phi": 1.0, "C": 1.0, "theta": theta_scale, "ux": 1e-6, "uy": 1e-6}
+    return {k: float(np.abs(got[k] - ref[k]).max() / max(float(np.abs(ref[k]).max()), floor[k])) for k in ref}
+
+
+def drift(sim, m_end) -> dict:
+    """Relative change of the solute and enthalpy sums over the run (the
+    walls of the workload are closed to both)."""
+    c0, h0 = sim.sums0
+    return {"sum_C_rel_drift": (m_end["sum_C"] - c0) / abs(c0), "sum_H_rel_drift": (m_end["sum_H"] - h0) / abs(h0)}
+
+
+def cpu_oracle_one_core(case, side: int = 256, target_s: float = 3.0) -> dict:
+    """The same oracle on one host thread (a subprocess started with
+    OMP_NUM_THREADS=1), on a side x side window for about target_s seconds."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import bench
+from oracle import oracle as O
+case = bench.workload({case.params["nx"]})
+p = dict(case.params); p["nx"] = p["ny"] = {side}; p["bc"] = ("periodic",) * 4
+o = O.Oracle(p)
+N = case.params["nx"]; x0 = (N - {side}) // 2
+o.init_seeds_window(case.seeds, case.U0, case.theta0, x0, x0, N, case.params["ny"], True, False)
+t = time.perf_counter(); o.step(2); per = (time.perf_counter() - t) / 2
+n = int(max(3, min(400, {target_s} / max(per, 1e-6))))
+t = time.perf_counter(); o.step(n); dt = time.perf_counter() - t
+print(json.dumps({{"n": n, "dt": dt}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": side * side * d["n"] / d["dt"] / 1e6, "unit": UNIT, "cores": 1,
+            "sample": f"{side}x{side} window, {d['n']} coupled steps, FP64, {d['dt']:.1f} s"}
+
+
 def cpu_oracle_sample(case, target_s: float = 15.0, side: int = 1024, max_steps: int = 400):
     """The FP64 oracle on a side x side window of the workload (seeded in the
     coordinates of the full grid), run for about target_s seconds."""
@@ -494,6 +538,8 @@ def main():
     def timed_run(storage: str, steps: int, warmup: int, clocks: bool):
         sim = lbm.Simulation(case.params, storage, stream=stream)
         sim.init_seeds(case.seeds, case.U0, case.theta0)
+        sums0 = sim.metrics(case.seeds[0][0], case.seeds[0][1], case.seeds[0][3], check=False)
+        sim.sums0 = (sums0["sum_C"], sums0["sum_H"])
         if storage == args.storage:
             sim.set_step_kernel(args.step_kernel)
         sim.step(warmup)
@@ -518,6 +564,8 @@ def main():
     sim, ms, clk, m = timed_run(args.storage, args.steps, max(args.warmup, 3), clocks=True)
     if m["nonfinite"]:
         raise RuntimeError("non-finite state after the timed run")
+    conservation = drift(sim, m)
+    ref_fields = sim.fields(ACCURACY_FIELDS) if not args.no_variants and args.storage == "fp32" else None
     value = whole_job_mlups(world, nodes, args.steps, ms)
 
     # fused-kernel time from CUDA events on the launching stream
@@ -571,7 +619,12 @@ def main():
             vs, vms, _, vm = timed_run(st, args.steps, max(args.warmup, 3), clocks=False)
             variants[st] = {"value": whole_job_mlups(world, nodes, args.steps, vms), "unit": UNIT,
                             "speedup_vs_fp32": ms / vms, "nonfinite": vm["nonfinite"]}
+            if not vm["nonfinite"]:
+                variants[st]["field_error_vs_fp32"] = field_errors(vs.fields(ACCURACY_FIELDS), ref_fields,
+                                                                   abs(case.theta0))
+                variants[st]["conservation"] = drift(vs, vm)
             del vs
+    del ref_fields
 
     batch = None
     if not args.no_batch:
@@ -587,6 +640,7 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(case)
+        cpu["one_core"] = cpu_oracle_one_core(case)
     wall_launches = (0 if case.params["bc"][2] == "periodic" else 1) + (0 if case.params["bc"][0] == "periodic" else 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -605,6 +659,7 @@ def main():
                 "d2h_bytes_per_step": d2h / e2e_steps,
                 "what": "lbm_load_state from pinned host memory, lbm_step(steps), lbm_get_fields of 5 fields"},
         "gpu_launches": args.steps * (1 + wall_launches),
+        "conservation": conservation,
         "clocks": clk,
         "cpu_baseline": cpu,
         "variants": variants,
