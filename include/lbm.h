@@ -126,7 +126,10 @@ typedef struct lbm_seed {
     double x, y, R, orient;
 } lbm_seed;
 
-/* Reductions of lbm_get_metrics, accumulated in FP64 on the device. */
+/* Reductions of lbm_get_metrics, on the device: each thread sums the
+ * deviations of 16 nodes from the reference state in FP32 and adds the
+ * reference terms in FP64; threads and blocks combine in FP64, in a fixed
+ * order (the same result on every call). */
 typedef struct lbm_metrics {
     double tip[3];         /* tip distance (lattice units) from the given centre
                               along the grain's +x, -x and +y axes: phi sampled

@@ -1,4 +1,4 @@
-// Initialisation, field extraction, state codecs and FP64 reductions.
+// Initialisation, field extraction, state codecs and the metrics reductions.
 #include <cuda_runtime.h>
 #include <math.h>
 

@@ -108,7 +108,7 @@ cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, cons
                           cudaStream_t s);
 cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, cudaStream_t s);
 
-// FP64 reductions: out[0..6] = solid fraction sum, sum C, sum H, sum h,
+// Metrics reductions (FP64 results): out[0..6] = solid fraction sum, sum C, sum H, sum h,
 // max |u| (flow lattice units), non-finite count, sum phi; then out[7..9] =
 // the three tip distances.  `partials` must hold reduce_partials_size()
 // doubles.

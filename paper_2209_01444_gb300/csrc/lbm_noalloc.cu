@@ -1,4 +1,4 @@
-// lbm_reduce_noalloc: the FP64 reductions of lbm_get_metrics for callers that
+// lbm_reduce_noalloc: the reductions of lbm_get_metrics for callers that
 // cannot allocate device memory.  The only scratch, one row of partial sums
 // per block, is a file-scope device array that every GPU loading the library
 // holds until the process exits; nothing here calls cudaMalloc or cudaFree.
