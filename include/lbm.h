@@ -190,6 +190,16 @@ LBM_API int lbm_step(lbm_handle* h, int nsteps);
  * (the flag is per process: any handle's kernel may have raised it). */
 LBM_API int lbm_synchronize(lbm_handle* h);
 
+/* Size limit, in bytes, of the device buffer that whole-grid transfers
+ * (lbm_init_seeds, lbm_init_fields, lbm_get_fields, lbm_get_state,
+ * lbm_get_state_region, lbm_set_state) work through, one band of rows at a
+ * time (default 64 MiB; at least one row of the widest transfer, 96 bytes per
+ * node, is always used).  The buffer is allocated on the first such call, so
+ * a handle holds only its state (about 217 bytes per node in FP32, 133 in
+ * FP16/BF16, plus O(nx + ny) tables) and the grid can fill most of the
+ * device.  Results do not depend on the band size. */
+LBM_API int lbm_set_io_chunk(lbm_handle* h, size_t bytes);
+
 /* Choose the kernel of the fused coupled step; both compute the same update
  * bit for bit.  LBM_STEP_KERNEL_TILED: one CTA per 32 x 8 tile, loads staged
  * in registers.  LBM_STEP_KERNEL_TMA: persistent CTAs; each tile's

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -43,8 +44,9 @@ struct lbm_handle {
     bool uniform = true;               // one orientation everywhere
     double* d_partials = nullptr;
     double* d_red = nullptr;
-    double* d_f64 = nullptr;           // 6 FP64 planes (initialisation)
-    float* d_f32 = nullptr;            // kPlanes FP32 planes (extraction)
+    void* scratch = nullptr;           // band buffer of the whole-grid transfers (allocated on first use)
+    size_t scratch_bytes = 0;
+    size_t io_chunk = (size_t)64 << 20;  // its size limit (lbm_set_io_chunk)
     double* d_seeds = nullptr;
     long long steps = 0;
     bool initialised = false;
@@ -223,14 +225,77 @@ int set_grains(lbm_handle* h, const std::vector<double>& orient_of_id, const std
     return LBM_OK;
 }
 
-int finish_init(lbm_handle* h)
+// Rows per band for a transfer that keeps `node_bytes` per node in the band
+// buffer, which is allocated (or grown) here: at most io_chunk bytes, at
+// least one row of the widest transfer (96 bytes per node), never more than
+// the whole grid needs.
+int band_rows(lbm_handle* h, size_t node_bytes, int* rows)
+{
+    const size_t row_max = (size_t)h->P.pitch * 96;
+    size_t want = std::min(h->io_chunk, row_max * (size_t)h->P.ny);
+    want = std::max(want, row_max);
+    if (h->scratch_bytes != want) {
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (h->scratch) cudaFree(h->scratch);
+        h->scratch = nullptr;
+        h->scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&h->scratch, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, LBM_ENOMEM, std::string("band buffer: ") + cudaGetErrorString(e));
+        }
+        h->scratch_bytes = want;
+    }
+    const size_t r = h->scratch_bytes / ((size_t)h->P.pitch * node_bytes);
+    *rows = (int)std::max<size_t>(1, std::min<size_t>(r, (size_t)h->P.ny));
+    return LBM_OK;
+}
+
+// Decoded state of the rows [y0, y0 + hgt) in bands: deliver(y, r, pops,
+// hist) receives each band's 24 FP32 population-deviation planes and 6
+// history planes in host memory (r * pitch values each).
+template <class Deliver>
+int decode_rows(lbm_handle* h, int y0, int hgt, Deliver deliver)
+{
+    int rows, rc;
+    if ((rc = band_rows(h, lbm::kPlanes * sizeof(float), &rows))) return rc;
+    const size_t pitch = (size_t)h->P.pitch, plane = (size_t)h->P.plane;
+    float* dev = (float*)h->scratch;
+    std::vector<float> pops((size_t)rows * pitch * lbm::kPlanes), hist((size_t)rows * pitch * lbm::kHist);
+    for (int y = y0; y < y0 + hgt; y += rows) {
+        const int r = std::min(rows, y0 + hgt - y);
+        const size_t band = (size_t)r * pitch;
+        LBM_CUDA(h, lbm::launch_decode(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], dev, y, r, h->stream));
+        LBM_CUDA(h, cudaMemcpyAsync(pops.data(), dev, band * lbm::kPlanes * sizeof(float), cudaMemcpyDeviceToHost,
+                                    h->stream));
+        for (int q = 0; q < lbm::kHist; ++q)
+            LBM_CUDA(h, cudaMemcpyAsync(hist.data() + q * band, h->B.hist + q * plane + (size_t)y * pitch,
+                                        band * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        if ((rc = deliver(y, r, pops.data(), hist.data()))) return rc;
+    }
+    return LBM_OK;
+}
+
+// Initial state, band by band: fill(y0, rows, fields) writes the band's six
+// FP64 macro planes (lattice units) into `fields`, then the equilibrium
+// populations and the history of those rows follow from them.
+template <class Fill>
+int init_bands(lbm_handle* h, Fill fill)
 {
     h->B.cs = 0;
     h->B.cf = 0;
     h->steps = 0;
     drop_graphs(h);
-    LBM_CUDA(h, lbm::launch_init_from_fields(h->P, h->storage, h->d_f64, h->B.sc[0], h->B.fl[0], h->B.hist,
-                                             h->stream));
+    int rows, rc;
+    if ((rc = band_rows(h, 6 * sizeof(double), &rows))) return rc;
+    double* fields = (double*)h->scratch;
+    for (int y0 = 0; y0 < h->P.ny; y0 += rows) {
+        const int r = std::min(rows, h->P.ny - y0);
+        if ((rc = fill(y0, r, fields))) return rc;
+        LBM_CUDA(h, lbm::launch_init_from_fields(h->P, h->storage, fields, h->B.sc[0], h->B.fl[0], h->B.hist, y0, r,
+                                                 h->stream));
+    }
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->initialised = true;
     return LBM_OK;
@@ -371,8 +436,6 @@ int lbm_create(const lbm_params* p, lbm_handle** out)
     alloc((void**)&h->grain_cs, 256 * sizeof(float2));
     alloc((void**)&h->d_partials, lbm::reduce_partials_size(h->P) * sizeof(double));
     alloc((void**)&h->d_red, 16 * sizeof(double));
-    alloc((void**)&h->d_f64, (size_t)h->P.plane * 6 * sizeof(double));
-    alloc((void**)&h->d_f32, fp * lbm::kPlanes);
     alloc((void**)&h->d_seeds, 256 * 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(h->grain, 0, (size_t)h->P.plane);
     if (e != cudaSuccess) {
@@ -392,6 +455,14 @@ int lbm_create(const lbm_params* p, lbm_handle** out)
     }
     h->B.maps = nullptr;  // LBM_STEP_KERNEL_AUTO: the tiled kernel
     *out = h;
+    return LBM_OK;
+}
+
+int lbm_set_io_chunk(lbm_handle* h, size_t bytes)
+{
+    if (!h) return LBM_EINVAL;
+    if (bytes < 1) return fail(h, LBM_EINVAL, "io chunk of 0 bytes");
+    h->io_chunk = bytes;
     return LBM_OK;
 }
 
@@ -421,7 +492,7 @@ void lbm_destroy(lbm_handle* h)
     lbm::destroy_step_maps(h->maps);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     void* ptrs[] = {h->B.sc[0], h->B.sc[1], h->B.fl[0], h->B.fl[1], h->B.hist, h->B.fb, h->grain,
-                    h->grain_cs, h->d_partials, h->d_red, h->d_f64, h->d_f32, h->d_seeds,
+                    h->grain_cs, h->d_partials, h->d_red, h->scratch, h->d_seeds,
                     h->snap_sc[0], h->snap_sc[1], h->snap_fl[0], h->snap_fl[1], h->snap_hist[0], h->snap_hist[1],
                     h->sur_x, h->sur_y, h->sur_l, h->d_mis, h->d_ring, h->flow_phi, h->flow_fy};
     for (void* q : ptrs)
@@ -452,11 +523,13 @@ int lbm_init_seeds(lbm_handle* h, const lbm_seed* seeds, int n, double U0, doubl
             return fail(h, LBM_EINVAL, "non-finite seed");
     }
     LBM_CUDA(h, cudaMemcpyAsync(h->d_seeds, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    LBM_CUDA(h, lbm::launch_seed_fields(h->P, h->d_seeds, n, U0, theta0, h->prm.W0 / h->prm.dx, h->d_f64, h->grain,
-                                        h->stream));
     int rc = set_grains(h, orient, nullptr);
     if (rc) return rc;
-    return finish_init(h);
+    const double W = h->prm.W0 / h->prm.dx;
+    return init_bands(h, [&](int y0, int r, double* fields) {
+        LBM_CUDA(h, lbm::launch_seed_fields(h->P, h->d_seeds, n, U0, theta0, W, fields, h->grain, y0, r, h->stream));
+        return LBM_OK;
+    });
 }
 
 int lbm_init_fields(lbm_handle* h, const double* fields, const double* orient)
@@ -492,11 +565,16 @@ int lbm_init_fields(lbm_handle* h, const double* fields, const double* orient)
     } else {
         table.push_back(0.0);
     }
-    LBM_CUDA(h, cudaMemcpyAsync(h->d_f64, f64.data(), f64.size() * sizeof(double), cudaMemcpyHostToDevice,
-                                h->stream));
     int rc = set_grains(h, table, &ids);
     if (rc) return rc;
-    return finish_init(h);
+    const size_t plane = (size_t)h->P.plane;
+    return init_bands(h, [&](int y0, int r, double* fields) {
+        const size_t band = (size_t)r * pitch;
+        for (int q = 0; q < 6; ++q)
+            LBM_CUDA(h, cudaMemcpyAsync(fields + q * band, f64.data() + q * plane + (size_t)y0 * pitch,
+                                        band * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        return LBM_OK;
+    });
 }
 
 namespace {
@@ -666,23 +744,30 @@ int lbm_get_fields(lbm_handle* h, unsigned mask, double* out)
     if (rc) return rc;
     if (!out) return fail(h, LBM_EINVAL, "out is NULL");
     if (mask >> LBM_NUM_FIELDS) return fail(h, LBM_EINVAL, "unknown field bit");
-    LBM_CUDA(h, lbm::launch_macros(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->d_f32, h->stream));
-    std::vector<float> host((size_t)h->P.plane * LBM_NUM_FIELDS);
-    LBM_CUDA(h, cudaMemcpyAsync(host.data(), h->d_f32, host.size() * sizeof(float), cudaMemcpyDeviceToHost,
-                                h->stream));
-    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     const int nx = h->P.nx, ny = h->P.ny, pitch = h->P.pitch;
     // device planes hold phi + 1, C - 1, U, theta - theta_ref, ux, uy, p
     const double scale[LBM_NUM_FIELDS] = {1, 1, 1, 1, 1.0 / h->vf, 1.0 / h->vf, h->pscale};
     const double offset[LBM_NUM_FIELDS] = {-1.0, 1.0, 0, (double)h->P.theta_ref, 0, 0, 0};
-    size_t k = 0;
-    for (int q = 0; q < LBM_NUM_FIELDS; ++q) {
-        if (!(mask & (1u << q))) continue;
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x)
-                out[k * (size_t)nx * ny + (size_t)y * nx + x] =
-                    (double)host[(size_t)q * h->P.plane + (size_t)y * pitch + x] * scale[q] + offset[q];
-        ++k;
+    int rows;
+    if ((rc = band_rows(h, LBM_NUM_FIELDS * sizeof(float), &rows))) return rc;
+    float* dev = (float*)h->scratch;
+    std::vector<float> host((size_t)rows * pitch * LBM_NUM_FIELDS);
+    for (int y0 = 0; y0 < ny; y0 += rows) {
+        const int r = std::min(rows, ny - y0);
+        const size_t band = (size_t)r * pitch;
+        LBM_CUDA(h, lbm::launch_macros(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], dev, y0, r, h->stream));
+        LBM_CUDA(h, cudaMemcpyAsync(host.data(), dev, band * LBM_NUM_FIELDS * sizeof(float), cudaMemcpyDeviceToHost,
+                                    h->stream));
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        size_t k = 0;
+        for (int q = 0; q < LBM_NUM_FIELDS; ++q) {
+            if (!(mask & (1u << q))) continue;
+            for (int y = 0; y < r; ++y)
+                for (int x = 0; x < nx; ++x)
+                    out[k * (size_t)nx * ny + (size_t)(y0 + y) * nx + x] =
+                        (double)host[(size_t)q * band + (size_t)y * pitch + x] * scale[q] + offset[q];
+            ++k;
+        }
     }
     return LBM_OK;
 }
@@ -692,22 +777,20 @@ int lbm_get_state(lbm_handle* h, double* out)
     int rc = ensure_initialised(h);
     if (rc) return rc;
     if (!out) return fail(h, LBM_EINVAL, "out is NULL");
-    const size_t plane = (size_t)h->P.plane;
-    LBM_CUDA(h, lbm::launch_decode(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->d_f32, h->stream));
-    std::vector<float> host(plane * LBM_STATE_PLANES);
-    LBM_CUDA(h, cudaMemcpyAsync(host.data(), h->d_f32, plane * lbm::kPlanes * sizeof(float), cudaMemcpyDeviceToHost,
-                                h->stream));
-    LBM_CUDA(h, cudaMemcpyAsync(host.data() + plane * lbm::kPlanes, h->B.hist, plane * lbm::kHist * sizeof(float),
-                                cudaMemcpyDeviceToHost, h->stream));
-    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-    const int nx = h->P.nx, ny = h->P.ny, pitch = h->P.pitch;
-    for (int q = 0; q < LBM_STATE_PLANES; ++q) {
-        const double r = q < lbm::kPlanes ? h->ref[q] : 0.0;
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x)
-                out[(size_t)q * nx * ny + (size_t)y * nx + x] = r + (double)host[q * plane + (size_t)y * pitch + x];
-    }
-    return LBM_OK;
+    const int nx = h->P.nx, ny = h->P.ny;
+    const size_t pitch = (size_t)h->P.pitch;
+    return decode_rows(h, 0, ny, [&](int y0, int r, const float* pops, const float* hist) {
+        const size_t band = (size_t)r * pitch;
+        for (int q = 0; q < LBM_STATE_PLANES; ++q) {
+            const bool pop = q < lbm::kPlanes;
+            const double ref = pop ? h->ref[q] : 0.0;
+            const float* src = pop ? pops + q * band : hist + (q - lbm::kPlanes) * band;
+            for (int y = 0; y < r; ++y)
+                for (int x = 0; x < nx; ++x)
+                    out[(size_t)q * nx * ny + (size_t)(y0 + y) * nx + x] = ref + (double)src[(size_t)y * pitch + x];
+        }
+        return LBM_OK;
+    });
 }
 
 int lbm_get_state_region(lbm_handle* h, int x0, int y0, int w, int hgt, double* out)
@@ -717,22 +800,19 @@ int lbm_get_state_region(lbm_handle* h, int x0, int y0, int w, int hgt, double* 
     if (!out) return fail(h, LBM_EINVAL, "out is NULL");
     if (w < 1 || hgt < 1 || x0 < 0 || y0 < 0 || x0 + w > h->P.nx || y0 + hgt > h->P.ny)
         return fail(h, LBM_EINVAL, "window outside the grid");
-    const size_t plane = (size_t)h->P.plane, pitch = (size_t)h->P.pitch;
-    LBM_CUDA(h, lbm::launch_decode(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->d_f32, h->stream));
-    std::vector<float> host((size_t)w * hgt * LBM_STATE_PLANES);
-    for (int q = 0; q < LBM_STATE_PLANES; ++q) {
-        const float* src = q < lbm::kPlanes ? h->d_f32 + q * plane : h->B.hist + (q - lbm::kPlanes) * plane;
-        LBM_CUDA(h, cudaMemcpy2DAsync(host.data() + (size_t)q * w * hgt, (size_t)w * sizeof(float),
-                                      src + (size_t)y0 * pitch + x0, pitch * sizeof(float), (size_t)w * sizeof(float),
-                                      hgt, cudaMemcpyDeviceToHost, h->stream));
-    }
-    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-    const size_t wn = (size_t)w * hgt;
-    for (int q = 0; q < LBM_STATE_PLANES; ++q) {
-        const double r = q < lbm::kPlanes ? h->ref[q] : 0.0;
-        for (size_t i = 0; i < wn; ++i) out[q * wn + i] = r + (double)host[q * wn + i];
-    }
-    return LBM_OK;
+    const size_t pitch = (size_t)h->P.pitch, wn = (size_t)w * hgt;
+    return decode_rows(h, y0, hgt, [&](int yb, int r, const float* pops, const float* hist) {
+        const size_t band = (size_t)r * pitch;
+        for (int q = 0; q < LBM_STATE_PLANES; ++q) {
+            const bool pop = q < lbm::kPlanes;
+            const double ref = pop ? h->ref[q] : 0.0;
+            const float* src = pop ? pops + q * band : hist + (q - lbm::kPlanes) * band;
+            for (int y = 0; y < r; ++y)
+                for (int x = 0; x < w; ++x)
+                    out[q * wn + (size_t)(yb - y0 + y) * w + x] = ref + (double)src[(size_t)y * pitch + x0 + x];
+        }
+        return LBM_OK;
+    });
 }
 
 int lbm_set_state(lbm_handle* h, const double* in)
@@ -740,22 +820,34 @@ int lbm_set_state(lbm_handle* h, const double* in)
     int rc = ensure_initialised(h);
     if (rc) return rc;
     if (!in) return fail(h, LBM_EINVAL, "in is NULL");
-    const size_t plane = (size_t)h->P.plane;
-    const int nx = h->P.nx, ny = h->P.ny, pitch = h->P.pitch;
-    std::vector<float> host(plane * LBM_STATE_PLANES, 0.0f);
-    for (int q = 0; q < LBM_STATE_PLANES; ++q)
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                double v = in[(size_t)q * nx * ny + (size_t)y * nx + x];
-                if (!isfinite(v)) return fail(h, LBM_EINVAL, "non-finite state value");
-                host[q * plane + (size_t)y * pitch + x] = (float)(q < lbm::kPlanes ? v - h->ref[q] : v);
-            }
-    LBM_CUDA(h, cudaMemcpyAsync(h->d_f32, host.data(), plane * lbm::kPlanes * sizeof(float), cudaMemcpyHostToDevice,
-                                h->stream));
-    LBM_CUDA(h, cudaMemcpyAsync(h->B.hist, host.data() + plane * lbm::kPlanes, plane * lbm::kHist * sizeof(float),
-                                cudaMemcpyHostToDevice, h->stream));
-    LBM_CUDA(h, lbm::launch_encode(h->P, h->storage, h->d_f32, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->stream));
-    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    const int nx = h->P.nx, ny = h->P.ny;
+    const size_t pitch = (size_t)h->P.pitch, plane = (size_t)h->P.plane, N = (size_t)nx * ny;
+    for (size_t i = 0; i < N * LBM_STATE_PLANES; ++i)  // the whole input first: a refusal changes nothing
+        if (!isfinite(in[i])) return fail(h, LBM_EINVAL, "non-finite state value");
+    int rows;
+    if ((rc = band_rows(h, lbm::kPlanes * sizeof(float), &rows))) return rc;
+    float* dev = (float*)h->scratch;
+    std::vector<float> host((size_t)rows * pitch * LBM_STATE_PLANES, 0.0f);
+    for (int y0 = 0; y0 < ny; y0 += rows) {
+        const int r = std::min(rows, ny - y0);
+        const size_t band = (size_t)r * pitch;
+        for (int q = 0; q < LBM_STATE_PLANES; ++q) {
+            const double ref = q < lbm::kPlanes ? h->ref[q] : 0.0;
+            for (int y = 0; y < r; ++y)
+                for (int x = 0; x < nx; ++x)
+                    host[q * band + (size_t)y * pitch + x] =
+                        (float)(in[(size_t)q * N + (size_t)(y0 + y) * nx + x] - ref);
+        }
+        LBM_CUDA(h, cudaMemcpyAsync(dev, host.data(), band * lbm::kPlanes * sizeof(float), cudaMemcpyHostToDevice,
+                                    h->stream));
+        for (int q = 0; q < lbm::kHist; ++q)
+            LBM_CUDA(h, cudaMemcpyAsync(h->B.hist + q * plane + (size_t)y0 * pitch,
+                                        host.data() + (lbm::kPlanes + q) * band, band * sizeof(float),
+                                        cudaMemcpyHostToDevice, h->stream));
+        LBM_CUDA(h, lbm::launch_encode(h->P, h->storage, dev, h->B.sc[h->B.cs], h->B.fl[h->B.cf], y0, r, h->stream));
+        // the host band buffer is refilled for the next band
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
     return LBM_OK;
 }
 

@@ -33,16 +33,24 @@ __device__ __forceinline__ double min_image(double d, int L, int periodic)
     return d;
 }
 
+// Row bands.  Whole-grid transfers go through a bounded scratch buffer one
+// band of rows [y0, y0 + rows) at a time; a band's scratch holds its planes
+// one after another, rows * pitch elements each, node (x, y) at
+// (y - y0) * pitch + x.
+
 // Seeds (Sec. 4): phi = max_j tanh[(R_j - d_j)/(sqrt2 W0)], grain = nearest
 // centre (ties to the lower index); FP64 so that both choices match an FP64
-// evaluation.  fields: 6 FP64 planes (phi, U, theta, ux, uy, p), lattice units.
+// evaluation.  fields: 6 FP64 band planes (phi, U, theta, ux, uy, p), lattice
+// units; grain: the whole grid's plane.
 __global__ void k_seed_fields(const StepParams P, const double* __restrict__ seeds, int ns, double U0,
-                              double theta0, double W, double* __restrict__ fields, uint8_t* __restrict__ grain)
+                              double theta0, double W, double* __restrict__ fields, uint8_t* __restrict__ grain,
+                              int y0, int rows)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
+    const int y = y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= y0 + rows || y >= P.ny) return;
     const long long o = (long long)y * P.pitch + x;
+    const long long ob = (long long)(y - y0) * P.pitch + x, bp = (long long)rows * P.pitch;
     double best_phi = -2.0, best_d2 = 1e300;
     int best = 0;
     const double inv = 1.0 / (sqrt(2.0) * W);
@@ -57,12 +65,12 @@ __global__ void k_seed_fields(const StepParams P, const double* __restrict__ see
             best = j;
         }
     }
-    fields[0 * P.plane + o] = best_phi;
-    fields[1 * P.plane + o] = U0;
-    fields[2 * P.plane + o] = theta0;
-    fields[3 * P.plane + o] = 0.0;
-    fields[4 * P.plane + o] = 0.0;
-    fields[5 * P.plane + o] = 0.0;
+    fields[0 * bp + ob] = best_phi;
+    fields[1 * bp + ob] = U0;
+    fields[2 * bp + ob] = theta0;
+    fields[3 * bp + ob] = 0.0;
+    fields[4 * bp + ob] = 0.0;
+    fields[5 * bp + ob] = 0.0;
     if (grain) grain[o] = (uint8_t)best;
 }
 
@@ -108,21 +116,21 @@ __device__ void init_node(const StepParams& P, long long o, float p1, float dC, 
 
 template <class Store>
 __global__ void k_init(const StepParams P, const double* __restrict__ fields, void* __restrict__ sc,
-                       void* __restrict__ fl, float* __restrict__ hist)
+                       void* __restrict__ fl, float* __restrict__ hist, int y0, int rows)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    const long long plane = P.plane;
+    const int y = y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= y0 + rows || y >= P.ny) return;
     const long long o = (long long)y * P.pitch + x;
+    const long long ob = (long long)(y - y0) * P.pitch + x, bp = (long long)rows * P.pitch;
     // macro deviations from the reference state, formed in FP64
-    const double phi = fields[0 * plane + o], U = fields[1 * plane + o];
+    const double phi = fields[0 * bp + ob], U = fields[1 * bp + ob];
     const double k = P.k;
     const float p1 = (float)(phi + 1.0);
     const float dC = (float)(0.5 * (1.0 + k - (1.0 - k) * phi) * (1.0 + (1.0 - k) * U) - 1.0);
-    const float dth = (float)(fields[2 * plane + o] - (double)P.theta_ref);
-    const float ux = (float)fields[3 * plane + o], uy = (float)fields[4 * plane + o];
-    init_node<Store>(P, o, p1, dC, (float)U, dth, ux, uy, (float)fields[5 * plane + o], sc, fl, hist, ux, uy);
+    const float dth = (float)(fields[2 * bp + ob] - (double)P.theta_ref);
+    const float ux = (float)fields[3 * bp + ob], uy = (float)fields[4 * bp + ob];
+    init_node<Store>(P, o, p1, dC, (float)U, dth, ux, uy, (float)fields[5 * bp + ob], sc, fl, hist, ux, uy);
 }
 
 // Fields of every node, pixel-interleaved for the surrogate network:
@@ -228,44 +236,48 @@ __global__ void k_phi_mismatch(const float* __restrict__ a, const float* __restr
 // uy, p (flow lattice units); the host adds the reference values in FP64.
 template <class Store>
 __global__ void k_macros(const StepParams P, const void* __restrict__ sc, const void* __restrict__ fl,
-                         float* __restrict__ out)
+                         float* __restrict__ out, int y0, int rows)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
+    const int y = y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= y0 + rows || y >= P.ny) return;
     const long long o = (long long)y * P.pitch + x;
     float f[5], n[5], g[5], h[9];
     load_node<Store>(P, sc, fl, o, f, n, g, h);
     const Macro m = node_macros(f, n, g, h, P);
-    const long long plane = P.plane;
-    out[0 * plane + o] = m.p1;
-    out[1 * plane + o] = m.dC;
-    out[2 * plane + o] = m.U;
-    out[3 * plane + o] = m.dth;
-    out[4 * plane + o] = m.ux;
-    out[5 * plane + o] = m.uy;
-    out[6 * plane + o] = m.p;
+    const long long ob = (long long)(y - y0) * P.pitch + x, bp = (long long)rows * P.pitch;
+    out[0 * bp + ob] = m.p1;
+    out[1 * bp + ob] = m.dC;
+    out[2 * bp + ob] = m.U;
+    out[3 * bp + ob] = m.dth;
+    out[4 * bp + ob] = m.ux;
+    out[5 * bp + ob] = m.uy;
+    out[6 * bp + ob] = m.p;
 }
 
 // Deviations of every population plane as FP32 planes (and back).
 template <class Store>
 __global__ void k_decode(const StepParams P, const void* __restrict__ sc, const void* __restrict__ fl,
-                         float* __restrict__ out)
+                         float* __restrict__ out, int y0, int rows)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= P.plane) return;
+    const long long bp = (long long)rows * P.pitch;
+    const long long ib = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (ib >= bp) return;
+    const long long i = (long long)y0 * P.pitch + ib;
 #pragma unroll
-    for (int q = 0; q < kPlanes; ++q) out[q * P.plane + i] = Store::load(sc, fl, q, i, P);
+    for (int q = 0; q < kPlanes; ++q) out[q * bp + ib] = Store::load(sc, fl, q, i, P);
 }
 
 template <class Store>
 __global__ void k_encode(const StepParams P, const float* __restrict__ in, void* __restrict__ sc,
-                         void* __restrict__ fl)
+                         void* __restrict__ fl, int y0, int rows)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= P.plane) return;
+    const long long bp = (long long)rows * P.pitch;
+    const long long ib = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (ib >= bp) return;
+    const long long i = (long long)y0 * P.pitch + ib;
 #pragma unroll
-    for (int q = 0; q < kPlanes; ++q) Store::store(sc, fl, q, i, in[q * P.plane + i], P);
+    for (int q = 0; q < kPlanes; ++q) Store::store(sc, fl, q, i, in[q * bp + ib], P);
 }
 
 // ------------------------------------------------------------- reductions
@@ -488,10 +500,11 @@ __global__ void __cluster_dims__(kTipCluster, 1, 1) __launch_bounds__(kTipThread
 }
 
 template <class Store>
-cudaError_t init_t(const StepParams& P, const double* fields, void* sc, void* fl, float* hist, cudaStream_t s)
+cudaError_t init_t(const StepParams& P, const double* fields, void* sc, void* fl, float* hist, int y0, int rows,
+                   cudaStream_t s)
 {
-    const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
-    k_init<Store><<<g, b, 0, s>>>(P, fields, sc, fl, hist);
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (rows + 3) / 4);
+    k_init<Store><<<g, b, 0, s>>>(P, fields, sc, fl, hist, y0, rows);
     return cudaGetLastError();
 }
 
@@ -514,24 +527,28 @@ cudaError_t set_fields_nhwc_t(const StepParams& P, const float* src, float vf, v
 }
 
 template <class Store>
-cudaError_t macros_t(const StepParams& P, const void* sc, const void* fl, float* out, cudaStream_t s)
+cudaError_t macros_t(const StepParams& P, const void* sc, const void* fl, float* out, int y0, int rows,
+                     cudaStream_t s)
 {
-    const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
-    k_macros<Store><<<g, b, 0, s>>>(P, sc, fl, out);
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (rows + 3) / 4);
+    k_macros<Store><<<g, b, 0, s>>>(P, sc, fl, out, y0, rows);
     return cudaGetLastError();
 }
 
 template <class Store>
-cudaError_t decode_t(const StepParams& P, const void* sc, const void* fl, float* out, cudaStream_t s)
+cudaError_t decode_t(const StepParams& P, const void* sc, const void* fl, float* out, int y0, int rows,
+                     cudaStream_t s)
 {
-    k_decode<Store><<<(unsigned)((P.plane + 255) / 256), 256, 0, s>>>(P, sc, fl, out);
+    const long long n = (long long)rows * P.pitch;
+    k_decode<Store><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, sc, fl, out, y0, rows);
     return cudaGetLastError();
 }
 
 template <class Store>
-cudaError_t encode_t(const StepParams& P, const float* in, void* sc, void* fl, cudaStream_t s)
+cudaError_t encode_t(const StepParams& P, const float* in, void* sc, void* fl, int y0, int rows, cudaStream_t s)
 {
-    k_encode<Store><<<(unsigned)((P.plane + 255) / 256), 256, 0, s>>>(P, in, sc, fl);
+    const long long n = (long long)rows * P.pitch;
+    k_encode<Store><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, in, sc, fl, y0, rows);
     return cudaGetLastError();
 }
 
@@ -549,20 +566,20 @@ cudaError_t reduce_t(const StepParams& P, const void* sc, const void* fl, double
 }  // namespace
 
 cudaError_t launch_seed_fields(const StepParams& P, const double* seeds, int ns, double U0, double theta0, double W,
-                               double* fields, uint8_t* grain, cudaStream_t s)
+                               double* fields, uint8_t* grain, int y0, int rows, cudaStream_t s)
 {
-    const dim3 b(64, 4), g((P.nx + 63) / 64, (P.ny + 3) / 4);
-    k_seed_fields<<<g, b, 0, s>>>(P, seeds, ns, U0, theta0, W, fields, grain);
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (rows + 3) / 4);
+    k_seed_fields<<<g, b, 0, s>>>(P, seeds, ns, U0, theta0, W, fields, grain, y0, rows);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_from_fields(const StepParams& P, int storage, const double* fields, void* sc, void* fl,
-                                    float* hist, cudaStream_t s)
+                                    float* hist, int y0, int rows, cudaStream_t s)
 {
     switch (storage) {
-    case kStoreF16: return init_t<StoreF16>(P, fields, sc, fl, hist, s);
-    case kStoreBF16: return init_t<StoreBF16>(P, fields, sc, fl, hist, s);
-    default: return init_t<StoreF32>(P, fields, sc, fl, hist, s);
+    case kStoreF16: return init_t<StoreF16>(P, fields, sc, fl, hist, y0, rows, s);
+    case kStoreBF16: return init_t<StoreBF16>(P, fields, sc, fl, hist, y0, rows, s);
+    default: return init_t<StoreF32>(P, fields, sc, fl, hist, y0, rows, s);
     }
 }
 
@@ -622,32 +639,33 @@ cudaError_t launch_phi_mismatch(const float* a, const float* b, long long n, uns
     return cudaGetLastError();
 }
 
-cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
-                          cudaStream_t s)
+cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out, int y0,
+                          int rows, cudaStream_t s)
 {
     switch (storage) {
-    case kStoreF16: return macros_t<StoreF16>(P, sc, fl, out, s);
-    case kStoreBF16: return macros_t<StoreBF16>(P, sc, fl, out, s);
-    default: return macros_t<StoreF32>(P, sc, fl, out, s);
+    case kStoreF16: return macros_t<StoreF16>(P, sc, fl, out, y0, rows, s);
+    case kStoreBF16: return macros_t<StoreBF16>(P, sc, fl, out, y0, rows, s);
+    default: return macros_t<StoreF32>(P, sc, fl, out, y0, rows, s);
     }
 }
 
-cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
-                          cudaStream_t s)
+cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, float* out, int y0,
+                          int rows, cudaStream_t s)
 {
     switch (storage) {
-    case kStoreF16: return decode_t<StoreF16>(P, sc, fl, out, s);
-    case kStoreBF16: return decode_t<StoreBF16>(P, sc, fl, out, s);
-    default: return decode_t<StoreF32>(P, sc, fl, out, s);
+    case kStoreF16: return decode_t<StoreF16>(P, sc, fl, out, y0, rows, s);
+    case kStoreBF16: return decode_t<StoreBF16>(P, sc, fl, out, y0, rows, s);
+    default: return decode_t<StoreF32>(P, sc, fl, out, y0, rows, s);
     }
 }
 
-cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, cudaStream_t s)
+cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, int y0, int rows,
+                          cudaStream_t s)
 {
     switch (storage) {
-    case kStoreF16: return encode_t<StoreF16>(P, in, sc, fl, s);
-    case kStoreBF16: return encode_t<StoreBF16>(P, in, sc, fl, s);
-    default: return encode_t<StoreF32>(P, in, sc, fl, s);
+    case kStoreF16: return encode_t<StoreF16>(P, in, sc, fl, y0, rows, s);
+    case kStoreBF16: return encode_t<StoreBF16>(P, in, sc, fl, y0, rows, s);
+    default: return encode_t<StoreF32>(P, in, sc, fl, y0, rows, s);
     }
 }
 

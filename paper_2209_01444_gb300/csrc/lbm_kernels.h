@@ -77,16 +77,21 @@ cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int run
 // CTAs of the persistent batched kernel that fit on the current device at once.
 int batch_resident_ctas(int storage, int ty);
 
-// Initialisation: equilibrium populations from lattice-unit macros
-// (phi, U, theta, ux, uy, p) in FP64 planes, then history = time-0 macros.
+// Row bands: the whole-grid transfers below work on the rows [y0, y0 + rows)
+// and keep their planes in a band buffer, rows * pitch elements per plane,
+// node (x, y) at (y - y0) * pitch + x.
+
+// Initialisation of a band: equilibrium populations from lattice-unit macros
+// (phi, U, theta, ux, uy, p) in FP64 band planes, then history = time-0 macros.
 cudaError_t launch_init_from_fields(const StepParams& P, int storage, const double* fields, void* sc, void* fl,
-                                    float* hist, cudaStream_t s);
+                                    float* hist, int y0, int rows, cudaStream_t s);
 
-// Seeded initial fields: phi, grain id, U = U0, theta = theta0 (FP64 planes).
+// Seeded initial fields of a band: phi, U = U0, theta = theta0 (FP64 band
+// planes) and the grain ids (the whole grid's plane).
 cudaError_t launch_seed_fields(const StepParams& P, const double* seeds, int ns, double U0, double theta0,
-                               double W, double* fields, uint8_t* grain, cudaStream_t s);
+                               double W, double* fields, uint8_t* grain, int y0, int rows, cudaStream_t s);
 
-// Macros of every node (FP32 planes phi, C, U, theta, ux, uy, p; lattice units).
+// Fields of every node pixel-interleaved for the network (FP32 NHWC), and back.
 cudaError_t launch_fields_nhwc(const StepParams& P, int storage, const void* sc, const void* fl, float inv_vf,
                                float* dst, cudaStream_t s);
 cudaError_t launch_set_fields_nhwc(const StepParams& P, int storage, const float* src, float vf, void* sc, void* fl,
@@ -100,13 +105,16 @@ cudaError_t launch_flow_inputs(const StepParams& P, int storage, const void* sc,
 cudaError_t flow_steps(const StepParams& P, int storage, int n, void* sc, void* const fl[2], int* cf, const float* phi,
                        const float* fy, cudaStream_t s);
 cudaError_t launch_phi_mismatch(const float* a, const float* b, long long n, unsigned long long* out, cudaStream_t s);
-cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
-                          cudaStream_t s);
+// Macros of a band (FP32 band planes phi + 1, C - 1, U, theta - theta_ref,
+// ux, uy, p; lattice units).
+cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out, int y0,
+                          int rows, cudaStream_t s);
 
-// Decode populations to FP32 planes / encode FP32 planes into populations.
-cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, float* out,
+// Decode a band's populations to FP32 band planes / encode them back.
+cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, float* out, int y0,
+                          int rows, cudaStream_t s);
+cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, int y0, int rows,
                           cudaStream_t s);
-cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, cudaStream_t s);
 
 // Metrics reductions (FP64 results): out[0..6] = solid fraction sum, sum C, sum H, sum h,
 // max |u| (flow lattice units), non-finite count, sum phi; then out[7..9] =

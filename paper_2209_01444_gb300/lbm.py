@@ -69,6 +69,7 @@ SIGNATURES = {
     "lbm_init_fields": (ct.c_int, [_H, _DP, _DP]),
     "lbm_step": (ct.c_int, [_H, ct.c_int]),
     "lbm_set_step_kernel": (ct.c_int, [_H, ct.c_int]),
+    "lbm_set_io_chunk": (ct.c_int, [_H, ct.c_size_t]),
     "lbm_step_kernel": (ct.c_int, [_H]),
     "lbm_synchronize": (ct.c_int, [_H]),
     "lbm_step_count": (ct.c_longlong, [_H]),
@@ -271,6 +272,10 @@ class Simulation:
 
     def synchronize(self) -> None:
         self._check(self.lib.lbm_synchronize(self.h))
+
+    def set_io_chunk(self, nbytes: int) -> None:
+        """Size limit of the device band buffer of whole-grid transfers."""
+        self._check(self.lib.lbm_set_io_chunk(self.h, int(nbytes)))
 
     STEP_KERNELS = {"auto": 0, "tiled": 1, "tma": 2}
 
