@@ -48,7 +48,13 @@ def oracle_window(case, x0, y0, w, h, bc):
     return o.state()
 
 
-def compare(g, case, cx, cy, size, bc, ylo_wall=False, xlo_wall=False):
+# FP16 storage: a stored deviation |d| <= 1 is rounded to 11 bits after the
+# scale of 16 (flow: 1024), at most 2^-11 / 2 per rounding; four steps of
+# rounding and mixing stay within 2e-3.
+TOL16 = 2e-3
+
+
+def compare(g, case, cx, cy, size, bc, ylo_wall=False, xlo_wall=False, tol=TOL):
     """GPU state of the size x size block at (cx, cy) against the oracle's
     window around it (margin on every side that is not a real wall)."""
     x0 = cx - (0 if xlo_wall else MARGIN)
@@ -60,7 +66,8 @@ def compare(g, case, cx, cy, size, bc, ylo_wall=False, xlo_wall=False):
     want = ref[:, oy:oy + size, ox:ox + size]
     got = g.state_region(cx, cy, size, size)
     err = np.abs(got - want).max(axis=(1, 2))
-    assert err.max() < TOL, f"window ({cx},{cy}): worst plane {int(err.argmax())} error {err.max():.2e}"
+    assert err.max() < tol, f"window ({cx},{cy}): worst plane {int(err.argmax())} error {err.max():.2e}"
+    return float(err.max())
 
 
 def test_multi_seed_4096_windows(lbm):
@@ -88,3 +95,38 @@ def test_forced_flow_1024_windows(lbm):
     compare(g, case, 384 - 16, 512 - 16, 32, per)              # around the seed
     compare(g, case, 0, 600, 24, ("inflow", "outflow", "periodic", "periodic"), xlo_wall=True)
     compare(g, case, 500, 0, 24, ("periodic", "periodic", "symmetry", "symmetry"), ylo_wall=True)
+
+
+def test_multi_seed_4096_windows_fp16(lbm):
+    """The same workload with FP16 population storage, as the bench's FP16
+    line runs it."""
+    case = W.multi_seed()
+    g = lbm.Simulation(case.params, "fp16")
+    g.init_seeds(case.seeds, case.U0, case.theta0)
+    g.step(K)
+    per = ("periodic",) * 4
+    worst = 0.0
+    for j in (0, 40):
+        sx, sy = int(case.seeds[j][0]), int(case.seeds[j][1])
+        worst = max(worst, compare(g, case, sx - 16, sy - 16, 32, per, tol=TOL16))
+    worst = max(worst, compare(g, case, 3000, 0, 24, ("periodic", "periodic", "noslip", "noslip"), ylo_wall=True,
+                               tol=TOL16))
+    print(f"FP16 full-size windows: worst population error {worst:.2e}")
+
+
+def test_tma_kernel_at_full_size(lbm):
+    """The TMA-staged kernel on the 4096^2 workload: the same windows as the
+    tiled kernel, bit for bit, after the bench's launch configuration has run
+    20 steps (a captured 16-step graph and direct launches)."""
+    case = W.multi_seed()
+    out = []
+    for kernel in ("tiled", "tma"):
+        g = lbm.Simulation(case.params)
+        g.set_step_kernel(kernel)
+        g.init_seeds(case.seeds, case.U0, case.theta0)
+        g.step(20)
+        out.append([g.state_region(x, y, 48, 40) for x, y in ((0, 0), (2040, 1900), (4048, 4056))])
+        del g
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
+
