@@ -87,7 +87,8 @@ enum { LBM_FIELD_PHI = 0, LBM_FIELD_C = 1, LBM_FIELD_U = 2, LBM_FIELD_THETA = 3,
 /* The problem as the paper states it (Secs. 2-4).  All doubles are in the
  * paper's units (lengths in W0, times in tau0). */
 typedef struct lbm_params {
-    int nx, ny;            /* lattice nodes along x and y (each >= 4)           */
+    int nx, ny;            /* lattice nodes along x and y (each >= 4; ny <= 262140,
+                              nx <= 2^30)                                       */
     double W0, tau0;       /* interface width and kinetic time, Eq. (1)          */
     double dx, dt;         /* lattice spacing (W0 units) and coupled time step   */
     double eps_s;          /* anisotropy strength, Eq. (2), 0 <= eps_s < 1/3     */

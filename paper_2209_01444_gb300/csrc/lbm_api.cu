@@ -113,6 +113,10 @@ std::string validate(const lbm_params* p)
 {
     if (!p) return "params is NULL";
     if (p->nx < 4 || p->ny < 4) return "nx and ny must be >= 4";
+    // the row-tiled kernels put 4 rows per CTA along grid.y (at most 65535)
+    if (p->ny > 4 * 65535) return "ny must be <= 262140";
+    if (p->nx > (1 << 30)) return "nx must be <= 2^30";
+    if (p->isothermal != 0 && p->isothermal != 1) return "isothermal must be 0 or 1";
     if ((long long)p->nx * p->ny > (1LL << 31)) return "grid too large";
     if (!(p->W0 > 0 && p->tau0 > 0 && p->dx > 0 && p->dt > 0)) return "W0, tau0, dx, dt must be > 0";
     if (!(p->eps_s >= 0 && p->eps_s < 1.0 / 3.0)) return "eps_s must be in [0, 1/3)";
@@ -127,7 +131,6 @@ std::string validate(const lbm_params* p)
     if ((p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) return "bottom/top periodicity must match";
     if (p->storage < LBM_FP32 || p->storage > LBM_BF16) return "unknown storage";
     if (p->grad_mode != LBM_GRAD_FD9 && p->grad_mode != LBM_GRAD_LOCAL) return "unknown grad_mode";
-    if (p->isothermal != 0 && p->isothermal != 1) return "isothermal must be 0 or 1";
     return "";
 }
 

@@ -71,6 +71,8 @@ def test_version_and_default_params(lib):
 
 @pytest.mark.parametrize("field,value,why", [
     ("nx", 3, "nx and ny"),
+    ("ny", 262141, "ny must be <= 262140"),
+    ("isothermal", 2, "isothermal"),
     ("k", 1.0, "k must"),
     ("eps_s", 0.4, "eps_s"),
     ("n_sub", 0, "n_sub"),
