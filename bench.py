@@ -357,6 +357,16 @@ def batch_leg(lbm, torch, stream, steps, world, max_over_ranks, barrier):
     ms = max_over_ranks(e0.elapsed_time(e1))
     value = world * nodes * k / (ms / 1e3) / 1e6
     bad = sum(b.metrics(j, *c.seeds[0][:2], c.seeds[0][3])["nonfinite"] for j, c in enumerate(cases[:8]))
+    # accuracy of the batched FP16 run: its first domains against the plain
+    # FP32 path after the same 16 + k steps (the tuner restores the state it times on)
+    errs = []
+    for j, c in enumerate(cases[:4]):
+        ref = lbm.Simulation(c.params, "fp32", stream=stream)
+        ref.init_seeds(c.seeds, c.U0, c.theta0)
+        ref.step(16 + k)
+        errs.append(field_errors(b.fields(j, ACCURACY_FIELDS), ref.fields(ACCURACY_FIELDS), abs(c.theta0)))
+        del ref
+    worst = {f: max(e[f] for e in errs) for f in errs[0]}
     del b
     # plain FP32 path, one domain after another
     sims = []
@@ -380,7 +390,7 @@ def batch_leg(lbm, torch, stream, steps, world, max_over_ranks, barrier):
             "nodes": nodes, "storage": "fp16", "tile_height": ty, "tiles_per_cta": tiles_per_cta, "steps": k,
             "value": value, "unit": UNIT,
             "ms_per_step": ms / k, "sequential_fp32_value": seq_value, "speedup_vs_sequential_fp32": value / seq_value,
-            "nonfinite_domains_of_first_8": bad}
+            "nonfinite_domains_of_first_8": bad, "field_error_vs_fp32_first_4_domains": worst}
 
 
 def surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, train_steps: int = 1500, windows: int = 400,
