@@ -74,50 +74,71 @@ __global__ void k_relu_bwd(G* __restrict__ g, int gpitch, const bf16* __restrict
 //   AT[t * C + c][p] = X[pixel p shifted by tap t][c]   (zero outside)
 // with taps 9 (the 3 x 3 neighbourhood, t = ky * 3 + kx) or 1 (no shift: a
 // plain transpose of [P][C] with pitch).  One CTA moves a 64-pixel x
-// 64-channel block through shared memory: 16-byte reads along channels,
-// 16-byte writes along pixels.  C and the pitches are multiples of 8; P and
-// the AT pitch multiples of 8.
+// 64-channel block through shared memory: 16-byte reads along channels (8
+// threads per pixel row), then each thread takes a pair of channels for 8
+// pixels, reading 32-bit words, splitting them with byte permutes and writing
+// 16 bytes along pixels per channel (8 threads per 128-byte line).  The 16-byte
+// chunks of tile row r sit at chunk ^ ((r / 8) % 8), so the eight pixel
+// groups a warp reads at once fall in different banks.  Each pixel's source
+// offset is computed once per CTA.  C and the pitches are multiples of 8; P
+// and the AT pitch multiples of 8; P < 2^31.
 __global__ void __launch_bounds__(256) k_gatherT(const bf16* __restrict__ X, int B, int H, int W, int C, int cpitch,
                                                  int taps, bf16* __restrict__ AT, long long atpitch)
 {
-    __shared__ __align__(16) bf16 tile[64][64 + 8];  // [pixel][channel], padded rows
-    const long long P = (long long)B * H * W;
-    const long long p0 = (long long)blockIdx.x * 64;
+    __shared__ uint4 tile[64][8];   // [pixel][16-byte chunk of 8 channels], chunks permuted per row group
+    __shared__ long long src[64];   // element offset of each pixel's shifted source, -1 outside the image
+    const int P = B * H * W;
+    const int p0 = blockIdx.x * 64;
     const int cblk = blockIdx.y;                 // 64-channel block within (tap, channel)
     const int cpb = (C + 63) / 64;                // channel blocks per tap
     const int t = taps == 9 ? cblk / cpb : 4;     // tap 4 is the centre
     const int c0 = (cblk % cpb) * 64;
     const int dy = t / 3 - 1, dx = t % 3 - 1;
-    // load: 64 pixels x 64 channels, 8 channels (16 bytes) per thread-step
-    for (int k = threadIdx.x; k < 64 * 8; k += 256) {
-        const int pi = k >> 3, g = k & 7;
-        const long long p = p0 + pi;
-        const int c = c0 + g * 8;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (p < P && c < C) {
-            const int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((long long)W * H));
+    if (threadIdx.x < 64) {
+        const int p = p0 + threadIdx.x;
+        long long off = -1;
+        if (p < P) {
+            const int x = p % W, r = p / W, y = r % H, b = r / H;
             const int xx = x + dx, yy = y + dy;
-            if (xx >= 0 && xx < W && yy >= 0 && yy < H)
-                v = *(const uint4*)(X + (((long long)b * H + yy) * W + xx) * cpitch + c);
+            if (xx >= 0 && xx < W && yy >= 0 && yy < H) off = (((long long)b * H + yy) * W + xx) * cpitch;
         }
-        *(uint4*)&tile[pi][g * 8] = v;
+        src[threadIdx.x] = off;
     }
     __syncthreads();
-    // store: for each of the 64 channels, 64 consecutive pixels (8 per thread-step)
     for (int k = threadIdx.x; k < 64 * 8; k += 256) {
-        const int ci = k >> 3, g = k & 7;
-        const int c = c0 + ci;
-        const long long p = p0 + g * 8;
-        if (c >= C || p >= P) continue;
-        __align__(16) bf16 v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = tile[g * 8 + j][ci];
-        const long long row = (long long)(taps == 9 ? t * C + c : c);
-        if (p + 8 <= P)
-            *(uint4*)(AT + row * atpitch + p) = *(const uint4*)v;
-        else
-            for (int j = 0; p + j < P; ++j) AT[row * atpitch + p + j] = v[j];
+        const int pi = k >> 3, g = k & 7;
+        const int c = c0 + g * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        const long long off = src[pi];
+        if (off >= 0 && c < C) v = *(const uint4*)(X + off + c);
+        tile[pi][g ^ ((pi >> 3) & 7)] = v;
     }
+    __syncthreads();
+    // lane: pixel group g (8 pixels) and one of four channel pairs; warp w
+    // holds channel pairs 4w .. 4w + 3 of the block
+    const int lane = threadIdx.x & 31, g = lane & 7;
+    const int cp = (threadIdx.x >> 5) * 4 + (lane >> 3);  // channel pair 0..31
+    const int c = c0 + 2 * cp;
+    const int p = p0 + g * 8;
+    if (c >= C || p >= P) return;
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t* row = (const uint32_t*)&tile[g * 8 + j][0];
+        w[j] = row[(((cp >> 2) ^ g) << 2) + (cp & 3)];
+    }
+    uint4 lo, hi;  // channel c and c + 1, pixels p .. p + 7
+    lo.x = __byte_perm(w[0], w[1], 0x5410);
+    lo.y = __byte_perm(w[2], w[3], 0x5410);
+    lo.z = __byte_perm(w[4], w[5], 0x5410);
+    lo.w = __byte_perm(w[6], w[7], 0x5410);
+    hi.x = __byte_perm(w[0], w[1], 0x7632);
+    hi.y = __byte_perm(w[2], w[3], 0x7632);
+    hi.z = __byte_perm(w[4], w[5], 0x7632);
+    hi.w = __byte_perm(w[6], w[7], 0x7632);
+    const long long row = (long long)(taps == 9 ? t * C + c : c);
+    *(uint4*)(AT + row * atpitch + p) = lo;
+    *(uint4*)(AT + (row + 1) * atpitch + p) = hi;
 }
 
 // out[r][c] = BF16(y[r][c] > 0 ? g[r][c] : 0): the ReLU mask of an FP32
@@ -630,6 +651,7 @@ cudaError_t gatherT(const void* X, int B, int H, int W, int C, int cpitch, int t
 {
     const long long P = (long long)B * H * W;
     if ((taps != 9 && taps != 1) || C % 8 || cpitch % 8 || atpitch % 8 || P % 8) return cudaErrorInvalidValue;
+    if (P > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (((uintptr_t)X | (uintptr_t)AT) & 15) return cudaErrorInvalidValue;
     const long long cblocks = (long long)((C + 63) / 64) * taps;
     if (cblocks > 65535) return cudaErrorInvalidValue;
