@@ -801,7 +801,46 @@ __global__ void k_split_reduce(const float* __restrict__ part, int splits, int M
         ((float*)D)[(size_t)row * ldd + col] = acc;
 }
 
+// The same sum written transposed, D[col][row] (FP32, no bias): reads run
+// along the partial tiles' rows, writes stride by ldd.
+__global__ void k_split_reduce_t(const float* __restrict__ part, int splits, int M, int N, int ldp,
+                                 float* __restrict__ D, int ldd)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)M * N) return;
+    const int row = (int)(i / N), col = (int)(i - (long long)row * N);
+    float acc = 0.0f;
+    for (int z = 0; z < splits; ++z) acc += part[(size_t)z * M * ldp + (size_t)row * ldp + col];
+    D[(size_t)col * ldd + row] = acc;
+}
+
 }  // namespace
+
+cudaError_t gemm_bf16_tout(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K,
+                           cudaStream_t s, int splits, float* workspace)
+{
+    const int bn = bn_for(N);
+    if (N < 8 || N % 8 || !workspace) return cudaErrorInvalidValue;
+    if (lda % 8 || ldb % 8 || K > lda || K > ldb || M > ldd || M < 1 || K < 1) return cudaErrorInvalidValue;
+    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)D) & 15) return cudaErrorInvalidValue;
+    const int nkb = (K + kBK - 1) / kBK;
+    if (splits < 1) splits = 1;
+    if (splits > nkb) splits = nkb;
+    const int kb_per_split = (nkb + splits - 1) / splits;
+    splits = (nkb + kb_per_split - 1) / kb_per_split;
+    CUtensorMap ta, tb;
+    cudaError_t e = make_map(&ta, A, M, K, lda, kBM, kBK);
+    if (e == cudaSuccess) e = make_map(&tb, B, N, K, ldb, bn, kBK);
+    if (e != cudaSuccess) return e;
+    // every split (one included) goes through the workspace; the reduction
+    // writes the transpose
+    e = dispatch<kBK, false>(bn, false, ta, tb, workspace, nullptr, M, N, K, N, 0, splits, kb_per_split, ConvGeo{},
+                             ShuffleGeo{}, s);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)M * N;
+    k_split_reduce_t<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(workspace, splits, M, N, N, D, ldd);
+    return cudaGetLastError();
+}
 
 cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,
                       int N, int K, bool out_bf16, bool relu, cudaStream_t s, int splits, float* workspace)

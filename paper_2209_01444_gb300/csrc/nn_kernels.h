@@ -13,6 +13,11 @@ namespace nn {
 cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,
                       int N, int K, bool out_bf16, bool relu, cudaStream_t s, int splits = 1,
                       float* workspace = nullptr);
+// D[n][m] = sum_k A[m][k] B[n][k] (FP32, pitch ldd >= M): the same GEMM with
+// its result transposed by the split-K reduction; `workspace` holds
+// splits * M * N floats.
+cudaError_t gemm_bf16_tout(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K,
+                           cudaStream_t s, int splits, float* workspace);
 
 // Implicit 3 x 3 convolution (zero padding) on tensor cores:
 // D[p][n] = act(sum over taps t and channels c < C of X[pixel p shifted by t][c]

@@ -154,6 +154,26 @@ __global__ void k_mask_cast(const float* __restrict__ g, int gpitch, const bf16*
     out[r * opitch + c] = __float2bfloat16(v);
 }
 
+// The same, eight channels per thread (C, the pitches and the pointers
+// aligned to 8 elements; rows * C / 8 < 2^31): 32-byte FP32 and 16-byte BF16
+// accesses, 32-bit index arithmetic.
+__global__ void k_mask_cast8(const float* __restrict__ g, int gpitch, const bf16* __restrict__ y, int ypitch,
+                             int groups, int cg, bf16* __restrict__ out, int opitch)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= groups) return;
+    const int r = i / cg, c = (i - r * cg) * 8;
+    const float4 g0 = *(const float4*)(g + (long long)r * gpitch + c);
+    const float4 g1 = *(const float4*)(g + (long long)r * gpitch + c + 4);
+    const uint4 yv = *(const uint4*)(y + (long long)r * ypitch + c);
+    const bf16* ys = (const bf16*)&yv;
+    const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16(bf(ys[j]) > 0.0f ? gv[j] : 0.0f);
+    *(uint4*)(out + (long long)r * opitch + c) = *(const uint4*)o;
+}
+
 // Out[c][r] = In[r][c] (BF16), 32 x 32 tiles through shared memory.
 __global__ void k_transpose(const bf16* __restrict__ in, int rows, int cols, int ipitch, bf16* __restrict__ out,
                             int opitch)
@@ -663,7 +683,16 @@ cudaError_t gatherT(const void* X, int B, int H, int W, int C, int cpitch, int t
 cudaError_t mask_cast(const float* g, int gpitch, const void* y, int ypitch, long long rows, int C, void* out,
                       int opitch, cudaStream_t s)
 {
-    k_mask_cast<<<blocks(rows * C), 256, 0, s>>>(g, gpitch, (const bf16*)y, ypitch, rows, C, (bf16*)out, opitch);
+    const bool vec = C % 8 == 0 && gpitch % 8 == 0 && ypitch % 8 == 0 && opitch % 8 == 0 &&
+                     (((uintptr_t)g | (uintptr_t)y | (uintptr_t)out) & 31) == 0 && rows * (C / 8) < 0x7fffffffLL;
+    if (vec) {
+        const int groups = (int)(rows * (C / 8));
+        k_mask_cast8<<<(groups + 255) / 256, 256, 0, s>>>(g, gpitch, (const bf16*)y, ypitch, groups, C / 8,
+                                                          (bf16*)out, opitch);
+    } else {
+        k_mask_cast<<<blocks(rows * C), 256, 0, s>>>(g, gpitch, (const bf16*)y, ypitch, rows, C, (bf16*)out,
+                                                     opitch);
+    }
     return cudaGetLastError();
 }
 

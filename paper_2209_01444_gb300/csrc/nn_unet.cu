@@ -282,7 +282,7 @@ cudaError_t allocate_backward(lbm_unet* u)
         for (Conv* cv : {&v.ea, &v.eb, &v.da, &v.db}) {
             if (!cv->cout) continue;
             col_n = std::max(col_n, 9 * P * std::max(cv->cin, cv->cout));
-            ws_n = std::max(ws_n, split_ws(cv->cout, 9 * cv->cin, P));
+            ws_n = std::max(ws_n, split_ws(9 * cv->cin, cv->cout, P));
             t_n = std::max(t_n, P * std::max(cv->cout, cv->cin));
             g_n = std::max(g_n, P * std::max(cv->cout, cv->cin));
         }
@@ -357,9 +357,12 @@ cudaError_t conv_bwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in
     cudaError_t e;
     if ((e = nn::gatherT(in, u->B, v.H, v.W, cv.cin, inpitch, 9, u->colT, P, u->s))) return e;
     if ((e = nn::gatherT(dY, u->B, v.H, v.W, cv.cout, cv.cout, 1, u->tA, P, u->s))) return e;
-    const int sp = splits_for(cv.cout, K9, P);
-    if ((e = nn::gemm_bf16(u->tA, (int)P, u->colT, (int)P, u->g + cv.w, K9, nullptr, cv.cout, K9, (int)P, false, false,
-                           u->s, sp, u->ws)))
+    // dW [cout][9 cin] = dY^T X_taps, computed as its transpose so that the
+    // 9 cin taps fill the MMA's 128 rows and cout (as small as 32) is the N
+    // width; the split-K reduction writes it back as [cout][9 cin]
+    const int sp = splits_for(K9, cv.cout, P);
+    if ((e = nn::gemm_bf16_tout(u->colT, (int)P, u->tA, (int)P, u->g + cv.w, K9, K9, cv.cout, (int)P, u->s, sp,
+                                u->ws)))
         return e;
     if ((e = nn::colsum(dY, false, P, cv.cout, cv.cout, u->g + cv.b, u->part, kPartBlocks, u->s))) return e;
     if (!dx) return cudaSuccess;
