@@ -1,7 +1,15 @@
-"""The two kernels of the fused coupled step: the TMA-staged persistent kernel
-and the register-staged tiled kernel run the same per-node arithmetic on the
-same inputs, so their states must agree bit for bit, on every wall type,
-ragged grids, grain maps and flow sub-steps.  Also the kernel choice itself."""
+"""The two kernels of the fused coupled step (register-staged tiled and
+TMA-staged persistent) run the same per-node arithmetic, coupled_node, on the
+same inputs; they differ in how the populations arrive.  Inlined into
+different kernels, that arithmetic may still round differently where the
+compiler fuses a product into a multiply-add, so the states must agree to
+rounding: 1e-5 with FP32 storage after 37 steps.  With 16-bit storage one
+rounding of a stored value may come out one step apart and spread for a few
+steps: a deviation near 1-2 is stored as FP16 after a scale of 16 (step
+2^-6 / 16 = 9.8e-4) or as BF16 unscaled (step 2^-7 = 7.8e-3), so 4e-3 and
+2e-2.
+A misplaced or missed load or store moves a population by O(0.1).  Every wall
+type, ragged grids, grain maps and flow sub-steps; also the kernel choice."""
 from __future__ import annotations
 
 import numpy as np
@@ -10,6 +18,14 @@ import pytest
 from paper_2209_01444_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "fp16": 4e-3, "bf16": 2e-2}
+
+
+def _agree(a, b, storage):
+    d = float(np.abs(a - b).max())
+    print(f"{storage}: largest state difference {d:.2e}")
+    assert d <= TOL[storage], d
 
 
 @pytest.fixture(scope="module")
@@ -54,14 +70,14 @@ def test_tma_kernel_equals_tiled_kernel(lbm, bcs, shape, storage):
                                gbetaC=W.GBETA_C * 5, theta_ref=-0.5, dir_theta=-0.4)
     f, orient = W.random_fields(nx, ny, rng_seed=3 + nx)
     a, b = _both(lbm, p, lambda s: s.init_fields(f, orient), 37, storage)
-    np.testing.assert_array_equal(a, b)
+    _agree(a, b, storage)
 
 
 def test_tma_kernel_smallest_fp32_grid(lbm):
     p = W.thermosolutal_params(40, 10, bc=BCS["mixed"], u_in=(0.15, 0.02), gbetaT=W.GBETA_T * 5)
     f, orient = W.random_fields(40, 10, rng_seed=43)
     a, b = _both(lbm, p, lambda s: s.init_fields(f, orient), 37)
-    np.testing.assert_array_equal(a, b)
+    _agree(a, b, "fp32")
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
@@ -73,7 +89,7 @@ def test_tma_kernel_equals_tiled_kernel_seeded(lbm, n_sub, storage):
     p = dict(c.params, ny=192, n_sub=n_sub, nu=2.0 * n_sub)
     seeds = c.seeds[c.seeds[:, 1] < 180]
     a, b = _both(lbm, p, lambda s: s.init_seeds(seeds, c.U0, c.theta0), 50, storage)
-    np.testing.assert_array_equal(a, b)
+    _agree(a, b, storage)
 
 
 def test_kernel_choice(lbm):
