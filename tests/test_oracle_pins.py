@@ -483,6 +483,52 @@ def test_warm_melt_rises_and_symmetry_walls_stop_normal_flow():
     assert np.abs(F["uy"][1]).max() > 1e-5
 
 
+
+def test_symmetry_side_walls_stop_normal_flow():
+    """The same for the left and right walls: a body force along x (the
+    reading of the external force as a constant lattice force) drives the melt
+    against symmetry walls at x = 0 and x = nx - 1, whose nodes keep u_x = 0
+    while the flow next to them does not."""
+    nx, ny = 24, 16
+    p = W.thermosolutal_params(nx, ny, eps_s=0.0, force=(2e-5, 0.0), gbetaT=0.0, gbetaC=0.0,
+                               bc=("symmetry", "symmetry", "periodic", "periodic"))
+    o = O.Oracle(p)
+    f = _liquid(nx, ny)
+    f[2] = p["theta_ref"]
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    f[3] = 1e-3 * np.sin(2 * np.pi * y / ny)  # a shear profile, so the flow is not uniform
+    o.init_fields(f)
+    o.step(40)
+    F = o.fields()
+    assert np.abs(F["ux"][:, 0]).max() < 1e-15 and np.abs(F["ux"][:, -1]).max() < 1e-15
+    assert np.abs(F["ux"][:, 1]).max() > 1e-5
+
+
+def test_stencil_gradient_is_the_nine_point_symbol():
+    """The isotropic nine-point stencil of reading R4, sum_i w_i c_i phi(x + c_i)
+    / cs^2, acts on a plane wave cos(k.x) exactly as its discrete symbol:
+    d_x -> -sin(k.x) sin(k_x) (2 + cos k_y) / 3 and likewise for y.  This pins
+    the stencil's weights and its 1/cs^2 scale (the magnitude of grad(phi),
+    which sets N of Eq. 3 and the grad(q~) term of Eq. 19), and, for small k,
+    the derivative itself to O(k^3)."""
+    nx, ny = 32, 24
+    p = W.thermosolutal_params(nx, ny)
+    for mx, my in ((1, 0), (0, 1), (3, 2), (5, -4)):
+        kx, ky = 2 * np.pi * mx / nx, 2 * np.pi * my / ny
+        y, x = np.mgrid[0:ny, 0:nx]
+        phase = kx * x + ky * y
+        f = _liquid(nx, ny)
+        f[0] = 0.5 * np.cos(phase)
+        o = O.Oracle(p)
+        o.init_fields(f)
+        g = o.grad_phi(0)
+        sx = -0.5 * np.sin(phase) * np.sin(kx) * (2 + np.cos(ky)) / 3
+        sy = -0.5 * np.sin(phase) * np.sin(ky) * (2 + np.cos(kx)) / 3
+        assert np.abs(g[0] - sx).max() < 1e-14 and np.abs(g[1] - sy).max() < 1e-14
+        k = math.hypot(kx, ky)
+        assert np.abs(g[0] + 0.5 * kx * np.sin(phase)).max() < 0.5 * k ** 3
+
+
 # ------------------------------------------------------------- invariants
 def test_periodic_run_conserves_solute_enthalpy_and_flow_mass():
     """Periodic walls: sum C and sum H are conserved (sum n^eq = C, sum g^eq = H,
