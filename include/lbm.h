@@ -156,7 +156,10 @@ LBM_API int lbm_params_default(lbm_params* p, int nx, int ny);
 
 /* Validate *p, derive the lattice-unit parameters and relaxation rates of
  * Sec. 4, and allocate the device state (double-buffered populations, history,
- * grain map).  On success *out receives a new handle. */
+ * grain map).  On success *out receives a new handle.  LBM_EINVAL, with the
+ * reason in lbm_last_error(NULL) and nothing allocated, for a value outside
+ * the ranges stated in lbm_params or a real parameter that is NaN or
+ * infinite; LBM_ENOMEM when the device memory does not suffice. */
 LBM_API int lbm_create(const lbm_params* p, lbm_handle** out);
 
 /* Release every resource of h (NULL is a no-op). */

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <string>
 #include <vector>
@@ -118,6 +119,12 @@ std::string validate(const lbm_params* p)
     if (p->nx > (1 << 30)) return "nx must be <= 2^30";
     if (p->isothermal != 0 && p->isothermal != 1) return "isothermal must be 0 or 1";
     if ((long long)p->nx * p->ny > (1LL << 31)) return "grid too large";
+    const double reals[] = {p->W0,     p->tau0,  p->dx,        p->dt,    p->eps_s,     p->lambda,
+                            p->k,      p->Mc_inf, p->D,        p->alpha, p->nu,        p->rho0,
+                            p->gbetaT, p->gbetaC, p->theta_ref, p->C_ref, p->force[0],  p->force[1],
+                            p->u_in[0], p->u_in[1], p->dir_phi, p->dir_U, p->dir_theta};
+    for (double v : reals)
+        if (!std::isfinite(v)) return "every real parameter must be finite";
     if (!(p->W0 > 0 && p->tau0 > 0 && p->dx > 0 && p->dt > 0)) return "W0, tau0, dx, dt must be > 0";
     if (!(p->eps_s >= 0 && p->eps_s < 1.0 / 3.0)) return "eps_s must be in [0, 1/3)";
     if (!(p->k > 0 && p->k < 1)) return "k must be in (0, 1)";

@@ -78,6 +78,9 @@ def test_version_and_default_params(lib):
     ("n_sub", 0, "n_sub"),
     ("D", 0.0, "D, alpha, nu"),
     ("storage", 7, "storage"),
+    ("lambda_", float("nan"), "finite"),
+    ("gbetaT", float("inf"), "finite"),
+    ("dir_theta", float("-inf"), "finite"),
 ])
 def test_create_rejects_invalid_parameters_without_touching_the_device(lib, field, value, why):
     from paper_2209_01444_gb300 import lbm
