@@ -362,8 +362,11 @@ int graph_for(lbm_handle* h, cudaGraphExec_t* out)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+        // the left/right walls of all but the last step are updated by the
+        // next step as it loads them (see launch_coupled_step); the graph's
+        // first step takes the state as stored and its last leaves it complete
         for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i)
-            e = lbm::launch_coupled_step(h->P, h->storage, h->prm.n_sub, h->B, cap);
+            e = lbm::launch_coupled_step(h->P, h->storage, h->prm.n_sub, h->B, cap, i > 0, i + 1 < kGraphSteps);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
     }
@@ -1257,7 +1260,9 @@ int batch_graph(lbm_batch* b, cudaGraphExec_t* out)
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     int par = b->parity;
     for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) {
-        e = lbm::launch_batch_step(T, b->storage, b->ty, b->run, par, b->ctas[tyk(b->ty)], cap);
+        // left/right walls as in the single-domain graphs
+        e = lbm::launch_batch_step(T, b->storage, b->ty, b->run, par, b->ctas[tyk(b->ty)], cap, i > 0,
+                                   i + 1 < kGraphSteps);
         par = 1 - par;
     }
     cudaError_t e2 = cudaStreamEndCapture(cap, &g);
@@ -1539,12 +1544,14 @@ int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height)
     const lbm::BatchTables T = tables(b);
     for (int k = 0; k < 3; ++k)
         for (int r = 0; r < 3; ++r) {
+            // steps as inside the captured graphs: left/right walls updated at
+            // the next step's load (the state is restored below)
             int par = start_parity;
             for (int i = 0; i < 2; ++i, par = 1 - par)
-                lbm::launch_batch_step(T, b->storage, tys[k], runs[r], par, b->ctas[k], b->stream);
+                lbm::launch_batch_step(T, b->storage, tys[k], runs[r], par, b->ctas[k], b->stream, i > 0, 1);
             cudaEventRecord(e0, b->stream);
             for (int i = 0; i < 10; ++i, par = 1 - par)
-                lbm::launch_batch_step(T, b->storage, tys[k], runs[r], par, b->ctas[k], b->stream);
+                lbm::launch_batch_step(T, b->storage, tys[k], runs[r], par, b->ctas[k], b->stream, 1, 1);
             cudaEventRecord(e1, b->stream);
             cudaEventSynchronize(e1);
             float ms = 0.0f;

@@ -41,7 +41,13 @@ void destroy_step_maps(StepMaps* m);
 // Flag raised when a bounded wait of the TMA-staged kernel expired.
 cudaError_t step_error(int* flag, bool clear);
 
-cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s);
+// One coupled step.  skip_columns: leave out the column pass of the left/right
+// walls (the tiled kernel with n_sub = 1 and walls in x; ignored otherwise);
+// the next step must then be launched with `repair`, which applies that
+// update to the wall cells as they are loaded.  A state read or kept between
+// launches must come from a step without skip_columns.
+cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s,
+                                int repair = 0, int skip_columns = 0);
 
 // One domain of a batch as the batched kernels see it: its parameters and the
 // two parities of its population buffers (n_sub = 1).
@@ -71,9 +77,10 @@ struct BatchTables {
 
 // One coupled step of every domain: buffers `parity` -> 1 - parity, then walls.
 // ty: tile height 4, 8 or 16; run: tiles per CTA (0: persistent grid of
-// `ctas` CTAs, each taking one contiguous run).
+// `ctas` CTAs, each taking one contiguous run).  repair, skip_columns: as for
+// launch_coupled_step.
 cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int run, int parity, int ctas,
-                              cudaStream_t s);
+                              cudaStream_t s, int repair = 0, int skip_columns = 0);
 // CTAs of the persistent batched kernel that fit on the current device at once.
 int batch_resident_ctas(int storage, int ty);
 

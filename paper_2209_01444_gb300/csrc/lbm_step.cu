@@ -62,6 +62,72 @@ __device__ __forceinline__ int mirror_or_wrap_local(int g, int n, int periodic, 
 #define LBM_STEP_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for (64 registers)
 #endif
 
+// Non-equilibrium extrapolation (Guo et al.) on one side pair, applied to the
+// freshly streamed buffer: pop(b) = pop^eq(boundary macros) + pop(f) -
+// pop^eq(macros of f), f the first interior node.  `axis` 1: bottom/top rows
+// over x in [xlo, xhi]; `axis` 0: left/right columns over every y.  The
+// result depends on the interior node alone, so applying it twice changes
+// nothing.
+//
+// Phase-field part: boundary populations fb from the interior populations ff,
+// whose sum (node_macros' order) is p1f = phi_f + 1.
+__device__ __forceinline__ void wall_phi(const StepParams& P, int type, const float (&ff)[5], float p1f,
+                                         float (&fb)[5])
+{
+    const float p1b = type == 5 ? P.dir_phi + 1.0f : p1f;  // Dirichlet far field, else zero gradient
+    float eb[5], ef[5];
+    deq_phi(p1b, eb);
+    deq_phi(p1f, ef);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) fb[i] = eb[i] + ff[i] - ef[i];
+}
+
+// Flow, solute and heat parts from the interior node's macros m and
+// populations n, g, h; the scalar parts only when !flow_only.
+__device__ __forceinline__ void wall_rest(const StepParams& P, int axis, int type, const Macro& m,
+                                          const float (&n)[5], const float (&g)[5], const float (&h)[9],
+                                          float (&nb)[5], float (&gb)[5], float (&hb)[9], int flow_only)
+{
+    float ubx = 0.0f, uby = 0.0f, pb = m.p;
+    if (type == 1) {  // inflow
+        ubx = P.uin_x;
+        uby = P.uin_y;
+    } else if (type == 2) {  // outflow
+        ubx = m.ux;
+        uby = m.uy;
+        pb = 0.0f;
+    } else if (type == 3) {  // symmetry
+        ubx = axis == 0 ? 0.0f : m.ux;
+        uby = axis == 0 ? m.uy : 0.0f;
+    }
+    float eb[9], ef[9];
+    deq_flow(pb, ubx, uby, eb);
+    deq_flow(m.p, m.ux, m.uy, ef);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) hb[i] = eb[i] + h[i] - ef[i];
+    if (flow_only) return;
+
+    float p1b = m.p1, dCb = m.dC, Ub = m.U, dthb = m.dth;
+    if (type == 5) {  // Dirichlet far field
+        p1b = P.dir_phi + 1.0f;
+        Ub = P.dir_U;
+        dCb = dC_of(Ub, p1b, P.k);
+        dthb = P.dir_theta - P.theta_ref;
+    }
+    const float hp1b = h_plus_1(P.h_kind, p1b);
+    const float Hb = (P.theta_ref + P.latent) + dthb - P.latent * hp1b;
+    const float Cb = 1.0f + dCb, Cf = 1.0f + m.dC;
+    const float sc = P.nsub;
+    deq_C(dCb, (1.0f - 0.5f * p1b) * Ub, Cb * ubx * sc, Cb * uby * sc, eb);
+    deq_C(m.dC, (1.0f - 0.5f * m.p1) * m.U, Cf * m.ux * sc, Cf * m.uy * sc, ef);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) nb[i] = eb[i] + n[i] - ef[i];
+    deq_H(dthb, P.latent * hp1b, Hb * ubx * sc, Hb * uby * sc, eb);
+    deq_H(m.dth, P.latent * m.hp1, m.H * m.ux * sc, m.H * m.uy * sc, ef);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gb[i] = eb[i] + g[i] - ef[i];
+}
+
 // Per-node part of the coupled step for node (x, y) = tile-local (lx - 1, ly - 1):
 // f, n, g, h are its populations at time n, the *_prev values its history;
 // fs holds the tile's phi populations with a one-node halo, node (x, y) at
@@ -199,19 +265,63 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
 
 // One tile of the coupled step: the CTA (TX x TYV threads) updates the nodes
 // [x0, x0 + TX) x [y0, y0 + TYV) of one domain.  GRAIN: the domain may carry a
-// grain map (read when `grain` is not null).  All threads reach the one
-// barrier, so callers may loop over tiles.
-template <class Store, bool GRAIN, bool WRITE_FB, int TYV>
+// grain map (read when `grain` is not null).  All threads reach the barriers,
+// so callers may loop over tiles.
+//
+// XWALL with xfix set: the left and right walls of a domain that is not
+// periodic in x were not updated after the previous step (the wall scheme's
+// column pass was skipped); the tile applies that update to the wall cells it
+// loads instead.  Extrapolation depends on the first interior node alone, and
+// the tile holding a wall column also holds that node (x = 1 or nx - 2), so
+// the result is the column pass's, without its strided sweep over 24 planes.
+// Rows (bottom/top walls) are still updated by their own pass after each step,
+// before the columns, as the corners belong to the columns.
+template <class Store, bool GRAIN, bool WRITE_FB, int TYV, bool XWALL = false>
 __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __restrict__ src,
                                              const void* __restrict__ srcf, void* __restrict__ dst,
                                              void* __restrict__ dstf, float* __restrict__ hist,
                                              const uint8_t* __restrict__ grain, float* __restrict__ fb, int x0,
-                                             int y0, float (&fs)[5][TYV + 2][TX + 2], float (&ps)[TYV + 2][TX + 2])
+                                             int y0, float (&fs)[5][TYV + 2][TX + 2], float (&ps)[TYV + 2][TX + 2],
+                                             int xfix = 0)
 {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const long long plane = P.plane;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < P.nx && y < P.ny;
+    // XWALL: C, H and flow populations of the tile's own wall nodes, computed
+    // first, while no other values are held in registers
+    const bool xwall_tile = XWALL && xfix && !P.periodic_x && (x0 == 0 || x0 + TX + 1 >= P.nx);
+    __shared__ float wnb[XWALL ? 2 : 1][XWALL ? TYV : 1][19];
+    if constexpr (XWALL) {
+        static_assert(2 * (TYV + 2) <= TX * TYV && 2 * TYV <= TX * TYV, "wall-repair thread ranges");
+        const int tid = ty * TX + tx;
+        if (xwall_tile && tid < 2 * TYV) {
+            const int side = tid / TYV, r = tid % TYV;
+            const int xw = side == 0 ? 0 : P.nx - 1, xi = side == 0 ? 1 : P.nx - 2;
+            const int yw = y0 + r;
+            if (xw >= x0 && xw < x0 + TX && yw < P.ny) {
+                const long long oi = (long long)yw * P.pitch + xi;
+                float fi[5], ni[5], gi[5], hi[9], nbw[5], gbw[5], hbw[9];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) fi[i] = Store::load(src, srcf, kF + i, oi, P);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) ni[i] = Store::load(src, srcf, kN + i, oi, P);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) gi[i] = Store::load(src, srcf, kG + i, oi, P);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) hi[i] = Store::load(src, srcf, kH + i, oi, P);
+                const Macro mi = node_macros(fi, ni, gi, hi, P);
+                wall_rest(P, 0, P.bc[side], mi, ni, gi, hi, nbw, gbw, hbw, 0);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) wnb[side][r][i] = nbw[i];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) wnb[side][r][5 + i] = gbw[i];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) wnb[side][r][10 + i] = hbw[i];
+            }
+        }
+        if (xwall_tile) __syncthreads();  // keeps the loads below after the repair
+    }
     // own-node loads first, so that they are in flight while the tile loads
     const long long o = active ? (long long)y * P.pitch + x : 0;
     float n[5], g[5], h[9];
@@ -248,6 +358,43 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
     }
     __syncthreads();
 
+    if constexpr (XWALL) {
+        if (xwall_tile) {
+            // (side, row) of each wall column the tile holds: x = 0 (side 0)
+            // at tile column 1 - x0, x = nx - 1 (side 1) at nx - x0
+            const int tid = ty * TX + tx;
+            if (tid < 2 * (TYV + 2)) {
+                // phase-field populations and phi of a wall cell of the tile or its halo rows
+                const int side = tid / (TYV + 2), hy = tid % (TYV + 2);
+                const int hx = side == 0 ? 1 - x0 : P.nx - x0;
+                if (hx >= 0 && hx <= TX + 1) {
+                    const int hf = side == 0 ? hx + 1 : hx - 1;  // the interior node, never a wall (nx >= 4)
+                    float ff[5], fbw[5];
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) ff[i] = fs[i][hy][hf];
+                    wall_phi(P, P.bc[side], ff, ff[0] + ff[1] + ff[2] + ff[3] + ff[4], fbw);
+                    float sum = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        fs[i][hy][hx] = fbw[i];
+                        sum += fbw[i];
+                    }
+                    ps[hy][hx] = sum;
+                }
+            }
+            __syncthreads();
+            if (active && (x == 0 || x == P.nx - 1)) {
+                const int side = x == 0 ? 0 : 1;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) n[i] = wnb[side][ty][i];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) g[i] = wnb[side][ty][5 + i];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) h[i] = wnb[side][ty][10 + i];
+            }
+        }
+    }
+
     if (!active) return;
     float f[5];
 #pragma unroll
@@ -257,16 +404,16 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
                                                           grain != nullptr, gid, fs, ps);
 }
 
-template <class Store, bool GRAIN, bool WRITE_FB>
+template <class Store, bool GRAIN, bool WRITE_FB, bool XWALL = false>
 __global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
     k_coupled_step(const StepParams P, const void* __restrict__ src, const void* __restrict__ srcf,
                    void* __restrict__ dst, void* __restrict__ dstf, float* __restrict__ hist,
-                   const uint8_t* __restrict__ grain, float* __restrict__ fb)
+                   const uint8_t* __restrict__ grain, float* __restrict__ fb, int xfix = 0)
 {
     __shared__ float fs[5][TY + 2][TX + 2];
     __shared__ float ps[TY + 2][TX + 2];
-    coupled_tile<Store, GRAIN, WRITE_FB, TY>(P, src, srcf, dst, dstf, hist, grain, fb, blockIdx.x * TX,
-                                             blockIdx.y * TY, fs, ps);
+    coupled_tile<Store, GRAIN, WRITE_FB, TY, XWALL>(P, src, srcf, dst, dstf, hist, grain, fb, blockIdx.x * TX,
+                                                    blockIdx.y * TY, fs, ps, xfix);
 }
 
 // ------------------------------------------------------- TMA-staged variant
@@ -575,7 +722,7 @@ __constant__ DomainDesc c_batch_desc[kMaxBatchDomains];
 // the domain and their halos stay in L2.  A kernel boundary separates steps.
 template <class Store, int TYV>
 __global__ void __launch_bounds__(TX* TYV, (LBM_BATCH_WARPS / TYV > 0 ? LBM_BATCH_WARPS / TYV : 1))
-    k_batch_step(const int4* __restrict__ tiles, int ntiles, int chunk, int parity)
+    k_batch_step(const int4* __restrict__ tiles, int ntiles, int chunk, int parity, int xfix)
 {
     __shared__ float fs[5][TYV + 2][TX + 2];
     __shared__ float ps[TYV + 2][TX + 2];
@@ -583,8 +730,9 @@ __global__ void __launch_bounds__(TX* TYV, (LBM_BATCH_WARPS / TYV > 0 ? LBM_BATC
     for (int t = blockIdx.x * chunk; t < t_end; ++t) {
         const int4 tl = tiles[t];
         const DomainDesc& d = c_batch_desc[tl.x];
-        coupled_tile<Store, true, false, TYV>(d.P, d.sc[parity], d.fl[parity], d.sc[1 - parity],
-                                              d.fl[1 - parity], d.hist, d.grain, nullptr, tl.y, tl.z, fs, ps);
+        coupled_tile<Store, true, false, TYV, true>(d.P, d.sc[parity], d.fl[parity], d.sc[1 - parity],
+                                                    d.fl[1 - parity], d.hist, d.grain, nullptr, tl.y, tl.z, fs, ps,
+                                                    xfix);
         __syncthreads();  // the tile arrays are reused by the next tile
     }
 }
@@ -628,10 +776,6 @@ __global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const 
     for (int i = 0; i < 9; ++i) Store::store(nullptr, dst, kH + i, d9[i], ho[i], P);
 }
 
-// Non-equilibrium extrapolation (Guo et al.) on one side pair, applied to the
-// freshly streamed buffer: pop(b) = pop^eq(boundary macros) + pop(f) -
-// pop^eq(macros of f), f the first interior node.  `axis` 1: bottom/top rows
-// over x in [xlo, xhi]; `axis` 0: left/right columns over every y.
 template <class Store>
 __device__ __forceinline__ void wall_node(const StepParams& P, void* __restrict__ pop, void* __restrict__ popf,
                                           int axis, int which, int j, int flow_only)
@@ -660,48 +804,18 @@ __device__ __forceinline__ void wall_node(const StepParams& P, void* __restrict_
     for (int i = 0; i < 9; ++i) h[i] = Store::load(pop, popf, kH + i, of, P);
     const Macro m = node_macros(f, n, g, h, P);
     const int type = P.bc[side];
-    float ubx = 0.0f, uby = 0.0f, pb = m.p;
-    if (type == 1) {  // inflow
-        ubx = P.uin_x;
-        uby = P.uin_y;
-    } else if (type == 2) {  // outflow
-        ubx = m.ux;
-        uby = m.uy;
-        pb = 0.0f;
-    } else if (type == 3) {  // symmetry
-        ubx = axis == 0 ? 0.0f : m.ux;
-        uby = axis == 0 ? m.uy : 0.0f;
-    }
-    float eb[9], ef[9];
-    deq_flow(pb, ubx, uby, eb);
-    deq_flow(m.p, m.ux, m.uy, ef);
+    float fb[5], nb[5], gb[5], hb[9];
+    wall_rest(P, axis, type, m, n, g, h, nb, gb, hb, flow_only);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store::store(pop, popf, kH + i, ob, eb[i] + h[i] - ef[i], P);
+    for (int i = 0; i < 9; ++i) Store::store(pop, popf, kH + i, ob, hb[i], P);
     if (flow_only) return;
-
-    float p1b = m.p1, dCb = m.dC, Ub = m.U, dthb = m.dth;
-    if (type == 5) {  // Dirichlet far field
-        p1b = P.dir_phi + 1.0f;
-        Ub = P.dir_U;
-        dCb = dC_of(Ub, p1b, P.k);
-        dthb = P.dir_theta - P.theta_ref;
-    }
-    const float hp1b = h_plus_1(P.h_kind, p1b);
-    const float Hb = (P.theta_ref + P.latent) + dthb - P.latent * hp1b;
-    const float Cb = 1.0f + dCb, Cf = 1.0f + m.dC;
-    const float sc = P.nsub;
-    deq_phi(p1b, eb);
-    deq_phi(m.p1, ef);
+    wall_phi(P, type, f, m.p1, fb);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(pop, popf, kF + i, ob, eb[i] + f[i] - ef[i], P);
-    deq_C(dCb, (1.0f - 0.5f * p1b) * Ub, Cb * ubx * sc, Cb * uby * sc, eb);
-    deq_C(m.dC, (1.0f - 0.5f * m.p1) * m.U, Cf * m.ux * sc, Cf * m.uy * sc, ef);
+    for (int i = 0; i < 5; ++i) Store::store(pop, popf, kF + i, ob, fb[i], P);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(pop, popf, kN + i, ob, eb[i] + n[i] - ef[i], P);
-    deq_H(dthb, P.latent * hp1b, Hb * ubx * sc, Hb * uby * sc, eb);
-    deq_H(m.dth, P.latent * m.hp1, m.H * m.ux * sc, m.H * m.uy * sc, ef);
+    for (int i = 0; i < 5; ++i) Store::store(pop, popf, kN + i, ob, nb[i], P);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(pop, popf, kG + i, ob, eb[i] + g[i] - ef[i], P);
+    for (int i = 0; i < 5; ++i) Store::store(pop, popf, kG + i, ob, gb[i], P);
 }
 
 template <class Store>
@@ -727,15 +841,17 @@ __global__ void k_batch_walls(const DomainDesc* __restrict__ descs, const int4* 
     wall_node<Store>(d.P, d.sc[parity], d.fl[parity], e.y, e.z, e.w, 0);
 }
 
+// Rows (bottom/top walls, x in [1, nx - 2] when x is not periodic), then,
+// with `columns`, the left/right columns over every y (corners included).
 template <class Store>
-cudaError_t walls(const StepParams& P, void* sc, void* fl, int flow_only, cudaStream_t s)
+cudaError_t walls(const StepParams& P, void* sc, void* fl, int flow_only, cudaStream_t s, bool columns = true)
 {
     if (!P.periodic_y) {
         const int lo = P.periodic_x ? 0 : 1, hi = P.periodic_x ? P.nx - 1 : P.nx - 2;
         const int count = hi - lo + 1;
         k_walls<Store><<<(2 * count + 127) / 128, 128, 0, s>>>(P, sc, fl, 1, lo, count, flow_only);
     }
-    if (!P.periodic_x) {
+    if (!P.periodic_x && columns) {
         k_walls<Store><<<(2 * P.ny + 127) / 128, 128, 0, s>>>(P, sc, fl, 0, 0, P.ny, flow_only);
     }
     return cudaGetLastError();
@@ -821,7 +937,7 @@ cudaError_t tma16_attributes()
 }
 
 template <class Store>
-cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStream_t s)
+cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStream_t s, int repair, int skip_columns)
 {
     const dim3 block(TX, TY), grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
     const void* src = B.sc[B.cs];
@@ -873,8 +989,20 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
                     <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
         }
     }
+    // left/right walls: with skip_columns their column pass is left out and
+    // the next step, launched with `repair`, updates them at its load
+    // (coupled_tile); only the tiled kernel with one flow step per coupled
+    // step does that, the other paths keep the column pass
+    const bool xwall = !staged && !wfb && !P.periodic_x;
+    const int xfix = xwall ? repair : 0;
     if (staged)
         ;  // the TMA-staged kernel above
+    else if (xwall && grain)
+        k_coupled_step<Store, true, false, true>
+            <<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb, xfix);
+    else if (xwall)
+        k_coupled_step<Store, false, false, true>
+            <<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb, xfix);
     else if (grain && wfb)
         k_coupled_step<Store, true, true><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
     else if (grain)
@@ -886,7 +1014,7 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (B.ev_end) cudaEventRecord(B.ev_end, s);
-    if ((e = walls<Store>(P, dst, dstf, 0, s)) != cudaSuccess) return e;
+    if ((e = walls<Store>(P, dst, dstf, 0, s, !(xwall && skip_columns))) != cudaSuccess) return e;
     B.cs = 1 - B.cs;
     B.cf = 1 - B.cf;
     const dim3 fblock(64, 4), fgrid((P.nx + 63) / 64, (P.ny + 3) / 4);
@@ -903,33 +1031,37 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
 
 // run: tiles per CTA; 0 makes the grid persistent (one contiguous run of
 // tiles per resident CTA).
+// repair / skip_columns: as for the single-domain step; the column list holds
+// the left/right walls of every domain that is not periodic in x.
 template <class Store, int TYV>
-cudaError_t batch_step_t(const BatchTables& T, int parity, int ctas, int run, cudaStream_t s)
+cudaError_t batch_step_t(const BatchTables& T, int parity, int ctas, int run, cudaStream_t s, int repair,
+                         int skip_columns)
 {
     const int k = TYV == 4 ? 0 : TYV == 8 ? 1 : 2;
     const int chunk = run > 0 ? run : (T.ntiles[k] + ctas - 1) / ctas;
     const int grid = (T.ntiles[k] + chunk - 1) / chunk;
-    k_batch_step<Store, TYV><<<grid, dim3(TX, TYV), 0, s>>>(T.tiles[k], T.ntiles[k], chunk, parity);
+    k_batch_step<Store, TYV><<<grid, dim3(TX, TYV), 0, s>>>(T.tiles[k], T.ntiles[k], chunk, parity, repair);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // the fused kernel wrote buffers 1 - parity; walls act on those
+    // the fused kernel wrote buffers 1 - parity; walls act on those (rows, then columns)
     if (T.nwall[0])
         k_batch_walls<Store><<<(T.nwall[0] + 127) / 128, 128, 0, s>>>(T.descs, T.walls[0], T.nwall[0], 1 - parity);
-    if (T.nwall[1])
+    if (T.nwall[1] && !skip_columns)
         k_batch_walls<Store><<<(T.nwall[1] + 127) / 128, 128, 0, s>>>(T.descs, T.walls[1], T.nwall[1], 1 - parity);
     return cudaGetLastError();
 }
 
 template <class Store>
-cudaError_t batch_step_store(const BatchTables& T, int ty, int parity, int ctas, int run, cudaStream_t s)
+cudaError_t batch_step_store(const BatchTables& T, int ty, int parity, int ctas, int run, cudaStream_t s,
+                             int repair, int skip_columns)
 {
     cudaError_t e = cudaMemcpyToSymbolAsync(c_batch_desc, T.descs, sizeof(DomainDesc) * T.ndomains, 0,
                                             cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     switch (ty) {
-    case 4: return batch_step_t<Store, 4>(T, parity, ctas, run, s);
-    case 16: return batch_step_t<Store, 16>(T, parity, ctas, run, s);
-    default: return batch_step_t<Store, 8>(T, parity, ctas, run, s);
+    case 4: return batch_step_t<Store, 4>(T, parity, ctas, run, s, repair, skip_columns);
+    case 16: return batch_step_t<Store, 16>(T, parity, ctas, run, s, repair, skip_columns);
+    default: return batch_step_t<Store, 8>(T, parity, ctas, run, s, repair, skip_columns);
     }
 }
 
@@ -1026,12 +1158,12 @@ cudaError_t step_error(int* flag, bool clear)
 }
 
 cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int run, int parity, int ctas,
-                              cudaStream_t s)
+                              cudaStream_t s, int repair, int skip_columns)
 {
     switch (storage) {
-    case kStoreF16: return batch_step_store<StoreF16>(T, ty, parity, ctas, run, s);
-    case kStoreBF16: return batch_step_store<StoreBF16>(T, ty, parity, ctas, run, s);
-    default: return batch_step_store<StoreF32>(T, ty, parity, ctas, run, s);
+    case kStoreF16: return batch_step_store<StoreF16>(T, ty, parity, ctas, run, s, repair, skip_columns);
+    case kStoreBF16: return batch_step_store<StoreBF16>(T, ty, parity, ctas, run, s, repair, skip_columns);
+    default: return batch_step_store<StoreF32>(T, ty, parity, ctas, run, s, repair, skip_columns);
     }
 }
 
@@ -1052,12 +1184,13 @@ cudaError_t flow_steps(const StepParams& P, int storage, int n, void* sc, void* 
     }
 }
 
-cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s)
+cudaError_t launch_coupled_step(const StepParams& P, int storage, int n_sub, StepBuffers& B, cudaStream_t s,
+                                int repair, int skip_columns)
 {
     switch (storage) {
-    case kStoreF16: return coupled_step<StoreF16>(P, n_sub, B, s);
-    case kStoreBF16: return coupled_step<StoreBF16>(P, n_sub, B, s);
-    default: return coupled_step<StoreF32>(P, n_sub, B, s);
+    case kStoreF16: return coupled_step<StoreF16>(P, n_sub, B, s, repair, skip_columns);
+    case kStoreBF16: return coupled_step<StoreBF16>(P, n_sub, B, s, repair, skip_columns);
+    default: return coupled_step<StoreF32>(P, n_sub, B, s, repair, skip_columns);
     }
 }
 
