@@ -185,7 +185,10 @@ LBM_API int lbm_init_fields(lbm_handle* h, const double* fields, const double* o
 /* Queue `nsteps` coupled time steps (the fused stream-collide kernel of all
  * four models, then the wall kernels, then n_sub - 1 flow-only sub-steps) on
  * the handle's stream and return without waiting.  Long runs are replayed
- * from a captured CUDA graph. */
+ * from captured 16-step CUDA graphs; inside one (n_sub = 1, tiled kernel) the
+ * left/right walls of a step are updated by the next step as it loads them,
+ * and the last step of the graph runs the wall kernels in full, so the state
+ * seen between calls is always complete. */
 LBM_API int lbm_step(lbm_handle* h, int nsteps);
 
 /* Wait for all queued work of h; reports an asynchronous CUDA error, and

@@ -15,8 +15,10 @@
 //   6. history (phi, Q, Cu, Hu at time n) is written in place for the
 //      backward time differences of the next step.
 // Periodic wrap is applied to every streaming destination; on non-periodic
-// sides the wrapped values land on wall nodes, which the wall kernel then
-// overwrites completely.
+// sides the wrapped values land on wall nodes, which the wall scheme then
+// overwrites completely: the wall kernel after the step, or, for the left and
+// right walls of steps inside a captured step graph, the next step as it
+// loads them (coupled_tile).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
