@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -117,20 +118,27 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and whitespace (string literals in these
+    files hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return "".join(text.split())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the tiled fused kernel's source: the device header and the
-    part of lbm_step.cu up to the end of k_coupled_step (the TMA-staged,
-    batched and flow-only kernels that follow it do not change its
-    traffic)."""
-    h = hashlib.sha256()
+    """Hash of the tiled fused kernel's code: the device header and the part
+    of lbm_step.cu up to the end of k_coupled_step (the TMA-staged, batched
+    and flow-only kernels that follow it do not change its traffic), comments
+    and whitespace left out."""
     csrc = os.path.join(ROOT, "paper_2209_01444_gb300", "csrc")
-    with open(os.path.join(csrc, "lbm_device.cuh"), "rb") as fh:
-        h.update(fh.read())
-    with open(os.path.join(csrc, "lbm_step.cu"), "rb") as fh:
+    with open(os.path.join(csrc, "lbm_device.cuh")) as fh:
+        head = fh.read()
+    with open(os.path.join(csrc, "lbm_step.cu")) as fh:
         text = fh.read()
-    cut = text.find(b"// ------------------------------------------------------- TMA-staged variant")
-    h.update(text if cut < 0 else text[:cut])
-    return h.hexdigest()[:16]
+    cut = text.find("// ------------------------------------------------------- TMA-staged variant")
+    body = text if cut < 0 else text[:cut]
+    return hashlib.sha256((_code_only(head) + _code_only(body)).encode()).hexdigest()[:16]
 
 
 def recorded_traffic(key: str):
