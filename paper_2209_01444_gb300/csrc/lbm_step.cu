@@ -739,12 +739,68 @@ __global__ void __launch_bounds__(TX* TYV, (LBM_BATCH_WARPS / TYV > 0 ? LBM_BATC
     }
 }
 
-// Flow sub-step (two-time-scaling of Sec. 4): collide and stream h with phi
-// and the force frozen at time n.
+// Flow populations the flow-only wall pass gives a wall node of `side` (axis
+// 0: left/right columns, 1: bottom/top rows) from its interior node at offset
+// oi, whose flow populations are hi: extrapolation with that node's macros,
+// its scalar populations read from sc.
 template <class Store>
-__global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const void* __restrict__ src,
+__device__ __forceinline__ void flow_wall_from(const StepParams& P, const void* __restrict__ sc, int axis, int side,
+                                               long long oi, const float (&hi)[9], float (&hb)[9])
+{
+    float fi[5], ni[5], gi[5], nb[5], gb[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) fi[i] = Store::load(sc, nullptr, kF + i, oi, P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ni[i] = Store::load(sc, nullptr, kN + i, oi, P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gi[i] = Store::load(sc, nullptr, kG + i, oi, P);
+    const Macro m = node_macros(fi, ni, gi, hi, P);
+    wall_rest(P, axis, P.bc[side], m, ni, gi, hi, nb, gb, hb, 1);
+}
+
+// The flow populations the flow-only wall pass (rows, then columns) would
+// have left at wall node (x, y) after the previous flow step, which skipped
+// it: a row node from its interior node; a column node from its interior
+// node; a corner from the row node beside it as the row pass leaves it.
+template <class Store>
+__device__ __forceinline__ void flow_wall_repair(const StepParams& P, const void* __restrict__ sc,
+                                              const void* __restrict__ src, int x, int y, bool wx, bool wy,
+                                              float (&h)[9])
+{
+    const int xi = x == 0 ? 1 : P.nx - 2, yi = y == 0 ? 1 : P.ny - 2;
+    const int row_side = y == 0 ? 2 : 3, col_side = x == 0 ? 0 : 1;
+    float hi[9];
+    if (!wx) {
+        const long long oi = (long long)yi * P.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) hi[i] = Store::load(nullptr, src, kH + i, oi, P);
+        flow_wall_from<Store>(P, sc, 1, row_side, oi, hi, h);
+        return;
+    }
+    const long long oc = (long long)y * P.pitch + xi;
+    if (wy) {
+        const long long oi = (long long)yi * P.pitch + xi;
+        float hr[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) hr[i] = Store::load(nullptr, src, kH + i, oi, P);
+        flow_wall_from<Store>(P, sc, 1, row_side, oi, hr, hi);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) hi[i] = Store::load(nullptr, src, kH + i, oc, P);
+    }
+    flow_wall_from<Store>(P, sc, 0, col_side, oc, hi, h);
+}
+
+// Flow sub-step (two-time-scaling of Sec. 4): collide and stream h with phi
+// and the force frozen at time n.  repair: the previous flow step skipped the
+// flow-only wall pass, so wall nodes first take the populations it would have
+// given them (flow_wall_repair; sc holds the newest scalar populations, whose
+// macros the wall scheme uses).
+template <class Store>
+__global__ void __launch_bounds__(256, 8) k_flow_substep(const StepParams P, const void* __restrict__ src,
                                                       void* __restrict__ dst, const float* __restrict__ hist,
-                                                      const float* __restrict__ fb)
+                                                      const float* __restrict__ fb, const void* __restrict__ sc,
+                                                      int repair)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -753,6 +809,11 @@ __global__ void __launch_bounds__(256) k_flow_substep(const StepParams P, const 
     float h[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] = Store::load(nullptr, src, kH + i, o, P);
+    if (repair) {
+        const bool wx = !P.periodic_x && (x == 0 || x == P.nx - 1);
+        const bool wy = !P.periodic_y && (y == 0 || y == P.ny - 1);
+        if (wx || wy) flow_wall_repair<Store>(P, sc, src, x, y, wx, wy, h);
+    }
     Macro m;
     m.phi = hist[o];
     m.p1 = m.phi + 1.0f;
@@ -866,9 +927,11 @@ cudaError_t flow_steps_t(const StepParams& P, int n, void* sc, void* const fl[2]
     const dim3 fblock(64, 4), fgrid((P.nx + 63) / 64, (P.ny + 3) / 4);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < n; ++k) {
-        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, fl[*cf], fl[1 - *cf], phi, fy);
+        // wall pass after the last step only; each later step repairs the wall
+        // nodes it loads instead
+        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, fl[*cf], fl[1 - *cf], phi, fy, sc, k > 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = walls<Store>(P, sc, fl[1 - *cf], 1, s)) != cudaSuccess) return e;
+        if (k + 1 == n && (e = walls<Store>(P, sc, fl[1 - *cf], 1, s)) != cudaSuccess) return e;
         *cf = 1 - *cf;
     }
     return e;
@@ -1022,10 +1085,13 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
     const dim3 fblock(64, 4), fgrid((P.nx + 63) / 64, (P.ny + 3) / 4);
     for (int sub = 1; sub < n_sub; ++sub) {
         // phi and the force of time n come from hist/fb; the wall scheme reads
-        // the scalar macros of time n+1 from the newest scalar buffer
-        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, B.fl[B.cf], B.fl[1 - B.cf], B.hist, B.fb);
+        // the scalar macros of time n+1 from the newest scalar buffer.  The
+        // flow-only wall pass runs after the last sub-step only: each later
+        // sub-step repairs the wall nodes it loads instead.
+        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, B.fl[B.cf], B.fl[1 - B.cf], B.hist, B.fb, B.sc[B.cs],
+                                                       sub > 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = walls<Store>(P, B.sc[B.cs], B.fl[1 - B.cf], 1, s)) != cudaSuccess) return e;
+        if (sub + 1 == n_sub && (e = walls<Store>(P, B.sc[B.cs], B.fl[1 - B.cf], 1, s)) != cudaSuccess) return e;
         B.cf = 1 - B.cf;
     }
     return cudaSuccess;

@@ -168,6 +168,27 @@ def test_flow_substeps_and_h_kind(lbm, n_sub, h_kind):
     cp.check()
 
 
+@pytest.mark.parametrize("bcs", ["mixed", "dirichlet", "channel_noslip"])
+def test_flow_substeps_every_wall_type(lbm, bcs):
+    """Flow sub-steps on every wall type, corners included: between sub-steps
+    the wall nodes are updated as the next sub-step loads them (rows from
+    their interior node, columns from theirs, a corner from the row node beside
+    it), and the last sub-step of each coupled step runs the full wall pass."""
+    nx, ny = 45, 38
+    p = W.thermosolutal_params(nx, ny, bc=BCS[bcs], u_in=(0.2, 0.03), n_sub=3, nu=6.0, gbetaT=W.GBETA_T * 5,
+                               theta_ref=-0.5, dir_theta=-0.4)
+    f, orient = W.random_fields(nx, ny, rng_seed=21)
+    g, o = pair(lbm, p)
+    g.init_fields(f, orient)
+    o.init_fields(f, orient)
+    cp = Checkpoints()
+    for T in (1, 2, 30):
+        g.step(T - g.steps)
+        o.step(T - o.steps)
+        cp.add(g.fields(), o.fields(), FP32_TOL, 0.5, f"{bcs} n_sub=3 step {T}")
+    cp.check()
+
+
 def test_metrics_match(lbm):
     c = W.single_seed_periodic()
     g, o = pair(lbm, c.params)
