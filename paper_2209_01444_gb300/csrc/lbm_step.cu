@@ -739,6 +739,18 @@ __global__ void __launch_bounds__(TX* TYV, (LBM_BATCH_WARPS / TYV > 0 ? LBM_BATC
     }
 }
 
+// v as a store to flow plane q and a load would return it (16-bit storage
+// rounds; FP32 keeps v).
+template <class Store>
+__device__ __forceinline__ float stored_flow(int q, float v)
+{
+    if constexpr (std::is_same<Store, StoreF32>::value) {
+        return v;
+    } else {
+        return Conv<typename Store::T>::to(Conv<typename Store::T>::from(v * Store::scale(q))) * Store::inv_scale(q);
+    }
+}
+
 // Flow populations the flow-only wall pass gives a wall node of `side` (axis
 // 0: left/right columns, 1: bottom/top rows) from its interior node at offset
 // oi, whose flow populations are hi: extrapolation with that node's macros,
@@ -775,20 +787,25 @@ __device__ __forceinline__ void flow_wall_repair(const StepParams& P, const void
 #pragma unroll
         for (int i = 0; i < 9; ++i) hi[i] = Store::load(nullptr, src, kH + i, oi, P);
         flow_wall_from<Store>(P, sc, 1, row_side, oi, hi, h);
-        return;
-    }
-    const long long oc = (long long)y * P.pitch + xi;
-    if (wy) {
-        const long long oi = (long long)yi * P.pitch + xi;
-        float hr[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) hr[i] = Store::load(nullptr, src, kH + i, oi, P);
-        flow_wall_from<Store>(P, sc, 1, row_side, oi, hr, hi);
     } else {
+        const long long oc = (long long)y * P.pitch + xi;
+        if (wy) {
+            const long long oi = (long long)yi * P.pitch + xi;
+            float hr[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) hi[i] = Store::load(nullptr, src, kH + i, oc, P);
+            for (int i = 0; i < 9; ++i) hr[i] = Store::load(nullptr, src, kH + i, oi, P);
+            flow_wall_from<Store>(P, sc, 1, row_side, oi, hr, hi);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) hi[i] = stored_flow<Store>(kH + i, hi[i]);  // as the row pass stores it
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) hi[i] = Store::load(nullptr, src, kH + i, oc, P);
+        }
+        flow_wall_from<Store>(P, sc, 0, col_side, oc, hi, h);
     }
-    flow_wall_from<Store>(P, sc, 0, col_side, oc, hi, h);
+    // as the wall pass would store them and this step's load return them
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = stored_flow<Store>(kH + i, h[i]);
 }
 
 // Flow sub-step (two-time-scaling of Sec. 4): collide and stream h with phi

@@ -122,10 +122,12 @@ def test_walls_repaired_at_load_match_the_column_pass(lbm, bcs, storage):
     by the next step as it loads them, instead of by the column pass.  The
     extrapolation depends on the interior node alone, so the states must agree
     with direct launches (column pass after every step) to rounding: the same
-    arithmetic in another kernel.  40 steps = two graphs and a remainder; a
-    grid whose last tile holds only the right wall (nx - 1 = 64), and one
-    narrower than a tile (both walls in one tile)."""
-    for nx, ny in ((65, 37), (29, 24)):
+    arithmetic in another kernel.  40 steps = two graphs and a remainder; grids
+    whose last tile holds only the right wall (nx - 1 = 64 or 32, the latter
+    also in the previous tile's halo column), one without a right wall in
+    its last tile's own columns (nx = 40), and one narrower than a tile (both
+    walls in one tile)."""
+    for nx, ny in ((65, 37), (29, 24), (40, 41), (33, 33)):
         bc = ("symmetry", "noslip", "periodic", "periodic") if bcs == "side_walls" else BCS[bcs]
         p = W.thermosolutal_params(nx, ny, bc=bc, u_in=(0.08, 0.01), gbetaT=W.GBETA_T * 5, dir_theta=-0.4)
         f, orient = W.random_fields(nx, ny, rng_seed=5 + nx)
