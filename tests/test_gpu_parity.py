@@ -207,11 +207,9 @@ def test_reduced_precision_with_dirichlet_walls(lbm):
     """FP16 storage with Dirichlet walls on all sides (the far field of Sec.
     4.4) from a seeded start: within the 16-bit bound at every checkpoint.
     (From a random start whose phi meets the wall's value within one node, FP16
-    shows a transient of up to 3e-2 at steps 2-3 next to the walls, gone by
-    step 5; periodic walls show none.  The wall nodes hold phi = dir_phi exactly
-    in the oracle, so its gradient along the wall is zero and a_s = 1 there,
-    while their 16-bit values leave a small gradient and a direction-dependent
-    a_s, which the modified streaming (Eq. 13) carries into the next node.)"""
+    shows a transient of up to 3e-2 at steps 2-3 next to the walls, down to
+    2e-3 by step 5; periodic walls from the same start and FP32 storage show
+    none.  Its cause is not identified.)"""
     nx, ny = 45, 38
     p = W.thermosolutal_params(nx, ny, bc=BCS["dirichlet"], dir_theta=-0.5, theta_ref=-0.5)
     seeds = np.array([[22.0, 19.0, 6.0, 0.3]])
