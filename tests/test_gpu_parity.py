@@ -209,7 +209,8 @@ def test_reduced_precision_with_dirichlet_walls(lbm):
     (From a random start whose phi meets the wall's value within one node, FP16
     shows a transient of up to 3e-2 at steps 2-3 next to the walls, down to
     2e-3 by step 5; periodic walls from the same start and FP32 storage show
-    none.  Its cause is not identified.)"""
+    none.  The oracle with the same 16-bit rounding of its state shows it too:
+    test_fp16_storage_matches_the_oracle_with_fp16_storage.)"""
     nx, ny = 45, 38
     p = W.thermosolutal_params(nx, ny, bc=BCS["dirichlet"], dir_theta=-0.5, theta_ref=-0.5)
     seeds = np.array([[22.0, 19.0, 6.0, 0.3]])
@@ -224,6 +225,62 @@ def test_reduced_precision_with_dirichlet_walls(lbm):
         keep = ("phi", "C", "theta")
         cp.add({k: got[k] for k in keep}, {k: want[k] for k in keep}, LOWP_TOL, 0.5, f"dirichlet fp16 step {T}")
     cp.check()
+
+
+def _round_like_fp16_storage(o, params):
+    """Round an oracle state as the equilibrium-shifted FP16 storage does:
+    each population's deviation from the equilibrium of the liquid at rest
+    (phi = -1, C = 1, theta = theta_ref, p = 0, u = 0) is scaled (16 for the
+    scalar models, 1024 for the flow), rounded to FP16 and scaled back; the
+    three scalar rest populations and the history keep FP32."""
+    w5 = np.array([1 / 3, 1 / 6, 1 / 6, 1 / 6, 1 / 6])
+    ref = np.zeros(24)
+    ref[0:5] = -w5
+    ref[5] = 1.0
+    ref[10:15] = w5 * params["theta_ref"]
+    ref[10] += 0.5 * (1 - params.get("isothermal", 0))
+    ref[15] = params["rho0"]
+    st = o.state()
+    for q in range(24):
+        dev = (st[q] - ref[q]).astype(np.float32)
+        if q in (0, 5, 10):
+            st[q] = ref[q] + dev.astype(np.float64)
+        else:
+            sc = np.float32(1024.0 if q >= 15 else 16.0)
+            st[q] = ref[q] + (np.float16(dev * sc).astype(np.float32) / sc).astype(np.float64)
+    st[24:] = st[24:].astype(np.float32).astype(np.float64)
+    o.set_state(st)
+
+
+@pytest.mark.parametrize("bcs", ["dirichlet", "periodic"])
+def test_fp16_storage_matches_the_oracle_with_fp16_storage(lbm, bcs):
+    """The FP16 path against the FP64 oracle whose state is rounded as the
+    FP16 storage rounds it after every step: the two agree far below the
+    16-bit error itself.  The Dirichlet case from this random start is where
+    FP16 storage departs most from the unrounded oracle (3e-2 at step 2, next
+    to the walls); the rounded oracle shows the same departure, so it is a
+    property of 16-bit storage of this state, not of the kernels."""
+    nx, ny = 45, 38
+    p = W.thermosolutal_params(nx, ny, bc=BCS[bcs], u_in=(0.2, 0.03), gbetaT=W.GBETA_T * 5, theta_ref=-0.5,
+                               dir_theta=-0.4)
+    f, orient = W.random_fields(nx, ny, rng_seed=21)
+    g = lbm.Simulation(p, "fp16")
+    o, r = O.Oracle(p), O.Oracle(p)
+    g.init_fields(f, orient)
+    o.init_fields(f, orient)
+    r.init_fields(f, orient)
+    _round_like_fp16_storage(r, p)
+    keep = ("phi", "C", "theta")
+    for T in range(1, 6):
+        g.step(1)
+        o.step(1)
+        r.step(1)
+        _round_like_fp16_storage(r, p)
+        G, Ro, Rr = g.fields(), o.fields(), r.fields()
+        vs_rounded = field_errors({k: G[k] for k in keep}, {k: Rr[k] for k in keep})
+        vs_plain = field_errors({k: G[k] for k in keep}, {k: Ro[k] for k in keep})
+        print(bcs, T, {k: f"{vs_rounded[k]:.1e} / {vs_plain[k]:.1e}" for k in keep})
+        assert max(vs_rounded.values()) <= 2e-3, (T, vs_rounded, vs_plain)
 
 
 def test_metrics_match(lbm):
