@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
+import storage_emulation as SE
 from paper_2209_01444_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -227,31 +228,6 @@ def test_reduced_precision_with_dirichlet_walls(lbm):
     cp.check()
 
 
-def _round_like_fp16_storage(o, params):
-    """Round an oracle state as the equilibrium-shifted FP16 storage does:
-    each population's deviation from the equilibrium of the liquid at rest
-    (phi = -1, C = 1, theta = theta_ref, p = 0, u = 0) is scaled (16 for the
-    scalar models, 1024 for the flow), rounded to FP16 and scaled back; the
-    three scalar rest populations and the history keep FP32."""
-    w5 = np.array([1 / 3, 1 / 6, 1 / 6, 1 / 6, 1 / 6])
-    ref = np.zeros(24)
-    ref[0:5] = -w5
-    ref[5] = 1.0
-    ref[10:15] = w5 * params["theta_ref"]
-    ref[10] += 0.5 * (1 - params.get("isothermal", 0))
-    ref[15] = params["rho0"]
-    st = o.state()
-    for q in range(24):
-        dev = (st[q] - ref[q]).astype(np.float32)
-        if q in (0, 5, 10):
-            st[q] = ref[q] + dev.astype(np.float64)
-        else:
-            sc = np.float32(1024.0 if q >= 15 else 16.0)
-            st[q] = ref[q] + (np.float16(dev * sc).astype(np.float32) / sc).astype(np.float64)
-    st[24:] = st[24:].astype(np.float32).astype(np.float64)
-    o.set_state(st)
-
-
 @pytest.mark.parametrize("bcs", ["dirichlet", "periodic"])
 def test_fp16_storage_matches_the_oracle_with_fp16_storage(lbm, bcs):
     """The FP16 path against the FP64 oracle whose state is rounded as the
@@ -269,13 +245,13 @@ def test_fp16_storage_matches_the_oracle_with_fp16_storage(lbm, bcs):
     g.init_fields(f, orient)
     o.init_fields(f, orient)
     r.init_fields(f, orient)
-    _round_like_fp16_storage(r, p)
+    SE.round_state(r, p, "fp16")
     keep = ("phi", "C", "theta")
     for T in range(1, 6):
         g.step(1)
         o.step(1)
         r.step(1)
-        _round_like_fp16_storage(r, p)
+        SE.round_state(r, p, "fp16")
         G, Ro, Rr = g.fields(), o.fields(), r.fields()
         vs_rounded = field_errors({k: G[k] for k in keep}, {k: Rr[k] for k in keep})
         vs_plain = field_errors({k: G[k] for k in keep}, {k: Ro[k] for k in keep})
