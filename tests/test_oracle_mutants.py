@@ -16,13 +16,17 @@ import subprocess
 
 import pytest
 
+import test_oracle_force
 import test_oracle_pins as pins
 from oracle import oracle as O
+
+MODULES = {"pins": pins, "force": test_oracle_force}
 
 SRC = os.path.join(os.path.dirname(O.__file__), "lbm_oracle.c")
 
 # name -> (the part of the method it breaks, original text, mistaken text, pins
-# as (test name, arguments)); each original text occurs exactly once.
+# as (test name, arguments), a name from test_oracle_force as "force:test");
+# each original text occurs exactly once.
 MUTANTS = {
     "d2q5_weights": (
         "D2Q5 weights (reading: w0 = 1/3 from cs^2 = 1/3)",
@@ -135,12 +139,28 @@ MUTANTS = {
         "Eq. 19, the backward difference of C u without its previous value",
         "s->Cu_prev[idx] = s->C[idx] * usx;", "s->Cu_prev[idx] = 0.0;",
         [("test_scalar_models_advect_with_the_flow", (0.1,))]),
+    "h_kind1_coefficient": (
+        "Sec. 2, the second h(phi) with 2 phi^3/3 written phi^3/3",
+        "return 15.0 / 8.0 * (phi - 2.0 * p3 / 3.0 + p3 * phi * phi / 5.0);",
+        "return 15.0 / 8.0 * (phi - p3 / 3.0 + p3 * phi * phi / 5.0);",
+        [("test_second_interpolation_function_releases_heat_by_its_closed_form", ())]),
+    "local_grad_anisotropy_sign": (
+        "Sec. 3.1, sign of the anisotropic term in the local grad(phi) scheme",
+        "gx = -s1 / CS2 * (jx + s->kappa0 * nx_);",
+        "gx = -s1 / CS2 * (jx - s->kappa0 * nx_);",
+        [("force:test_local_gradient_scheme_matches_stencil", ())]),
     "U_of_C_sign": (
         "Eq. 20, sign of the (1 - k) phi term",
         "return (2.0 * C / (1.0 + k - (1.0 - k) * phi) - 1.0) / (1.0 - k);",
         "return (2.0 * C / (1.0 + k + (1.0 - k) * phi) - 1.0) / (1.0 - k);",
         [("test_initial_supersaturation_round_trips", ())]),
 }
+
+
+def _pin(name):
+    """A pin by name: `test_x` from the pin module, or `module:test_x`."""
+    mod, _, test = name.rpartition(":")
+    return getattr(MODULES[mod or "pins"], test)
 
 
 @pytest.fixture(scope="module")
@@ -174,7 +194,7 @@ def test_pins_catch_the_mutant(name, mutant_libs, monkeypatch):
     failed = []
     for test, args in checks:
         try:
-            getattr(pins, test)(*args)
+            _pin(test)(*args)
         except AssertionError:
             failed.append(test)
     assert failed, f"no pin caught the mistake in {what}"
@@ -196,4 +216,4 @@ def test_unmutated_copy_passes_the_same_pins(tmp_path, monkeypatch):
         for test, args in checks:
             if (test, args) not in seen:
                 seen.add((test, args))
-                getattr(pins, test)(*args)
+                _pin(test)(*args)

@@ -451,6 +451,39 @@ def test_quasi_uniform_phase_field_follows_the_discrete_recurrence():
         assert o.fields()["phi"].mean() == pytest.approx(ph[T], abs=2e-6)
 
 
+def test_second_interpolation_function_releases_heat_by_its_closed_form():
+    """h_kind = 1, the second h(phi) of Sec. 2: h = 15/8 (phi - 2 phi^3/3 +
+    phi^5/5), so h(+-1) = +-1 and h' = 15/8 (1 - phi^2)^2.  On a periodic
+    box sum H is conserved (sum g^eq = H, sum G = 0), so with theta = H +
+    h(phi)/2 (Eq. 23) the mean of theta must move by exactly half the mean of
+    h(phi) computed from that polynomial, while phi itself moves (the
+    quasi-uniform field of the recurrence pin)."""
+    nx, eps, lam = 64, 0.2, 0.6
+    p = W.thermosolutal_params(nx, 4, eps_s=eps, lambda_=lam, Mc_inf=0.0, k=0.3, h_kind=1)
+    o = O.Oracle(p)
+    x = np.arange(nx)
+    f = _liquid(nx, 4)
+    f[0] = 0.1 + 3e-4 * np.cos(2 * math.pi * (x + 0.5) / nx)[None, :]
+    f[1] = -0.3
+    f[2] = -0.1
+    o.init_fields(f)
+
+    def h(ph):
+        return 15.0 / 8.0 * (ph - 2.0 * ph**3 / 3.0 + ph**5 / 5.0)
+
+    assert h(1.0) == pytest.approx(1.0, abs=1e-15) and h(-1.0) == pytest.approx(-1.0, abs=1e-15)
+    F0 = o.fields()
+    moved = 0.0
+    for T in (20, 60):
+        o.step(T - o.steps)
+        F = o.fields()
+        moved = max(moved, float(np.abs(F["phi"] - F0["phi"]).max()))
+        d_theta = F["theta"].mean() - F0["theta"].mean()
+        d_h = (h(F["phi"]).mean() - h(F0["phi"]).mean()) / 2
+        assert d_theta == pytest.approx(d_h, abs=1e-13)
+    assert moved > 1e-3
+
+
 def test_seed_profile_is_the_stationary_tanh():
     """The seed profile of Sec. 4 read as tanh[(R - d)/(sqrt2 W0)] is the
     stationary solution of Eq. (1) across a flat interface; on a large seed
