@@ -138,7 +138,7 @@ MUTANTS = {
     "Cu_history_dropped": (
         "Eq. 19, the backward difference of C u without its previous value",
         "s->Cu_prev[idx] = s->C[idx] * usx;", "s->Cu_prev[idx] = 0.0;",
-        [("test_scalar_models_advect_with_the_flow", (0.1,))]),
+        [("test_scalar_models_advect_with_the_flow", (0.1, 1))]),
     "h_kind1_coefficient": (
         "Sec. 2, the second h(phi) with 2 phi^3/3 written phi^3/3",
         "return 15.0 / 8.0 * (phi - 2.0 * p3 / 3.0 + p3 * phi * phi / 5.0);",
@@ -149,6 +149,10 @@ MUTANTS = {
         "gx = -s1 / CS2 * (jx + s->kappa0 * nx_);",
         "gx = -s1 / CS2 * (jx - s->kappa0 * nx_);",
         [("force:test_local_gradient_scheme_matches_stencil", ())]),
+    "nsub_velocity_scale": (
+        "Sec. 4, two-time-scaling: the scalars seeing the flow lattice's velocity, not n_sub times it",
+        "s->nsub_scale = (double)P->n_sub;", "s->nsub_scale = 1.0;",
+        [("test_scalar_models_advect_with_the_flow", (0.02, 2))]),
     "U_of_C_sign": (
         "Eq. 20, sign of the (1 - k) phi term",
         "return (2.0 * C / (1.0 + k - (1.0 - k) * phi) - 1.0) / (1.0 - k);",
