@@ -153,6 +153,10 @@ MUTANTS = {
         "Sec. 4, two-time-scaling: the scalars seeing the flow lattice's velocity, not n_sub times it",
         "s->nsub_scale = (double)P->n_sub;", "s->nsub_scale = 1.0;",
         [("test_scalar_models_advect_with_the_flow", (0.02, 2))]),
+    "dirichlet_solute_zero_gradient": (
+        "Sec. 4.4's far field: the solute on Dirichlet walls copied from the interior",
+        "        Cb = C_of_U(Ub, phib, k);\n", "        Cb = mf.C;\n",
+        [("test_dirichlet_walls_give_the_heat_equation_series_solution", ())]),
     "U_of_C_sign": (
         "Eq. 20, sign of the (1 - k) phi term",
         "return (2.0 * C / (1.0 + k - (1.0 - k) * phi) - 1.0) / (1.0 - k);",

@@ -321,14 +321,18 @@ def test_inflow_outflow_channel_becomes_plug_flow():
 def test_dirichlet_walls_give_the_heat_equation_series_solution():
     """theta held at theta_w on the Dirichlet walls x = 0 and x = L, initially
     theta_1 inside: theta = theta_w + (theta_1 - theta_w) sum_odd 4/(m pi)
-    sin(m pi x/L) exp(-alpha (m pi/L)^2 t)."""
+    sin(m pi x/L) exp(-alpha (m pi/L)^2 t).  The same for the supersaturation
+    U held at U_w (Sec. 4.4's far field): in the liquid C = 1 + (1 - k) U
+    (Eq. 20) diffuses at D, so U follows the same series with D."""
     nx, ny = 41, 4
     p = W.thermosolutal_params(nx, ny, eps_s=0.0, bc=("dirichlet", "dirichlet", "periodic", "periodic"),
-                               dir_theta=-0.2, dir_phi=-1.0, dir_U=0.0)
+                               dir_theta=-0.2, dir_phi=-1.0, dir_U=-0.3)
     o = O.Oracle(p)
     f = _liquid(nx, ny)
     f[2] = -0.6
     f[2][:, 0] = f[2][:, -1] = -0.2
+    f[1] = 0.1
+    f[1][:, 0] = f[1][:, -1] = -0.3
     o.init_fields(f)
     T = 600
     o.step(T)
@@ -340,6 +344,10 @@ def test_dirichlet_walls_give_the_heat_equation_series_solution():
     exact = -0.2 + (-0.6 + 0.2) * series
     assert th[0] == pytest.approx(-0.2, abs=1e-14) and th[-1] == pytest.approx(-0.2, abs=1e-14)
     assert np.abs(th - exact).max() < 2e-3
+    U = o.fields()["U"][1]
+    exact_U = -0.3 + (0.1 + 0.3) * series  # D = alpha here
+    assert U[0] == pytest.approx(-0.3, abs=1e-13) and U[-1] == pytest.approx(-0.3, abs=1e-13)
+    assert np.abs(U - exact_U).max() < 2e-3
 
 
 def test_planar_interface_profile_is_stationary():
