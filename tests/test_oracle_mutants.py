@@ -157,6 +157,10 @@ MUTANTS = {
         "Sec. 4.4's far field: the solute on Dirichlet walls copied from the interior",
         "        Cb = C_of_U(Ub, phib, k);\n", "        Cb = mf.C;\n",
         [("test_dirichlet_walls_give_the_heat_equation_series_solution", ())]),
+    "solutal_buoyancy_sign": (
+        "reading of the external force: sign of the solutal buoyancy",
+        "s->gbC * (C - s->P.C_ref)", "s->gbC * (s->P.C_ref - C)",
+        [("test_solute_rich_melt_moves_with_the_sign_of_the_solutal_coefficient", ())]),
     "U_of_C_sign": (
         "Eq. 20, sign of the (1 - k) phi term",
         "return (2.0 * C / (1.0 + k - (1.0 - k) * phi) - 1.0) / (1.0 - k);",

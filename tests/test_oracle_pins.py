@@ -574,6 +574,30 @@ def test_stencil_gradient_is_the_nine_point_symbol():
         assert np.abs(g[0] + 0.5 * kx * np.sin(phase)).max() < 0.5 * k ** 3
 
 
+def test_solute_rich_melt_moves_with_the_sign_of_the_solutal_coefficient():
+    """The solutal half of the Boussinesq force (reading of the external
+    force): F_y = g beta_C (C - C_ref) with gravity along -y.  With the thermal
+    part off, a blob of higher supersaturation (C above C_ref = 1 in the
+    liquid, Eq. 20) is pushed along -y for g beta_C < 0 and along +y for
+    g beta_C > 0, by the same amount to first order (the flow's advection of
+    the solute it drives is second order)."""
+    n = 32
+    y, x = np.mgrid[0:n, 0:n]
+    uy = []
+    for sign in (1.0, -1.0):
+        p = W.thermosolutal_params(n, n, eps_s=0.0, gbetaT=0.0, gbetaC=sign * 10 * abs(W.GBETA_C),
+                                   bc=("periodic", "periodic", "symmetry", "symmetry"))
+        o = O.Oracle(p)
+        f = _liquid(n, n)
+        f[2] = p["theta_ref"]
+        f[1] = 0.3 * np.exp(-((x - 16) ** 2 + (y - 16) ** 2) / 20.0)
+        o.init_fields(f)
+        o.step(50)
+        uy.append(o.fields()["uy"][16, 16])
+    assert uy[0] > 1e-4 and uy[1] < -1e-4
+    assert uy[0] == pytest.approx(-uy[1], rel=1e-3)
+
+
 # ------------------------------------------------------------- invariants
 def test_periodic_run_conserves_solute_enthalpy_and_flow_mass():
     """Periodic walls: sum C and sum H are conserved (sum n^eq = C, sum g^eq = H,
