@@ -161,6 +161,10 @@ MUTANTS = {
         "reading of the external force: sign of the solutal buoyancy",
         "s->gbC * (C - s->P.C_ref)", "s->gbC * (s->P.C_ref - C)",
         [("test_solute_rich_melt_moves_with_the_sign_of_the_solutal_coefficient", ())]),
+    "dirichlet_phi_zero_gradient": (
+        "Sec. 4.4's far field: phi on Dirichlet walls copied from the interior",
+        "        phib = s->P.dir_phi;\n", "",
+        [("test_dirichlet_walls_hold_the_far_field_values", ())]),
     "U_of_C_sign": (
         "Eq. 20, sign of the (1 - k) phi term",
         "return (2.0 * C / (1.0 + k - (1.0 - k) * phi) - 1.0) / (1.0 - k);",

@@ -350,6 +350,26 @@ def test_dirichlet_walls_give_the_heat_equation_series_solution():
     assert np.abs(U - exact_U).max() < 2e-3
 
 
+def test_dirichlet_walls_hold_the_far_field_values():
+    """Sec. 4.4's far field: after every step the Dirichlet wall nodes carry
+    phi = dir_phi, U = dir_U and theta = dir_theta exactly (the equilibrium
+    part of the extrapolation is that of the far field, and the
+    non-equilibrium part adds nothing to the zeroth moments), whatever the
+    interior holds next to them."""
+    n = 24
+    p = W.thermosolutal_params(n, n, eps_s=0.02, bc=("dirichlet",) * 4, dir_phi=-1.0, dir_U=-0.25, dir_theta=-0.45)
+    o = O.Oracle(p)
+    f, orient = W.random_fields(n, n, rng_seed=4)
+    o.init_fields(f, orient)
+    for T in (1, 7):
+        o.step(T - o.steps)
+        F = o.fields()
+        for k, want in (("phi", -1.0), ("U", -0.25), ("theta", -0.45)):
+            edge = np.concatenate([F[k][0], F[k][-1], F[k][:, 0], F[k][:, -1]])
+            assert np.abs(edge - want).max() < 1e-12, (k, T)
+            assert np.abs(F[k][1:-1, 1:-1] - want).max() > 1e-3  # the interior differs
+
+
 def test_planar_interface_profile_is_stationary():
     """Eq. (1) with lambda = 0 and eps = 0: phi = tanh(x/(sqrt2 W0)) solves
     W0^2 phi'' + phi - phi^3 = 0 and must stay put (W0 = 4 lattice nodes)."""
