@@ -165,6 +165,16 @@ MUTANTS = {
         "Sec. 4.4's far field: phi on Dirichlet walls copied from the interior",
         "        phib = s->P.dir_phi;\n", "",
         [("test_dirichlet_walls_hold_the_far_field_values", ())]),
+    "local_grad_rate_with_a_s": (
+        "Sec. 3.1, a_s instead of a_s^2 in the local grad(phi) scheme's relaxation rate",
+        "const double s1 = 1.0 / (a1 * a1 * s->kappa0 / CS2 + 0.5);",
+        "const double s1 = 1.0 / (a1 * s->kappa0 / CS2 + 0.5);",
+        [("force:test_local_gradient_scheme_matches_stencil", ())]),
+    "C_of_U_sign": (
+        "Eq. 20 inverted: sign of the (1 - k) U term",
+        "return 0.5 * (1.0 + k - (1.0 - k) * phi) * (1.0 + (1.0 - k) * U);",
+        "return 0.5 * (1.0 + k - (1.0 - k) * phi) * (1.0 - (1.0 - k) * U);",
+        [("test_initial_supersaturation_round_trips", ())]),
     "U_of_C_sign": (
         "Eq. 20, sign of the (1 - k) phi term",
         "return (2.0 * C / (1.0 + k - (1.0 - k) * phi) - 1.0) / (1.0 - k);",
