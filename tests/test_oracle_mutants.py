@@ -180,6 +180,29 @@ MUTANTS = {
         "return (2.0 * C / (1.0 + k - (1.0 - k) * phi) - 1.0) / (1.0 - k);",
         "return (2.0 * C / (1.0 + k + (1.0 - k) * phi) - 1.0) / (1.0 - k);",
         [("test_initial_supersaturation_round_trips", ())]),
+    "substep_walls_skipped": (
+        "Sec. 4, two-time-scaling: no flow wall pass after the flow sub-steps",
+        "        apply_boundaries(s, s->f, s->nC, s->g, 1);\n        swap_ptr(&s->h, &s->h2);\n    }\n    s->steps++;",
+        "        swap_ptr(&s->h, &s->h2);\n    }\n    s->steps++;",
+        [("test_poiseuille_flow_with_flow_substeps_and_flow_only_steps", (2, False)),
+         ("test_inflow_outflow_channel_becomes_plug_flow_with_flow_substeps", (2, False))]),
+    "substep_walls_stale_scalars": (
+        "reading R11 in the flow sub-steps: wall macros from the previous time level's scalar populations",
+        "        apply_boundaries(s, s->f, s->nC, s->g, 1);\n        swap_ptr(&s->h, &s->h2);\n    }\n    s->steps++;",
+        "        apply_boundaries(s, s->f2, s->n2, s->g2, 1);\n        swap_ptr(&s->h, &s->h2);\n    }\n    s->steps++;",
+        [("test_walls_hold_their_velocity_while_the_melt_warms_them", (2, 0, "symmetry")),
+         ("test_walls_hold_their_velocity_while_the_melt_warms_them", (3, 0, "noslip"))]),
+    "flow_only_walls_skipped": (
+        "Sec. 4.1, flow-only steps without the flow wall pass",
+        "        apply_boundaries(s, s->f, s->nC, s->g, 1);\n        swap_ptr(&s->h, &s->h2);\n    }\n    return 0;",
+        "        swap_ptr(&s->h, &s->h2);\n    }\n    return 0;",
+        [("test_poiseuille_flow_with_flow_substeps_and_flow_only_steps", (1, True)),
+         ("test_inflow_outflow_channel_becomes_plug_flow_with_flow_substeps", (1, True))]),
+    "flow_only_walls_stale_scalars": (
+        "reading R11 in flow-only steps: wall macros from the previous time level's scalar populations",
+        "        apply_boundaries(s, s->f, s->nC, s->g, 1);\n        swap_ptr(&s->h, &s->h2);\n    }\n    return 0;",
+        "        apply_boundaries(s, s->f2, s->n2, s->g2, 1);\n        swap_ptr(&s->h, &s->h2);\n    }\n    return 0;",
+        [("test_walls_hold_their_velocity_while_the_melt_warms_them", (1, 20, "symmetry"))]),
 }
 
 

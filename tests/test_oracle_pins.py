@@ -275,15 +275,23 @@ def test_shear_wave_decays_at_the_viscous_rate():
     assert a / 0.2 == pytest.approx(math.exp(-0.1 * k * k * T), rel=1e-3)
 
 
-def _poiseuille_error(ny):
+def _poiseuille_error(ny, n_sub=1, flow_only=False):
+    """Largest deviation from the parabola, relative to its peak, once the
+    flow has settled: by coupled steps with n_sub flow sub-steps each, or by
+    flow-only steps (the flow model alone, Sec. 4.1)."""
     Fx_lat, nu_paper = 1e-5, 10.0
-    p = W.thermosolutal_params(4, ny, eps_s=0.0, nu=nu_paper, bc=("periodic", "periodic", "noslip", "noslip"))
+    p = W.thermosolutal_params(4, ny, eps_s=0.0, nu=nu_paper, n_sub=n_sub,
+                               bc=("periodic", "periodic", "noslip", "noslip"))
     lp = O.Oracle(p).lattice_params()
     p["force"] = (Fx_lat / lp["fscale"], 0.0)
     o = O.Oracle(p)
     o.init_fields(_liquid(4, ny))
-    nul = nu_paper * lp["vscale"]  # dx = 1: lattice viscosity = nu dt
-    o.step(int(6 * (ny - 1) ** 2 / nul))
+    nul = nu_paper * lp["vscale"]  # dx = 1: flow lattice viscosity = nu dt / n_sub
+    flow_steps = int(6 * (ny - 1) ** 2 / nul)
+    if flow_only:
+        o.step_flow(flow_steps)
+    else:
+        o.step(-(-flow_steps // n_sub))
     H = ny - 1
     y = np.arange(ny)
     exact = Fx_lat / (2 * nul) * y * (H - y)
@@ -300,6 +308,45 @@ def test_poiseuille_flow_converges_at_second_order():
     assert e16 < 0.05
     assert e32 < 0.0125
     assert e16 / e32 == pytest.approx(4.0, rel=0.1)
+
+
+@pytest.mark.parametrize("n_sub,flow_only", [(2, False), (3, False), (1, True), (3, True)])
+def test_poiseuille_flow_with_flow_substeps_and_flow_only_steps(n_sub, flow_only):
+    """The same channel when the flow model advances by n_sub sub-steps of
+    dt/n_sub per coupled step (the two-time-scaling of Sec. 4), or by
+    flow-only steps with the scalars frozen (Sec. 4.1): the flow wall pass
+    then runs after every sub-step or flow-only step, and the profile must
+    still converge to u = F y (H - y)/(2 nu) at second order, with the wall
+    nodes at rest.  (At n_sub = 3 the flow lattice's viscosity is 1/6, where
+    the relaxation rate s2 is 1 and the discrete profile meets the parabola
+    to round-off; the error at n_sub = 1, 2 falls as H^-2.)"""
+    e16, e32 = _poiseuille_error(17, n_sub, flow_only), _poiseuille_error(33, n_sub, flow_only)
+    assert e16 < 0.05 and e32 < 0.0125
+    if e16 > 1e-10:
+        assert e16 / e32 == pytest.approx(4.0, rel=0.1)
+    else:
+        assert e32 < 1e-10
+
+
+@pytest.mark.parametrize("n_sub,flow_only", [(2, False), (1, True)])
+def test_inflow_outflow_channel_becomes_plug_flow_with_flow_substeps(n_sub, flow_only):
+    """The inflow/outflow/symmetry channel below, advanced by coupled steps of
+    two flow sub-steps each, or by flow-only steps: every flow sub-step's wall
+    pass holds the inlet velocity and the outlet pressure, so the channel
+    reaches the plug flow u = u_in, p = 0 all the same."""
+    nx, ny = 24, 8
+    p = W.thermosolutal_params(nx, ny, eps_s=0.0, bc=("inflow", "outflow", "symmetry", "symmetry"),
+                               u_in=(0.2, 0.0), n_sub=n_sub)
+    o = O.Oracle(p)
+    o.init_fields(_liquid(nx, ny))
+    if flow_only:
+        o.step_flow(20000)
+    else:
+        o.step(40000 // n_sub)
+    F = o.fields()
+    np.testing.assert_allclose(F["ux"], 0.2, rtol=1e-8)
+    np.testing.assert_allclose(F["uy"], 0.0, atol=1e-14)
+    np.testing.assert_allclose(F["p"], 0.0, atol=1e-8)
 
 
 def test_inflow_outflow_channel_becomes_plug_flow():
@@ -547,6 +594,41 @@ def test_warm_melt_rises_and_symmetry_walls_stop_normal_flow():
     assert np.abs(F["uy"][0]).max() < 1e-15 and np.abs(F["uy"][-1]).max() < 1e-15
     assert np.abs(F["uy"][1]).max() > 1e-5
 
+
+
+@pytest.mark.parametrize("n_sub,flow_only_steps,bc", [(2, 0, "symmetry"), (3, 0, "noslip"),
+                                                      (1, 20, "symmetry"), (2, 20, "noslip")])
+def test_walls_hold_their_velocity_while_the_melt_warms_them(n_sub, flow_only_steps, bc):
+    """Guo's extrapolation gives a wall node the equilibrium of the boundary
+    velocity plus the non-equilibrium part of its interior neighbour.  The
+    velocity recovered at the wall node by Eq. (26), with the buoyancy of its
+    own temperature (which the scalar wall pass copies from the interior
+    node, zero gradient), is then exactly the boundary velocity: zero normal
+    velocity on a symmetry wall, zero velocity on a no-slip wall.  This holds
+    only if the flow wall pass evaluates the interior macros from the
+    populations the interior node holds at that moment (reading R11).  Here a
+    warm blob next to the bottom wall heats it every step, so the interior
+    temperature, and with it the buoyancy, changes between coupled steps;
+    the wall pass after each flow sub-step (n_sub > 1) and after each
+    flow-only step that follows coupled steps must still see the current
+    one."""
+    n = 32
+    p = W.thermosolutal_params(n, n, eps_s=0.0, gbetaT=10 * W.GBETA_T, theta_ref=-0.5, n_sub=n_sub,
+                               bc=("periodic", "periodic", bc, bc))
+    o = O.Oracle(p)
+    y, x = np.mgrid[0:n, 0:n]
+    f = _liquid(n, n)
+    f[2] = -0.5 + 0.2 * np.exp(-((x - 16) ** 2 + (y - 4) ** 2) / 20.0)
+    o.init_fields(f)
+    for T in (1, 10, 50):
+        o.step(T - o.steps)
+        if flow_only_steps:
+            o.step_flow(flow_only_steps)
+        F = o.fields()
+        assert np.abs(F["uy"][0]).max() < 1e-15 and np.abs(F["uy"][-1]).max() < 1e-15, T
+        if bc == "noslip":
+            assert np.abs(F["ux"][0]).max() < 1e-15 and np.abs(F["ux"][-1]).max() < 1e-15, T
+        assert np.abs(F["uy"][1]).max() > 1e-6  # the flow next to the wall does move
 
 
 def test_symmetry_side_walls_stop_normal_flow():
