@@ -228,7 +228,8 @@ LBM_API long long lbm_step_count(const lbm_handle* h);
 /* Write the fields selected by `mask` (bit LBM_FIELD_*) into `out`, in
  * increasing field order, nx*ny doubles each: phi, C, U (Eq. 20), theta
  * (Eq. 23), u_x, u_y (corrected velocity of Eq. 26, paper units), p (Eq. 26,
- * paper units).  Synchronous. */
+ * paper units).  Only the selected planes are copied to the host (as FP32,
+ * converted there).  Synchronous. */
 LBM_API int lbm_get_fields(lbm_handle* h, unsigned mask, double* out);
 
 /* FP64 copy of the decoded state: LBM_STATE_PLANES planes of nx*ny
@@ -576,13 +577,17 @@ LBM_API int lbm_reduce_noalloc(const lbm_params* p, const void* scalar_pops, con
 
 /* ------------------------------------------------------------ diagnostics */
 /* Kernel timing for roofline measurements: while enabled, lbm_step launches
- * every coupled step directly (no graph) and brackets the fused
- * stream-collide kernel with CUDA events on the handle's stream.  Enabling or
- * disabling resets the accumulated time. */
+ * every coupled step directly (no graph) and brackets kernels with CUDA events
+ * on the handle's stream.  enable = 1: the fused stream-collide kernel of each
+ * coupled step; enable = 2: the n_sub - 1 flow sub-step kernels of each
+ * coupled step (two-time-scaling, Sec. 4; LBM_EINVAL when n_sub = 1), their
+ * final wall pass excluded; 0 disables.  Enabling or disabling resets the
+ * accumulated time. */
 LBM_API int lbm_set_profiling(lbm_handle* h, int enable);
 
-/* Total device time (ms) of the fused kernel launches timed since profiling
- * was enabled, and their number.  Synchronises the pending events. */
+/* Total device time (ms) of the kernel launches timed since profiling was
+ * enabled, and their number (fused kernels, or flow sub-step kernels).
+ * Synchronises the pending events. */
 LBM_API int lbm_kernel_time(lbm_handle* h, double* total_ms, long long* launches);
 
 /* Reason for the last failing call on h (or of lbm_create when h is NULL). */

@@ -57,6 +57,7 @@ struct lbm_handle {
     int step_kernel = LBM_STEP_KERNEL_AUTO;
     // kernel timing (lbm_set_profiling)
     bool profiling = false;
+    int prof_substeps = 0;         // 1: time the flow sub-step kernels instead of the fused kernel
     std::vector<cudaEvent_t> ev;   // begin/end pairs of pending fused-kernel launches
     size_t ev_used = 0;
     double prof_ms = 0.0;
@@ -319,7 +320,7 @@ int collect_profile(lbm_handle* h)
         float ms = 0.0f;
         LBM_CUDA(h, cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
         h->prof_ms += ms;
-        h->prof_launches += 1;
+        h->prof_launches += h->prof_substeps ? h->prm.n_sub - 1 : 1;
     }
     h->ev_used = 0;
     return LBM_OK;
@@ -340,6 +341,7 @@ int run_steps_direct(lbm_handle* h, int n)
             }
             h->B.ev_begin = h->ev[h->ev_used++];
             h->B.ev_end = h->ev[h->ev_used++];
+            h->B.ev_substeps = h->prof_substeps;
         }
         cudaError_t e = lbm::launch_coupled_step(h->P, h->storage, h->prm.n_sub, h->B, h->stream);
         h->B.ev_begin = h->B.ev_end = nullptr;
@@ -764,21 +766,29 @@ int lbm_get_fields(lbm_handle* h, unsigned mask, double* out)
     int rows;
     if ((rc = band_rows(h, LBM_NUM_FIELDS * sizeof(float), &rows))) return rc;
     float* dev = (float*)h->scratch;
-    std::vector<float> host((size_t)rows * pitch * LBM_NUM_FIELDS);
+    int nsel = 0;
+    for (int q = 0; q < LBM_NUM_FIELDS; ++q) nsel += (mask >> q) & 1u;
+    std::vector<float> host((size_t)rows * pitch * std::max(nsel, 1));
     for (int y0 = 0; y0 < ny; y0 += rows) {
         const int r = std::min(rows, ny - y0);
         const size_t band = (size_t)r * pitch;
         LBM_CUDA(h, lbm::launch_macros(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], dev, y0, r, h->stream));
-        LBM_CUDA(h, cudaMemcpyAsync(host.data(), dev, band * LBM_NUM_FIELDS * sizeof(float), cudaMemcpyDeviceToHost,
-                                    h->stream));
-        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        // only the requested planes cross to the host
         size_t k = 0;
+        for (int q = 0; q < LBM_NUM_FIELDS; ++q) {
+            if (!(mask & (1u << q))) continue;
+            LBM_CUDA(h, cudaMemcpyAsync(host.data() + k * band, dev + (size_t)q * band, band * sizeof(float),
+                                        cudaMemcpyDeviceToHost, h->stream));
+            ++k;
+        }
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        k = 0;
         for (int q = 0; q < LBM_NUM_FIELDS; ++q) {
             if (!(mask & (1u << q))) continue;
             for (int y = 0; y < r; ++y)
                 for (int x = 0; x < nx; ++x)
                     out[k * (size_t)nx * ny + (size_t)(y0 + y) * nx + x] =
-                        (double)host[(size_t)q * band + (size_t)y * pitch + x] * scale[q] + offset[q];
+                        (double)host[k * band + (size_t)y * pitch + x] * scale[q] + offset[q];
             ++k;
         }
     }
@@ -1110,7 +1120,10 @@ int lbm_set_profiling(lbm_handle* h, int enable)
     if (!h) return LBM_EINVAL;
     int rc = collect_profile(h);
     if (rc) return rc;
+    if (enable < 0 || enable > 2) return fail(h, LBM_EINVAL, "profiling mode must be 0, 1 or 2");
+    if (enable == 2 && h->prm.n_sub < 2) return fail(h, LBM_EINVAL, "no flow sub-steps to time (n_sub = 1)");
     h->profiling = enable != 0;
+    h->prof_substeps = enable == 2;
     h->prof_ms = 0.0;
     h->prof_launches = 0;
     return LBM_OK;

@@ -27,7 +27,8 @@ struct StepBuffers {
     float* fb;             // force plane for flow sub-steps (n_sub > 1) or null
     const uint8_t* grain;  // grain id plane or null (uniform orientation)
     int cs, cf;            // indices of the buffers holding the newest populations
-    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // recorded around the fused kernel when set
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // recorded around the timed kernels when set
+    int ev_substeps = 0;   // 0: the events bracket the fused kernel; 1: the n_sub - 1 flow sub-step kernels
     const struct StepMaps* maps = nullptr;  // TMA descriptors: use the TMA-staged fused kernel when set
 };
 

@@ -1027,7 +1027,7 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
     void* dst = B.sc[1 - B.cs];
     void* dstf = B.fl[1 - B.cf];
     const bool grain = B.grain != nullptr, wfb = n_sub > 1;
-    if (B.ev_begin) cudaEventRecord(B.ev_begin, s);
+    if (B.ev_begin && !B.ev_substeps) cudaEventRecord(B.ev_begin, s);
     const StepMaps* SM = B.maps;
     bool staged = false;
     if constexpr (!std::is_same<Store, StoreF32>::value) {
@@ -1095,7 +1095,7 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
         k_coupled_step<Store, false, false><<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (B.ev_end) cudaEventRecord(B.ev_end, s);
+    if (B.ev_end && !B.ev_substeps) cudaEventRecord(B.ev_end, s);
     if ((e = walls<Store>(P, dst, dstf, 0, s, !(xwall && skip_columns))) != cudaSuccess) return e;
     B.cs = 1 - B.cs;
     B.cf = 1 - B.cf;
@@ -1105,9 +1105,11 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
         // the scalar macros of time n+1 from the newest scalar buffer.  The
         // flow-only wall pass runs after the last sub-step only: each later
         // sub-step repairs the wall nodes it loads instead.
+        if (sub == 1 && B.ev_begin && B.ev_substeps) cudaEventRecord(B.ev_begin, s);
         k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, B.fl[B.cf], B.fl[1 - B.cf], B.hist, B.fb, B.sc[B.cs],
                                                        sub > 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (sub + 1 == n_sub && B.ev_end && B.ev_substeps) cudaEventRecord(B.ev_end, s);
         if (sub + 1 == n_sub && (e = walls<Store>(P, B.sc[B.cs], B.fl[1 - B.cf], 1, s)) != cudaSuccess) return e;
         B.cf = 1 - B.cf;
     }

@@ -389,11 +389,14 @@ class Simulation:
         return {"audited": bool(rep.audited), "accepted": bool(rep.accepted), "tip_err": rep.tip_err,
                 "tip": tuple(rep.tip), "mismatch": rep.mismatch, "max_dphi": rep.max_dphi}
 
-    def set_profiling(self, enable: bool) -> None:
-        self._check(self.lib.lbm_set_profiling(self.h, int(enable)))
+    def set_profiling(self, enable: bool, what: str = "fused") -> None:
+        """Time the fused kernel (`what` = "fused") or the flow sub-step
+        kernels ("substep") of every coupled step with CUDA events."""
+        mode = 0 if not enable else {"fused": 1, "substep": 2}[what]
+        self._check(self.lib.lbm_set_profiling(self.h, mode))
 
     def kernel_time(self) -> tuple[float, int]:
-        """(total ms, launches) of the fused kernel since profiling was enabled."""
+        """(total ms, launches) of the timed kernels since profiling was enabled."""
         ms, n = ct.c_double(), ct.c_longlong()
         self._check(self.lib.lbm_kernel_time(self.h, ct.byref(ms), ct.byref(n)))
         return ms.value, n.value

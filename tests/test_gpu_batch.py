@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
+import storage_emulation as SE
 from paper_2209_01444_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -111,3 +112,113 @@ def test_batch_rejects_mixed_storage(lbm):
     h = ct.c_void_p()
     assert lib.lbm_batch_create(arr, 2, ct.byref(h)) == lbm.LBM_EINVAL
     assert b"storage" in lib.lbm_batch_last_error(None)
+
+
+# ------------------------------------------------------------ FP16 storage
+def errors(got, want, theta0):
+    """The parity metric: max|X - X_ref| / max(max|X_ref|, floor), floors phi,
+    C: 1, theta: |theta0|.  The velocity components share one scale, the
+    largest speed |u| of the reference (floor 1e-6): the tolerance reading's u
+    floor is that of the velocity, so a cross-stream component that is still
+    small next to the stream is not measured against its own tiny maximum."""
+    out = {}
+    for k, fl in (("phi", 1.0), ("C", 1.0), ("theta", abs(theta0))):
+        out[k] = float(np.abs(got[k] - want[k]).max() / max(np.abs(want[k]).max(), fl))
+    speed = max(float(np.hypot(want["ux"], want["uy"]).max()), 1e-6)
+    for k in ("ux", "uy"):
+        out[k] = float(np.abs(got[k] - want[k]).max() / speed)
+    return out
+
+
+ACC = ("phi", "C", "theta", "ux", "uy")
+
+
+@pytest.mark.parametrize("ty,run", [(4, 1), (8, 1), (16, 0)])
+def test_fp16_batch_matches_fp16_single_domain_runs(lbm, ty, run):
+    """The batched kernel with FP16 storage against each domain stepped alone
+    by the single-domain FP16 kernel: the same per-node arithmetic and the
+    same rounding of every stored population, so the two agree to a few
+    units of the 16-bit rounding (a product fused into a multiply-add
+    differently by the compiler can move a value across a rounding boundary)."""
+    cases = small_cases()
+    b = lbm.Batch([c.params for c in cases], "fp16")
+    b.set_tiling(ty, run)
+    singles = []
+    for j, c in enumerate(cases):
+        b.init_seeds(j, c.seeds, c.U0, c.theta0)
+        s = lbm.Simulation(c.params, "fp16")
+        s.init_seeds(c.seeds, c.U0, c.theta0)
+        singles.append(s)
+    b.step(37)           # two 16-step graphs + 5 direct steps
+    worst = {}
+    for j, (c, s) in enumerate(zip(cases, singles)):
+        s.step(37)
+        e = errors(b.fields(j, ACC), s.fields(ACC), c.theta0)
+        print(j, {k: f"{v:.1e}" for k, v in e.items()})
+        for k, v in e.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    assert max(worst.values()) <= 1e-3, worst
+
+
+def test_fp16_batch_matches_the_oracle_with_fp16_storage(lbm):
+    """The FP16 batched launch against the FP64 oracle whose state is rounded
+    after every step as FP16 storage rounds it (within 2e-3: the kernels'
+    FP32 arithmetic against FP64, amplified by nothing), and against the plain
+    oracle within the 16-bit bound of 1e-2."""
+    cases = small_cases()[:4]
+    b = lbm.Batch([c.params for c in cases], "fp16")
+    for j, c in enumerate(cases):
+        b.init_seeds(j, c.seeds, c.U0, c.theta0)
+    steps = 60
+    b.step(steps)
+    for j, c in enumerate(cases):
+        o, r = O.Oracle(c.params), O.Oracle(c.params)
+        o.init_seeds(c.seeds, c.U0, c.theta0)
+        r.init_seeds(c.seeds, c.U0, c.theta0)
+        SE.round_state(r, c.params, "fp16")
+        o.step(steps)
+        for _ in range(steps):
+            r.step(1)
+            SE.round_state(r, c.params, "fp16")
+        got = b.fields(j, ACC)
+        vs_rounded, vs_plain = errors(got, r.fields(), c.theta0), errors(got, o.fields(), c.theta0)
+        print(j, {k: f"{vs_rounded[k]:.1e} / {vs_plain[k]:.1e}" for k in ACC})
+        assert max(vs_rounded.values()) <= 2e-3, (j, vs_rounded, vs_plain)
+        assert max(vs_plain.values()) <= 1e-2, (j, vs_rounded, vs_plain)
+
+
+def test_fp16_batch_of_the_sweep_matches_the_oracle(lbm):
+    """The 256-domain parameter sweep (sides log-uniform in 128..1024, the
+    benchmarked batched FP16 launch with its 16-step graphs) on its smallest
+    domain (130 x 130, inflow u_x = 0.27 W0/tau0) against the FP64 oracle,
+    after 32 steps (the flow still starting impulsively, its cross-stream
+    component small) and 516 steps: within 2e-3 of the oracle rounded as
+    FP16 storage rounds it, and within 1e-2 of the plain oracle.  The
+    cross-stream velocity measured against its own maximum is reported too:
+    that is where the FP16 format itself departs most from FP64."""
+    cases = W.batch_domains()
+    j = min(range(len(cases)), key=lambda i: cases[i].nodes)
+    c = cases[j]
+    b = lbm.Batch([q.params for q in cases], "fp16")
+    for i, q in enumerate(cases):
+        b.init_seeds(i, q.seeds, q.U0, q.theta0)
+    o, r = O.Oracle(c.params), O.Oracle(c.params)
+    o.init_seeds(c.seeds, c.U0, c.theta0)
+    r.init_seeds(c.seeds, c.U0, c.theta0)
+    SE.round_state(r, c.params, "fp16")
+    for T in (32, 516):
+        b.step(T - o.steps)
+        for _ in range(T - o.steps):
+            o.step(1)
+            r.step(1)
+            SE.round_state(r, c.params, "fp16")
+        got, want, rw = b.fields(j, ACC), o.fields(), r.fields()
+        vs_rounded, vs_plain = errors(got, rw, c.theta0), errors(got, want, c.theta0)
+        own = float(np.abs(got["uy"] - want["uy"]).max() / np.abs(want["uy"]).max())
+        fmt = float(np.abs(rw["uy"] - want["uy"]).max() / np.abs(want["uy"]).max())
+        print(T, {k: f"{vs_rounded[k]:.1e} / {vs_plain[k]:.1e}" for k in ACC},
+              f"uy of its own max: gpu {own:.2e}, rounded oracle {fmt:.2e}")
+        assert max(vs_rounded.values()) <= 2e-3, (T, vs_rounded, vs_plain)
+        assert max(vs_plain.values()) <= 1e-2, (T, vs_rounded, vs_plain)
+        assert b.metrics(j, *c.seeds[0][:2], c.seeds[0][3])["tip_px"] == pytest.approx(
+            o.metrics(*c.seeds[0][:2], c.seeds[0][3])["tip_px"], abs=1.0)
