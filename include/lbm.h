@@ -71,9 +71,6 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_INFLOW = 1, LBM_BC_OUTFLOW = 2, LBM_BC_SYMMET
  * C = 1, theta = theta_ref, p = 0); the history fields stay FP32. */
 enum { LBM_FP32 = 0, LBM_FP16 = 1, LBM_BF16 = 2 };
 enum { LBM_GRAD_FD9 = 0, LBM_GRAD_LOCAL = 1 };
-/* Fused-step kernels (lbm_set_step_kernel). */
-enum { LBM_STEP_KERNEL_AUTO = 0, LBM_STEP_KERNEL_TILED = 1, LBM_STEP_KERNEL_TMA = 2 };
-
 /* Field indices for lbm_get_fields (bit i of the mask selects field i). */
 enum { LBM_FIELD_PHI = 0, LBM_FIELD_C = 1, LBM_FIELD_U = 2, LBM_FIELD_THETA = 3,
        LBM_FIELD_UX = 4, LBM_FIELD_UY = 5, LBM_FIELD_P = 6, LBM_NUM_FIELDS = 7 };
@@ -185,41 +182,24 @@ LBM_API int lbm_init_fields(lbm_handle* h, const double* fields, const double* o
 /* Queue `nsteps` coupled time steps (the fused stream-collide kernel of all
  * four models, then the wall kernels, then n_sub - 1 flow-only sub-steps) on
  * the handle's stream and return without waiting.  Long runs are replayed
- * from captured 16-step CUDA graphs; inside one (n_sub = 1, tiled kernel) the
+ * from captured 16-step CUDA graphs; inside one (n_sub = 1) the
  * left/right walls of a step are updated by the next step as it loads them,
  * and the last step of the graph runs the wall kernels in full, so the state
  * seen between calls is always complete. */
 LBM_API int lbm_step(lbm_handle* h, int nsteps);
 
-/* Wait for all queued work of h; reports an asynchronous CUDA error, and
- * LBM_ETIMEOUT (once; the flag is then cleared) if a fused step of the TMA
- * kernel gave up a bounded wait (1 s) for its copies since the last report
- * (the flag is per process: any handle's kernel may have raised it). */
+/* Wait for all queued work of h; reports an asynchronous CUDA error. */
 LBM_API int lbm_synchronize(lbm_handle* h);
 
 /* Size limit, in bytes, of the device buffer that whole-grid transfers
  * (lbm_init_seeds, lbm_init_fields, lbm_get_fields, lbm_get_state,
  * lbm_get_state_region, lbm_set_state) work through, one band of rows at a
- * time (default 64 MiB; at least one row of the widest transfer, 96 bytes per
+ * time (default 64 MiB; at least one row of the widest transfer, 120 bytes per
  * node, is always used).  The buffer is allocated on the first such call, so
  * a handle holds only its state (about 217 bytes per node in FP32, 133 in
  * FP16/BF16, plus O(nx + ny) tables) and the grid can fill most of the
  * device.  Results do not depend on the band size. */
 LBM_API int lbm_set_io_chunk(lbm_handle* h, size_t bytes);
-
-/* Choose the kernel of the fused coupled step; both compute the same update
- * bit for bit.  LBM_STEP_KERNEL_TILED: one CTA per 32 x 8 tile, loads staged
- * in registers.  LBM_STEP_KERNEL_TMA: persistent CTAs; each tile's
- * populations, history and grain ids are copied into shared memory by TMA
- * while the previous tile is computed (grids of at least 40 x 10 nodes, 48 x 10
- * with 16-bit storage, else LBM_EINVAL).  LBM_STEP_KERNEL_AUTO (the default)
- * takes the tiled kernel, the faster of the two on GB300 so far.  Drops the
- * captured step graphs. */
-LBM_API int lbm_set_step_kernel(lbm_handle* h, int kernel);
-
-/* The kernel lbm_step uses now: LBM_STEP_KERNEL_TILED or LBM_STEP_KERNEL_TMA
- * (negative for a NULL handle). */
-LBM_API int lbm_step_kernel(const lbm_handle* h);
 
 /* Number of coupled steps taken since the last initialisation. */
 LBM_API long long lbm_step_count(const lbm_handle* h);

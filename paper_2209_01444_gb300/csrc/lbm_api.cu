@@ -53,8 +53,6 @@ struct lbm_handle {
     bool initialised = false;
     std::string err;
     std::map<GraphKey, cudaGraphExec_t> graphs;
-    lbm::StepMaps* maps = nullptr;     // TMA descriptors of the fused step, when supported
-    int step_kernel = LBM_STEP_KERNEL_AUTO;
     // kernel timing (lbm_set_profiling)
     bool profiling = false;
     int prof_substeps = 0;         // 1: time the flow sub-step kernels instead of the fused kernel
@@ -242,7 +240,7 @@ int set_grains(lbm_handle* h, const std::vector<double>& orient_of_id, const std
 // the whole grid needs.
 int band_rows(lbm_handle* h, size_t node_bytes, int* rows)
 {
-    const size_t row_max = (size_t)h->P.pitch * 96;
+    const size_t row_max = (size_t)h->P.pitch * (LBM_STATE_PLANES * sizeof(float));  // the widest transfer
     size_t want = std::min(h->io_chunk, row_max * (size_t)h->P.ny);
     want = std::max(want, row_max);
     if (h->scratch_bytes != want) {
@@ -269,21 +267,19 @@ template <class Deliver>
 int decode_rows(lbm_handle* h, int y0, int hgt, Deliver deliver)
 {
     int rows, rc;
-    if ((rc = band_rows(h, lbm::kPlanes * sizeof(float), &rows))) return rc;
-    const size_t pitch = (size_t)h->P.pitch, plane = (size_t)h->P.plane;
+    if ((rc = band_rows(h, LBM_STATE_PLANES * sizeof(float), &rows))) return rc;
+    const size_t pitch = (size_t)h->P.pitch;
     float* dev = (float*)h->scratch;
-    std::vector<float> pops((size_t)rows * pitch * lbm::kPlanes), hist((size_t)rows * pitch * lbm::kHist);
+    std::vector<float> planes((size_t)rows * pitch * LBM_STATE_PLANES);
     for (int y = y0; y < y0 + hgt; y += rows) {
         const int r = std::min(rows, y0 + hgt - y);
         const size_t band = (size_t)r * pitch;
-        LBM_CUDA(h, lbm::launch_decode(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], dev, y, r, h->stream));
-        LBM_CUDA(h, cudaMemcpyAsync(pops.data(), dev, band * lbm::kPlanes * sizeof(float), cudaMemcpyDeviceToHost,
-                                    h->stream));
-        for (int q = 0; q < lbm::kHist; ++q)
-            LBM_CUDA(h, cudaMemcpyAsync(hist.data() + q * band, h->B.hist + q * plane + (size_t)y * pitch,
-                                        band * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(h, lbm::launch_decode(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->B.hist, dev, y, r,
+                                       h->stream));
+        LBM_CUDA(h, cudaMemcpyAsync(planes.data(), dev, band * LBM_STATE_PLANES * sizeof(float),
+                                    cudaMemcpyDeviceToHost, h->stream));
         LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-        if ((rc = deliver(y, r, pops.data(), hist.data()))) return rc;
+        if ((rc = deliver(y, r, planes.data(), planes.data() + lbm::kPlanes * band))) return rc;
     }
     return LBM_OK;
 }
@@ -460,15 +456,6 @@ int lbm_create(const lbm_params* p, lbm_handle** out)
         return fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, msg);
     }
     h->P.grain_cs = h->grain_cs;
-    if (lbm::step_maps_supported(h->P, h->storage)) {
-        lbm::StepBuffers b = h->B;
-        b.grain = h->grain;  // the map covers the grain plane, used once the grid has grains
-        if (lbm::create_step_maps(h->P, h->storage, b, &h->maps) != cudaSuccess) {
-            h->maps = nullptr;  // the tiled kernel serves
-            cudaGetLastError();
-        }
-    }
-    h->B.maps = nullptr;  // LBM_STEP_KERNEL_AUTO: the tiled kernel
     *out = h;
     return LBM_OK;
 }
@@ -481,30 +468,10 @@ int lbm_set_io_chunk(lbm_handle* h, size_t bytes)
     return LBM_OK;
 }
 
-int lbm_set_step_kernel(lbm_handle* h, int kernel)
-{
-    if (!h) return LBM_EINVAL;
-    if (kernel != LBM_STEP_KERNEL_AUTO && kernel != LBM_STEP_KERNEL_TILED && kernel != LBM_STEP_KERNEL_TMA)
-        return fail(h, LBM_EINVAL, "unknown step kernel");
-    if (kernel == LBM_STEP_KERNEL_TMA && !h->maps)
-        return fail(h, LBM_EINVAL, "the TMA step kernel needs a grid of at least 40 x 10 nodes (48 x 10 with 16-bit storage)");
-    h->step_kernel = kernel;
-    h->B.maps = kernel == LBM_STEP_KERNEL_TMA ? h->maps : nullptr;
-    drop_graphs(h);
-    return LBM_OK;
-}
-
-int lbm_step_kernel(const lbm_handle* h)
-{
-    if (!h) return LBM_EINVAL;
-    return h->B.maps ? LBM_STEP_KERNEL_TMA : LBM_STEP_KERNEL_TILED;
-}
-
 void lbm_destroy(lbm_handle* h)
 {
     if (!h) return;
     drop_graphs(h);
-    lbm::destroy_step_maps(h->maps);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     void* ptrs[] = {h->B.sc[0], h->B.sc[1], h->B.fl[0], h->B.fl[1], h->B.hist, h->B.fb, h->grain,
                     h->grain_cs, h->d_partials, h->d_red, h->scratch, h->d_seeds,
@@ -745,9 +712,6 @@ int lbm_synchronize(lbm_handle* h)
 {
     if (!h) return LBM_EINVAL;
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-    int flag = 0;
-    LBM_CUDA(h, lbm::step_error(&flag, true));
-    if (flag) return fail(h, LBM_ETIMEOUT, "a fused step gave up a bounded wait for its TMA copies");
     return LBM_OK;
 }
 
@@ -844,11 +808,11 @@ int lbm_set_state(lbm_handle* h, const double* in)
     if (rc) return rc;
     if (!in) return fail(h, LBM_EINVAL, "in is NULL");
     const int nx = h->P.nx, ny = h->P.ny;
-    const size_t pitch = (size_t)h->P.pitch, plane = (size_t)h->P.plane, N = (size_t)nx * ny;
+    const size_t pitch = (size_t)h->P.pitch, N = (size_t)nx * ny;
     for (size_t i = 0; i < N * LBM_STATE_PLANES; ++i)  // the whole input first: a refusal changes nothing
         if (!isfinite(in[i])) return fail(h, LBM_EINVAL, "non-finite state value");
     int rows;
-    if ((rc = band_rows(h, lbm::kPlanes * sizeof(float), &rows))) return rc;
+    if ((rc = band_rows(h, LBM_STATE_PLANES * sizeof(float), &rows))) return rc;
     float* dev = (float*)h->scratch;
     std::vector<float> host((size_t)rows * pitch * LBM_STATE_PLANES, 0.0f);
     for (int y0 = 0; y0 < ny; y0 += rows) {
@@ -861,13 +825,10 @@ int lbm_set_state(lbm_handle* h, const double* in)
                     host[q * band + (size_t)y * pitch + x] =
                         (float)(in[(size_t)q * N + (size_t)(y0 + y) * nx + x] - ref);
         }
-        LBM_CUDA(h, cudaMemcpyAsync(dev, host.data(), band * lbm::kPlanes * sizeof(float), cudaMemcpyHostToDevice,
-                                    h->stream));
-        for (int q = 0; q < lbm::kHist; ++q)
-            LBM_CUDA(h, cudaMemcpyAsync(h->B.hist + q * plane + (size_t)y0 * pitch,
-                                        host.data() + (lbm::kPlanes + q) * band, band * sizeof(float),
-                                        cudaMemcpyHostToDevice, h->stream));
-        LBM_CUDA(h, lbm::launch_encode(h->P, h->storage, dev, h->B.sc[h->B.cs], h->B.fl[h->B.cf], y0, r, h->stream));
+        LBM_CUDA(h, cudaMemcpyAsync(dev, host.data(), band * LBM_STATE_PLANES * sizeof(float),
+                                    cudaMemcpyHostToDevice, h->stream));
+        LBM_CUDA(h, lbm::launch_encode(h->P, h->storage, dev, h->B.sc[h->B.cs], h->B.fl[h->B.cf], h->B.hist, y0, r,
+                                       h->stream));
         // the host band buffer is refilled for the next band
         LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     }
@@ -927,7 +888,7 @@ int lbm_save_state(lbm_handle* h, void* host, size_t bytes)
     char* p = (char*)host;
     CkptHeader hd;
     memset(&hd, 0, sizeof(hd));
-    memcpy(hd.magic, "LBMCKPT1", 8);
+    memcpy(hd.magic, "LBMCKPT2", 8);
     hd.prm = h->prm;
     hd.steps = h->steps;
     hd.uniform = h->uniform ? 1 : 0;
@@ -955,7 +916,7 @@ int lbm_load_state(lbm_handle* h, const void* host, size_t bytes)
     const char* p = (const char*)host;
     CkptHeader hd;
     memcpy(&hd, p, sizeof(hd));
-    if (memcmp(hd.magic, "LBMCKPT1", 8) != 0) return fail(h, LBM_EINVAL, "not a checkpoint");
+    if (memcmp(hd.magic, "LBMCKPT2", 8) != 0) return fail(h, LBM_EINVAL, "not a checkpoint of this layout");
     if (memcmp(&hd.prm, &h->prm, sizeof(lbm_params)) != 0) return fail(h, LBM_EINVAL, "checkpoint parameters differ");
     p += sizeof(hd);
     const size_t plane = (size_t)h->P.plane;

@@ -83,7 +83,6 @@ __device__ void init_node(const StepParams& P, long long o, float p1, float dC, 
                           float uy, float p, void* __restrict__ sc, void* __restrict__ fl, float* __restrict__ hist,
                           float heqx, float heqy)
 {
-    const long long plane = P.plane;
     const float hp1 = h_plus_1(P.h_kind, p1);
     const float H = (P.theta_ref + P.latent) + dth - P.latent * hp1;
     const float C = 1.0f + dC;
@@ -106,12 +105,12 @@ __device__ void init_node(const StepParams& P, long long o, float p1, float dC, 
     load_node<Store>(P, sc, fl, o, f, n, g, h);
     const Macro m = node_macros(f, n, g, h, P);
     const float usx = m.ux * P.nsub, usy = m.uy * P.nsub;
-    hist[0 * plane + o] = m.phi;
-    hist[1 * plane + o] = coupling_Q(m.phi, P.theta_ref + m.dth, m.U, P);
-    hist[2 * plane + o] = (1.0f + m.dC) * usx;
-    hist[3 * plane + o] = (1.0f + m.dC) * usy;
-    hist[4 * plane + o] = m.H * usx;
-    hist[5 * plane + o] = m.H * usy;
+    hist_at(hist, 0, o) = m.phi;
+    hist_at(hist, 1, o) = coupling_Q(m.phi, P.theta_ref + m.dth, m.U, P);
+    hist_at(hist, 2, o) = (1.0f + m.dC) * usx;
+    hist_at(hist, 3, o) = (1.0f + m.dC) * usy;
+    hist_at(hist, 4, o) = m.H * usx;
+    hist_at(hist, 5, o) = m.H * usy;
 }
 
 template <class Store>
@@ -198,13 +197,12 @@ __global__ void k_set_fields_nhwc(const StepParams P, const float* __restrict__ 
     const float ux_b = ux - (ux - q[3] * vf) * inv_k, uy_b = uy - (uy - q[4] * vf) * inv_k;
     const float U_b = (2.0f * C_b / (1.0f + k - (1.0f - k) * phi_b) - 1.0f) / (1.0f - k);
     const float H_b = th_b - 0.5f * (h_plus_1(P.h_kind, phi_b + 1.0f) - 1.0f);  // H = theta - h/2
-    const long long plane = P.plane;
-    hist[0 * plane + o] = phi_b;
-    hist[1 * plane + o] = coupling_Q(phi_b, th_b, U_b, P);
-    hist[2 * plane + o] = C_b * ux_b * P.nsub;
-    hist[3 * plane + o] = C_b * uy_b * P.nsub;
-    hist[4 * plane + o] = H_b * ux_b * P.nsub;
-    hist[5 * plane + o] = H_b * uy_b * P.nsub;
+    hist_at(hist, 0, o) = phi_b;
+    hist_at(hist, 1, o) = coupling_Q(phi_b, th_b, U_b, P);
+    hist_at(hist, 2, o) = C_b * ux_b * P.nsub;
+    hist_at(hist, 3, o) = C_b * uy_b * P.nsub;
+    hist_at(hist, 4, o) = H_b * ux_b * P.nsub;
+    hist_at(hist, 5, o) = H_b * uy_b * P.nsub;
 }
 
 // Interface mismatch between two pixel-interleaved field sets (stride 5,
@@ -255,10 +253,11 @@ __global__ void k_macros(const StepParams P, const void* __restrict__ sc, const 
     out[6 * bp + ob] = m.p;
 }
 
-// Deviations of every population plane as FP32 planes (and back).
+// Deviations of every population as FP32 band planes 0..23 and the history
+// as planes 24..29 (and back).
 template <class Store>
 __global__ void k_decode(const StepParams P, const void* __restrict__ sc, const void* __restrict__ fl,
-                         float* __restrict__ out, int y0, int rows)
+                         const float* __restrict__ hist, float* __restrict__ out, int y0, int rows)
 {
     const long long bp = (long long)rows * P.pitch;
     const long long ib = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -266,11 +265,13 @@ __global__ void k_decode(const StepParams P, const void* __restrict__ sc, const 
     const long long i = (long long)y0 * P.pitch + ib;
 #pragma unroll
     for (int q = 0; q < kPlanes; ++q) out[q * bp + ib] = Store::load(sc, fl, q, i, P);
+#pragma unroll
+    for (int k = 0; k < kHist; ++k) out[(kPlanes + k) * bp + ib] = hist_at(hist, k, i);
 }
 
 template <class Store>
 __global__ void k_encode(const StepParams P, const float* __restrict__ in, void* __restrict__ sc,
-                         void* __restrict__ fl, int y0, int rows)
+                         void* __restrict__ fl, float* __restrict__ hist, int y0, int rows)
 {
     const long long bp = (long long)rows * P.pitch;
     const long long ib = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -278,6 +279,8 @@ __global__ void k_encode(const StepParams P, const float* __restrict__ in, void*
     const long long i = (long long)y0 * P.pitch + ib;
 #pragma unroll
     for (int q = 0; q < kPlanes; ++q) Store::store(sc, fl, q, i, in[q * bp + ib], P);
+#pragma unroll
+    for (int k = 0; k < kHist; ++k) hist_at(hist, k, i) = in[(kPlanes + k) * bp + ib];
 }
 
 // ------------------------------------------------------------- reductions
@@ -536,19 +539,20 @@ cudaError_t macros_t(const StepParams& P, const void* sc, const void* fl, float*
 }
 
 template <class Store>
-cudaError_t decode_t(const StepParams& P, const void* sc, const void* fl, float* out, int y0, int rows,
-                     cudaStream_t s)
+cudaError_t decode_t(const StepParams& P, const void* sc, const void* fl, const float* hist, float* out, int y0,
+                     int rows, cudaStream_t s)
 {
     const long long n = (long long)rows * P.pitch;
-    k_decode<Store><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, sc, fl, out, y0, rows);
+    k_decode<Store><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, sc, fl, hist, out, y0, rows);
     return cudaGetLastError();
 }
 
 template <class Store>
-cudaError_t encode_t(const StepParams& P, const float* in, void* sc, void* fl, int y0, int rows, cudaStream_t s)
+cudaError_t encode_t(const StepParams& P, const float* in, void* sc, void* fl, float* hist, int y0, int rows,
+                     cudaStream_t s)
 {
     const long long n = (long long)rows * P.pitch;
-    k_encode<Store><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, in, sc, fl, y0, rows);
+    k_encode<Store><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, in, sc, fl, hist, y0, rows);
     return cudaGetLastError();
 }
 
@@ -649,23 +653,23 @@ cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, cons
     }
 }
 
-cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, float* out, int y0,
-                          int rows, cudaStream_t s)
+cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, const float* hist,
+                          float* out, int y0, int rows, cudaStream_t s)
 {
     switch (storage) {
-    case kStoreF16: return decode_t<StoreF16>(P, sc, fl, out, y0, rows, s);
-    case kStoreBF16: return decode_t<StoreBF16>(P, sc, fl, out, y0, rows, s);
-    default: return decode_t<StoreF32>(P, sc, fl, out, y0, rows, s);
+    case kStoreF16: return decode_t<StoreF16>(P, sc, fl, hist, out, y0, rows, s);
+    case kStoreBF16: return decode_t<StoreBF16>(P, sc, fl, hist, out, y0, rows, s);
+    default: return decode_t<StoreF32>(P, sc, fl, hist, out, y0, rows, s);
     }
 }
 
-cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, int y0, int rows,
-                          cudaStream_t s)
+cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, float* hist, int y0,
+                          int rows, cudaStream_t s)
 {
     switch (storage) {
-    case kStoreF16: return encode_t<StoreF16>(P, in, sc, fl, y0, rows, s);
-    case kStoreBF16: return encode_t<StoreBF16>(P, in, sc, fl, y0, rows, s);
-    default: return encode_t<StoreF32>(P, in, sc, fl, y0, rows, s);
+    case kStoreF16: return encode_t<StoreF16>(P, in, sc, fl, hist, y0, rows, s);
+    case kStoreBF16: return encode_t<StoreBF16>(P, in, sc, fl, hist, y0, rows, s);
+    default: return encode_t<StoreF32>(P, in, sc, fl, hist, y0, rows, s);
     }
 }
 

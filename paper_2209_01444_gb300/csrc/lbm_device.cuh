@@ -69,14 +69,50 @@ struct StepParams {
     float dir_phi, dir_U, dir_theta;
 };
 
+// ------------------------------------------------------------------ layout
+// Node blocks.  Every per-node buffer (populations, history) keeps its values
+// in blocks of 32 nodes along x: node o = y * pitch + x (pitch a multiple of
+// 32, so no block spans two rows) is lane o & 31 of block o >> 5, and the
+// block holds plane q of its 32 nodes contiguously at [block][q][lane].  A
+// warp's 32 nodes still read or write each plane as one contiguous segment,
+// and all planes of one node lie in one block: a kernel forms one address per
+// node and reaches every plane at a compile-time offset from it.
+// Element index of plane 0 of node o in a buffer of np planes per block.
+__device__ __forceinline__ long long block_index(long long o, int np)
+{
+    return (long long)((unsigned long long)(unsigned)(o >> 5) * (unsigned)(np * 32)) + (long long)(o & 31);
+}
+
+// The same index split into a row term and a column term, so that the
+// pushes of one node to its neighbours share three row and three column terms:
+// block_index(y * pitch + x, np) = block_row(y, pitch, np) + block_col(x, np).
+// (Grids hold fewer than 2^31 nodes, so y * pitch / 32 fits in 32 bits.)
+__device__ __forceinline__ long long block_row(int y, int pitch, int np)
+{
+    return (long long)((unsigned long long)(unsigned)(y * (pitch >> 5)) * (unsigned)(np * 32));
+}
+__device__ __forceinline__ int block_col(int x, int np) { return (x >> 5) * (np * 32) + (x & 31); }
+
+// History value k (phi, Q, (Cu)_x, (Cu)_y, (Hu)_x, (Hu)_y) of node o.
+__device__ __forceinline__ float& hist_at(float* hist, int k, long long o)
+{
+    return hist[block_index(o, kHist) + 32 * k];
+}
+__device__ __forceinline__ float hist_at(const float* hist, int k, long long o)
+{
+    return hist[block_index(o, kHist) + 32 * k];
+}
+
 // ------------------------------------------------------------------ codecs
 // A state is two buffers: the scalar populations (phi, C, H) and the flow
-// populations.  FP32 storage keeps all 15 scalar planes in FP32.  16-bit
-// storage keeps the 12 moving scalar planes and the 9 flow planes in FP16 or
-// BF16 (scaled, rounded to nearest even) and the three scalar rest planes
-// (q = 0, 5, 10), which carry the O(1) solid/liquid contrast and the smallest
-// per-step increments, in FP32 after the 16-bit planes.  q is always a
-// compile-time constant at the call sites, so the plane mapping folds away.
+// populations, each in node blocks.  FP32 storage keeps all 15 scalar planes
+// in FP32.  16-bit storage keeps the 12 moving scalar planes and the 9 flow
+// planes in FP16 or BF16 (scaled, rounded to nearest even) and the three
+// scalar rest planes (q = 0, 5, 10), which carry the O(1) solid/liquid
+// contrast and the smallest per-step increments, in FP32: a scalar block is
+// 12 x 32 16-bit values followed by 3 x 32 FP32 values (1152 bytes).  q is
+// always a compile-time constant at the call sites, so the plane mapping
+// folds into address offsets.
 struct StoreF32 {
     using T = float;
     static constexpr int kScalarBytes = 15 * 4;  // per node
@@ -84,16 +120,25 @@ struct StoreF32 {
     static __device__ __forceinline__ float load(const void* sc, const void* fl, int q, long long o,
                                                  const StepParams& P)
     {
-        return q < kH ? ((const float*)sc)[q * P.plane + o] : ((const float*)fl)[(q - kH) * P.plane + o];
+        return q < kH ? ((const float*)sc)[block_index(o, 15) + 32 * q]
+                      : ((const float*)fl)[block_index(o, 9) + 32 * (q - kH)];
     }
     static __device__ __forceinline__ void store(void* sc, void* fl, int q, long long o, float v,
                                                  const StepParams& P)
     {
         if (q < kH)
-            ((float*)sc)[q * P.plane + o] = v;
+            ((float*)sc)[block_index(o, 15) + 32 * q] = v;
         else
-            ((float*)fl)[(q - kH) * P.plane + o] = v;
+            ((float*)fl)[block_index(o, 9) + 32 * (q - kH)] = v;
     }
+    // Pushes: element index of node (x, y) in the moving scalar planes
+    // (row + column terms) and in the flow buffer; q a moving scalar plane.
+    static __device__ __forceinline__ long long mov_row(int y, const StepParams& P) { return block_row(y, P.pitch, 15); }
+    static __device__ __forceinline__ int mov_col(int x) { return block_col(x, 15); }
+    static __device__ __forceinline__ long long flow_row(int y, const StepParams& P) { return block_row(y, P.pitch, 9); }
+    static __device__ __forceinline__ int flow_col(int x) { return block_col(x, 9); }
+    static __device__ __forceinline__ void store_mov(void* sc, int q, long long e, float v) { ((float*)sc)[e + 32 * q] = v; }
+    static __device__ __forceinline__ void store_flow(void* fl, int i, long long e, float v) { ((float*)fl)[e + 32 * i] = v; }
 };
 
 template <class H>
@@ -120,26 +165,47 @@ struct Store16 {
     static constexpr int kFlowBytes = 9 * 2;
     static __device__ __forceinline__ bool rest(int q) { return q == kF || q == kN || q == kG; }
     static __device__ __forceinline__ int slot(int q) { return q - 1 - q / 5; }  // moving planes 0..11
-    static __device__ __forceinline__ const float* rest_base(const void* sc, const StepParams& P)
+    // 16-bit index of moving slot 0 and FP32 index of rest plane 0 of node o
+    // in the scalar buffer (1152-byte blocks: 576 16-bit or 288 FP32 values)
+    static __device__ __forceinline__ long long moving_index(long long o)
     {
-        return (const float*)((const char*)sc + 24 * P.plane);
+        return (long long)((unsigned long long)(unsigned)(o >> 5) * 576u) + (long long)(o & 31);
+    }
+    static __device__ __forceinline__ long long rest_index(long long o)
+    {
+        return (long long)((unsigned long long)(unsigned)(o >> 5) * 288u) + 192 + (long long)(o & 31);
     }
     static __device__ __forceinline__ float load(const void* sc, const void* fl, int q, long long o,
                                                  const StepParams& P)
     {
-        if (q >= kH) return Conv<H>::to(((const H*)fl)[(q - kH) * P.plane + o]) * inv_scale(q);
-        if (rest(q)) return rest_base(sc, P)[(q / 5) * P.plane + o];
-        return Conv<H>::to(((const H*)sc)[slot(q) * P.plane + o]) * inv_scale(q);
+        if (q >= kH) return Conv<H>::to(((const H*)fl)[block_index(o, 9) + 32 * (q - kH)]) * inv_scale(q);
+        if (rest(q)) return ((const float*)sc)[rest_index(o) + 32 * (q / 5)];
+        return Conv<H>::to(((const H*)sc)[moving_index(o) + 32 * slot(q)]) * inv_scale(q);
     }
     static __device__ __forceinline__ void store(void* sc, void* fl, int q, long long o, float v,
                                                  const StepParams& P)
     {
         if (q >= kH)
-            ((H*)fl)[(q - kH) * P.plane + o] = Conv<H>::from(v * scale(q));
+            ((H*)fl)[block_index(o, 9) + 32 * (q - kH)] = Conv<H>::from(v * scale(q));
         else if (rest(q))
-            ((float*)rest_base(sc, P))[(q / 5) * P.plane + o] = v;
+            ((float*)sc)[rest_index(o) + 32 * (q / 5)] = v;
         else
-            ((H*)sc)[slot(q) * P.plane + o] = Conv<H>::from(v * scale(q));
+            ((H*)sc)[moving_index(o) + 32 * slot(q)] = Conv<H>::from(v * scale(q));
+    }
+    static __device__ __forceinline__ long long mov_row(int y, const StepParams& P)
+    {
+        return (long long)((unsigned long long)(unsigned)(y * (P.pitch >> 5)) * 576u);
+    }
+    static __device__ __forceinline__ int mov_col(int x) { return (x >> 5) * 576 + (x & 31); }
+    static __device__ __forceinline__ long long flow_row(int y, const StepParams& P) { return block_row(y, P.pitch, 9); }
+    static __device__ __forceinline__ int flow_col(int x) { return block_col(x, 9); }
+    static __device__ __forceinline__ void store_mov(void* sc, int q, long long e, float v)
+    {
+        ((H*)sc)[e + 32 * slot(q)] = Conv<H>::from(v * scale(q));
+    }
+    static __device__ __forceinline__ void store_flow(void* fl, int i, long long e, float v)
+    {
+        ((H*)fl)[e + 32 * i] = Conv<H>::from(v * (float)S_FL);
     }
 };
 using StoreF16 = Store16<__half, 16, 1024>;

@@ -21,29 +21,18 @@ inline size_t flow_node_bytes(int storage) { return storage == kStoreF32 ? 9 * 4
 // One coupled step (Sec. 3 + Sec. 4): the fused kernel, the wall kernels and
 // the n_sub - 1 flow-only sub-steps; on return cs/cf name the newest buffers.
 struct StepBuffers {
-    void* sc[2];           // scalar populations (phi, C, H): planes 0..14
-    void* fl[2];           // flow populations: planes 15..23
-    float* hist;           // kHist planes
+    void* sc[2];           // scalar populations (phi, C, H): planes 0..14, node blocks
+    void* fl[2];           // flow populations: planes 15..23, node blocks
+    float* hist;           // kHist planes, node blocks
     float* fb;             // force plane for flow sub-steps (n_sub > 1) or null
     const uint8_t* grain;  // grain id plane or null (uniform orientation)
     int cs, cf;            // indices of the buffers holding the newest populations
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // recorded around the timed kernels when set
     int ev_substeps = 0;   // 0: the events bracket the fused kernel; 1: the n_sub - 1 flow sub-step kernels
-    const struct StepMaps* maps = nullptr;  // TMA descriptors: use the TMA-staged fused kernel when set
 };
 
-// TMA descriptors of a handle's buffers for the TMA-staged fused kernel
-// (FP32 storage, grids of at least 40 x 10 nodes): cudaErrorNotSupported
-// otherwise.  The buffers of B must stay where they are while the maps live.
-struct StepMaps;
-bool step_maps_supported(const StepParams& P, int storage);
-cudaError_t create_step_maps(const StepParams& P, int storage, const StepBuffers& B, StepMaps** out);
-void destroy_step_maps(StepMaps* m);
-// Flag raised when a bounded wait of the TMA-staged kernel expired.
-cudaError_t step_error(int* flag, bool clear);
-
 // One coupled step.  skip_columns: leave out the column pass of the left/right
-// walls (the tiled kernel with n_sub = 1 and walls in x; ignored otherwise);
+// walls (n_sub = 1 and walls in x; ignored otherwise);
 // the next step must then be launched with `repair`, which applies that
 // update to the wall cells as they are loaded.  A state read or kept between
 // launches must come from a step without skip_columns.
@@ -118,11 +107,12 @@ cudaError_t launch_phi_mismatch(const float* a, const float* b, long long n, uns
 cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out, int y0,
                           int rows, cudaStream_t s);
 
-// Decode a band's populations to FP32 band planes / encode them back.
-cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, float* out, int y0,
+// Decode a band's populations and history to FP32 band planes (24
+// population deviations, then the kHist history values) / encode them back.
+cudaError_t launch_decode(const StepParams& P, int storage, const void* sc, const void* fl, const float* hist,
+                          float* out, int y0, int rows, cudaStream_t s);
+cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, float* hist, int y0,
                           int rows, cudaStream_t s);
-cudaError_t launch_encode(const StepParams& P, int storage, const float* in, void* sc, void* fl, int y0, int rows,
-                          cudaStream_t s);
 
 // Metrics reductions (FP64 results): out[0..6] = solid fraction sum, sum C, sum H, sum h,
 // max |u| (flow lattice units), non-finite count, sum phi; then out[7..9] =

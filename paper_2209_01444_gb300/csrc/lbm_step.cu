@@ -19,29 +19,14 @@
 // overwrites completely: the wall kernel after the step, or, for the left and
 // right walls of steps inside a captured step graph, the next step as it
 // loads them (coupled_tile).
-#include <cuda.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 #include <stddef.h>
 
-#include <mutex>
 #include <type_traits>
 
-#include "lbm_tma.cuh"
 #include "lbm_kernels.h"
 
 namespace lbm {
-
-// Tensor maps of the TMA-staged fused kernel for one pair of source buffers.
-struct StepTensorMaps {
-    CUtensorMap f, ng, h, hist, grain;
-    CUtensorMap f_rest, ng_rest;  // 16-bit storage: the FP32 rest planes of phi and of C, H
-};
-
-struct StepMaps {
-    StepTensorMaps m[2][2];  // [scalar buffer index][flow buffer index]
-    int ctas;                // persistent CTAs: resident CTAs per SM x SMs
-};
 
 namespace {
 
@@ -146,7 +131,6 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
                                              const float (&fs)[5][TYV + 2][FW],
                                              const float (&ps)[TYV + 2][TX + 2])
 {
-    const long long plane = P.plane;
     const long long o = (long long)y * P.pitch + x;
     const int fx = lx - 1 + XO;
 
@@ -231,36 +215,45 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
     float ho[9];
     collide_flow(h, m, P.s2u, ho);
 
-    // ---- push streaming
+    // ---- push streaming: the rest populations stay at o; every moving one
+    // goes to the neighbour node (x + c_x, y + c_y), whose element index is a
+    // row term plus a column term (three of each)
     const int xp = (x + 1 == P.nx) ? 0 : x + 1, xm = (x == 0) ? P.nx - 1 : x - 1;
     const int yp = (y + 1 == P.ny) ? 0 : y + 1, ym = (y == 0) ? P.ny - 1 : y - 1;
-    const long long rY = (long long)y * P.pitch, rP = (long long)yp * P.pitch, rM = (long long)ym * P.pitch;
-    const long long d5[5] = {rY + x, rY + xp, rP + x, rY + xm, rM + x};
-    const long long d9[9] = {rY + x, rY + xp, rP + x, rY + xm, rM + x, rP + xp, rP + xm, rM + xm, rM + xp};
-
     {
+        const long long rY = Store::mov_row(y, P), rP = Store::mov_row(yp, P), rM = Store::mov_row(ym, P);
+        const int c0 = Store::mov_col(x), cP = Store::mov_col(xp), cM = Store::mov_col(xm);
+        const long long d5[5] = {0, rY + cP, rP + c0, rY + cM, rM + c0};
         // modified streaming of the phase field: the destination's time-n
         // population sits in the shared tile (its halo is periodic-wrapped)
         const float ia = 1.0f / as2, ib = ia - 1.0f;
         const float fd[5] = {fs[0][ly][fx], fs[1][ly][fx + 1], fs[2][ly + 1][fx], fs[3][ly][fx - 1],
                              fs[4][ly - 1][fx]};
+        Store::store(dst, dstf, kF, o, fo[0] * ia - ib * fd[0], P);
+        Store::store(dst, dstf, kN, o, no[0], P);
+        Store::store(dst, dstf, kG, o, go[0], P);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) Store::store(dst, dstf, kF + i, d5[i], fo[i] * ia - ib * fd[i], P);
+        for (int i = 1; i < 5; ++i) Store::store_mov(dst, kF + i, d5[i], fo[i] * ia - ib * fd[i]);
+#pragma unroll
+        for (int i = 1; i < 5; ++i) Store::store_mov(dst, kN + i, d5[i], no[i]);
+#pragma unroll
+        for (int i = 1; i < 5; ++i) Store::store_mov(dst, kG + i, d5[i], go[i]);
     }
+    {
+        const long long rY = Store::flow_row(y, P), rP = Store::flow_row(yp, P), rM = Store::flow_row(ym, P);
+        const int c0 = Store::flow_col(x), cP = Store::flow_col(xp), cM = Store::flow_col(xm);
+        const long long d9[9] = {rY + c0, rY + cP, rP + c0, rY + cM, rM + c0, rP + cP, rP + cM, rM + cM, rM + cP};
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(dst, dstf, kN + i, d5[i], no[i], P);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) Store::store(dst, dstf, kG + i, d5[i], go[i], P);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Store::store(dst, dstf, kH + i, d9[i], ho[i], P);
+        for (int i = 0; i < 9; ++i) Store::store_flow(dstf, i, d9[i], ho[i]);
+    }
 
     // ---- history of the backward differences
-    hist[0 * plane + o] = m.phi;
-    hist[1 * plane + o] = Q;
-    hist[2 * plane + o] = (1.0f + m.dC) * usx;
-    hist[3 * plane + o] = (1.0f + m.dC) * usy;
-    hist[4 * plane + o] = m.H * usx;
-    hist[5 * plane + o] = m.H * usy;
+    hist_at(hist, 0, o) = m.phi;
+    hist_at(hist, 1, o) = Q;
+    hist_at(hist, 2, o) = (1.0f + m.dC) * usx;
+    hist_at(hist, 3, o) = (1.0f + m.dC) * usy;
+    hist_at(hist, 4, o) = m.H * usx;
+    hist_at(hist, 5, o) = m.H * usy;
     if (WRITE_FB) fb[o] = m.Fy;
 }
 
@@ -287,7 +280,6 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
                                              int xfix = 0)
 {
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const long long plane = P.plane;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < P.nx && y < P.ny;
     // XWALL: C, H and flow populations of the tile's own wall nodes, computed
@@ -333,10 +325,11 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
     for (int i = 0; i < 5; ++i) g[i] = Store::load(src, srcf, kG + i, o, P);
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] = Store::load(src, srcf, kH + i, o, P);
-    const float phi_prev = hist[0 * plane + o];
-    const float Q_prev = hist[1 * plane + o];
-    const float Cux_prev = hist[2 * plane + o], Cuy_prev = hist[3 * plane + o];
-    const float Hux_prev = hist[4 * plane + o], Huy_prev = hist[5 * plane + o];
+    const float* hn = hist;
+    const float phi_prev = hist_at(hn, 0, o);
+    const float Q_prev = hist_at(hn, 1, o);
+    const float Cux_prev = hist_at(hn, 2, o), Cuy_prev = hist_at(hn, 3, o);
+    const float Hux_prev = hist_at(hn, 4, o), Huy_prev = hist_at(hn, 5, o);
     uint8_t gid = 0;
     if (GRAIN && grain) gid = grain[o];
 
@@ -417,301 +410,6 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MIN_BLOCKS)
     coupled_tile<Store, GRAIN, WRITE_FB, TY, XWALL>(P, src, srcf, dst, dstf, hist, grain, fb, blockIdx.x * TX,
                                                     blockIdx.y * TY, fs, ps, xfix);
 }
-
-// ------------------------------------------------------- TMA-staged variant
-// The same per-node update (coupled_node) with the tile's inputs staged in
-// shared memory by TMA.  Persistent CTAs walk the tiles; while a CTA computes
-// one tile, the copies of its next tile are in flight into the other of two
-// stages, so the loads no longer wait in registers (the register-staged
-// kernel holds 25 loads per thread across its tile barrier).  FP32 storage.
-//
-// Per stage, five boxes of the populations at time n (x fastest):
-//   f:     phi populations, x0 - 4 .. x0 + 35 (a 16-byte aligned start that
-//          covers the one-node halo), y0 - 1 .. y0 + TY, planes 0..4;
-//   ng:    C and H populations of the tile, planes 5..14;
-//   h:     flow populations of the tile;
-//   hist:  the kHist history planes of the tile;
-//   grain: grain ids of the tile (grain map only).
-// Boxes reaching past the grid are zero-filled by TMA; the halo cells there
-// are then loaded with the periodic wrap the register-staged kernel uses.
-namespace tmastep {
-
-constexpr int FW = 40;          // f-box row: x0 - 4 .. x0 + 35
-constexpr int XO = 4;           // column of node x0 in the f-box
-constexpr int kStages = 2;
-constexpr int kMinBlocks = 3;   // resident CTAs per SM (shared memory and registers)
-
-struct __align__(128) Stage {
-    float f[5][TY + 2][FW];
-    float pad[16];  // next box 128-byte aligned
-    float ng[10][TY][TX];
-    float h[9][TY][TX];
-    float hist[kHist][TY][TX];
-    uint8_t grain[TY][TX];
-};
-static_assert(offsetof(Stage, ng) % 128 == 0 && offsetof(Stage, h) % 128 == 0, "TMA box alignment");
-static_assert(offsetof(Stage, hist) % 128 == 0 && offsetof(Stage, grain) % 128 == 0, "TMA box alignment");
-static_assert(sizeof(Stage) % 128 == 0, "stage alignment");
-
-constexpr uint32_t kBytesF = sizeof(float) * 5 * (TY + 2) * FW;
-constexpr uint32_t kBytesNG = sizeof(float) * 10 * TY * TX;
-constexpr uint32_t kBytesH = sizeof(float) * 9 * TY * TX;
-constexpr uint32_t kBytesHist = sizeof(float) * kHist * TY * TX;
-constexpr uint32_t kBytesGrain = TY * TX;
-constexpr size_t kSmemBytes = kStages * sizeof(Stage) + 128;  // + alignment slack
-
-__device__ int g_step_error;  // set when a bounded wait of the staged kernel expired
-
-using Maps = StepTensorMaps;
-
-__device__ __forceinline__ void issue(Stage& st, uint64_t* bar, const Maps& M, bool grain, int x0, int y0)
-{
-    tma_mbar_expect(bar, kBytesF + kBytesNG + kBytesH + kBytesHist + (grain ? kBytesGrain : 0));
-    tma_load_3d(&st.f[0][0][0], &M.f, x0 - XO, y0 - 1, kF, bar);
-    tma_load_3d(&st.ng[0][0][0], &M.ng, x0, y0, kN, bar);
-    tma_load_3d(&st.h[0][0][0], &M.h, x0, y0, 0, bar);
-    tma_load_3d(&st.hist[0][0][0], &M.hist, x0, y0, 0, bar);
-    if (grain) tma_load_2d(&st.grain[0][0], &M.grain, x0, y0, bar);
-}
-
-template <bool GRAIN, bool WRITE_FB>
-__global__ void __launch_bounds__(TX* TY, kMinBlocks)
-    k_coupled_step_tma(const StepParams P, const __grid_constant__ Maps M, const void* __restrict__ src,
-                       void* __restrict__ dst, void* __restrict__ dstf, float* __restrict__ hist,
-                       const uint8_t* __restrict__ grain, float* __restrict__ fb, int tiles_x, int ntiles)
-{
-    extern __shared__ unsigned char smem_raw[];
-    Stage* stages = (Stage*)(smem_raw + ((128u - (tma_smem_u32(smem_raw) & 127u)) & 127u));
-    __shared__ uint64_t full[kStages];
-    __shared__ float ps[TY + 2][TX + 2];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const bool has_grain = GRAIN && grain != nullptr;
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) tma_mbar_init(&full[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&M.f) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&M.ng) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&M.h) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&M.hist) : "memory");
-    }
-    __syncthreads();
-    int tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles)
-        issue(stages[0], &full[0], M, has_grain, (tile % tiles_x) * TX, (tile / tiles_x) * TY);
-    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        const int s = it & 1;
-        const int next = tile + gridDim.x;
-        if (tid == 0 && next < ntiles) {
-            // stage s ^ 1 was released by the barrier that ended the last tile
-            issue(stages[s ^ 1], &full[s ^ 1], M, has_grain, (next % tiles_x) * TX, (next / tiles_x) * TY);
-        }
-        const bool ok = tma_mbar_wait(&full[s], (uint32_t)((it >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicExch(&g_step_error, 1);
-                // let the copies in flight land (bounded) before the CTA exits
-                tma_mbar_wait(&full[s], (uint32_t)((it >> 1) & 1));
-                if (next < ntiles) tma_mbar_wait(&full[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
-            }
-            return;
-        }
-        Stage& st = stages[s];
-        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
-
-        // halo cells outside the grid: periodic wrap, as the register-staged
-        // kernel loads them; then phi = sum f on the tile and its halo
-        const bool edge = x0 == 0 || y0 == 0 || x0 + TX + 1 > P.nx || y0 + TY + 1 > P.ny;
-        for (int e = tid; e < (TX + 2) * (TY + 2); e += TX * TY) {
-            const int hx = e % (TX + 2), hy = e / (TX + 2);
-            const int c = hx + XO - 1;
-            if (edge) {
-                const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-                if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny) {
-                    const long long oh = (long long)wrap(gy, P.ny) * P.pitch + wrap(gx, P.nx);
-#pragma unroll
-                    for (int i = 0; i < 5; ++i) st.f[i][hy][c] = ((const float*)src)[(kF + i) * P.plane + oh];
-                }
-            }
-            float sum = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) sum += st.f[i][hy][c];
-            ps[hy][hx] = sum;
-        }
-        __syncthreads();
-
-        const int x = x0 + tx, y = y0 + ty;
-        if (x < P.nx && y < P.ny) {
-            float f[5], n[5], g[5], h[9];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) f[i] = st.f[i][ty + 1][tx + XO];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) n[i] = st.ng[i][ty][tx];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) g[i] = st.ng[5 + i][ty][tx];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) h[i] = st.h[i][ty][tx];
-            const uint8_t gid = has_grain ? st.grain[ty][tx] : (uint8_t)0;
-            coupled_node<StoreF32, GRAIN, WRITE_FB, TY, FW, XO>(
-                P, dst, dstf, hist, fb, x, y, tx + 1, ty + 1, f, n, g, h, st.hist[0][ty][tx], st.hist[1][ty][tx],
-                st.hist[2][ty][tx], st.hist[3][ty][tx], st.hist[4][ty][tx], st.hist[5][ty][tx], has_grain, gid,
-                st.f, ps);
-        }
-        tma_fence_proxy();  // this thread's accesses of stage s precede the TMA copies that refill it
-        __syncthreads();    // stage s and ps are free again
-    }
-}
-
-
-// 16-bit storage (FP16 or BF16 deviations, FP32 rest planes).  The boxes of a
-// stage hold the raw 16-bit values; each tile decodes its phi populations
-// and halo into an FP32 tile (the layout of the tiled kernel), and each node
-// decodes its own populations from shared memory, with the same conversion
-// and scale as Store16::load.  A stage is 22.7 KB, so four CTAs (32 warps)
-// fit on an SM, as many as the tiled kernel keeps.
-constexpr int FW16 = 48;          // 16-bit phi box row: x0 - 8 .. x0 + 39 (16-byte aligned start)
-constexpr int XO16 = 8;
-constexpr int kMinBlocks16 = 4;
-
-struct __align__(128) Stage16 {
-    uint16_t fm[4][TY + 2][FW16];   // phi moving planes (slots 0..3)
-    float fr[TY + 2][FW];           // phi rest plane, x0 - 4 .. x0 + 35
-    float pad[16];
-    uint16_t ngm[8][TY][TX];        // C and H moving planes (slots 4..11)
-    float ngr[2][TY][TX];           // C and H rest planes
-    uint16_t h[9][TY][TX];
-    float hist[kHist][TY][TX];
-    uint8_t grain[TY][TX];
-};
-static_assert(offsetof(Stage16, fr) % 128 == 0 && offsetof(Stage16, ngm) % 128 == 0, "TMA box alignment");
-static_assert(offsetof(Stage16, ngr) % 128 == 0 && offsetof(Stage16, h) % 128 == 0, "TMA box alignment");
-static_assert(offsetof(Stage16, hist) % 128 == 0 && offsetof(Stage16, grain) % 128 == 0, "TMA box alignment");
-static_assert(sizeof(Stage16) % 128 == 0, "stage alignment");
-
-constexpr uint32_t kBytes16 = 2 * 4 * (TY + 2) * FW16 + 4 * (TY + 2) * FW + 2 * 8 * TY * TX + 4 * 2 * TY * TX +
-                              2 * 9 * TY * TX + 4 * kHist * TY * TX;
-constexpr size_t kSmemBytes16 = kStages * sizeof(Stage16) + 128;
-
-__device__ __forceinline__ void issue16(Stage16& st, uint64_t* bar, const Maps& M, bool grain, int x0, int y0)
-{
-    tma_mbar_expect(bar, kBytes16 + (grain ? kBytesGrain : 0));
-    tma_load_3d(&st.fm[0][0][0], &M.f, x0 - XO16, y0 - 1, 0, bar);
-    tma_load_3d(&st.fr[0][0], &M.f_rest, x0 - XO, y0 - 1, 0, bar);
-    tma_load_3d(&st.ngm[0][0][0], &M.ng, x0, y0, 4, bar);
-    tma_load_3d(&st.ngr[0][0][0], &M.ng_rest, x0, y0, 1, bar);
-    tma_load_3d(&st.h[0][0][0], &M.h, x0, y0, 0, bar);
-    tma_load_3d(&st.hist[0][0][0], &M.hist, x0, y0, 0, bar);
-    if (grain) tma_load_2d(&st.grain[0][0], &M.grain, x0, y0, bar);
-}
-
-template <class H>
-__device__ __forceinline__ H __ushort_as_half_or_bf16(uint16_t raw);
-template <>
-__device__ __forceinline__ __half __ushort_as_half_or_bf16<__half>(uint16_t raw)
-{
-    return __ushort_as_half(raw);
-}
-template <>
-__device__ __forceinline__ __nv_bfloat16 __ushort_as_half_or_bf16<__nv_bfloat16>(uint16_t raw)
-{
-    return __ushort_as_bfloat16(raw);
-}
-
-template <class Store>
-__device__ __forceinline__ float dec16(uint16_t raw, int q)
-{
-    return Conv<typename Store::T>::to(__ushort_as_half_or_bf16<typename Store::T>(raw)) * Store::inv_scale(q);
-}
-
-template <class Store, bool GRAIN, bool WRITE_FB>
-__global__ void __launch_bounds__(TX* TY, kMinBlocks16)
-    k_coupled_step_tma16(const StepParams P, const __grid_constant__ Maps M, const void* __restrict__ src,
-                         void* __restrict__ dst, void* __restrict__ dstf, float* __restrict__ hist,
-                         const uint8_t* __restrict__ grain, float* __restrict__ fb, int tiles_x, int ntiles)
-{
-    extern __shared__ unsigned char smem_raw[];
-    Stage16* stages = (Stage16*)(smem_raw + ((128u - (tma_smem_u32(smem_raw) & 127u)) & 127u));
-    __shared__ uint64_t full[kStages];
-    __shared__ float fs[5][TY + 2][TX + 2];
-    __shared__ float ps[TY + 2][TX + 2];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const bool has_grain = GRAIN && grain != nullptr;
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) tma_mbar_init(&full[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    int tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles)
-        issue16(stages[0], &full[0], M, has_grain, (tile % tiles_x) * TX, (tile / tiles_x) * TY);
-    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        const int s = it & 1;
-        const int next = tile + gridDim.x;
-        if (tid == 0 && next < ntiles)
-            issue16(stages[s ^ 1], &full[s ^ 1], M, has_grain, (next % tiles_x) * TX, (next / tiles_x) * TY);
-        const bool ok = tma_mbar_wait(&full[s], (uint32_t)((it >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicExch(&g_step_error, 1);
-                tma_mbar_wait(&full[s], (uint32_t)((it >> 1) & 1));
-                if (next < ntiles) tma_mbar_wait(&full[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
-            }
-            return;
-        }
-        Stage16& st = stages[s];
-        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
-
-        // decoded phi populations of the tile and halo (cells outside the
-        // grid: periodic wrap, as the tiled kernel loads them), and phi there
-        const bool edge = x0 == 0 || y0 == 0 || x0 + TX + 1 > P.nx || y0 + TY + 1 > P.ny;
-        for (int e = tid; e < (TX + 2) * (TY + 2); e += TX * TY) {
-            const int hx = e % (TX + 2), hy = e / (TX + 2);
-            float v[5];
-            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-            if (edge && (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny)) {
-                const long long oh = (long long)wrap(gy, P.ny) * P.pitch + wrap(gx, P.nx);
-#pragma unroll
-                for (int i = 0; i < 5; ++i) v[i] = Store::load(src, nullptr, kF + i, oh, P);
-            } else {
-                v[0] = st.fr[hy][hx + XO - 1];
-#pragma unroll
-                for (int i = 1; i < 5; ++i) v[i] = dec16<Store>(st.fm[i - 1][hy][hx + XO16 - 1], kF + i);
-            }
-            float sum = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                fs[i][hy][hx] = v[i];
-                sum += v[i];
-            }
-            ps[hy][hx] = sum;
-        }
-        __syncthreads();
-
-        const int x = x0 + tx, y = y0 + ty;
-        if (x < P.nx && y < P.ny) {
-            float f[5], n[5], g[5], h[9];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) f[i] = fs[i][ty + 1][tx + 1];
-            n[0] = st.ngr[0][ty][tx];
-            g[0] = st.ngr[1][ty][tx];
-#pragma unroll
-            for (int i = 1; i < 5; ++i) {
-                n[i] = dec16<Store>(st.ngm[i - 1][ty][tx], kN + i);
-                g[i] = dec16<Store>(st.ngm[3 + i][ty][tx], kG + i);
-            }
-#pragma unroll
-            for (int i = 0; i < 9; ++i) h[i] = dec16<Store>(st.h[i][ty][tx], kH + i);
-            const uint8_t gid = has_grain ? st.grain[ty][tx] : (uint8_t)0;
-            coupled_node<Store, GRAIN, WRITE_FB, TY, TX + 2, 1>(
-                P, dst, dstf, hist, fb, x, y, tx + 1, ty + 1, f, n, g, h, st.hist[0][ty][tx], st.hist[1][ty][tx],
-                st.hist[2][ty][tx], st.hist[3][ty][tx], st.hist[4][ty][tx], st.hist[5][ty][tx], has_grain, gid,
-                fs, ps);
-        }
-        tma_fence_proxy();
-        __syncthreads();
-    }
-}
-
-}  // namespace tmastep
 
 // Descriptors of the batch being stepped, in constant memory: the domain
 // index is uniform across a CTA, so parameter reads are broadcast from the
@@ -813,11 +511,13 @@ __device__ __forceinline__ void flow_wall_repair(const StepParams& P, const void
 // flow-only wall pass, so wall nodes first take the populations it would have
 // given them (flow_wall_repair; sc holds the newest scalar populations, whose
 // macros the wall scheme uses).
+// phi: plane 0 of a node-block array of phi_np planes (the history, or the
+// frozen phi of flow-only steps, phi_np = 1: a plain plane).
 template <class Store>
 __global__ void __launch_bounds__(256, 8) k_flow_substep(const StepParams P, const void* __restrict__ src,
-                                                      void* __restrict__ dst, const float* __restrict__ hist,
-                                                      const float* __restrict__ fb, const void* __restrict__ sc,
-                                                      int repair)
+                                                      void* __restrict__ dst, const float* __restrict__ phi,
+                                                      int phi_np, const float* __restrict__ fb,
+                                                      const void* __restrict__ sc, int repair)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -832,7 +532,7 @@ __global__ void __launch_bounds__(256, 8) k_flow_substep(const StepParams P, con
         if (wx || wy) flow_wall_repair<Store>(P, sc, src, x, y, wx, wy, h);
     }
     Macro m;
-    m.phi = hist[o];
+    m.phi = phi[block_index(o, phi_np)];
     m.p1 = m.phi + 1.0f;
     m.Fx = P.Fx;
     m.Fy = fb[o];
@@ -850,10 +550,11 @@ __global__ void __launch_bounds__(256, 8) k_flow_substep(const StepParams P, con
     collide_flow(h, m, P.s2u, ho);
     const int xp = (x + 1 == P.nx) ? 0 : x + 1, xm = (x == 0) ? P.nx - 1 : x - 1;
     const int yp = (y + 1 == P.ny) ? 0 : y + 1, ym = (y == 0) ? P.ny - 1 : y - 1;
-    const long long rY = (long long)y * P.pitch, rP = (long long)yp * P.pitch, rM = (long long)ym * P.pitch;
-    const long long d9[9] = {rY + x, rY + xp, rP + x, rY + xm, rM + x, rP + xp, rP + xm, rM + xm, rM + xp};
+    const long long rY = Store::flow_row(y, P), rP = Store::flow_row(yp, P), rM = Store::flow_row(ym, P);
+    const int c0 = Store::flow_col(x), cP = Store::flow_col(xp), cM = Store::flow_col(xm);
+    const long long d9[9] = {rY + c0, rY + cP, rP + c0, rY + cM, rM + c0, rP + cP, rP + cM, rM + cM, rM + cP};
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store::store(nullptr, dst, kH + i, d9[i], ho[i], P);
+    for (int i = 0; i < 9; ++i) Store::store_flow(dst, i, d9[i], ho[i]);
 }
 
 template <class Store>
@@ -946,75 +647,11 @@ cudaError_t flow_steps_t(const StepParams& P, int n, void* sc, void* const fl[2]
     for (int k = 0; k < n; ++k) {
         // wall pass after the last step only; each later step repairs the wall
         // nodes it loads instead
-        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, fl[*cf], fl[1 - *cf], phi, fy, sc, k > 0);
+        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, fl[*cf], fl[1 - *cf], phi, 1, fy, sc, k > 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (k + 1 == n && (e = walls<Store>(P, sc, fl[1 - *cf], 1, s)) != cudaSuccess) return e;
         *cf = 1 - *cf;
     }
-    return e;
-}
-
-// ------------------------------------------------ TMA descriptors (host)
-PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
-std::mutex g_encode_mutex;
-
-cudaError_t tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* out)
-{
-    std::lock_guard<std::mutex> lock(g_encode_mutex);
-    if (!g_encode_tiled) {
-        cudaDriverEntryPointQueryResult q;
-        void* fn = nullptr;
-        cudaError_t e =
-            cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess) return e;
-        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-        g_encode_tiled = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
-    *out = g_encode_tiled;
-    return cudaSuccess;
-}
-
-// Tensor map of `planes` planes of an nx x ny grid (row pitch `pitch`,
-// plane stride `plane` elements) with the given box; zero fill outside.
-cudaError_t plane_map(CUtensorMap* tm, CUtensorMapDataType dt, size_t esize, const void* base, const StepParams& P,
-                      int planes, int bx, int by, int bq, CUtensorMapL2promotion promo)
-{
-    PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
-    cudaError_t e = tensor_map_encoder(&enc);
-    if (e != cudaSuccess) return e;
-    const cuuint32_t rank = planes > 1 ? 3 : 2;
-    cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)planes};
-    cuuint64_t strides[2] = {(cuuint64_t)P.pitch * esize, (cuuint64_t)P.plane * esize};
-    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bq};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(tm, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, promo,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-template <bool G, bool W>
-cudaError_t tma_attributes()
-{
-    return cudaFuncSetAttribute(tmastep::k_coupled_step_tma<G, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tmastep::kSmemBytes);
-}
-
-template <class Store>
-cudaError_t tma16_attributes()
-{
-    const int b = (int)tmastep::kSmemBytes16;
-    cudaError_t e = cudaFuncSetAttribute(tmastep::k_coupled_step_tma16<Store, true, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tmastep::k_coupled_step_tma16<Store, true, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tmastep::k_coupled_step_tma16<Store, false, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tmastep::k_coupled_step_tma16<Store, false, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     return e;
 }
 
@@ -1028,58 +665,13 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
     void* dstf = B.fl[1 - B.cf];
     const bool grain = B.grain != nullptr, wfb = n_sub > 1;
     if (B.ev_begin && !B.ev_substeps) cudaEventRecord(B.ev_begin, s);
-    const StepMaps* SM = B.maps;
-    bool staged = false;
-    if constexpr (!std::is_same<Store, StoreF32>::value) {
-        if (SM) {
-            staged = true;
-            const tmastep::Maps& M = SM->m[B.cs][B.cf];
-            const int tiles_x = (P.nx + TX - 1) / TX, ntiles = tiles_x * ((P.ny + TY - 1) / TY);
-            const int ctas = ntiles < SM->ctas ? ntiles : SM->ctas;
-            const size_t sm = tmastep::kSmemBytes16;
-            if (grain && wfb)
-                tmastep::k_coupled_step_tma16<Store, true, true>
-                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-            else if (grain)
-                tmastep::k_coupled_step_tma16<Store, true, false>
-                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-            else if (wfb)
-                tmastep::k_coupled_step_tma16<Store, false, true>
-                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-            else
-                tmastep::k_coupled_step_tma16<Store, false, false>
-                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-        }
-    } else {
-        if (SM) {
-            staged = true;
-            const tmastep::Maps& M = SM->m[B.cs][B.cf];
-            const int tiles_x = (P.nx + TX - 1) / TX, ntiles = tiles_x * ((P.ny + TY - 1) / TY);
-            const int ctas = ntiles < SM->ctas ? ntiles : SM->ctas;
-            const size_t sm = tmastep::kSmemBytes;
-            if (grain && wfb)
-                tmastep::k_coupled_step_tma<true, true>
-                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-            else if (grain)
-                tmastep::k_coupled_step_tma<true, false>
-                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-            else if (wfb)
-                tmastep::k_coupled_step_tma<false, true>
-                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-            else
-                tmastep::k_coupled_step_tma<false, false>
-                    <<<ctas, block, sm, s>>>(P, M, src, dst, dstf, B.hist, B.grain, B.fb, tiles_x, ntiles);
-        }
-    }
     // left/right walls: with skip_columns their column pass is left out and
     // the next step, launched with `repair`, updates them at its load
-    // (coupled_tile); only the tiled kernel with one flow step per coupled
-    // step does that, the other paths keep the column pass
-    const bool xwall = !staged && !wfb && !P.periodic_x;
+    // (coupled_tile); only steps with one flow step per coupled step do
+    // that, with flow sub-steps the column pass stays
+    const bool xwall = !wfb && !P.periodic_x;
     const int xfix = xwall ? repair : 0;
-    if (staged)
-        ;  // the TMA-staged kernel above
-    else if (xwall && grain)
+    if (xwall && grain)
         k_coupled_step<Store, true, false, true>
             <<<grid, block, 0, s>>>(P, src, srcf, dst, dstf, B.hist, B.grain, B.fb, xfix);
     else if (xwall)
@@ -1106,8 +698,8 @@ cudaError_t coupled_step(const StepParams& P, int n_sub, StepBuffers& B, cudaStr
         // flow-only wall pass runs after the last sub-step only: each later
         // sub-step repairs the wall nodes it loads instead.
         if (sub == 1 && B.ev_begin && B.ev_substeps) cudaEventRecord(B.ev_begin, s);
-        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, B.fl[B.cf], B.fl[1 - B.cf], B.hist, B.fb, B.sc[B.cs],
-                                                       sub > 1);
+        k_flow_substep<Store><<<fgrid, fblock, 0, s>>>(P, B.fl[B.cf], B.fl[1 - B.cf], B.hist, kHist, B.fb,
+                                                       B.sc[B.cs], sub > 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (sub + 1 == n_sub && B.ev_end && B.ev_substeps) cudaEventRecord(B.ev_end, s);
         if (sub + 1 == n_sub && (e = walls<Store>(P, B.sc[B.cs], B.fl[1 - B.cf], 1, s)) != cudaSuccess) return e;
@@ -1163,86 +755,6 @@ int batch_ctas_t()
 }
 
 }  // namespace
-
-bool step_maps_supported(const StepParams& P, int storage)
-{
-    // boxes no larger than the grid: the phi box (40 FP32 or 48 16-bit
-    // columns, TY + 2 rows)
-    return P.nx >= (storage == kStoreF32 ? tmastep::FW : tmastep::FW16) && P.ny >= TY + 2;
-}
-
-cudaError_t create_step_maps(const StepParams& P, int storage, const StepBuffers& B, StepMaps** out)
-{
-    *out = nullptr;
-    if (!step_maps_supported(P, storage)) return cudaErrorNotSupported;
-    StepMaps* M = new StepMaps();
-    cudaError_t e = cudaSuccess;
-    const bool b16 = storage != kStoreF32;
-    for (int c = 0; c < 2 && e == cudaSuccess; ++c)
-        for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
-            tmastep::Maps& m = M->m[c][d];
-            if (b16) {
-                const CUtensorMapL2promotion none = CU_TENSOR_MAP_L2_PROMOTION_NONE;
-                const CUtensorMapL2promotion line = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
-                const CUtensorMapDataType u16 = CU_TENSOR_MAP_DATA_TYPE_UINT16, f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-                const void* rest = (const char*)B.sc[c] + 24 * (size_t)P.plane;  // FP32 rest planes
-                e = plane_map(&m.f, u16, 2, B.sc[c], P, 12, tmastep::FW16, TY + 2, 4, none);
-                if (e == cudaSuccess) e = plane_map(&m.f_rest, f32, 4, rest, P, 3, tmastep::FW, TY + 2, 1, none);
-                if (e == cudaSuccess) e = plane_map(&m.ng, u16, 2, B.sc[c], P, 12, TX, TY, 8, line);
-                if (e == cudaSuccess) e = plane_map(&m.ng_rest, f32, 4, rest, P, 3, TX, TY, 2, line);
-                if (e == cudaSuccess) e = plane_map(&m.h, u16, 2, B.fl[d], P, 9, TX, TY, 9, line);
-                if (e == cudaSuccess) e = plane_map(&m.hist, f32, 4, B.hist, P, kHist, TX, TY, kHist, line);
-                if (e == cudaSuccess && B.grain)
-                    e = plane_map(&m.grain, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, B.grain, P, 1, TX, TY, 1, line);
-                continue;
-            }
-            // no promotion on the phi box: its 16-byte halo edges would pull
-            // whole 256-byte lines of the neighbouring tiles
-            const CUtensorMapL2promotion none = CU_TENSOR_MAP_L2_PROMOTION_NONE;
-            const CUtensorMapL2promotion line = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
-            e = plane_map(&m.f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.sc[c], P, 15, tmastep::FW, TY + 2, 5, none);
-            if (e == cudaSuccess)
-                e = plane_map(&m.ng, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.sc[c], P, 15, TX, TY, 10, line);
-            if (e == cudaSuccess)
-                e = plane_map(&m.h, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.fl[d], P, 9, TX, TY, 9, line);
-            if (e == cudaSuccess)
-                e = plane_map(&m.hist, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.hist, P, kHist, TX, TY, kHist, line);
-            if (e == cudaSuccess && B.grain)
-                e = plane_map(&m.grain, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, B.grain, P, 1, TX, TY, 1, line);
-        }
-    if (!b16) {
-        if (e == cudaSuccess) e = tma_attributes<true, true>();
-        if (e == cudaSuccess) e = tma_attributes<true, false>();
-        if (e == cudaSuccess) e = tma_attributes<false, true>();
-        if (e == cudaSuccess) e = tma_attributes<false, false>();
-    } else if (storage == kStoreF16) {
-        if (e == cudaSuccess) e = tma16_attributes<StoreF16>();
-    } else {
-        if (e == cudaSuccess) e = tma16_attributes<StoreBF16>();
-    }
-    int dev = 0, sms = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) {
-        delete M;
-        return e;
-    }
-    M->ctas = sms * (b16 ? tmastep::kMinBlocks16 : tmastep::kMinBlocks);
-    *out = M;
-    return cudaSuccess;
-}
-
-void destroy_step_maps(StepMaps* m) { delete m; }
-
-cudaError_t step_error(int* flag, bool clear)
-{
-    cudaError_t e = cudaMemcpyFromSymbol(flag, tmastep::g_step_error, sizeof(int));
-    if (e == cudaSuccess && clear && *flag) {
-        const int zero = 0;
-        e = cudaMemcpyToSymbol(tmastep::g_step_error, &zero, sizeof(int));
-    }
-    return e;
-}
 
 cudaError_t launch_batch_step(const BatchTables& T, int storage, int ty, int run, int parity, int ctas,
                               cudaStream_t s, int repair, int skip_columns)

@@ -68,9 +68,7 @@ SIGNATURES = {
     "lbm_init_seeds": (ct.c_int, [_H, ct.POINTER(lbm_seed), ct.c_int, ct.c_double, ct.c_double]),
     "lbm_init_fields": (ct.c_int, [_H, _DP, _DP]),
     "lbm_step": (ct.c_int, [_H, ct.c_int]),
-    "lbm_set_step_kernel": (ct.c_int, [_H, ct.c_int]),
     "lbm_set_io_chunk": (ct.c_int, [_H, ct.c_size_t]),
-    "lbm_step_kernel": (ct.c_int, [_H]),
     "lbm_synchronize": (ct.c_int, [_H]),
     "lbm_step_count": (ct.c_longlong, [_H]),
     "lbm_get_fields": (ct.c_int, [_H, ct.c_uint, _DP]),
@@ -276,17 +274,6 @@ class Simulation:
     def set_io_chunk(self, nbytes: int) -> None:
         """Size limit of the device band buffer of whole-grid transfers."""
         self._check(self.lib.lbm_set_io_chunk(self.h, int(nbytes)))
-
-    STEP_KERNELS = {"auto": 0, "tiled": 1, "tma": 2}
-
-    def set_step_kernel(self, kernel: str) -> None:
-        """'tiled', 'tma' or 'auto' (TMA where it applies): lbm_set_step_kernel."""
-        self._check(self.lib.lbm_set_step_kernel(self.h, self.STEP_KERNELS[kernel]))
-
-    @property
-    def step_kernel(self) -> str:
-        """The fused-step kernel lbm_step uses now: 'tiled' or 'tma'."""
-        return {1: "tiled", 2: "tma"}[int(self.lib.lbm_step_kernel(self.h))]
 
     @property
     def steps(self) -> int:

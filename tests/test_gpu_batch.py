@@ -46,6 +46,13 @@ def small_cases():
 
 @pytest.mark.parametrize("ty,run", [(4, 1), (8, 1), (16, 1), (8, 4), (4, 0), (16, 0)])
 def test_batch_matches_single_domain_runs(lbm, ty, run):
+    """Each domain of the batched launch evolves as it does alone in the
+    single-domain kernel.  Both run the same per-node code, inlined into
+    kernels with different tile heights, where the compiler may fuse a
+    product into a multiply-add differently: the fields agree to FP32
+    rounding grown over 37 steps (1e-5 of each field's scale; U, which
+    multiplies solute differences by up to 16 in the solid, shows the
+    largest, about 2e-6).  A misplaced load or store moves a field by O(0.1)."""
     cases = small_cases()
     b = lbm.Batch([c.params for c in cases])
     b.set_tiling(ty, run)
@@ -61,7 +68,7 @@ def test_batch_matches_single_domain_runs(lbm, ty, run):
         got, want = b.fields(j), s.fields()
         for k in want:
             scale = max(np.abs(want[k]).max(), 1e-6)
-            assert np.abs(got[k] - want[k]).max() <= 1e-6 * scale, (j, k)
+            assert np.abs(got[k] - want[k]).max() <= 1e-5 * scale, (j, k)
 
 
 def test_batch_matches_the_oracle(lbm):

@@ -112,23 +112,3 @@ def test_multi_seed_4096_windows_fp16(lbm):
     worst = max(worst, compare(g, case, 3000, 0, 24, ("periodic", "periodic", "noslip", "noslip"), ylo_wall=True,
                                tol=TOL16))
     print(f"FP16 full-size windows: worst population error {worst:.2e}")
-
-
-def test_tma_kernel_at_full_size(lbm):
-    """The TMA-staged kernel on the 4096^2 workload: the same windows as the
-    tiled kernel, to FP32 rounding (the same arithmetic, inlined into another
-    kernel, may fuse a product into a multiply-add differently), after the
-    bench's launch configuration has run 20 steps (a captured 16-step graph
-    and direct launches)."""
-    case = W.multi_seed()
-    out = []
-    for kernel in ("tiled", "tma"):
-        g = lbm.Simulation(case.params)
-        g.set_step_kernel(kernel)
-        g.init_seeds(case.seeds, case.U0, case.theta0)
-        g.step(20)
-        out.append([g.state_region(x, y, 48, 40) for x, y in ((0, 0), (2040, 1900), (4048, 4056))])
-        del g
-    for a, b in zip(*out):
-        assert float(np.abs(a - b).max()) <= 1e-5
-
