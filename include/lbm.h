@@ -533,21 +533,28 @@ LBM_API int lbm_nn_error(int clear);
  *
  * Inputs (device memory, read only): the scalar and flow population buffers of
  * a state for the problem *p, in the layout the library keeps (the two buffers
- * that lbm_save_state writes right after its header): each plane has
- * pitch*ny elements with pitch = nx rounded up to a multiple of 32 and holds the
- * deviations of one population from the reference equilibrium; the scalar
- * buffer has 15 FP32 planes (LBM_FP32) or 12 16-bit planes followed by the 3
- * FP32 rest planes (LBM_FP16/LBM_BF16); the flow buffer has 9 planes of the
- * storage type.  Output: `out`, 10 doubles in device memory: sum (1 + phi)/2,
+ * that lbm_save_state writes right after its header).  Each buffer holds the
+ * deviations of its populations from the reference equilibrium for
+ * pitch*ny nodes, pitch = nx rounded up to a multiple of 32, in blocks of 32
+ * nodes: node (x, y) is lane (y*pitch + x) % 32 of block (y*pitch + x) / 32,
+ * and a block stores each of its planes as 32 consecutive values, plane after
+ * plane.  A scalar block has the 15 FP32 planes f_0..4, n_0..4, g_0..4
+ * (LBM_FP32; 1920 bytes), or the 12 moving planes f_1..4, n_1..4, g_1..4 in
+ * 16 bits followed by the FP32 rest planes f_0, n_0, g_0 (LBM_FP16/LBM_BF16;
+ * 1152 bytes); a flow block has the 9 planes h_0..8 of the storage type.  Output: `out`, 10 doubles in device memory: sum (1 + phi)/2,
  * sum C, sum H, sum of all h_i, max |u| in flow lattice units, number of nodes
  * with a non-finite macro, sum phi, and the three tip distances of
  * lbm_metrics.tip.  The work is queued on `stream` (a cudaStream_t, NULL for the
  * legacy default stream) and the call returns without waiting.
  *
  * Limits and sharing: grids larger than 33,554,432 nodes are rejected with
- * LBM_EINVAL.  The first call on a device looks up the device address of the
- * static array (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  Every call shares the one array and leaves
+ * LBM_EINVAL.  A call made outside stream capture looks up the device
+ * address of the static array (cudaGetSymbolAddress, with the device current)
+ * and keeps it for that device and CUDA context (a device reset ends the
+ * context; the next call outside capture looks the address up again).  A call
+ * made while `stream` is being captured, with no address kept for the current
+ * context, is refused with LBM_EINVAL: make the first call on a device before
+ * any stream capture.  Every call shares the one array and leaves
  * its partial sums in it (each call overwrites every row it reads, so nothing
  * needs clearing), so calls whose kernels overlap on the GPU, for example on two
  * streams at once, race.  Errors: LBM_EINVAL for bad arguments or parameters,

@@ -2,10 +2,11 @@
 // cannot allocate device memory.  The only scratch, one row of partial sums
 // per block, is a file-scope device array that every GPU loading the library
 // holds until the process exits; nothing here calls cudaMalloc or cudaFree.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
-#include <atomic>
+#include <mutex>
 
 #include "lbm.h"
 #include "lbm_kernels.h"
@@ -24,26 +25,76 @@ constexpr int kVals = lbm::kRedValues;     // same partials as the handle's redu
 static __device__ __align__(256) double g_reduce_scratch[kMaxBlocks * kVals];
 
 constexpr int kMaxDevices = 64;
-std::atomic<double*> g_scratch_ptr[kMaxDevices];
 
-// Device address of the scratch array on the current device.  In host code
-// the name g_reduce_scratch is only a host-side stand-in, so the address is
-// looked up once per device with that device current.
-cudaError_t scratch_for_current_device(double** out)
+// Device address of the scratch array, per device, with the CUDA context it
+// was looked up in: a device reset ends that context, the module is loaded
+// again in the next one, and the old address is then stale.
+struct ScratchEntry {
+    unsigned long long ctx_id = 0;
+    double* ptr = nullptr;
+};
+std::mutex g_scratch_mutex;
+ScratchEntry g_scratch[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// Identifier of the CUDA context current on this thread (unique for the
+// life of the process).  Caller holds g_scratch_mutex.
+cudaError_t current_context_id(unsigned long long* id)
 {
+    if (!g_ctx_current || !g_ctx_id) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 4000, cudaEnableDefault, &qa);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess) return e;
+        if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            return cudaErrorNotSupported;
+        g_ctx_current = (CtxGetCurrentFn)a;
+        g_ctx_id = (CtxGetIdFn)b;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorContextIsDestroyed;
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorContextIsDestroyed;
+}
+
+// Device address of the scratch array for a call on `stream`.  In host code
+// the name g_reduce_scratch is only a host-side stand-in, so the address is
+// looked up with the device current: on every call outside stream capture,
+// and kept per device and context for calls made while the stream is being
+// captured.  *capture_first is set when a call under capture finds no
+// address looked up in the current context.
+cudaError_t scratch_for_stream(cudaStream_t stream, double** out, bool* capture_first)
+{
+    *capture_first = false;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    double* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
-    if (!p) {
-        void* q = nullptr;
-        e = cudaGetSymbolAddress(&q, g_reduce_scratch);
-        if (e != cudaSuccess) return e;
-        p = (double*)q;
-        g_scratch_ptr[dev].store(p, std::memory_order_release);
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(stream, &st)) != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    ScratchEntry& c = g_scratch[dev];
+    if (st != cudaStreamCaptureStatusNone && !c.ptr) {  // nothing looked up yet: refuse before any other call
+        *capture_first = true;
+        return cudaSuccess;
     }
-    *out = p;
+    unsigned long long id = 0;
+    if ((e = current_context_id(&id)) != cudaSuccess) return e;
+    if (st == cudaStreamCaptureStatusNone) {
+        void* q = nullptr;
+        if ((e = cudaGetSymbolAddress(&q, g_reduce_scratch)) != cudaSuccess) return e;
+        c.ctx_id = id;
+        c.ptr = (double*)q;
+    } else if (c.ctx_id != id) {
+        *capture_first = true;
+        return cudaSuccess;
+    }
+    *out = c.ptr;
     return cudaSuccess;
 }
 
@@ -79,10 +130,15 @@ extern "C" int lbm_reduce_noalloc(const lbm_params* p, const void* scalar_pops, 
     const long long blocks = (N + kNodesPerBlock - 1) / kNodesPerBlock;
     if (blocks > kMaxBlocks)
         return fail(LBM_EINVAL, "lbm_reduce_noalloc: grid larger than its 33554432-node limit");
-    double* scratch = nullptr;
-    cudaError_t e = scratch_for_current_device(&scratch);
-    if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)stream;
+    double* scratch = nullptr;
+    bool capture_first = false;
+    cudaError_t e = scratch_for_stream(s, &scratch, &capture_first);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
+    if (capture_first)
+        return fail(LBM_EINVAL,
+                    "lbm_reduce_noalloc: the stream is being captured and no earlier call on this device and "
+                    "context looked up the scratch address; make one call before capture");
     switch (p->storage) {
     case LBM_FP16:
         k_reduce_chunks<lbm::StoreF16><<<(unsigned)blocks, kThreads, 0, s>>>(P, scalar_pops, flow_pops, scratch);

@@ -82,6 +82,117 @@ def test_noalloc_reduction_matches_the_handle_reduction_twice_in_a_row(storage):
         _compare(got, m, case.nodes, vscale)
 
 
+def _exactly_equal(got, m, nodes, vscale):
+    """Both paths fold the same per-node terms in the same blocks and order
+    (one shared reduction routine), so every output is the same double."""
+    assert got[0] / nodes == m["solid_fraction"]
+    for i, k in ((1, "sum_C"), (2, "sum_H"), (3, "sum_h"), (6, "sum_phi")):
+        assert got[i] == m[k], k
+    assert got[4] / vscale == m["max_u"]
+    assert got[5] == 0 and m["nonfinite"] == 0
+    for j, k in enumerate(("tip_px", "tip_mx", "tip_py")):
+        assert got[7 + j] == m[k], k
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_noalloc_reduction_on_a_ragged_grid_equals_the_handle_exactly(storage):
+    """131 x 97 nodes: a row pitch of 160 (the padding columns must be
+    skipped) and 12,707 nodes, so the last of the four blocks of 4096 nodes
+    is partial (419 nodes).  Two calls in a row on two states, every output
+    compared for equality."""
+    torch = pytest.importorskip("torch")
+    from paper_2209_01444_gb300 import build_ext, lbm
+
+    build_ext.build()
+    lbm.load()
+    params = W.thermosolutal_params(131, 97, bc=("inflow", "outflow", "symmetry", "symmetry"), u_in=(0.2, 0.0),
+                                    gbetaT=W.GBETA_T, gbetaC=W.GBETA_C)
+    seeds = np.array([[49.0, 48.0, 7.0, 0.3]])
+    sim = lbm.Simulation(params, storage, stream=torch.cuda.current_stream())
+    sim.init_seeds(seeds, -0.2, -0.5)
+    vscale = params["dt"] / params["n_sub"] / params["dx"]
+    for steps in (25, 40):
+        sim.step(steps)
+        m = sim.metrics(49.0, 48.0, 0.3)
+        d_sc, d_fl = _device_buffers(torch, sim, params, storage)
+        got = _noalloc(lbm, torch, params, storage, d_sc, d_fl, 49.0, 48.0, 0.3)
+        _exactly_equal(got, m, 131 * 97, vscale)
+
+
+def test_noalloc_reduction_allocates_no_device_memory():
+    """After one call (which looks up the static array's address), further
+    calls change neither the device's free memory nor the memory the torch
+    caching allocator holds: the entry point allocates nothing."""
+    torch = pytest.importorskip("torch")
+    from paper_2209_01444_gb300 import build_ext, lbm
+
+    build_ext.build()
+    lbm.load()
+    case = W.single_seed_periodic(n=128)
+    sim = lbm.Simulation(case.params, "fp32", stream=torch.cuda.current_stream())
+    sim.init_seeds(case.seeds, case.U0, case.theta0)
+    sim.step(10)
+    d_sc, d_fl = _device_buffers(torch, sim, case.params, "fp32")
+    first = _noalloc(lbm, torch, case.params, "fp32", d_sc, d_fl, 64.0, 64.0, 0.2)
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    lib = lbm.load()
+    p = lbm.make_params(case.params, "fp32")
+    out = torch.empty(10, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        rc = lib.lbm_reduce_noalloc(ct.byref(p), ct.c_void_p(d_sc.data_ptr()), ct.c_void_p(d_fl.data_ptr()), 64.0,
+                                    64.0, 0.2, ct.c_void_p(out.data_ptr()), ct.c_void_p(stream.cuda_stream))
+        assert rc == 0, lib.lbm_last_error(None)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    np.testing.assert_array_equal(out.cpu().numpy(), first)
+
+
+_CAPTURE_FIRST = r"""
+import ctypes as ct, sys
+sys.path.insert(0, {root!r})
+import torch
+from paper_2209_01444_gb300 import lbm, workloads as W
+lib = lbm.load()
+p = lbm.make_params(W.thermosolutal_params(64, 64))
+buf = torch.zeros(64 * 64 * 16, dtype=torch.float32, device="cuda")
+out = torch.zeros(10, dtype=torch.float64, device="cuda")
+torch.cuda.synchronize()
+s = torch.cuda.Stream()
+g = torch.cuda.CUDAGraph()
+with torch.cuda.stream(s):
+    g.capture_begin()
+    rc = lib.lbm_reduce_noalloc(ct.byref(p), ct.c_void_p(buf.data_ptr()), ct.c_void_p(buf.data_ptr()), 0.0, 0.0,
+                                0.0, ct.c_void_p(out.data_ptr()), ct.c_void_p(s.cuda_stream))
+    msg = lib.lbm_last_error(None).decode()
+    g.capture_end()
+print(rc, msg)
+"""
+
+
+def test_noalloc_first_call_under_stream_capture_is_refused():
+    """In a fresh process, a first call made while its stream is being
+    captured has no device address of the static array yet (looking it up
+    is not a stream operation): it is refused with LBM_EINVAL and a reason,
+    and launches nothing."""
+    pytest.importorskip("torch")
+    import os
+    import subprocess
+    import sys
+
+    from paper_2209_01444_gb300 import build_ext
+
+    build_ext.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _CAPTURE_FIRST.format(root=root)], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    rc, _, msg = r.stdout.strip().splitlines()[-1].partition(" ")
+    assert int(rc) == -1 and "before capture" in msg, r.stdout
+
+
 def test_noalloc_reduction_rejects_grids_beyond_its_limit():
     torch = pytest.importorskip("torch")
     from paper_2209_01444_gb300 import build_ext, lbm
