@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-domain leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
     ap.add_argument("--no-substeps", action="store_true", help="skip the n_sub = 15 flow-sub-step leg")
+    ap.add_argument("--substep-n", type=int, default=1024,
+                    help="grid side of the n_sub = 15 leg (default: the paper's 1024^2 flow configuration)")
     ap.add_argument("--surrogate-train-steps", type=int, default=1500)
     ap.add_argument("--surrogate-windows", type=int, default=400)
     ap.add_argument("--reference-seconds", type=float, default=90.0,
@@ -403,7 +405,8 @@ def substep_leg(lbm, torch, stream, max_over_ranks, barrier, n: int = 1024, step
             "roofline": {"bound": "hbm", "kernel": "k_flow_substep", "achieved": s_ach, "peak": peak,
                          "unit": "GB/s", "frac": s_ach / peak, "bytes_per_node": s_bpn, "kernel_ms": s_ms,
                          "launches": slaunches, "peak_kind": kind,
-                         "note": "the 84 MB flow state of this grid stays in L2 between sub-steps"},
+                         "note": ("the flow state of this grid stays in L2 between sub-steps"
+                                  if n * n * 80 < 129e6 else "flow state larger than L2")},
             "nonfinite": bad}
 
 
@@ -436,20 +439,31 @@ def batch_leg(lbm, torch, stream, steps, world, max_over_ranks, barrier):
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1))
     value = world * nodes * k / (ms / 1e3) / 1e6
+    # the batched kernel alone: CUDA events around each launch (direct launches)
+    b.set_profiling(True)
+    b.step(8)
+    bkms, blaunch = b.kernel_time()
+    b.set_profiling(False)
+    b_ms = bkms / max(blaunch, 1)
+    # per node: 16-bit populations and FP32 history read and written; each
+    # domain holds one grain, so no grain map is read
+    b_bpn = algorithmic_bytes_per_node("fp16", False)
+    peak, kind = peaks()
+    b_ach = b_bpn * nodes / (b_ms / 1e3) / 1e9
     bad = sum(b.metrics(j, *c.seeds[0][:2], c.seeds[0][3])["nonfinite"] for j, c in enumerate(cases[:8]))
     # accuracy of the batched FP16 run: its first domains against the plain
-    # FP32 path after the same 16 + k steps (the tuner restores the state it times on)
+    # FP32 path after the same 16 + k + 8 steps (the tuner restores the state it times on)
     errs = []
     for j, c in enumerate(cases[:4]):
         ref = lbm.Simulation(c.params, "fp32", stream=stream)
         ref.init_seeds(c.seeds, c.U0, c.theta0)
-        ref.step(16 + k)
+        ref.step(16 + k + 8)
         errs.append(field_errors(b.fields(j, ACCURACY_FIELDS), ref.fields(ACCURACY_FIELDS), abs(c.theta0)))
         del ref
     worst = {f: max(e[f] for e in errs) for f in errs[0]}
     # the smallest domain's fields, for the CPU baseline leg's FP64 oracle run
     j_small = min(range(len(cases)), key=lambda i: cases[i].nodes)
-    small = {"domain": j_small, "case": cases[j_small], "steps": 16 + k,
+    small = {"domain": j_small, "case": cases[j_small], "steps": 16 + k + 8,
              "fields": b.fields(j_small, ACCURACY_FIELDS)}
     del b
     # plain FP32 path, one domain after another
@@ -474,6 +488,9 @@ def batch_leg(lbm, torch, stream, steps, world, max_over_ranks, barrier):
             "nodes": nodes, "storage": "fp16", "tile_height": ty, "tiles_per_cta": tiles_per_cta, "steps": k,
             "value": value, "unit": UNIT,
             "ms_per_step": ms / k, "sequential_fp32_value": seq_value, "speedup_vs_sequential_fp32": value / seq_value,
+            "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": b_ach, "peak": peak, "unit": "GB/s",
+                         "frac": b_ach / peak, "bytes_per_node": b_bpn, "kernel_ms": b_ms, "launches": blaunch,
+                         "peak_kind": kind},
             "nonfinite_domains_of_first_8": bad, "field_error_vs_fp32_first_4_domains": worst,
             "velocity_error_scale": "largest speed |u| of the reference",
             "_smallest_domain": small}
@@ -737,7 +754,7 @@ def main():
 
     substeps = None
     if not args.no_substeps:
-        substeps = substep_leg(lbm, torch, stream, max_ranks, barrier_)
+        substeps = substep_leg(lbm, torch, stream, max_ranks, barrier_, n=args.substep_n)
 
     batch = None
     if not args.no_batch:

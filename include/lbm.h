@@ -310,6 +310,14 @@ LBM_API int lbm_batch_set_tiling(lbm_batch* b, int tile_height, int tiles_per_ct
  * which is restored afterwards (needs that much free memory); the step counter
  * does not move. */
 LBM_API int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height);
+/* Kernel timing of the batched step, as lbm_set_profiling does for a handle:
+ * while enabled, lbm_batch_step launches every step directly (no graph) and
+ * brackets the batched fused kernel with CUDA events on the batch's stream;
+ * lbm_batch_kernel_time returns the total device time (ms) of the kernels
+ * timed since profiling was enabled, and their number (synchronises the
+ * pending events).  Enabling or disabling resets the accumulated time. */
+LBM_API int lbm_batch_set_profiling(lbm_batch* b, int enable);
+LBM_API int lbm_batch_kernel_time(lbm_batch* b, double* total_ms, long long* launches);
 LBM_API const char* lbm_batch_last_error(const lbm_batch* b);
 
 /* ------------------------------------------------------- surrogate network */

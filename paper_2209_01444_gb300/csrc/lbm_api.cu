@@ -1153,6 +1153,12 @@ struct lbm_batch {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (parity, ty * 1000 + run)
     long long steps = 0, nodes = 0;
     std::string err;
+    // kernel timing (lbm_batch_set_profiling): begin/end pairs of pending launches
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double prof_ms = 0.0;
+    long long prof_launches = 0;
 };
 
 namespace {
@@ -1263,10 +1269,37 @@ int batch_ready(lbm_batch* b)
     return LBM_OK;
 }
 
+int batch_collect_profile(lbm_batch* b)
+{
+    if (!b->ev_used) return LBM_OK;
+    LBM_BCUDA(b, cudaEventSynchronize(b->ev[b->ev_used - 1]));
+    for (size_t i = 0; i + 1 < b->ev_used; i += 2) {
+        float ms = 0.0f;
+        LBM_BCUDA(b, cudaEventElapsedTime(&ms, b->ev[i], b->ev[i + 1]));
+        b->prof_ms += ms;
+        b->prof_launches += 1;
+    }
+    b->ev_used = 0;
+    return LBM_OK;
+}
+
 int batch_run_direct(lbm_batch* b, int n)
 {
-    const lbm::BatchTables T = tables(b);
+    lbm::BatchTables T = tables(b);
     for (int i = 0; i < n; ++i) {
+        if (b->profiling) {
+            if (b->ev_used + 2 > b->ev.size()) {
+                int rc = batch_collect_profile(b);
+                if (rc) return rc;
+                while (b->ev.size() < 512) {
+                    cudaEvent_t e;
+                    LBM_BCUDA(b, cudaEventCreate(&e));
+                    b->ev.push_back(e);
+                }
+            }
+            T.ev_begin = b->ev[b->ev_used++];
+            T.ev_end = b->ev[b->ev_used++];
+        }
         LBM_BCUDA(b, lbm::launch_batch_step(T, b->storage, b->ty, b->run, b->parity, b->ctas[tyk(b->ty)], b->stream));
         b->parity = 1 - b->parity;
     }
@@ -1358,6 +1391,7 @@ void lbm_batch_destroy(lbm_batch* b)
 {
     if (!b) return;
     drop_batch_graphs(b);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     for (lbm_handle* h : b->dom) lbm_destroy(h);
     for (int k = 0; k < 3; ++k)
         if (b->d_tiles[k]) cudaFree(b->d_tiles[k]);
@@ -1397,7 +1431,7 @@ int lbm_batch_step(lbm_batch* b, int nsteps)
     if (rc) return rc;
     if (nsteps < 0) return bfail(b, LBM_EINVAL, "nsteps < 0");
     int left = nsteps;
-    while (left >= kGraphSteps) {
+    while (!b->profiling && left >= kGraphSteps) {
         cudaGraphExec_t ex;
         if ((rc = batch_graph(b, &ex))) return rc;
         LBM_BCUDA(b, cudaGraphLaunch(ex, b->stream));
@@ -1406,6 +1440,27 @@ int lbm_batch_step(lbm_batch* b, int nsteps)
     if ((rc = batch_run_direct(b, left))) return rc;
     b->steps += nsteps;
     sync_domain_parity(b);
+    return LBM_OK;
+}
+
+int lbm_batch_set_profiling(lbm_batch* b, int enable)
+{
+    if (!b) return LBM_EINVAL;
+    int rc = batch_collect_profile(b);
+    if (rc) return rc;
+    b->profiling = enable != 0;
+    b->prof_ms = 0.0;
+    b->prof_launches = 0;
+    return LBM_OK;
+}
+
+int lbm_batch_kernel_time(lbm_batch* b, double* total_ms, long long* launches)
+{
+    if (!b || !total_ms || !launches) return LBM_EINVAL;
+    int rc = batch_collect_profile(b);
+    if (rc) return rc;
+    *total_ms = b->prof_ms;
+    *launches = b->prof_launches;
     return LBM_OK;
 }
 

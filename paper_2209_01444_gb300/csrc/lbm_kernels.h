@@ -63,6 +63,7 @@ struct BatchTables {
     int ntiles[3];
     const int4* walls[2];
     int nwall[2];
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // recorded around the batched kernel when set
 };
 
 // One coupled step of every domain: buffers `parity` -> 1 - parity, then walls.

@@ -719,9 +719,11 @@ cudaError_t batch_step_t(const BatchTables& T, int parity, int ctas, int run, cu
     const int k = TYV == 4 ? 0 : TYV == 8 ? 1 : 2;
     const int chunk = run > 0 ? run : (T.ntiles[k] + ctas - 1) / ctas;
     const int grid = (T.ntiles[k] + chunk - 1) / chunk;
+    if (T.ev_begin) cudaEventRecord(T.ev_begin, s);
     k_batch_step<Store, TYV><<<grid, dim3(TX, TYV), 0, s>>>(T.tiles[k], T.ntiles[k], chunk, parity, repair);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (T.ev_end) cudaEventRecord(T.ev_end, s);
     // the fused kernel wrote buffers 1 - parity; walls act on those (rows, then columns)
     if (T.nwall[0])
         k_batch_walls<Store><<<(T.nwall[0] + 127) / 128, 128, 0, s>>>(T.descs, T.walls[0], T.nwall[0], 1 - parity);

@@ -95,6 +95,8 @@ SIGNATURES = {
     "lbm_batch_tiles_per_cta": (ct.c_int, [_H]),
     "lbm_batch_set_tiling": (ct.c_int, [_H, ct.c_int, ct.c_int]),
     "lbm_batch_tune": (ct.c_int, [_H, ct.c_char_p, ct.POINTER(ct.c_int)]),
+    "lbm_batch_set_profiling": (ct.c_int, [_H, ct.c_int]),
+    "lbm_batch_kernel_time": (ct.c_int, [_H, ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong)]),
     "lbm_batch_last_error": (ct.c_char_p, [_H]),
     "lbm_nn_gemm": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
                                ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]),
@@ -446,6 +448,16 @@ class Batch:
         a = np.asarray(seeds, np.float64).reshape(-1, 4)
         arr = (lbm_seed * len(a))(*[lbm_seed(*row) for row in a])
         self._check(self.lib.lbm_batch_init_seeds(self.h, dom, arr, len(a), U0, theta0))
+
+    def set_profiling(self, enable: bool) -> None:
+        """Time the batched kernel of every step with CUDA events (direct launches)."""
+        self._check(self.lib.lbm_batch_set_profiling(self.h, int(enable)))
+
+    def kernel_time(self) -> tuple[float, int]:
+        """(total ms, launches) of the batched kernel since profiling was enabled."""
+        ms, n = ct.c_double(), ct.c_longlong()
+        self._check(self.lib.lbm_batch_kernel_time(self.h, ct.byref(ms), ct.byref(n)))
+        return ms.value, n.value
 
     def tune(self, cache_path: str | None = None) -> int:
         ty = ct.c_int()

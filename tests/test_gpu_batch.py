@@ -229,3 +229,28 @@ def test_fp16_batch_of_the_sweep_matches_the_oracle(lbm):
         assert max(vs_plain.values()) <= 1e-2, (T, vs_rounded, vs_plain)
         assert b.metrics(j, *c.seeds[0][:2], c.seeds[0][3])["tip_px"] == pytest.approx(
             o.metrics(*c.seeds[0][:2], c.seeds[0][3])["tip_px"], abs=1.0)
+
+
+def test_batch_kernel_timing_runs_direct_steps_and_keeps_the_state(lbm):
+    """lbm_batch_set_profiling: timed steps launch the batched kernel directly
+    (one timed launch per step) and give the state graph replay gives, to
+    16-bit rounding (inside the step graphs the left/right walls are updated
+    as the next step loads them, in direct launches by the column pass: the
+    same arithmetic in another kernel, rounded once more or once less)."""
+    cases = small_cases()[:3]
+    out = []
+    for prof in (False, True):
+        b = lbm.Batch([c.params for c in cases], "fp16")
+        for j, c in enumerate(cases):
+            b.init_seeds(j, c.seeds, c.U0, c.theta0)
+        b.set_profiling(prof)
+        b.step(20)
+        if prof:
+            ms, n = b.kernel_time()
+            assert n == 20 and ms > 0
+            b.set_profiling(False)
+            assert b.kernel_time() == (0.0, 0)
+        out.append([b.fields(j, ACC) for j in range(len(cases))])
+    for a, c, case in zip(*out, cases):
+        e = errors(a, c, case.theta0)
+        assert max(e.values()) <= 4e-3, e
