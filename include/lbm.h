@@ -528,6 +528,16 @@ LBM_API int lbm_surrogate_advance(lbm_handle* h, lbm_unet* net, int K, double ti
  * last cleared (clear != 0 clears it), else LBM_OK.  Synchronous. */
 LBM_API int lbm_nn_error(int clear);
 
+/* Bound, in nanoseconds, on how long the GEMMs' tensor-core issuer waits for
+ * the TMA copies of each k block's operand tiles (default 1e9, one second;
+ * for the current device, from the next launch on).  Every other wait of the
+ * GEMMs keeps its one-second bound.  When a wait runs out the GEMM raises the
+ * flag that lbm_nn_error reports (LBM_ETIMEOUT), leaves its output unwritten,
+ * waits (bounded) for every copy and MMA it already issued, frees its tensor
+ * memory and returns.  0 makes the first such wait give up at once, which
+ * exercises that path without a fault.  Synchronous. */
+LBM_API int lbm_nn_set_operand_wait(unsigned long long ns);
+
 /* ------------------------------------------------ allocation-free reduction */
 /* The reductions of lbm_get_metrics, computed straight from population
  * buffers the caller owns, without allocating anything.  The paper has no

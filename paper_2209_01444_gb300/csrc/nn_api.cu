@@ -151,6 +151,8 @@ int lbm_nn_cast_bf16(const float* a, long long rows, int C, int apitch, void* b,
     return nn_status(nn::cast_bf16(a, rows, C, apitch, b, bpitch, NN_S(stream)));
 }
 
+int lbm_nn_set_operand_wait(unsigned long long ns) { return nn_status(nn::set_operand_wait(ns)); }
+
 int lbm_nn_error(int clear)
 {
     int flag = 0;

@@ -34,6 +34,9 @@ constexpr int kThreads = 128;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
 
 __device__ int g_gemm_error;  // set when a bounded wait expired
+// Bound of the MMA issuer's waits for its operand tiles (set_operand_wait);
+// every other wait keeps kWaitNs.  0: such a wait gives up at once.
+__device__ unsigned long long g_operand_wait_ns = kWaitNs;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -71,6 +74,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
             : "memory");
         if (done) return true;
         if ((it & 63) == 63 && global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// The MMA issuer's wait for the operand tiles of one k block: bounded by
+// g_operand_wait_ns (0: gives up without waiting).
+__device__ __forceinline__ bool mbar_wait_operands(uint64_t* bar, uint32_t parity)
+{
+    const unsigned long long lim = g_operand_wait_ns;
+    if (lim == 0) return false;
+    const uint32_t addr = smem_u32(bar);
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > lim) return false;
     }
 }
 
@@ -286,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ++issued;
             }
             const int s = kb % S;
-            ok = mbar_wait(&full[s], (uint32_t)((kb / S) & 1));
+            ok = mbar_wait_operands(&full[s], (uint32_t)((kb / S) & 1));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(smem + s * STAGE), b0s = a0 + A_BYTES;
@@ -412,6 +437,36 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, 
     }
 }
 
+// The warp-specialised MMA issuer's wait for its operand tiles, bounded by
+// g_operand_wait_ns; on expiry it raises the error and abort flags as
+// mbar_wait_abort does.
+__device__ __forceinline__ bool mbar_wait_operands_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
+{
+    const unsigned long long lim = g_operand_wait_ns;
+    const uint32_t addr = smem_u32(bar);
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done = 0;
+        if (lim != 0)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(addr), "r"(parity)
+                : "memory");
+        if (done) return true;
+        if (lim == 0 || (it & 63) == 63) {
+            if (*abort_flag) return false;
+            if (lim == 0 || global_ns() - t0 > lim) {
+                *abort_flag = 1;
+                atomicExch(&g_gemm_error, 1);
+                return false;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -524,7 +579,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 const uint32_t d = tmem + (uint32_t)(acc * ACC_COLS);
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int st = it % S;
-                    if (!(ok = mbar_wait_abort(&full[st], (uint32_t)((it / S) & 1), abort_flag))) break;
+                    if (!(ok = mbar_wait_operands_abort(&full[st], (uint32_t)((it / S) & 1), abort_flag))) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = smem_u32(smem + st * STAGE), b0s = a0 + MT * A_BYTES;
 #pragma unroll
@@ -949,6 +1004,11 @@ cudaError_t upconv2x2_bf16(const void* X, int lda, const void* Wm, int ldw, void
     sh.c = c;
     sh.c0 = c0;
     return dispatch<kBK, false>(bn, true, ta, tb, Y, bias, M, N, K, ypitch, 0, 1, 1 << 30, ConvGeo{}, sh, s);
+}
+
+cudaError_t set_operand_wait(unsigned long long ns)
+{
+    return cudaMemcpyToSymbol(g_operand_wait_ns, &ns, sizeof(ns));
 }
 
 cudaError_t gemm_error(int* flag, bool clear)

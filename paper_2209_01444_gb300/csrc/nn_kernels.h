@@ -38,5 +38,7 @@ cudaError_t upconv2x2_bf16(const void* X, int lda, const void* Wm, int ldw, void
 
 // Read (and optionally clear) the flag a GEMM raises when a bounded wait ran out.
 cudaError_t gemm_error(int* flag, bool clear);
+// Bound of the GEMMs' waits for their operand tiles on the current device.
+cudaError_t set_operand_wait(unsigned long long ns);
 
 }  // namespace nn

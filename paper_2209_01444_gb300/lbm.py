@@ -101,6 +101,7 @@ SIGNATURES = {
     "lbm_nn_gemm": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
                                ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]),
     "lbm_nn_error": (ct.c_int, [ct.c_int]),
+    "lbm_nn_set_operand_wait": (ct.c_int, [ct.c_ulonglong]),
     "lbm_nn_gemm_split": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int,
                                      ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int,
                                      ct.c_void_p, ct.c_void_p]),

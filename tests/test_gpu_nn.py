@@ -69,6 +69,43 @@ def _stream(torch):
     return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+@pytest.mark.parametrize("splits", [1, 3])
+def test_gemm_operand_wait_that_runs_out_is_reported_and_recovered(env, splits):
+    """A bounded device wait that runs out, made to happen without a fault:
+    with the operand-wait bound at 0 the tensor-core issuer gives up its
+    first wait for operand tiles (the persistent warp-specialised GEMM,
+    splits = 1, and the split-K GEMM).  The GEMM must raise the flag
+    lbm_nn_error reports as LBM_ETIMEOUT, leave its output unwritten, drain
+    the copies it issued and free its tensor memory; with the default bound
+    back, the next GEMM on the same context runs and matches the FP32 matmul."""
+    torch, lib = env
+    M, N, K = 512, 128, 1024
+    g = torch.Generator(device="cuda").manual_seed(5)
+    A = torch.randn(M, K, generator=g, device="cuda").to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g, device="cuda").to(torch.bfloat16)
+    ws = torch.empty(splits * M * N, dtype=torch.float32, device="cuda")
+    D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    args = (_p(A), K, _p(B), K, _p(D), N, None, M, N, K, 1, 0, splits, _p(ws), _stream(torch))
+    torch.cuda.synchronize()
+    assert lib.lbm_nn_error(1) == 0
+    try:
+        assert lib.lbm_nn_set_operand_wait(0) == 0
+        assert lib.lbm_nn_gemm_split(*args) == 0
+        torch.cuda.synchronize()
+        assert lib.lbm_nn_error(0) == -5  # LBM_ETIMEOUT
+        if splits == 1:
+            assert bool(torch.isnan(D).all())  # the epilogue never ran
+    finally:
+        assert lib.lbm_nn_set_operand_wait(1000000000) == 0
+    assert lib.lbm_nn_error(1) == -5  # reported once more, then cleared
+    assert lib.lbm_nn_error(0) == 0
+    assert lib.lbm_nn_gemm_split(*args) == 0
+    torch.cuda.synchronize()
+    assert lib.lbm_nn_error(1) == 0
+    ref = A.float() @ B.float().T
+    assert float((D - ref).abs().max()) <= 2e-5 * float(ref.abs().max())
+
+
 @pytest.mark.parametrize("M,N,K,splits", [(32, 72, 4096, 16), (64, 288, 2048, 7), (512, 200, 1000, 3),
                                           (128, 264, 640, 1), (96, 8, 512, 2), (1024, 576, 16384, 64)])
 def test_gemm_ragged_n_and_split_k(env, M, N, K, splits):
