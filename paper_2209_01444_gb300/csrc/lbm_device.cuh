@@ -227,9 +227,11 @@ __device__ __forceinline__ float h_plus_1(int kind, float p)
 
 // Eq. (20) with C = 1 + dC and phi = p - 1:
 // U = [2C/(1 + k - (1 - k) phi) - 1]/(1 - k) = (2 dC + (1 - k) p) / ((2 - (1 - k) p)(1 - k)).
+// (The denominator is at least 2k(1 - k) for p in [0, 2]: the fast division,
+// within 2 ulp, is safe and saves the exact division's instruction sequence.)
 __device__ __forceinline__ float U_of(float dC, float p, float k)
 {
-    return (2.0f * dC + (1.0f - k) * p) / ((2.0f - (1.0f - k) * p) * (1.0f - k));
+    return __fdividef(2.0f * dC + (1.0f - k) * p, (2.0f - (1.0f - k) * p) * (1.0f - k));
 }
 // Its inverse: C - 1 = (2 - (1 - k) p)(1 + (1 - k) U)/2 - 1.
 __device__ __forceinline__ float dC_of(float U, float p, float k)
@@ -299,7 +301,7 @@ __device__ __forceinline__ void anisotropy(float gx, float gy, float eps, float 
         Ny = 0.0f;
         return;
     }
-    float inv = 1.0f / (m2 * m2);
+    float inv = __fdividef(1.0f, m2 * m2);  // m2^2 in [1e-24, 1e20]: fast division within 2 ulp
     float a = 1.0f - 3.0f * eps + 4.0f * eps * (px2 * px2 + py2 * py2) * inv;
     float t = 16.0f * eps * a * px * py * (px2 - py2) * inv;  // N'_x = t py, N'_y = -t px
     float nx_ = t * py, ny_ = -t * px;

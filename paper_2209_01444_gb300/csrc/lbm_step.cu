@@ -161,14 +161,14 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
         // with s1 and N taken at grad(phi): two fixed-point passes from a_s = 1, N = 0
         const float jx = f[1] - f[3], jy = f[2] - f[4];
         const float k0 = P.kappa3 * (1.0f / 3.0f);
-        float s1 = 1.0f / (P.kappa3 + 0.5f);
+        float s1 = __fdividef(1.0f, P.kappa3 + 0.5f);
         gx = -3.0f * s1 * jx;
         gy = -3.0f * s1 * jy;
 #pragma unroll
         for (int it = 0; it < kLocalGradIters; ++it) {
             float a1, nx_, ny_;
             anisotropy(gx, gy, P.eps, co, so, a1, nx_, ny_);
-            s1 = 1.0f / (P.kappa3 * a1 * a1 + 0.5f);
+            s1 = __fdividef(1.0f, P.kappa3 * a1 * a1 + 0.5f);
             gx = -3.0f * s1 * (jx + k0 * nx_);
             gy = -3.0f * s1 * (jy + k0 * ny_);
         }
@@ -176,15 +176,18 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
     float as, Nx, Ny;
     anisotropy(gx, gy, P.eps, co, so, as, Nx, Ny);
     const float as2 = as * as;
+    // 1/a_s^2 (a_s^2 within (1 - 3 eps)^2 .. (1 + eps)^2) and the phase-field
+    // rate, by fast division (within 2 ulp; both denominators are O(1))
+    const float ia = __fdividef(1.0f, as2);
     const float g2 = gx * gx + gy * gy;
     const float Q = coupling_Q(m.phi, P.theta_ref + m.dth, m.U, P);
 
     // ---- phase field: Eqs. (13)-(14), relaxation rate of Sec. 3.1
     float fo[5];
     {
-        const float s1 = 1.0f / (P.kappa3 * as2 + 0.5f);
+        const float s1 = __fdividef(1.0f, P.kappa3 * as2 + 0.5f);
         const float S0 = (Q + 0.5f * as2 * (Q - Q_prev)) * P.inv_tau;
-        const float ga = -(1.0f / 3.0f) / as2;
+        const float ga = -(1.0f / 3.0f) * ia;
         collide_d2q5(f, m.p1, 0.0f, 0.0f, m.p1, s1, ga * Nx, ga * Ny, S0, fo);
     }
     // ---- solute: Eqs. (17)-(19) with J_at of Eq. (7)
@@ -226,7 +229,7 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
         const long long d5[5] = {0, rY + cP, rP + c0, rY + cM, rM + c0};
         // modified streaming of the phase field: the destination's time-n
         // population sits in the shared tile (its halo is periodic-wrapped)
-        const float ia = 1.0f / as2, ib = ia - 1.0f;
+        const float ib = ia - 1.0f;
         const float fd[5] = {fs[0][ly][fx], fs[1][ly][fx + 1], fs[2][ly + 1][fx], fs[3][ly][fx - 1],
                              fs[4][ly - 1][fx]};
         Store::store(dst, dstf, kF, o, fo[0] * ia - ib * fd[0], P);
@@ -316,9 +319,20 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
         }
         if (xwall_tile) __syncthreads();  // keeps the loads below after the repair
     }
-    // own-node loads first, so that they are in flight while the tile loads
+    // own-node loads first, so that they are in flight while the halo loads.
+    // Every thread loads its own tile cell (x, y), wrapped into the grid when
+    // the tile reaches past it (such cells serve as periodic neighbours of
+    // the edge nodes); the first 2 (TX + 2) + 2 TYV threads load the halo ring.
     const long long o = active ? (long long)y * P.pitch + x : 0;
-    float n[5], g[5], h[9];
+    int cx = x, cy = y;
+    if (!active) {
+        cx = cx >= P.nx ? wrap(cx, P.nx) : cx;
+        cy = cy >= P.ny ? wrap(cy, P.ny) : cy;
+    }
+    const long long oc = active ? o : (long long)cy * P.pitch + cx;
+    float f[5], n[5], g[5], h[9];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) f[i] = Store::load(src, srcf, kF + i, oc, P);
 #pragma unroll
     for (int i = 0; i < 5; ++i) n[i] = Store::load(src, srcf, kN + i, o, P);
 #pragma unroll
@@ -333,9 +347,18 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
     uint8_t gid = 0;
     if (GRAIN && grain) gid = grain[o];
 
-    // phi populations of the tile and its halo (periodic wrap), and phi there.
-    for (int e = ty * TX + tx; e < (TX + 2) * (TYV + 2); e += TX * TYV) {
-        const int hx = e % (TX + 2), hy = e / (TX + 2);
+    static_assert(2 * (TX + 2) + 2 * TYV <= TX * TYV, "halo ring thread range");
+    const int tid = ty * TX + tx;
+    if (tid < 2 * (TX + 2) + 2 * TYV) {
+        int hx, hy;
+        if (tid < 2 * (TX + 2)) {  // the rows below and above the tile, corners included
+            hy = tid < TX + 2 ? 0 : TYV + 1;
+            hx = tid < TX + 2 ? tid : tid - (TX + 2);
+        } else {  // the columns left and right of it
+            const int r = tid - 2 * (TX + 2);
+            hx = r < TYV ? 0 : TX + 1;
+            hy = 1 + (r < TYV ? r : r - TYV);
+        }
         int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
         gx = (gx < 0) ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
         gy = (gy < 0) ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
@@ -345,11 +368,20 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
         float sum = 0.0f;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            float v = Store::load(src, srcf, kF + i, oh, P);
+            const float v = Store::load(src, srcf, kF + i, oh, P);
             fs[i][hy][hx] = v;
             sum += v;
         }
         ps[hy][hx] = sum;
+    }
+    {
+        float sum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            fs[i][ty + 1][tx + 1] = f[i];
+            sum += f[i];
+        }
+        ps[ty + 1][tx + 1] = sum;
     }
     __syncthreads();
 
@@ -381,6 +413,8 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
             if (active && (x == 0 || x == P.nx - 1)) {
                 const int side = x == 0 ? 0 : 1;
 #pragma unroll
+                for (int i = 0; i < 5; ++i) f[i] = fs[i][ty + 1][tx + 1];  // as the repair left the tile
+#pragma unroll
                 for (int i = 0; i < 5; ++i) n[i] = wnb[side][ty][i];
 #pragma unroll
                 for (int i = 0; i < 5; ++i) g[i] = wnb[side][ty][5 + i];
@@ -391,9 +425,6 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
     }
 
     if (!active) return;
-    float f[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) f[i] = fs[i][ty + 1][tx + 1];
     coupled_node<Store, GRAIN, WRITE_FB, TYV, TX + 2, 1>(P, dst, dstf, hist, fb, x, y, tx + 1, ty + 1, f, n, g, h,
                                                           phi_prev, Q_prev, Cux_prev, Cuy_prev, Hux_prev, Huy_prev,
                                                           grain != nullptr, gid, fs, ps);
