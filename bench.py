@@ -497,16 +497,17 @@ def batch_leg(lbm, torch, stream, steps, world, max_over_ranks, barrier):
 
 
 def surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, train_steps: int = 1500, windows: int = 400,
-                  domains: int = 12, side: int = 512, data_windows: int = 400, lr: float = 1e-3,
+                  per_generator: int = 8, side: int = 512, data_windows: int = 400, lr: float = 1e-3,
                   pushforward: float = 0.3, audits=(4, 8), lb_first: int = 40, short_warm: int = 2000,
                   short_windows: int = 40, batch: int = 4, drift_factor: float = 2.5):
     """The learned surrogate against the plain LB on the forced-flow case
     (1024^2, one seed, inflow u_x = 0.01).
 
-    Training: (t, t + 50) pairs of LB trajectories of `domains` domains of
-    side^2 in the same geometry (half with the forced-flow parameters, half
-    drawn; other seeds), 400 windows from the seed, with the push-forward
-    samples of surrogate.train_rollout.
+    Training: (t, t + 50) pairs of LB trajectories on side^2 domains from the
+    three workload generators (workloads.surrogate_training_set: the forced-
+    flow dendrite, the parameter sweep's draws, crops of the multi-seed
+    thermosolutal box; per_generator each), 400 windows from the seed, with
+    the push-forward samples of surrogate.train_rollout.
 
     Long run (the headline): `windows` windows of K = 50 steps from the seed;
     the first lb_first windows by the LB, then the audited rollout with the
@@ -523,7 +524,7 @@ def surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, train_steps: int 
     K, tol = 50, 1.0
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
-    cases = W.surrogate_domains(count=domains, n=side, rng_seed=5)
+    cases = W.surrogate_training_set(n=side, per_generator=per_generator, rng_seed=5)
     snaps = S.make_snapshots(cases, K=K, windows=data_windows)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
@@ -610,9 +611,10 @@ def surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, train_steps: int 
         "short": {"workload": f"{short_windows} windows after {short_warm} LB steps", "lb_ms": s_lb_ms,
                   "rollouts": s_runs},
         "network_forward_ms_1024": fwd10 / 10, "lb_ms_per_window": lb_ms / windows,
-        "training": {"data": f"{domains} domains {side}^2 (forced-flow geometry; half the forced-flow parameters, "
-                             f"half drawn; seed 5), {data_windows} windows from the seed",
-                     "pairs": int(data_windows * domains), "data_s": t_data, "steps": train_steps, "batch": batch,
+        "training": {"data": f"{len(cases)} trajectories {side}^2 ({per_generator} each of the forced-flow dendrite, "
+                             f"the parameter sweep's draws and multi-seed thermosolutal crops; seed 5), "
+                             f"{data_windows} windows from the seed",
+                     "pairs": int(data_windows * len(cases)), "data_s": t_data, "steps": train_steps, "batch": batch,
                      "pushforward": pushforward, "lr": lr, "ms": train_ms,
                      "loss_first_last": [hist[0][1], hist[-1][1]]},
     }

@@ -441,7 +441,8 @@ LBM_API int lbm_nn_cast_bf16(const float* a, long long rows, int C, int apitch, 
  * [width][fields].  The network reads the inputs as (x - mean)/std_in and its
  * output is the increment in units of std_out: the prediction is
  * y = x + std_out * out (lbm_unet_set_norm; default mean 0, both scales 1);
- * the loss is the mean squared error of out against (target - x)/std_out.  All calls queue work on the object's stream and
+ * the loss is the mean squared error of out against (target - x)/std_out
+ * (weighted at the interface with lbm_unet_set_loss_weight).  All calls queue work on the object's stream and
  * return without waiting, except set_params, get_params, get_grads, set_norm
  * and loss, which synchronise.  Errors: LBM_EINVAL for bad arguments,
  * LBM_ENOMEM / LBM_ECUDA from CUDA; lbm_unet_last_error gives the reason. */
@@ -457,6 +458,13 @@ LBM_API int lbm_unet_get_params(lbm_unet* u, float* host);
 /* Gradients of the loss from the last lbm_unet_backward / train_step. */
 LBM_API int lbm_unet_get_grads(lbm_unet* u, float* host);
 LBM_API int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_in, const float* std_out);
+/* Interface weight of the training loss (not in the paper, which has no
+ * network): each pixel's squared errors are weighted by 1 + alpha max(0, 1 - phi^2),
+ * phi the phase field of the input x (field 0, physical units), so that the
+ * pixels where the interface moves, a few per cent of a field, weigh in the
+ * loss as the far field does; the loss is sum w d^2 / n.  alpha >= 0; 0 (the
+ * default) is the plain mean squared error. */
+LBM_API int lbm_unet_set_loss_weight(lbm_unet* u, float alpha);
 /* Writes the FP32 parameters and the normalisation to a file (magic
  * "LBMUNET1", int32 levels, base, fields, 0, int64 parameter count, FP32 mean,
  * std_in, std_out and parameters, little-endian); synchronous.  The Adam

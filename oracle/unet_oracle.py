@@ -179,6 +179,10 @@ def backward(params: dict, cache: dict, dy, levels: int, q=None):
     return g
 
 
-def mse(y, t):
+def mse(y, t, x=None, alpha=0.0):
+    """Mean squared error and its gradient; with the input x (fields last,
+    phase field first), each pixel's squared errors weighted by
+    w = 1 + alpha max(0, 1 - phi^2): mean(w d^2), gradient 2 w d / n."""
     d = y - t
-    return float((d * d).mean()), 2.0 * d / d.size
+    w = 1.0 if x is None else (1.0 + alpha * np.maximum(0.0, 1.0 - x[..., :1] ** 2))
+    return float((w * d * d).mean()), 2.0 * w * d / d.size

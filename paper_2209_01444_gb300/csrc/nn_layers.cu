@@ -526,19 +526,26 @@ __global__ void k_sum_parts(const float* __restrict__ part, int nb, int slots, f
     if (lane == 0) out[s] = acc;
 }
 
-// Squared error: d[i] = pred - target; per-block partial sums of d^2 and
-// the gradient 2 d / n.
+// Weighted squared error: d[i] = pred - target, weight w = 1 + alpha max(0,
+// 1 - phi^2) with phi = x[pixel * F] the phase field of the input at the
+// element's pixel (w = 1 without x); per-block partial sums of w d^2 and the
+// gradient 2 w d / n.
 __global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target, long long n,
-                      float* __restrict__ grad, float* __restrict__ part)
+                      const float* __restrict__ x, int F, float alpha, float* __restrict__ grad,
+                      float* __restrict__ part)
 {
     __shared__ float sm[256];
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    float d = 0.0f;
+    float d = 0.0f, w = 1.0f;
     if (i < n) {
         d = pred[i] - target[i];
-        grad[i] = 2.0f * d / (float)n;
+        if (x) {
+            const float phi = x[(i / F) * F];
+            w = 1.0f + alpha * fmaxf(0.0f, 1.0f - phi * phi);
+        }
+        grad[i] = 2.0f * w * d / (float)n;
     }
-    sm[threadIdx.x] = d * d;
+    sm[threadIdx.x] = w * d * d;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
         if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
@@ -808,10 +815,10 @@ cudaError_t colsum(const void* g, bool g_fp32, long long rows, int C, int pitch,
 }
 
 cudaError_t mse(const float* pred, const float* target, long long n, float* grad, float* loss, float* part,
-                cudaStream_t s)
+                cudaStream_t s, const float* x, int F, float alpha)
 {
     const int nb = (int)((n + 255) / 256);
-    k_mse<<<nb, 256, 0, s>>>(pred, target, n, grad, part);
+    k_mse<<<nb, 256, 0, s>>>(pred, target, n, x, F, alpha, grad, part);
     k_sum_parts<<<1, 32, 0, s>>>(part, nb, 1, loss);
     return cudaGetLastError();
 }

@@ -28,8 +28,11 @@ cudaError_t mask_cast(const float* g, int gpitch, const void* y, int ypitch, lon
 cudaError_t pad_conv3x3(const void* W, int cout, int cin, int cin_pad, void* Wp, cudaStream_t s);
 cudaError_t colsum(const void* g, bool g_fp32, long long rows, int C, int pitch, float* out, float* part,
                    int part_blocks, cudaStream_t s);
+// Mean of w (pred - target)^2 over n elements and its gradient; with x (the
+// network input, F fields per pixel, phase field first) each pixel's
+// elements are weighted by w = 1 + alpha max(0, 1 - phi^2), else w = 1.
 cudaError_t mse(const float* pred, const float* target, long long n, float* grad, float* loss, float* part,
-                cudaStream_t s);
+                cudaStream_t s, const float* x = nullptr, int F = 1, float alpha = 0.0f);
 cudaError_t adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
                  int t, void* wb, cudaStream_t s);
 cudaError_t pack(const float* f, long long P, int F, const float* mean, const float* inv_std, void* X, int cpitch,

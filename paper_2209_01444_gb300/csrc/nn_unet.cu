@@ -88,6 +88,7 @@ struct lbm_unet {
     bf16* wb = nullptr;
     int t = 0;
     float *mean = nullptr, *inv_std = nullptr, *inv_out = nullptr;
+    float iface_w = 0.0f;  // interface weight of the loss (lbm_unet_set_loss_weight)
     std::vector<float> norm_h;  // host copy: mean, std_in, std_out (F each)
     bf16* x0 = nullptr;
     float *Y = nullptr, *T = nullptr, *G = nullptr;
@@ -421,7 +422,9 @@ cudaError_t backward(lbm_unet* u, const float* x, const float* t)
     const long long P0 = u->P0;
     const int L = u->L, F = u->F, w0 = u->base;
     if ((e = nn::increment(t, x, P0, F, u->inv_out, u->T, u->s))) return e;
-    if ((e = nn::mse(u->Y, u->T, P0 * F, u->G, u->loss, u->part, u->s))) return e;
+    if ((e = nn::mse(u->Y, u->T, P0 * F, u->G, u->loss, u->part, u->s, u->iface_w != 0.0f ? x : nullptr, F,
+                     u->iface_w)))
+        return e;
     const bf16* top = L > 1 ? u->lv[0].dD : u->lv[0].s;
     if ((e = nn::proj_bwd(u->G, top, (int)P0, w0, w0, u->w + u->out_w, F, u->g32, w0, u->g + u->out_w, u->g + u->out_b,
                           u->part, kPartBlocks, u->s)))
@@ -564,6 +567,13 @@ static int get_vec(lbm_unet* u, const float* dev, float* host)
 int lbm_unet_get_params(lbm_unet* u, float* host) { return get_vec(u, u ? u->w : nullptr, host); }
 
 int lbm_unet_get_grads(lbm_unet* u, float* host) { return get_vec(u, u ? u->g : nullptr, host); }
+
+int lbm_unet_set_loss_weight(lbm_unet* u, float alpha)
+{
+    if (!u || !(alpha >= 0.0f) || !isfinite(alpha)) return LBM_EINVAL;
+    u->iface_w = alpha;
+    return LBM_OK;
+}
 
 int lbm_unet_set_norm(lbm_unet* u, const float* mean, const float* std_in, const float* std_out)
 {

@@ -137,6 +137,7 @@ SIGNATURES = {
     "lbm_unet_get_params": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_get_grads": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "lbm_unet_set_norm": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "lbm_unet_set_loss_weight": (ct.c_int, [ct.c_void_p, ct.c_float]),
     "lbm_unet_save": (ct.c_int, [ct.c_void_p, ct.c_char_p]),
     "lbm_unet_load": (ct.c_int, [ct.c_void_p, ct.c_char_p]),
     "lbm_unet_forward": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),

@@ -127,6 +127,12 @@ class UNet:
                                                so.ctypes.data_as(ct.c_void_p)))
         self.norm = (m, si, so)
 
+    def set_loss_weight(self, alpha: float) -> None:
+        """Interface weight of the loss: squared errors at each pixel weighted
+        by 1 + alpha max(0, 1 - phi^2), phi the input's phase field."""
+        self._check(self.lib.lbm_unet_set_loss_weight(self.h, float(alpha)))
+        self.loss_weight = float(alpha)
+
     def save(self, path: str) -> None:
         """Parameters and normalisation to a weight file (lbm_unet_save)."""
         self._check(self.lib.lbm_unet_save(self.h, os.fsencode(path)))

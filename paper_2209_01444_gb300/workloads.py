@@ -270,6 +270,45 @@ def surrogate_domains(count: int = 32, n: int = 256, rng_seed: int = 5, steps: i
     return cases
 
 
+def surrogate_training_set(n: int = 512, per_generator: int = 8, rng_seed: int = 5) -> list[Case]:
+    """Training trajectories for the surrogate from the three workload
+    generators, per_generator each, on n x n domains:
+      - the single dendrite in forced flow (inflow left at u_x = 0.01 lattice
+        units, outflow right, symmetry top and bottom; Delta = 0.55,
+        eps = 0.05, orientation 0), one seed of radius 6-12 near
+        (0.375 n, 0.5 n);
+      - the parameter sweep's draws in the same geometry: Delta in [0.3, 0.7],
+        eps in [0.02, 0.06], orientation in [0, 45 deg), inflow u_x in
+        [0, 0.02], one seed of radius 8 at (0.375 n, 0.5 n);
+      - crops of the multi-seed thermosolutal box: periodic in x, no-slip
+        walls in y, buoyancy on, Delta = 0.45, eps = 0.04, 1-3 seeds by dart
+        throwing (spacing >= n/4, margin 20), radii 6-10, orientations in
+        [0, 45 deg)."""
+    rng = np.random.Generator(np.random.PCG64(rng_seed))
+    flow_bc = ("inflow", "outflow", "symmetry", "symmetry")
+    cases = []
+    for j in range(per_generator):
+        cx = 0.375 * n + float(rng.uniform(-0.05, 0.05)) * n
+        cy = 0.5 * n + float(rng.uniform(-0.05, 0.05)) * n
+        R = float(rng.uniform(6.0, 12.0))
+        p = thermosolutal_params(n, n, eps_s=0.05, theta_ref=-0.55, bc=flow_bc, u_in=(0.01 * DX / DT, 0.0))
+        cases.append(Case(f"train_forced_{j}_{n}", p, np.array([[cx, cy, R, 0.0]]), 0.0, -0.55, 0))
+    for j in range(per_generator):
+        delta = float(rng.uniform(0.3, 0.7))
+        eps = float(rng.uniform(0.02, 0.06))
+        orient = float(rng.uniform(0.0, math.pi / 4))
+        uin = float(rng.uniform(0.0, 0.02))
+        p = thermosolutal_params(n, n, eps_s=eps, theta_ref=-delta, bc=flow_bc, u_in=(uin * DX / DT, 0.0))
+        cases.append(Case(f"train_sweep_{j}_{n}", p, np.array([[0.375 * n, 0.5 * n, 8.0, orient]]), 0.0, -delta, 0))
+    for j in range(per_generator):
+        count = int(rng.integers(1, 4))
+        seeds = dart_seeds(n, n, count, n / 4, 20.0, 6.0, 10.0, math.pi / 4, rng)
+        p = thermosolutal_params(n, n, eps_s=0.04, gbetaT=GBETA_T, gbetaC=GBETA_C, theta_ref=-0.45,
+                                 bc=("periodic", "periodic", "noslip", "noslip"))
+        cases.append(Case(f"train_multi_{j}_{n}", p, seeds, 0.0, -0.45, 0))
+    return cases
+
+
 def cylinder_flow(Re: float = 40.0, nx: int = 1400, ny: int = 800, R: float = 20.0, u0: float = 0.1) -> Case:
     """Flow past a stationary cylinder (Sec. 4.1): a (70 x 40) R_s domain of
     nx x ny nodes, the disc of radius R nodes at (20 R, 20 R) as a diffuse

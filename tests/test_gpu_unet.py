@@ -96,7 +96,7 @@ def _all_active(params):
     return out
 
 
-def _grad_errors(S, torch, levels, B, H, seed, active=False):
+def _grad_errors(S, torch, levels, B, H, seed, active=False, alpha=0.0):
     shapes = U.init_shapes(levels, BASE, 8, F)
     params = workloads.unet_params(shapes, seed)
     if active:
@@ -104,6 +104,7 @@ def _grad_errors(S, torch, levels, B, H, seed, active=False):
     x, t = _inputs(seed, B, H, H)
     net = S.UNet(B, H, H, levels=levels)
     net.set_params(params)
+    net.set_loss_weight(alpha)
     net.backward(_dev(torch, x), _dev(torch, t))
     loss, g = net.loss(), net.grads()
     out = {}
@@ -111,7 +112,7 @@ def _grad_errors(S, torch, levels, B, H, seed, active=False):
         yr, cache = U.forward(params, _pad8(x), levels, F, q=q)
         if active:
             assert all((v > 0).all() for k, v in cache.items() if k.endswith((".a", ".s", ".d")))
-        lr, dy = U.mse(yr, t)
+        lr, dy = U.mse(yr, t, x, alpha) if alpha else U.mse(yr, t)
         gr = U.backward(params, cache, dy, levels, q=q)
         assert abs(loss - lr) <= 1e-3 * lr, (loss, lr)
         for name, _ in shapes:
@@ -120,6 +121,22 @@ def _grad_errors(S, torch, levels, B, H, seed, active=False):
             cos = float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b)))
             out[(q is None, name)] = (rel, cos)
     return out
+
+
+@pytest.mark.parametrize("levels,B,H,tol", [(1, 2, 16, 2e-3), (2, 2, 16, 2e-2)])
+def test_gradients_with_the_interface_weighted_loss_match_oracle(env, levels, B, H, tol):
+    """The loss weighted by 1 + alpha max(0, 1 - phi^2) at each pixel (alpha =
+    30; the random inputs' phase field falls both inside and outside [-1, 1]):
+    the loss and every parameter gradient against the oracle's weighted loss
+    with the same rounding points."""
+    torch, lib, S = env
+    err = _grad_errors(S, torch, levels, B, H, 40 + levels, alpha=30.0)
+    assert lib.lbm_nn_error(1) == 0
+    for (pure, name), (rel, cos) in err.items():
+        if pure:
+            assert cos >= 0.98, (name, cos)
+        else:
+            assert rel <= tol, (name, rel)
 
 
 @pytest.mark.parametrize("levels,B,H,tol", [(1, 2, 16, 2e-3), (2, 2, 16, 2e-2)])

@@ -192,3 +192,32 @@ def test_bf16_round_matches_torch_and_quantised_network_is_close():
     yq, _ = U.forward(params, x, 3, 5, q=U.bf16_round)
     d64, dq = y64 - x[..., :5], yq - x[..., :5]
     assert 0 < np.abs(dq - d64).max() <= 0.05 * np.abs(d64).max()
+
+
+def test_interface_weighted_mse_against_its_definition_and_finite_differences():
+    """The weighted loss mean(w d^2), w = 1 + alpha max(0, 1 - phi^2) per
+    pixel (phi the input's first field), by brute force over pixels and
+    channels, its gradient by central differences, and alpha = 0 (or phi
+    outside [-1, 1]) giving the plain mean."""
+    rng = np.random.default_rng(7)
+    x = rng.uniform(-1, 1, size=(2, 3, 4, 5))
+    y, t = rng.normal(size=x.shape), rng.normal(size=x.shape)
+    alpha = 12.0
+    loss, g = U.mse(y, t, x, alpha)
+    acc = 0.0
+    for idx in np.ndindex(x.shape):
+        w = 1.0 + alpha * max(0.0, 1.0 - x[idx[:3] + (0,)] ** 2)
+        acc += w * (y[idx] - t[idx]) ** 2
+    assert loss == pytest.approx(acc / x.size, rel=1e-14)
+    h = 1e-6
+    for idx in [(0, 0, 0, 0), (1, 2, 3, 4), (0, 1, 2, 3)]:
+        yp, ym = y.copy(), y.copy()
+        yp[idx] += h
+        ym[idx] -= h
+        fd = (U.mse(yp, t, x, alpha)[0] - U.mse(ym, t, x, alpha)[0]) / (2 * h)
+        assert g[idx] == pytest.approx(fd, rel=1e-6)
+    assert U.mse(y, t, x, 0.0)[0] == pytest.approx(U.mse(y, t)[0], rel=1e-15)
+    # outside [-1, 1] (a prediction's overshoot) the weight stays 1
+    xo = x.copy()
+    xo[..., 0] = 1.5
+    assert U.mse(y, t, xo, alpha)[0] == pytest.approx(U.mse(y, t)[0], rel=1e-15)
