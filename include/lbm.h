@@ -565,9 +565,10 @@ LBM_API int lbm_nn_set_operand_wait(unsigned long long ns);
  * nodes: node (x, y) is lane (y*pitch + x) % 32 of block (y*pitch + x) / 32,
  * and a block stores each of its planes as 32 consecutive values, plane after
  * plane.  A scalar block has the 15 FP32 planes f_0..4, n_0..4, g_0..4
- * (LBM_FP32; 1920 bytes), or the 12 moving planes f_1..4, n_1..4, g_1..4 in
- * 16 bits followed by the FP32 rest planes f_0, n_0, g_0 (LBM_FP16/LBM_BF16;
- * 1152 bytes); a flow block has the 9 planes h_0..8 of the storage type.  Output: `out`, 10 doubles in device memory: sum (1 + phi)/2,
+ * (LBM_FP32; 1920 bytes), or (LBM_FP16/LBM_BF16; 1152 bytes) the planes
+ * f_1..4 in 16 bits, then four planes of 32-bit words holding (n_i, g_i) for
+ * i = 1..4 (n_i in the low half), then the FP32 rest planes f_0, n_0, g_0; a
+ * flow block has the 9 planes h_0..8 of the storage type.  Output: `out`, 10 doubles in device memory: sum (1 + phi)/2,
  * sum C, sum H, sum of all h_i, max |u| in flow lattice units, number of nodes
  * with a non-finite macro, sum phi, and the three tip distances of
  * lbm_metrics.tip.  The work is queued on `stream` (a cudaStream_t, NULL for the

@@ -888,7 +888,7 @@ int lbm_save_state(lbm_handle* h, void* host, size_t bytes)
     char* p = (char*)host;
     CkptHeader hd;
     memset(&hd, 0, sizeof(hd));
-    memcpy(hd.magic, "LBMCKPT2", 8);
+    memcpy(hd.magic, "LBMCKPT3", 8);
     hd.prm = h->prm;
     hd.steps = h->steps;
     hd.uniform = h->uniform ? 1 : 0;
@@ -916,7 +916,7 @@ int lbm_load_state(lbm_handle* h, const void* host, size_t bytes)
     const char* p = (const char*)host;
     CkptHeader hd;
     memcpy(&hd, p, sizeof(hd));
-    if (memcmp(hd.magic, "LBMCKPT2", 8) != 0) return fail(h, LBM_EINVAL, "not a checkpoint of this layout");
+    if (memcmp(hd.magic, "LBMCKPT3", 8) != 0) return fail(h, LBM_EINVAL, "not a checkpoint of this layout");
     if (memcmp(&hd.prm, &h->prm, sizeof(lbm_params)) != 0) return fail(h, LBM_EINVAL, "checkpoint parameters differ");
     p += sizeof(hd);
     const size_t plane = (size_t)h->P.plane;

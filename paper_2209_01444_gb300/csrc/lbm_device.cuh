@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace lbm {
 
@@ -139,6 +140,21 @@ struct StoreF32 {
     static __device__ __forceinline__ int flow_col(int x) { return block_col(x, 9); }
     static __device__ __forceinline__ void store_mov(void* sc, int q, long long e, float v) { ((float*)sc)[e + 32 * q] = v; }
     static __device__ __forceinline__ void store_flow(void* fl, int i, long long e, float v) { ((float*)fl)[e + 32 * i] = v; }
+    // n_i and g_i (i = 1..4), which stream to the same neighbour: the moving
+    // scalar index serves both (16-bit storage keeps them in one word)
+    static __device__ __forceinline__ long long pair_row(int y, const StepParams& P) { return mov_row(y, P); }
+    static __device__ __forceinline__ int pair_col(int x) { return mov_col(x); }
+    static __device__ __forceinline__ void load_pair(const void* sc, int i, long long o, float& n, float& g)
+    {
+        const long long b = block_index(o, 15);
+        n = ((const float*)sc)[b + 32 * (kN + i)];
+        g = ((const float*)sc)[b + 32 * (kG + i)];
+    }
+    static __device__ __forceinline__ void store_pair(void* sc, int i, long long e, float n, float g)
+    {
+        ((float*)sc)[e + 32 * (kN + i)] = n;
+        ((float*)sc)[e + 32 * (kG + i)] = g;
+    }
 };
 
 template <class H>
@@ -147,15 +163,48 @@ template <>
 struct Conv<__half> {
     static __device__ __forceinline__ float to(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half from(float v) { return __float2half_rn(v); }
+    // a 32-bit word of two values (low half first)
+    static __device__ __forceinline__ float2 to2(uint32_t w)
+    {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        return __half22float2(h);
+    }
+    static __device__ __forceinline__ uint32_t from2(float a, float b)
+    {
+        const __half2 h = __floats2half2_rn(a, b);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
 };
 template <>
 struct Conv<__nv_bfloat16> {
     static __device__ __forceinline__ float to(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float2 to2(uint32_t w)
+    {
+        __nv_bfloat162 h;
+        memcpy(&h, &w, 4);
+        return __bfloat1622float2(h);
+    }
+    static __device__ __forceinline__ uint32_t from2(float a, float b)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
 };
 
 // S_SC, S_FL: power-of-two scales of the scalar and flow deviations before
 // rounding (FP16 keeps the smallest deviations out of its subnormal range).
+// A scalar block (1152 bytes = 288 32-bit words) holds, for its 32 nodes:
+// words 0..63 the phase-field planes f_1..f_4 in 16 bits (f_i at 16-bit index
+// 32 (i - 1) + lane); words 64..191 the pairs (n_i, g_i), i = 1..4, one word
+// per node (n in the low half; pair i at word 64 + 32 (i - 1) + lane), since
+// both go to the same neighbour; words 192..287 the FP32 rest planes f_0,
+// n_0, g_0 (word 192 + 32 r + lane).
 template <class H, int S_SC, int S_FL>
 struct Store16 {
     using T = H;
@@ -164,23 +213,29 @@ struct Store16 {
     static constexpr int kScalarBytes = 12 * 2 + 3 * 4;
     static constexpr int kFlowBytes = 9 * 2;
     static __device__ __forceinline__ bool rest(int q) { return q == kF || q == kN || q == kG; }
-    static __device__ __forceinline__ int slot(int q) { return q - 1 - q / 5; }  // moving planes 0..11
-    // 16-bit index of moving slot 0 and FP32 index of rest plane 0 of node o
-    // in the scalar buffer (1152-byte blocks: 576 16-bit or 288 FP32 values)
+    // word index of word 0 of node o's block plus its lane
+    static __device__ __forceinline__ long long word_index(long long o)
+    {
+        return (long long)((unsigned long long)(unsigned)(o >> 5) * 288u) + (long long)(o & 31);
+    }
+    // 16-bit index of f_1 of node o
     static __device__ __forceinline__ long long moving_index(long long o)
     {
         return (long long)((unsigned long long)(unsigned)(o >> 5) * 576u) + (long long)(o & 31);
     }
-    static __device__ __forceinline__ long long rest_index(long long o)
+    // 16-bit index of the value of scalar population q (moving, not rest) of node o
+    static __device__ __forceinline__ long long half_index(int q, long long o)
     {
-        return (long long)((unsigned long long)(unsigned)(o >> 5) * 288u) + 192 + (long long)(o & 31);
+        if (q < kN) return moving_index(o) + 32 * (q - 1);
+        const int i = q < kG ? q - kN : q - kG;
+        return 2 * (word_index(o) + 64 + 32 * (i - 1)) + (q < kG ? 0 : 1);
     }
     static __device__ __forceinline__ float load(const void* sc, const void* fl, int q, long long o,
                                                  const StepParams& P)
     {
         if (q >= kH) return Conv<H>::to(((const H*)fl)[block_index(o, 9) + 32 * (q - kH)]) * inv_scale(q);
-        if (rest(q)) return ((const float*)sc)[rest_index(o) + 32 * (q / 5)];
-        return Conv<H>::to(((const H*)sc)[moving_index(o) + 32 * slot(q)]) * inv_scale(q);
+        if (rest(q)) return ((const float*)sc)[word_index(o) + 192 + 32 * (q / 5)];
+        return Conv<H>::to(((const H*)sc)[half_index(q, o)]) * inv_scale(q);
     }
     static __device__ __forceinline__ void store(void* sc, void* fl, int q, long long o, float v,
                                                  const StepParams& P)
@@ -188,24 +243,41 @@ struct Store16 {
         if (q >= kH)
             ((H*)fl)[block_index(o, 9) + 32 * (q - kH)] = Conv<H>::from(v * scale(q));
         else if (rest(q))
-            ((float*)sc)[rest_index(o) + 32 * (q / 5)] = v;
+            ((float*)sc)[word_index(o) + 192 + 32 * (q / 5)] = v;
         else
-            ((H*)sc)[moving_index(o) + 32 * slot(q)] = Conv<H>::from(v * scale(q));
+            ((H*)sc)[half_index(q, o)] = Conv<H>::from(v * scale(q));
     }
+    // pushes: the moving phase-field planes (16-bit index, row + column terms),
+    // the (n_i, g_i) words (word index) and the flow planes
     static __device__ __forceinline__ long long mov_row(int y, const StepParams& P)
     {
         return (long long)((unsigned long long)(unsigned)(y * (P.pitch >> 5)) * 576u);
     }
     static __device__ __forceinline__ int mov_col(int x) { return (x >> 5) * 576 + (x & 31); }
+    static __device__ __forceinline__ long long pair_row(int y, const StepParams& P)
+    {
+        return (long long)((unsigned long long)(unsigned)(y * (P.pitch >> 5)) * 288u);
+    }
+    static __device__ __forceinline__ int pair_col(int x) { return (x >> 5) * 288 + (x & 31) + 64; }
     static __device__ __forceinline__ long long flow_row(int y, const StepParams& P) { return block_row(y, P.pitch, 9); }
     static __device__ __forceinline__ int flow_col(int x) { return block_col(x, 9); }
-    static __device__ __forceinline__ void store_mov(void* sc, int q, long long e, float v)
+    static __device__ __forceinline__ void store_mov(void* sc, int q, long long e, float v)  // q = f_1..f_4
     {
-        ((H*)sc)[e + 32 * slot(q)] = Conv<H>::from(v * scale(q));
+        ((H*)sc)[e + 32 * (q - 1)] = Conv<H>::from(v * (float)S_SC);
     }
     static __device__ __forceinline__ void store_flow(void* fl, int i, long long e, float v)
     {
         ((H*)fl)[e + 32 * i] = Conv<H>::from(v * (float)S_FL);
+    }
+    static __device__ __forceinline__ void load_pair(const void* sc, int i, long long o, float& n, float& g)
+    {
+        const float2 v = Conv<H>::to2(((const uint32_t*)sc)[word_index(o) + 64 + 32 * (i - 1)]);
+        n = v.x * (1.0f / S_SC);
+        g = v.y * (1.0f / S_SC);
+    }
+    static __device__ __forceinline__ void store_pair(void* sc, int i, long long e, float n, float g)
+    {
+        ((uint32_t*)sc)[e + 32 * (i - 1)] = Conv<H>::from2(n * (float)S_SC, g * (float)S_SC);
     }
 };
 using StoreF16 = Store16<__half, 16, 1024>;

@@ -237,10 +237,12 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
         Store::store(dst, dstf, kG, o, go[0], P);
 #pragma unroll
         for (int i = 1; i < 5; ++i) Store::store_mov(dst, kF + i, d5[i], fo[i] * ia - ib * fd[i]);
+        // n_i and g_i go to the same neighbour (one word in 16-bit storage)
+        const long long qY = Store::pair_row(y, P), qP = Store::pair_row(yp, P), qM = Store::pair_row(ym, P);
+        const int p0 = Store::pair_col(x), pP = Store::pair_col(xp), pM = Store::pair_col(xm);
+        const long long e5[5] = {0, qY + pP, qP + p0, qY + pM, qM + p0};
 #pragma unroll
-        for (int i = 1; i < 5; ++i) Store::store_mov(dst, kN + i, d5[i], no[i]);
-#pragma unroll
-        for (int i = 1; i < 5; ++i) Store::store_mov(dst, kG + i, d5[i], go[i]);
+        for (int i = 1; i < 5; ++i) Store::store_pair(dst, i, e5[i], no[i], go[i]);
     }
     {
         const long long rY = Store::flow_row(y, P), rP = Store::flow_row(yp, P), rM = Store::flow_row(ym, P);
@@ -333,10 +335,10 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
     float f[5], n[5], g[5], h[9];
 #pragma unroll
     for (int i = 0; i < 5; ++i) f[i] = Store::load(src, srcf, kF + i, oc, P);
+    n[0] = Store::load(src, srcf, kN, o, P);
+    g[0] = Store::load(src, srcf, kG, o, P);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) n[i] = Store::load(src, srcf, kN + i, o, P);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) g[i] = Store::load(src, srcf, kG + i, o, P);
+    for (int i = 1; i < 5; ++i) Store::load_pair(src, i, o, n[i], g[i]);
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] = Store::load(src, srcf, kH + i, o, P);
     const float* hn = hist;
