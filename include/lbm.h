@@ -209,7 +209,10 @@ LBM_API long long lbm_step_count(const lbm_handle* h);
  * increasing field order, nx*ny doubles each: phi, C, U (Eq. 20), theta
  * (Eq. 23), u_x, u_y (corrected velocity of Eq. 26, paper units), p (Eq. 26,
  * paper units).  Only the selected planes are copied to the host (as FP32,
- * converted there).  Synchronous. */
+ * band by band through a pinned staging buffer of at most 64 MiB that the
+ * process's handles share, allocated on the first call and kept until exit),
+ * and converted there on up to 16 host threads while the next band is
+ * copied.  Synchronous. */
 LBM_API int lbm_get_fields(lbm_handle* h, unsigned mask, double* out);
 
 /* FP64 copy of the decoded state: LBM_STATE_PLANES planes of nx*ny

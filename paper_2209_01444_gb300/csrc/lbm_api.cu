@@ -10,7 +10,9 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lbm.h"
@@ -77,6 +79,8 @@ struct lbm_handle {
     std::vector<long long> mon_steps;  // step of each record, in order of recording
     // flow-only steps: frozen phi and F_y
     float *flow_phi = nullptr, *flow_fy = nullptr;
+    // events of the two halves of the shared pinned staging buffer (lbm_get_fields)
+    cudaEvent_t pin_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -383,6 +387,30 @@ int graph_for(lbm_handle* h, cudaGraphExec_t* out)
     return LBM_OK;
 }
 
+// Pinned host staging buffer of lbm_get_fields, shared by every handle of the
+// process (at most 2 x kPinHalf bytes, allocated on first use, kept until
+// exit); a call holds the mutex while it uses it.
+constexpr size_t kPinHalf = (size_t)32 << 20;
+struct PinnedStaging {
+    std::mutex mu;
+    float* p = nullptr;
+    size_t bytes = 0;
+} g_pinned;
+
+// Runs fn(r0, r1) over the row range [0, rows) on up to 16 host threads.
+template <class Fn>
+void parallel_rows(int rows, Fn fn)
+{
+    const int nt = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 16, rows / 8}));
+    if (nt == 1) {
+        fn(0, rows);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(fn, rows * t / nt, rows * (t + 1) / nt);
+    for (std::thread& th : pool) th.join();
+}
+
 }  // namespace
 
 extern "C" {
@@ -479,6 +507,8 @@ void lbm_destroy(lbm_handle* h)
                     h->sur_x, h->sur_y, h->sur_l, h->d_mis, h->d_ring, h->flow_phi, h->flow_fy};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    for (cudaEvent_t e : h->pin_ev)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 
@@ -730,32 +760,62 @@ int lbm_get_fields(lbm_handle* h, unsigned mask, double* out)
     int rows;
     if ((rc = band_rows(h, LBM_NUM_FIELDS * sizeof(float), &rows))) return rc;
     float* dev = (float*)h->scratch;
-    int nsel = 0;
-    for (int q = 0; q < LBM_NUM_FIELDS; ++q) nsel += (mask >> q) & 1u;
-    std::vector<float> host((size_t)rows * pitch * std::max(nsel, 1));
-    for (int y0 = 0; y0 < ny; y0 += rows) {
+    int sel[LBM_NUM_FIELDS], nsel = 0;
+    for (int q = 0; q < LBM_NUM_FIELDS; ++q)
+        if (mask & (1u << q)) sel[nsel++] = q;
+    if (!nsel) return LBM_OK;
+    // two pinned halves: the host converts one band while the next is computed and copied
+    rows = std::max(1, std::min<int>(rows, (int)(kPinHalf / ((size_t)pitch * nsel * sizeof(float)))));
+    const size_t half = (size_t)rows * pitch * nsel;
+    std::lock_guard<std::mutex> lock(g_pinned.mu);
+    if (g_pinned.bytes < 2 * half * sizeof(float)) {
+        if (g_pinned.p) cudaFreeHost(g_pinned.p);
+        g_pinned.p = nullptr;
+        g_pinned.bytes = 0;
+        cudaError_t e = cudaHostAlloc((void**)&g_pinned.p, 2 * half * sizeof(float), cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, LBM_ENOMEM, std::string("pinned band buffer: ") + cudaGetErrorString(e));
+        }
+        g_pinned.bytes = 2 * half * sizeof(float);
+    }
+    float* pin = g_pinned.p;
+    for (cudaEvent_t& e : h->pin_ev)
+        if (!e) LBM_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    auto convert = [&](int y0, int r, const float* src) {
+        const size_t band = (size_t)r * pitch;
+        parallel_rows(r, [&](int r0, int r1) {
+            for (int k = 0; k < nsel; ++k) {
+                const int q = sel[k];
+                const double sq = scale[q], oq = offset[q];
+                for (int y = r0; y < r1; ++y) {
+                    const float* in = src + (size_t)k * band + (size_t)y * pitch;
+                    double* o = out + (size_t)k * nx * ny + (size_t)(y0 + y) * nx;
+                    for (int x = 0; x < nx; ++x) o[x] = (double)in[x] * sq + oq;
+                }
+            }
+        });
+    };
+    int prev_y0 = -1, prev_r = 0, slot = 0;
+    for (int y0 = 0; y0 < ny; y0 += rows, slot ^= 1) {
         const int r = std::min(rows, ny - y0);
         const size_t band = (size_t)r * pitch;
+        float* dst = pin + (size_t)slot * half;
         LBM_CUDA(h, lbm::launch_macros(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], dev, y0, r, h->stream));
         // only the requested planes cross to the host
-        size_t k = 0;
-        for (int q = 0; q < LBM_NUM_FIELDS; ++q) {
-            if (!(mask & (1u << q))) continue;
-            LBM_CUDA(h, cudaMemcpyAsync(host.data() + k * band, dev + (size_t)q * band, band * sizeof(float),
+        for (int k = 0; k < nsel; ++k)
+            LBM_CUDA(h, cudaMemcpyAsync(dst + k * band, dev + (size_t)sel[k] * band, band * sizeof(float),
                                         cudaMemcpyDeviceToHost, h->stream));
-            ++k;
+        LBM_CUDA(h, cudaEventRecord(h->pin_ev[slot], h->stream));
+        if (prev_y0 >= 0) {
+            LBM_CUDA(h, cudaEventSynchronize(h->pin_ev[slot ^ 1]));
+            convert(prev_y0, prev_r, pin + (size_t)(slot ^ 1) * half);
         }
-        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-        k = 0;
-        for (int q = 0; q < LBM_NUM_FIELDS; ++q) {
-            if (!(mask & (1u << q))) continue;
-            for (int y = 0; y < r; ++y)
-                for (int x = 0; x < nx; ++x)
-                    out[k * (size_t)nx * ny + (size_t)(y0 + y) * nx + x] =
-                        (double)host[k * band + (size_t)y * pitch + x] * scale[q] + offset[q];
-            ++k;
-        }
+        prev_y0 = y0;
+        prev_r = r;
     }
+    LBM_CUDA(h, cudaEventSynchronize(h->pin_ev[slot ^ 1]));
+    convert(prev_y0, prev_r, pin + (size_t)(slot ^ 1) * half);
     return LBM_OK;
 }
 
