@@ -405,11 +405,23 @@ LBM_API int lbm_nn_proj_bwd(const float* dY, const void* X, int P, int C, int xp
                             void* stream);
 LBM_API int lbm_nn_flip3x3(const void* W, int cout, int cin, void* Wf, void* stream);
 /* Transposed gather for weight gradients: AT[t*C + c][p] = X[pixel p shifted
- * by tap t][c] (zero outside the image) for taps = 9 (t = ky*3 + kx), or
- * AT[c][p] = X[p][c] for taps = 1; BF16, row pitch atpitch; C, cpitch, atpitch
- * and B*H*W multiples of 8. */
+ * by tap t][c] (zero outside the image) for taps = 9 (t = ky*3 + kx); for
+ * taps = 3 the middle row of those taps only, AT[kx*C + c][p] = X[p shifted by
+ * (dy, dx) = (0, kx - 1)][c]; AT[c][p] = X[p][c] for taps = 1; BF16, row pitch
+ * atpitch; C, cpitch, atpitch and B*H*W multiples of 8. */
 LBM_API int lbm_nn_gather_t(const void* X, int B, int H, int W, int C, int cpitch, int taps, void* AT,
                             long long atpitch, void* stream);
+/* Weight gradient of a 3 x 3 zero-padded convolution from three copies of its
+ * input: D[n][t*C + c] = sum_p X[p shifted by tap t][c] dY[p][n] (t = ky*3 +
+ * kx), FP32 with row pitch ldd >= 9C, from XT3 = lbm_nn_gather_t(X, taps = 3)
+ * (BF16 [3C][B*H*W], pitch B*H*W) and dYT = dY transposed (BF16 [cout][B*H*W],
+ * pitch B*H*W).  The vertical shifts are taken by the tensor-core GEMM's TMA
+ * coordinates, zero filled outside the image.  K = B*H*W is split into
+ * `splits` slices whose partial sums go to `workspace` (splits * 9C * cout
+ * floats).  W and C multiples of 32, cout a multiple of 8: LBM_EINVAL
+ * otherwise. */
+LBM_API int lbm_nn_wgrad3x3(const void* XT3, const void* dYT, int B, int H, int W, int C, int cout, float* D,
+                            int ldd, int splits, float* workspace, void* stream);
 LBM_API int lbm_nn_colsum(const void* g, int g_fp32, long long rows, int C, int pitch, float* out, float* part,
                           int part_blocks, void* stream);
 LBM_API int lbm_nn_mse(const float* pred, const float* target, long long n, float* grad, float* loss, float* part,

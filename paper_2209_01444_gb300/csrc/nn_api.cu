@@ -111,6 +111,16 @@ int lbm_nn_gather_t(const void* X, int B, int H, int W, int C, int cpitch, int t
     return nn_status(nn::gatherT(X, B, H, W, C, cpitch, taps, AT, atpitch, NN_S(stream)));
 }
 
+int lbm_nn_wgrad3x3(const void* XT3, const void* dYT, int B, int H, int W, int C, int cout, float* D, int ldd,
+                    int splits, float* workspace, void* stream)
+{
+    if (!XT3 || !dYT || !D || !workspace) {
+        lbm::set_last_error("lbm_nn_wgrad3x3: NULL argument");
+        return LBM_EINVAL;
+    }
+    return nn_status(nn::wgrad3_bf16(XT3, dYT, B, H, W, C, cout, D, ldd, NN_S(stream), splits, workspace));
+}
+
 int lbm_nn_flip3x3(const void* W, int cout, int cin, void* Wf, void* stream)
 {
     return nn_status(nn::flip3x3(W, cout, cin, Wf, NN_S(stream)));

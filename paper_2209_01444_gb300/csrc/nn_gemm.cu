@@ -223,7 +223,16 @@ namespace {
 // blockIdx.z selects a slice of kb_per_split K blocks; with more than one
 // slice each writes its FP32 partial tile to D + z * M * ldd (no bias or
 // activation) and a reduction kernel finishes.
-template <int BN, bool OUT_BF16, int BK, bool CONV>
+//
+// WG (weight gradient of a 3 x 3 convolution, dW^T = X_taps^T dY, K = pixels):
+// the A rows are (tap t, input channel ci), t = 3 ky + kx, and tmA is a 4-D
+// map (x, y, image, row) over three transposed copies of the input shifted
+// by dx = kx - 1, row kx * C + ci (geo.C = C input channels); each K block of
+// BK pixels lies in one image row, and each tap's rows of the A tile come
+// from one box at that row shifted by dy = ky - 1 along y (zero filled
+// outside the image, the convolution's padding).  The shift is on the y
+// coordinate, so the innermost (x) coordinate stays a multiple of BK.
+template <int BN, bool OUT_BF16, int BK, bool CONV, bool WG = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, void* __restrict__ D,
            const float* __restrict__ bias, int M, int N, int K, int ldd, int relu, int kb_per_split, ConvGeo geo,
@@ -279,10 +288,48 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
+    // WG: the A boxes of this CTA's rows (fixed for the CTA) and the pixel
+    // position (x, y, image) of the next K block to load, advanced by one K
+    // block per load, so that the thread issuing the loads and MMAs does no
+    // division in its loop (load is called with kb = 0, 1, 2, ... in order).
+    int wx = 0, wy = 0, wb = 0, nbox = 0;
+    int wrow[4] = {0, 0, 0, 0}, wdy[4] = {0, 0, 0, 0};
+    if constexpr (WG) {
+        const long long pp = (long long)kb0 * BK;  // first pixel of the slice
+        wx = (int)(pp % geo.W);
+        const long long rw = pp / geo.W;
+        wy = (int)(rw % geo.H);
+        wb = (int)(rw / geo.H);
+        nbox = kBM / geo.cblocks;  // boxes of geo.cblocks rows (128, 64 or 32; divides C)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int row = m0 + j * geo.cblocks;
+            const int t = row / geo.C, ci0 = row - t * geo.C;
+            const int ky = t / 3, kx = t - 3 * ky;
+            // rows past the nine taps: a box outside the map, zero filled
+            wrow[j] = t < 9 ? kx * geo.C + ci0 : 3 * geo.C;
+            wdy[j] = ky - 1;
+        }
+    }
+
     auto load = [&](int kb, int st) {
         uint8_t* a = smem + st * STAGE;
         mbar_expect_tx(&full[st], STAGE);
-        if constexpr (CONV) {
+        if constexpr (WG) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < nbox)
+                    tma_load_4d(a + j * geo.cblocks * BK * 2, &tmA, wx, wy + wdy[j], wb, wrow[j], &full[st]);
+            tma_load_2d(a + A_BYTES, &tmB, (kb0 + kb) * BK, n0, &full[st]);
+            wx += BK;
+            if (wx == geo.W) {
+                wx = 0;
+                if (++wy == geo.H) {
+                    wy = 0;
+                    ++wb;
+                }
+            }
+        } else if constexpr (CONV) {
             const int tap = kb / geo.cblocks, cb = kb - tap * geo.cblocks;
             const int ky = tap / 3, kx = tap - 3 * ky;
             tma_load_4d(a, &tmA, cb * BK, x0 + kx - 1, y0 + ky - 1, b0, &full[st]);
@@ -736,7 +783,7 @@ cudaError_t make_map_4d(CUtensorMap* tm, const void* ptr, int B, int H, int W, i
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN, bool OUT_BF16, int BK, bool CONV>
+template <int BN, bool OUT_BF16, int BK, bool CONV, bool WG = false>
 cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
                       int ldd, int relu, int splits, int kb_per_split, const ConvGeo& geo, const ShuffleGeo& sh,
                       cudaStream_t s)
@@ -744,14 +791,14 @@ cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const
     constexpr int smem = stages_for<BK, BN>() * (kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, OUT_BF16, BK, CONV>,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, OUT_BF16, BK, CONV, WG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, splits);
-    k_gemm<BN, OUT_BF16, BK, CONV><<<grid, kThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu, kb_per_split,
-                                                                geo, sh);
+    k_gemm<BN, OUT_BF16, BK, CONV, WG><<<grid, kThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu,
+                                                                    kb_per_split, geo, sh);
     return cudaGetLastError();
 }
 
@@ -891,6 +938,73 @@ cudaError_t gemm_bf16_tout(const void* A, int lda, const void* B, int ldb, float
     // writes the transpose
     e = dispatch<kBK, false>(bn, false, ta, tb, workspace, nullptr, M, N, K, N, 0, splits, kb_per_split, ConvGeo{},
                              ShuffleGeo{}, s);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)M * N;
+    k_split_reduce_t<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(workspace, splits, M, N, N, D, ldd);
+    return cudaGetLastError();
+}
+
+bool wgrad3_supported(int B, int H, int W, int C, int cout)
+{
+    const long long P = (long long)B * H * W;
+    return B >= 1 && H >= 1 && W >= 32 && W % 32 == 0 && C >= 32 && C % 32 == 0 && cout >= 8 && cout % 8 == 0 &&
+           P <= 0x7fffffffLL && 9LL * C <= 0x7fffffffLL;
+}
+
+cudaError_t wgrad3_bf16(const void* XT3, const void* dYT, int B, int H, int W, int C, int cout, float* D, int ldd,
+                        cudaStream_t s, int splits, float* workspace)
+{
+    if (!wgrad3_supported(B, H, W, C, cout) || !workspace) return cudaErrorInvalidValue;
+    if (((uintptr_t)XT3 | (uintptr_t)dYT | (uintptr_t)D) & 15) return cudaErrorInvalidValue;
+    const long long P = (long long)B * H * W;
+    const int M = 9 * C, N = cout, K = (int)P;
+    if (M > ldd) return cudaErrorInvalidValue;
+    const int bk = W % 64 == 0 ? 64 : 32;
+    // A rows per box: 128, 64 or 32, whichever is the largest to divide C, so
+    // that no box straddles two taps
+    const int rb = C % 128 == 0 ? 128 : C % 64 == 0 ? 64 : 32;
+    cudaError_t e = encoder();
+    if (e != cudaSuccess) return e;
+    CUtensorMap ta, tb;
+    {
+        cuuint64_t dims[4] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B, (cuuint64_t)(3 * C)};
+        cuuint64_t strides[3] = {(cuuint64_t)W * 2, (cuuint64_t)H * W * 2, (cuuint64_t)P * 2};
+        cuuint32_t box[4] = {(cuuint32_t)bk, 1, 1, (cuuint32_t)rb};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        CUresult r = g_encode(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(XT3), dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    const int bn = bn_for(N);
+    if ((e = make_map(&tb, dYT, N, K, K, bn, bk)) != cudaSuccess) return e;
+    const int nkb = K / bk;
+    if (splits < 1) splits = 1;
+    if (splits > nkb) splits = nkb;
+    const int kb_per_split = (nkb + splits - 1) / splits;
+    splits = (nkb + kb_per_split - 1) / kb_per_split;
+    ConvGeo geo;
+    geo.W = W;
+    geo.H = H;
+    geo.C = C;
+    geo.cblocks = rb;
+#define NN_WG_CASE(BNV)                                                                                        \
+    case BNV:                                                                                                  \
+        e = bk == 64 ? launch_bn<BNV, false, 64, false, true>(ta, tb, workspace, nullptr, M, N, K, N, 0, splits, \
+                                                              kb_per_split, geo, ShuffleGeo{}, s)              \
+                     : launch_bn<BNV, false, 32, false, true>(ta, tb, workspace, nullptr, M, N, K, N, 0, splits, \
+                                                              kb_per_split, geo, ShuffleGeo{}, s);             \
+        break;
+    switch (bn) {
+        NN_WG_CASE(32)
+        NN_WG_CASE(64)
+        NN_WG_CASE(128)
+        NN_WG_CASE(256)
+    default:
+        return cudaErrorInvalidValue;
+    }
+#undef NN_WG_CASE
     if (e != cudaSuccess) return e;
     const long long n = (long long)M * N;
     k_split_reduce_t<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(workspace, splits, M, N, N, D, ldd);

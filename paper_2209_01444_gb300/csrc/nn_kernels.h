@@ -36,6 +36,16 @@ bool conv3x3_supported(int B, int H, int W, int C);
 cudaError_t upconv2x2_bf16(const void* X, int lda, const void* Wm, int ldw, void* Y, int ypitch, int c0,
                            const float* bias, int B, int Hl, int Wl, int cin, int c, cudaStream_t s);
 
+// Weight gradient of a 3 x 3 convolution from three horizontally shifted
+// transposed copies of its input (XT3 [3 C][B H W], gatherT with taps 3) and
+// the transposed output gradient (dYT [cout][B H W]): D[cout][9 C] (pitch
+// ldd >= 9 C) = sum over pixels, the vertical taps taken by TMA coordinates.
+// Needs W % 32 == 0, C % 32 == 0, cout % 8 == 0 and a workspace of
+// splits x 9 C x cout floats.
+bool wgrad3_supported(int B, int H, int W, int C, int cout);
+cudaError_t wgrad3_bf16(const void* XT3, const void* dYT, int B, int H, int W, int C, int cout, float* D, int ldd,
+                        cudaStream_t s, int splits, float* workspace);
+
 // Read (and optionally clear) the flag a GEMM raises when a bounded wait ran out.
 cudaError_t gemm_error(int* flag, bool clear);
 // Bound of the GEMMs' waits for their operand tiles on the current device.

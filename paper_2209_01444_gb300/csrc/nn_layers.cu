@@ -72,7 +72,8 @@ __global__ void k_relu_bwd(G* __restrict__ g, int gpitch, const bf16* __restrict
 
 // Transposed gather for weight gradients:
 //   AT[t * C + c][p] = X[pixel p shifted by tap t][c]   (zero outside)
-// with taps 9 (the 3 x 3 neighbourhood, t = ky * 3 + kx) or 1 (no shift: a
+// with taps 9 (the 3 x 3 neighbourhood, t = ky * 3 + kx), 3 (the middle row
+// of it, dy = 0 and dx = -1, 0, 1: tap rows kx * C + c) or 1 (no shift: a
 // plain transpose of [P][C] with pitch).  One CTA moves a 64-pixel x
 // 64-channel block through shared memory: 16-byte reads along channels (8
 // threads per pixel row), then each thread takes a pair of channels for 8
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(256) k_gatherT(const bf16* __restrict__ X, int
     const int p0 = blockIdx.x * 64;
     const int cblk = blockIdx.y;                 // 64-channel block within (tap, channel)
     const int cpb = (C + 63) / 64;                // channel blocks per tap
-    const int t = taps == 9 ? cblk / cpb : 4;     // tap 4 is the centre
+    const int t = taps == 9 ? cblk / cpb : taps == 3 ? 3 + cblk / cpb : 4;  // taps 3-5: the middle row; 4: centre
     const int c0 = (cblk % cpb) * 64;
     const int dy = t / 3 - 1, dx = t % 3 - 1;
     if (threadIdx.x < 64) {
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(256) k_gatherT(const bf16* __restrict__ X, int
     hi.y = __byte_perm(w[2], w[3], 0x7632);
     hi.z = __byte_perm(w[4], w[5], 0x7632);
     hi.w = __byte_perm(w[6], w[7], 0x7632);
-    const long long row = (long long)(taps == 9 ? t * C + c : c);
+    const long long row = (long long)(taps == 1 ? c : (cblk / cpb) * C + c);
     *(uint4*)(AT + row * atpitch + p) = lo;
     *(uint4*)(AT + (row + 1) * atpitch + p) = hi;
 }
@@ -762,7 +763,8 @@ cudaError_t gatherT(const void* X, int B, int H, int W, int C, int cpitch, int t
                     cudaStream_t s)
 {
     const long long P = (long long)B * H * W;
-    if ((taps != 9 && taps != 1) || C % 8 || cpitch % 8 || atpitch % 8 || P % 8) return cudaErrorInvalidValue;
+    if ((taps != 9 && taps != 3 && taps != 1) || C % 8 || cpitch % 8 || atpitch % 8 || P % 8)
+        return cudaErrorInvalidValue;
     if (P > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (((uintptr_t)X | (uintptr_t)AT) & 15) return cudaErrorInvalidValue;
     const long long cblocks = (long long)((C + 63) / 64) * taps;

@@ -123,6 +123,8 @@ SIGNATURES = {
                                    ct.c_void_p]),
     "lbm_nn_flip3x3": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "lbm_nn_gather_t": (ct.c_int, [ct.c_void_p] + [ct.c_int] * 6 + [ct.c_void_p, ct.c_longlong, ct.c_void_p]),
+    "lbm_nn_wgrad3x3": (ct.c_int, [ct.c_void_p, ct.c_void_p] + [ct.c_int] * 5 + [ct.c_void_p, ct.c_int, ct.c_int,
+                                                                                ct.c_void_p, ct.c_void_p]),
     "lbm_nn_conv3x3": (ct.c_int, [ct.c_void_p] + [ct.c_int] * 5 + [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int,
                                                                     ct.c_void_p, ct.c_int, ct.c_int, ct.c_int,
                                                                     ct.c_void_p]),

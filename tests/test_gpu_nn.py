@@ -350,7 +350,8 @@ def test_upconv2x2_shuffle_epilogue(env, B, Hl, Wl, cin, c):
 
 
 @pytest.mark.parametrize("B,H,W,C,cp,taps", [(2, 4, 7, 16, 24, 9), (1, 16, 16, 8, 32, 9), (3, 8, 8, 72, 80, 9),
-                                            (2, 6, 10, 40, 48, 1), (1, 1, 1000, 200, 200, 1)])
+                                            (2, 6, 10, 40, 48, 1), (1, 1, 1000, 200, 200, 1),
+                                            (2, 5, 32, 96, 104, 3), (1, 3, 8, 8, 8, 3)])
 def test_gather_transposed_exact(env, B, H, W, C, cp, taps):
     torch, lib = env
     g = torch.Generator(device="cuda").manual_seed(B * H * W + C)
@@ -364,7 +365,62 @@ def test_gather_transposed_exact(env, B, H, W, C, cp, taps):
         Xp = torch.nn.functional.pad(X[..., :C].float(), (0, 0, 1, 1, 1, 1))
         ref = torch.stack([Xp[:, ky:ky + H, kx:kx + W, :] for ky in range(3) for kx in range(3)], dim=3)
         ref = ref.reshape(P, 9 * C).T
+    elif taps == 3:  # the middle row of the nine taps: dy = 0, dx = -1, 0, 1
+        Xp = torch.nn.functional.pad(X[..., :C].float(), (0, 0, 1, 1))
+        ref = torch.stack([Xp[:, :, kx:kx + W, :] for kx in range(3)], dim=3).reshape(P, 3 * C).T
     else:
         ref = X[..., :C].float().reshape(P, C).T
     assert torch.equal(AT[:, :P].float(), ref)
     assert bool((AT[:, P:] == 9.0).all())
+
+
+def _wgrad_reference(X, dY):
+    """dW[n][t*C + c] = sum over pixels of X shifted by tap t (zero padded) times
+    dY, t = ky*3 + kx, in FP64 on the host."""
+    B, H, W, C = X.shape
+    Xp = np.pad(X.astype(np.float64), ((0, 0), (1, 1), (1, 1), (0, 0)))
+    taps = np.stack([Xp[:, ky:ky + H, kx:kx + W, :] for ky in range(3) for kx in range(3)], axis=3)
+    return dY.reshape(-1, dY.shape[-1]).astype(np.float64).T @ taps.reshape(-1, 9 * C)
+
+
+@pytest.mark.parametrize("B,H,W,C,cout,splits", [
+    (2, 8, 64, 32, 32, 1),      # 64-pixel K blocks, one box of 32 rows per tap, no split
+    (2, 8, 64, 64, 48, 3),      # 64-row boxes, cout not a multiple of the N tile
+    (1, 5, 32, 96, 64, 4),      # 32-pixel K blocks, 9C = 864 (a ragged last M tile), odd H
+    (3, 4, 32, 128, 32, 7),     # 128-row boxes, more splits than fit evenly
+    (1, 2, 96, 160, 16, 2),     # C = 160: 32-row boxes; W = 96: 32-pixel K blocks
+])
+def test_wgrad_from_three_copies_matches_the_nine_tap_sum(env, B, H, W, C, cout, splits):
+    """The weight gradient from three horizontally shifted copies, the vertical
+    taps taken by TMA coordinates with zero fill at the top and bottom image
+    rows, against the plain nine-tap sum in FP64 (same BF16 inputs)."""
+    torch, lib = env
+    g = torch.Generator(device="cuda").manual_seed(B * 1000 + H * 100 + W + C + cout)
+    X = torch.randn(B, H, W, C, generator=g, device="cuda").to(torch.bfloat16)
+    dY = torch.randn(B, H, W, cout, generator=g, device="cuda").to(torch.bfloat16)
+    P = B * H * W
+    XT3 = torch.full((3 * C, P), 7.0, dtype=torch.bfloat16, device="cuda")
+    assert lib.lbm_nn_gather_t(_p(X), B, H, W, C, C, 3, _p(XT3), P, _stream(torch)) == 0
+    dYT = dY.reshape(P, cout).T.contiguous()
+    ldd = 9 * C + 8
+    D = torch.full((cout, ldd), 5.0, dtype=torch.float32, device="cuda")
+    ws = torch.empty(splits * 9 * C * cout, dtype=torch.float32, device="cuda")
+    rc = lib.lbm_nn_wgrad3x3(_p(XT3), _p(dYT), B, H, W, C, cout, _p(D), ldd, splits, _p(ws), _stream(torch))
+    assert rc == 0, lib.lbm_last_error(None)
+    torch.cuda.synchronize()
+    assert lib.lbm_nn_error(1) == 0
+    ref = _wgrad_reference(X.float().cpu().numpy(), dY.float().cpu().numpy())
+    got = D[:, :9 * C].double().cpu().numpy()
+    # FP32 accumulation of P products of BF16-exact values
+    assert np.abs(got - ref).max() <= 4e-6 * np.sqrt(P) * np.abs(ref).max()
+    assert bool((D[:, 9 * C:] == 5.0).all())
+
+
+def test_wgrad_from_three_copies_rejects_unsupported_shapes(env):
+    torch, lib = env
+    buf = torch.zeros(1 << 16, dtype=torch.float32, device="cuda")
+    for (B, H, W, C, cout) in ((1, 4, 48, 32, 32), (1, 4, 64, 40, 32), (1, 4, 64, 32, 12), (1, 4, 16, 32, 32)):
+        rc = lib.lbm_nn_wgrad3x3(_p(buf), _p(buf), B, H, W, C, cout, _p(buf), 9 * C, 1, _p(buf), _stream(torch))
+        assert rc == -1, (B, H, W, C, cout)
+    assert lib.lbm_nn_wgrad3x3(_p(buf), _p(buf), 1, 4, 64, 32, 32, _p(buf), 9 * 32 - 8, 1, _p(buf),
+                               _stream(torch)) == -1

@@ -155,6 +155,25 @@ def test_gradients_match_oracle(env, levels, B, H, tol):
             assert rel <= tol, (name, rel)
 
 
+@pytest.mark.parametrize("levels,B,H,active,tol", [(2, 2, 64, False, 2e-2), (3, 1, 128, True, 1.5e-2)])
+def test_gradients_with_the_three_copy_weight_gradient_match_oracle(env, levels, B, H, active, tol):
+    """Image widths of 32 to 128 and channel counts of 32 to 256, so that
+    every convolution with a multiple of 32 input channels takes its weight
+    gradient from three shifted copies of its input (boxes of 32, 64 and 128
+    rows, 32- and 64-pixel K blocks): every parameter gradient against the
+    oracle with the same rounding points."""
+    torch, lib, S = env
+    err = _grad_errors(S, torch, levels, B, H, 50 + levels, active=active)
+    assert lib.lbm_nn_error(1) == 0
+    worst = max(v[0] for k, v in err.items() if not k[0])
+    print(f"levels {levels}, {H} x {H}: worst per-tensor relative L2 error {worst:.3e} (same rounding points)")
+    for (pure, name), (rel, cos) in err.items():
+        if pure:
+            assert cos >= 0.98, (name, cos)
+        else:
+            assert rel <= tol, (name, rel)
+
+
 @pytest.mark.parametrize("seed", [31, 32])
 def test_gradients_five_levels_all_units_active(env, seed):
     """The full five-level network with every ReLU active: each gradient
