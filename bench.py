@@ -534,7 +534,7 @@ def surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, train_steps: int 
     net.set_norm(mean, std_in, std_out)
     torch.cuda.synchronize()
     ev0.record(stream)
-    hist = S.train_rollout(net, snaps, steps=train_steps, lr=lr, seed=1, log_every=max(1, train_steps // 10),
+    hist = S.train_rollout(net, snaps, steps=train_steps, lr=lr, seed=1, log_every=max(1, train_steps // 100),
                            pushforward=pushforward)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -616,7 +616,12 @@ def surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, train_steps: int 
                              f"{data_windows} windows from the seed",
                      "pairs": int(data_windows * len(cases)), "data_s": t_data, "steps": train_steps, "batch": batch,
                      "pushforward": pushforward, "lr": lr, "ms": train_ms,
-                     "loss_first_last": [hist[0][1], hist[-1][1]]},
+                     "loss_first": hist[0][1],
+                     # mean of the sampled mini-batch losses in each tenth of training (single losses vary
+                     # with the share of push-forward samples, whose targets lie two windows ahead)
+                     "loss_by_tenth": [float(np.mean([l for (i, l) in hist if k * train_steps <= 10 * i
+                                                      < (k + 1) * train_steps] or [float("nan")]))
+                                       for k in range(10)]},
     }
 
 
@@ -714,9 +719,14 @@ def main():
     rc = e2e_sim.lib.lbm_load_state(e2e_sim.h, ct.c_void_p(pinned.data_ptr()), len(blob))
     if rc:
         raise RuntimeError(e2e_sim.lib.lbm_last_error(e2e_sim.h).decode())
+    t_load = time.perf_counter()
     e2e_sim.step(e2e_steps)
+    e2e_sim.synchronize()
+    t_steps = time.perf_counter()
     out = e2e_sim.fields(names)
     t1 = time.perf_counter()
+    e2e_phases = {"load_state": (t_load - t0) * 1e3, "steps": (t_steps - t_load) * 1e3,
+                  "get_fields": (t1 - t_steps) * 1e3}
     barrier_()
     e2e_s = max_ranks(t1 - t0)
     e2e_value = whole_job_mlups(world, nodes, e2e_steps, e2e_s * 1e3)
@@ -791,7 +801,8 @@ def main():
                      "kernel_ms": k_avg_ms, "peak_kind": peak_kind},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(blob) / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps,
-                "what": "lbm_load_state from pinned host memory, lbm_step(steps), lbm_get_fields of 5 fields"},
+                "what": "lbm_load_state from pinned host memory, lbm_step(steps), lbm_get_fields of 5 fields",
+                "phases_ms": e2e_phases},
         "gpu_launches": args.steps * (1 + wall_launches),
         "conservation": conservation,
         "clocks": clk,
