@@ -175,6 +175,51 @@ def test_smallest_and_block_edge_grids_match_the_oracle(lbm, shape, bcs):
     cp.check()
 
 
+def test_tallest_grid_matches_the_oracle(lbm):
+    """The tallest grid the library accepts (ny = 262140: the launches of
+    64 x 4-node blocks reach the 65535 limit of the grid's y dimension),
+    about a million nodes: random fields against the oracle over three steps."""
+    nx, ny = 4, 262140
+    p = W.thermosolutal_params(nx, ny, bc=BCS["channel_noslip"], u_in=(0.15, 0.02), gbetaT=W.GBETA_T * 5,
+                               gbetaC=W.GBETA_C * 5, theta_ref=-0.5, dir_theta=-0.4)
+    f, orient = W.random_fields(nx, ny, rng_seed=7)
+    g, o = pair(lbm, p)
+    g.init_fields(f, orient)
+    o.init_fields(f, orient)
+    cp = Checkpoints()
+    for T in (1, 3):
+        g.step(T - g.steps)
+        o.step(T - o.steps)
+        cp.add(g.fields(), o.fields(), FP32_TOL, 0.5, f"(4, 262140) step {T}")
+    cp.check()
+
+
+def test_widest_tested_grid_matches_the_oracle(lbm):
+    """A strip 65543 nodes wide and 16 high (2049 node blocks per row, the
+    last holding 7 nodes; about a million nodes) with inflow, outflow and
+    no-slip walls, 40 seeds of radius 3-5 along it: against the oracle over
+    three steps.  (Random fields, whose phi jumps between -1 and +1 from one
+    row to the next, are not used on such strips: there the gradient of a flat
+    wall row lies within FP32 rounding of the degenerate threshold at some
+    nodes, and the jump of a_s it switches is pushed into the one-node spike
+    next to it, an O(1e-2) difference between two admissible results.)"""
+    nx, ny = 65543, 16
+    p = W.thermosolutal_params(nx, ny, bc=BCS["mixed"], u_in=(0.05, 0.0), gbetaT=W.GBETA_T * 5,
+                               gbetaC=W.GBETA_C * 5)
+    r = np.random.Generator(np.random.PCG64(21))
+    seeds = np.stack([np.linspace(800.0, nx - 800.0, 40), r.uniform(6.0, 9.0, 40), r.uniform(3.0, 5.0, 40),
+                      r.uniform(0.0, math.pi / 4, 40)], axis=1)
+    g, o = pair(lbm, p)
+    g.init_seeds(seeds, -0.2, -0.45)
+    o.init_seeds(seeds, -0.2, -0.45)
+    cp = Checkpoints()
+    for T in (1, 3):
+        g.step(T - g.steps)
+        o.step(T - o.steps)
+        cp.add(g.fields(), o.fields(), FP32_TOL, 0.45, f"(65543, 16) step {T}")
+    cp.check()
+
+
 def _uniform(nx, ny, phi, U, theta, ux=0.0, uy=0.0):
     f = np.zeros((6, ny, nx))
     f[0], f[1], f[2], f[3], f[4] = phi, U, theta, ux, uy
