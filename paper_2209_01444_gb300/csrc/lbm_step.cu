@@ -46,7 +46,8 @@ __device__ __forceinline__ int mirror_or_wrap_local(int g, int n, int periodic, 
 #endif
 
 #ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for (64 registers)
+#define LBM_STEP_MIN_BLOCKS 9  // resident CTAs of 128 threads per SM the register budget is sized for
+                               // (56 registers; 36 warps hide more of the memory latency than 32)
 #endif
 
 // Non-equilibrium extrapolation (Guo et al.) on one side pair, applied to the
