@@ -51,21 +51,23 @@ __global__ void k_seed_fields(const StepParams P, const double* __restrict__ see
     if (x >= P.nx || y >= y0 + rows || y >= P.ny) return;
     const long long o = (long long)y * P.pitch + x;
     const long long ob = (long long)(y - y0) * P.pitch + x, bp = (long long)rows * P.pitch;
-    double best_phi = -2.0, best_d2 = 1e300;
+    // phi is the largest of the seeds' profiles; tanh increases, so that is
+    // the profile of the largest argument: one tanh per node (ns >= 1)
+    double best_arg = -1e300, best_d2 = 1e300;
     int best = 0;
     const double inv = 1.0 / (sqrt(2.0) * W);
     for (int j = 0; j < ns; ++j) {
         const double dx = min_image(x - seeds[4 * j + 0], P.nx, P.periodic_x);
         const double dy = min_image(y - seeds[4 * j + 1], P.ny, P.periodic_y);
         const double d2 = dx * dx + dy * dy;
-        const double ph = tanh((seeds[4 * j + 2] - sqrt(d2)) * inv);
-        if (ph > best_phi) best_phi = ph;
+        const double a = (seeds[4 * j + 2] - sqrt(d2)) * inv;
+        if (a > best_arg) best_arg = a;
         if (d2 < best_d2) {
             best_d2 = d2;
             best = j;
         }
     }
-    fields[0 * bp + ob] = best_phi;
+    fields[0 * bp + ob] = tanh(best_arg);
     fields[1 * bp + ob] = U0;
     fields[2 * bp + ob] = theta0;
     fields[3 * bp + ob] = 0.0;
