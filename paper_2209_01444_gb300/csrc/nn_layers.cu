@@ -447,12 +447,14 @@ __global__ void __launch_bounds__(256) k_proj_bwd_w_warps(const float* __restric
 // kernel rotated by 180 degrees, input and output channels swapped).
 __global__ void k_flip3x3(const bf16* __restrict__ W, int cout, int cin, bf16* __restrict__ Wf)
 {
+    // one thread per output element, so that the writes are contiguous; the
+    // scattered reads come from a kernel small enough to stay in L2
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)cout * 9 * cin) return;
-    const int ci = (int)(i % cin);
-    const long long r = i / cin;
-    const int t = (int)(r % 9), co = (int)(r / 9);
-    Wf[((long long)ci * 9 + (8 - t)) * cout + co] = W[i];
+    const int co = (int)(i % cout);
+    const long long r = i / cout;
+    const int tf = (int)(r % 9), ci = (int)(r / 9);
+    Wf[i] = W[((long long)co * 9 + (8 - tf)) * cin + ci];
 }
 
 // Wp[co][t * cin_pad + ci] = W[co][t * cin + ci] for ci < cin, else 0: the
@@ -496,6 +498,43 @@ __global__ void k_colsum_part(const G* __restrict__ g, long long rows, int C, in
     }
 }
 
+// The same partial sums for a BF16 matrix with C and the pitch multiples of 8
+// and at most 1024 columns: each thread adds 8 columns of a row from one
+// 16-byte load; the block's 128 threads are 128 / G row lanes of G = C / 8
+// column groups, whose lanes are then added in shared memory in a fixed order.
+__global__ void k_colsum_part8(const bf16* __restrict__ g, long long rows, int C, int pitch, int chunk,
+                               float* __restrict__ part)
+{
+    __shared__ float sm[128][8];
+    const int G = C >> 3;
+    const int lanes = 128 / G;
+    const int cg = threadIdx.x % G, rl = threadIdx.x / G;
+    const long long r0 = (long long)blockIdx.x * chunk;
+    const long long r1 = r0 + chunk < rows ? r0 + chunk : rows;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (rl < lanes)
+        for (long long r = r0 + rl; r < r1; r += lanes) {
+            const uint4 v = *(const uint4*)(g + r * pitch + 8 * cg);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc[2 * k] += __uint_as_float(w[k] << 16);
+                acc[2 * k + 1] += __uint_as_float(w[k] & 0xffff0000u);
+            }
+        }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sm[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < G) {
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int l = 0; l < lanes; ++l)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] += sm[l * G + threadIdx.x][k];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) part[(long long)blockIdx.x * C + 8 * threadIdx.x + k] = v[k];
+    }
+}
+
 // dW[o][c] and db[o] from the nb partial rows of O x (C + 1) slots (fixed order).
 __global__ void k_proj_sum(const float* __restrict__ part, int nb, int O, int C, float* __restrict__ dW,
                            float* __restrict__ db)
@@ -525,6 +564,23 @@ __global__ void k_sum_parts(const float* __restrict__ part, int nb, int slots, f
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
     if (lane == 0) out[s] = acc;
+}
+
+// out[0] = the sum of part[0 .. nb): 1024 threads add strided subsets, then a
+// shared-memory tree adds the threads (a fixed order, so the result is
+// reproducible).
+__global__ void __launch_bounds__(1024) k_sum_one(const float* __restrict__ part, int nb, float* __restrict__ out)
+{
+    __shared__ float sm[1024];
+    float acc = 0.0f;
+    for (int b = threadIdx.x; b < nb; b += 1024) acc += part[b];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 512; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sm[0];
 }
 
 // Weighted squared error: d[i] = pred - target, weight w = 1 + alpha max(0,
@@ -806,12 +862,22 @@ cudaError_t flip3x3(const void* W, int cout, int cin, void* Wf, cudaStream_t s)
 cudaError_t colsum(const void* g, bool g_fp32, long long rows, int C, int pitch, float* out, float* part,
                    int part_blocks, cudaStream_t s)
 {
-    const int chunk = (int)((rows + part_blocks - 1) / part_blocks);
+    if (rows < 1 || C < 1 || part_blocks < 1) return cudaErrorInvalidValue;
+    // at most part_blocks partial rows; a block's rows are split among its
+    // row lanes, and a block takes about 32 rows per lane (fewer, longer blocks
+    // for short matrices: less to add afterwards, without starving the grid)
+    const bool vec = !g_fp32 && C % 8 == 0 && pitch % 8 == 0 && C <= 1024 && ((uintptr_t)g & 15) == 0;
+    const int G = vec ? C / 8 : (C < 128 ? C : 128);
+    const long long lanes = G < 128 ? 128 / G : 1;
+    long long chunk = (rows + part_blocks - 1) / part_blocks;
+    if (chunk < 32 * lanes) chunk = 32 * lanes;
     const int nb = (int)((rows + chunk - 1) / chunk);
     if (g_fp32)
-        k_colsum_part<float><<<nb, 128, 0, s>>>((const float*)g, rows, C, pitch, chunk, part);
+        k_colsum_part<float><<<nb, 128, 0, s>>>((const float*)g, rows, C, pitch, (int)chunk, part);
+    else if (vec)
+        k_colsum_part8<<<nb, 128, 0, s>>>((const bf16*)g, rows, C, pitch, (int)chunk, part);
     else
-        k_colsum_part<bf16><<<nb, 128, 0, s>>>((const bf16*)g, rows, C, pitch, chunk, part);
+        k_colsum_part<bf16><<<nb, 128, 0, s>>>((const bf16*)g, rows, C, pitch, (int)chunk, part);
     k_sum_parts<<<(unsigned)((C + 7) / 8), 256, 0, s>>>(part, nb, C, out);
     return cudaGetLastError();
 }
@@ -821,7 +887,7 @@ cudaError_t mse(const float* pred, const float* target, long long n, float* grad
 {
     const int nb = (int)((n + 255) / 256);
     k_mse<<<nb, 256, 0, s>>>(pred, target, n, x, F, alpha, grad, part);
-    k_sum_parts<<<1, 32, 0, s>>>(part, nb, 1, loss);
+    k_sum_one<<<1, 1024, 0, s>>>(part, nb, loss);
     return cudaGetLastError();
 }
 
