@@ -442,6 +442,86 @@ __global__ void __launch_bounds__(256) k_proj_bwd_w_warps(const float* __restric
     }
 }
 
+// dX[p][c] = sum_o dY[p][o] Wt[o][c] for C a multiple of 4: threadIdx.x takes
+// four channels, threadIdx.y a pixel, so that every store is 16 bytes and no
+// thread divides.
+__global__ void k_proj_bwd_x4(const float* __restrict__ dY, int P, int O, const float* __restrict__ Wt, int C,
+                              float* __restrict__ dX, int dpitch)
+{
+    const int c = 4 * threadIdx.x;
+    const long long p = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    if (p >= P) return;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int o = 0; o < O; ++o) {
+        const float d = dY[p * O + o];
+        const float4 w = *(const float4*)(Wt + o * C + c);
+        acc.x += d * w.x;
+        acc.y += d * w.y;
+        acc.z += d * w.z;
+        acc.w += d * w.w;
+    }
+    *(float4*)(dX + p * dpitch + c) = acc;
+}
+
+// Per-block partial sums of dW[o][c] = sum_p dY[p][o] X[p][c] and db[o] =
+// sum_p dY[p][o] for C = 8 G with G in {1, 2, 4, 8}: thread t adds channels
+// 8 (t % G) .. + 7 of every (256 / G)-th pixel of the block's chunk from one
+// 16-byte load; the threads of one channel group are added by shuffles within
+// each warp and then over the warps through shared memory, in a fixed order.
+template <int O>
+__global__ void __launch_bounds__(256) k_proj_bwd_w8(const float* __restrict__ dY, const bf16* __restrict__ X, int P,
+                                                     int C, int xpitch, int chunk, float* __restrict__ part)
+{
+    __shared__ float sm[8][8][O * 9];  // [warp][group][o * 9 + k], k = 8: the bias
+    const int G = C >> 3, lanes = 256 / G;
+    const int cg = threadIdx.x % G, pl = threadIdx.x / G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p0 = blockIdx.x * chunk, p1 = min(P, p0 + chunk);
+    float acc[O][9];
+#pragma unroll
+    for (int o = 0; o < O; ++o)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[o][k] = 0.0f;
+    for (int p = p0 + pl; p < p1; p += lanes) {
+        const uint4 v = *(const uint4*)(X + (long long)p * xpitch + 8 * cg);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            x[2 * k] = __uint_as_float(w[k] << 16);
+            x[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+#pragma unroll
+        for (int o = 0; o < O; ++o) {
+            const float d = dY[(long long)p * O + o];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[o][k] += d * x[k];
+            acc[o][8] += d;
+        }
+    }
+    // lanes with the same group differ in the bits above log2(G)
+#pragma unroll
+    for (int o = 0; o < O; ++o)
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            for (int off = G; off < 32; off <<= 1) acc[o][k] += __shfl_xor_sync(0xffffffffu, acc[o][k], off);
+    if (lane < G)
+#pragma unroll
+        for (int o = 0; o < O; ++o)
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sm[warp][lane][o * 9 + k] = acc[o][k];
+    __syncthreads();
+    const int slots = O * (C + 1);
+    for (int s = threadIdx.x; s < slots; s += 256) {
+        const int o = s / (C + 1), c = s - o * (C + 1);
+        // the bias (c == C) is the same sum in every group: take group 0's
+        const int g = c < C ? c >> 3 : 0, k = c < C ? c & 7 : 8;
+        float v = 0.0f;
+        for (int w = 0; w < 8; ++w) v += sm[w][g][o * 9 + k];
+        part[(long long)blockIdx.x * slots + s] = v;
+    }
+}
+
 // Weights of the transposed 3 x 3 convolution that carries the gradient back
 // to the input: Wf[ci][t * cout + co] = W[co][(8 - t) * cin + ci] (the
 // kernel rotated by 180 degrees, input and output channels swapped).
@@ -535,15 +615,20 @@ __global__ void k_colsum_part8(const bf16* __restrict__ g, long long rows, int C
     }
 }
 
-// dW[o][c] and db[o] from the nb partial rows of O x (C + 1) slots (fixed order).
+// dW[o][c] and db[o] from the nb partial rows of O x (C + 1) slots: one warp
+// per slot, lanes over the partial rows, a shuffle tree (a fixed order).
 __global__ void k_proj_sum(const float* __restrict__ part, int nb, int O, int C, float* __restrict__ dW,
                            float* __restrict__ db)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     const int slots = O * (C + 1);
     if (s >= slots) return;
     float acc = 0.0f;
-    for (int b = 0; b < nb; ++b) acc += part[(long long)b * slots + s];
+    for (int b = lane; b < nb; b += 32) acc += part[(long long)b * slots + s];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+    if (lane) return;
     const int o = s / (C + 1), c = s % (C + 1);
     if (c < C)
         dW[o * C + c] = acc;
@@ -804,14 +889,41 @@ cudaError_t proj_fwd(const void* X, int P, int C, int xpitch, const float* Wt, c
 cudaError_t proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, const float* Wt, int O, float* dX,
                      int dpitch, float* dW, float* db, float* part, int part_blocks, cudaStream_t s)
 {
-    if (dX) k_proj_bwd_x<<<blocks((long long)P * C), 256, 0, s>>>(dY, P, O, Wt, C, dX, dpitch);
+    if (dX) {
+        const bool vec = C % 4 == 0 && C / 4 <= 256 && dpitch % 4 == 0 &&
+                         (((uintptr_t)dX | (uintptr_t)Wt) & 15) == 0;
+        if (vec) {
+            const dim3 b(C / 4, 256 / (C / 4));
+            k_proj_bwd_x4<<<(unsigned)((P + b.y - 1) / b.y), b, 0, s>>>(dY, P, O, Wt, C, dX, dpitch);
+        } else {
+            k_proj_bwd_x<<<blocks((long long)P * C), 256, 0, s>>>(dY, P, O, Wt, C, dX, dpitch);
+        }
+    }
     const int chunk = (P + part_blocks - 1) / part_blocks;
     const int nb = (P + chunk - 1) / chunk;
-    if (C <= 64 && O <= 8)
+    const bool vec = (C == 8 || C == 16 || C == 32 || C == 64) && O >= 1 && O <= 8 && xpitch % 8 == 0 &&
+                     ((uintptr_t)X & 15) == 0;
+    if (vec) {
+        switch (O) {
+#define NN_PROJ_W8(OV) \
+    case OV: k_proj_bwd_w8<OV><<<nb, 256, 0, s>>>(dY, (const bf16*)X, P, C, xpitch, chunk, part); break;
+            NN_PROJ_W8(1)
+            NN_PROJ_W8(2)
+            NN_PROJ_W8(3)
+            NN_PROJ_W8(4)
+            NN_PROJ_W8(5)
+            NN_PROJ_W8(6)
+            NN_PROJ_W8(7)
+            NN_PROJ_W8(8)
+#undef NN_PROJ_W8
+        }
+    } else if (C <= 64 && O <= 8) {
         k_proj_bwd_w_warps<<<nb, 256, 0, s>>>(dY, (const bf16*)X, P, C, xpitch, O, chunk, part);
-    else
+    } else {
         k_proj_bwd_w<<<nb, 128, 0, s>>>(dY, (const bf16*)X, P, C, xpitch, O, chunk, part);
-    k_proj_sum<<<blocks(O * (C + 1)), 256, 0, s>>>(part, nb, O, C, dW, db);
+    }
+    const int slots = O * (C + 1);
+    k_proj_sum<<<(unsigned)((slots + 7) / 8), 256, 0, s>>>(part, nb, O, C, dW, db);
     return cudaGetLastError();
 }
 

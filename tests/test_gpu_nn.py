@@ -214,8 +214,14 @@ def test_reductions_projection_and_adam(env):
     torch.cuda.synchronize()
     ref = G[:, :C].double().sum(0)
     assert float((out.double() - ref).abs().max()) <= 1e-4 * float(G[:, :C].abs().sum(0).max())
-    # projection with residual, and its backward
-    P, Cx, O = 3000, 32, 5
+    # projection with residual, and its backward (C = 32: the vector kernels;
+    # C = 20: the scalar ones)
+    for P, Cx, O in ((3000, 32, 5), (1001, 20, 3)):
+        _check_projection(torch, lib, g, s, part, P, Cx, O)
+    _check_mse_and_adam(torch, lib, g, s, part)
+
+
+def _check_projection(torch, lib, g, s, part, P, Cx, O):
     X = _bf(torch, (P, Cx), g)
     Wt = torch.randn(O, Cx, generator=g, device="cuda")
     b = torch.randn(O, generator=g, device="cuda")
@@ -235,6 +241,9 @@ def test_reductions_projection_and_adam(env):
     refW = dY.double().T @ X.double()
     assert float((dW.double() - refW).abs().max()) <= 1e-5 * float(refW.abs().max()) * 10
     assert float((db.double() - dY.double().sum(0)).abs().max()) <= 1e-3
+
+
+def _check_mse_and_adam(torch, lib, g, s, part):
     # mean squared error
     n = 100_003
     pr, tg = torch.randn(n, generator=g, device="cuda"), torch.randn(n, generator=g, device="cuda")
