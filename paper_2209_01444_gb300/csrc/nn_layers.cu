@@ -261,6 +261,61 @@ __global__ void k_maxpool_bwd(const bf16* __restrict__ X, int B, int H, int W, i
     for (int k = 0; k < 4; ++k) dX[off[k] * dpitch + c] += (k == arg) ? g : 0.0f;
 }
 
+// The same for C and xpitch multiples of 8 and dpitch a multiple of 4:
+// threadIdx.x takes 8 channels of the output pixel blockIdx.x * blockDim.y +
+// threadIdx.y, reading each window position's 8 inputs in one 16-byte load and
+// adding the gradient to its 8 dX values with two 16-byte read-modify-writes
+// (each input position belongs to one window, so no two threads meet).
+__global__ void k_maxpool_bwd8(const bf16* __restrict__ X, int B, int H, int W, int C, int xpitch,
+                               const float* __restrict__ dY, float* __restrict__ dX, int dpitch)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const int c = 8 * threadIdx.x;
+    const long long p = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    if (p >= (long long)B * Ho * Wo) return;
+    const int x = (int)(p % Wo);
+    const long long r = p / Wo;
+    const int y = (int)(r % Ho), b = (int)(r / Ho);
+    float v[4][8];
+    long long off[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        off[k] = ((long long)b * H + 2 * y + k / 2) * W + 2 * x + k % 2;
+        const uint4 q = *(const uint4*)(X + off[k] * xpitch + c);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[k][2 * j] = __uint_as_float(w[j] << 16);
+            v[k][2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+        }
+    }
+    const float4 g0 = *(const float4*)(dY + p * C + c), g1 = *(const float4*)(dY + p * C + c + 4);
+    const float g[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+    int arg[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        arg[j] = 0;
+#pragma unroll
+        for (int k = 1; k < 4; ++k)
+            if (v[k][j] > v[arg[j]][j]) arg[j] = k;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float4* d = (float4*)(dX + off[k] * dpitch + c);
+        float4 a = d[0], e = d[1];
+        a.x += arg[0] == k ? g[0] : 0.0f;
+        a.y += arg[1] == k ? g[1] : 0.0f;
+        a.z += arg[2] == k ? g[2] : 0.0f;
+        a.w += arg[3] == k ? g[3] : 0.0f;
+        e.x += arg[4] == k ? g[4] : 0.0f;
+        e.y += arg[5] == k ? g[5] : 0.0f;
+        e.z += arg[6] == k ? g[6] : 0.0f;
+        e.w += arg[7] == k ? g[7] : 0.0f;
+        d[0] = a;
+        d[1] = e;
+    }
+}
+
 // U[(b, y, x)][(dy, dx, c)] (2 x 2 up-convolution output) -> Y[b, 2y + dy, 2x + dx, c0 + c].
 __global__ void k_shuffle_fwd(const bf16* __restrict__ U, int B, int H, int W, int C, bf16* __restrict__ Y,
                               int ypitch, int c0)
@@ -840,8 +895,16 @@ cudaError_t maxpool_fwd(const void* X, int B, int H, int W, int C, int xpitch, v
 cudaError_t maxpool_bwd(const void* X, int B, int H, int W, int C, int xpitch, const float* dY, float* dX, int dpitch,
                         cudaStream_t s)
 {
-    k_maxpool_bwd<<<blocks((long long)B * (H / 2) * (W / 2) * C), 256, 0, s>>>((const bf16*)X, B, H, W, C, xpitch, dY,
-                                                                             dX, dpitch);
+    const long long Po = (long long)B * (H / 2) * (W / 2);
+    const bool vec = C % 8 == 0 && C / 8 <= 256 && xpitch % 8 == 0 && dpitch % 4 == 0 &&
+                     (((uintptr_t)X | (uintptr_t)dY | (uintptr_t)dX) & 15) == 0;
+    if (vec) {
+        const dim3 b(C / 8, 256 / (C / 8));
+        k_maxpool_bwd8<<<(unsigned)((Po + b.y - 1) / b.y), b, 0, s>>>((const bf16*)X, B, H, W, C, xpitch, dY, dX,
+                                                                         dpitch);
+    } else {
+        k_maxpool_bwd<<<blocks(Po * C), 256, 0, s>>>((const bf16*)X, B, H, W, C, xpitch, dY, dX, dpitch);
+    }
     return cudaGetLastError();
 }
 

@@ -167,7 +167,13 @@ def test_im2col_flip_transpose_exact(env):
 def test_pool_and_shuffle_exact(env):
     torch, lib = env
     g = torch.Generator(device="cuda").manual_seed(6)
-    B, H, W, C, xp = 2, 6, 8, 16, 32
+    # C = 16: the kernels moving 8 channels per 16-byte access; C = 12: the scalar ones
+    for C, xp in ((16, 32), (12, 12)):
+        _check_pool(torch, lib, g, 2, 6, 8, C, xp)
+    _check_shuffle(torch, lib, g, 2)
+
+
+def _check_pool(torch, lib, g, B, H, W, C, xp):
     X = _bf(torch, (B, H, W, xp), g)
     X[0, 0, 0, 0] = X[0, 1, 1, 0] = 9.0  # tie: the first maximum takes the gradient
     Y = torch.empty(B, H // 2, W // 2, C, dtype=torch.bfloat16, device="cuda")
@@ -187,6 +193,9 @@ def test_pool_and_shuffle_exact(env):
     ref = base.cpu().numpy()
     ref[..., :C] = ref[..., :C] + add
     assert np.array_equal(dX.cpu().numpy(), ref)
+
+
+def _check_shuffle(torch, lib, g, B):
     # up-convolution shuffle into the second half of a concatenation buffer and back
     Hl, Wl, c = 3, 4, 8
     U = _bf(torch, (B * Hl * Wl, 4 * c), g)
