@@ -903,17 +903,62 @@ __global__ void k_split_reduce(const float* __restrict__ part, int splits, int M
         ((float*)D)[(size_t)row * ldd + col] = acc;
 }
 
-// The same sum written transposed, D[col][row] (FP32, no bias): reads run
-// along the partial tiles' rows, writes stride by ldd.
-__global__ void k_split_reduce_t(const float* __restrict__ part, int splits, int M, int N, int ldp,
-                                 float* __restrict__ D, int ldd)
+// The transposed sum with many slices: a CTA takes 32 columns of one row, its
+// 8 thread rows slices ty, ty + 8, ... (reads along the columns), and the 8
+// partial sums of each column are added through shared memory in a fixed order.
+__global__ void k_split_reduce_t_many(const float* __restrict__ part, int splits, int M, int N, int ldp,
+                                      float* __restrict__ D, int ldd)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)M * N) return;
-    const int row = (int)(i / N), col = (int)(i - (long long)row * N);
+    __shared__ float t[8][32];
+    const int row = blockIdx.y, col = blockIdx.x * 32 + threadIdx.x;
     float acc = 0.0f;
-    for (int z = 0; z < splits; ++z) acc += part[(size_t)z * M * ldp + (size_t)row * ldp + col];
-    D[(size_t)col * ldd + row] = acc;
+    if (col < N)
+        for (int z = threadIdx.y; z < splits; z += 8) acc += part[(size_t)z * M * ldp + (size_t)row * ldp + col];
+    t[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && col < N) {
+        float v = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v += t[k][threadIdx.x];
+        D[(size_t)col * ldd + row] = v;
+    }
+}
+
+// The transposed sum with few slices: a 32 x 32 tile of (row, col) per CTA,
+// summed with reads along col and written through shared memory along row.
+__global__ void k_split_reduce_t_tile(const float* __restrict__ part, int splits, int M, int N, int ldp,
+                                      float* __restrict__ D, int ldd)
+{
+    __shared__ float t[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int row = r0 + ty + 8 * k, col = c0 + tx;
+        float acc = 0.0f;
+        if (row < M && col < N)
+            for (int z = 0; z < splits; ++z) acc += part[(size_t)z * M * ldp + (size_t)row * ldp + col];
+        t[ty + 8 * k][tx] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int col = c0 + ty + 8 * k, row = r0 + tx;
+        if (row < M && col < N) D[(size_t)col * ldd + row] = t[tx][ty + 8 * k];
+    }
+}
+
+// D[col][row] (pitch ldd) = the sum of the slices' partial tiles.
+cudaError_t launch_split_reduce_t(const float* part, int splits, int M, int N, float* D, int ldd, cudaStream_t s)
+{
+    if (splits >= 16 && M <= 65535) {
+        const dim3 grid((unsigned)((N + 31) / 32), (unsigned)M);
+        k_split_reduce_t_many<<<grid, dim3(32, 8), 0, s>>>(part, splits, M, N, N, D, ldd);
+    } else {
+        const dim3 grid((unsigned)((N + 31) / 32), (unsigned)((M + 31) / 32));  // M < 2^21 (M = 9 C)
+        k_split_reduce_t_tile<<<grid, dim3(32, 8), 0, s>>>(part, splits, M, N, N, D, ldd);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -939,9 +984,7 @@ cudaError_t gemm_bf16_tout(const void* A, int lda, const void* B, int ldb, float
     e = dispatch<kBK, false>(bn, false, ta, tb, workspace, nullptr, M, N, K, N, 0, splits, kb_per_split, ConvGeo{},
                              ShuffleGeo{}, s);
     if (e != cudaSuccess) return e;
-    const long long n = (long long)M * N;
-    k_split_reduce_t<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(workspace, splits, M, N, N, D, ldd);
-    return cudaGetLastError();
+    return launch_split_reduce_t(workspace, splits, M, N, D, ldd, s);
 }
 
 bool wgrad3_supported(int B, int H, int W, int C, int cout)
@@ -1006,9 +1049,7 @@ cudaError_t wgrad3_bf16(const void* XT3, const void* dYT, int B, int H, int W, i
     }
 #undef NN_WG_CASE
     if (e != cudaSuccess) return e;
-    const long long n = (long long)M * N;
-    k_split_reduce_t<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(workspace, splits, M, N, N, D, ldd);
-    return cudaGetLastError();
+    return launch_split_reduce_t(workspace, splits, M, N, D, ldd, s);
 }
 
 cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,

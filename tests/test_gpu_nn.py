@@ -407,6 +407,7 @@ def _wgrad_reference(X, dY):
     (1, 5, 32, 96, 64, 4),      # 32-pixel K blocks, 9C = 864 (a ragged last M tile), odd H
     (3, 4, 32, 128, 32, 7),     # 128-row boxes, more splits than fit evenly
     (1, 2, 96, 160, 16, 2),     # C = 160: 32-row boxes; W = 96: 32-pixel K blocks
+    (2, 8, 64, 32, 32, 24),     # many slices: the reduction that splits the slices among threads
 ])
 def test_wgrad_from_three_copies_matches_the_nine_tap_sum(env, B, H, W, C, cout, splits):
     """The weight gradient from three horizontally shifted copies, the vertical
