@@ -210,7 +210,44 @@ struct ConvGeo {
 struct ShuffleGeo {
     int Wl = 0, Hl = 0;    // low-resolution image; Wl == 0: plain row-major store
     int c = 0, c0 = 0;     // channels per sub-pixel, first destination channel
+    // ReLU mask of a plain store: each output becomes 0 where mask[row][col]
+    // (BF16, pitch mpitch) is not positive, as the gradient of a ReLU whose
+    // output was mask; null: no mask
+    const __nv_bfloat16* mask = nullptr;
+    int mpitch = 0;
 };
+
+// The ReLU mask of 16 output columns: m[row][col .. col + 15] loaded before
+// the accumulator is read (so that the two latencies overlap), then v[j] = 0
+// where the mask is not positive.  `all`: the 16 columns lie inside the
+// matrix, else only its first n do (loaded element by element).
+struct Mask16 {
+    uint4 a, b;
+};
+__device__ __forceinline__ Mask16 load_relu_mask(const __nv_bfloat16* __restrict__ m, bool all)
+{
+    Mask16 k{};
+    if (all) {
+        k.a = ((const uint4*)m)[0];
+        k.b = ((const uint4*)m)[1];
+    }
+    return k;
+}
+__device__ __forceinline__ void apply_relu_mask(float (&v)[16], const Mask16& k, const __nv_bfloat16* __restrict__ m,
+                                                bool all, int n)
+{
+    if (all) {
+        const uint32_t w[8] = {k.a.x, k.a.y, k.a.z, k.a.w, k.b.x, k.b.y, k.b.z, k.b.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (!(__uint_as_float(w[j] << 16) > 0.0f)) v[2 * j] = 0.0f;
+            if (!(__uint_as_float(w[j] & 0xffff0000u) > 0.0f)) v[2 * j + 1] = 0.0f;
+        }
+    } else {
+        for (int j = 0; j < n && j < 16; ++j)
+            if (!(__bfloat162float(m[j]) > 0.0f)) v[j] = 0.0f;
+    }
+}
 
 namespace {
 
@@ -394,6 +431,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
 #pragma unroll 1
         for (int c = 0; c < BN; c += 16) {
+            const bool mrow = sh.mask && row < M && n0 + c < N;
+            const __nv_bfloat16* mp = mrow ? sh.mask + (long long)row * sh.mpitch + n0 + c : nullptr;
+            const Mask16 mk = mrow ? load_relu_mask(mp, n0 + c + 16 <= N) : Mask16{};
             uint32_t r[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -411,6 +451,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float x = __uint_as_float(r[j]) + ((bias && col + j < N) ? bias[col + j] : 0.0f);
                     v[j] = relu ? fmaxf(x, 0.0f) : x;
                 }
+                if (mrow) apply_relu_mask(v, mk, mp, col + 16 <= N, N - col);
                 long long off = rbase + col;
                 if (sh.Wl) {  // 16 columns of one sub-pixel (c is a multiple of 16)
                     const int sub = col / sh.c, co = col - sub * sh.c;
@@ -666,6 +707,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             }
 #pragma unroll 1
             for (int c = 0; c < BN; c += 16) {
+                const bool mrow = sh.mask && row < M && n0 + c < N;
+                const __nv_bfloat16* mp = mrow ? sh.mask + (long long)row * sh.mpitch + n0 + c : nullptr;
+                const Mask16 mk = mrow ? load_relu_mask(mp, n0 + c + 16 <= N) : Mask16{};
                 uint32_t r[16];
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -683,6 +727,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                         float x = __uint_as_float(r[j]) + ((bias && col + j < N) ? bias[col + j] : 0.0f);
                         v[j] = relu ? fmaxf(x, 0.0f) : x;
                     }
+                    if (mrow) apply_relu_mask(v, mk, mp, col + 16 <= N, N - col);
                     long long off = rbase + col;
                     if (sh.Wl) {
                         const int sub = col / sh.c, co = col - sub * sh.c;
@@ -1052,11 +1097,20 @@ cudaError_t wgrad3_bf16(const void* XT3, const void* dYT, int B, int H, int W, i
     return launch_split_reduce_t(workspace, splits, M, N, D, ldd, s);
 }
 
+// The ReLU-mask epilogue of a single-slice GEMM or convolution storing BF16:
+// mask rows of pitch mpitch (a multiple of 8), 16-byte aligned.
+static bool mask_ok(const void* mask, int mpitch, bool out_bf16, int N)
+{
+    return out_bf16 && mpitch % 8 == 0 && mpitch >= N && ((uintptr_t)mask & 15) == 0;
+}
+
 cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,
-                      int N, int K, bool out_bf16, bool relu, cudaStream_t s, int splits, float* workspace)
+                      int N, int K, bool out_bf16, bool relu, cudaStream_t s, int splits, float* workspace,
+                      const void* mask, int mpitch)
 {
     const int bn = bn_for(N);
     if (N < 8 || N % 8) return cudaErrorInvalidValue;
+    if (mask && (!mask_ok(mask, mpitch, out_bf16, N) || splits > 1)) return cudaErrorInvalidValue;
     if (lda % 8 || ldb % 8 || ldd % 8 || K > lda || K > ldb || N > ldd || M < 1 || K < 1) return cudaErrorInvalidValue;
     if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)D) & 15) return cudaErrorInvalidValue;
     const int nkb = (K + kBK - 1) / kBK;
@@ -1073,8 +1127,10 @@ cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, i
     void* out = splits > 1 ? (void*)workspace : D;
     const int ldo = splits > 1 ? N : ldd;
     const bool ob = splits > 1 ? false : out_bf16;
-    e = dispatch<kBK, false>(bn, ob, ta, tb, out, bias, M, N, K, ldo, r, splits, kb_per_split, ConvGeo{}, ShuffleGeo{},
-                             s);
+    ShuffleGeo sh;
+    sh.mask = (const __nv_bfloat16*)mask;
+    sh.mpitch = mpitch;
+    e = dispatch<kBK, false>(bn, ob, ta, tb, out, bias, M, N, K, ldo, r, splits, kb_per_split, ConvGeo{}, sh, s);
     if (e != cudaSuccess || splits == 1) return e;
     const long long n = (long long)M * N;
     const unsigned grid = (unsigned)((n + 255) / 256);
@@ -1117,11 +1173,13 @@ bool conv3x3_supported(int B, int H, int W, int C)
 }
 
 cudaError_t conv3x3_bf16(const void* X, int B, int H, int W, int C, int cpitch, const void* Wm, int ldw, void* D,
-                         int ldd, const float* bias, int N, bool out_bf16, bool relu, cudaStream_t s)
+                         int ldd, const float* bias, int N, bool out_bf16, bool relu, cudaStream_t s,
+                         const void* mask, int mpitch)
 {
     const int bk = C % 64 == 0 ? 64 : C % 32 == 0 ? 32 : 0;
     int bw, bh, bb;
     if (!bk || !conv_tile(B, H, W, &bw, &bh, &bb)) return cudaErrorNotSupported;
+    if (mask && !mask_ok(mask, mpitch, out_bf16, N)) return cudaErrorInvalidValue;
     if (N < 8 || N % 8 || cpitch % 8 || C > cpitch || ldw % 8 || ldw < 9 * C || ldd % 8 || N > ldd)
         return cudaErrorInvalidValue;
     if (((uintptr_t)X | (uintptr_t)Wm | (uintptr_t)D) & 15) return cudaErrorInvalidValue;
@@ -1136,10 +1194,13 @@ cudaError_t conv3x3_bf16(const void* X, int B, int H, int W, int C, int cpitch, 
     geo.C = C;
     geo.cblocks = C / bk;
     const int M = B * H * W, K = 9 * C;
+    ShuffleGeo sh;
+    sh.mask = (const __nv_bfloat16*)mask;
+    sh.mpitch = mpitch;
     return bk == 64 ? dispatch<64, true>(bn, out_bf16, ta, tb, D, bias, M, N, K, ldd, relu ? 1 : 0, 1, 1 << 30, geo,
-                                         ShuffleGeo{}, s)
+                                         sh, s)
                     : dispatch<32, true>(bn, out_bf16, ta, tb, D, bias, M, N, K, ldd, relu ? 1 : 0, 1, 1 << 30, geo,
-                                         ShuffleGeo{}, s);
+                                         sh, s);
 }
 
 cudaError_t upconv2x2_bf16(const void* X, int lda, const void* Wm, int ldw, void* Y, int ypitch, int c0,

@@ -10,9 +10,12 @@ namespace nn {
 // BF16 row-major with pitches lda, ldb (multiples of 8, >= K); D BF16 or FP32
 // with pitch ldd; N a multiple of 8.  splits > 1 divides K into slices whose
 // FP32 partials go to `workspace` (splits * M * N floats) and are then summed.
+// mask (BF16 [M][mpitch], mpitch a multiple of 8, 16-byte aligned; BF16
+// output and one slice only): each output becomes 0 where mask is not
+// positive, the gradient through a ReLU whose output was mask.
 cudaError_t gemm_bf16(const void* A, int lda, const void* B, int ldb, void* D, int ldd, const float* bias, int M,
                       int N, int K, bool out_bf16, bool relu, cudaStream_t s, int splits = 1,
-                      float* workspace = nullptr);
+                      float* workspace = nullptr, const void* mask = nullptr, int mpitch = 0);
 // D[n][m] = sum_k A[m][k] B[n][k] (FP32, pitch ldd >= M): the same GEMM with
 // its result transposed by the split-K reduction; `workspace` holds
 // splits * M * N floats.
@@ -25,8 +28,10 @@ cudaError_t gemm_bf16_tout(const void* A, int lda, const void* B, int ldb, float
 // weight matrix Wm [N][ldw] (ldw >= 9C).  C must be a multiple of 32 and a
 // 128-pixel tile whole rows of whole images (W a multiple of 128, or a divisor
 // of 128 with matching H); cudaErrorNotSupported otherwise.
+// mask: as for gemm_bf16 (BF16 output).
 cudaError_t conv3x3_bf16(const void* X, int B, int H, int W, int C, int cpitch, const void* Wm, int ldw, void* D,
-                         int ldd, const float* bias, int N, bool out_bf16, bool relu, cudaStream_t s);
+                         int ldd, const float* bias, int N, bool out_bf16, bool relu, cudaStream_t s,
+                         const void* mask = nullptr, int mpitch = 0);
 
 bool conv3x3_supported(int B, int H, int W, int C);
 

@@ -369,8 +369,18 @@ cudaError_t conv_fwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in
 // Weight and bias gradients of one convolution from its input `in` and the
 // (masked) BF16 output gradient dY [P][cout]; the FP32 input gradient goes to
 // dx (pitch dxpitch) when dx is not NULL.
+// g32 [rows][C] (pitch) masked by y > 0, then rounded into BF16 [rows][C].
+cudaError_t mask_cast(lbm_unet* u, float* g32, int gpitch, const bf16* y, int ypitch, long long rows, int C, bf16* out)
+{
+    return nn::mask_cast(g32, gpitch, y, ypitch, rows, C, out, C, u->s);
+}
+
+// Gradients of a 3 x 3 convolution: weights and bias, and the input gradient
+// into dx (FP32, pitch dxpitch) or, with dxb, masked by the convolution's
+// input (the output of a ReLU) and rounded to BF16 [P][cin] in the GEMM's
+// epilogue (dx then only serves a shape the implicit convolution lacks).
 cudaError_t conv_bwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in, int inpitch, const bf16* dY,
-                     float* dx, int dxpitch)
+                     float* dx, int dxpitch, bf16* dxb = nullptr)
 {
     const long long P = v.P;
     const int K9 = 9 * cv.cin;
@@ -392,19 +402,22 @@ cudaError_t conv_bwd(lbm_unet* u, const Level& v, const Conv& cv, const bf16* in
     if (e) return e;
     if ((e = nn::colsum(dY, false, P, cv.cout, cv.cout, u->g + cv.b, u->part, kPartBlocks, u->s))) return e;
     if (!dx) return cudaSuccess;
-    e = nn::conv3x3_bf16(dY, u->B, v.H, v.W, cv.cout, cv.cout, cv.wf, 9 * cv.cout, dx, dxpitch, nullptr, cv.cin, false,
-                         false, u->s);
-    if (e != cudaErrorNotSupported) return e;
+    if (dxb) {
+        e = nn::conv3x3_bf16(dY, u->B, v.H, v.W, cv.cout, cv.cout, cv.wf, 9 * cv.cout, dxb, cv.cin, nullptr, cv.cin,
+                             true, false, u->s, in, inpitch);
+        if (e != cudaErrorNotSupported) return e;
+    } else {
+        e = nn::conv3x3_bf16(dY, u->B, v.H, v.W, cv.cout, cv.cout, cv.wf, 9 * cv.cout, dx, dxpitch, nullptr, cv.cin,
+                             false, false, u->s);
+        if (e != cudaErrorNotSupported) return e;
+    }
     if ((e = nn::im2col3x3(dY, u->B, v.H, v.W, cv.cout, cv.cout, u->col, u->s))) return e;
-    return nn::gemm_bf16(u->col, 9 * cv.cout, cv.wf, 9 * cv.cout, dx, dxpitch, nullptr, (int)P, cv.cin, 9 * cv.cout,
-                         false, false, u->s);
+    if ((e = nn::gemm_bf16(u->col, 9 * cv.cout, cv.wf, 9 * cv.cout, dx, dxpitch, nullptr, (int)P, cv.cin,
+                           9 * cv.cout, false, false, u->s)))
+        return e;
+    return dxb ? mask_cast(u, dx, dxpitch, in, inpitch, P, cv.cin, dxb) : cudaSuccess;
 }
 
-// g32 [rows][C] (pitch) masked by y > 0, then rounded into BF16 [rows][C].
-cudaError_t mask_cast(lbm_unet* u, float* g32, int gpitch, const bf16* y, int ypitch, long long rows, int C, bf16* out)
-{
-    return nn::mask_cast(g32, gpitch, y, ypitch, rows, C, out, C, u->s);
-}
 
 cudaError_t forward(lbm_unet* u, const float* x)
 {
@@ -460,8 +473,7 @@ cudaError_t backward(lbm_unet* u, const float* x, const float* t)
         Level& v = u->lv[l];
         const Level& lo = u->lv[l + 1];
         const int c = v.c;
-        if ((e = conv_bwd(u, v, v.db, v.dA, c, u->gA, u->g32, c))) return e;
-        if ((e = mask_cast(u, u->g32, c, v.dA, c, v.P, c, u->gB))) return e;
+        if ((e = conv_bwd(u, v, v.db, v.dA, c, u->gA, u->g32, c, u->gB))) return e;
         if ((e = conv_bwd(u, v, v.da, v.s, 2 * c, u->gB, v.dcat, 2 * c))) return e;
         // up-convolution: gradient of u_l is the second half of dcat
         if ((e = nn::shuffle_bwd(v.dcat, true, 2 * c, c, u->B, lo.H, lo.W, c, u->dU, u->s))) return e;
@@ -473,10 +485,11 @@ cudaError_t backward(lbm_unet* u, const float* x, const float* t)
         if ((e = nn::gemm_bf16(u->tA, (int)lo.P, u->tB, (int)lo.P, u->g + v.up.w, 2 * c, nullptr, 4 * c, 2 * c,
                                (int)lo.P, false, false, u->s, sp, u->ws)))
             return e;
-        if ((e = nn::gemm_bf16(u->dU, 4 * c, v.up.wt, 4 * c, u->g32, 2 * c, nullptr, (int)lo.P, 2 * c, 4 * c, false,
-                               false, u->s)))
+        // gradient of the up-convolution's input, masked by that input (a ReLU
+        // output) and rounded to BF16 in the GEMM's epilogue
+        if ((e = nn::gemm_bf16(u->dU, 4 * c, v.up.wt, 4 * c, u->gA, 2 * c, nullptr, (int)lo.P, 2 * c, 4 * c, true,
+                               false, u->s, 1, nullptr, hlow, 2 * c)))
             return e;
-        if ((e = mask_cast(u, u->g32, 2 * c, hlow, 2 * c, lo.P, 2 * c, u->gA))) return e;
     }
     // encoder, bottom level first
     for (int l = L - 1; l >= 0; --l) {
@@ -487,8 +500,7 @@ cudaError_t backward(lbm_unet* u, const float* x, const float* t)
             if ((e = nn::maxpool_bwd(v.s, u->B, v.H, v.W, c, 2 * c, u->g32, v.dcat, 2 * c, u->s))) return e;
             if ((e = mask_cast(u, v.dcat, 2 * c, v.s, 2 * c, v.P, c, u->gA))) return e;
         }
-        if ((e = conv_bwd(u, v, v.eb, v.a, c, u->gA, u->g32, c))) return e;
-        if ((e = mask_cast(u, u->g32, c, v.a, c, v.P, c, u->gB))) return e;
+        if ((e = conv_bwd(u, v, v.eb, v.a, c, u->gA, u->g32, c, u->gB))) return e;
         const bf16* in = l == 0 ? u->x0 : u->lv[l - 1].pool;
         const int inpitch = l == 0 ? kX0Pitch : u->lv[l - 1].c;
         if ((e = conv_bwd(u, v, v.ea, in, inpitch, u->gB, l == 0 ? nullptr : u->g32, v.ea.cin))) return e;
