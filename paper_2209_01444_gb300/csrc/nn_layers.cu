@@ -142,6 +142,58 @@ __global__ void __launch_bounds__(256) k_gatherT(const bf16* __restrict__ X, int
     *(uint4*)(AT + (row + 1) * atpitch + p) = hi;
 }
 
+// The three taps of the middle row (dx = -1, 0, 1) from one read of the
+// input: the CTA stages pixels p0 - 1 .. p0 + 64 of a 64-channel block once and
+// writes the three shifted transposed copies from that tile (rows kx * C + c).
+// W is a multiple of 8, so the 8 pixels a thread writes lie in one image row
+// and only a row's first pixel (dx = -1) or last (dx = +1) has its source
+// outside the image.
+__global__ void __launch_bounds__(256) k_gather3(const bf16* __restrict__ X, int P, int W, int C, int cpitch,
+                                                 bf16* __restrict__ AT, long long atpitch)
+{
+    __shared__ uint4 tile[66][8];  // [pixel - (p0 - 1)][16-byte chunk], chunks permuted per row group
+    const int p0 = blockIdx.x * 64;
+    const int c0 = blockIdx.y * 64;
+    for (int k = threadIdx.x; k < 66 * 8; k += 256) {
+        const int ti = k >> 3, g = k & 7;
+        const int q = p0 - 1 + ti, c = c0 + g * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (q >= 0 && q < P && c < C) v = *(const uint4*)(X + (long long)q * cpitch + c);
+        tile[ti][g ^ ((ti >> 3) & 7)] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane & 7;
+    const int cp = (threadIdx.x >> 5) * 4 + (lane >> 3);  // channel pair 0..31
+    const int c = c0 + 2 * cp;
+    const int p = p0 + g * 8;
+    if (c >= C || p >= P) return;
+    const int x = p % W;  // of the first of the 8 pixels
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+        uint32_t w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int ti = g * 8 + j + kx;  // source pixel p + j + kx - 1
+            const uint32_t* row = (const uint32_t*)&tile[ti][0];
+            w[j] = row[(((cp >> 2) ^ ((ti >> 3) & 7)) << 2) + (cp & 3)];
+        }
+        if (kx == 0 && x == 0) w[0] = 0;
+        if (kx == 2 && x + 7 == W - 1) w[7] = 0;
+        uint4 lo, hi;
+        lo.x = __byte_perm(w[0], w[1], 0x5410);
+        lo.y = __byte_perm(w[2], w[3], 0x5410);
+        lo.z = __byte_perm(w[4], w[5], 0x5410);
+        lo.w = __byte_perm(w[6], w[7], 0x5410);
+        hi.x = __byte_perm(w[0], w[1], 0x7632);
+        hi.y = __byte_perm(w[2], w[3], 0x7632);
+        hi.z = __byte_perm(w[4], w[5], 0x7632);
+        hi.w = __byte_perm(w[6], w[7], 0x7632);
+        const long long r = (long long)kx * C + c;
+        *(uint4*)(AT + r * atpitch + p) = lo;
+        *(uint4*)(AT + (r + 1) * atpitch + p) = hi;
+    }
+}
+
 // out[r][c] = BF16(y[r][c] > 0 ? g[r][c] : 0): the ReLU mask of an FP32
 // gradient and its rounding for the next GEMM, in one pass.
 __global__ void k_mask_cast(const float* __restrict__ g, int gpitch, const bf16* __restrict__ y, int ypitch,
@@ -998,6 +1050,12 @@ cudaError_t gatherT(const void* X, int B, int H, int W, int C, int cpitch, int t
         return cudaErrorInvalidValue;
     if (P > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (((uintptr_t)X | (uintptr_t)AT) & 15) return cudaErrorInvalidValue;
+    if (taps == 3 && W % 8 == 0) {
+        const dim3 grid((unsigned)((P + 63) / 64), (unsigned)((C + 63) / 64));
+        if (grid.y > 65535) return cudaErrorInvalidValue;
+        k_gather3<<<grid, 256, 0, s>>>((const bf16*)X, (int)P, W, C, cpitch, (bf16*)AT, atpitch);
+        return cudaGetLastError();
+    }
     const long long cblocks = (long long)((C + 63) / 64) * taps;
     if (cblocks > 65535) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((P + 63) / 64), (unsigned)cblocks);

@@ -369,7 +369,7 @@ def test_upconv2x2_shuffle_epilogue(env, B, Hl, Wl, cin, c):
 
 @pytest.mark.parametrize("B,H,W,C,cp,taps", [(2, 4, 7, 16, 24, 9), (1, 16, 16, 8, 32, 9), (3, 8, 8, 72, 80, 9),
                                             (2, 6, 10, 40, 48, 1), (1, 1, 1000, 200, 200, 1),
-                                            (2, 5, 32, 96, 104, 3), (1, 3, 8, 8, 8, 3)])
+                                            (2, 5, 32, 96, 104, 3), (1, 3, 8, 8, 8, 3), (1, 3, 16, 40, 48, 3)])
 def test_gather_transposed_exact(env, B, H, W, C, cp, taps):
     torch, lib = env
     g = torch.Generator(device="cuda").manual_seed(B * H * W + C)
