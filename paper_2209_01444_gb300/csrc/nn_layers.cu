@@ -142,24 +142,29 @@ __global__ void __launch_bounds__(256) k_gatherT(const bf16* __restrict__ X, int
     *(uint4*)(AT + (row + 1) * atpitch + p) = hi;
 }
 
-// The three taps of the middle row (dx = -1, 0, 1) from one read of the
-// input: the CTA stages pixels p0 - 1 .. p0 + 64 of a 64-channel block once and
-// writes the three shifted transposed copies from that tile (rows kx * C + c).
-// W is a multiple of 8, so the 8 pixels a thread writes lie in one image row
-// and only a row's first pixel (dx = -1) or last (dx = +1) has its source
-// outside the image.
-__global__ void __launch_bounds__(256) k_gather3(const bf16* __restrict__ X, int P, int W, int C, int cpitch,
-                                                 bf16* __restrict__ AT, long long atpitch)
+// Shifted transposed copies from one staged read of the input: the CTA
+// stages pixels p0 - 1 .. p0 + 64 of a 64-channel block, in NR image rows
+// (NR = 1: the middle row, taps 3 .. 5 written as rows kx * C + c; NR = 3:
+// the rows above, at and below, all nine taps, rows (3 ky + kx) * C + c), and
+// writes every tap's copy from that tile.  W is a multiple of 8, so the 8
+// pixels a thread writes lie in one image row: only a row's first pixel
+// (dx = -1) or last (dx = +1), or a whole group in the first (dy = -1) or last
+// (dy = +1) image row, has its source outside the image.
+template <int NR>
+__global__ void __launch_bounds__(256) k_gather_rows(const bf16* __restrict__ X, int P, int H, int W, int C,
+                                                     int cpitch, bf16* __restrict__ AT, long long atpitch)
 {
-    __shared__ uint4 tile[66][8];  // [pixel - (p0 - 1)][16-byte chunk], chunks permuted per row group
+    __shared__ uint4 tile[NR * 66][8];  // [row * 66 + pixel - (p0 - 1)][16-byte chunk], chunks permuted
     const int p0 = blockIdx.x * 64;
     const int c0 = blockIdx.y * 64;
-    for (int k = threadIdx.x; k < 66 * 8; k += 256) {
+    for (int k = threadIdx.x; k < NR * 66 * 8; k += 256) {
         const int ti = k >> 3, g = k & 7;
-        const int q = p0 - 1 + ti, c = c0 + g * 8;
+        const int rr = ti / 66, pi = ti - rr * 66;
+        const long long q = (long long)p0 - 1 + pi + (long long)(NR == 3 ? rr - 1 : 0) * W;
+        const int c = c0 + g * 8;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (q >= 0 && q < P && c < C) v = *(const uint4*)(X + (long long)q * cpitch + c);
-        tile[ti][g ^ ((ti >> 3) & 7)] = v;
+        if (q >= 0 && q < P && c < C) v = *(const uint4*)(X + q * cpitch + c);
+        tile[ti][g ^ ((pi >> 3) & 7)] = v;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, g = lane & 7;
@@ -168,29 +173,34 @@ __global__ void __launch_bounds__(256) k_gather3(const bf16* __restrict__ X, int
     const int p = p0 + g * 8;
     if (c >= C || p >= P) return;
     const int x = p % W;  // of the first of the 8 pixels
+    const int y = (p / W) % H;
 #pragma unroll
-    for (int kx = 0; kx < 3; ++kx) {
-        uint32_t w[8];
+    for (int rr = 0; rr < NR; ++rr) {
+        const bool row_out = NR == 3 && ((rr == 0 && y == 0) || (rr == 2 && y == H - 1));
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int ti = g * 8 + j + kx;  // source pixel p + j + kx - 1
-            const uint32_t* row = (const uint32_t*)&tile[ti][0];
-            w[j] = row[(((cp >> 2) ^ ((ti >> 3) & 7)) << 2) + (cp & 3)];
+        for (int kx = 0; kx < 3; ++kx) {
+            uint32_t w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int pi = g * 8 + j + kx;  // source pixel p + j + kx - 1 of row rr
+                const uint32_t* row = (const uint32_t*)&tile[rr * 66 + pi][0];
+                w[j] = row_out ? 0u : row[(((cp >> 2) ^ ((pi >> 3) & 7)) << 2) + (cp & 3)];
+            }
+            if (kx == 0 && x == 0) w[0] = 0;
+            if (kx == 2 && x + 7 == W - 1) w[7] = 0;
+            uint4 lo, hi;
+            lo.x = __byte_perm(w[0], w[1], 0x5410);
+            lo.y = __byte_perm(w[2], w[3], 0x5410);
+            lo.z = __byte_perm(w[4], w[5], 0x5410);
+            lo.w = __byte_perm(w[6], w[7], 0x5410);
+            hi.x = __byte_perm(w[0], w[1], 0x7632);
+            hi.y = __byte_perm(w[2], w[3], 0x7632);
+            hi.z = __byte_perm(w[4], w[5], 0x7632);
+            hi.w = __byte_perm(w[6], w[7], 0x7632);
+            const long long r = (long long)(NR == 3 ? 3 * rr + kx : kx) * C + c;
+            *(uint4*)(AT + r * atpitch + p) = lo;
+            *(uint4*)(AT + (r + 1) * atpitch + p) = hi;
         }
-        if (kx == 0 && x == 0) w[0] = 0;
-        if (kx == 2 && x + 7 == W - 1) w[7] = 0;
-        uint4 lo, hi;
-        lo.x = __byte_perm(w[0], w[1], 0x5410);
-        lo.y = __byte_perm(w[2], w[3], 0x5410);
-        lo.z = __byte_perm(w[4], w[5], 0x5410);
-        lo.w = __byte_perm(w[6], w[7], 0x5410);
-        hi.x = __byte_perm(w[0], w[1], 0x7632);
-        hi.y = __byte_perm(w[2], w[3], 0x7632);
-        hi.z = __byte_perm(w[4], w[5], 0x7632);
-        hi.w = __byte_perm(w[6], w[7], 0x7632);
-        const long long r = (long long)kx * C + c;
-        *(uint4*)(AT + r * atpitch + p) = lo;
-        *(uint4*)(AT + (r + 1) * atpitch + p) = hi;
     }
 }
 
@@ -1050,10 +1060,13 @@ cudaError_t gatherT(const void* X, int B, int H, int W, int C, int cpitch, int t
         return cudaErrorInvalidValue;
     if (P > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (((uintptr_t)X | (uintptr_t)AT) & 15) return cudaErrorInvalidValue;
-    if (taps == 3 && W % 8 == 0) {
+    if ((taps == 3 || taps == 9) && W % 8 == 0) {
         const dim3 grid((unsigned)((P + 63) / 64), (unsigned)((C + 63) / 64));
         if (grid.y > 65535) return cudaErrorInvalidValue;
-        k_gather3<<<grid, 256, 0, s>>>((const bf16*)X, (int)P, W, C, cpitch, (bf16*)AT, atpitch);
+        if (taps == 3)
+            k_gather_rows<1><<<grid, 256, 0, s>>>((const bf16*)X, (int)P, H, W, C, cpitch, (bf16*)AT, atpitch);
+        else
+            k_gather_rows<3><<<grid, 256, 0, s>>>((const bf16*)X, (int)P, H, W, C, cpitch, (bf16*)AT, atpitch);
         return cudaGetLastError();
     }
     const long long cblocks = (long long)((C + 63) / 64) * taps;
