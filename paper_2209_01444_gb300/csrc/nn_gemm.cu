@@ -379,14 +379,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     int issued = 0;    // blocks whose loads were issued (thread 0)
     int consumed = 0;  // blocks whose MMAs were issued (thread 0)
+    // Loads run LA blocks ahead of the MMAs.  With LA = S - 2 the buffer a
+    // prefetch reuses was read by the MMAs of two blocks back, which have
+    // normally completed, so the thread does not wait for the MMAs it has just
+    // issued before it can load again.
+    constexpr int LA = S >= 4 ? S - 2 : S - 1;
     if (threadIdx.x == 0) {
         bool ok = true;
-        for (int kb = 0; kb < nk && kb < S - 1; ++kb) {
+        for (int kb = 0; kb < nk && kb < LA; ++kb) {
             load(kb, kb);
             ++issued;
         }
         for (int kb = 0; kb < nk && ok; ++kb) {
-            const int pf = kb + S - 1;  // block to prefetch now
+            const int pf = kb + LA;  // block to prefetch now
             if (pf < nk) {
                 const int ps = pf % S;
                 if (pf >= S) ok = mbar_wait(&empty[ps], (uint32_t)((pf / S - 1) & 1));
