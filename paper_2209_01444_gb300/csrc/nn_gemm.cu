@@ -198,6 +198,17 @@ constexpr int stages_for()
     return n < 2 ? 2 : n > 8 ? 8 : n;
 }
 
+// Ring depth of the split-K kernel.  Narrow tiles (N <= 64) take at most 4
+// stages (about 80 KB), so that two CTAs share an SM: their one issuing thread
+// waits on load latency, and two CTAs keep twice the loads in flight (measured:
+// 32- and 64-channel weight gradients 1.3x and 1.7x faster); wider tiles keep
+// the deeper ring of one CTA per SM, which is faster for them.
+template <int BK, int BN>
+constexpr int gemm_stages()
+{
+    return (BN <= 64 && stages_for<BK, BN>() > 4) ? 4 : stages_for<BK, BN>();
+}
+
 }  // namespace
 
 // Geometry of an implicit 3 x 3 convolution (the A operand gathered by
@@ -270,12 +281,12 @@ namespace {
 // outside the image, the convolution's padding).  The shift is on the y
 // coordinate, so the innermost (x) coordinate stays a multiple of BK.
 template <int BN, bool OUT_BF16, int BK, bool CONV, bool WG = false>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, void* __restrict__ D,
            const float* __restrict__ bias, int M, int N, int K, int ldd, int relu, int kb_per_split, ConvGeo geo,
            ShuffleGeo sh)
 {
-    constexpr int S = stages_for<BK, BN>();
+    constexpr int S = gemm_stages<BK, BN>();
     constexpr int A_BYTES = kBM * BK * 2;
     constexpr int B_BYTES = BN * BK * 2;
     constexpr int STAGE = A_BYTES + B_BYTES;
@@ -838,7 +849,7 @@ cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const
                       int ldd, int relu, int splits, int kb_per_split, const ConvGeo& geo, const ShuffleGeo& sh,
                       cudaStream_t s)
 {
-    constexpr int smem = stages_for<BK, BN>() * (kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
+    constexpr int smem = gemm_stages<BK, BN>() * (kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, OUT_BF16, BK, CONV, WG>,

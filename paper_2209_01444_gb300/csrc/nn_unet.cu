@@ -151,16 +151,18 @@ int sm_count()
 }
 
 // K slices so that the weight-gradient GEMM runs as one wave of CTAs (one
-// per SM, each with the longest K loop that allows): measured on the U-Net's
-// shapes, one wave takes 10 to 30 % less time than two, whose partial tiles
-// are twice as many to write and add, and whose last CTAs often start a
-// third, nearly empty wave.
+// per SM for wide tiles, two for tiles up to 64 columns, which the split-K
+// kernel runs two to an SM), each with the longest K loop that allows:
+// measured on the U-Net's shapes, one wave takes 10 to 30 % less time than
+// two, whose partial tiles are twice as many to write and add, and whose last
+// CTAs often start a third, nearly empty wave.
 int splits_for(int M, int N, long long K)
 {
     const int bn = N >= 256 ? 256 : N > 64 ? 128 : N > 32 ? 64 : 32;
     const long long tiles = (long long)((M + 127) / 128) * ((N + bn - 1) / bn);
     const long long nkb = (K + 63) / 64;
-    long long sp = sm_count() / tiles;
+    // narrow tiles run two CTAs per SM (the split-K kernel's shallower ring)
+    long long sp = (bn <= 64 ? 2 : 1) * sm_count() / tiles;
     sp = std::min<long long>(sp, nkb);
     sp = std::min<long long>(sp, 256);
     return (int)std::max<long long>(sp, 1);
