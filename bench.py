@@ -581,7 +581,8 @@ def surrogate_leg(lbm, torch, stream, max_over_ranks, barrier, train_steps: int 
             err = float(np.abs(tips(sur) - tip_ref).max())
             runs.append({"audit_every": a, "ms": ms, "speedup_vs_plain_lb": lb_ms / ms, "final_tip_error_lu": err,
                          "windows_by_network": st["surrogate"], "audited": st["audited"],
-                         "rejected_audits": st["rejected"], "lb_first": st["lb_first"],
+                         "rejected_audits": st["rejected"], "nonfinite_windows": st["nonfinite"],
+                         "lb_first": st["lb_first"],
                          "lb_after_budget": st["lb_after_budget"], "drift_charged_lu": st["drift_charged"],
                          "audit_tip_error_max_lu": max(st["tip_err"]) if st["tip_err"] else None})
             del sur

@@ -529,14 +529,16 @@ LBM_API int lbm_batch_fields_nhwc(lbm_batch* b, int dom, float* dst);
 
 /* One surrogate window of K steps (the paper has no counterpart).  The network
  * (sized for one ny x nx image of 5 fields, run on the handle's stream)
- * predicts the fields K steps ahead.  audit == 0: the state becomes the
- * equilibrium of the prediction and the step count advances by K.  audit != 0:
- * the plain LB also runs the window from the same state and its result is
+ * predicts the fields K steps ahead.  audit == 0: if every predicted value is
+ * finite, the state becomes the equilibrium of the prediction, the step count
+ * advances by K and accepted = 1; otherwise nothing changes, accepted = 0 and
+ * tip_err = infinity (the caller runs the window with the plain LB).  audit !=
+ * 0: the plain LB also runs the window from the same state and its result is
  * kept; the report compares the two: the largest tip difference over the
  * three rays of lbm_metrics (origin cx, cy, orientation `orient`), the nodes
  * whose phi sign differs and the largest |phi| difference; accepted = tip
  * error <= tip_tol (a non-finite prediction is never accepted).
- * Synchronises when audit != 0. */
+ * Synchronises. */
 typedef struct lbm_surrogate_report {
     int audited, accepted;
     double tip_err;     /* lattice units */

@@ -1096,8 +1096,20 @@ int lbm_surrogate_advance(lbm_handle* h, lbm_unet* net, int K, double tip_tol, i
     if ((rc = lbm_unet_forward(net, h->sur_x, h->sur_y)))
         return fail(h, rc, std::string("network: ") + lbm_unet_last_error(net));
     if (!audit) {
+        // a prediction that is not finite is not applied: the state stays at
+        // the window's start and the report says so (the caller runs the
+        // window with the LB)
+        unsigned long long bad = 0;
+        LBM_CUDA(h, lbm::launch_count_nonfinite(h->sur_y, (long long)n5, h->d_mis, h->stream));
+        LBM_CUDA(h, cudaMemcpyAsync(&bad, h->d_mis, sizeof bad, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (bad) {
+            rep->tip_err = INFINITY;
+            return LBM_OK;
+        }
         if ((rc = lbm_set_fields_nhwc(h, h->sur_y, nullptr, 0))) return rc;
         h->steps += K;
+        rep->accepted = 1;
         return LBM_OK;
     }
     // audit: the plain LB over the same window decides; its result is kept

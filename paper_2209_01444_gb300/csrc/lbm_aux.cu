@@ -232,6 +232,16 @@ __global__ void k_phi_mismatch(const float* __restrict__ a, const float* __restr
     }
 }
 
+// out[0] += the number of values of a[0 .. n) that are not finite.
+__global__ void k_count_nonfinite(const float* __restrict__ a, long long n, unsigned long long* __restrict__ out)
+{
+    unsigned long long cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        cnt += isfinite(a[i]) ? 0ull : 1ull;
+    for (int s = 16; s > 0; s >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, s);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&out[0], cnt);
+}
+
 // Macro deviations of every node: phi + 1, C - 1, U, theta - theta_ref, ux,
 // uy, p (flow lattice units); the host adds the reference values in FP64.
 template <class Store>
@@ -631,6 +641,17 @@ cudaError_t launch_flow_inputs(const StepParams& P, int storage, const void* sc,
     case kStoreBF16: k_flow_inputs<StoreBF16><<<g, b, 0, st>>>(P, sc, fl, phi, fy); break;
     default: k_flow_inputs<StoreF32><<<g, b, 0, st>>>(P, sc, fl, phi, fy); break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_nonfinite(const float* a, long long n, unsigned long long* out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 1216) blocks = 1216;
+    if (blocks < 1) blocks = 1;
+    k_count_nonfinite<<<(unsigned)blocks, 256, 0, s>>>(a, n, out);
     return cudaGetLastError();
 }
 

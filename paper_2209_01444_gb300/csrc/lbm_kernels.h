@@ -103,6 +103,8 @@ cudaError_t launch_flow_inputs(const StepParams& P, int storage, const void* sc,
 cudaError_t flow_steps(const StepParams& P, int storage, int n, void* sc, void* const fl[2], int* cf, const float* phi,
                        const float* fy, cudaStream_t s);
 cudaError_t launch_phi_mismatch(const float* a, const float* b, long long n, unsigned long long* out, cudaStream_t s);
+// out[0] = the number of values of a[0 .. n) that are not finite (queued on s).
+cudaError_t launch_count_nonfinite(const float* a, long long n, unsigned long long* out, cudaStream_t s);
 // Macros of a band (FP32 band planes phi + 1, C - 1, U, theta - theta_ref,
 // ux, uy, p; lattice units).
 cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out, int y0,

@@ -311,7 +311,10 @@ def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: i
     the plain LB from the same state (the LB result is kept).  If the
     audit's tip error exceeds tip_tol, the state returns to the snapshot taken
     at the previous passed audit, every window since is re-run by the LB, and
-    the network sits out the next `backoff` windows.
+    the network sits out the next `backoff` windows.  An unaudited window
+    whose prediction is not finite is not applied and counts as a failed audit;
+    so does a window in which the state or the audit's LB run goes non-finite
+    (from a finite but unphysical prediction kept earlier).
 
     Drift budget: window errors add up over a rollout, which a one-window
     audit does not see.  Each passed audit charges drift_factor times its tip
@@ -321,8 +324,8 @@ def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: i
     windows.
     Returns counts."""
     budget = tip_tol if drift_budget is None else drift_budget
-    st = {"surrogate": 0, "audited": 0, "rejected": 0, "lb_rerun": 0, "lb_backoff": 0, "lb_first": 0,
-          "lb_after_budget": 0, "drift_charged": 0.0, "tip_err": []}
+    st = {"surrogate": 0, "audited": 0, "rejected": 0, "nonfinite": 0, "lb_rerun": 0, "lb_backoff": 0,
+          "lb_first": 0, "lb_after_budget": 0, "drift_charged": 0.0, "tip_err": []}
     w = 0
     if lb_first:  # the first windows (fast early growth of the seed) by the LB
         n = min(lb_first, windows)
@@ -342,11 +345,33 @@ def rollout(sim, net: UNet, windows: int, K: int, tip_tol: float, audit_every: i
                 since = 0
             continue
         audit = since + 1 >= audit_every or w == windows - 1
-        rep = sim.surrogate_advance(net, K, tip_tol, audit, cx, cy, orient)
+        try:
+            rep = sim.surrogate_advance(net, K, tip_tol, audit, cx, cy, orient)
+        except L.LBMError as err:
+            # a finite but unphysical prediction kept in an earlier window can
+            # make the state, or this window's LB audit, go non-finite: the
+            # stretch since the last passed audit is rejected like a failed audit
+            if err.code != L.LBM_ENUMERIC:
+                raise
+            rep = {"audited": audit, "accepted": False, "tip_err": math.inf, "nonfinite": True}
         w += 1
-        if not audit:
+        if rep.get("nonfinite"):
+            st["nonfinite"] += 1
+        if not audit and rep["accepted"]:
             st["surrogate"] += 1
             since += 1
+            continue
+        if not audit:  # a prediction that is not finite was not applied: as a failed audit
+            st["rejected"] += 1
+            if not rep.get("nonfinite"):
+                st["nonfinite"] += 1
+            sim.snapshot_restore(0)
+            sim.step(K * (since + 1))
+            st["surrogate"] -= since
+            st["lb_rerun"] += since
+            off = backoff
+            sim.snapshot_save(0)
+            since = 0
             continue
         st["audited"] += 1
         st["tip_err"].append(rep["tip_err"])

@@ -104,6 +104,30 @@ def test_surrogate_window_and_audit(env):
     assert float((f1 - f0).abs().max()) <= 1e-4
 
 
+def test_prediction_that_is_not_finite_is_never_applied(env):
+    """A network whose output is not finite (here a NaN output bias): an
+    unaudited window leaves the state and the step count as they were and
+    reports the window as not accepted; an audited one keeps the plain LB
+    result and rejects the prediction."""
+    torch, lbm, S = env
+    sim, c = _sim(lbm)
+    net = S.UNet(1, 64, 64)
+    p = workloads.unet_params(S.param_shapes(), 7)
+    p["out.b"][:] = np.nan
+    net.set_params(p)
+    cx, cy = float(c.seeds[0, 0]), float(c.seeds[0, 1])
+    state0, n0 = sim.state(), sim.steps
+    rep = sim.surrogate_advance(net, 50, 1.0, False, cx, cy)
+    assert not rep["audited"] and not rep["accepted"] and rep["tip_err"] == float("inf")
+    assert sim.steps == n0
+    np.testing.assert_array_equal(sim.state(), state0)
+    ref, _ = _sim(lbm)
+    ref.step(50)
+    rep = sim.surrogate_advance(net, 50, 1.0, True, cx, cy)
+    assert rep["audited"] and not rep["accepted"]
+    np.testing.assert_array_equal(sim.state(), ref.state())
+
+
 def test_training_on_lb_trajectories_beats_persistence(env):
     """A network trained for 500 steps on (t, t + 50) pairs of LB runs
     predicts the pairs of a held-out domain better than 'no change'."""
