@@ -4,12 +4,12 @@
 // contiguous, row pitch a multiple of 8 elements), FP32 accumulation in tensor
 // memory, and a BF16 or FP32 result.
 //
-// One CTA of 128 threads computes a 128 x BN tile.  Thread 0 drives a
-// kStages-deep ring: TMA (cp.async.bulk.tensor, 128-byte swizzle) fills a
-// stage and completes its `full` mbarrier; four tcgen05.mma (M = 128, N = BN,
-// K = 16 each) consume it and tcgen05.commit arrives on its `empty` mbarrier,
-// which frees the stage for the load issued kStages - 1 blocks ahead.  The
-// accumulator lives in TMEM (BN FP32 columns x 128 lanes); after the last
+// One CTA of 128 threads computes a 128 x BN tile.  Thread 0 drives an
+// S-deep ring (gemm_stages): TMA (cp.async.bulk.tensor, 128- or 64-byte
+// swizzle) fills a stage and completes its `full` mbarrier; tcgen05.mma
+// (M = 128, N = BN, K = 16 each) consume it and tcgen05.commit arrives on its
+// `empty` mbarrier, which frees the stage for the load issued S - 2 blocks
+// ahead.  The accumulator lives in TMEM (BN FP32 columns x 128 lanes); after the last
 // commit every warp reads its 32 lanes with tcgen05.ld, adds the bias, applies
 // the activation and stores.  Every wait is bounded by a wall-clock limit:
 // on expiry the kernel raises the error flag, drains what it issued (again
@@ -29,7 +29,6 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;       // 64 BF16 = 128 bytes: one swizzle row
-constexpr int kStages = 4;
 constexpr int kThreads = 128;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
 
