@@ -1599,15 +1599,15 @@ int lbm_batch_tune(lbm_batch* b, const char* cache_path, int* tile_height)
         cls /= 10;
         scale *= 10;
     }
-    char key[256];
+    char key[512];  // the device name (up to 256 characters) and the batch's class
     snprintf(key, sizeof(key), "%s|storage%d|nodes%lld|domains%zu", prop.name, b->storage, cls * scale, b->dom.size());
     for (char* c = key; *c; ++c)
         if (*c == ' ') *c = '_';
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
-            char k[256];
+            char k[512];
             int v, r;
-            while (fscanf(f, "%255s %d %d", k, &v, &r) == 3)
+            while (fscanf(f, "%511s %d %d", k, &v, &r) == 3)
                 if (strcmp(k, key) == 0 && (v == 4 || v == 8 || v == 16) && r >= 0) {
                     b->ty = v;
                     b->run = r;
