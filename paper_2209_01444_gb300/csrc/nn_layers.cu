@@ -654,6 +654,22 @@ __global__ void k_flip3x3(const bf16* __restrict__ W, int cout, int cin, bf16* _
     Wf[i] = W[((long long)co * 9 + (8 - tf)) * cin + ci];
 }
 
+// Every kernel of a network in one launch: element i belongs to the last job
+// whose start is <= i (at most a few tens of jobs, scanned in order).
+__global__ void k_flip3x3_many(const FlipJob* __restrict__ jobs, int njobs, long long total)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    int j = 0;
+    while (j + 1 < njobs && jobs[j + 1].start <= i) ++j;
+    const FlipJob jb = jobs[j];
+    const long long k = i - jb.start;
+    const int co = (int)(k % jb.cout);
+    const long long r = k / jb.cout;
+    const int tf = (int)(r % 9), ci = (int)(r / 9);
+    ((bf16*)jb.Wf)[k] = ((const bf16*)jb.W)[((long long)co * 9 + (8 - tf)) * jb.cin + ci];
+}
+
 // Wp[co][t * cin_pad + ci] = W[co][t * cin + ci] for ci < cin, else 0: the
 // kernel of a convolution whose input carries cin_pad channels, the extra ones zero.
 __global__ void k_pad_conv3x3(const bf16* __restrict__ W, int cout, int cin, int cin_pad, bf16* __restrict__ Wp)
@@ -1096,6 +1112,13 @@ cudaError_t pad_conv3x3(const void* W, int cout, int cin, int cin_pad, void* Wp,
 {
     if (cin_pad < cin) return cudaErrorInvalidValue;
     k_pad_conv3x3<<<blocks((long long)cout * 9 * cin_pad), 256, 0, s>>>((const bf16*)W, cout, cin, cin_pad, (bf16*)Wp);
+    return cudaGetLastError();
+}
+
+cudaError_t flip3x3_many(const FlipJob* jobs, int njobs, long long total, cudaStream_t s)
+{
+    if (njobs < 1 || total < 1) return cudaSuccess;
+    k_flip3x3_many<<<blocks(total), 256, 0, s>>>(jobs, njobs, total);
     return cudaGetLastError();
 }
 

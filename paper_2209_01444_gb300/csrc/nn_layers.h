@@ -21,6 +21,15 @@ cudaError_t proj_fwd(const void* X, int P, int C, int xpitch, const float* Wt, c
 cudaError_t proj_bwd(const float* dY, const void* X, int P, int C, int xpitch, const float* Wt, int O, float* dX,
                      int dpitch, float* dW, float* db, float* part, int part_blocks, cudaStream_t s);
 cudaError_t flip3x3(const void* W, int cout, int cin, void* Wf, cudaStream_t s);
+// Several flips in one launch: job j flips the kernel at W (cout x 9 cin) into
+// Wf, its elements numbered from start (jobs in order of start; device table).
+struct FlipJob {
+    const void* W;
+    void* Wf;
+    int cout, cin;
+    long long start;
+};
+cudaError_t flip3x3_many(const FlipJob* jobs, int njobs, long long total, cudaStream_t s);
 cudaError_t gatherT(const void* X, int B, int H, int W, int C, int cpitch, int taps, void* AT, long long atpitch,
                     cudaStream_t s);
 cudaError_t mask_cast(const float* g, int gpitch, const void* y, int ypitch, long long rows, int C, void* out,

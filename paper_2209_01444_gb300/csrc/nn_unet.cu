@@ -98,6 +98,9 @@ struct lbm_unet {
     float* g32 = nullptr;
     float* ws = nullptr;
     long long ws_n = 0;
+    nn::FlipJob* flip_jobs = nullptr;  // device table of the kernel flips (derive)
+    int n_flip = 0;
+    long long flip_total = 0;
     cudaStream_t s = nullptr;
     std::vector<void*> allocs;
     long long bytes = 0;
@@ -281,6 +284,22 @@ cudaError_t allocate(lbm_unet* u)
         for (const Conv* cv : {&v.ea, &v.eb, &v.da, &v.db})
             if (cv->cout && !nn::conv3x3_supported(u->B, v.H, v.W, cv->cin)) col_n = std::max(col_n, 9 * v.P * cv->cin);
     UN_ALLOC(u->col, col_n);
+    // the table of kernel flips derive() runs in one launch (the weight and
+    // flipped-weight buffers stay where they are for the network's life)
+    std::vector<nn::FlipJob> jobs;
+    long long total = 0;
+    for (Level& v : u->lv)
+        for (Conv* cv : {&v.ea, &v.eb, &v.da, &v.db})
+            if (cv->cout) {
+                jobs.push_back({u->wb + cv->w, cv->wf, cv->cout, cv->cin, total});
+                total += 9LL * cv->cout * cv->cin;
+            }
+    nn::FlipJob* table = nullptr;
+    UN_ALLOC(table, (long long)jobs.size());
+    if ((e = cudaMemcpy(table, jobs.data(), jobs.size() * sizeof(nn::FlipJob), cudaMemcpyHostToDevice))) return e;
+    u->flip_jobs = table;
+    u->n_flip = (int)jobs.size();
+    u->flip_total = total;
 #undef UN_ALLOC
     return e;
 }
@@ -336,11 +355,11 @@ cudaError_t allocate_backward(lbm_unet* u)
 cudaError_t derive(lbm_unet* u)
 {
     cudaError_t e = cudaSuccess;
+    if ((e = nn::flip3x3_many(u->flip_jobs, u->n_flip, u->flip_total, u->s))) return e;
     for (Level& v : u->lv) {
         for (Conv* cv : {&v.ea, &v.eb, &v.da, &v.db}) {
-            if (!cv->cout) continue;
-            if ((e = nn::flip3x3(u->wb + cv->w, cv->cout, cv->cin, cv->wf, u->s))) return e;
-            if (cv->wpad && (e = nn::pad_conv3x3(u->wb + cv->w, cv->cout, cv->cin, cv->cin_pad, cv->wpad, u->s)))
+            if (cv->cout && cv->wpad &&
+                (e = nn::pad_conv3x3(u->wb + cv->w, cv->cout, cv->cin, cv->cin_pad, cv->wpad, u->s)))
                 return e;
         }
         if (v.up.cout) {
