@@ -119,6 +119,7 @@ struct StoreF32 {
     using T = float;
     static constexpr int kScalarBytes = 15 * 4;  // per node
     static constexpr int kFlowBytes = 9 * 4;
+    static constexpr int kSS = 1, kSF = 1;       // scales of the moving scalar and the flow planes
     static __device__ __forceinline__ float load(const void* sc, const void* fl, int q, long long o,
                                                  const StepParams& P)
     {
@@ -141,6 +142,10 @@ struct StoreF32 {
     static __device__ __forceinline__ int flow_col(int x) { return block_col(x, 9); }
     static __device__ __forceinline__ void store_mov(void* sc, int q, long long e, float v) { ((float*)sc)[e + 32 * q] = v; }
     static __device__ __forceinline__ void store_flow(void* fl, int i, long long e, float v) { ((float*)fl)[e + 32 * i] = v; }
+    static __device__ __forceinline__ float load_flow(const void* fl, int i, long long o)
+    {
+        return ((const float*)fl)[block_index(o, 9) + 32 * i];
+    }
     // n_i and g_i (i = 1..4), which stream to the same neighbour: the moving
     // scalar index serves both (16-bit storage keeps them in one word)
     static __device__ __forceinline__ long long pair_row(int y, const StepParams& P) { return mov_row(y, P); }
@@ -206,9 +211,15 @@ struct Conv<__nv_bfloat16> {
 // per node (n in the low half; pair i at word 64 + 32 (i - 1) + lane), since
 // both go to the same neighbour; words 192..287 the FP32 rest planes f_0,
 // n_0, g_0 (word 192 + 32 r + lane).
+// load/store take and give deviations.  The push stores (store_mov,
+// store_pair, store_flow) take, and load_pair and load_flow give, values in
+// units of the plane's scale (kSS for the moving scalar planes, kSF for the
+// flow planes): the fused step folds the scale into the constants of its
+// moment transforms, which is exact for a power of two.
 template <class H, int S_SC, int S_FL>
 struct Store16 {
     using T = H;
+    static constexpr int kSS = S_SC, kSF = S_FL;
     static __device__ __forceinline__ float scale(int q) { return q >= kH ? (float)S_FL : (float)S_SC; }
     static __device__ __forceinline__ float inv_scale(int q) { return q >= kH ? 1.0f / S_FL : 1.0f / S_SC; }
     static constexpr int kScalarBytes = 12 * 2 + 3 * 4;
@@ -262,23 +273,27 @@ struct Store16 {
     static __device__ __forceinline__ int pair_col(int x) { return (x >> 5) * 288 + (x & 31) + 64; }
     static __device__ __forceinline__ long long flow_row(int y, const StepParams& P) { return block_row(y, P.pitch, 9); }
     static __device__ __forceinline__ int flow_col(int x) { return block_col(x, 9); }
-    static __device__ __forceinline__ void store_mov(void* sc, int q, long long e, float v)  // q = f_1..f_4
+    static __device__ __forceinline__ void store_mov(void* sc, int q, long long e, float vs)  // q = f_1..f_4
     {
-        ((H*)sc)[e + 32 * (q - 1)] = Conv<H>::from(v * (float)S_SC);
+        ((H*)sc)[e + 32 * (q - 1)] = Conv<H>::from(vs);
     }
-    static __device__ __forceinline__ void store_flow(void* fl, int i, long long e, float v)
+    static __device__ __forceinline__ void store_flow(void* fl, int i, long long e, float vs)
     {
-        ((H*)fl)[e + 32 * i] = Conv<H>::from(v * (float)S_FL);
+        ((H*)fl)[e + 32 * i] = Conv<H>::from(vs);
     }
-    static __device__ __forceinline__ void load_pair(const void* sc, int i, long long o, float& n, float& g)
+    static __device__ __forceinline__ float load_flow(const void* fl, int i, long long o)
+    {
+        return Conv<H>::to(((const H*)fl)[block_index(o, 9) + 32 * i]);
+    }
+    static __device__ __forceinline__ void load_pair(const void* sc, int i, long long o, float& ns, float& gs)
     {
         const float2 v = Conv<H>::to2(((const uint32_t*)sc)[word_index(o) + 64 + 32 * (i - 1)]);
-        n = v.x * (1.0f / S_SC);
-        g = v.y * (1.0f / S_SC);
+        ns = v.x;
+        gs = v.y;
     }
-    static __device__ __forceinline__ void store_pair(void* sc, int i, long long e, float n, float g)
+    static __device__ __forceinline__ void store_pair(void* sc, int i, long long e, float ns, float gs)
     {
-        ((uint32_t*)sc)[e + 32 * (i - 1)] = Conv<H>::from2(n * (float)S_SC, g * (float)S_SC);
+        ((uint32_t*)sc)[e + 32 * (i - 1)] = Conv<H>::from2(ns, gs);
     }
 };
 using StoreF16 = Store16<__half, 16, 1024>;
@@ -330,14 +345,29 @@ struct Macro {
     float fsx, fsy;       // fluid-solid force f = -u*
 };
 
+// SN, SF: n_1..n_4, g_1..g_4 given in units of 1/SN, h in units of 1/SF (a
+// power of two, so every sum below equals the unscaled one bit for bit).
+template <int SN, int SF>
+__device__ __forceinline__ float scaled_rest_sum(const float* v)
+{
+    if constexpr (SN == 1) {
+        return v[0] + v[1] + v[2] + v[3] + v[4];
+    } else {
+        constexpr float iN = 1.0f / SN;
+        return fmaf(v[4], iN, fmaf(v[3], iN, fmaf(v[2], iN, fmaf(v[1], iN, v[0]))));
+    }
+}
+
+template <int SN = 1, int SF = 1>
 __device__ __forceinline__ Macro node_macros(const float* f, const float* n, const float* g, const float* h,
                                              const StepParams& P)
 {
+    constexpr float iF = 1.0f / SF;
     Macro m;
     m.p1 = f[0] + f[1] + f[2] + f[3] + f[4];
     m.phi = m.p1 - 1.0f;
-    m.dC = n[0] + n[1] + n[2] + n[3] + n[4];
-    const float dH = g[0] + g[1] + g[2] + g[3] + g[4];
+    m.dC = scaled_rest_sum<SN, SF>(n);
+    const float dH = scaled_rest_sum<SN, SF>(g);
     m.hp1 = h_plus_1(P.h_kind, m.p1);
     m.dth = dH + P.latent * m.hp1;             // theta = H + L h
     m.dH = dH;
@@ -345,9 +375,9 @@ __device__ __forceinline__ Macro node_macros(const float* f, const float* n, con
     m.U = U_of(m.dC, m.p1, P.k);
     m.Fx = P.Fx;
     m.Fy = P.Fy + P.gbT * m.dth + P.gbC * (m.dC + P.dC_ref);
-    float jx = h[1] - h[3] + h[5] - h[6] - h[7] + h[8];
-    float jy = h[2] - h[4] + h[5] + h[6] - h[7] - h[8];
-    float rest = h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
+    float jx = (h[1] - h[3] + h[5] - h[6] - h[7] + h[8]) * iF;
+    float jy = (h[2] - h[4] + h[5] + h[6] - h[7] - h[8]) * iF;
+    float rest = (h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8]) * iF;
     float usx = jx + 0.5f * m.Fx, usy = jy + 0.5f * m.Fy;   // u*
     float qt = 1.0f - 0.5f * m.p1;                         // q~ = (1 - phi)/2
     m.fsx = -usx;
@@ -432,35 +462,41 @@ __device__ __forceinline__ void deq_flow(float p, float ux, float uy, float* e)
 // dCv = Cv - Cv_ref of the reference state; (Gx, Gy) are the first moments of
 // the auxiliary term, weighted by (1 - s1/2); S0 is an isotropic source added
 // with weights w_i.  The post-collision deviations follow through the inverse
-// of Eq. (B.1).
+// of Eq. (B.1).  SI, SO: d_1..d_4 are given, and out_1..out_4 returned, in
+// units of 1/SI and 1/SO (powers of two; d_0 and out_0 unscaled).
+template <int SI = 1, int SO = 1>
 __device__ __forceinline__ void collide_d2q5(const float* d, float dA, float Bx, float By, float dCv, float s1,
                                              float Gx, float Gy, float S0, float* out)
 {
-    float m1 = d[1] - d[3], m2 = d[2] - d[4];
+    constexpr float iI = 1.0f / SI, hO = 0.5f * SO;
+    float m1 = (d[1] - d[3]) * iI, m2 = (d[2] - d[4]) * iI;
     float k1 = 1.0f - 0.5f * s1;
     float r1 = m1 - s1 * (m1 - Bx) + k1 * Gx;
     float r2 = m2 - s1 * (m2 - By) + k1 * Gy;
     float e = (dCv + S0) * (1.0f / 3.0f);   // deviation of each post-collision second moment
     out[0] = dA + S0 - 2.0f * e;
-    out[1] = 0.5f * (e + r1);
-    out[3] = 0.5f * (e - r1);
-    out[2] = 0.5f * (e + r2);
-    out[4] = 0.5f * (e - r2);
+    out[1] = hO * (e + r1);
+    out[3] = hO * (e - r1);
+    out[2] = hO * (e + r2);
+    out[4] = hO * (e - r2);
 }
 
 // D2Q9 raw-moment MRT of Eq. (24): m* = m - S (m - m^eq) + (I - S/2) m_F with
 // m^eq and m_F of Eq. (B.3) (varphi = 0) and F' = F + [1 - q~] f; returns the
 // post-collision deviations through the inverse of Eq. (B.2) (m0* = rho0).
+// SI, SO: h given and out returned in units of 1/SI and 1/SO (powers of two).
+template <int SI = 1, int SO = 1>
 __device__ __forceinline__ void collide_flow(const float* h, const Macro& m, float s2, float* out)
 {
+    constexpr float iI = 1.0f / SI, hO = 0.5f * SO, qO = 0.25f * SO;
     float qt = 1.0f - 0.5f * m.p1;
     float Fpx = m.Fx + (1.0f - qt) * m.fsx;
     float Fpy = m.Fy + (1.0f - qt) * m.fsy;
     float u = m.ux, v = m.uy, p = m.p;
     // pre-collision second-order moments that relax with s2
-    float mxx = h[1] + h[3] + h[5] + h[6] + h[7] + h[8];
-    float myy = h[2] + h[4] + h[5] + h[6] + h[7] + h[8];
-    float mxy = h[5] - h[6] + h[7] - h[8];
+    float mxx = (h[1] + h[3] + h[5] + h[6] + h[7] + h[8]) * iI;
+    float myy = (h[2] + h[4] + h[5] + h[6] + h[7] + h[8]) * iI;
+    float mxy = (h[5] - h[6] + h[7] - h[8]) * iI;
     // post-collision moments
     float r1 = u + 0.5f * Fpx;
     float r2 = v + 0.5f * Fpy;
@@ -471,15 +507,18 @@ __device__ __forceinline__ void collide_flow(const float* h, const Macro& m, flo
     float r7 = (u + 0.5f * Fpx) * (1.0f / 3.0f);
     float r8 = (p + u * u + v * v) * (1.0f / 3.0f);
     // inverse of the tensor-product raw-moment matrix (r0 - rho0 = 0)
-    out[0] = -r3 - r4 + r8;
-    out[1] = 0.5f * (r1 + r3 - r7 - r8);
-    out[3] = 0.5f * (-r1 + r3 + r7 - r8);
-    out[2] = 0.5f * (r2 + r4 - r6 - r8);
-    out[4] = 0.5f * (-r2 + r4 + r6 - r8);
-    out[5] = 0.25f * (r5 + r6 + r7 + r8);
-    out[6] = 0.25f * (-r5 + r6 - r7 + r8);
-    out[7] = 0.25f * (r5 - r6 - r7 + r8);
-    out[8] = 0.25f * (-r5 - r6 + r7 + r8);
+    if constexpr (SO == 1)
+        out[0] = -r3 - r4 + r8;
+    else
+        out[0] = (float)SO * (-r3 - r4 + r8);
+    out[1] = hO * (r1 + r3 - r7 - r8);
+    out[3] = hO * (-r1 + r3 + r7 - r8);
+    out[2] = hO * (r2 + r4 - r6 - r8);
+    out[4] = hO * (-r2 + r4 + r6 - r8);
+    out[5] = qO * (r5 + r6 + r7 + r8);
+    out[6] = qO * (-r5 + r6 - r7 + r8);
+    out[7] = qO * (r5 - r6 - r7 + r8);
+    out[8] = qO * (-r5 - r6 + r7 + r8);
 }
 
 }  // namespace lbm

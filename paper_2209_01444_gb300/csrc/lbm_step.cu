@@ -117,7 +117,9 @@ __device__ __forceinline__ void wall_rest(const StepParams& P, int axis, int typ
 }
 
 // Per-node part of the coupled step for node (x, y) = tile-local (lx - 1, ly - 1):
-// f, n, g, h are its populations at time n, the *_prev values its history;
+// f, n, g, h are its populations at time n (n_1..n_4 and g_1..g_4 in units
+// of 1/Store::kSS, h in units of 1/Store::kSF: the codec's push scales), the
+// *_prev values its history;
 // fs holds the tile's phi populations with a one-node halo, node (x, y) at
 // column fx = lx - 1 + XO of rows of FW floats; ps holds phi on the tile and
 // halo with node (x, y) at [ly][lx].  Collides, push-streams (the phase field
@@ -135,7 +137,8 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
     const long long o = (long long)y * P.pitch + x;
     const int fx = lx - 1 + XO;
 
-    const Macro m = node_macros(f, n, g, h, P);
+    constexpr int SS = Store::kSS, SF = Store::kSF;
+    const Macro m = node_macros<SS, SF>(f, n, g, h, P);
     const float usx = m.ux * P.nsub, usy = m.uy * P.nsub;  // velocity of the scalar lattice
 
     float co = P.cos_o, so = P.sin_o;
@@ -189,7 +192,7 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
         const float s1 = __fdividef(1.0f, P.kappa3 * as2 + 0.5f);
         const float S0 = (Q + 0.5f * as2 * (Q - Q_prev)) * P.inv_tau;
         const float ga = -(1.0f / 3.0f) * ia;
-        collide_d2q5(f, m.p1, 0.0f, 0.0f, m.p1, s1, ga * Nx, ga * Ny, S0, fo);
+        collide_d2q5<1, SS>(f, m.p1, 0.0f, 0.0f, m.p1, s1, ga * Nx, ga * Ny, S0, fo);
     }
     // ---- solute: Eqs. (17)-(19) with J_at of Eq. (7)
     float no[5];
@@ -207,17 +210,17 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
         // sum_i c_i G_i = d_t(Cu) + cs^2 (U grad q~ + J_at/D), grad q~ = -grad(phi)/2
         const float Gx = (Cux - Cux_prev) + (1.0f / 3.0f) * (-0.5f * m.U * gx + Jx * P.inv_D);
         const float Gy = (Cuy - Cuy_prev) + (1.0f / 3.0f) * (-0.5f * m.U * gy + Jy * P.inv_D);
-        collide_d2q5(n, m.dC, Cux, Cuy, qt * m.U, P.s1C, Gx, Gy, 0.0f, no);
+        collide_d2q5<SS, SS>(n, m.dC, Cux, Cuy, qt * m.U, P.s1C, Gx, Gy, 0.0f, no);
     }
     // ---- heat: Eqs. (21)-(23)
     float go[5];
     {
         const float Hux = m.H * usx, Huy = m.H * usy;
-        collide_d2q5(g, m.dH, Hux, Huy, m.dth, P.s1T, Hux - Hux_prev, Huy - Huy_prev, 0.0f, go);
+        collide_d2q5<SS, SS>(g, m.dH, Hux, Huy, m.dth, P.s1T, Hux - Hux_prev, Huy - Huy_prev, 0.0f, go);
     }
     // ---- flow: Eqs. (24)-(26)
     float ho[9];
-    collide_flow(h, m, P.s2u, ho);
+    collide_flow<SF, SF>(h, m, P.s2u, ho);
 
     // ---- push streaming: the rest populations stay at o; every moving one
     // goes to the neighbour node (x + c_x, y + c_y), whose element index is a
@@ -230,14 +233,14 @@ __device__ __forceinline__ void coupled_node(const StepParams& P, void* __restri
         const long long d5[5] = {0, rY + cP, rP + c0, rY + cM, rM + c0};
         // modified streaming of the phase field: the destination's time-n
         // population sits in the shared tile (its halo is periodic-wrapped)
-        const float ib = ia - 1.0f;
+        const float ib = ia - 1.0f, ibs = ib * (float)SS;
         const float fd[5] = {fs[0][ly][fx], fs[1][ly][fx + 1], fs[2][ly + 1][fx], fs[3][ly][fx - 1],
                              fs[4][ly - 1][fx]};
         Store::store(dst, dstf, kF, o, fo[0] * ia - ib * fd[0], P);
         Store::store(dst, dstf, kN, o, no[0], P);
         Store::store(dst, dstf, kG, o, go[0], P);
 #pragma unroll
-        for (int i = 1; i < 5; ++i) Store::store_mov(dst, kF + i, d5[i], fo[i] * ia - ib * fd[i]);
+        for (int i = 1; i < 5; ++i) Store::store_mov(dst, kF + i, d5[i], fo[i] * ia - ibs * fd[i]);
         // n_i and g_i go to the same neighbour (one word in 16-bit storage)
         const long long qY = Store::pair_row(y, P), qP = Store::pair_row(yp, P), qM = Store::pair_row(ym, P);
         const int p0 = Store::pair_col(x), pP = Store::pair_col(xp), pM = Store::pair_col(xm);
@@ -312,12 +315,15 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
                 for (int i = 0; i < 9; ++i) hi[i] = Store::load(src, srcf, kH + i, oi, P);
                 const Macro mi = node_macros(fi, ni, gi, hi, P);
                 wall_rest(P, 0, P.bc[side], mi, ni, gi, hi, nbw, gbw, hbw, 0);
+                // in the units the node update takes (rest populations unscaled)
+                wnb[side][r][0] = nbw[0];
+                wnb[side][r][5] = gbw[0];
 #pragma unroll
-                for (int i = 0; i < 5; ++i) wnb[side][r][i] = nbw[i];
+                for (int i = 1; i < 5; ++i) wnb[side][r][i] = nbw[i] * (float)Store::kSS;
 #pragma unroll
-                for (int i = 0; i < 5; ++i) wnb[side][r][5 + i] = gbw[i];
+                for (int i = 1; i < 5; ++i) wnb[side][r][5 + i] = gbw[i] * (float)Store::kSS;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) wnb[side][r][10 + i] = hbw[i];
+                for (int i = 0; i < 9; ++i) wnb[side][r][10 + i] = hbw[i] * (float)Store::kSF;
             }
         }
         if (xwall_tile) __syncthreads();  // keeps the loads below after the repair
@@ -341,7 +347,7 @@ __device__ __forceinline__ void coupled_tile(const StepParams& P, const void* __
 #pragma unroll
     for (int i = 1; i < 5; ++i) Store::load_pair(src, i, o, n[i], g[i]);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = Store::load(src, srcf, kH + i, o, P);
+    for (int i = 0; i < 9; ++i) h[i] = Store::load_flow(srcf, i, o);
     const float* hn = hist;
     const float phi_prev = hist_at(hn, 0, o);
     const float Q_prev = hist_at(hn, 1, o);
@@ -581,7 +587,7 @@ __global__ void __launch_bounds__(256, 8) k_flow_substep(const StepParams P, con
     m.uy = usy + 0.5f * (1.0f - qt) * m.fsy;
     m.p = 0.6f * (rest - (2.0f / 3.0f) * (m.ux * m.ux + m.uy * m.uy));
     float ho[9];
-    collide_flow(h, m, P.s2u, ho);
+    collide_flow<1, Store::kSF>(h, m, P.s2u, ho);
     const int xp = (x + 1 == P.nx) ? 0 : x + 1, xm = (x == 0) ? P.nx - 1 : x - 1;
     const int yp = (y + 1 == P.ny) ? 0 : y + 1, ym = (y == 0) ? P.ny - 1 : y - 1;
     const long long rY = Store::flow_row(y, P), rP = Store::flow_row(yp, P), rM = Store::flow_row(ym, P);
