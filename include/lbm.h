@@ -215,6 +215,19 @@ LBM_API long long lbm_step_count(const lbm_handle* h);
  * copied.  Synchronous. */
 LBM_API int lbm_get_fields(lbm_handle* h, unsigned mask, double* out);
 
+/* The same fields in FP32, the precision the device computes them in: `out`
+ * receives nx*ny floats per selected field, in increasing field order (the
+ * macros of Eqs. 15, 20, 23 and 26 as for lbm_get_fields, each rounded once
+ * to FP32 from deviation * scale + offset).  The fields are formed on the
+ * device band by band.  Page-locked `out` (cudaHostAlloc, cudaHostRegister)
+ * receives each band's planes straight from the device, at the host link's
+ * rate, and no host thread touches the values; pageable `out` receives them
+ * through the pinned staging buffer lbm_get_fields uses, copied on up to 16
+ * host threads while the next band crosses.  Synchronous; the caller owns
+ * `out`.  LBM_EINVAL for a NULL out or an unknown mask bit, LBM_ENOMEM when
+ * the staging buffer cannot be allocated. */
+LBM_API int lbm_get_fields_f32(lbm_handle* h, unsigned mask, float* out);
+
 /* FP64 copy of the decoded state: LBM_STATE_PLANES planes of nx*ny
  * (populations in lattice units, history as stored).  Synchronous. */
 LBM_API int lbm_get_state(lbm_handle* h, double* out);

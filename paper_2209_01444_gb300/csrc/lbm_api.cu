@@ -387,15 +387,36 @@ int graph_for(lbm_handle* h, cudaGraphExec_t* out)
     return LBM_OK;
 }
 
-// Pinned host staging buffer of lbm_get_fields, shared by every handle of the
-// process (at most 2 x kPinHalf bytes, allocated on first use, kept until
-// exit); a call holds the mutex while it uses it.
+// Pinned host staging buffer of lbm_get_fields (and of lbm_get_fields_f32 into
+// pageable memory), shared by every handle of the process (at most 2 x
+// kPinHalf bytes, allocated on first use, kept until exit); a call holds the
+// mutex while it uses it.
 constexpr size_t kPinHalf = (size_t)32 << 20;
 struct PinnedStaging {
     std::mutex mu;
     float* p = nullptr;
     size_t bytes = 0;
 } g_pinned;
+
+// The shared staging buffer, grown to at least `bytes`; the caller holds
+// g_pinned.mu for as long as it uses the buffer.  Null (with h's error set)
+// when page-locked memory cannot be had.
+float* staging_buffer(lbm_handle* h, size_t bytes)
+{
+    if (g_pinned.bytes < bytes) {
+        if (g_pinned.p) cudaFreeHost(g_pinned.p);
+        g_pinned.p = nullptr;
+        g_pinned.bytes = 0;
+        cudaError_t e = cudaHostAlloc((void**)&g_pinned.p, bytes, cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(h, LBM_ENOMEM, std::string("pinned band buffer: ") + cudaGetErrorString(e));
+            return nullptr;
+        }
+        g_pinned.bytes = bytes;
+    }
+    return g_pinned.p;
+}
 
 // Runs fn(r0, r1) over the row range [0, rows) on up to 16 host threads.
 template <class Fn>
@@ -768,18 +789,8 @@ int lbm_get_fields(lbm_handle* h, unsigned mask, double* out)
     rows = std::max(1, std::min<int>(rows, (int)(kPinHalf / ((size_t)pitch * nsel * sizeof(float)))));
     const size_t half = (size_t)rows * pitch * nsel;
     std::lock_guard<std::mutex> lock(g_pinned.mu);
-    if (g_pinned.bytes < 2 * half * sizeof(float)) {
-        if (g_pinned.p) cudaFreeHost(g_pinned.p);
-        g_pinned.p = nullptr;
-        g_pinned.bytes = 0;
-        cudaError_t e = cudaHostAlloc((void**)&g_pinned.p, 2 * half * sizeof(float), cudaHostAllocPortable);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(h, LBM_ENOMEM, std::string("pinned band buffer: ") + cudaGetErrorString(e));
-        }
-        g_pinned.bytes = 2 * half * sizeof(float);
-    }
-    float* pin = g_pinned.p;
+    float* pin = staging_buffer(h, 2 * half * sizeof(float));
+    if (!pin) return LBM_ENOMEM;
     for (cudaEvent_t& e : h->pin_ev)
         if (!e) LBM_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     auto convert = [&](int y0, int r, const float* src) {
@@ -816,6 +827,84 @@ int lbm_get_fields(lbm_handle* h, unsigned mask, double* out)
     }
     LBM_CUDA(h, cudaEventSynchronize(h->pin_ev[slot ^ 1]));
     convert(prev_y0, prev_r, pin + (size_t)(slot ^ 1) * half);
+    return LBM_OK;
+}
+
+int lbm_get_fields_f32(lbm_handle* h, unsigned mask, float* out)
+{
+    int rc = ensure_initialised(h);
+    if (rc) return rc;
+    if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+    if (mask >> LBM_NUM_FIELDS) return fail(h, LBM_EINVAL, "unknown field bit");
+    const int nx = h->P.nx, ny = h->P.ny;
+    // device planes hold phi + 1, C - 1, U, theta - theta_ref, ux, uy, p
+    const double scale[LBM_NUM_FIELDS] = {1, 1, 1, 1, 1.0 / h->vf, 1.0 / h->vf, h->pscale};
+    const double offset[LBM_NUM_FIELDS] = {-1.0, 1.0, 0, (double)h->P.theta_ref, 0, 0, 0};
+    lbm::FieldsF32 spec{};
+    for (int q = 0; q < LBM_NUM_FIELDS; ++q)
+        if (mask & (1u << q)) {
+            spec.sel[spec.n] = q;
+            spec.scale[spec.n] = (float)scale[q];
+            spec.offset[spec.n] = (float)offset[q];
+            ++spec.n;
+        }
+    if (!spec.n) return LBM_OK;
+    int rows;
+    if ((rc = band_rows(h, spec.n * sizeof(float), &rows))) return rc;
+    float* dev = (float*)h->scratch;
+    // page-locked output takes the copies directly; pageable output goes through
+    // the pinned staging halves, a host copy of one band overlapping the next
+    cudaPointerAttributes at{};
+    const bool locked = cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    std::unique_lock<std::mutex> lock(g_pinned.mu, std::defer_lock);
+    float* pin = nullptr;
+    size_t half = 0;
+    if (!locked) {
+        rows = std::max(1, std::min<int>(rows, (int)(kPinHalf / ((size_t)nx * spec.n * sizeof(float)))));
+        half = (size_t)rows * nx * spec.n;
+        lock.lock();
+        if (!(pin = staging_buffer(h, 2 * half * sizeof(float)))) return LBM_ENOMEM;
+        for (cudaEvent_t& e : h->pin_ev)
+            if (!e) LBM_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    auto unstage = [&](int y0, int r, const float* src) {
+        const size_t band = (size_t)r * nx;
+        parallel_rows(r, [&](int r0, int r1) {
+            for (int k = 0; k < spec.n; ++k)
+                memcpy(out + (size_t)k * nx * ny + (size_t)(y0 + r0) * nx, src + k * band + (size_t)r0 * nx,
+                       (size_t)(r1 - r0) * nx * sizeof(float));
+        });
+    };
+    int prev_y0 = -1, prev_r = 0, slot = 0;
+    for (int y0 = 0; y0 < ny; y0 += rows, slot ^= 1) {
+        const int r = std::min(rows, ny - y0);
+        const size_t band = (size_t)r * nx;
+        LBM_CUDA(h, lbm::launch_fields_f32(h->P, h->storage, h->B.sc[h->B.cs], h->B.fl[h->B.cf], spec, dev, y0, r,
+                                           h->stream));
+        if (locked) {
+            // plane k of the band is one contiguous run of the caller's array
+            for (int k = 0; k < spec.n; ++k)
+                LBM_CUDA(h, cudaMemcpyAsync(out + (size_t)k * nx * ny + (size_t)y0 * nx, dev + k * band,
+                                            band * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+            continue;
+        }
+        LBM_CUDA(h, cudaMemcpyAsync(pin + (size_t)slot * half, dev, band * spec.n * sizeof(float),
+                                    cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(h, cudaEventRecord(h->pin_ev[slot], h->stream));
+        if (prev_y0 >= 0) {
+            LBM_CUDA(h, cudaEventSynchronize(h->pin_ev[slot ^ 1]));
+            unstage(prev_y0, prev_r, pin + (size_t)(slot ^ 1) * half);
+        }
+        prev_y0 = y0;
+        prev_r = r;
+    }
+    if (locked) {
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        return LBM_OK;
+    }
+    LBM_CUDA(h, cudaEventSynchronize(h->pin_ev[slot ^ 1]));
+    unstage(prev_y0, prev_r, pin + (size_t)(slot ^ 1) * half);
     return LBM_OK;
 }
 

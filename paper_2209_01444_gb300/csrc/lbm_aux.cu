@@ -265,6 +265,32 @@ __global__ void k_macros(const StepParams P, const void* __restrict__ sc, const 
     out[6 * bp + ob] = m.p;
 }
 
+// The selected fields of the rows [y0, y0 + rows) in their final FP32 form,
+// plane k of the band at out + k * rows * nx with rows of nx values (the
+// layout of the caller's array, so each plane of the band is one contiguous
+// copy): field = deviation * scale + offset, the deviations of k_macros.
+template <class Store>
+__global__ void k_fields_f32(const StepParams P, const void* __restrict__ sc, const void* __restrict__ fl,
+                             const FieldsF32 spec, float* __restrict__ out, int y0, int rows)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= y0 + rows || y >= P.ny) return;
+    const long long o = (long long)y * P.pitch + x;
+    float f[5], n[5], g[5], h[9];
+    load_node<Store>(P, sc, fl, o, f, n, g, h);
+    const Macro m = node_macros(f, n, g, h, P);
+    const float v[7] = {m.p1, m.dC, m.U, m.dth, m.ux, m.uy, m.p};
+    const long long ob = (long long)(y - y0) * P.nx + x, bp = (long long)rows * P.nx;
+    for (int k = 0; k < spec.n; ++k) {
+        float d = v[0];
+#pragma unroll
+        for (int q = 1; q < 7; ++q)
+            if (spec.sel[k] == q) d = v[q];
+        out[k * bp + ob] = fmaf(d, spec.scale[k], spec.offset[k]);
+    }
+}
+
 // Deviations of every population as FP32 band planes 0..23 and the history
 // as planes 24..29 (and back).
 template <class Store>
@@ -551,6 +577,15 @@ cudaError_t macros_t(const StepParams& P, const void* sc, const void* fl, float*
 }
 
 template <class Store>
+cudaError_t fields_f32_t(const StepParams& P, const void* sc, const void* fl, const FieldsF32& spec, float* out,
+                         int y0, int rows, cudaStream_t s)
+{
+    const dim3 b(64, 4), g((P.nx + 63) / 64, (rows + 3) / 4);
+    k_fields_f32<Store><<<g, b, 0, s>>>(P, sc, fl, spec, out, y0, rows);
+    return cudaGetLastError();
+}
+
+template <class Store>
 cudaError_t decode_t(const StepParams& P, const void* sc, const void* fl, const float* hist, float* out, int y0,
                      int rows, cudaStream_t s)
 {
@@ -673,6 +708,16 @@ cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, cons
     case kStoreF16: return macros_t<StoreF16>(P, sc, fl, out, y0, rows, s);
     case kStoreBF16: return macros_t<StoreBF16>(P, sc, fl, out, y0, rows, s);
     default: return macros_t<StoreF32>(P, sc, fl, out, y0, rows, s);
+    }
+}
+
+cudaError_t launch_fields_f32(const StepParams& P, int storage, const void* sc, const void* fl,
+                              const FieldsF32& spec, float* out, int y0, int rows, cudaStream_t s)
+{
+    switch (storage) {
+    case kStoreF16: return fields_f32_t<StoreF16>(P, sc, fl, spec, out, y0, rows, s);
+    case kStoreBF16: return fields_f32_t<StoreBF16>(P, sc, fl, spec, out, y0, rows, s);
+    default: return fields_f32_t<StoreF32>(P, sc, fl, spec, out, y0, rows, s);
     }
 }
 

@@ -109,6 +109,16 @@ cudaError_t launch_count_nonfinite(const float* a, long long n, unsigned long lo
 // ux, uy, p; lattice units).
 cudaError_t launch_macros(const StepParams& P, int storage, const void* sc, const void* fl, float* out, int y0,
                           int rows, cudaStream_t s);
+// Fields of a band in their final FP32 form: field k (of n) is the macro
+// plane sel[k] of launch_macros times scale[k] plus offset[k], written at
+// out + k * rows * nx in rows of nx values.
+struct FieldsF32 {
+    int n;
+    int sel[7];
+    float scale[7], offset[7];
+};
+cudaError_t launch_fields_f32(const StepParams& P, int storage, const void* sc, const void* fl,
+                              const FieldsF32& spec, float* out, int y0, int rows, cudaStream_t s);
 
 // Decode a band's populations and history to FP32 band planes (24
 // population deviations, then the kHist history values) / encode them back.

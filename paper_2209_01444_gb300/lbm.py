@@ -72,6 +72,7 @@ SIGNATURES = {
     "lbm_synchronize": (ct.c_int, [_H]),
     "lbm_step_count": (ct.c_longlong, [_H]),
     "lbm_get_fields": (ct.c_int, [_H, ct.c_uint, _DP]),
+    "lbm_get_fields_f32": (ct.c_int, [_H, ct.c_uint, ct.c_void_p]),
     "lbm_get_state": (ct.c_int, [_H, _DP]),
     "lbm_get_state_region": (ct.c_int, [_H, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _DP]),
     "lbm_set_state": (ct.c_int, [_H, _DP]),
@@ -292,6 +293,20 @@ class Simulation:
         order = [n for n in FIELDS if mask & (1 << FIELDS.index(n))]
         out = np.empty((len(order), self.ny, self.nx))
         self._check(self.lib.lbm_get_fields(self.h, mask, _dptr(out)))
+        return {n: out[i] for i, n in enumerate(order)}
+
+    def fields_f32(self, names=FIELDS, out=None) -> dict:
+        """FP32 fields through lbm_get_fields_f32; `out` (float32, C order,
+        [len(names), ny, nx]) may be page-locked memory the caller keeps."""
+        mask = 0
+        for n in names:
+            mask |= 1 << FIELDS.index(n)
+        order = [n for n in FIELDS if mask & (1 << FIELDS.index(n))]
+        if out is None:
+            out = np.empty((len(order), self.ny, self.nx), np.float32)
+        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == len(order) * self.ny * self.nx
+        out = out.reshape(len(order), self.ny, self.nx)
+        self._check(self.lib.lbm_get_fields_f32(self.h, mask, ct.c_void_p(out.ctypes.data)))
         return {n: out[i] for i, n in enumerate(order)}
 
     def state(self) -> np.ndarray:

@@ -60,6 +60,38 @@ def test_one_row_bands_equal_the_default(lbm, storage):
     np.testing.assert_array_equal(*seeded)
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_fp32_fields_are_the_fp64_fields_rounded(lbm, storage):
+    """lbm_get_fields_f32 on a 45 x 37 grid (row pitch 64): phi, C, U and theta
+    (offsets of -1, +1, 0 and theta_ref added to FP32 deviations) are the FP64
+    fields rounded to FP32 exactly; u_x, u_y and p carry one more rounding (of
+    their FP32 scale factor), within 2 units in the last place.  One-row bands,
+    page-locked output and a subset of the fields give the same values."""
+    import torch
+
+    nx, ny = 45, 37
+    p = W.thermosolutal_params(nx, ny, bc=("inflow", "outflow", "noslip", "symmetry"), u_in=(0.15, 0.02),
+                               gbetaT=W.GBETA_T * 5, theta_ref=-0.5, dir_theta=-0.4)
+    f, orient = W.random_fields(nx, ny, rng_seed=78)
+    s = lbm.Simulation(p, storage)
+    s.init_fields(f, orient)
+    s.step(11)
+    want = s.fields()
+    got = s.fields_f32()  # pageable output, default bands
+    for k in ("phi", "C", "U", "theta"):
+        np.testing.assert_array_equal(got[k], want[k].astype(np.float32), err_msg=k)
+    for k in ("ux", "uy", "p"):
+        np.testing.assert_array_max_ulp(got[k], want[k].astype(np.float32), maxulp=2)
+    pinned = torch.empty((2, ny, nx), dtype=torch.float32, pin_memory=True).numpy()
+    s.set_io_chunk(1)
+    for out in (pinned, None):  # page-locked: direct copies; pageable: staged, one row per band
+        sub = s.fields_f32(("uy", "theta"), out=out)
+        assert list(sub) == ["theta", "uy"]
+        np.testing.assert_array_equal(sub["theta"], got["theta"])
+        np.testing.assert_array_equal(sub["uy"], got["uy"])
+    np.testing.assert_array_equal(pinned[1], got["uy"])
+
+
 def test_largest_grid_that_fits(lbm):
     """FP16 storage on the largest square grid within 75 % of the free device
     memory (below 2^31 nodes): seeds, 4 steps and the metrics, all on the
