@@ -197,6 +197,27 @@ constexpr int stages_for()
     return n < 2 ? 2 : n > 8 ? 8 : n;
 }
 
+// Row-reuse form of the implicit 3 x 3 convolution: per stage and sub-tile
+// one box of the 128 + 2 pixels of one input row around the sub-tile's 128
+// output pixels, kept in a region of kRow3Rows rows (a whole number of swizzle
+// patterns), and the three weight tiles of that row's taps.
+constexpr int kRow3Rows = 136;
+
+template <int BK, int BN, int MT, bool ROW3>
+constexpr int ws_stage_bytes()
+{
+    return ROW3 ? MT * kRow3Rows * BK * 2 + 3 * BN * BK * 2 : (MT * kBM + BN) * BK * 2;
+}
+
+// Ring depth of the persistent kernel: as many stages as fit in about 200 KB,
+// 2 to 8.
+template <int BK, int BN, int MT, bool ROW3>
+constexpr int ws_stages()
+{
+    constexpr int n = (200 * 1024) / ws_stage_bytes<BK, BN, MT, ROW3>();
+    return n < 2 ? 2 : n > 8 ? 8 : n;
+}
+
 // Ring depth of the split-K kernel.  Narrow tiles (N <= 64) take at most 4
 // stages (about 80 KB), so that two CTAs share an SM: their one issuing thread
 // waits on load latency, and two CTAs keep twice the loads in flight (measured:
@@ -216,6 +237,7 @@ struct ConvGeo {
     int W = 0, H = 0;      // image size; W == 0: plain 2-D A operand
     int C = 0;             // input channels (a multiple of BK)
     int cblocks = 0;       // C / BK
+    int row3 = 0;          // the A map's box is kBM + 2 pixels of one row (row-reuse form)
 };
 struct ShuffleGeo {
     int Wl = 0, Hl = 0;    // low-resolution image; Wl == 0: plain row-major store
@@ -575,16 +597,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int BN, bool OUT_BF16, int BK, bool CONV, int MT>
+template <int BN, bool OUT_BF16, int BK, bool CONV, int MT, bool ROW3 = false>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, void* __restrict__ D,
               const float* __restrict__ bias, int M, int N, int K, int ldd, int relu, ConvGeo geo, ShuffleGeo sh,
               int tiles_m, int tiles)
 {
-    constexpr int S = stages_for<BK, BN, MT>();
-    constexpr int A_BYTES = kBM * BK * 2;          // one 128-row sub-tile
+    static_assert(!ROW3 || CONV, "row reuse is a form of the implicit convolution");
+    constexpr int S = ws_stages<BK, BN, MT, ROW3>();
+    constexpr int A_BYTES = ROW3 ? kRow3Rows * BK * 2 : kBM * BK * 2;  // one sub-tile's A region
     constexpr int B_BYTES = BN * BK * 2;
-    constexpr int STAGE = MT * A_BYTES + B_BYTES;
+    constexpr int NB = ROW3 ? 3 : 1;               // weight tiles per stage
+    constexpr int STAGE = MT * A_BYTES + NB * B_BYTES;
+    static_assert(STAGE == ws_stage_bytes<BK, BN, MT, ROW3>(), "stage layout");
+    // bytes the TMA delivers per stage (ROW3: boxes of kBM + 2 rows)
+    constexpr int TX = ROW3 ? MT * (kBM + 2) * BK * 2 + NB * B_BYTES : STAGE;
     constexpr uint32_t SUB_COLS = BN < 32 ? 32 : BN;
     constexpr uint32_t ACC_COLS = MT * SUB_COLS;
     constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
@@ -601,7 +628,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     int* counts = (int*)(tmem_slot + 2);  // [0] loads issued, [1] k blocks consumed
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (K + BK - 1) / BK;
+    // k blocks: ROW3 takes the three taps of one input row per block
+    const int nk = ROW3 ? 3 * geo.cblocks : (K + BK - 1) / BK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -652,8 +680,18 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     if (it >= S && !(ok = mbar_wait_abort(&empty[st], (uint32_t)((it / S - 1) & 1), abort_flag)))
                         break;
                     uint8_t* a = smem + st * STAGE;
-                    mbar_expect_tx(&full[st], STAGE);
-                    if constexpr (CONV) {
+                    mbar_expect_tx(&full[st], TX);
+                    if constexpr (ROW3) {
+                        // input row y + ky - 1, pixels x0 - 1 .. x0 + kBM (zero filled outside the image)
+                        const int ky = kb / geo.cblocks, cb = kb - ky * geo.cblocks;
+#pragma unroll
+                        for (int i = 0; i < MT; ++i)
+                            tma_load_4d(a + i * A_BYTES, &tmA, cb * BK, x0[i] - 1, y0[i] + ky - 1, b0[i], &full[st]);
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx)
+                            tma_load_2d(a + MT * A_BYTES + kx * B_BYTES, &tmB, (3 * ky + kx) * geo.C + cb * BK, n0,
+                                        &full[st]);
+                    } else if constexpr (CONV) {
                         const int tap = kb / geo.cblocks, cb = kb - tap * geo.cblocks;
                         const int ky = tap / 3, kx = tap - 3 * ky;
 #pragma unroll
@@ -685,12 +723,26 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     if (!(ok = mbar_wait_operands_abort(&full[st], (uint32_t)((it / S) & 1), abort_flag))) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = smem_u32(smem + st * STAGE), b0s = a0 + MT * A_BYTES;
+                    if constexpr (ROW3) {
+                        // tap kx reads the row box from pixel kx on: its A tile starts kx rows in
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
+                        for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
-                        for (int i = 0; i < MT; ++i)
-                            umma(d + (uint32_t)(i * SUB_COLS), tile_desc<BK>(a0 + i * A_BYTES + k * 32),
-                                 tile_desc<BK>(b0s + k * 32), IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                            for (int k = 0; k < BK / 16; ++k)
+#pragma unroll
+                                for (int i = 0; i < MT; ++i)
+                                    umma(d + (uint32_t)(i * SUB_COLS),
+                                         tile_desc<BK>(a0 + i * A_BYTES + kx * BK * 2 + k * 32),
+                                         tile_desc<BK>(b0s + kx * B_BYTES + k * 32), IDESC,
+                                         (kb > 0 || kx > 0 || k > 0) ? 1u : 0u);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < BK / 16; ++k)
+#pragma unroll
+                            for (int i = 0; i < MT; ++i)
+                                umma(d + (uint32_t)(i * SUB_COLS), tile_desc<BK>(a0 + i * A_BYTES + k * 32),
+                                     tile_desc<BK>(b0s + k * 32), IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                    }
                     umma_commit(&empty[st]);
                     counts[1] = it + 1;
                 }
@@ -862,30 +914,31 @@ cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, void* D, const
     return cudaGetLastError();
 }
 
-template <int BN, bool OUT_BF16, int BK, bool CONV, int MT>
+template <int BN, bool OUT_BF16, int BK, bool CONV, int MT, bool ROW3>
 cudaError_t launch_ws_mt(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
                          int ldd, int relu, const ConvGeo& geo, const ShuffleGeo& sh, cudaStream_t s)
 {
-    constexpr int smem = stages_for<BK, BN, MT>() * (MT * kBM * BK * 2 + BN * BK * 2) + 1024 + 256;
+    constexpr int smem = ws_stages<BK, BN, MT, ROW3>() * ws_stage_bytes<BK, BN, MT, ROW3>() + 1024 + 256;
+    static_assert(smem <= 227 * 1024, "shared memory per CTA");
     static int per_sm = 0, sms = 0;
     if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_ws<BN, OUT_BF16, BK, CONV, MT>,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_ws<BN, OUT_BF16, BK, CONV, MT, ROW3>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         int dev = 0;
         if ((e = cudaGetDevice(&dev))) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
         int occ = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gemm_ws<BN, OUT_BF16, BK, CONV, MT>, kWsThreads,
-                                                               smem)))
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gemm_ws<BN, OUT_BF16, BK, CONV, MT, ROW3>,
+                                                               kWsThreads, smem)))
             return e;
         per_sm = occ < 1 ? 1 : occ;
     }
     const int tiles_m = (M + kBM * MT - 1) / (kBM * MT);
     const int tiles = tiles_m * ((N + BN - 1) / BN);
     const int grid = tiles < sms * per_sm ? tiles : sms * per_sm;
-    k_gemm_ws<BN, OUT_BF16, BK, CONV, MT><<<grid, kWsThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu, geo, sh,
-                                                                         tiles_m, tiles);
+    k_gemm_ws<BN, OUT_BF16, BK, CONV, MT, ROW3><<<grid, kWsThreads, smem, s>>>(a, b, D, bias, M, N, K, ldd, relu, geo,
+                                                                               sh, tiles_m, tiles);
     return cudaGetLastError();
 }
 
@@ -905,19 +958,32 @@ int sm_count()
 // Sub-tiles per tile: narrow tiles stack 128-row sub-tiles that share each
 // weight tile (four for N = 32 with 32-channel K blocks, two up to N = 128),
 // unless that leaves fewer tiles than SMs.
-template <int BN, bool OUT_BF16, int BK, bool CONV>
-cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
-                      int ldd, int relu, const ConvGeo& geo, const ShuffleGeo& sh, cudaStream_t s)
+template <int BN, bool OUT_BF16, int BK, bool CONV, bool ROW3>
+cudaError_t launch_ws_rows(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N,
+                           int K, int ldd, int relu, const ConvGeo& geo, const ShuffleGeo& sh, cudaStream_t s)
 {
     sm_count();
     constexpr int MTMAX = (BN <= 32 && BK == 32) ? 4 : BN <= 128 ? 2 : 1;
     const long long ntiles_n = (N + BN - 1) / BN;
     auto fills = [&](int mt) { return (M + 128LL * mt - 1) / (128LL * mt) * ntiles_n >= g_sms; };
     if constexpr (MTMAX == 4)
-        if (fills(4)) return launch_ws_mt<BN, OUT_BF16, BK, CONV, 4>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
+        if (fills(4))
+            return launch_ws_mt<BN, OUT_BF16, BK, CONV, 4, ROW3>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
     if constexpr (MTMAX >= 2)
-        if (fills(2)) return launch_ws_mt<BN, OUT_BF16, BK, CONV, 2>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
-    return launch_ws_mt<BN, OUT_BF16, BK, CONV, 1>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
+        if (fills(2))
+            return launch_ws_mt<BN, OUT_BF16, BK, CONV, 2, ROW3>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
+    return launch_ws_mt<BN, OUT_BF16, BK, CONV, 1, ROW3>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
+}
+
+// Row reuse (geo.row3, set by conv3x3_bf16 with its matching A map) serves
+// tiles up to 64 columns: wider ones would leave a ring of two stages.
+template <int BN, bool OUT_BF16, int BK, bool CONV>
+cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& b, void* D, const float* bias, int M, int N, int K,
+                      int ldd, int relu, const ConvGeo& geo, const ShuffleGeo& sh, cudaStream_t s)
+{
+    if constexpr (CONV && BN <= 64)
+        if (geo.row3) return launch_ws_rows<BN, OUT_BF16, BK, CONV, true>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
+    return launch_ws_rows<BN, OUT_BF16, BK, CONV, false>(a, b, D, bias, M, N, K, ldd, relu, geo, sh, s);
 }
 
 // Widest tile that N allows: narrower tiles with more CTAs re-read A and
@@ -1199,8 +1265,11 @@ cudaError_t conv3x3_bf16(const void* X, int B, int H, int W, int C, int cpitch, 
         return cudaErrorInvalidValue;
     if (((uintptr_t)X | (uintptr_t)Wm | (uintptr_t)D) & 15) return cudaErrorInvalidValue;
     const int bn = bn_for(N);
+    // rows of at least 256 pixels: each stage loads one box of 130 pixels of
+    // an input row and serves its three taps from it
+    const bool row3 = bw == kBM && W >= 2 * kBM && bn <= 64;
     CUtensorMap ta, tb;
-    cudaError_t e = make_map_4d(&ta, X, B, H, W, C, cpitch, bw, bh, bb, bk);
+    cudaError_t e = make_map_4d(&ta, X, B, H, W, C, cpitch, row3 ? kBM + 2 : bw, bh, bb, bk);
     if (e == cudaSuccess) e = make_map(&tb, Wm, N, 9 * C, ldw, bn, bk);
     if (e != cudaSuccess) return e;
     ConvGeo geo;
@@ -1208,6 +1277,7 @@ cudaError_t conv3x3_bf16(const void* X, int B, int H, int W, int C, int cpitch, 
     geo.H = H;
     geo.C = C;
     geo.cblocks = C / bk;
+    geo.row3 = row3 ? 1 : 0;
     const int M = B * H * W, K = 9 * C;
     ShuffleGeo sh;
     sh.mask = (const __nv_bfloat16*)mask;

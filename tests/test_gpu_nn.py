@@ -309,13 +309,19 @@ def test_pack_unpack_cast(env):
 
 @pytest.mark.parametrize("B,H,W,C,cp,N", [(2, 16, 16, 32, 32, 32), (1, 8, 256, 64, 128, 128), (3, 8, 8, 64, 64, 72),
                                           (1, 4, 4, 96, 96, 64), (2, 32, 32, 128, 128, 256), (1, 2, 2, 512, 512, 512),
-                                          (4, 64, 64, 32, 64, 40)])
+                                          (4, 64, 64, 32, 64, 40),
+                                          # row reuse (rows of >= 256 pixels, N <= 64): one or two sub-tiles,
+                                          # four 32-channel sub-tiles, two 64-channel ones
+                                          (1, 6, 256, 32, 40, 64), (2, 4, 512, 64, 64, 40),
+                                          (1, 160, 512, 32, 32, 32), (1, 80, 512, 64, 72, 64)])
 @pytest.mark.parametrize("out_fp32", [1, 0])
 def test_implicit_conv3x3_matches_fp64_conv2d(env, B, H, W, C, cp, N, out_fp32):
     """The implicit convolution (4-D TMA tap shifts, zero padding from the
     out-of-bounds fill) against a CPU FP64 conv2d of the same BF16 values,
     over tiles of whole rows, several rows and several images, 64- and 32-
-    channel K blocks, channel pitches wider than C and ragged N."""
+    channel K blocks, channel pitches wider than C and ragged N; on rows of
+    256 pixels or more with N <= 64, the row-reuse form (one box of 130
+    pixels per input row serving its three taps)."""
     torch, lib = env
     g = torch.Generator(device="cuda").manual_seed(B * 1000 + H * 10 + C + N)
     X = _bf(torch, (B, H, W, cp), g)
