@@ -103,3 +103,19 @@ def test_create_rejects_unpaired_periodic_walls(lib):
     h = ct.c_void_p()
     assert lib.lbm_create(ct.byref(p), ct.byref(h)) == lbm.LBM_EINVAL
     assert "periodicity" in lib.lbm_last_error(None).decode()
+
+
+def test_null_handle_is_refused_without_touching_the_device(lib):
+    """Entry points given no handle return LBM_EINVAL before any CUDA call
+    (each checks the handle first), so a caller's mistake costs no device
+    state."""
+    from paper_2209_01444_gb300 import lbm
+
+    buf = (ct.c_double * 4)()
+    fbuf = (ct.c_float * 4)()
+    assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_synchronize(None) == lbm.LBM_EINVAL
+    assert lib.lbm_set_io_chunk(None, 1 << 20) == lbm.LBM_EINVAL
+    assert lib.lbm_get_fields(None, 1, ct.cast(buf, ct.POINTER(ct.c_double))) == lbm.LBM_EINVAL
+    assert lib.lbm_get_fields_f32(None, 1, ct.cast(fbuf, ct.c_void_p)) == lbm.LBM_EINVAL
+    assert lib.lbm_get_state(None, ct.cast(buf, ct.POINTER(ct.c_double))) == lbm.LBM_EINVAL
