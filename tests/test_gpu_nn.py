@@ -313,7 +313,7 @@ def test_pack_unpack_cast(env):
                                           # row reuse (rows of >= 256 pixels, N <= 64): one or two sub-tiles,
                                           # four 32-channel sub-tiles, two 64-channel ones
                                           (1, 6, 256, 32, 40, 64), (2, 4, 512, 64, 64, 40),
-                                          (1, 160, 512, 32, 32, 32), (1, 80, 512, 64, 72, 64)])
+                                          (1, 160, 512, 32, 32, 32), (1, 80, 512, 64, 72, 64), (2, 3, 256, 32, 32, 16)])
 @pytest.mark.parametrize("out_fp32", [1, 0])
 def test_implicit_conv3x3_matches_fp64_conv2d(env, B, H, W, C, cp, N, out_fp32):
     """The implicit convolution (4-D TMA tap shifts, zero padding from the

@@ -155,13 +155,16 @@ def test_gradients_match_oracle(env, levels, B, H, tol):
             assert rel <= tol, (name, rel)
 
 
-@pytest.mark.parametrize("levels,B,H,active,tol", [(2, 2, 64, False, 2e-2), (3, 1, 128, True, 1.5e-2)])
+@pytest.mark.parametrize("levels,B,H,active,tol", [(2, 2, 64, False, 2e-2), (3, 1, 128, True, 1.5e-2),
+                                                    (2, 1, 256, False, 2e-2)])
 def test_gradients_with_the_three_copy_weight_gradient_match_oracle(env, levels, B, H, active, tol):
-    """Image widths of 32 to 128 and channel counts of 32 to 256, so that
+    """Image widths of 32 to 256 and channel counts of 32 to 256, so that
     every convolution with a multiple of 32 input channels takes its weight
     gradient from three shifted copies of its input (boxes of 32, 64 and 128
-    rows, 32- and 64-pixel K blocks): every parameter gradient against the
-    oracle with the same rounding points."""
+    rows, 32- and 64-pixel K blocks), and at 256 pixels the level-0
+    convolutions and their ReLU-masked input gradients take the row-reuse
+    form: every parameter gradient against the oracle with the same rounding
+    points."""
     torch, lib, S = env
     err = _grad_errors(S, torch, levels, B, H, 50 + levels, active=active)
     assert lib.lbm_nn_error(1) == 0
