@@ -534,7 +534,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 // the epilogue of one tile overlaps the main loop of the next.  Every wait is
 // bounded; a wait that runs out raises the error flag and a shared abort flag
 // that makes the other roles stop, then the CTA drains its copies and MMAs
-// (bounded) and frees its TMEM.
+// (bounded) and frees its TMEM.  For an implicit 3 x 3 convolution a stage is
+// one (tap, channel block) pair, or, in the row-reuse form (ROW3), one (input
+// row, channel block) pair whose box serves the row's three taps.
 constexpr int kWsThreads = 192;
 
 __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
