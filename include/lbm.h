@@ -185,7 +185,9 @@ LBM_API int lbm_init_fields(lbm_handle* h, const double* fields, const double* o
  * from captured 16-step CUDA graphs; inside one (n_sub = 1) the
  * left/right walls of a step are updated by the next step as it loads them,
  * and the last step of the graph runs the wall kernels in full, so the state
- * seen between calls is always complete. */
+ * seen between calls is always complete.  The graph is captured,
+ * instantiated and uploaded when a state is set (lbm_init_seeds,
+ * lbm_init_fields, lbm_load_state), so the first lbm_step pays none of it. */
 LBM_API int lbm_step(lbm_handle* h, int nsteps);
 
 /* Wait for all queued work of h; reports an asynchronous CUDA error. */

@@ -288,6 +288,19 @@ int decode_rows(lbm_handle* h, int y0, int hgt, Deliver deliver)
     return LBM_OK;
 }
 
+int graph_for(lbm_handle* h, cudaGraphExec_t* out);
+
+// The step graph of the current buffer parity, built when a state is set so
+// that its capture, instantiation and upload belong to initialisation, not to
+// the first lbm_step.  Best effort: a capture that fails here is retried, and
+// reported, by lbm_step.
+void prebuild_graph(lbm_handle* h)
+{
+    if (h->profiling) return;
+    cudaGraphExec_t ex;
+    if (graph_for(h, &ex) != LBM_OK || cudaGraphUpload(ex, h->stream) != cudaSuccess) cudaGetLastError();
+}
+
 // Initial state, band by band: fill(y0, rows, fields) writes the band's six
 // FP64 macro planes (lattice units) into `fields`, then the equilibrium
 // populations and the history of those rows follow from them.
@@ -309,6 +322,7 @@ int init_bands(lbm_handle* h, Fill fill)
     }
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->initialised = true;
+    prebuild_graph(h);
     return LBM_OK;
 }
 
@@ -1092,6 +1106,7 @@ int lbm_load_state(lbm_handle* h, const void* host, size_t bytes)
     h->B.grain = h->uniform ? nullptr : h->grain;
     h->steps = hd.steps;
     h->initialised = true;
+    prebuild_graph(h);
     return LBM_OK;
 }
 
