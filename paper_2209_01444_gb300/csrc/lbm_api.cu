@@ -17,6 +17,7 @@
 
 #include "lbm.h"
 #include "lbm_kernels.h"
+#include "trace.h"
 
 using lbm::StepParams;
 
@@ -656,6 +657,7 @@ int monitor_record(lbm_handle* h)
 
 int lbm_step(lbm_handle* h, int nsteps)
 {
+    trace::Range range("lbm_step");
     int rc = ensure_initialised(h);
     if (rc) return rc;
     if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
@@ -674,6 +676,7 @@ int lbm_step(lbm_handle* h, int nsteps)
 
 int lbm_step_flow(lbm_handle* h, int nsteps)
 {
+    trace::Range range("lbm_step_flow");
     int rc = ensure_initialised(h);
     if (rc) return rc;
     if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
@@ -1180,6 +1183,7 @@ int tips_now(lbm_handle* h, double cx, double cy, double orient, double tip[3])
 int lbm_surrogate_advance(lbm_handle* h, lbm_unet* net, int K, double tip_tol, int audit, double cx, double cy,
                           double orient, lbm_surrogate_report* rep)
 {
+    trace::Range range("lbm_surrogate_advance");
     int rc = ensure_initialised(h);
     if (rc) return rc;
     if (!net || !rep || K < 1) return fail(h, LBM_EINVAL, "need a network, a report and K >= 1");
@@ -1603,6 +1607,7 @@ int lbm_batch_init_seeds(lbm_batch* b, int dom, const lbm_seed* seeds, int n, do
 
 int lbm_batch_step(lbm_batch* b, int nsteps)
 {
+    trace::Range range("lbm_batch_step");
     int rc = batch_ready(b);
     if (rc) return rc;
     if (nsteps < 0) return bfail(b, LBM_EINVAL, "nsteps < 0");

@@ -32,6 +32,7 @@
 #include "lbm.h"
 #include "nn_kernels.h"
 #include "nn_layers.h"
+#include "trace.h"
 
 namespace {
 
@@ -717,6 +718,7 @@ int lbm_unet_load(lbm_unet* u, const char* path)
 
 int lbm_unet_forward(lbm_unet* u, const float* x, float* y)
 {
+    trace::Range range("lbm_unet_forward");
     if (!u || !x) return LBM_EINVAL;
     UN_CHECK(u, forward(u, x));
     if (y) UN_CHECK(u, nn::add_increment(u->Y, x, u->P0, u->F, u->inv_out, y, u->s));
@@ -725,6 +727,7 @@ int lbm_unet_forward(lbm_unet* u, const float* x, float* y)
 
 int lbm_unet_backward(lbm_unet* u, const float* x, const float* target)
 {
+    trace::Range range("lbm_unet_backward");
     if (!u || !x || !target) return LBM_EINVAL;
     UN_CHECK(u, allocate_backward(u));
     UN_CHECK(u, forward(u, x));
@@ -743,6 +746,7 @@ int lbm_unet_adam(lbm_unet* u, float lr, float beta1, float beta2, float eps)
 
 int lbm_unet_train_step(lbm_unet* u, const float* x, const float* target, float lr)
 {
+    trace::Range range("lbm_unet_train_step");
     int r = lbm_unet_backward(u, x, target);
     if (r != LBM_OK) return r;
     return lbm_unet_adam(u, lr, 0.9f, 0.999f, 1e-8f);
